@@ -1,0 +1,7 @@
+"""CPU FP64 oracle for the 2D elastic Lippmann-Schwinger operator and the distorted-Born products.
+
+TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's CPU-baseline leg use it.
+It shares no code with the CUDA library and imports nothing from it.
+"""
+from .dbi_oracle import *  # noqa: F401,F403
+from .dbi_oracle import LSOracle, normalized_error  # noqa: F401
