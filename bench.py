@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the batched hot path on the 256 x 256 VTI workload (32 sources x 8 frequencies).
+
+One step = one pass of the whole hot path over the batch: Green's tables for the 8 frequencies,
+incident fields, the batched complex64 BiCGSTAB forward solve of A u = u0 (every iteration two
+fused LS-operator passes), the data residual at the receivers, and the adjoint: conj(residual)
+injected at the receivers, convolved with G, solved in the background and imaged against u into
+the misfit gradient for (rho, C11, C13, C33, C55). The metric counts LS-operator cell-applies
+(cells x problems x operator passes, the Green's convolution of the adjoint source included) per
+second of wall time on the device.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own 32 sources x 8 frequencies
+(weak scaling) and the gradients are summed across ranks with one all-reduce per step.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2402_02116_gb300 import inputs  # noqa: E402
+
+METRIC = "LS operator cell-applies/s (cells x sources x frequencies)"
+UNIT = "cell-applies/s"
+TOL = 1e-5
+MAX_ITER = 3000
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle sample")
+    ap.add_argument("--no-plain", action="store_true", help="skip the complex128 plain-path sample")
+    return ap.parse_args()
+
+
+def workload(rank: int, world: int):
+    """The 256 x 256 VTI workload; with several ranks each gets its own 32 surface sources."""
+    w = inputs.config2_batched_forward()
+    if world > 1:
+        cols = inputs.surface_line(w.nx, 32 * world)[rank::world]
+        w.src_cells = np.stack([np.zeros_like(cols), cols], axis=1)
+    return w
+
+
+def config_dict(w, world):
+    return {"workload": w.name, "nz": w.nz, "nx": w.nx, "lz": w.lz, "lx": w.lx, "h_m": w.h,
+            "sources": w.n_src * world, "frequencies_hz": [round(float(f), 3) for f in w.freqs_hz],
+            "receivers": int(len(w.rec_cells)), "problems_per_gpu": w.n_problems,
+            "krylov": f"BiCGSTAB to {TOL:g} relative residual", "precision": "complex64 operator, FP64 reductions",
+            "step": "greens_tabulate + incident_field + ls_solve + data_residual + adjoint_apply (gradient)",
+            "l2": "inputs larger than L2: each wavefield batch is 256 MB (the L2 holds 129 MB)",
+            "parallelism": f"dp{world} (sources sharded, gradient all-reduce)" if world > 1 else "single GPU"}
+
+
+def synthetic_data(w, seed=7):
+    """Observed data of the same shape as the receiver data, at the scale of the incident field
+    (|d| ~ 1e-10 m for a unit force): seeded Gaussian."""
+    return inputs.seeded_complex((w.n_problems, len(w.rec_cells), 2), seed) * 1e-10
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index  # nvidia-smi --id: an index or a GPU UUID
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2402_02116_gb300 import build, dbi
+    from paper_2402_02116_gb300.problem import DeviceProblem
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    dbi.load()
+
+    w = workload(rank, world)
+    P = DeviceProblem(w, dbi.C64, device=dev)
+    d_obs_host = synthetic_data(w, seed=7 + rank)
+    d_obs = P.to_field(d_obs_host)
+    cells = w.nz * w.nx
+
+    def step(m, d_obs):
+        Ghat, Gspace = dbi.greens_tabulate(P.grid, P.ref, P.omega, dbi.C64)
+        u0 = dbi.incident_field(P.grid, P.omega, P.fidx, Gspace, P.src_cells, P.forces)
+        u, it_f, _, code_f = dbi.ls_solve(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u0, tol=TOL,
+                                          max_iter=MAX_ITER)
+        r, phi = dbi.data_residual(P.grid, P.omega, P.fidx, P.rec_cells, u, d_obs)
+        g, (it_a, _, code_a) = dbi.adjoint_apply(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u, P.rec_cells, r,
+                                                 tol=TOL, max_iter=MAX_ITER, with_status=True)
+        if world > 1:
+            dist.all_reduce(g)
+        return phi, g, it_f, it_a, code_f, code_a
+
+    def applies(it_f, it_a):
+        # two operator passes per BiCGSTAB iteration, plus the adjoint source's convolution
+        return int(2 * it_f.sum().item() + 2 * it_a.sum().item() + it_a.numel())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        out = step(P.m, d_obs)
+    barrier()
+    ok = bool((out[4] == dbi.CONVERGED).all().item() and (out[5] == dbi.CONVERGED).all().item())
+
+    # timed region: device events on the launching stream, barrier + synchronize on both sides
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_applies = 0
+    launches0 = dbi.kernel_launches()
+    dbi.profile_begin(dbi.PROF_COLS)
+    with ClockSampler(gpu_id(dev)) as clk:
+        barrier()
+        ev0.record(stream)
+        per_step = []
+        for _ in range(args.steps):
+            phi, g, it_f, it_a, code_f, code_a = step(P.m, d_obs)
+            per_step.append((it_f, it_a))
+        ev1.record(stream)
+        barrier()
+    cols_ms, cols_launches = dbi.profile_end()
+    launches = dbi.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    for it_f, it_a in per_step:
+        total_applies += applies(it_f, it_a)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    a = torch.tensor([total_applies], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    job_applies = float(a.item())
+    value = job_applies * cells / (ms_max * 1e-3)
+    ok = ok and bool((code_f == dbi.CONVERGED).all().item() and (code_a == dbi.CONVERGED).all().item())
+
+    # roofline of the column-pass kernel (the largest share of the step's device time)
+    peaks = load_peaks()
+    rank_applies = total_applies
+    cols_algo_bytes = cols_bytes_per_cell_apply(w) * cells * rank_applies
+    cols_flops = cols_flops_per_cell_apply(w) * cells * rank_applies
+    cols_s = cols_ms * 1e-3
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6  # FMA lanes x 2 flop x measured SM clock
+    hbm_peak = peaks.get("hbm_gbs", 6800.0) * 1e9
+    t_hbm, t_alu = cols_algo_bytes / hbm_peak, cols_flops / fp32_peak
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": cols_flops / cols_s / 1e12, "peak": fp32_peak / 1e12,
+                "unit": "TFLOP/s", "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured median)"}
+    else:
+        roof = {"bound": "hbm", "achieved": cols_algo_bytes / cols_s / 1e9, "peak": hbm_peak / 1e9,
+                "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = "k_cols (column FFTs x Green's tensor x inverse column FFTs)"
+    roof["traffic"] = None
+    roof["hbm_frac_of_algorithmic_bytes"] = cols_algo_bytes / cols_s / hbm_peak
+    roof["launches_timed"] = cols_launches
+    roof["avg_launch_ms"] = cols_ms / max(cols_launches, 1)
+    roof["share_of_step_time"] = cols_ms / ms if ms > 0 else None
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    e2e = run_e2e(args, P, step, d_obs_host, w, world, dev, barrier, applies)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 (fp32 complex operator; fp64 inner products and scalars)",
+        "data": "synthetic (seeded VTI model with layers and anomalies; seeded observed data)",
+        "config": config_dict(w, world),
+        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / args.steps, "clocks": clocks,
+        "all_converged": ok,
+        "krylov_iterations_per_step": {"forward_mean": float(per_step[-1][0].float().mean()),
+                                       "adjoint_mean": float(per_step[-1][1].float().mean())},
+    }
+    if rank == 0 and world == 1 and not args.no_plain:
+        result["plain_c128"] = plain_c128_sample(w, dev, cells, value)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = oracle_samples(w, [0, w.n_problems // 2 + 3, w.n_problems - 1])
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def gpu_id(dev):
+    """nvidia-smi id of the device: its UUID when torch exposes it, else the visible index."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[dev.index] if vis else str(dev.index)
+
+
+def run_e2e(args, P, step, d_obs_host, w, world, dev, barrier, applies):
+    """Same step, with the model and observed data copied from pinned host memory each step and
+    the gradient and misfit read back."""
+    import torch
+    m_host = torch.as_tensor(np.asarray(w.model, dtype=np.float32)).pin_memory()
+    d_host = torch.as_tensor(np.asarray(d_obs_host, dtype=np.complex64)).pin_memory()
+    g_host = torch.empty((5, w.nz, w.nx), dtype=torch.float32).pin_memory()
+    phi_host = torch.empty((), dtype=torch.float64).pin_memory()
+    m_dev = torch.empty(m_host.shape, dtype=torch.float32, device=dev)
+    d_dev = torch.empty(d_host.shape, dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    its = []
+    for _ in range(args.steps):
+        m_dev.copy_(m_host, non_blocking=True)
+        d_dev.copy_(d_host, non_blocking=True)
+        phi, g, it_f, it_a, _, _ = step(m_dev, d_dev)
+        g_host.copy_(g, non_blocking=True)
+        phi_host.copy_(phi, non_blocking=True)
+        its.append((it_f, it_a))
+    ev1.record(stream)
+    barrier()
+    total = sum(applies(it_f, it_a) for it_f, it_a in its)
+    ms = ev0.elapsed_time(ev1)
+    cells = w.nz * w.nx
+    h2d = m_host.numel() * 4 + d_host.numel() * 8
+    d2h = g_host.numel() * 4 + 8
+    return {"value": total * world * cells / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms / args.steps,
+            "api": "dbi.greens_tabulate/incident_field/ls_solve/data_residual/adjoint_apply"}
+
+
+def plain_c128_sample(w, dev, cells, value_c64):
+    """The plain unbatched complex128 path (same kernels, one problem per call, FP64 throughout)
+    on a sample of the problems: per-problem forward + adjoint time, scaled to the batch."""
+    import torch
+
+    from paper_2402_02116_gb300 import dbi
+    from paper_2402_02116_gb300.problem import DeviceProblem
+    P = DeviceProblem(w, dbi.C128, device=dev)
+    d_obs = P.to_field(synthetic_data(w))
+    sample = [0, w.n_problems // 2 + 3, w.n_problems - 1]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot_ms, tot_applies = 0.0, 0
+    for b in sample:
+        fidx = P.fidx[b:b + 1].contiguous()
+        src, frc = P.src_cells[b:b + 1].contiguous(), P.forces[b:b + 1].contiguous()
+        torch.cuda.synchronize()
+        ev0.record()
+        Ghat, Gspace = dbi.greens_tabulate(P.grid, P.ref, P.omega, dbi.C128)
+        u0 = dbi.incident_field(P.grid, P.omega, fidx, Gspace, src, frc)
+        u, it_f, _, _ = dbi.ls_solve(P.grid, P.ref, P.m, P.omega, fidx, Ghat, u0, tol=TOL, max_iter=MAX_ITER)
+        r, phi = dbi.data_residual(P.grid, P.omega, fidx, P.rec_cells, u, d_obs[b:b + 1].contiguous())
+        g, (it_a, _, _) = dbi.adjoint_apply(P.grid, P.ref, P.m, P.omega, fidx, Ghat, u, P.rec_cells, r, tol=TOL,
+                                            max_iter=MAX_ITER, with_status=True)
+        ev1.record()
+        torch.cuda.synchronize()
+        tot_ms += ev0.elapsed_time(ev1)
+        tot_applies += int(2 * it_f.sum() + 2 * it_a.sum() + 1)
+    rate = tot_applies * cells / (tot_ms * 1e-3)
+    return {"value": rate, "unit": UNIT, "sample": f"problems {sample} of the batch, one per call",
+            "ms_per_problem_gradient": tot_ms / len(sample),
+            "est_ms_per_step": tot_ms / len(sample) * w.n_problems,
+            "speedup_c64_batched": value_c64 / rate}
+
+
+# ---------------------------------------------------------------------------------------------
+# roofline arithmetic of the column pass (per D-cell per operator pass)
+# ---------------------------------------------------------------------------------------------
+def cols_bytes_per_cell_apply(w):
+    """Compulsory bytes of k_cols: the row-transformed field T[2][nz][lx] read once and written
+    once (complex64), plus the Green's spectrum [3][lz][lx] read once per frequency and shared by
+    the sources of that frequency."""
+    cells = w.nz * w.nx
+    t = 2 * 2 * w.nz * w.lx * 8
+    g = 3 * w.lz * w.lx * 8 * w.nf / w.n_problems
+    return (t + g) / cells
+
+
+def cols_flops_per_cell_apply(w):
+    """Nominal flops of k_cols: 5 L log2 L per complex FFT of length lz (2 components, forward
+    and inverse, lx columns) plus the symmetric 2x2 complex multiply (4 complex products and 2
+    sums, 28 flops) at each of the lz x lx wavenumbers."""
+    cells = w.nz * w.nx
+    fft = 2 * 2 * w.lx * 5 * w.lz * math.log2(w.lz)
+    mult = 28 * w.lz * w.lx
+    return (fft + mult) / cells
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+
+
+# ---------------------------------------------------------------------------------------------
+# the FP64 CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------------------------
+def oracle_samples(w, problems):
+    """oracle_sample over several problems, merged into one rate."""
+    res = [oracle_sample(w, b) for b in problems]
+    sec = sum(r["seconds"] for r in res)
+    applies = sum(r["value"] * r["seconds"] for r in res)
+    return {"value": applies / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": " | ".join(r["sample"] for r in res), "seconds": sec}
+
+
+def oracle_sample(w, problems=None):
+    """One gradient contribution (forward solve, residual, adjoint solve, imaging) of one problem
+    of the workload, by the FP64 CPU oracle as it stands (numpy, one core)."""
+    import oracle as O
+    b = w.n_problems // 2 + 3 if problems is None else problems
+    f = int(w.problem_fidx()[b])
+    s = int(w.problem_src()[b])
+    t0 = time.perf_counter()
+    orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
+    u0 = orc.incident(0, w.src_cells[s], w.src_force[s])
+    u, info_f = orc.solve_info(u0, w.model, 0, tol=TOL)
+    r = orc.sample(u, w.rec_cells) - synthetic_data(w)[b]
+    q = orc.inject(np.conj(r), w.rec_cells)
+    ua, info_a = orc.solve_info(orc.convolve(q, 0), w.model, 0, tol=TOL)
+    orc.imaging(ua, u, orc.omegas[0], orc.h)
+    dt = time.perf_counter() - t0
+    # the oracle's solve_info applies A once more to report the true residual
+    applies = 2 * info_f["iters"] + 1 + 2 * info_a["iters"] + 1 + 1
+    return {"value": applies * w.nz * w.nx / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"problem {b} (source {s}, {w.freqs_hz[f]:.2f} Hz) of {w.name}: forward solve, residual, "
+                      f"adjoint solve, imaging; {applies} operator passes in {dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(0, 1)
+    # each step is one problem's gradient contribution (a bounded sample of the batch)
+    problems = [w.n_problems // 2 + 3, 0, w.n_problems - 1]
+    if args.warmup > 0:  # one untimed sample warms numpy/scipy; more would only add minutes
+        oracle_sample(w, problems[0])
+    t_applies, t_sec = 0.0, 0.0
+    samples = []
+    for k in range(args.steps):
+        res = oracle_sample(w, problems[k % len(problems)])
+        t_applies += res["value"] * res["seconds"]
+        t_sec += res["seconds"]
+        samples.append(res["sample"])
+    value = t_applies / t_sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_sec / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)",
+            "data": "synthetic", "config": config_dict(w, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": "one problem's gradient contribution per step (FP64 numpy oracle): "
+                                       + "; ".join(samples[:3])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

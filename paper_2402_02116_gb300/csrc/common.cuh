@@ -1,0 +1,100 @@
+// Shared types, complex arithmetic and error reporting of the DBI library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/dbi.h"
+
+namespace dbi {
+
+// ---------------------------------------------------------------------------------------------
+// complex helpers on float2 / double2 (interleaved re, im)
+// ---------------------------------------------------------------------------------------------
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { using type = float; };
+template <> struct RealOf<double2> { using type = double; };
+
+template <typename C> __host__ __device__ __forceinline__ C mk(typename RealOf<C>::type re,
+                                                                 typename RealOf<C>::type im) {
+  C c; c.x = re; c.y = im; return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cscale(C a, typename RealOf<C>::type s) {
+  return mk<C>(a.x * s, a.y * s);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk<C>(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse)
+template <typename C, bool INV> __device__ __forceinline__ C mul_mi(C a) {
+  return INV ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+template <typename C> __device__ __forceinline__ C czero() { return mk<C>(0, 0); }
+
+// ---------------------------------------------------------------------------------------------
+// sizes and launch helpers
+// ---------------------------------------------------------------------------------------------
+constexpr int kTwiddleN = 3072;  // W_3072^m covers every FFT length that divides 3072
+
+inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+inline bool fft_len_ok(int L) {
+  return L >= 16 && L <= 1024 && (L & (L - 1)) == 0;
+}
+
+// Error reporting (per host thread).
+void set_error(const char *fmt, ...);
+void clear_error();
+int cuda_fail(const char *what, cudaError_t e);
+// Checks the last launch and counts it (every kernel launch is followed by exactly one call).
+int check_launch(const char *what);
+
+// Event timing of one operator stage on its launching stream (see dbi_profile_begin).
+enum { PROF_NONE = 0, PROF_ROWS_FORWARD = 1, PROF_COLS = 2, PROF_ROWS_INVERSE = 3, PROF_OPERATOR = 4 };
+void prof_mark(int stage, bool after, cudaStream_t s);
+
+// Validation shared by the entry points.
+int check_grid(const dbi_grid *g);
+int check_batch(const dbi_batch *b);
+int check_precision(int precision);
+
+// Twiddle table W_3072^m, m in [0, 3072), in the precision's complex type (written into `tw`).
+int launch_twiddles(void *tw, int precision, cudaStream_t s);
+
+// A bump allocator over the caller's work buffer.
+struct Arena {
+  char *base;
+  size_t cap;
+  size_t used = 0;
+  Arena(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
+  void *take(size_t n) {
+    size_t off = used;
+    used += align256(n);
+    return (base && used <= cap) ? base + off : nullptr;
+  }
+};
+
+// Sizes of the buffers each operation carves out of the work buffer (see workspace.cu).
+size_t bytes_twiddles(int precision);
+size_t bytes_spectral(const dbi_grid *g, int B, int precision);
+size_t bytes_field(const dbi_grid *g, int B, int precision);
+size_t bytes_partials(int B);
+
+// Geometry of the FP64 partial sums of the Krylov reductions.
+constexpr int kRedBlocks = 64;    // blocks per problem in a reduction pass
+constexpr int kRedThreads = 256;  // threads per reduction block
+constexpr int kRedSlots = 4;      // doubles per block partial
+
+}  // namespace dbi

@@ -1,0 +1,262 @@
+// Green's tensor tables (Appendix A, Eq. A-3, A-4) and the incident field (Eq. 7).
+//
+// greens_tabulate evaluates the 2D isotropic Green's tensor
+//   G_ij(y) = 1/(8 i rho) [A delta_ij - B (2 g_i g_j - delta_ij)],
+//   A = H0(w r/alpha)/alpha^2 + H0(w r/beta)/beta^2,  B = H2(w r/alpha)/alpha^2 - H2(w r/beta)/beta^2,
+// H_n = J_n - i Y_n (second kind, outgoing for exp(+i w t)), in FP64 at the cell-centre offsets
+// (dx h, dz h), |dz| < nz, |dx| < nx, placed at slot (dz mod lz, dx mod lx). The self cell takes
+// the mean of G over the disk of radius h / sqrt(pi): only A survives the angular mean, and
+// the disk mean of H0(k r) is 2 H1(k a)/(k a) - 4i/(pi k^2 a^2). The table is then transformed by
+// an FP64 2D FFT (rows, then columns) and scaled by h^2 / (lz lx), which folds the quadrature
+// weight and the inverse-FFT normalisation of Eq. 12 into it.
+#include <cmath>
+
+#include "fft.cuh"
+#include "operator.cuh"
+
+namespace dbi {
+
+// H_n^(2)(z) = J_n(z) - i Y_n(z), n = 0, 1, 2 (n = 2 by the recurrence H2 = (2/z) H1 - H0).
+__device__ __forceinline__ void hankel2_012(double z, double2 &h0, double2 &h1, double2 &h2) {
+  h0 = make_double2(j0(z), -y0(z));
+  h1 = make_double2(j1(z), -y1(z));
+  h2 = make_double2(2.0 * h1.x / z - h0.x, 2.0 * h1.y / z - h0.y);
+}
+
+__device__ __forceinline__ double2 times_inv_8i_rho(double2 v, double rho) {
+  // v / (8 i rho) = -i v / (8 rho)
+  const double s = 1.0 / (8.0 * rho);
+  return make_double2(v.y * s, -v.x * s);
+}
+
+__device__ void green_offset(double y1, double y3, double omega, double alpha, double beta,
+                             double rho, double2 &g11, double2 &g13, double2 &g33) {
+  const double r = hypot(y1, y3);
+  const double c1 = y1 / r, c3 = y3 / r;
+  double2 h0a, h1a, h2a, h0b, h1b, h2b;
+  hankel2_012(omega * r / alpha, h0a, h1a, h2a);
+  hankel2_012(omega * r / beta, h0b, h1b, h2b);
+  const double ia2 = 1.0 / (alpha * alpha), ib2 = 1.0 / (beta * beta);
+  const double2 A = make_double2(h0a.x * ia2 + h0b.x * ib2, h0a.y * ia2 + h0b.y * ib2);
+  const double2 B = make_double2(h2a.x * ia2 - h2b.x * ib2, h2a.y * ia2 - h2b.y * ib2);
+  const double q11 = 2.0 * c1 * c1 - 1.0, q33 = 2.0 * c3 * c3 - 1.0, q13 = 2.0 * c1 * c3;
+  g11 = times_inv_8i_rho(make_double2(A.x - B.x * q11, A.y - B.y * q11), rho);
+  g33 = times_inv_8i_rho(make_double2(A.x - B.x * q33, A.y - B.y * q33), rho);
+  g13 = times_inv_8i_rho(make_double2(-B.x * q13, -B.y * q13), rho);
+}
+
+__device__ double2 green_self(double h, double omega, double alpha, double beta, double rho) {
+  const double a = h / sqrt(M_PI);
+  double2 tot = make_double2(0.0, 0.0);
+  const double cs[2] = {alpha, beta};
+  for (int i = 0; i < 2; ++i) {
+    const double k = omega / cs[i], ka = k * a;
+    const double2 h1 = make_double2(j1(ka), -y1(ka));
+    // 2 H1(ka)/(ka) - 4 i / (pi k^2 a^2)
+    const double2 mean = make_double2(2.0 * h1.x / ka, 2.0 * h1.y / ka - 4.0 / (M_PI * ka * ka));
+    const double ic2 = 1.0 / (cs[i] * cs[i]);
+    tot.x += mean.x * ic2;
+    tot.y += mean.y * ic2;
+  }
+  return times_inv_8i_rho(tot, rho);
+}
+
+// Offset held by slot i of a length-L periodic axis for a domain of n cells, or INT_MIN for a gap.
+__device__ __forceinline__ int slot_offset(int i, int n, int L) {
+  if (i <= n - 1) return i;
+  if (i >= L - (n - 1)) return i - L;
+  return -0x7fffffff;
+}
+
+template <typename C>
+__global__ void k_green_space(int nz, int nx, int lz, int lx, double h, const double *omega,
+                              double rho, double alpha, double beta, double2 *W, C *Gspace) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iz = blockIdx.y;
+  const int f = blockIdx.z;
+  if (ix >= lx) return;
+  const int dz = slot_offset(iz, nz, lz), dx = slot_offset(ix, nx, lx);
+  double2 g11 = make_double2(0, 0), g13 = g11, g33 = g11;
+  if (dz != -0x7fffffff && dx != -0x7fffffff) {
+    const double w = omega[f];
+    if (dz == 0 && dx == 0) {
+      g11 = g33 = green_self(h, w, alpha, beta, rho);
+    } else {
+      green_offset(dx * h, dz * h, w, alpha, beta, rho, g11, g13, g33);
+    }
+  }
+  const size_t plane = size_t(lz) * lx, cell = size_t(iz) * lx + ix, base = size_t(f) * 3 * plane;
+  W[base + cell] = g11;
+  W[base + plane + cell] = g13;
+  W[base + 2 * plane + cell] = g33;
+  if (Gspace) {
+    using R = typename RealOf<C>::type;
+    Gspace[base + cell] = mk<C>(R(g11.x), R(g11.y));
+    Gspace[base + plane + cell] = mk<C>(R(g13.x), R(g13.y));
+    Gspace[base + 2 * plane + cell] = mk<C>(R(g33.x), R(g33.y));
+  }
+}
+
+// In-place FP64 FFT of NL contiguous lines of length L per block.
+template <int L>
+__global__ void __launch_bounds__(256) k_fft_rows64(double2 *data, long nlines, const double2 *tw) {
+  constexpr int NL = 2048 / L > 0 ? 2048 / L : 1, LS = L + 1, NT = NL * L / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *s = reinterpret_cast<double2 *>(smem_raw);
+  const long l0 = long(blockIdx.x) * NL;
+  for (int idx = threadIdx.x; idx < NL * L; idx += NT) {
+    const int l = idx / L, k = idx - l * L;
+    s[l * LS + k] = (l0 + l < nlines) ? data[(l0 + l) * L + k] : make_double2(0, 0);
+  }
+  __syncthreads();
+  Plan<L>::template run<double2, NL, LS, NT, false>(s, tw);
+  for (int idx = threadIdx.x; idx < NL * L; idx += NT) {
+    const int l = idx / L, k = idx - l * L;
+    if (l0 + l < nlines) data[(l0 + l) * L + k] = s[l * LS + k];
+  }
+}
+
+// In-place FP64 FFT along the columns of row-major [L][width] matrices; CC columns per block,
+// matrix blockIdx.y.
+template <int L>
+__global__ void __launch_bounds__(256) k_fft_cols64(double2 *data, int width, const double2 *tw) {
+  constexpr int CC = 2048 / L > 0 ? 2048 / L : 1, LS = L + 1, NT = CC * L / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *s = reinterpret_cast<double2 *>(smem_raw);
+  double2 *M = data + size_t(blockIdx.y) * L * width;
+  const int c0 = blockIdx.x * CC;
+  for (int idx = threadIdx.x; idx < CC * L; idx += NT) {
+    const int z = idx / CC, j = idx - z * CC;
+    s[j * LS + z] = (c0 + j < width) ? M[size_t(z) * width + c0 + j] : make_double2(0, 0);
+  }
+  __syncthreads();
+  Plan<L>::template run<double2, CC, LS, NT, false>(s, tw);
+  for (int idx = threadIdx.x; idx < CC * L; idx += NT) {
+    const int z = idx / CC, j = idx - z * CC;
+    if (c0 + j < width) M[size_t(z) * width + c0 + j] = s[j * LS + z];
+  }
+}
+
+template <typename C>
+__global__ void k_scale_cast(const double2 *W, C *Ghat, size_t n, double scale) {
+  using R = typename RealOf<C>::type;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    Ghat[i] = mk<C>(R(W[i].x * scale), R(W[i].y * scale));
+}
+
+template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
+static int fft2_fp64(double2 *W, int nmat, int lz, int lx, const double2 *tw, cudaStream_t s) {
+  int rc = DBI_OK;
+  dispatch_len(lx, [&]<int L>() {
+    constexpr int NL = 2048 / L > 0 ? 2048 / L : 1, LS = L + 1, NT = NL * L / 8;
+    const size_t bytes = size_t(NL) * LS * sizeof(double2);
+    const long nlines = long(nmat) * lz;
+    cudaError_t e = allow_smem(k_fft_rows64<L>, bytes);
+    if (e == cudaSuccess) k_fft_rows64<L><<<unsigned((nlines + NL - 1) / NL), NT, bytes, s>>>(W, nlines, tw);
+    rc = e != cudaSuccess ? cuda_fail("k_fft_rows64 smem", e) : check_launch("k_fft_rows64");
+  });
+  if (rc) return rc;
+  dispatch_len(lz, [&]<int L>() {
+    constexpr int CC = 2048 / L > 0 ? 2048 / L : 1, LS = L + 1, NT = CC * L / 8;
+    const size_t bytes = size_t(CC) * LS * sizeof(double2);
+    cudaError_t e = allow_smem(k_fft_cols64<L>, bytes);
+    dim3 grid((lx + CC - 1) / CC, nmat);
+    if (e == cudaSuccess) k_fft_cols64<L><<<grid, NT, bytes, s>>>(W, lx, tw);
+    rc = e != cudaSuccess ? cuda_fail("k_fft_cols64 smem", e) : check_launch("k_fft_cols64");
+  });
+  return rc;
+}
+
+// Problems whose source cell or frequency index is out of range get u0 = 0.
+template <typename C>
+__global__ void k_incident(int B, int nf, int nz, int nx, int lz, int lx, const int *fidx, const C *Gspace,
+                           const int *src_cells, const double *forces, C *u0) {
+  using R = typename RealOf<C>::type;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int z = blockIdx.y;
+  const int b = blockIdx.z;
+  if (x >= nx) return;
+  const int zs = src_cells[2 * b], xs = src_cells[2 * b + 1];
+  const size_t o = size_t(b) * 2 * nz * nx + size_t(z) * nx + x;
+  if (zs < 0 || zs >= nz || xs < 0 || xs >= nx || unsigned(fidx[b]) >= unsigned(nf)) {
+    u0[o] = czero<C>();
+    u0[o + size_t(nz) * nx] = czero<C>();
+    return;
+  }
+  int dz = z - zs, dx = x - xs;
+  dz = dz < 0 ? dz + lz : dz;
+  dx = dx < 0 ? dx + lx : dx;
+  const size_t plane = size_t(lz) * lx, cell = size_t(dz) * lx + dx;
+  const C *G = Gspace + size_t(fidx[b]) * 3 * plane;
+  const C g11 = G[cell], g13 = G[plane + cell], g33 = G[2 * plane + cell];
+  const R f1 = R(forces[2 * b]), f3 = R(forces[2 * b + 1]);
+  u0[o] = cadd(cscale(g11, f1), cscale(g13, f3));
+  u0[o + size_t(nz) * nx] = cadd(cscale(g13, f1), cscale(g33, f3));
+}
+
+}  // namespace dbi
+
+using namespace dbi;
+
+extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const double *omega,
+                               int nf, int precision, void *Ghat, void *Gspace, void *work,
+                               size_t work_bytes, dbi_stream stream) {
+  clear_error();
+  int rc;
+  if ((rc = check_grid(g)) || (rc = check_precision(precision))) return rc;
+  if (!ref || !(ref->rho0 > 0) || !(ref->alpha0 > 0) || !(ref->beta0 > 0) || !(ref->alpha0 > ref->beta0)) {
+    set_error("reference medium needs rho0 > 0 and alpha0 > beta0 > 0");
+    return DBI_ERR_ARG;
+  }
+  if (nf < 1 || !omega || !Ghat) { set_error("need nf >= 1, omega and Ghat"); return DBI_ERR_ARG; }
+  const size_t need = dbi_workspace_bytes(g, nf, precision, DBI_OP_GREENS);
+  if (!work || work_bytes < need) {
+    set_error("work buffer of %zu bytes, need %zu", work_bytes, need);
+    return DBI_ERR_WORKSPACE;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Arena ar(work, work_bytes);
+  double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
+  double2 *W = static_cast<double2 *>(ar.take(size_t(nf) * 3 * g->lz * g->lx * sizeof(double2)));
+  if ((rc = launch_twiddles(tw, DBI_C128, s))) return rc;
+  dim3 grid((g->lx + 127) / 128, g->lz, nf);
+  if (precision == DBI_C64)
+    k_green_space<float2><<<grid, 128, 0, s>>>(g->nz, g->nx, g->lz, g->lx, g->h, omega, ref->rho0,
+                                               ref->alpha0, ref->beta0, W, static_cast<float2 *>(Gspace));
+  else
+    k_green_space<double2><<<grid, 128, 0, s>>>(g->nz, g->nx, g->lz, g->lx, g->h, omega, ref->rho0,
+                                                ref->alpha0, ref->beta0, W, static_cast<double2 *>(Gspace));
+  if ((rc = check_launch("k_green_space"))) return rc;
+  if ((rc = fft2_fp64(W, 3 * nf, g->lz, g->lx, tw, s))) return rc;
+  const size_t n = size_t(nf) * 3 * g->lz * g->lx;
+  const double scale = g->h * g->h / (double(g->lz) * double(g->lx));
+  const int blocks = int((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (precision == DBI_C64) k_scale_cast<float2><<<blocks, 256, 0, s>>>(W, static_cast<float2 *>(Ghat), n, scale);
+  else k_scale_cast<double2><<<blocks, 256, 0, s>>>(W, static_cast<double2 *>(Ghat), n, scale);
+  return check_launch("k_scale_cast");
+}
+
+extern "C" int incident_field(const dbi_grid *g, const dbi_batch *batch, const void *Gspace,
+                              const int *src_cells, const double *forces, void *u0, int precision,
+                              dbi_stream stream) {
+  clear_error();
+  int rc;
+  if ((rc = check_grid(g)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
+  if (batch->B == 0) return DBI_OK;
+  if (!Gspace || !src_cells || !forces || !u0) { set_error("NULL Gspace, sources, forces or u0"); return DBI_ERR_ARG; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  dim3 grid((g->nx + 127) / 128, g->nz, batch->B);
+  if (precision == DBI_C64)
+    k_incident<float2><<<grid, 128, 0, s>>>(batch->B, batch->nf, g->nz, g->nx, g->lz, g->lx, batch->fidx,
+                                            static_cast<const float2 *>(Gspace), src_cells, forces,
+                                            static_cast<float2 *>(u0));
+  else
+    k_incident<double2><<<grid, 128, 0, s>>>(batch->B, batch->nf, g->nz, g->nx, g->lz, g->lx, batch->fidx,
+                                             static_cast<const double2 *>(Gspace), src_cells, forces,
+                                             static_cast<double2 *>(u0));
+  return check_launch("k_incident");
+}

@@ -1,0 +1,490 @@
+// Batched BiCGSTAB for the LS equation A u = u0 (Eq. 11), one independent system per
+// (source, frequency) problem.
+//
+// Per iteration i (van der Vorst's BiCGSTAB, <a, b> = sum conj(a) b):
+//   p = r + beta (p - omega v)                  k_update_p      (beta from the previous k_check)
+//   v = A p                                     operator
+//   sigma = <rhat, v>                           k_dot           (FP64 partial sums)
+//   alpha = rho / sigma, s = r - alpha v        k_update_s      (+ partials of ||s||^2)
+//   t = A s                                     operator
+//   <t, s>, <t, t>                              k_dot2
+//   omega = <t,s>/<t,t>, x += alpha p + omega s, r = s - omega t   k_update_xr (+ <rhat, r>, ||r||^2)
+//   convergence, breakdown, beta = (rho_new / rho)(alpha / omega)  k_check
+// Every scalar lives on the device in FP64. Each reduction is two-stage and deterministic: each
+// thread sums its elements, the CTA sums its threads in a fixed tree, and every consumer sums the
+// kRedBlocks CTA partials of its problem in the same fixed order. Converged problems drop out
+// (their CTAs return at once); the host polls an active-problem counter every check_every
+// iterations. A breakdown (rho or omega vanishing) restarts the problem from its iterate.
+#include <cmath>
+
+#include "krylov.cuh"
+
+namespace dbi {
+
+template <typename C> struct Acc;                         // per-thread accumulation type
+template <> struct Acc<float2> { using type = float; };   // short per-thread sums, then FP64
+template <> struct Acc<double2> { using type = double; };
+
+// Sum NS values over the CTA (fixed order); thread 0 stores them to out[0..NS).
+template <int NS> __device__ __forceinline__ void block_sum_store(double (&v)[NS], double *out) {
+  __shared__ double sh[NS][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    double a = v[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+    if (lane == 0) sh[k][warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < kRedThreads / 32; ++w) a += sh[k][w];
+      out[k] = a;
+    }
+  }
+}
+
+// Sum slot k (k < NS) of the kRedBlocks partials of one problem; every thread gets the result.
+template <int NS> __device__ __forceinline__ void gather(const double *part, double (&out)[NS]) {
+  static_assert(kRedBlocks == 64, "gather assumes 64 partials");
+  __shared__ double sh[NS];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      double a = part[lane * kRedSlots + k] + part[(lane + 32) * kRedSlots + k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+      if (lane == 0) sh[k] = a;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NS; ++k) out[k] = sh[k];
+}
+
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C from_z(double2 z) {
+  using R = typename RealOf<C>::type;
+  return mk<C>(R(z.x), R(z.y));
+}
+
+#define DBI_PROBLEM_LOOP(n)                                                                   \
+  const int b = blockIdx.y;                                                                   \
+  const size_t off = size_t(b) * (n);                                                         \
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < (n); i += size_t(gridDim.x) * blockDim.x)
+
+// ||rhs||^2 with every square formed in FP64: the right-hand side may lie far from unit scale
+// (a data residual of 1e-12 back-propagates to fields of 1e-21), where FP32 squares underflow.
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_bnorm(size_t n, const C *rhs, double *part) {
+  double bb = 0.0;
+  DBI_PROBLEM_LOOP(n) {
+    const C bi = rhs[off + i];
+    const double x = bi.x, y = bi.y;
+    bb += x * x + y * y;
+  }
+  double acc[1] = {bb};
+  block_sum_store<1>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+}
+
+// Power-of-two scale per problem that brings ||rhs|| into [1, 2); the solver iterates on the
+// scaled system (exact in any precision) and unscales the solution at the end.
+__global__ void k_scale(KState *st, const double *part) {
+  double s[1];
+  gather<1>(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, s);
+  if (threadIdx.x == 0) st[blockIdx.x].scale = s[0] > 0.0 ? ldexp(1.0, -ilogb(sqrt(s[0]))) : 1.0;
+}
+
+// x *= scale (inverse = 0) or x /= scale (inverse = 1)
+template <typename C>
+__global__ void k_scale_x(size_t n, const KState *st, C *x, int inverse) {
+  using R = typename RealOf<C>::type;
+  const double sc = st[blockIdx.y].scale;
+  const R f = R(inverse ? 1.0 / sc : sc);
+  DBI_PROBLEM_LOOP(n) x[off + i] = cscale(x[off + i], f);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_init(size_t n, const KState *st, const C *rhs, C *v, C *r,
+                                                      C *rhat, C *p, C *x, int x_zero, double *part) {
+  using A = typename Acc<C>::type;
+  using R = typename RealOf<C>::type;
+  const R sc = R(st[blockIdx.y].scale);
+  A bb = 0, rr = 0;
+  DBI_PROBLEM_LOOP(n) {
+    const C bi = cscale(rhs[off + i], sc);
+    const C ax = x_zero ? czero<C>() : v[off + i];
+    const C ri = csub(bi, ax);
+    r[off + i] = ri;
+    rhat[off + i] = ri;
+    p[off + i] = czero<C>();
+    v[off + i] = czero<C>();
+    if (x_zero) x[off + i] = czero<C>();
+    bb += bi.x * bi.x + bi.y * bi.y;
+    rr += ri.x * ri.x + ri.y * ri.y;
+  }
+  double acc[2] = {double(bb), double(rr)};
+  block_sum_store<2>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_init_state(KState *st, int *active, int *counters, const double *part, double tol,
+                             int max_iter) {
+  const int b = blockIdx.x;
+  double s[2];
+  gather<2>(part + size_t(b) * kRedBlocks * kRedSlots, s);
+  if (threadIdx.x == 0) {
+    KState k{};
+    k.scale = st[b].scale;
+    k.bnorm2 = s[0];
+    k.rnorm2 = s[1];
+    k.rho_re = s[1]; k.rho_im = 0.0;  // rhat = r
+    k.alpha_re = 1.0; k.om_re = 1.0;
+    k.beta_re = 0.0; k.beta_im = 0.0;  // p = r on the first iteration (p = v = 0)
+    k.rhatnorm2 = s[1];
+    k.zero_rhs = s[0] == 0.0;
+    const bool conv = k.zero_rhs || s[1] <= tol * tol * s[0];
+    k.code = conv ? DBI_CONVERGED : DBI_NOT_CONVERGED;
+    st[b] = k;
+    const int act = (!conv && max_iter > 0) ? 1 : 0;
+    active[b] = act;
+    atomicAdd(&counters[1], act);
+  }
+}
+
+template <typename C>
+__global__ void k_zero_flagged(size_t n, const KState *st, C *x) {
+  if (!st[blockIdx.y].zero_rhs) return;
+  DBI_PROBLEM_LOOP(n) x[off + i] = czero<C>();
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const KState *st, const int *active,
+                                                          int *counters, int parity, const C *r,
+                                                          C *rhat, C *p, const C *v) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[parity] = 0;
+  if (!active[blockIdx.y]) return;
+  const KState k = st[blockIdx.y];
+  if (k.restart) {
+    DBI_PROBLEM_LOOP(n) {
+      const C ri = r[off + i];
+      rhat[off + i] = ri;
+      p[off + i] = ri;
+    }
+    return;
+  }
+  const C be = from_z<C>(make_double2(k.beta_re, k.beta_im));
+  const C om = from_z<C>(make_double2(k.om_re, k.om_im));
+  DBI_PROBLEM_LOOP(n) {
+    const C pv = csub(p[off + i], cmul(om, v[off + i]));
+    p[off + i] = cadd(r[off + i], cmul(be, pv));
+  }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_dot(size_t n, const int *active, const C *a,
+                                                     const C *bv, double *part) {
+  using A = typename Acc<C>::type;
+  if (!active[blockIdx.y]) return;
+  A re = 0, im = 0;
+  DBI_PROBLEM_LOOP(n) {
+    const C x = a[off + i], y = bv[off + i];
+    re += x.x * y.x + x.y * y.y;  // conj(x) y
+    im += x.x * y.y - x.y * y.x;
+  }
+  double acc[2] = {double(re), double(im)};
+  block_sum_store<2>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, KState *st, const int *active,
+                                                          const double *partA, const C *r, const C *v,
+                                                          C *s, double *partS) {
+  using A = typename Acc<C>::type;
+  if (!active[blockIdx.y]) return;
+  double sg[2];
+  gather<2>(partA + size_t(blockIdx.y) * kRedBlocks * kRedSlots, sg);
+  const KState k = st[blockIdx.y];
+  const double2 sigma = make_double2(sg[0], sg[1]);
+  const double2 alpha = (sigma.x == 0.0 && sigma.y == 0.0)
+                            ? make_double2(0.0, 0.0)
+                            : zdiv(make_double2(k.rho_re, k.rho_im), sigma);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st[blockIdx.y].alpha_re = alpha.x;
+    st[blockIdx.y].alpha_im = alpha.y;
+  }
+  const C al = from_z<C>(alpha);
+  A ss = 0;
+  DBI_PROBLEM_LOOP(n) {
+    const C si = csub(r[off + i], cmul(al, v[off + i]));
+    s[off + i] = si;
+    ss += si.x * si.x + si.y * si.y;
+  }
+  double acc[1] = {double(ss)};
+  block_sum_store<1>(acc, partS + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_dot2(size_t n, const int *active, const C *t,
+                                                      const C *s, double *part) {
+  using A = typename Acc<C>::type;
+  if (!active[blockIdx.y]) return;
+  A re = 0, im = 0, tt = 0;
+  DBI_PROBLEM_LOOP(n) {
+    const C x = t[off + i], y = s[off + i];
+    re += x.x * y.x + x.y * y.y;  // conj(t) s
+    im += x.x * y.y - x.y * y.x;
+    tt += x.x * x.x + x.y * x.y;
+  }
+  double acc[3] = {double(re), double(im), double(tt)};
+  block_sum_store<3>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(size_t n, KState *st, const int *active,
+                                                           const double *partB, const double *partS,
+                                                           double tol, const C *p, const C *s,
+                                                           const C *t, const C *rhat, C *x, C *r,
+                                                           double *partC) {
+  using A = typename Acc<C>::type;
+  if (!active[blockIdx.y]) return;
+  double q[3], sn[1];
+  gather<3>(partB + size_t(blockIdx.y) * kRedBlocks * kRedSlots, q);
+  gather<1>(partS + size_t(blockIdx.y) * kRedBlocks * kRedSlots, sn);
+  const KState k = st[blockIdx.y];
+  const int half = sn[0] <= tol * tol * k.bnorm2;
+  const double2 om = (half || q[2] == 0.0) ? make_double2(0.0, 0.0)
+                                           : make_double2(q[0] / q[2], q[1] / q[2]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st[blockIdx.y].om_re = om.x;
+    st[blockIdx.y].om_im = om.y;
+    st[blockIdx.y].half = half;
+    st[blockIdx.y].snorm2 = sn[0];
+  }
+  const C al = from_z<C>(make_double2(k.alpha_re, k.alpha_im));
+  const C o = from_z<C>(om);
+  A re = 0, im = 0, rr = 0;
+  DBI_PROBLEM_LOOP(n) {
+    const C si = s[off + i];
+    x[off + i] = cadd(x[off + i], cadd(cmul(al, p[off + i]), cmul(o, si)));
+    const C ri = csub(si, cmul(o, t[off + i]));
+    r[off + i] = ri;
+    const C h = rhat[off + i];
+    re += h.x * ri.x + h.y * ri.y;
+    im += h.x * ri.y - h.y * ri.x;
+    rr += ri.x * ri.x + ri.y * ri.y;
+  }
+  double acc[3] = {double(re), double(im), double(rr)};
+  block_sum_store<3>(acc, partC + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+}
+
+// Convergence test, breakdown restart and beta for the next iteration (one CTA per problem).
+__global__ void k_check(KState *st, int *active, int *counters, int parity, const double *partC,
+                        double tol, int max_iter) {
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  double q[3];
+  gather<3>(partC + size_t(b) * kRedBlocks * kRedSlots, q);
+  if (threadIdx.x != 0) return;
+  KState k = st[b];
+  k.iters += 1;
+  k.rnorm2 = q[2];
+  k.restart = 0;
+  const bool conv = k.half || q[2] <= tol * tol * k.bnorm2;
+  int act = 1;
+  if (conv) {
+    k.code = DBI_CONVERGED;
+    act = 0;
+  } else if (k.iters >= max_iter) {
+    k.code = DBI_NOT_CONVERGED;
+    act = 0;
+  } else {
+    const double2 rho_new = make_double2(q[0], q[1]);
+    const double rho_abs = sqrt(rho_new.x * rho_new.x + rho_new.y * rho_new.y);
+    const bool om_zero = k.om_re == 0.0 && k.om_im == 0.0;
+    const bool breakdown = om_zero || rho_abs <= 1e-14 * sqrt(k.rhatnorm2 * q[2]);
+    if (breakdown) {  // restart: rhat := r, p := r, so <rhat, r> = ||r||^2
+      k.restart = 1;
+      k.code = DBI_BREAKDOWN;
+      k.rho_re = q[2]; k.rho_im = 0.0;
+      k.alpha_re = 1.0; k.alpha_im = 0.0;
+      k.om_re = 1.0; k.om_im = 0.0;
+      k.beta_re = 0.0; k.beta_im = 0.0;
+      k.rhatnorm2 = q[2];
+    } else {
+      const double2 rho = make_double2(k.rho_re, k.rho_im);
+      const double2 beta = zmul(zdiv(rho_new, rho),
+                                zdiv(make_double2(k.alpha_re, k.alpha_im), make_double2(k.om_re, k.om_im)));
+      k.rho_re = rho_new.x; k.rho_im = rho_new.y;
+      k.beta_re = beta.x; k.beta_im = beta.y;
+      k.code = DBI_NOT_CONVERGED;
+    }
+  }
+  st[b] = k;
+  active[b] = act;
+  atomicAdd(&counters[parity], act);
+}
+
+__global__ void k_finalize(int B, const KState *st, int *iters, double *relres, int *code) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const KState k = st[b];
+  if (iters) iters[b] = k.iters;
+  if (relres) relres[b] = k.bnorm2 > 0 ? sqrt(k.rnorm2 / k.bnorm2) : 0.0;
+  if (code) code[b] = k.code;
+}
+
+size_t bytes_solver(const dbi_grid *g, int B, int precision) {
+  return 6 * bytes_field(g, B, precision) + align256(size_t(B) * sizeof(KState)) +
+         align256(size_t(B) * sizeof(int)) + 256 + 4 * bytes_partials(B);
+}
+
+SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision) {
+  SolverBufs sb{};
+  const size_t f = bytes_field(g, B, precision);
+  sb.r = ar.take(f); sb.rhat = ar.take(f); sb.p = ar.take(f);
+  sb.v = ar.take(f); sb.s = ar.take(f); sb.t = ar.take(f);
+  sb.st = static_cast<KState *>(ar.take(size_t(B) * sizeof(KState)));
+  sb.active = static_cast<int *>(ar.take(size_t(B) * sizeof(int)));
+  sb.counters = static_cast<int *>(ar.take(256));
+  sb.partA = static_cast<double *>(ar.take(bytes_partials(B)));
+  sb.partS = static_cast<double *>(ar.take(bytes_partials(B)));
+  sb.partB = static_cast<double *>(ar.take(bytes_partials(B)));
+  sb.partC = static_cast<double *>(ar.take(bytes_partials(B)));
+  return sb;
+}
+
+static int read_counter(const int *dev, cudaStream_t s, int *host) {
+  cudaError_t e = cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? DBI_OK : cuda_fail("reading the active-problem counter", e);
+}
+
+template <typename C>
+static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, void *x_, bool x_zero,
+                          const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s) {
+  const int B = op.B;
+  if (B == 0) return DBI_OK;
+  const size_t n = size_t(2) * op.nz * op.nx;
+  const C *rhs = static_cast<const C *>(rhs_);
+  C *x = static_cast<C *>(x_);
+  C *r = static_cast<C *>(sb.r), *rhat = static_cast<C *>(sb.rhat), *p = static_cast<C *>(sb.p);
+  C *v = static_cast<C *>(sb.v), *sv = static_cast<C *>(sb.s), *t = static_cast<C *>(sb.t);
+  const dim3 grid(kRedBlocks, B);
+  int rc;
+  cudaError_t e = cudaMemsetAsync(sb.counters, 0, 2 * sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(counters)", e);
+  op.stencil = true;
+  op.active = nullptr;
+  k_bnorm<C><<<grid, kRedThreads, 0, s>>>(n, rhs, sb.partA);
+  if ((rc = check_launch("k_bnorm"))) return rc;
+  k_scale<<<B, 32, 0, s>>>(sb.st, sb.partA);
+  if ((rc = check_launch("k_scale"))) return rc;
+  if (!x_zero) {  // x0 into the scaled system, v = A x0
+    k_scale_x<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x, 0);
+    if ((rc = check_launch("k_scale_x"))) return rc;
+    op.in = x; op.ident = x; op.out = v;
+    if ((rc = run_operator(op, s))) return rc;
+  }
+  k_init<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, rhs, v, r, rhat, p, x, x_zero ? 1 : 0, sb.partA);
+  if ((rc = check_launch("k_init"))) return rc;
+  k_init_state<<<B, 32, 0, s>>>(sb.st, sb.active, sb.counters, sb.partA, o.tol, o.max_iter);
+  if ((rc = check_launch("k_init_state"))) return rc;
+  if (!x_zero) {
+    k_zero_flagged<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x);
+    if ((rc = check_launch("k_zero_flagged"))) return rc;
+  }
+  int remaining = B;
+  if (o.check_every > 0 && (rc = read_counter(sb.counters + 1, s, &remaining))) return rc;
+  op.active = sb.active;
+  for (int it = 0; it < o.max_iter && remaining > 0; ++it) {
+    const int parity = it & 1;
+    k_update_p<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, sb.counters, parity, r, rhat, p, v);
+    if ((rc = check_launch("k_update_p"))) return rc;
+    op.in = p; op.ident = p; op.out = v;
+    if ((rc = run_operator(op, s))) return rc;
+    k_dot<C><<<grid, kRedThreads, 0, s>>>(n, sb.active, rhat, v, sb.partA);
+    if ((rc = check_launch("k_dot"))) return rc;
+    k_update_s<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, sb.partA, r, v, sv, sb.partS);
+    if ((rc = check_launch("k_update_s"))) return rc;
+    op.in = sv; op.ident = sv; op.out = t;
+    if ((rc = run_operator(op, s))) return rc;
+    k_dot2<C><<<grid, kRedThreads, 0, s>>>(n, sb.active, t, sv, sb.partB);
+    if ((rc = check_launch("k_dot2"))) return rc;
+    k_update_xr<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, sb.partB, sb.partS, o.tol, p, sv,
+                                                 t, rhat, x, r, sb.partC);
+    if ((rc = check_launch("k_update_xr"))) return rc;
+    k_check<<<B, 32, 0, s>>>(sb.st, sb.active, sb.counters, parity, sb.partC, o.tol, o.max_iter);
+    if ((rc = check_launch("k_check"))) return rc;
+    if (o.check_every > 0 && ((it + 1) % o.check_every == 0) &&
+        (rc = read_counter(sb.counters + parity, s, &remaining)))
+      return rc;
+  }
+  k_scale_x<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x, 1);
+  if ((rc = check_launch("k_scale_x"))) return rc;
+  if (status) {
+    k_finalize<<<(B + 127) / 128, 128, 0, s>>>(B, sb.st, status->iters, status->relres, status->code);
+    if ((rc = check_launch("k_finalize"))) return rc;
+  }
+  return DBI_OK;
+}
+
+int run_bicgstab(OpArgs op, const SolverBufs &sb, const void *rhs, void *x, bool x_zero,
+                 const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s) {
+  return op.precision == DBI_C64 ? bicgstab_typed<float2>(op, sb, rhs, x, x_zero, o, status, s)
+                                 : bicgstab_typed<double2>(op, sb, rhs, x, x_zero, o, status, s);
+}
+
+int check_krylov(const dbi_krylov_opts *o) {
+  if (!o || !(o->tol >= 0) || o->max_iter < 0 || o->check_every < 0) {
+    set_error("Krylov options need tol >= 0, max_iter >= 0, check_every >= 0");
+    return DBI_ERR_ARG;
+  }
+  return DBI_OK;
+}
+
+}  // namespace dbi
+
+using namespace dbi;
+
+extern "C" int ls_solve(const dbi_model *model, const dbi_batch *batch, const void *Ghat,
+                        const void *rhs, void *u, const dbi_krylov_opts *opts,
+                        const dbi_status *status, int precision, void *work, size_t work_bytes,
+                        dbi_stream stream) {
+  clear_error();
+  int rc;
+  if (!model) { set_error("model is NULL"); return DBI_ERR_ARG; }
+  const dbi_grid *g = &model->grid;
+  if ((rc = check_grid(g)) || (rc = check_batch(batch)) || (rc = check_precision(precision)) ||
+      (rc = check_krylov(opts)))
+    return rc;
+  if (batch->B == 0) return DBI_OK;
+  if (!model->m || !Ghat || !rhs || !u) { set_error("NULL model, Ghat, rhs or u"); return DBI_ERR_ARG; }
+  if (rhs == u) { set_error("rhs and u must be distinct buffers"); return DBI_ERR_ARG; }
+  const size_t need = dbi_workspace_bytes(g, batch->B, precision, DBI_OP_SOLVE);
+  if (!work || work_bytes < need) {
+    set_error("work buffer of %zu bytes, need %zu", work_bytes, need);
+    return DBI_ERR_WORKSPACE;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Arena ar(work, work_bytes);
+  void *tw = ar.take(bytes_twiddles(precision));
+  void *T = ar.take(bytes_spectral(g, batch->B, precision));
+  SolverBufs sb = carve_solver(ar, g, batch->B, precision);
+  if ((rc = launch_twiddles(tw, precision, s))) return rc;
+  OpArgs a{};
+  a.precision = precision; a.nz = g->nz; a.nx = g->nx; a.lz = g->lz; a.lx = g->lx; a.h = g->h;
+  a.B = batch->B; a.nf = batch->nf; a.omega = batch->omega; a.fidx = batch->fidx;
+  a.m = model->m; reference_values(model->ref, a.ref);
+  a.T = T; a.Ghat = Ghat; a.tw = tw;
+  return run_bicgstab(a, sb, rhs, u, opts->zero_guess != 0, *opts, status, s);
+}

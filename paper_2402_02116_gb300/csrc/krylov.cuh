@@ -1,0 +1,36 @@
+// Internal interface of the batched BiCGSTAB solver.
+#pragma once
+
+#include "operator.cuh"
+
+namespace dbi {
+
+// Per-problem solver state (FP64 scalars of the BiCGSTAB recurrences).
+struct KState {
+  double rho_re, rho_im;      // <rhat, r> of the current residual
+  double alpha_re, alpha_im;  // alpha of the current iteration
+  double om_re, om_im;        // omega of the last completed iteration
+  double beta_re, beta_im;    // beta for the next direction update
+  double bnorm2, rnorm2, snorm2, rhatnorm2;  // of the scaled system
+  double scale;                              // power of two applied to rhs and x
+  int iters, code, restart, half;
+  int zero_rhs, pad[3];
+};
+
+struct SolverBufs {
+  void *r, *rhat, *p, *v, *s, *t;  // [B][2][nz][nx] complex
+  KState *st;                      // [B]
+  int *active;                     // [B]
+  int *counters;                   // [2]
+  double *partA, *partS, *partB, *partC;  // [B][kRedBlocks][kRedSlots]
+};
+
+size_t bytes_solver(const dbi_grid *g, int B, int precision);
+SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision);
+
+// Solves A x = rhs for every problem of `op` (op.in / op.out / op.ident are set internally).
+// x_zero: the initial guess is zero (x is overwritten without being read).
+int run_bicgstab(OpArgs op, const SolverBufs &sb, const void *rhs, void *x, bool x_zero,
+                 const dbi_krylov_opts &opts, const dbi_status *status, cudaStream_t s);
+
+}  // namespace dbi

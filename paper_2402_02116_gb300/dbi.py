@@ -1,0 +1,380 @@
+"""Python binding of the C ABI in include/dbi.h (ctypes; argument marshalling only).
+
+Every function here allocates its outputs and the work buffer with PyTorch on the inputs' CUDA
+device, passes raw pointers and the current CUDA stream to `libdbi.so`, and raises DBIError when
+the library returns a non-zero code. All arithmetic runs in the library's CUDA kernels; there is
+no CPU path. The library must have been built (`paper_2402_02116_gb300.build.build()`); loading
+fails loudly otherwise.
+
+Precision follows the tensors: complex64 fields use the DBI_C64 path (float model arrays),
+complex128 fields the DBI_C128 path (double model arrays).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_size_t, c_void_p
+
+import torch
+
+from . import build as _build
+
+C64, C128 = 0, 1
+OP_GREENS, OP_CONVOLVE, OP_APPLY, OP_SOLVE, OP_FRECHET, OP_ADJOINT, OP_NORMAL_CG = range(7)
+CONVERGED, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+
+
+class DBIError(RuntimeError):
+    pass
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nz", c_int), ("nx", c_int), ("lz", c_int), ("lx", c_int), ("h", c_double)]
+
+
+class Medium(ctypes.Structure):
+    _fields_ = [("rho0", c_double), ("alpha0", c_double), ("beta0", c_double)]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("ref", Medium), ("m", c_void_p)]
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("B", c_int), ("nf", c_int), ("omega", c_void_p), ("fidx", c_void_p)]
+
+
+class Receivers(ctypes.Structure):
+    _fields_ = [("n", c_int), ("cells", c_void_p)]
+
+
+class KrylovOpts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("max_iter", c_int), ("check_every", c_int), ("zero_guess", c_int)]
+
+
+class Status(ctypes.Structure):
+    _fields_ = [("iters", c_void_p), ("relres", c_void_p), ("code", c_void_p)]
+
+
+class CGOpts(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("lam", c_double), ("lambda_rel", c_double), ("power_iters", c_int)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/dbi.h
+SIGNATURES = {
+    "dbi_last_error": (ctypes.c_char_p, []),
+    "dbi_version": (c_int, []),
+    "dbi_workspace_bytes": (c_size_t, [POINTER(Grid), c_int, c_int, c_int]),
+    "dbi_kernel_launches": (ctypes.c_ulonglong, []),
+    "dbi_profile_begin": (c_int, [c_int]),
+    "dbi_profile_end": (c_int, [POINTER(c_double), POINTER(ctypes.c_longlong)]),
+    "greens_tabulate": (c_int, [POINTER(Grid), POINTER(Medium), c_void_p, c_int, c_int, c_void_p,
+                                c_void_p, c_void_p, c_size_t, c_void_p]),
+    "incident_field": (c_int, [POINTER(Grid), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_int, c_void_p]),
+    "green_convolve": (c_int, [POINTER(Grid), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int,
+                               c_void_p, c_size_t, c_void_p]),
+    "ls_apply": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                         c_size_t, c_void_p]),
+    "ls_solve": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
+                         POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
+    "frechet_apply": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, POINTER(Receivers),
+                              c_void_p, c_void_p, POINTER(KrylovOpts), POINTER(Status), c_int, c_void_p,
+                              c_size_t, c_void_p]),
+    "adjoint_apply": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, POINTER(Receivers),
+                              c_void_p, c_void_p, POINTER(KrylovOpts), POINTER(Status), c_int, c_void_p,
+                              c_size_t, c_void_p]),
+    "data_residual": (c_int, [POINTER(Grid), POINTER(Batch), POINTER(Receivers), c_void_p, c_void_p,
+                              c_void_p, c_void_p, c_int, c_void_p]),
+    "normal_cg": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, POINTER(Receivers), c_void_p,
+                          POINTER(CGOpts), c_void_p, c_void_p, POINTER(c_double), POINTER(c_double),
+                          POINTER(KrylovOpts), POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libdbi.so (once) and declare its entry points; raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise DBIError(f"CUDA library not built: {path} is missing; run paper_2402_02116_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(rc: int, name: str):
+    if rc != 0:
+        msg = load().dbi_last_error().decode(errors="replace")
+        raise DBIError(f"{name} returned {rc}: {msg}")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _precision(t: torch.Tensor) -> int:
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.complex128:
+        return C128
+    raise DBIError(f"fields must be complex64 or complex128, got {t.dtype}")
+
+
+def real_dtype(precision: int):
+    return torch.float32 if precision == C64 else torch.float64
+
+
+def complex_dtype(precision: int):
+    return torch.complex64 if precision == C64 else torch.complex128
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise DBIError("every tensor must be a contiguous CUDA tensor")
+
+
+def make_grid(nz, nx, lz, lx, h) -> Grid:
+    return Grid(int(nz), int(nx), int(lz), int(lx), float(h))
+
+
+def make_medium(rho0, alpha0, beta0) -> Medium:
+    return Medium(float(rho0), float(alpha0), float(beta0))
+
+
+def workspace_bytes(grid: Grid, B: int, precision: int, op: int) -> int:
+    return int(load().dbi_workspace_bytes(ctypes.byref(grid), int(B), int(precision), int(op)))
+
+
+def _work(grid, B, precision, op, device):
+    n = workspace_bytes(grid, B, precision, op)
+    if n == 0:
+        raise DBIError("invalid grid or precision for the workspace query")
+    return torch.empty(n, dtype=torch.uint8, device=device), n
+
+
+def _batch(omega: torch.Tensor, fidx: torch.Tensor) -> Batch:
+    if omega.dtype != torch.float64 or fidx.dtype != torch.int32:
+        raise DBIError("omega must be float64 and fidx int32")
+    _need_cuda(omega, fidx)
+    return Batch(int(fidx.numel()), int(omega.numel()), omega.data_ptr(), fidx.data_ptr())
+
+
+def _model(grid, ref, m, precision) -> Model:
+    if m.dtype != real_dtype(precision):
+        raise DBIError(f"model must be {real_dtype(precision)} for this precision, got {m.dtype}")
+    _need_cuda(m)
+    if tuple(m.shape) != (5, grid.nz, grid.nx):
+        raise DBIError(f"model shape {tuple(m.shape)} != (5, {grid.nz}, {grid.nx})")
+    return Model(grid, ref, m.data_ptr())
+
+
+def _receivers(cells: torch.Tensor) -> Receivers:
+    if cells.dtype != torch.int32:
+        raise DBIError("receiver cells must be int32 [n][2]")
+    _need_cuda(cells)
+    return Receivers(int(cells.shape[0]), cells.data_ptr())
+
+
+def _kopts(tol, max_iter, check_every, zero_guess=False) -> KrylovOpts:
+    return KrylovOpts(float(tol), int(max_iter), int(check_every), int(bool(zero_guess)))
+
+
+def _status(B, device):
+    iters = torch.zeros(B, dtype=torch.int32, device=device)
+    relres = torch.zeros(B, dtype=torch.float64, device=device)
+    code = torch.zeros(B, dtype=torch.int32, device=device)
+    return (iters, relres, code), Status(iters.data_ptr(), relres.data_ptr(), code.data_ptr())
+
+
+PROF_ROWS_FORWARD, PROF_COLS, PROF_ROWS_INVERSE, PROF_OPERATOR = 1, 2, 3, 4
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().dbi_kernel_launches())
+
+
+def profile_begin(stage: int):
+    _check(load().dbi_profile_begin(int(stage)), "dbi_profile_begin")
+
+
+def profile_end():
+    """(summed ms, launches) of the stage timed since profile_begin."""
+    ms, n = c_double(0.0), ctypes.c_longlong(0)
+    _check(load().dbi_profile_end(ctypes.byref(ms), ctypes.byref(n)), "dbi_profile_end")
+    return float(ms.value), int(n.value)
+
+
+# ---------------------------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------------------------
+def greens_tabulate(grid: Grid, ref: Medium, omega: torch.Tensor, precision: int = C64,
+                    with_space: bool = True):
+    """Ghat [nf][3][lz][lx] (h^2/(lz lx) FFT(G)) and, if asked, Gspace [nf][3][lz][lx]."""
+    _need_cuda(omega)
+    dev = omega.device
+    nf = int(omega.numel())
+    cd = complex_dtype(precision)
+    Ghat = torch.empty((nf, 3, grid.lz, grid.lx), dtype=cd, device=dev)
+    Gspace = torch.empty_like(Ghat) if with_space else None
+    work, n = _work(grid, nf, precision, OP_GREENS, dev)
+    _check(load().greens_tabulate(ctypes.byref(grid), ctypes.byref(ref), _ptr(omega), nf, precision,
+                                  _ptr(Ghat), _ptr(Gspace), _ptr(work), n, _stream(dev)), "greens_tabulate")
+    return Ghat, Gspace
+
+
+def incident_field(grid: Grid, omega, fidx, Gspace, src_cells, forces):
+    """u0 [B][2][nz][nx] = G_h(x - x_s) f for every problem."""
+    precision = _precision(Gspace)
+    _need_cuda(Gspace, src_cells, forces)
+    if src_cells.dtype != torch.int32 or forces.dtype != torch.float64:
+        raise DBIError("src_cells must be int32 [B][2] and forces float64 [B][2]")
+    batch = _batch(omega, fidx)
+    u0 = torch.empty((batch.B, 2, grid.nz, grid.nx), dtype=Gspace.dtype, device=Gspace.device)
+    _check(load().incident_field(ctypes.byref(grid), ctypes.byref(batch), _ptr(Gspace), _ptr(src_cells),
+                                 _ptr(forces), _ptr(u0), precision, _stream(Gspace.device)), "incident_field")
+    return u0
+
+
+def green_convolve(grid: Grid, omega, fidx, Ghat, src):
+    """h^2 G * src for every problem."""
+    precision = _precision(src)
+    _need_cuda(Ghat, src)
+    batch = _batch(omega, fidx)
+    out = torch.empty_like(src)
+    work, n = _work(grid, batch.B, precision, OP_CONVOLVE, src.device)
+    _check(load().green_convolve(ctypes.byref(grid), ctypes.byref(batch), _ptr(Ghat), _ptr(src), _ptr(out),
+                                 precision, _ptr(work), n, _stream(src.device)), "green_convolve")
+    return out
+
+
+def ls_apply(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None, work=None):
+    """A u (Eq. 10) for every problem."""
+    precision = _precision(u)
+    _need_cuda(Ghat, u)
+    model = _model(grid, ref, m, precision)
+    batch = _batch(omega, fidx)
+    out = torch.empty_like(u) if out is None else out
+    if work is None:
+        work, n = _work(grid, batch.B, precision, OP_APPLY, u.device)
+    else:
+        n = work.numel()
+    _check(load().ls_apply(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u), _ptr(out), precision,
+                           _ptr(work), n, _stream(u.device)), "ls_apply")
+    return out
+
+
+def ls_solve(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, tol=1e-6, max_iter=1000,
+             check_every=8, work=None, out=None):
+    """Solve A u = rhs for every problem (from u0, or from zero); returns (u, iters, relres, code)."""
+    precision = _precision(rhs)
+    _need_cuda(Ghat, rhs)
+    model = _model(grid, ref, m, precision)
+    batch = _batch(omega, fidx)
+    if out is None:
+        u = torch.empty_like(rhs) if u0 is None else u0.clone()
+    else:
+        u = out
+        if u0 is not None:
+            u.copy_(u0)
+    if work is None:
+        work, n = _work(grid, batch.B, precision, OP_SOLVE, rhs.device)
+    else:
+        n = work.numel()
+    (iters, relres, code), st = _status(batch.B, rhs.device)
+    opts = _kopts(tol, max_iter, check_every, zero_guess=u0 is None)
+    _check(load().ls_solve(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(rhs), _ptr(u),
+                           ctypes.byref(opts), ctypes.byref(st), precision, _ptr(work), n,
+                           _stream(rhs.device)), "ls_solve")
+    return u, iters, relres, code
+
+
+def frechet_apply(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, dm, tol=1e-6,
+                  max_iter=1000, check_every=8, with_status=False):
+    """J dm sampled at the receivers, [B][n_rec][2] (and the solve's (iters, relres, code))."""
+    precision = _precision(u_b)
+    _need_cuda(Ghat, u_b, dm)
+    model = _model(grid, ref, m_b, precision)
+    if dm.dtype != real_dtype(precision):
+        raise DBIError("dm must have the model's real dtype")
+    batch = _batch(omega, fidx)
+    rec = _receivers(rec_cells)
+    d = torch.empty((batch.B, rec.n, 2), dtype=u_b.dtype, device=u_b.device)
+    work, n = _work(grid, batch.B, precision, OP_FRECHET, u_b.device)
+    (iters, relres, code), st = _status(batch.B, u_b.device)
+    opts = _kopts(tol, max_iter, check_every)
+    _check(load().frechet_apply(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u_b),
+                                ctypes.byref(rec), _ptr(dm), _ptr(d), ctypes.byref(opts), ctypes.byref(st),
+                                precision, _ptr(work), n, _stream(u_b.device)), "frechet_apply")
+    return (d, (iters, relres, code)) if with_status else d
+
+
+def adjoint_apply(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, r, tol=1e-6,
+                  max_iter=1000, check_every=8, with_status=False):
+    """Re J^H r summed over problems, [5][nz][nx] (and the solve's (iters, relres, code))."""
+    precision = _precision(u_b)
+    _need_cuda(Ghat, u_b, r)
+    model = _model(grid, ref, m_b, precision)
+    batch = _batch(omega, fidx)
+    rec = _receivers(rec_cells)
+    g = torch.empty((5, grid.nz, grid.nx), dtype=real_dtype(precision), device=u_b.device)
+    work, n = _work(grid, batch.B, precision, OP_ADJOINT, u_b.device)
+    (iters, relres, code), st = _status(batch.B, u_b.device)
+    opts = _kopts(tol, max_iter, check_every)
+    _check(load().adjoint_apply(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u_b),
+                                ctypes.byref(rec), _ptr(r), _ptr(g), ctypes.byref(opts), ctypes.byref(st),
+                                precision, _ptr(work), n, _stream(u_b.device)), "adjoint_apply")
+    return (g, (iters, relres, code)) if with_status else g
+
+
+def data_residual(grid: Grid, omega, fidx, rec_cells, u, d_obs):
+    """(r = P u - d_obs, phi = 1/2 ||r||^2 as a device float64 scalar tensor)."""
+    precision = _precision(u)
+    _need_cuda(u, d_obs)
+    batch = _batch(omega, fidx)
+    rec = _receivers(rec_cells)
+    r = torch.empty_like(d_obs)
+    phi = torch.empty((), dtype=torch.float64, device=u.device)
+    _check(load().data_residual(ctypes.byref(grid), ctypes.byref(batch), ctypes.byref(rec), _ptr(u),
+                                _ptr(d_obs), _ptr(r), _ptr(phi), precision, _stream(u.device)), "data_residual")
+    return r, phi
+
+
+def normal_cg(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, dd, iters=30, lam=None,
+              lambda_rel=1e-3, power_iters=10, power_start=None, tol=1e-6, max_iter=1000, check_every=8):
+    """Tikhonov normal-equation CG; returns (dm [5][nz][nx], lambda, residual history)."""
+    precision = _precision(u_b)
+    _need_cuda(Ghat, u_b, dd, power_start)
+    model = _model(grid, ref, m_b, precision)
+    batch = _batch(omega, fidx)
+    rec = _receivers(rec_cells)
+    dm = torch.empty((5, grid.nz, grid.nx), dtype=real_dtype(precision), device=u_b.device)
+    work, n = _work(grid, batch.B, precision, OP_NORMAL_CG, u_b.device)
+    (its, relres, code), st = _status(batch.B, u_b.device)
+    opts = _kopts(tol, max_iter, check_every)
+    cg = CGOpts(int(iters), float(lam) if lam is not None else 0.0, float(lambda_rel), int(power_iters))
+    lam_out = c_double(0.0)
+    hist = (c_double * (int(iters) + 1))()
+    _check(load().normal_cg(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u_b), ctypes.byref(rec),
+                            _ptr(dd), ctypes.byref(cg), _ptr(power_start), _ptr(dm), ctypes.byref(lam_out),
+                            hist, ctypes.byref(opts), ctypes.byref(st), precision, _ptr(work), n,
+                            _stream(u_b.device)), "normal_cg")
+    return dm, float(lam_out.value), list(hist)

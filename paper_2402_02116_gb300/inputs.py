@@ -229,6 +229,14 @@ def config4_misfit(n=512, n_src=64, nf=6, seed=4) -> Workload:
         krylov_tol=1e-6, seed=seed)
 
 
+def fft_len(n: int) -> int:
+    """Smallest power of two >= max(16, 2n - 1): an FFT length that holds every offset of n cells."""
+    p = 16
+    while p < 2 * n - 1:
+        p *= 2
+    return p
+
+
 def small_case(nz=12, nx=10, h=10.0, seed=11, n_src=2, freqs=(8.0, 14.0), amp=0.1, vti=False,
                lz=None, lx=None) -> Workload:
     """A small, non-square case with a ragged contrast for parity and pin tests."""
@@ -244,7 +252,7 @@ def small_case(nz=12, nx=10, h=10.0, seed=11, n_src=2, freqs=(8.0, 14.0), amp=0.
     cols = surface_line(nx, n_src)
     return Workload(
         name=f"small{nz}x{nx}", nz=nz, nx=nx, h=h,
-        lz=lz if lz is not None else 2 * nz, lx=lx if lx is not None else 2 * nx,
+        lz=lz if lz is not None else fft_len(nz), lx=lx if lx is not None else fft_len(nx),
         rho0=rho0, alpha0=a0, beta0=b0, model=model,
         freqs_hz=np.asarray(freqs, dtype=np.float64),
         src_cells=np.stack([np.zeros_like(cols), cols], axis=1),

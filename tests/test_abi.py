@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads and exports every entry point that include/dbi.h declares; its
+host-side argument checks reject bad calls before any CUDA work. No GPU is needed."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2402_02116_gb300 import build, dbi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dbi.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^(?:const\s+char\s*\*|int|size_t)\s*\**\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return dbi.load()
+
+
+def test_header_declares_the_paper_entry_points():
+    names = declared_functions()
+    for want in ("greens_tabulate", "ls_apply", "ls_solve", "frechet_apply", "adjoint_apply", "normal_cg",
+                 "incident_field", "green_convolve", "data_residual", "dbi_workspace_bytes", "dbi_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in dbi.SIGNATURES, name
+
+
+def test_workspace_query_is_host_only(lib):
+    g = dbi.make_grid(32, 32, 64, 64, 10.0)
+    assert dbi.workspace_bytes(g, 4, dbi.C64, dbi.OP_APPLY) > 4 * 2 * 32 * 64 * 8
+    assert dbi.workspace_bytes(g, 4, dbi.C128, dbi.OP_SOLVE) > dbi.workspace_bytes(g, 4, dbi.C64, dbi.OP_SOLVE)
+    bad = dbi.make_grid(32, 32, 48, 64, 10.0)  # 48 is not a supported FFT length
+    assert dbi.workspace_bytes(bad, 4, dbi.C64, dbi.OP_APPLY) == 0
+    small = dbi.make_grid(40, 32, 64, 64, 10.0)  # 64 < 2 * 40 - 1
+    assert dbi.workspace_bytes(small, 4, dbi.C64, dbi.OP_APPLY) == 0
+
+
+def test_argument_errors_are_reported_without_a_gpu(lib):
+    ref = dbi.make_medium(2000.0, 2000.0, 1155.0)
+    rc = lib.greens_tabulate(None, ctypes.byref(ref), None, 1, 0, None, None, None, 0, None)
+    assert rc == -1 and b"NULL" in lib.dbi_last_error()
+    g = dbi.make_grid(32, 32, 48, 64, 10.0)
+    rc = lib.greens_tabulate(ctypes.byref(g), ctypes.byref(ref), None, 1, 0, None, None, None, 0, None)
+    assert rc == -2 and b"power of two" in lib.dbi_last_error()
+    g = dbi.make_grid(32, 32, 64, 64, 10.0)
+    rc = lib.greens_tabulate(ctypes.byref(g), ctypes.byref(ref), None, 1, 7, None, None, None, 0, None)
+    assert rc == -2
+    bad_ref = dbi.make_medium(2000.0, 1000.0, 1155.0)  # alpha0 < beta0
+    rc = lib.greens_tabulate(ctypes.byref(g), ctypes.byref(bad_ref), None, 1, 0, None, None, None, 0, None)
+    assert rc == -1
+    model = dbi.Model(g, ref, None)
+    batch = dbi.Batch(2, 1, None, None)
+    rc = lib.ls_apply(ctypes.byref(model), ctypes.byref(batch), None, None, None, 0, None, 0, None)
+    assert rc == -1
+    opts = dbi.KrylovOpts(-1.0, 10, 1)
+    batch = dbi.Batch(0, 1, 1, None)
+    rc = lib.ls_solve(ctypes.byref(model), ctypes.byref(batch), None, None, None, ctypes.byref(opts), None, 0,
+                      None, 0, None)
+    assert rc == -1 and b"tol" in lib.dbi_last_error()
+    assert lib.dbi_version() >= 100

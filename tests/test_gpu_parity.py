@@ -1,0 +1,295 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L2 unless stated): complex128 path 1e-10 for single operator passes, 1e-8
+for solves; complex64 path 1e-5 for wavefields and data (the wavefield tolerance of the
+benchmark configurations) and 1e-4 for gradients. The complex64 bound comes from FP32 rounding
+(u = 6e-8) amplified by the O(log L) depth of the FFTs and the stencil's cancellation.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2402_02116_gb300 import build, dbi, inputs
+from paper_2402_02116_gb300.problem import DeviceProblem
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+TOL = {dbi.C64: 1e-5, dbi.C128: 1e-10}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    dbi.load()
+
+
+def npy(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def oracle_for(w, method="fft"):
+    return O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas, method=method)
+
+
+SHAPES = [
+    dict(nz=12, nx=10),                  # ragged, single tile
+    dict(nz=5, nx=9, lz=16, lx=32),      # non-square FFT grid
+    dict(nz=1, nx=8),                    # one row
+    dict(nz=40, nx=24, vti=True),        # several row tiles, VTI background
+    dict(nz=64, nx=64, lz=128, lx=128),  # several column tiles
+]
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("nz", "nx")))
+def test_greens_tables(precision, shape):
+    w = inputs.small_case(freqs=(3.0, 17.0), **shape)
+    P = DeviceProblem(w, precision)
+    orc = oracle_for(w)
+    # FP64: CUDA's and scipy's Bessel routines differ by a few ulp, amplified near the zeros of
+    # J_n, Y_n and by the cancellation of the 1/r^2 parts of H2 between the P and S terms
+    tol = 1e-10 if precision == dbi.C128 else 1e-6
+    for f in range(w.nf):
+        Gs = O.embed_circulant(orc.G_lat[f], w.lz, w.lx)
+        assert rel(npy(P.Gspace[f]), Gs) < tol
+        Gh = orc.G_hat[f] * w.h * w.h / (w.lz * w.lx)
+        assert rel(npy(P.Ghat[f]), Gh) < 10 * tol
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_incident_field(precision):
+    w = inputs.small_case(nz=14, nx=11, n_src=3, freqs=(6.0, 11.0))
+    P = DeviceProblem(w, precision)
+    orc = oracle_for(w)
+    u0 = npy(P.incident())
+    srcs = w.problem_src()
+    for b, f in enumerate(w.problem_fidx()):
+        want = orc.incident(f, w.src_cells[srcs[b]], w.src_force[srcs[b]])
+        assert rel(u0[b], want) < (1e-10 if precision == dbi.C128 else 1e-6)
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("nz", "nx")))
+def test_green_convolve(precision, shape):
+    w = inputs.small_case(freqs=(5.0, 12.0), **shape)
+    P = DeviceProblem(w, precision)
+    orc = oracle_for(w)
+    src = inputs.seeded_complex((w.n_problems, 2, w.nz, w.nx), 3)
+    out = npy(P.convolve(P.to_field(src)))
+    for b, f in enumerate(w.problem_fidx()):
+        assert rel(out[b], orc.convolve(src[b], f)) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(str(s[k]) for k in ("nz", "nx")))
+def test_ls_apply(precision, shape):
+    w = inputs.small_case(freqs=(7.0, 15.0), amp=0.15, **shape)
+    P = DeviceProblem(w, precision)
+    orc = oracle_for(w)
+    u = inputs.seeded_complex((w.n_problems, 2, w.nz, w.nx), 4)
+    out = npy(P.apply(P.to_field(u)))
+    for b, f in enumerate(w.problem_fidx()):
+        want = orc.apply(u[b], w.model, f)
+        assert rel(out[b], want) < TOL[precision]
+        # the scattered part alone (A u - u) also matches to the same relative accuracy
+        assert rel(out[b] - u[b], want - u[b]) < 20 * TOL[precision]
+
+
+def test_ls_apply_direct_sum_tiny():
+    """The operator equals the oracle's direct O(N^4) sum (no FFT on the oracle side)."""
+    w = inputs.small_case(nz=7, nx=6, amp=0.2, vti=True)
+    P = DeviceProblem(w, dbi.C128)
+    orc = oracle_for(w, method="direct")
+    u = inputs.seeded_complex((w.n_problems, 2, w.nz, w.nx), 5)
+    out = npy(P.apply(P.to_field(u)))
+    for b, f in enumerate(w.problem_fidx()):
+        assert rel(out[b], orc.apply(u[b], w.model, f)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_ls_solve(precision):
+    w = inputs.small_case(nz=20, nx=18, amp=0.12, vti=True, n_src=2, freqs=(6.0, 13.0))
+    P = DeviceProblem(w, precision)
+    orc = oracle_for(w)
+    tol = 1e-11 if precision == dbi.C128 else 1e-6
+    u, iters, relres, code = P.forward(tol=tol)
+    u = npy(u)
+    assert np.all(npy(code) == dbi.CONVERGED)
+    assert np.all(npy(relres) <= tol)
+    srcs = w.problem_src()
+    for b, f in enumerate(w.problem_fidx()):
+        want = orc.solve(orc.incident(f, w.src_cells[srcs[b]], w.src_force[srcs[b]]), w.model, f, tol=1e-13)
+        assert rel(u[b], want) < (1e-8 if precision == dbi.C128 else 1e-5)
+
+
+def test_config1_tiny_complex128():
+    """The 32 x 32 isotropic inclusion case, complex128 BiCGSTAB to 1e-8, against the oracle."""
+    w = inputs.config1_tiny()
+    P = DeviceProblem(w, dbi.C128)
+    orc = oracle_for(w)
+    u, iters, relres, code = P.forward(tol=1e-8)
+    assert npy(code)[0] == dbi.CONVERGED and npy(relres)[0] <= 1e-8
+    want = orc.solve(orc.incident(0, w.src_cells[0], w.src_force[0]), w.model, 0, tol=1e-13)
+    assert rel(npy(u)[0], want) < 1e-7
+    d = npy(P.sample(u))[0]
+    assert rel(d, orc.sample(want, w.rec_cells)) < 1e-7
+
+
+def test_solver_status_and_edge_cases():
+    w = inputs.small_case(nz=10, nx=10, amp=0.1)
+    P = DeviceProblem(w, dbi.C64)
+    u0 = P.incident()
+    # an iteration cap of one leaves the problems unconverged after exactly one iteration
+    _, iters, relres, code = P.solve(u0, tol=1e-12, max_iter=1, check_every=1)
+    assert np.all(npy(iters) == 1) and np.all(npy(code) == dbi.NOT_CONVERGED)
+    # a zero right-hand side converges at once to zero, whatever the initial guess
+    z = torch.zeros_like(u0)
+    x, iters, relres, code = P.solve(z, u0=u0, tol=1e-6)
+    assert np.all(npy(code) == dbi.CONVERGED) and np.all(npy(iters) == 0)
+    assert float(torch.abs(x).max()) == 0.0
+    # the solver is scale-invariant: a right-hand side of 2^-90 (squares far below FP32's range)
+    # gives the same solution scaled by 2^-90
+    x, _, _, code = P.solve(u0, tol=1e-6)
+    xt, _, _, code_t = P.solve(u0 * 2.0 ** -90, tol=1e-6)
+    assert np.all(npy(code_t) == dbi.CONVERGED)
+    assert rel(npy(xt).astype(np.complex128) * 2.0 ** 90, npy(x)) < 1e-6
+    # a converged initial guess takes no iterations
+    _, iters, _, code = P.solve(u0, u0=x, tol=1e-3)
+    assert np.all(npy(iters) == 0)
+    # an empty batch is a no-op
+    w0 = inputs.small_case(nz=8, nx=8, n_src=0 + 1, freqs=(5.0,))
+    P0 = DeviceProblem(w0, dbi.C64)
+    empty = torch.zeros((0, 2, 8, 8), dtype=torch.complex64, device="cuda")
+    out = dbi.ls_apply(P0.grid, P0.ref, P0.m, P0.omega, P0.fidx[:0], P0.Ghat, empty)
+    assert out.shape == (0, 2, 8, 8)
+
+
+def test_largest_fft_grid():
+    """512 x 512 cells on the 1024 x 1024 FFT grid (the largest supported), one problem."""
+    w = inputs.small_case(nz=512, nx=512, n_src=1, freqs=(9.0,), amp=0.1, h=5.0)
+    P = DeviceProblem(w, dbi.C64)
+    orc = oracle_for(w)
+    u = inputs.seeded_complex((1, 2, 512, 512), 6)
+    out = npy(P.apply(P.to_field(u)))
+    assert rel(out[0], orc.apply(u[0], w.model, 0)) < TOL[dbi.C64]
+
+
+def _dbi_setup(precision, seed=31):
+    w = inputs.small_case(nz=12, nx=11, amp=0.12, vti=True, n_src=2, freqs=(7.0, 12.0), seed=seed)
+    P = DeviceProblem(w, precision)
+    orc = oracle_for(w)
+    fidx = w.problem_fidx()
+    srcs = w.src_cells[w.problem_src()]
+    forces = w.src_force[w.problem_src()]
+    U = orc.forward(w.model, fidx, srcs, forces)
+    return w, P, orc, fidx, U
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_frechet_apply(precision):
+    w, P, orc, fidx, U = _dbi_setup(precision)
+    dm = inputs.seeded_real((5, w.nz, w.nx), 12) * orc.param_scale()[:, None, None] * 0.01
+    tol = 1e-11 if precision == dbi.C128 else 1e-6
+    d = npy(P.frechet(P.to_field(U), P.to_model(dm), tol=tol))
+    want = orc.frechet(w.model, U, fidx, dm, w.rec_cells)
+    assert rel(d, want) < (1e-8 if precision == dbi.C128 else 1e-5)
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_adjoint_apply(precision):
+    w, P, orc, fidx, U = _dbi_setup(precision)
+    R = inputs.seeded_complex((len(fidx), len(w.rec_cells), 2), 13)
+    tol = 1e-11 if precision == dbi.C128 else 1e-6
+    g = npy(P.adjoint(P.to_field(U), P.to_field(R), tol=tol))
+    want = orc.adjoint(w.model, U, fidx, R, w.rec_cells)
+    for p in range(5):
+        assert rel(g[p], want[p]) < (1e-8 if precision == dbi.C128 else 1e-4), p
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_gpu_dot_product_test(precision):
+    """<J dm, r> = <dm, Re J^H r> with both products from the CUDA path."""
+    w, P, orc, fidx, U = _dbi_setup(precision, seed=33)
+    tol = 1e-12 if precision == dbi.C128 else 1e-7
+    Ub = P.to_field(U)
+    dm = inputs.seeded_real((5, w.nz, w.nx), 14) * orc.param_scale()[:, None, None] * 0.01
+    R = inputs.seeded_complex((len(fidx), len(w.rec_cells), 2), 15)
+    Jd = npy(P.frechet(Ub, P.to_model(dm), tol=tol)).astype(np.complex128)
+    g = npy(P.adjoint(Ub, P.to_field(R), tol=tol)).astype(np.float64)
+    lhs = np.real(np.vdot(R, Jd))
+    rhs = np.sum(npy(P.to_model(dm)).astype(np.float64) * g)
+    assert abs(lhs - rhs) / abs(lhs) < (1e-10 if precision == dbi.C128 else 1e-5)
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_data_residual(precision):
+    w, P, orc, fidx, U = _dbi_setup(precision)
+    dobs = inputs.seeded_complex((len(fidx), len(w.rec_cells), 2), 16) * 1e-10
+    r, phi = P.residual(P.to_field(U), P.to_field(dobs))
+    want = np.stack([orc.sample(U[b], w.rec_cells) for b in range(len(fidx))]) - dobs
+    assert rel(npy(r), want) < (1e-12 if precision == dbi.C128 else 1e-6)
+    assert abs(float(phi) - 0.5 * np.sum(np.abs(want) ** 2)) < 1e-5 * 0.5 * np.sum(np.abs(want) ** 2)
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_normal_cg(precision):
+    w = inputs.small_case(nz=8, nx=7, amp=0.1, vti=True, n_src=2, freqs=(8.0, 13.0), seed=41)
+    P = DeviceProblem(w, precision)
+    orc = oracle_for(w)
+    fidx = w.problem_fidx()
+    U = orc.forward(w.model, fidx, w.src_cells[w.problem_src()], w.src_force[w.problem_src()])
+    dd = inputs.seeded_complex((len(fidx), len(w.rec_cells), 2), 17) * 1e-12
+    start = inputs.seeded_real((5, w.nz, w.nx), 18)
+    tol = 1e-12 if precision == dbi.C128 else 1e-7
+    dm, lam, hist = P.normal_cg(P.to_field(U), P.to_field(dd), iters=12, power_start=start, tol=tol)
+    want, lam_o, hist_o = orc.normal_cg(w.model, U, fidx, dd, w.rec_cells, iters=12, power_start=start)
+    # complex64: every application of Re J~^H J~ runs two FP32 solves (relative error ~1e-5 each) and
+    # lambda compounds eleven of them; the CG iterates inherit the same level
+    lam_err = abs(lam - lam_o) / lam_o
+    hist_err = rel(np.asarray(hist), np.asarray(hist_o))
+    dm_err = rel(npy(dm), want)
+    limits = (1e-8, 1e-7, 1e-7) if precision == dbi.C128 else (5e-4, 1e-3, 1e-3)
+    assert lam_err < limits[0] and hist_err < limits[1] and dm_err < limits[2], (lam_err, hist_err, dm_err)
+
+
+# --- the batched-forward workload at full size, in the benchmark's launch configuration --------
+@pytest.fixture(scope="module")
+def config2():
+    w = inputs.config2_batched_forward()
+    return w, DeviceProblem(w, dbi.C64)
+
+
+def test_config2_apply_sampled(config2):
+    """All 256 problems of the 256 x 256 VTI workload in one batched apply; two problems (two
+    frequencies) checked against the oracle."""
+    w, P = config2
+    orc = oracle_for(w)
+    u = P.incident()
+    out = npy(P.apply(u))
+    un = npy(u)
+    for b in (3, w.n_problems - 5):
+        f = int(w.problem_fidx()[b])
+        assert rel(out[b], orc.apply(un[b].astype(np.complex128), w.model, f)) < TOL[dbi.C64]
+
+
+def test_config2_solve_residual_sampled(config2):
+    """The batched complex64 solve converges for all 256 problems; for sampled problems the FP64
+    oracle confirms the residual of the returned wavefield (a property that holds at any size)."""
+    w, P = config2
+    orc = oracle_for(w)
+    u0 = P.incident()
+    u, iters, relres, code = P.solve(u0, tol=1e-5, max_iter=3000)
+    assert np.all(npy(code) == dbi.CONVERGED), np.unique(npy(code), return_counts=True)
+    un, u0n = npy(u).astype(np.complex128), npy(u0).astype(np.complex128)
+    for b in (0, w.n_problems - 1):
+        f = int(w.problem_fidx()[b])
+        res = rel(orc.apply(un[b], w.model, f), u0n[b])
+        assert res < 3e-5, (b, res, float(npy(relres)[b]))
