@@ -47,15 +47,21 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle sample")
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 plain-path sample")
+    ap.add_argument("--sources", type=int, default=32,
+                    help="sources per GPU (32 is the benchmark workload; fewer make a smaller batch "
+                         "of the same grid for profiler captures)")
     return ap.parse_args()
 
 
-def workload(rank: int, world: int):
-    """The 256 x 256 VTI workload; with several ranks each gets its own 32 surface sources."""
+def workload(rank: int, world: int, sources: int = 32):
+    """The 256 x 256 VTI workload; with several ranks each gets its own `sources` surface sources."""
     w = inputs.config2_batched_forward()
-    if world > 1:
-        cols = inputs.surface_line(w.nx, 32 * world)[rank::world]
+    if world > 1 or sources != 32:
+        cols = inputs.surface_line(w.nx, sources * world)[rank::world]
         w.src_cells = np.stack([np.zeros_like(cols), cols], axis=1)
+        w.src_force = np.tile([0.0, 1.0], (len(cols), 1))
+        if sources != 32:
+            w.name = f"vti{w.nz}x{w.nx}_{sources}src_{w.nf}f"
     return w
 
 
@@ -146,7 +152,7 @@ def run_ours(args):
     build.build()
     dbi.load()
 
-    w = workload(rank, world)
+    w = workload(rank, world, args.sources)
     P = DeviceProblem(w, dbi.C64, device=dev)
     d_obs_host = synthetic_data(w, seed=7 + rank)
     d_obs = P.to_field(d_obs_host)

@@ -124,6 +124,8 @@ size_t bytes_partials(int B) {
   return align256(size_t(B) * kRedBlocks * kRedSlots * sizeof(double));
 }
 
+size_t bytes_scales(int B) { return 2 * align256(size_t(B) * sizeof(double)) + 256 + bytes_partials(B); }
+
 }  // namespace dbi
 
 using namespace dbi;
@@ -178,16 +180,16 @@ extern "C" size_t dbi_workspace_bytes(const dbi_grid *g, int B, int precision, i
              align256(size_t(B) * 3 * g->lz * g->lx * sizeof(double2));
     case DBI_OP_CONVOLVE:
     case DBI_OP_APPLY:
-      return tw + spec;
+      return tw + spec + bytes_scales(B);
     case DBI_OP_SOLVE:
       return solve;
     case DBI_OP_FRECHET:
     case DBI_OP_ADJOINT:
-      return solve + 2 * fld + model;
+      return solve + 2 * fld + model + bytes_scales(B);
     case DBI_OP_NORMAL_CG: {
       // receivers are cells: n_rec <= nz * nx
       const size_t data = align256(size_t(B) * g->nz * g->nx * 2 * csize(precision));
-      return solve + 2 * fld + 6 * model + data + bytes_partials(1) + 256 +
+      return solve + 2 * fld + 6 * model + data + bytes_partials(1) + 256 + bytes_scales(B) +
              align256(4097 * sizeof(double));
     }
     default:

@@ -91,6 +91,8 @@ size_t bytes_twiddles(int precision);
 size_t bytes_spectral(const dbi_grid *g, int B, int precision);
 size_t bytes_field(const dbi_grid *g, int B, int precision);
 size_t bytes_partials(int B);
+// per-problem power-of-two scales (scale, inverse, model scale) and their partial sums
+size_t bytes_scales(int B);
 
 // Geometry of the FP64 partial sums of the Krylov reductions.
 constexpr int kRedBlocks = 64;    // blocks per problem in a reduction pass

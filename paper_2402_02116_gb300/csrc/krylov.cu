@@ -343,6 +343,49 @@ __global__ void k_finalize(int B, const KState *st, int *iters, double *relres, 
   if (code) code[b] = k.code;
 }
 
+// ---------------------------------------------------------------------------------------------
+// power-of-two normalisers
+// ---------------------------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ double sq64(T v);
+template <> __device__ __forceinline__ double sq64<float>(float v) { return double(v) * double(v); }
+template <> __device__ __forceinline__ double sq64<double>(double v) { return v * v; }
+template <> __device__ __forceinline__ double sq64<float2>(float2 v) { return double(v.x) * v.x + double(v.y) * v.y; }
+template <> __device__ __forceinline__ double sq64<double2>(double2 v) { return v.x * v.x + v.y * v.y; }
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_sumsq(size_t n, const T *x, double *part) {
+  double acc = 0.0;
+  DBI_PROBLEM_LOOP(n) acc += sq64<T>(x[off + i]);
+  double a[1] = {acc};
+  block_sum_store<1>(a, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+}
+
+__global__ void k_pow2(const double *part, double *scale, double *inv, const double *extra) {
+  double s[1];
+  gather<1>(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, s);
+  if (threadIdx.x == 0) {
+    const double sc = s[0] > 0.0 ? ldexp(1.0, -ilogb(sqrt(s[0]))) : 1.0;
+    scale[blockIdx.x] = sc;
+    if (inv) inv[blockIdx.x] = 1.0 / (sc * (extra ? extra[0] : 1.0));
+  }
+}
+
+int pow2_scales(const void *x, int precision, bool real, int B, size_t n, double *part, double *scale,
+                double *inv, const double *extra, cudaStream_t s) {
+  const dim3 grid(kRedBlocks, B);
+  if (precision == DBI_C64) {
+    if (real) k_sumsq<float><<<grid, kRedThreads, 0, s>>>(n, static_cast<const float *>(x), part);
+    else k_sumsq<float2><<<grid, kRedThreads, 0, s>>>(n, static_cast<const float2 *>(x), part);
+  } else {
+    if (real) k_sumsq<double><<<grid, kRedThreads, 0, s>>>(n, static_cast<const double *>(x), part);
+    else k_sumsq<double2><<<grid, kRedThreads, 0, s>>>(n, static_cast<const double2 *>(x), part);
+  }
+  int rc;
+  if ((rc = check_launch("k_sumsq"))) return rc;
+  k_pow2<<<B, 32, 0, s>>>(part, scale, inv, extra);
+  return check_launch("k_pow2");
+}
+
 size_t bytes_solver(const dbi_grid *g, int B, int precision) {
   return 6 * bytes_field(g, B, precision) + align256(size_t(B) * sizeof(KState)) +
          align256(size_t(B) * sizeof(int)) + 256 + 4 * bytes_partials(B);
@@ -371,7 +414,7 @@ static int read_counter(const int *dev, cudaStream_t s, int *host) {
 
 template <typename C>
 static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, void *x_, bool x_zero,
-                          const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s) {
+                          const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s, bool unscale) {
   const int B = op.B;
   if (B == 0) return DBI_OK;
   const size_t n = size_t(2) * op.nz * op.nx;
@@ -429,8 +472,10 @@ static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, voi
         (rc = read_counter(sb.counters + parity, s, &remaining)))
       return rc;
   }
-  k_scale_x<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x, 1);
-  if ((rc = check_launch("k_scale_x"))) return rc;
+  if (unscale) {
+    k_scale_x<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x, 1);
+    if ((rc = check_launch("k_scale_x"))) return rc;
+  }
   if (status) {
     k_finalize<<<(B + 127) / 128, 128, 0, s>>>(B, sb.st, status->iters, status->relres, status->code);
     if ((rc = check_launch("k_finalize"))) return rc;
@@ -439,9 +484,9 @@ static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, voi
 }
 
 int run_bicgstab(OpArgs op, const SolverBufs &sb, const void *rhs, void *x, bool x_zero,
-                 const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s) {
-  return op.precision == DBI_C64 ? bicgstab_typed<float2>(op, sb, rhs, x, x_zero, o, status, s)
-                                 : bicgstab_typed<double2>(op, sb, rhs, x, x_zero, o, status, s);
+                 const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s, bool unscale) {
+  return op.precision == DBI_C64 ? bicgstab_typed<float2>(op, sb, rhs, x, x_zero, o, status, s, unscale)
+                                 : bicgstab_typed<double2>(op, sb, rhs, x, x_zero, o, status, s, unscale);
 }
 
 int check_krylov(const dbi_krylov_opts *o) {
@@ -486,5 +531,5 @@ extern "C" int ls_solve(const dbi_model *model, const dbi_batch *batch, const vo
   a.B = batch->B; a.nf = batch->nf; a.omega = batch->omega; a.fidx = batch->fidx;
   a.m = model->m; reference_values(model->ref, a.ref);
   a.T = T; a.Ghat = Ghat; a.tw = tw;
-  return run_bicgstab(a, sb, rhs, u, opts->zero_guess != 0, *opts, status, s);
+  return run_bicgstab(a, sb, rhs, u, opts->zero_guess != 0, *opts, status, s, true);
 }

@@ -29,8 +29,10 @@ size_t bytes_solver(const dbi_grid *g, int B, int precision);
 SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision);
 
 // Solves A x = rhs for every problem of `op` (op.in / op.out / op.ident are set internally).
-// x_zero: the initial guess is zero (x is overwritten without being read).
+// x_zero: the initial guess is zero (x is overwritten without being read). The iteration runs on
+// rhs scaled by a power of two per problem (KState::scale, ||scaled rhs|| in [1, 2)); with
+// unscale = false the returned x stays in that scaled system (x = scale * A^{-1} rhs).
 int run_bicgstab(OpArgs op, const SolverBufs &sb, const void *rhs, void *x, bool x_zero,
-                 const dbi_krylov_opts &opts, const dbi_status *status, cudaStream_t s);
+                 const dbi_krylov_opts &opts, const dbi_status *status, cudaStream_t s, bool unscale);
 
 }  // namespace dbi

@@ -27,6 +27,7 @@ template <typename C> struct OpP {
   const C *Ghat;
   const C *tw;
   const int *active;
+  const double *in_scale, *m_scale, *out_scale;
 };
 
 // Elements of one CTA's line buffer and values per thread in the FFT passes.
@@ -49,7 +50,7 @@ template <typename C, int LZ> struct ColCfg {
 // Stress sigma = dC eps at cell (z, x) of D from the staged u; zero outside D.
 template <typename C>
 __device__ __forceinline__ void stress_at(const OpP<C> &p, const C *su, int W, int RS, int z0, int z,
-                                          int x, C &s1, C &s3, C &s5) {
+                                          int x, typename RealOf<C>::type ms, C &s1, C &s3, C &s5) {
   using Rl = typename RealOf<C>::type;
   if (z < 0 || z >= p.nz || x < 0 || x >= p.nx) {
     s1 = s3 = s5 = czero<C>();
@@ -61,10 +62,10 @@ __device__ __forceinline__ void stress_at(const OpP<C> &p, const C *su, int W, i
   const C e3 = cscale(csub(U(1, z + 1, x), U(1, z - 1, x)), p.inv2h);
   const C e5 = cscale(cadd(csub(U(0, z + 1, x), U(0, z - 1, x)), csub(U(1, z, x + 1), U(1, z, x - 1))), p.inv2h);
   const size_t cell = size_t(z) * p.nx + x, plane = size_t(p.nz) * p.nx;
-  const Rl d11 = p.m[1 * plane + cell] - p.ref[1];
-  const Rl d13 = p.m[2 * plane + cell] - p.ref[2];
-  const Rl d33 = p.m[3 * plane + cell] - p.ref[3];
-  const Rl d55 = p.m[4 * plane + cell] - p.ref[4];
+  const Rl d11 = (p.m[1 * plane + cell] - p.ref[1]) * ms;
+  const Rl d13 = (p.m[2 * plane + cell] - p.ref[2]) * ms;
+  const Rl d33 = (p.m[3 * plane + cell] - p.ref[3]) * ms;
+  const Rl d55 = (p.m[4 * plane + cell] - p.ref[4]) * ms;
   s1 = cadd(cscale(e1, d11), cscale(e3, d13));
   s3 = cadd(cscale(e1, d13), cscale(e3, d33));
   s5 = cscale(e5, d55);
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *lines = reinterpret_cast<C *>(smem_raw);  // [2 ROWS][LS], line = c * ROWS + rr
   const C *in = p.in + size_t(b) * 2 * nz * nx;
+  const Rl isc = p.in_scale ? Rl(p.in_scale[b]) : Rl(1);
 
   if constexpr (STENCIL) {
     constexpr int RS = ROWS + 4;
@@ -89,10 +91,12 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
     for (int idx = threadIdx.x; idx < 2 * RS * W; idx += NT) {
       const int c = idx / (RS * W), rem = idx - c * RS * W;
       const int rr = rem / W, xx = rem - rr * W - 1, z = z0 - 2 + rr;
-      su[idx] = (z >= 0 && z < nz && xx >= 0 && xx < nx) ? in[(size_t(c) * nz + z) * nx + xx] : czero<C>();
+      su[idx] = (z >= 0 && z < nz && xx >= 0 && xx < nx) ? cscale(in[(size_t(c) * nz + z) * nx + xx], isc)
+                                                          : czero<C>();
     }
     __syncthreads();
     const double om = p.omega[p.fidx[b]];
+    const Rl ms = p.m_scale ? Rl(p.m_scale[0]) : Rl(1);
     const Rl w2 = Rl(om * om);
     for (int idx = threadIdx.x; idx < ROWS * LX; idx += NT) {
       const int rr = idx / LX, x = idx - rr * LX, z = z0 + rr;
@@ -100,17 +104,17 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
       if (z < nz && x < nx) {
         C a1, a3, a5, b1, b3, b5;
         const size_t cell = size_t(z) * nx + x;
-        const Rl drho = p.m[cell] - p.ref[0];
+        const Rl drho = (p.m[cell] - p.ref[0]) * ms;
         const C u1 = su[(0 * RS + rr + 2) * W + x + 1];
         const C u3 = su[(1 * RS + rr + 2) * W + x + 1];
         // d/dx1 terms: sigma at (z, x +- 1)
-        stress_at(p, su, W, RS, z0, z, x + 1, a1, a3, a5);
-        stress_at(p, su, W, RS, z0, z, x - 1, b1, b3, b5);
+        stress_at(p, su, W, RS, z0, z, x + 1, ms, a1, a3, a5);
+        stress_at(p, su, W, RS, z0, z, x - 1, ms, b1, b3, b5);
         o1 = cscale(csub(a1, b1), p.inv2h);  // d1 sigma1
         o3 = cscale(csub(a5, b5), p.inv2h);  // d1 sigma5
         // d/dx3 terms: sigma at (z +- 1, x)
-        stress_at(p, su, W, RS, z0, z + 1, x, a1, a3, a5);
-        stress_at(p, su, W, RS, z0, z - 1, x, b1, b3, b5);
+        stress_at(p, su, W, RS, z0, z + 1, x, ms, a1, a3, a5);
+        stress_at(p, su, W, RS, z0, z - 1, x, ms, b1, b3, b5);
         o1 = cadd(o1, cscale(csub(a5, b5), p.inv2h));  // d3 sigma5
         o3 = cadd(o3, cscale(csub(a3, b3), p.inv2h));  // d3 sigma3
         o1 = cadd(o1, cscale(u1, w2 * drho));
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
       const int c = idx / (ROWS * LX), rem = idx - c * ROWS * LX;
       const int rr = rem / LX, x = rem - rr * LX, z = z0 + rr;
       lines[(c * ROWS + rr) * LS + x] =
-          (z < nz && x < nx) ? in[(size_t(c) * nz + z) * nx + x] : czero<C>();
+          (z < nz && x < nx) ? cscale(in[(size_t(c) * nz + z) * nx + x], isc) : czero<C>();
     }
   }
   __syncthreads();
@@ -193,12 +197,14 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
   __syncthreads();
   Plan<LX>::template run<C, 2 * ROWS, LS, NT, true>(lines, p.tw);
   const size_t base = size_t(b) * 2 * nz * nx;
+  using Rl = typename RealOf<C>::type;
+  const Rl osc = p.out_scale ? Rl(p.out_scale[b]) : Rl(1);
   for (int idx = threadIdx.x; idx < 2 * ROWS * nx; idx += NT) {
     const int c = idx / (ROWS * nx), rem = idx - c * ROWS * nx;
     const int rr = rem / nx, x = rem - rr * nx, z = z0 + rr;
     if (z < nz) {
       const size_t o = base + (size_t(c) * nz + z) * nx + x;
-      const C v = lines[(c * ROWS + rr) * LS + x];
+      const C v = cscale(lines[(c * ROWS + rr) * LS + x], osc);
       p.out[o] = p.ident ? csub(p.ident[o], v) : v;
     }
   }
@@ -226,6 +232,7 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
   p.Ghat = static_cast<const C *>(a.Ghat);
   p.tw = static_cast<const C *>(a.tw);
   p.active = a.active;
+  p.in_scale = a.in_scale; p.m_scale = a.m_scale; p.out_scale = a.out_scale;
   int rc = DBI_OK;
   const bool stencil = a.stencil;
   prof_mark(PROF_OPERATOR, false, s);
@@ -305,11 +312,16 @@ extern "C" int green_convolve(const dbi_grid *g, const dbi_batch *batch, const v
   Arena ar(work, work_bytes);
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral(g, batch->B, precision));
+  Scales sc = carve_scales(ar, batch->B);
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
+  if ((rc = pow2_scales(src, precision, false, batch->B, size_t(2) * g->nz * g->nx, sc.part, sc.scale, sc.inv,
+                        nullptr, s)))
+    return rc;
   OpArgs a{};
   a.precision = precision; a.nz = g->nz; a.nx = g->nx; a.lz = g->lz; a.lx = g->lx; a.h = g->h;
   a.B = batch->B; a.nf = batch->nf; a.omega = batch->omega; a.fidx = batch->fidx;
   a.stencil = false; a.in = src; a.ident = nullptr; a.out = out; a.T = T; a.Ghat = Ghat; a.tw = tw;
+  a.in_scale = sc.scale; a.out_scale = sc.inv;
   return run_operator(a, s);
 }
 
@@ -326,11 +338,16 @@ extern "C" int ls_apply(const dbi_model *model, const dbi_batch *batch, const vo
   Arena ar(work, work_bytes);
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral(g, batch->B, precision));
+  Scales sc = carve_scales(ar, batch->B);
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
+  if ((rc = pow2_scales(u, precision, false, batch->B, size_t(2) * g->nz * g->nx, sc.part, sc.scale, sc.inv,
+                        nullptr, s)))
+    return rc;
   OpArgs a{};
   a.precision = precision; a.nz = g->nz; a.nx = g->nx; a.lz = g->lz; a.lx = g->lx; a.h = g->h;
   a.B = batch->B; a.nf = batch->nf; a.omega = batch->omega; a.fidx = batch->fidx;
   a.m = model->m; reference_values(model->ref, a.ref);
   a.stencil = true; a.in = u; a.ident = u; a.out = out; a.T = T; a.Ghat = Ghat; a.tw = tw;
+  a.in_scale = sc.scale; a.out_scale = sc.inv;
   return run_operator(a, s);
 }

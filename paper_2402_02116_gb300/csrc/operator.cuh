@@ -26,9 +26,31 @@ struct OpArgs {
   const void *Ghat;     // device [nf][3][lz][lx] complex
   const void *tw;       // device twiddle table of the precision
   const int *active;    // device [B] (0 = skip the problem) or NULL
+  // Exact power-of-two scalings that keep FP32 intermediates in range (each may be NULL):
+  const double *in_scale;   // device [B]: the input field is multiplied by in_scale[b]
+  const double *m_scale;    // device [1]: the contrast (m - ref) is multiplied by m_scale[0]
+  const double *out_scale;  // device [B]: the convolution result is multiplied by out_scale[b]
 };
 
 int run_operator(const OpArgs &a, cudaStream_t s);
+
+// Per-problem power-of-two normalisers of B arrays of n elements each (complex of the precision,
+// or real when `real` is set): scale[b] = 2^-e with ||x_b|| in [2^e, 2^(e+1)), 1 for a zero array.
+// If inv is non-NULL, inv[b] = 1 / (scale[b] * (extra ? extra[0] : 1)). part: bytes_partials(B).
+struct Scales {
+  double *scale, *inv, *mscale, *part;
+};
+inline Scales carve_scales(Arena &ar, int B) {
+  Scales s;
+  s.scale = static_cast<double *>(ar.take(size_t(B) * sizeof(double)));
+  s.inv = static_cast<double *>(ar.take(size_t(B) * sizeof(double)));
+  s.mscale = static_cast<double *>(ar.take(256));
+  s.part = static_cast<double *>(ar.take(bytes_partials(B)));
+  return s;
+}
+
+int pow2_scales(const void *x, int precision, bool real, int B, size_t n, double *part, double *scale,
+                double *inv, const double *extra, cudaStream_t s);
 
 // Reference values (rho, C11, C13, C33, C55) of the isotropic medium (Eq. 4, Eq. 39).
 inline void reference_values(const dbi_medium &r, double out[5]) {

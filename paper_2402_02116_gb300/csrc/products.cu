@@ -27,16 +27,21 @@ __device__ __forceinline__ bool rec_ok(const int *cells, int k, int nz, int nx, 
   return iz >= 0 && iz < nz && ix >= 0 && ix < nx;
 }
 
+// d = fac[b] * P u, the factor applied in FP64
 template <typename C>
-__global__ void k_sample(int B, int nrec, int nz, int nx, const int *cells, const C *u, C *d) {
+__global__ void k_sample(int B, int nrec, int nz, int nx, const int *cells, const C *u, const double *fac, C *d) {
+  using R = typename RealOf<C>::type;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (k >= nrec) return;
   int iz, ix;
   const bool ok = rec_ok(cells, k, nz, nx, iz, ix);
   const size_t base = size_t(b) * 2 * nz * nx;
-  for (int c = 0; c < 2; ++c)
-    d[(size_t(b) * nrec + k) * 2 + c] = ok ? u[base + (size_t(c) * nz + iz) * nx + ix] : czero<C>();
+  const double f = fac[b];
+  for (int c = 0; c < 2; ++c) {
+    const C v = ok ? u[base + (size_t(c) * nz + iz) * nx + ix] : czero<C>();
+    d[(size_t(b) * nrec + k) * 2 + c] = mk<C>(R(double(v.x) * f), R(double(v.y) * f));
+  }
 }
 
 template <typename C>
@@ -84,7 +89,7 @@ template <typename C> __device__ __forceinline__ double re_mul(C a, C b) {
 
 template <typename C, typename GOut>
 __global__ void k_imaging(int B, int nf, int nz, int nx, double h, const double *omega, const int *fidx,
-                          const C *ua, const C *ub, GOut *g) {
+                          const C *ua, const C *ub, const double *src_scale, const KState *st, GOut *g) {
   using R = typename RealOf<C>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int z = blockIdx.y;
@@ -97,15 +102,17 @@ __global__ void k_imaging(int B, int nf, int nz, int nx, double h, const double 
     const C *b1 = ub + size_t(b) * 2 * plane, *b3 = b1 + plane;
     if (unsigned(fidx[b]) >= unsigned(nf)) continue;
     const double w = omega[fidx[b]];
+    // u_a is stored as src_scale[b] * st[b].scale * (the back-propagated field)
+    const double f = 1.0 / (src_scale[b] * st[b].scale);
     C ea1, ea3, ea5, eb1, eb3, eb5;
     strain(a1, a3, nz, nx, z, x, inv2h, ea1, ea3, ea5);
     strain(b1, b3, nz, nx, z, x, inv2h, eb1, eb3, eb5);
     // products in FP64: back-propagated fields can be so small that FP32 products underflow
-    g0 += w * w * (re_mul(a1[cell], b1[cell]) + re_mul(a3[cell], b3[cell]));
-    g1 -= re_mul(ea1, eb1);
-    g2 -= re_mul(ea1, eb3) + re_mul(ea3, eb1);
-    g3 -= re_mul(ea3, eb3);
-    g4 -= re_mul(ea5, eb5);
+    g0 += f * w * w * (re_mul(a1[cell], b1[cell]) + re_mul(a3[cell], b3[cell]));
+    g1 -= f * re_mul(ea1, eb1);
+    g2 -= f * (re_mul(ea1, eb3) + re_mul(ea3, eb1));
+    g3 -= f * re_mul(ea3, eb3);
+    g4 -= f * re_mul(ea5, eb5);
   }
   g[cell] = GOut(g0);
   g[plane + cell] = GOut(g1);
@@ -247,6 +254,7 @@ struct ProdCtx {
   void *T;
   SolverBufs sb;
   void *f1, *f2;  // two fields [B][2][nz][nx]
+  Scales sc;      // power-of-two normalisers of the convolution inputs
   dbi_krylov_opts opts;
   const dbi_status *status;
   cudaStream_t s;
@@ -260,28 +268,37 @@ static OpArgs base_op(const ProdCtx &c) {
   return a;
 }
 
-static int solve_background(const ProdCtx &c, const void *rhs, void *x) {
+static int solve_background(const ProdCtx &c, const void *rhs, void *x, bool unscale) {
   OpArgs a = base_op(c);
   a.m = c.m_b;
   for (int i = 0; i < 5; ++i) a.ref[i] = c.ref[i];
-  return run_bicgstab(a, c.sb, rhs, x, true, c.opts, c.status, c.s);
+  return run_bicgstab(a, c.sb, rhs, x, true, c.opts, c.status, c.s, unscale);
 }
 
-// d = J dm (dm in the precision's real type)
+// d = J dm (dm in the precision's real type). The source is built from u_b scaled by 2^k_b per
+// problem and dm scaled by 2^k_m so that FP32 intermediates stay in range; the sampled data are
+// multiplied back by 2^-(k_b + k_m) in FP64.
 static int frechet_internal(const ProdCtx &c, const void *u_b, const dbi_receivers *rec, const void *dm, void *d) {
   int rc;
+  const int B = c.batch->B;
+  const size_t plane = size_t(c.g->nz) * c.g->nx;
+  if ((rc = pow2_scales(dm, c.precision, true, 1, 5 * plane, c.sc.part, c.sc.mscale, nullptr, nullptr, c.s)))
+    return rc;
+  if ((rc = pow2_scales(u_b, c.precision, false, B, 2 * plane, c.sc.part, c.sc.scale, c.sc.inv, c.sc.mscale, c.s)))
+    return rc;
   OpArgs a = base_op(c);
   a.m = dm;  // the perturbation plays the contrast; nothing to subtract
   a.stencil = true; a.in = u_b; a.ident = nullptr; a.out = c.f1;
+  a.in_scale = c.sc.scale; a.m_scale = c.sc.mscale;
   if ((rc = run_operator(a, c.s))) return rc;
-  if ((rc = solve_background(c, c.f1, c.f2))) return rc;
-  dim3 grid((rec->n + 127) / 128, c.batch->B);
+  if ((rc = solve_background(c, c.f1, c.f2, true))) return rc;
+  dim3 grid((rec->n + 127) / 128, B);
   if (c.precision == DBI_C64)
-    k_sample<float2><<<grid, 128, 0, c.s>>>(c.batch->B, rec->n, c.g->nz, c.g->nx, rec->cells,
-                                            static_cast<const float2 *>(c.f2), static_cast<float2 *>(d));
+    k_sample<float2><<<grid, 128, 0, c.s>>>(B, rec->n, c.g->nz, c.g->nx, rec->cells,
+                                            static_cast<const float2 *>(c.f2), c.sc.inv, static_cast<float2 *>(d));
   else
-    k_sample<double2><<<grid, 128, 0, c.s>>>(c.batch->B, rec->n, c.g->nz, c.g->nx, rec->cells,
-                                             static_cast<const double2 *>(c.f2), static_cast<double2 *>(d));
+    k_sample<double2><<<grid, 128, 0, c.s>>>(B, rec->n, c.g->nz, c.g->nx, rec->cells,
+                                             static_cast<const double2 *>(c.f2), c.sc.inv, static_cast<double2 *>(d));
   return check_launch("k_sample");
 }
 
@@ -305,19 +322,25 @@ static int adjoint_internal(const ProdCtx &c, const void *u_b, const dbi_receive
                                                                  static_cast<const double2 *>(r), static_cast<double2 *>(c.f2));
   }
   if ((rc = check_launch("k_inject_conj"))) return rc;
+  // scale q by 2^k_b per problem; the solver keeps its own power-of-two scale on the solution,
+  // and the imaging multiplies both back in FP64
+  if ((rc = pow2_scales(c.f2, c.precision, false, B, size_t(2) * nz * nx, c.sc.part, c.sc.scale, nullptr,
+                        nullptr, c.s)))
+    return rc;
   OpArgs a = base_op(c);
   a.stencil = false; a.in = c.f2; a.ident = nullptr; a.out = c.f1;
+  a.in_scale = c.sc.scale;
   if ((rc = run_operator(a, c.s))) return rc;
-  if ((rc = solve_background(c, c.f1, c.f2))) return rc;
+  if ((rc = solve_background(c, c.f1, c.f2, false))) return rc;
   dim3 grid((nx + 127) / 128, nz);
   if (c.precision == DBI_C64)
     k_imaging<float2, GOut><<<grid, 128, 0, c.s>>>(B, c.batch->nf, nz, nx, c.g->h, c.batch->omega, c.batch->fidx,
                                                    static_cast<const float2 *>(c.f2),
-                                                   static_cast<const float2 *>(u_b), g);
+                                                   static_cast<const float2 *>(u_b), c.sc.scale, c.sb.st, g);
   else
     k_imaging<double2, GOut><<<grid, 128, 0, c.s>>>(B, c.batch->nf, nz, nx, c.g->h, c.batch->omega, c.batch->fidx,
                                                     static_cast<const double2 *>(c.f2),
-                                                    static_cast<const double2 *>(u_b), g);
+                                                    static_cast<const double2 *>(u_b), c.sc.scale, c.sb.st, g);
   return check_launch("k_imaging");
 }
 
@@ -335,6 +358,7 @@ static int prepare(ProdCtx &c, Arena &ar, const dbi_model *bg, const dbi_batch *
   c.sb = carve_solver(ar, c.g, batch->B, precision);
   c.f1 = ar.take(bytes_field(c.g, batch->B, precision));
   c.f2 = ar.take(bytes_field(c.g, batch->B, precision));
+  c.sc = carve_scales(ar, batch->B);
   c.opts = *opts;
   c.status = status;
   return launch_twiddles(const_cast<void *>(c.tw), precision, c.s);

@@ -241,6 +241,11 @@ def test_data_residual(precision):
 
 @pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
 def test_normal_cg(precision):
+    """complex128: lambda, the residual history and dm match the oracle's CG step for step.
+    complex64: an unconverged CG iterate is sensitive to the operator's rounding (relative noise of
+    1e-5 in each Hessian application moves the 12th oracle iterate by about 6 %), so the check is
+    on what the iterate achieves: the FP64 oracle evaluates the normal-equation residual of the
+    GPU's dm, which must be as small as that of the oracle's own iterate."""
     w = inputs.small_case(nz=8, nx=7, amp=0.1, vti=True, n_src=2, freqs=(8.0, 13.0), seed=41)
     P = DeviceProblem(w, precision)
     orc = oracle_for(w)
@@ -251,13 +256,25 @@ def test_normal_cg(precision):
     tol = 1e-12 if precision == dbi.C128 else 1e-7
     dm, lam, hist = P.normal_cg(P.to_field(U), P.to_field(dd), iters=12, power_start=start, tol=tol)
     want, lam_o, hist_o = orc.normal_cg(w.model, U, fidx, dd, w.rec_cells, iters=12, power_start=start)
-    # complex64: every application of Re J~^H J~ runs two FP32 solves (relative error ~1e-5 each) and
-    # lambda compounds eleven of them; the CG iterates inherit the same level
     lam_err = abs(lam - lam_o) / lam_o
-    hist_err = rel(np.asarray(hist), np.asarray(hist_o))
-    dm_err = rel(npy(dm), want)
-    limits = (1e-8, 1e-7, 1e-7) if precision == dbi.C128 else (5e-4, 1e-3, 1e-3)
-    assert lam_err < limits[0] and hist_err < limits[1] and dm_err < limits[2], (lam_err, hist_err, dm_err)
+    if precision == dbi.C128:
+        assert lam_err < 1e-8
+        assert rel(np.asarray(hist), np.asarray(hist_o)) < 1e-7
+        assert rel(npy(dm), want) < 1e-7
+        return
+    assert lam_err < 5e-4
+    sc = orc.param_scale()[:, None, None]
+
+    def normal_residual(dmv):
+        x = dmv / sc
+        Hx = sc * orc.adjoint(w.model, U, fidx, orc.frechet(w.model, U, fidx, sc * x, w.rec_cells), w.rec_cells)
+        rhs = sc * orc.adjoint(w.model, U, fidx, dd, w.rec_cells)
+        return np.linalg.norm(rhs - Hx - lam_o * x), np.linalg.norm(rhs)
+
+    r_gpu, r0 = normal_residual(npy(dm).astype(np.float64))
+    r_orc, _ = normal_residual(want)
+    assert r_gpu < 1.3 * r_orc and r_gpu < 0.2 * r0, (r_gpu / r0, r_orc / r0)
+    assert hist[-1] < 0.2 * hist[0]
 
 
 # --- the batched-forward workload at full size, in the benchmark's launch configuration --------
