@@ -127,7 +127,8 @@ size_t dbi_workspace_bytes(const dbi_grid *g, int B, int precision, int op);
  *   (the self cell gets the disk average of radius h / sqrt(pi)), places offset d at slot d mod L of
  *   the lz x lx grid (other slots 0), and takes the FP64 2D FFT.
  *   omega  device [nf] angular frequencies.
- *   Ghat   device [nf][3][lz][lx] complex out: h^2 / (lz lx) * FFT(G) for components 11, 13, 33.
+ *   Ghat   device [nf][3][lx][lz] complex out: h^2 / (lz lx) * FFT(G) for components 11, 13, 33,
+ *          stored column-major: entry [f][c][kx][kz] holds wavenumber (kz, kx).
  *   Gspace device [nf][3][lz][lx] complex out (may be NULL): the spatial G_h on the same slots.
  *   Work: DBI_OP_GREENS bytes.
  */

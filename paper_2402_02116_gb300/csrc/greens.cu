@@ -7,8 +7,8 @@
 // (dx h, dz h), |dz| < nz, |dx| < nx, placed at slot (dz mod lz, dx mod lx). The self cell takes
 // the mean of G over the disk of radius h / sqrt(pi): only A survives the angular mean, and
 // the disk mean of H0(k r) is 2 H1(k a)/(k a) - 4i/(pi k^2 a^2). The table is then transformed by
-// an FP64 2D FFT (rows, then columns) and scaled by h^2 / (lz lx), which folds the quadrature
-// weight and the inverse-FFT normalisation of Eq. 12 into it.
+// an FP64 2D FFT (rows, then columns), scaled by h^2 / (lz lx), which folds the quadrature
+// weight and the inverse-FFT normalisation of Eq. 12 into it, and stored column-major.
 #include <cmath>
 
 #include "fft.cuh"
@@ -137,11 +137,28 @@ __global__ void __launch_bounds__(256) k_fft_cols64(double2 *data, int width, co
   }
 }
 
+// Ghat[f][c][kx][kz] = scale * W[f][c][kz][kx]: scaled, rounded and stored column-major (kz
+// contiguous) for the column pass. One 32 x 32 tile per block, transposed through shared memory.
 template <typename C>
-__global__ void k_scale_cast(const double2 *W, C *Ghat, size_t n, double scale) {
+__global__ void k_scale_cast_t(const double2 *W, C *Ghat, int lz, int lx, double scale) {
   using R = typename RealOf<C>::type;
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
-    Ghat[i] = mk<C>(R(W[i].x * scale), R(W[i].y * scale));
+  __shared__ double2 tile[32][33];
+  const size_t plane = size_t(lz) * lx;
+  const double2 *Wm = W + size_t(blockIdx.z) * plane;
+  C *Gm = Ghat + size_t(blockIdx.z) * plane;
+  const int kx0 = blockIdx.x * 32, kz0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int kz = kz0 + i, kx = kx0 + threadIdx.x;
+    if (kz < lz && kx < lx) tile[i][threadIdx.x] = Wm[size_t(kz) * lx + kx];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int kx = kx0 + i, kz = kz0 + threadIdx.x;
+    if (kz < lz && kx < lx) {
+      const double2 w = tile[threadIdx.x][i];
+      Gm[size_t(kx) * lz + kz] = mk<C>(R(w.x * scale), R(w.y * scale));
+    }
+  }
 }
 
 template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
@@ -232,12 +249,13 @@ extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const d
                                                 ref->alpha0, ref->beta0, W, static_cast<double2 *>(Gspace));
   if ((rc = check_launch("k_green_space"))) return rc;
   if ((rc = fft2_fp64(W, 3 * nf, g->lz, g->lx, tw, s))) return rc;
-  const size_t n = size_t(nf) * 3 * g->lz * g->lx;
   const double scale = g->h * g->h / (double(g->lz) * double(g->lx));
-  const int blocks = int((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  if (precision == DBI_C64) k_scale_cast<float2><<<blocks, 256, 0, s>>>(W, static_cast<float2 *>(Ghat), n, scale);
-  else k_scale_cast<double2><<<blocks, 256, 0, s>>>(W, static_cast<double2 *>(Ghat), n, scale);
-  return check_launch("k_scale_cast");
+  const dim3 tgrid((g->lx + 31) / 32, (g->lz + 31) / 32, 3 * nf), tblock(32, 8);
+  if (precision == DBI_C64)
+    k_scale_cast_t<float2><<<tgrid, tblock, 0, s>>>(W, static_cast<float2 *>(Ghat), g->lz, g->lx, scale);
+  else
+    k_scale_cast_t<double2><<<tgrid, tblock, 0, s>>>(W, static_cast<double2 *>(Ghat), g->lz, g->lx, scale);
+  return check_launch("k_scale_cast_t");
 }
 
 extern "C" int incident_field(const dbi_grid *g, const dbi_batch *batch, const void *Gspace,

@@ -2,12 +2,18 @@
 // plain Green's convolution, both evaluated by Eq. 12 on the zero-padded lz x lx grid as three
 // kernels per batch:
 //   k_rows_forward : contrast source by central differences (fields zero outside D) for a few rows,
-//                    zero-pad each row to lx, forward FFT along x  -> T[b][c][z][kx]   (z < nz)
-//   k_cols         : for a tile of kx columns, forward FFT along z of the nz non-zero rows padded
-//                    to lz, 2x2 multiply by Ghat(kz, kx), inverse FFT along z, keep z < nz -> T
-//   k_rows_inverse : inverse FFT along x, keep x < nx, out = ident - result (or the result).
+//                    zero-pad each row to lx, forward FFT along x  -> T[b][c][kx][z]   (z < nz)
+//                    (the stress of each cell is formed once, in shared memory; the spectra are
+//                    transposed through shared memory so that T is column-major)
+//   k_cols         : for a few kx columns, forward FFT along z of the nz non-zero rows padded to
+//                    lz, 2x2 multiply by Ghat(kz, kx), inverse FFT along z, keep z < nz -> T
+//                    (contiguous column reads and writes, one named barrier per column)
+//   k_rows_inverse : transpose rows back, inverse FFT along x, keep x < nx,
+//                    out = ident - result (or the result).
 // Ghat already carries h^2 / (lz lx), so no other scaling is applied.
-#include "fft.cuh"
+#include <algorithm>
+
+#include "fft_reg.cuh"
 #include "operator.cuh"
 
 namespace dbi {
@@ -30,187 +36,293 @@ template <typename C> struct OpP {
   const double *in_scale, *m_scale, *out_scale;
 };
 
-// Elements of one CTA's line buffer and values per thread in the FFT passes.
+// Launch shapes. Rows kernels: ROWS rows per CTA, T = L/8 threads per row (t fastest), both
+// components of a row held by each thread. Column kernel: CC columns per CTA, thread (c, t) with c
+// fastest so that a warp reads CC adjacent columns of a row.
 template <typename C> struct Cfg;
-template <> struct Cfg<float2> { static constexpr int rowElems = 4096, colElems = 8192, vpt = 16; };
-template <> struct Cfg<double2> { static constexpr int rowElems = 2048, colElems = 4096, vpt = 8; };
+template <> struct Cfg<float2> { static constexpr int rowThreads = 256, colThreads = 256, colMinBlocks = 3; };
+template <> struct Cfg<double2> { static constexpr int rowThreads = 256, colThreads = 256, colMinBlocks = 1; };
 
 template <typename C, int LX> struct RowCfg {
-  static constexpr int ROWS = Cfg<C>::rowElems / (2 * LX) > 0 ? Cfg<C>::rowElems / (2 * LX) : 1;
-  static constexpr int NT = 2 * ROWS * LX / Cfg<C>::vpt;
-  static constexpr int LS = LX + 1;
+  static constexpr int T = LX / 8;
+  static constexpr int ROWS = Cfg<C>::rowThreads / T > 0 ? Cfg<C>::rowThreads / T : 1;
+  static constexpr int NT = ROWS * T;
+  static constexpr int LP = RegFFT<C, LX>::LP;
 };
 template <typename C, int LZ> struct ColCfg {
-  static constexpr int CCr = Cfg<C>::colElems / (2 * LZ);
-  static constexpr int CC = CCr > 64 ? 64 : (CCr > 0 ? CCr : 1);
-  static constexpr int NT = 2 * CC * LZ / Cfg<C>::vpt;
-  static constexpr int LS = LZ + 1;
+  static constexpr int T = LZ / 8;
+  static constexpr int CCr = Cfg<C>::colThreads / T;
+  static constexpr int CC = CCr > 15 ? 15 : (CCr > 0 ? CCr : 1);  // named barriers 1..15
+  static constexpr int NT = CC * T;
+  static constexpr int LP = RegFFT<C, LZ>::LP;
+};
+// Transposition tile of the rows kernels: [2][LX][ROWS + 1] (padded against bank conflicts).
+template <typename C, int LX> constexpr size_t tile_elems() {
+  return size_t(2) * LX * (RowCfg<C, LX>::ROWS + 1);
+}
+
+// Barrier over the threads that share a line: the T threads of one row (rows kernels).
+template <int T> struct RowSync {
+  int id;
+  __device__ __forceinline__ void operator()() const {
+    if constexpr (T <= 32) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(T) : "memory");
+    }
+  }
+};
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
 
-// Stress sigma = dC eps at cell (z, x) of D from the staged u; zero outside D.
+// Stress sigma = dC eps at cell (z, x) of D (zero outside D), from the staged u (rows z0 - 2 ..
+// z0 + ROWS + 1 with a zero column on each side; u already multiplied by its input scale).
 template <typename C>
-__device__ __forceinline__ void stress_at(const OpP<C> &p, const C *su, int W, int RS, int z0, int z,
-                                          int x, typename RealOf<C>::type ms, C &s1, C &s3, C &s5) {
+__device__ __forceinline__ void stress_at(const OpP<C> &p, const C *su, int RS, int W, int z0, int z, int x,
+                                          typename RealOf<C>::type ms, C &s1, C &s3, C &s5) {
   using Rl = typename RealOf<C>::type;
-  if (z < 0 || z >= p.nz || x < 0 || x >= p.nx) {
+  const int nz = p.nz, nx = p.nx;
+  if (z < 0 || z >= nz || x < 0 || x >= nx) {
     s1 = s3 = s5 = czero<C>();
     return;
   }
-  // su[c][rr][xx]: rr = z - (z0 - 2), xx = x + 1
   auto U = [&](int c, int zz, int xx) { return su[(c * RS + (zz - z0 + 2)) * W + xx + 1]; };
-  const C e1 = cscale(csub(U(0, z, x + 1), U(0, z, x - 1)), p.inv2h);
-  const C e3 = cscale(csub(U(1, z + 1, x), U(1, z - 1, x)), p.inv2h);
-  const C e5 = cscale(cadd(csub(U(0, z + 1, x), U(0, z - 1, x)), csub(U(1, z, x + 1), U(1, z, x - 1))), p.inv2h);
-  const size_t cell = size_t(z) * p.nx + x, plane = size_t(p.nz) * p.nx;
-  const Rl d11 = (p.m[1 * plane + cell] - p.ref[1]) * ms;
-  const Rl d13 = (p.m[2 * plane + cell] - p.ref[2]) * ms;
-  const Rl d33 = (p.m[3 * plane + cell] - p.ref[3]) * ms;
-  const Rl d55 = (p.m[4 * plane + cell] - p.ref[4]) * ms;
+  const Rl f = p.inv2h;
+  const C e1 = cscale(csub(U(0, z, x + 1), U(0, z, x - 1)), f);
+  const C e3 = cscale(csub(U(1, z + 1, x), U(1, z - 1, x)), f);
+  const C e5 = cscale(cadd(csub(U(0, z + 1, x), U(0, z - 1, x)), csub(U(1, z, x + 1), U(1, z, x - 1))), f);
+  const size_t cell = size_t(z) * nx + x, plane = size_t(nz) * nx;
+  const Rl d11 = (__ldg(p.m + 1 * plane + cell) - p.ref[1]) * ms;
+  const Rl d13 = (__ldg(p.m + 2 * plane + cell) - p.ref[2]) * ms;
+  const Rl d33 = (__ldg(p.m + 3 * plane + cell) - p.ref[3]) * ms;
+  const Rl d55 = (__ldg(p.m + 4 * plane + cell) - p.ref[4]) * ms;
   s1 = cadd(cscale(e1, d11), cscale(e3, d13));
   s3 = cadd(cscale(e1, d13), cscale(e3, d33));
   s5 = cscale(e5, d55);
 }
 
+// Copy n elements with a strided index map into shared memory, four global loads in flight per
+// thread before their stores.
+template <typename C, int NT, typename Src, typename Dst>
+__device__ __forceinline__ void staged_copy(int n, Src &&src, Dst &&dst) {
+  for (int base = threadIdx.x; base < n; base += 4 * NT) {
+    C v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = base + i * NT;
+      v[i] = idx < n ? src(idx) : czero<C>();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = base + i * NT;
+      if (idx < n) dst(idx, v[i]);
+    }
+  }
+}
+
+// Contrast source (or the raw source) of ROWS rows, zero-padded to LX, forward FFT along x.
+//   stencil: stress of rows z0-1 .. z0+ROWS (each computed once, kept in shared memory), then
+//            s1 = w^2 drho u1 + d1 sigma1 + d3 sigma5, s3 = w^2 drho u3 + d1 sigma5 + d3 sigma3.
 template <typename C, int LX, bool STENCIL>
 __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
   using Rl = typename RealOf<C>::type;
-  constexpr int ROWS = RowCfg<C, LX>::ROWS, NT = RowCfg<C, LX>::NT, LS = RowCfg<C, LX>::LS;
+  using RC = RowCfg<C, LX>;
+  constexpr int ROWS = RC::ROWS, T = RC::T, LP = RC::LP;
   const int b = blockIdx.y;
   if ((p.active && !p.active[b]) || unsigned(p.fidx[b]) >= unsigned(p.nf)) return;
   const int z0 = blockIdx.x * ROWS;
   const int nz = p.nz, nx = p.nx;
+  const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *lines = reinterpret_cast<C *>(smem_raw);  // [2 ROWS][LS], line = c * ROWS + rr
-  const C *in = p.in + size_t(b) * 2 * nz * nx;
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  const size_t plane = size_t(nz) * nx;
+  const C *u1 = p.in + size_t(b) * 2 * plane, *u3 = u1 + plane;
   const Rl isc = p.in_scale ? Rl(p.in_scale[b]) : Rl(1);
+  C v[2][8];
 
   if constexpr (STENCIL) {
-    constexpr int RS = ROWS + 4;
-    const int W = nx + 2;
-    C *su = lines + 2 * ROWS * LS;  // [2][ROWS + 4][nx + 2]
-    for (int idx = threadIdx.x; idx < 2 * RS * W; idx += NT) {
-      const int c = idx / (RS * W), rem = idx - c * RS * W;
-      const int rr = rem / W, xx = rem - rr * W - 1, z = z0 - 2 + rr;
-      su[idx] = (z >= 0 && z < nz && xx >= 0 && xx < nx) ? cscale(in[(size_t(c) * nz + z) * nx + xx], isc)
-                                                          : czero<C>();
+    const int W = nx + 2;          // rows with one zero column on each side
+    constexpr int RS = ROWS + 4;   // staged u rows z0 - 2 .. z0 + ROWS + 1
+    C *sg = smem;                  // [3][ROWS + 2][W] stress
+    C *su = smem + size_t(3) * (ROWS + 2) * W;  // [2][RS][W] u
+    staged_copy<C, RC::NT>(
+        2 * RS * W,
+        [&](int idx) {
+          const int c = idx / (RS * W), rem = idx - c * RS * W;
+          const int r = rem / W, xx = rem - r * W - 1, zz = z0 - 2 + r;
+          return (zz >= 0 && zz < nz && xx >= 0 && xx < nx) ? cscale(__ldg((c ? u3 : u1) + size_t(zz) * nx + xx), isc)
+                                                            : czero<C>();
+        },
+        [&](int idx, C val) { su[idx] = val; });
+    __syncthreads();
+    const Rl ms = p.m_scale ? Rl(p.m_scale[0]) : Rl(1);
+    for (int idx = threadIdx.x; idx < (ROWS + 2) * W; idx += RC::NT) {
+      const int r2 = idx / W, xx = idx - r2 * W - 1, zz = z0 - 1 + r2;
+      C a1, a3, a5;
+      stress_at(p, su, RS, W, z0, zz, xx, ms, a1, a3, a5);
+      sg[(0 * (ROWS + 2) + r2) * W + xx + 1] = a1;
+      sg[(1 * (ROWS + 2) + r2) * W + xx + 1] = a3;
+      sg[(2 * (ROWS + 2) + r2) * W + xx + 1] = a5;
     }
     __syncthreads();
-    const double om = p.omega[p.fidx[b]];
-    const Rl ms = p.m_scale ? Rl(p.m_scale[0]) : Rl(1);
-    const Rl w2 = Rl(om * om);
-    for (int idx = threadIdx.x; idx < ROWS * LX; idx += NT) {
-      const int rr = idx / LX, x = idx - rr * LX, z = z0 + rr;
+    const Rl w2 = Rl(p.omega[p.fidx[b]] * p.omega[p.fidx[b]]);
+    auto S = [&](int c, int r2, int xx) { return sg[(c * (ROWS + 2) + r2) * W + xx + 1]; };
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int x = t + m * T;
       C o1 = czero<C>(), o3 = czero<C>();
       if (z < nz && x < nx) {
-        C a1, a3, a5, b1, b3, b5;
+        const int r2 = rr + 1;
+        o1 = cadd(csub(S(0, r2, x + 1), S(0, r2, x - 1)), csub(S(2, r2 + 1, x), S(2, r2 - 1, x)));
+        o3 = cadd(csub(S(2, r2, x + 1), S(2, r2, x - 1)), csub(S(1, r2 + 1, x), S(1, r2 - 1, x)));
+        o1 = cscale(o1, p.inv2h);
+        o3 = cscale(o3, p.inv2h);
         const size_t cell = size_t(z) * nx + x;
-        const Rl drho = (p.m[cell] - p.ref[0]) * ms;
-        const C u1 = su[(0 * RS + rr + 2) * W + x + 1];
-        const C u3 = su[(1 * RS + rr + 2) * W + x + 1];
-        // d/dx1 terms: sigma at (z, x +- 1)
-        stress_at(p, su, W, RS, z0, z, x + 1, ms, a1, a3, a5);
-        stress_at(p, su, W, RS, z0, z, x - 1, ms, b1, b3, b5);
-        o1 = cscale(csub(a1, b1), p.inv2h);  // d1 sigma1
-        o3 = cscale(csub(a5, b5), p.inv2h);  // d1 sigma5
-        // d/dx3 terms: sigma at (z +- 1, x)
-        stress_at(p, su, W, RS, z0, z + 1, x, ms, a1, a3, a5);
-        stress_at(p, su, W, RS, z0, z - 1, x, ms, b1, b3, b5);
-        o1 = cadd(o1, cscale(csub(a5, b5), p.inv2h));  // d3 sigma5
-        o3 = cadd(o3, cscale(csub(a3, b3), p.inv2h));  // d3 sigma3
-        o1 = cadd(o1, cscale(u1, w2 * drho));
-        o3 = cadd(o3, cscale(u3, w2 * drho));
+        const Rl wr = w2 * (__ldg(p.m + cell) - p.ref[0]) * ms;
+        o1 = cadd(o1, cscale(su[(0 * RS + rr + 2) * W + x + 1], wr));
+        o3 = cadd(o3, cscale(su[(1 * RS + rr + 2) * W + x + 1], wr));
       }
-      lines[rr * LS + x] = o1;
-      lines[(ROWS + rr) * LS + x] = o3;
+      v[0][m] = o1;
+      v[1][m] = o3;
     }
+    __syncthreads();  // the FFT lines reuse the staging buffers
   } else {
-    for (int idx = threadIdx.x; idx < 2 * ROWS * LX; idx += NT) {
-      const int c = idx / (ROWS * LX), rem = idx - c * ROWS * LX;
-      const int rr = rem / LX, x = rem - rr * LX, z = z0 + rr;
-      lines[(c * ROWS + rr) * LS + x] =
-          (z < nz && x < nx) ? cscale(in[(size_t(c) * nz + z) * nx + x], isc) : czero<C>();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int x = t + m * T;
+      const bool in = z < nz && x < nx;
+      v[0][m] = in ? cscale(__ldg(u1 + size_t(z) * nx + x), isc) : czero<C>();
+      v[1][m] = in ? cscale(__ldg(u3 + size_t(z) * nx + x), isc) : czero<C>();
     }
   }
+  C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
+  RegPlan<LX>::template run<C, 2, false>(v, lines, t, p.tw, RowSync<T>{1 + rr});
+  // transpose through shared memory: tile[c][kx][rr], then ROWS consecutive z per kx
   __syncthreads();
-  Plan<LX>::template run<C, 2 * ROWS, LS, NT, false>(lines, p.tw);
-  C *T = p.T + size_t(b) * 2 * nz * LX;
-  for (int idx = threadIdx.x; idx < 2 * ROWS * LX; idx += NT) {
-    const int c = idx / (ROWS * LX), rem = idx - c * ROWS * LX;
-    const int rr = rem / LX, x = rem - rr * LX, z = z0 + rr;
-    if (z < nz) T[(size_t(c) * nz + z) * LX + x] = lines[(c * ROWS + rr) * LS + x];
+  constexpr int RP = ROWS + 1;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) smem[(size_t(c) * LX + t + m * T) * RP + rr] = v[c][m];
+  __syncthreads();
+  C *Tb = p.T + size_t(b) * 2 * LX * nz;
+  for (int idx = threadIdx.x; idx < 2 * LX * ROWS; idx += RC::NT) {
+    const int r = idx % ROWS, ck = idx / ROWS;  // ck = c * LX + kx
+    if (z0 + r < nz) Tb[size_t(ck) * nz + z0 + r] = smem[size_t(ck) * RP + r];
   }
 }
 
+// For CC columns kx: forward FFT along z of the nz non-zero rows padded to LZ, 2x2 multiply by
+// Ghat(kz, kx), inverse FFT along z, keep z < nz. Thread (col, t), t fastest: a warp reads a
+// contiguous run of one column; the T threads of a column share a named barrier.
 template <typename C, int LZ>
-__global__ void __launch_bounds__(ColCfg<C, LZ>::NT) k_cols(OpP<C> p) {
-  constexpr int CC = ColCfg<C, LZ>::CC, NT = ColCfg<C, LZ>::NT, LS = ColCfg<C, LZ>::LS;
+__global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_cols(OpP<C> p) {
+  using CF = ColCfg<C, LZ>;
+  constexpr int CC = CF::CC, T = CF::T, LP = CF::LP;
   const int b = blockIdx.y;
   if ((p.active && !p.active[b]) || unsigned(p.fidx[b]) >= unsigned(p.nf)) return;
-  const int kx0 = blockIdx.x * CC;
+  const int col = threadIdx.x / T, t = threadIdx.x - col * T;
+  const int kx = blockIdx.x * CC + col;
   const int nz = p.nz, lx = p.lx;
+  const bool live = kx < lx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *lines = reinterpret_cast<C *>(smem_raw);  // [2 CC][LS], line = c * CC + j
-  C *T = p.T + size_t(b) * 2 * nz * lx;
-  for (int idx = threadIdx.x; idx < 2 * CC * LZ; idx += NT) {
-    const int c = idx / (CC * LZ), rem = idx - c * CC * LZ;
-    const int z = rem / CC, j = rem - z * CC, kx = kx0 + j;
-    lines[(c * CC + j) * LS + z] = (z < nz && kx < lx) ? T[(size_t(c) * nz + z) * lx + kx] : czero<C>();
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  C *Tb = p.T + size_t(b) * 2 * lx * nz;
+  const C *c0 = Tb + size_t(kx) * nz, *c1 = Tb + (size_t(lx) + kx) * nz;
+  C v[2][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int z = t + m * T;
+    const bool in = live && z < nz;
+    v[0][m] = in ? c0[z] : czero<C>();
+    v[1][m] = in ? c1[z] : czero<C>();
   }
-  __syncthreads();
-  Plan<LZ>::template run<C, 2 * CC, LS, NT, false>(lines, p.tw);
-  const C *G = p.Ghat + size_t(p.fidx[b]) * 3 * LZ * lx;
-  for (int idx = threadIdx.x; idx < CC * LZ; idx += NT) {
-    const int kz = idx / CC, j = idx - kz * CC, kx = kx0 + j;
-    if (kx < lx) {
-      const C g11 = G[(size_t(0) * LZ + kz) * lx + kx];
-      const C g13 = G[(size_t(1) * LZ + kz) * lx + kx];
-      const C g33 = G[(size_t(2) * LZ + kz) * lx + kx];
-      const C s1 = lines[j * LS + kz], s3 = lines[(CC + j) * LS + kz];
-      lines[j * LS + kz] = cadd(cmul(g11, s1), cmul(g13, s3));
-      lines[(CC + j) * LS + kz] = cadd(cmul(g13, s1), cmul(g33, s3));
+  C *const lines[2] = {smem + size_t(col) * LP, smem + size_t(CC + col) * LP};
+  RegPlan<LZ>::template run<C, 2, false>(v, lines, t, p.tw, RowSync<T>{1 + col});
+  if (live) {
+    const size_t plane = size_t(lx) * LZ;
+    const C *G = p.Ghat + size_t(p.fidx[b]) * 3 * plane + size_t(kx) * LZ;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int kz = t + m * T;
+      const C g11 = __ldg(G + kz), g13 = __ldg(G + plane + kz), g33 = __ldg(G + 2 * plane + kz);
+      const C s1 = v[0][m], s3 = v[1][m];
+      v[0][m] = cadd(cmul(g11, s1), cmul(g13, s3));
+      v[1][m] = cadd(cmul(g13, s1), cmul(g33, s3));
     }
   }
-  __syncthreads();
-  Plan<LZ>::template run<C, 2 * CC, LS, NT, true>(lines, p.tw);
-  for (int idx = threadIdx.x; idx < 2 * CC * LZ; idx += NT) {
-    const int c = idx / (CC * LZ), rem = idx - c * CC * LZ;
-    const int z = rem / CC, j = rem - z * CC, kx = kx0 + j;
-    if (z < nz && kx < lx) T[(size_t(c) * nz + z) * lx + kx] = lines[(c * CC + j) * LS + z];
+  RegPlan<LZ>::template run<C, 2, true>(v, lines, t, p.tw, RowSync<T>{1 + col});
+  if (live) {
+    C *o0 = Tb + size_t(kx) * nz, *o1 = Tb + (size_t(lx) + kx) * nz;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int z = t + m * T;
+      if (z < nz) {
+        o0[z] = v[0][m];
+        o1[z] = v[1][m];
+      }
+    }
   }
 }
 
+// Inverse FFT along x of ROWS rows, keep x < nx, out = ident - out_scale * result (or the scaled
+// result when there is no identity term).
 template <typename C, int LX>
 __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
-  constexpr int ROWS = RowCfg<C, LX>::ROWS, NT = RowCfg<C, LX>::NT, LS = RowCfg<C, LX>::LS;
+  using Rl = typename RealOf<C>::type;
+  using RC = RowCfg<C, LX>;
+  constexpr int ROWS = RC::ROWS, T = RC::T, LP = RC::LP;
   const int b = blockIdx.y;
   if ((p.active && !p.active[b]) || unsigned(p.fidx[b]) >= unsigned(p.nf)) return;
   const int z0 = blockIdx.x * ROWS;
   const int nz = p.nz, nx = p.nx;
+  const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *lines = reinterpret_cast<C *>(smem_raw);
-  const C *T = p.T + size_t(b) * 2 * nz * LX;
-  for (int idx = threadIdx.x; idx < 2 * ROWS * LX; idx += NT) {
-    const int c = idx / (ROWS * LX), rem = idx - c * ROWS * LX;
-    const int rr = rem / LX, x = rem - rr * LX, z = z0 + rr;
-    lines[(c * ROWS + rr) * LS + x] = z < nz ? T[(size_t(c) * nz + z) * LX + x] : czero<C>();
-  }
-  __syncthreads();
-  Plan<LX>::template run<C, 2 * ROWS, LS, NT, true>(lines, p.tw);
-  const size_t base = size_t(b) * 2 * nz * nx;
-  using Rl = typename RealOf<C>::type;
-  const Rl osc = p.out_scale ? Rl(p.out_scale[b]) : Rl(1);
-  for (int idx = threadIdx.x; idx < 2 * ROWS * nx; idx += NT) {
-    const int c = idx / (ROWS * nx), rem = idx - c * ROWS * nx;
-    const int rr = rem / nx, x = rem - rr * nx, z = z0 + rr;
-    if (z < nz) {
-      const size_t o = base + (size_t(c) * nz + z) * nx + x;
-      const C v = cscale(lines[(c * ROWS + rr) * LS + x], osc);
-      p.out[o] = p.ident ? csub(p.ident[o], v) : v;
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  const C *Tb = p.T + size_t(b) * 2 * LX * nz;
+  // ROWS consecutive z of every (c, kx) into tile[c][kx][r], then each thread takes its row
+  constexpr int RP = ROWS + 1, NLD = 2 * LX * ROWS / RC::NT;
+  static_assert((2 * LX * ROWS) % RC::NT == 0, "tile load");
+  {
+    C ld[NLD];
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {  // all loads in flight before the shared-memory stores
+      const int idx = threadIdx.x + i * RC::NT, r = idx % ROWS, ck = idx / ROWS;
+      ld[i] = z0 + r < nz ? Tb[size_t(ck) * nz + z0 + r] : czero<C>();
+    }
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int idx = threadIdx.x + i * RC::NT, r = idx % ROWS, ck = idx / ROWS;
+      smem[size_t(ck) * RP + r] = ld[i];
     }
   }
+  __syncthreads();
+  C v[2][8];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[c][m] = smem[(size_t(c) * LX + t + m * T) * RP + rr];
+  __syncthreads();  // the FFT lines reuse the tile
+  C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
+  RegPlan<LX>::template run<C, 2, true>(v, lines, t, p.tw, RowSync<T>{1 + rr});
+  if (z >= nz) return;
+  const Rl osc = p.out_scale ? Rl(p.out_scale[b]) : Rl(1);
+  const size_t base = size_t(b) * 2 * nz * nx + size_t(z) * nx;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int x = t + m * T;
+      if (x < nx) {
+        const size_t o = base + size_t(c) * nz * nx + x;
+        const C r = cscale(v[c][m], osc);
+        p.out[o] = p.ident ? csub(p.ident[o], r) : r;
+      }
+    }
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory once per device.
+// Opt a kernel into more than 48 KB of dynamic shared memory.
 template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
@@ -239,16 +351,18 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
   prof_mark(PROF_ROWS_FORWARD, false, s);
   dispatch_len(a.lx, [&]<int LX>() {
     using RC = RowCfg<C, LX>;
-    const size_t lines = size_t(2) * RC::ROWS * RC::LS * sizeof(C);
-    const size_t su = stencil ? size_t(2) * (RC::ROWS + 4) * (a.nx + 2) * sizeof(C) : 0;
+    const size_t lines = size_t(2) * RC::ROWS * RC::LP * sizeof(C);
+    const size_t tile = tile_elems<C, LX>() * sizeof(C);
+    const size_t sg = stencil ? (size_t(3) * (RC::ROWS + 2) + size_t(2) * (RC::ROWS + 4)) * (a.nx + 2) * sizeof(C) : 0;
+    const size_t bytes = std::max(std::max(lines, tile), sg);
     dim3 grid((a.nz + RC::ROWS - 1) / RC::ROWS, a.B);
     cudaError_t e;
     if (stencil) {
-      e = allow_smem(k_rows_forward<C, LX, true>, lines + su);
-      if (e == cudaSuccess) k_rows_forward<C, LX, true><<<grid, RC::NT, lines + su, s>>>(p);
+      e = allow_smem(k_rows_forward<C, LX, true>, bytes);
+      if (e == cudaSuccess) k_rows_forward<C, LX, true><<<grid, RC::NT, bytes, s>>>(p);
     } else {
-      e = allow_smem(k_rows_forward<C, LX, false>, lines);
-      if (e == cudaSuccess) k_rows_forward<C, LX, false><<<grid, RC::NT, lines, s>>>(p);
+      e = allow_smem(k_rows_forward<C, LX, false>, bytes);
+      if (e == cudaSuccess) k_rows_forward<C, LX, false><<<grid, RC::NT, bytes, s>>>(p);
     }
     rc = e != cudaSuccess ? cuda_fail("k_rows_forward smem", e) : check_launch("k_rows_forward");
   });
@@ -256,11 +370,11 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
   if (rc) return rc;
   prof_mark(PROF_COLS, false, s);
   dispatch_len(a.lz, [&]<int LZ>() {
-    using CCfg = ColCfg<C, LZ>;
-    const size_t bytes = size_t(2) * CCfg::CC * CCfg::LS * sizeof(C);
-    dim3 grid((a.lx + CCfg::CC - 1) / CCfg::CC, a.B);
+    using CF = ColCfg<C, LZ>;
+    const size_t bytes = size_t(2) * CF::CC * CF::LP * sizeof(C);
+    dim3 grid((a.lx + CF::CC - 1) / CF::CC, a.B);
     cudaError_t e = allow_smem(k_cols<C, LZ>, bytes);
-    if (e == cudaSuccess) k_cols<C, LZ><<<grid, CCfg::NT, bytes, s>>>(p);
+    if (e == cudaSuccess) k_cols<C, LZ><<<grid, CF::NT, bytes, s>>>(p);
     rc = e != cudaSuccess ? cuda_fail("k_cols smem", e) : check_launch("k_cols");
   });
   prof_mark(PROF_COLS, true, s);
@@ -268,7 +382,7 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
   prof_mark(PROF_ROWS_INVERSE, false, s);
   dispatch_len(a.lx, [&]<int LX>() {
     using RC = RowCfg<C, LX>;
-    const size_t bytes = size_t(2) * RC::ROWS * RC::LS * sizeof(C);
+    const size_t bytes = std::max(size_t(2) * RC::ROWS * RC::LP, tile_elems<C, LX>()) * sizeof(C);
     dim3 grid((a.nz + RC::ROWS - 1) / RC::ROWS, a.B);
     cudaError_t e = allow_smem(k_rows_inverse<C, LX>, bytes);
     if (e == cudaSuccess) k_rows_inverse<C, LX><<<grid, RC::NT, bytes, s>>>(p);

@@ -22,8 +22,8 @@ struct OpArgs {
   const void *in;       // device [B][2][nz][nx] complex
   const void *ident;    // device [B][2][nz][nx] complex or NULL
   void *out;            // device [B][2][nz][nx] complex
-  void *T;              // device [B][2][nz][lx] complex scratch
-  const void *Ghat;     // device [nf][3][lz][lx] complex
+  void *T;              // device [B][2][lx][nz] complex scratch (column-major spectra)
+  const void *Ghat;     // device [nf][3][lx][lz] complex (column-major)
   const void *tw;       // device twiddle table of the precision
   const int *active;    // device [B] (0 = skip the problem) or NULL
   // Exact power-of-two scalings that keep FP32 intermediates in range (each may be NULL):

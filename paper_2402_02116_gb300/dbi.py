@@ -228,13 +228,14 @@ def profile_end():
 # ---------------------------------------------------------------------------------------------
 def greens_tabulate(grid: Grid, ref: Medium, omega: torch.Tensor, precision: int = C64,
                     with_space: bool = True):
-    """Ghat [nf][3][lz][lx] (h^2/(lz lx) FFT(G)) and, if asked, Gspace [nf][3][lz][lx]."""
+    """Ghat [nf][3][lx][lz] (h^2/(lz lx) FFT(G), column-major) and, if asked, Gspace
+    [nf][3][lz][lx]."""
     _need_cuda(omega)
     dev = omega.device
     nf = int(omega.numel())
     cd = complex_dtype(precision)
-    Ghat = torch.empty((nf, 3, grid.lz, grid.lx), dtype=cd, device=dev)
-    Gspace = torch.empty_like(Ghat) if with_space else None
+    Ghat = torch.empty((nf, 3, grid.lx, grid.lz), dtype=cd, device=dev)
+    Gspace = torch.empty((nf, 3, grid.lz, grid.lx), dtype=cd, device=dev) if with_space else None
     work, n = _work(grid, nf, precision, OP_GREENS, dev)
     _check(load().greens_tabulate(ctypes.byref(grid), ctypes.byref(ref), _ptr(omega), nf, precision,
                                   _ptr(Ghat), _ptr(Gspace), _ptr(work), n, _stream(dev)), "greens_tabulate")
