@@ -78,9 +78,11 @@ template <typename C> __device__ __forceinline__ C from_z(double2 z) {
   return mk<C>(R(z.x), R(z.y));
 }
 
+// Grid-stride loop over the n elements of problem blockIdx.y (unrolled for memory parallelism).
 #define DBI_PROBLEM_LOOP(n)                                                                   \
   const int b = blockIdx.y;                                                                   \
   const size_t off = size_t(b) * (n);                                                         \
+  _Pragma("unroll 4")                                                                         \
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < (n); i += size_t(gridDim.x) * blockDim.x)
 
 // ||rhs||^2 with every square formed in FP64: the right-hand side may lie far from unit scale

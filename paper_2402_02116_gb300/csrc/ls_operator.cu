@@ -102,25 +102,6 @@ __device__ __forceinline__ void stress_at(const OpP<C> &p, const C *su, int RS, 
   s5 = cscale(e5, d55);
 }
 
-// Copy n elements with a strided index map into shared memory, four global loads in flight per
-// thread before their stores.
-template <typename C, int NT, typename Src, typename Dst>
-__device__ __forceinline__ void staged_copy(int n, Src &&src, Dst &&dst) {
-  for (int base = threadIdx.x; base < n; base += 4 * NT) {
-    C v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int idx = base + i * NT;
-      v[i] = idx < n ? src(idx) : czero<C>();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int idx = base + i * NT;
-      if (idx < n) dst(idx, v[i]);
-    }
-  }
-}
-
 // Contrast source (or the raw source) of ROWS rows, zero-padded to LX, forward FFT along x.
 //   stencil: stress of rows z0-1 .. z0+ROWS (each computed once, kept in shared memory), then
 //            s1 = w^2 drho u1 + d1 sigma1 + d3 sigma5, s3 = w^2 drho u3 + d1 sigma5 + d3 sigma3.
@@ -146,24 +127,46 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
     constexpr int RS = ROWS + 4;   // staged u rows z0 - 2 .. z0 + ROWS + 1
     C *sg = smem;                  // [3][ROWS + 2][W] stress
     C *su = smem + size_t(3) * (ROWS + 2) * W;  // [2][RS][W] u
-    staged_copy<C, RC::NT>(
-        2 * RS * W,
-        [&](int idx) {
-          const int c = idx / (RS * W), rem = idx - c * RS * W;
-          const int r = rem / W, xx = rem - r * W - 1, zz = z0 - 2 + r;
-          return (zz >= 0 && zz < nz && xx >= 0 && xx < nx) ? cscale(__ldg((c ? u3 : u1) + size_t(zz) * nx + xx), isc)
-                                                            : czero<C>();
-        },
-        [&](int idx, C val) { su[idx] = val; });
+    // stage u (rows x columns loops: no runtime division in the index arithmetic)
+    constexpr int KW = (LX / 2 + 2 + RC::NT - 1) / RC::NT;  // column sweeps: W <= LX / 2 + 2
+    constexpr int UR = RS <= 12 ? RS : 2;                    // full unroll for the few-row shapes
+#pragma unroll UR
+    for (int r = 0; r < RS; ++r) {
+      const int zz = z0 - 2 + r;
+      const bool row = zz >= 0 && zz < nz;
+      C a[KW], c3[KW];
+#pragma unroll
+      for (int k = 0; k < KW; ++k) {
+        const int xx = int(threadIdx.x) - 1 + k * RC::NT;
+        const bool in = row && xx >= 0 && xx < nx;
+        a[k] = in ? cscale(__ldg(u1 + size_t(zz) * nx + xx), isc) : czero<C>();
+        c3[k] = in ? cscale(__ldg(u3 + size_t(zz) * nx + xx), isc) : czero<C>();
+      }
+#pragma unroll
+      for (int k = 0; k < KW; ++k) {
+        const int xx = int(threadIdx.x) - 1 + k * RC::NT;
+        if (xx <= nx) {
+          su[(0 * RS + r) * W + xx + 1] = a[k];
+          su[(1 * RS + r) * W + xx + 1] = c3[k];
+        }
+      }
+    }
     __syncthreads();
     const Rl ms = p.m_scale ? Rl(p.m_scale[0]) : Rl(1);
-    for (int idx = threadIdx.x; idx < (ROWS + 2) * W; idx += RC::NT) {
-      const int r2 = idx / W, xx = idx - r2 * W - 1, zz = z0 - 1 + r2;
-      C a1, a3, a5;
-      stress_at(p, su, RS, W, z0, zz, xx, ms, a1, a3, a5);
-      sg[(0 * (ROWS + 2) + r2) * W + xx + 1] = a1;
-      sg[(1 * (ROWS + 2) + r2) * W + xx + 1] = a3;
-      sg[(2 * (ROWS + 2) + r2) * W + xx + 1] = a5;
+#pragma unroll UR
+    for (int r2 = 0; r2 < ROWS + 2; ++r2) {
+      const int zz = z0 - 1 + r2;
+#pragma unroll
+      for (int k = 0; k < KW; ++k) {
+        const int xx = int(threadIdx.x) - 1 + k * RC::NT;
+        if (xx <= nx) {
+          C a1, a3, a5;
+          stress_at(p, su, RS, W, z0, zz, xx, ms, a1, a3, a5);
+          sg[(0 * (ROWS + 2) + r2) * W + xx + 1] = a1;
+          sg[(1 * (ROWS + 2) + r2) * W + xx + 1] = a3;
+          sg[(2 * (ROWS + 2) + r2) * W + xx + 1] = a5;
+        }
+      }
     }
     __syncthreads();
     const Rl w2 = Rl(p.omega[p.fidx[b]] * p.omega[p.fidx[b]]);
