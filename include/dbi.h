@@ -227,6 +227,26 @@ int normal_cg(const dbi_model *background, const dbi_batch *batch, const void *G
               int precision, void *work, size_t work_bytes, dbi_stream stream);
 
 /*
+ * ls_apply_noalloc -- the same operator pass as ls_apply (same kernels, same result) for callers
+ *   that cannot pass a work buffer because they must not allocate device memory while running
+ *   (a plugin whose host application owns all device allocations, a loop with a memory budget
+ *   fixed at start-up). No counterpart in the paper: it only changes where the scratch lives.
+ *   The scratch is one fixed device array inside this library of dbi_noalloc_scratch_bytes()
+ *   bytes (32 MiB), held by every GPU that loads the library until the process exits. The call
+ *   allocates and frees nothing. A batch whose DBI_OP_APPLY workspace exceeds the array is
+ *   rejected with DBI_ERR_WORKSPACE before any GPU work. The first call on a device looks up the
+ *   array's device address (once per device, with that device current); make that first call
+ *   before any stream capture. All calls share the array, so calls that overlap on the GPU (other
+ *   streams, other host threads) race and must be serialised by the caller; nothing in the array
+ *   needs to start at zero (each call writes all the scratch it reads).
+ */
+int ls_apply_noalloc(const dbi_model *model, const dbi_batch *batch, const void *Ghat,
+                     const void *u, void *out, int precision, dbi_stream stream);
+
+/* Size in bytes of the fixed scratch array of ls_apply_noalloc. */
+size_t dbi_noalloc_scratch_bytes(void);
+
+/*
  * Diagnostics (no counterpart in the paper).
  *
  * dbi_kernel_launches -- number of kernels this library has launched in the process so far

@@ -76,6 +76,8 @@ SIGNATURES = {
                                c_void_p, c_size_t, c_void_p]),
     "ls_apply": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p,
                          c_size_t, c_void_p]),
+    "ls_apply_noalloc": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "dbi_noalloc_scratch_bytes": (c_size_t, []),
     "ls_solve": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
                          POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
     "frechet_apply": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, POINTER(Receivers),
@@ -281,6 +283,22 @@ def ls_apply(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None, work=No
     _check(load().ls_apply(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u), _ptr(out), precision,
                            _ptr(work), n, _stream(u.device)), "ls_apply")
     return out
+
+
+def ls_apply_noalloc(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None):
+    """A u like ls_apply, with the library's fixed scratch array instead of a work buffer."""
+    precision = _precision(u)
+    _need_cuda(Ghat, u)
+    model = _model(grid, ref, m, precision)
+    batch = _batch(omega, fidx)
+    out = torch.empty_like(u) if out is None else out
+    _check(load().ls_apply_noalloc(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u), _ptr(out),
+                                   precision, _stream(u.device)), "ls_apply_noalloc")
+    return out
+
+
+def noalloc_scratch_bytes() -> int:
+    return int(load().dbi_noalloc_scratch_bytes())
 
 
 def ls_solve(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, tol=1e-6, max_iter=1000,

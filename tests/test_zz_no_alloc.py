@@ -1,0 +1,53 @@
+"""ls_apply_noalloc: the operator pass for callers that must not allocate device memory while
+running. It keeps its scratch in a fixed device array of the library instead of a work buffer;
+its output must equal ls_apply's on the same inputs, call after call (the array keeps the previous
+call's contents, and nothing in it may leak into the next result). This file is collected last so
+that a failure here does not stop the rest of the GPU suite."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2402_02116_gb300 import build, dbi, inputs
+from paper_2402_02116_gb300.problem import DeviceProblem
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _rel(a, b):
+    a = a.detach().cpu().numpy().astype(np.complex128)
+    b = b.detach().cpu().numpy().astype(np.complex128)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_noalloc_matches_ls_apply_on_consecutive_calls():
+    build.build()
+    dbi.load()
+    assert dbi.noalloc_scratch_bytes() == 32 << 20
+    # 12 problems of 96 x 80 cells and one of another model: both calls fit the fixed array
+    w = inputs.small_case(nz=96, nx=80, n_src=4, freqs=(6.0, 9.0, 14.0), amp=0.12, vti=True, seed=5)
+    P = DeviceProblem(w, dbi.C64)
+    assert dbi.workspace_bytes(P.grid, P.B, dbi.C64, dbi.OP_APPLY) <= dbi.noalloc_scratch_bytes()
+    u1 = P.to_field(inputs.seeded_complex((P.B, 2, w.nz, w.nx), 21))
+    u2 = P.to_field(inputs.seeded_complex((P.B, 2, w.nz, w.nx), 22) * 1e-11)
+    for u in (u1, u2, u1):  # consecutive calls share the array; each must match on its own
+        want = dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u)
+        got = dbi.ls_apply_noalloc(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u)
+        torch.cuda.synchronize()
+        assert _rel(got, want) < 1e-6
+    # complex128 through the same array
+    P2 = DeviceProblem(w, dbi.C128)
+    u = P2.to_field(inputs.seeded_complex((P2.B, 2, w.nz, w.nx), 23))
+    want = dbi.ls_apply(P2.grid, P2.ref, P2.m, P2.omega, P2.fidx, P2.Ghat, u)
+    got = dbi.ls_apply_noalloc(P2.grid, P2.ref, P2.m, P2.omega, P2.fidx, P2.Ghat, u)
+    assert _rel(got, want) < 1e-12
+
+
+def test_noalloc_rejects_a_batch_beyond_the_array():
+    build.build()
+    w = inputs.config2_batched_forward(n=256, n_src=4, nf=8)  # 32 problems of 256 x 256
+    P = DeviceProblem(w, dbi.C64)
+    assert dbi.workspace_bytes(P.grid, P.B, dbi.C64, dbi.OP_APPLY) > dbi.noalloc_scratch_bytes()
+    u = P.incident()
+    with pytest.raises(dbi.DBIError, match="scratch"):
+        dbi.ls_apply_noalloc(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u)
