@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2402_02116_gb300 import inputs  # noqa: E402
+from paper_2402_02116_gb300.shard import reduce_gradient, shard_workload  # noqa: E402
 
 METRIC = "LS operator cell-applies/s (cells x sources x frequencies)"
 UNIT = "cell-applies/s"
@@ -54,12 +55,14 @@ def parse_args():
 
 
 def workload(rank: int, world: int, sources: int = 32):
-    """The 256 x 256 VTI workload; with several ranks each gets its own `sources` surface sources."""
+    """The 256 x 256 VTI workload; with several ranks the job has `sources` surface sources per
+    rank and every rank keeps its round-robin shard of them (weak scaling)."""
     w = inputs.config2_batched_forward()
     if world > 1 or sources != 32:
-        cols = inputs.surface_line(w.nx, sources * world)[rank::world]
+        cols = inputs.surface_line(w.nx, sources * world)
         w.src_cells = np.stack([np.zeros_like(cols), cols], axis=1)
         w.src_force = np.tile([0.0, 1.0], (len(cols), 1))
+        w = shard_workload(w, rank, world)
         if sources != 32:
             w.name = f"vti{w.nz}x{w.nx}_{sources}src_{w.nf}f"
     return w
@@ -166,8 +169,7 @@ def run_ours(args):
         r, phi = dbi.data_residual(P.grid, P.omega, P.fidx, P.rec_cells, u, d_obs)
         g, (it_a, _, code_a) = dbi.adjoint_apply(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u, P.rec_cells, r,
                                                  tol=TOL, max_iter=MAX_ITER, with_status=True)
-        if world > 1:
-            dist.all_reduce(g)
+        reduce_gradient(g, phi)  # sum over ranks (no-op on one GPU)
         return phi, g, it_f, it_a, code_f, code_a
 
     def applies(it_f, it_a):

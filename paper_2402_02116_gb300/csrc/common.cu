@@ -1,5 +1,6 @@
 // Error reporting, argument validation, twiddle tables and workspace sizes.
 #include <atomic>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -112,8 +113,24 @@ static size_t csize(int precision) { return precision == DBI_C64 ? sizeof(float2
 
 size_t bytes_twiddles(int precision) { return align256(size_t(kTwiddleN) * csize(precision)); }
 
+int spectral_chunk(const dbi_grid *g, int B, int precision) {
+  // Default: the whole batch in one pass (measured faster on the 256-problem benchmark batch than
+  // L2-sized chunks: the column pass is bound by shared memory, not by HBM, and small launches
+  // lose to wave tails). DBI_SPECTRAL_CHUNK_MB bounds the spectral scratch per pass.
+  static const size_t budget = [] {
+    const char *e = getenv("DBI_SPECTRAL_CHUNK_MB");
+    const long mb = e ? atol(e) : 0;
+    return mb > 0 ? size_t(mb) << 20 : ~size_t(0);
+  }();
+  const size_t per = size_t(2) * g->nz * g->lx * csize(precision);
+  size_t c = budget / per;
+  if (c < 1) c = 1;
+  if (c > size_t(B)) c = size_t(B);
+  return int(c);
+}
+
 size_t bytes_spectral(const dbi_grid *g, int B, int precision) {
-  return align256(size_t(B) * 2 * g->nz * g->lx * csize(precision));
+  return align256(size_t(spectral_chunk(g, B, precision)) * 2 * g->nz * g->lx * csize(precision));
 }
 
 size_t bytes_field(const dbi_grid *g, int B, int precision) {
@@ -121,10 +138,12 @@ size_t bytes_field(const dbi_grid *g, int B, int precision) {
 }
 
 size_t bytes_partials(int B) {
-  return align256(size_t(B) * kRedBlocks * kRedSlots * sizeof(double));
+  return align256(size_t(B) * kMaxParts * kRedSlots * sizeof(double));
 }
 
-size_t bytes_scales(int B) { return 2 * align256(size_t(B) * sizeof(double)) + 256 + bytes_partials(B); }
+size_t bytes_scales(int B) { return 3 * align256(size_t(B) * sizeof(double)) + 256 + bytes_partials(B); }
+
+int imaging_chunks(int B) { return B < 16 ? (B > 0 ? B : 1) : 16; }
 
 }  // namespace dbi
 
@@ -185,11 +204,12 @@ extern "C" size_t dbi_workspace_bytes(const dbi_grid *g, int B, int precision, i
       return solve;
     case DBI_OP_FRECHET:
     case DBI_OP_ADJOINT:
-      return solve + 2 * fld + model + bytes_scales(B);
+      return solve + 2 * fld + model + bytes_scales(B) + imaging_chunks(B) * model;
     case DBI_OP_NORMAL_CG: {
       // receivers are cells: n_rec <= nz * nx
       const size_t data = align256(size_t(B) * g->nz * g->nx * 2 * csize(precision));
       return solve + 2 * fld + 6 * model + data + bytes_partials(1) + 256 + bytes_scales(B) +
+             imaging_chunks(B) * model +
              align256(4097 * sizeof(double));
     }
     default:

@@ -89,14 +89,20 @@ struct Arena {
 // Sizes of the buffers each operation carves out of the work buffer (see workspace.cu).
 size_t bytes_twiddles(int precision);
 size_t bytes_spectral(const dbi_grid *g, int B, int precision);
+// Problems per operator pass: the three operator kernels run chunk by chunk over the batch; by
+// default one chunk holds the whole batch (DBI_SPECTRAL_CHUNK_MB bounds the scratch per chunk).
+int spectral_chunk(const dbi_grid *g, int B, int precision);
 size_t bytes_field(const dbi_grid *g, int B, int precision);
 size_t bytes_partials(int B);
 // per-problem power-of-two scales (scale, inverse, model scale) and their partial sums
 size_t bytes_scales(int B);
+// problem chunks of the adjoint imaging (each accumulates its own FP64 partial image)
+int imaging_chunks(int B);
 
 // Geometry of the FP64 partial sums of the Krylov reductions.
 constexpr int kRedBlocks = 64;    // blocks per problem in a reduction pass
 constexpr int kRedThreads = 256;  // threads per reduction block
 constexpr int kRedSlots = 4;      // doubles per block partial
+constexpr int kMaxParts = 512;    // partials per problem at most (operator kernels: one per row block)
 
 }  // namespace dbi

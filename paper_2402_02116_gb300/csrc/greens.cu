@@ -61,39 +61,43 @@ __device__ double2 green_self(double h, double omega, double alpha, double beta,
   return times_inv_8i_rho(tot, rho);
 }
 
-// Offset held by slot i of a length-L periodic axis for a domain of n cells, or INT_MIN for a gap.
-__device__ __forceinline__ int slot_offset(int i, int n, int L) {
-  if (i <= n - 1) return i;
-  if (i >= L - (n - 1)) return i - L;
-  return -0x7fffffff;
-}
-
+// One thread per offset (dz, dx) with dz, dx >= 0: G11 and G33 are even and G13 odd in each
+// offset coordinate (Eq. A-3), so the four slots (+-dz, +-dx) are filled from one evaluation (the
+// mirrored values are bit-identical to direct evaluations). Gap slots are zeroed beforehand.
 template <typename C>
 __global__ void k_green_space(int nz, int nx, int lz, int lx, double h, const double *omega,
                               double rho, double alpha, double beta, double2 *W, C *Gspace) {
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  const int iz = blockIdx.y;
+  const int dx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int dz = blockIdx.y;
   const int f = blockIdx.z;
-  if (ix >= lx) return;
-  const int dz = slot_offset(iz, nz, lz), dx = slot_offset(ix, nx, lx);
-  double2 g11 = make_double2(0, 0), g13 = g11, g33 = g11;
-  if (dz != -0x7fffffff && dx != -0x7fffffff) {
-    const double w = omega[f];
-    if (dz == 0 && dx == 0) {
-      g11 = g33 = green_self(h, w, alpha, beta, rho);
-    } else {
-      green_offset(dx * h, dz * h, w, alpha, beta, rho, g11, g13, g33);
-    }
+  if (dx >= nx) return;
+  double2 g11, g13 = make_double2(0, 0), g33;
+  const double w = omega[f];
+  if (dz == 0 && dx == 0) {
+    g11 = g33 = green_self(h, w, alpha, beta, rho);
+  } else {
+    green_offset(dx * h, dz * h, w, alpha, beta, rho, g11, g13, g33);
   }
-  const size_t plane = size_t(lz) * lx, cell = size_t(iz) * lx + ix, base = size_t(f) * 3 * plane;
-  W[base + cell] = g11;
-  W[base + plane + cell] = g13;
-  W[base + 2 * plane + cell] = g33;
-  if (Gspace) {
-    using R = typename RealOf<C>::type;
-    Gspace[base + cell] = mk<C>(R(g11.x), R(g11.y));
-    Gspace[base + plane + cell] = mk<C>(R(g13.x), R(g13.y));
-    Gspace[base + 2 * plane + cell] = mk<C>(R(g33.x), R(g33.y));
+  const size_t plane = size_t(lz) * lx, base = size_t(f) * 3 * plane;
+  using R = typename RealOf<C>::type;
+  for (int sz = 0; sz < 2; ++sz) {
+    if (sz == 1 && dz == 0) continue;
+    const int iz = sz ? lz - dz : dz;
+    for (int sx = 0; sx < 2; ++sx) {
+      if (sx == 1 && dx == 0) continue;
+      const int ix = sx ? lx - dx : dx;
+      const double sg = (sz ^ sx) ? -1.0 : 1.0;  // G13 is odd in each coordinate
+      const double2 q13 = make_double2(sg * g13.x, sg * g13.y);
+      const size_t cell = size_t(iz) * lx + ix;
+      W[base + cell] = g11;
+      W[base + plane + cell] = q13;
+      W[base + 2 * plane + cell] = g33;
+      if (Gspace) {
+        Gspace[base + cell] = mk<C>(R(g11.x), R(g11.y));
+        Gspace[base + plane + cell] = mk<C>(R(q13.x), R(q13.y));
+        Gspace[base + 2 * plane + cell] = mk<C>(R(g33.x), R(g33.y));
+      }
+    }
   }
 }
 
@@ -240,7 +244,12 @@ extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const d
   double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
   double2 *W = static_cast<double2 *>(ar.take(size_t(nf) * 3 * g->lz * g->lx * sizeof(double2)));
   if ((rc = launch_twiddles(tw, DBI_C128, s))) return rc;
-  dim3 grid((g->lx + 127) / 128, g->lz, nf);
+  const size_t tab = size_t(nf) * 3 * g->lz * g->lx;
+  cudaError_t e = cudaMemsetAsync(W, 0, tab * sizeof(double2), s);
+  if (e == cudaSuccess && Gspace)
+    e = cudaMemsetAsync(Gspace, 0, tab * (precision == DBI_C64 ? sizeof(float2) : sizeof(double2)), s);
+  if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(Green table)", e);
+  dim3 grid((g->nx + 127) / 128, g->nz, nf);
   if (precision == DBI_C64)
     k_green_space<float2><<<grid, 128, 0, s>>>(g->nz, g->nx, g->lz, g->lx, g->h, omega, ref->rho0,
                                                ref->alpha0, ref->beta0, W, static_cast<float2 *>(Gspace));

@@ -3,11 +3,9 @@
 //
 // Per iteration i (van der Vorst's BiCGSTAB, <a, b> = sum conj(a) b):
 //   p = r + beta (p - omega v)                  k_update_p      (beta from the previous k_check)
-//   v = A p                                     operator
-//   sigma = <rhat, v>                           k_dot           (FP64 partial sums)
-//   alpha = rho / sigma, s = r - alpha v        k_update_s      (+ partials of ||s||^2)
-//   t = A s                                     operator
-//   <t, s>, <t, t>                              k_dot2
+//   v = A p, partials of <rhat, v>              operator (inner product in k_rows_inverse)
+//   alpha = rho / <rhat, v>, s = r - alpha v    k_update_s      (+ partials of ||s||^2)
+//   t = A s, partials of <t, s>, <t, t>         operator (inner products in k_rows_inverse)
 //   omega = <t,s>/<t,t>, x += alpha p + omega s, r = s - omega t   k_update_xr (+ <rhat, r>, ||r||^2)
 //   convergence, breakdown, beta = (rho_new / rho)(alpha / omega)  k_check
 // Every scalar lives on the device in FP64. Each reduction is two-stage and deterministic: each
@@ -18,53 +16,13 @@
 #include <cmath>
 
 #include "krylov.cuh"
+#include "reduce.cuh"
 
 namespace dbi {
 
 template <typename C> struct Acc;                         // per-thread accumulation type
 template <> struct Acc<float2> { using type = float; };   // short per-thread sums, then FP64
 template <> struct Acc<double2> { using type = double; };
-
-// Sum NS values over the CTA (fixed order); thread 0 stores them to out[0..NS).
-template <int NS> __device__ __forceinline__ void block_sum_store(double (&v)[NS], double *out) {
-  __shared__ double sh[NS][kRedThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    double a = v[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) sh[k][warp] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      double a = 0.0;
-      for (int w = 0; w < kRedThreads / 32; ++w) a += sh[k][w];
-      out[k] = a;
-    }
-  }
-}
-
-// Sum slot k (k < NS) of the kRedBlocks partials of one problem; every thread gets the result.
-template <int NS> __device__ __forceinline__ void gather(const double *part, double (&out)[NS]) {
-  static_assert(kRedBlocks == 64, "gather assumes 64 partials");
-  __shared__ double sh[NS];
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      double a = part[lane * kRedSlots + k] + part[(lane + 32) * kRedSlots + k];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-      if (lane == 0) sh[k] = a;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NS; ++k) out[k] = sh[k];
-}
 
 __device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
   const double d = b.x * b.x + b.y * b.y;
@@ -103,7 +61,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bnorm(size_t n, const C *rhs, d
 // scaled system (exact in any precision) and unscales the solution at the end.
 __global__ void k_scale(KState *st, const double *part) {
   double s[1];
-  gather<1>(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, s);
+  gather_n<1>(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, kRedBlocks, s);
   if (threadIdx.x == 0) st[blockIdx.x].scale = s[0] > 0.0 ? ldexp(1.0, -ilogb(sqrt(s[0]))) : 1.0;
 }
 
@@ -143,7 +101,7 @@ __global__ void k_init_state(KState *st, int *active, int *counters, const doubl
                              int max_iter) {
   const int b = blockIdx.x;
   double s[2];
-  gather<2>(part + size_t(b) * kRedBlocks * kRedSlots, s);
+  gather_n<2>(part + size_t(b) * kRedBlocks * kRedSlots, kRedBlocks, s);
   if (threadIdx.x == 0) {
     KState k{};
     k.scale = st[b].scale;
@@ -193,28 +151,13 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const KState
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_dot(size_t n, const int *active, const C *a,
-                                                     const C *bv, double *part) {
-  using A = typename Acc<C>::type;
-  if (!active[blockIdx.y]) return;
-  A re = 0, im = 0;
-  DBI_PROBLEM_LOOP(n) {
-    const C x = a[off + i], y = bv[off + i];
-    re += x.x * y.x + x.y * y.y;  // conj(x) y
-    im += x.x * y.y - x.y * y.x;
-  }
-  double acc[2] = {double(re), double(im)};
-  block_sum_store<2>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
-}
-
-template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, KState *st, const int *active,
-                                                          const double *partA, const C *r, const C *v,
-                                                          C *s, double *partS) {
+                                                          int nparts, const double *partA, const C *r,
+                                                          const C *v, C *s, double *partS) {
   using A = typename Acc<C>::type;
   if (!active[blockIdx.y]) return;
   double sg[2];
-  gather<2>(partA + size_t(blockIdx.y) * kRedBlocks * kRedSlots, sg);
+  gather_n<2>(partA + size_t(blockIdx.y) * nparts * kRedSlots, nparts, sg);
   const KState k = st[blockIdx.y];
   const double2 sigma = make_double2(sg[0], sg[1]);
   const double2 alpha = (sigma.x == 0.0 && sigma.y == 0.0)
@@ -236,32 +179,16 @@ __global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, KState *st, 
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_dot2(size_t n, const int *active, const C *t,
-                                                      const C *s, double *part) {
-  using A = typename Acc<C>::type;
-  if (!active[blockIdx.y]) return;
-  A re = 0, im = 0, tt = 0;
-  DBI_PROBLEM_LOOP(n) {
-    const C x = t[off + i], y = s[off + i];
-    re += x.x * y.x + x.y * y.y;  // conj(t) s
-    im += x.x * y.y - x.y * y.x;
-    tt += x.x * x.x + x.y * x.y;
-  }
-  double acc[3] = {double(re), double(im), double(tt)};
-  block_sum_store<3>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
-}
-
-template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_update_xr(size_t n, KState *st, const int *active,
-                                                           const double *partB, const double *partS,
+                                                           int nparts, const double *partB, const double *partS,
                                                            double tol, const C *p, const C *s,
                                                            const C *t, const C *rhat, C *x, C *r,
                                                            double *partC) {
   using A = typename Acc<C>::type;
   if (!active[blockIdx.y]) return;
   double q[3], sn[1];
-  gather<3>(partB + size_t(blockIdx.y) * kRedBlocks * kRedSlots, q);
-  gather<1>(partS + size_t(blockIdx.y) * kRedBlocks * kRedSlots, sn);
+  gather_n<3>(partB + size_t(blockIdx.y) * nparts * kRedSlots, nparts, q);
+  gather_n<1>(partS + size_t(blockIdx.y) * kRedBlocks * kRedSlots, kRedBlocks, sn);
   const KState k = st[blockIdx.y];
   const int half = sn[0] <= tol * tol * k.bnorm2;
   const double2 om = (half || q[2] == 0.0) ? make_double2(0.0, 0.0)
@@ -295,7 +222,7 @@ __global__ void k_check(KState *st, int *active, int *counters, int parity, cons
   const int b = blockIdx.x;
   if (!active[b]) return;
   double q[3];
-  gather<3>(partC + size_t(b) * kRedBlocks * kRedSlots, q);
+  gather_n<3>(partC + size_t(b) * kRedBlocks * kRedSlots, kRedBlocks, q);
   if (threadIdx.x != 0) return;
   KState k = st[b];
   k.iters += 1;
@@ -364,7 +291,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sumsq(size_t n, const T *x, dou
 
 __global__ void k_pow2(const double *part, double *scale, double *inv, const double *extra) {
   double s[1];
-  gather<1>(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, s);
+  gather_n<1>(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, kRedBlocks, s);
   if (threadIdx.x == 0) {
     const double sc = s[0] > 0.0 ? ldexp(1.0, -ilogb(sqrt(s[0]))) : 1.0;
     scale[blockIdx.x] = sc;
@@ -451,22 +378,20 @@ static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, voi
   int remaining = B;
   if (o.check_every > 0 && (rc = read_counter(sb.counters + 1, s, &remaining))) return rc;
   op.active = sb.active;
+  op.krhat = rhat;
+  const int nparts = operator_parts(op.nz, op.lx, op.precision);
   for (int it = 0; it < o.max_iter && remaining > 0; ++it) {
     const int parity = it & 1;
     k_update_p<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, sb.counters, parity, r, rhat, p, v);
     if ((rc = check_launch("k_update_p"))) return rc;
-    op.in = p; op.ident = p; op.out = v;
+    op.epi = 1; op.in = p; op.ident = p; op.out = v; op.part_out = sb.partA;
     if ((rc = run_operator(op, s))) return rc;
-    k_dot<C><<<grid, kRedThreads, 0, s>>>(n, sb.active, rhat, v, sb.partA);
-    if ((rc = check_launch("k_dot"))) return rc;
-    k_update_s<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, sb.partA, r, v, sv, sb.partS);
+    k_update_s<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, nparts, sb.partA, r, v, sv, sb.partS);
     if ((rc = check_launch("k_update_s"))) return rc;
-    op.in = sv; op.ident = sv; op.out = t;
+    op.epi = 2; op.in = sv; op.ident = sv; op.out = t; op.part_out = sb.partB;
     if ((rc = run_operator(op, s))) return rc;
-    k_dot2<C><<<grid, kRedThreads, 0, s>>>(n, sb.active, t, sv, sb.partB);
-    if ((rc = check_launch("k_dot2"))) return rc;
-    k_update_xr<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, sb.partB, sb.partS, o.tol, p, sv,
-                                                 t, rhat, x, r, sb.partC);
+    k_update_xr<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, nparts, sb.partB, sb.partS, o.tol, p,
+                                                 sv, t, rhat, x, r, sb.partC);
     if ((rc = check_launch("k_update_xr"))) return rc;
     k_check<<<B, 32, 0, s>>>(sb.st, sb.active, sb.counters, parity, sb.partC, o.tol, o.max_iter);
     if ((rc = check_launch("k_check"))) return rc;

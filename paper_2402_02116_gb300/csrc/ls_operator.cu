@@ -15,6 +15,7 @@
 
 #include "fft_reg.cuh"
 #include "operator.cuh"
+#include "reduce.cuh"
 
 namespace dbi {
 
@@ -34,6 +35,9 @@ template <typename C> struct OpP {
   const C *tw;
   const int *active;
   const double *in_scale, *m_scale, *out_scale;
+  const C *krhat;
+  double *part_out;
+  int part_count;
 };
 
 // Launch shapes. Rows kernels: ROWS rows per CTA, T = L/8 threads per row (t fastest), both
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_col
 
 // Inverse FFT along x of ROWS rows, keep x < nx, out = ident - out_scale * result (or the scaled
 // result when there is no identity term).
-template <typename C, int LX>
+template <typename C, int LX, int EPI>
 __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
   using Rl = typename RealOf<C>::type;
   using RC = RowCfg<C, LX>;
@@ -309,20 +313,40 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
   __syncthreads();  // the FFT lines reuse the tile
   C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
   RegPlan<LX>::template run<C, 2, true>(v, lines, t, p.tw, RowSync<T>{1 + rr});
-  if (z >= nz) return;
   const Rl osc = p.out_scale ? Rl(p.out_scale[b]) : Rl(1);
   const size_t base = size_t(b) * 2 * nz * nx + size_t(z) * nx;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // per-thread partials of the fused inner products
+  if (z < nz) {
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int x = t + m * T;
-      if (x < nx) {
-        const size_t o = base + size_t(c) * nz * nx + x;
-        const C r = cscale(v[c][m], osc);
-        p.out[o] = p.ident ? csub(p.ident[o], r) : r;
+      for (int m = 0; m < 8; ++m) {
+        const int x = t + m * T;
+        if (x < nx) {
+          const size_t o = base + size_t(c) * nz * nx + x;
+          const C r = cscale(v[c][m], osc);
+          const C id = p.ident ? p.ident[o] : czero<C>();
+          const C w = p.ident ? csub(id, r) : r;
+          p.out[o] = w;
+          if constexpr (EPI == 1) {  // conj(rhat) w
+            const C h = p.krhat[o];
+            a0 += float(h.x) * float(w.x) + float(h.y) * float(w.y);
+            a1 += float(h.x) * float(w.y) - float(h.y) * float(w.x);
+          } else if constexpr (EPI == 2) {  // conj(w) id and |w|^2
+            a0 += float(w.x) * float(id.x) + float(w.y) * float(id.y);
+            a1 += float(w.x) * float(id.y) - float(w.y) * float(id.x);
+            a2 += float(w.x) * float(w.x) + float(w.y) * float(w.y);
+          }
+        }
       }
-    }
+  }
+  if constexpr (EPI == 1) {
+    double acc[2] = {double(a0), double(a1)};
+    block_sum_store<2>(acc, p.part_out + (size_t(b) * p.part_count + blockIdx.x) * kRedSlots);
+  } else if constexpr (EPI == 2) {
+    double acc[3] = {double(a0), double(a1), double(a2)};
+    block_sum_store<3>(acc, p.part_out + (size_t(b) * p.part_count + blockIdx.x) * kRedSlots);
+  }
 }
 
 // Opt a kernel into more than 48 KB of dynamic shared memory.
@@ -331,26 +355,33 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
-template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
+// The three kernels for problems [b0, b0 + nb) of the batch, using the first nb problems' worth of
+// the spectral scratch.
+template <typename C> static int run_chunk(const OpArgs &a, int b0, int nb, cudaStream_t s) {
   using Rl = typename RealOf<C>::type;
-  if (a.B == 0) return DBI_OK;
+  const size_t fo = size_t(b0) * 2 * a.nz * a.nx;  // field offset of the chunk
   OpP<C> p;
   p.nz = a.nz; p.nx = a.nx; p.lz = a.lz; p.lx = a.lx; p.nf = a.nf;
   p.inv2h = Rl(1.0 / (2.0 * a.h));
-  p.omega = a.omega; p.fidx = a.fidx;
+  p.omega = a.omega; p.fidx = a.fidx + b0;
   p.m = static_cast<const Rl *>(a.m);
   for (int i = 0; i < 5; ++i) p.ref[i] = Rl(a.ref[i]);
-  p.in = static_cast<const C *>(a.in);
-  p.ident = static_cast<const C *>(a.ident);
-  p.out = static_cast<C *>(a.out);
+  p.in = static_cast<const C *>(a.in) + fo;
+  p.ident = a.ident ? static_cast<const C *>(a.ident) + fo : nullptr;
+  p.out = static_cast<C *>(a.out) + fo;
   p.T = static_cast<C *>(a.T);
   p.Ghat = static_cast<const C *>(a.Ghat);
   p.tw = static_cast<const C *>(a.tw);
-  p.active = a.active;
-  p.in_scale = a.in_scale; p.m_scale = a.m_scale; p.out_scale = a.out_scale;
+  p.active = a.active ? a.active + b0 : nullptr;
+  p.in_scale = a.in_scale ? a.in_scale + b0 : nullptr;
+  p.m_scale = a.m_scale;
+  p.out_scale = a.out_scale ? a.out_scale + b0 : nullptr;
+  p.part_count = operator_parts(a.nz, a.lx, a.precision);
+  const size_t pk = size_t(b0) * p.part_count * kRedSlots;
+  p.krhat = a.krhat ? static_cast<const C *>(a.krhat) + fo : nullptr;
+  p.part_out = a.part_out ? a.part_out + pk : nullptr;
   int rc = DBI_OK;
   const bool stencil = a.stencil;
-  prof_mark(PROF_OPERATOR, false, s);
   prof_mark(PROF_ROWS_FORWARD, false, s);
   dispatch_len(a.lx, [&]<int LX>() {
     using RC = RowCfg<C, LX>;
@@ -358,15 +389,14 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
     const size_t tile = tile_elems<C, LX>() * sizeof(C);
     const size_t sg = stencil ? (size_t(3) * (RC::ROWS + 2) + size_t(2) * (RC::ROWS + 4)) * (a.nx + 2) * sizeof(C) : 0;
     const size_t bytes = std::max(std::max(lines, tile), sg);
-    dim3 grid((a.nz + RC::ROWS - 1) / RC::ROWS, a.B);
+    dim3 grid((a.nz + RC::ROWS - 1) / RC::ROWS, nb);
     cudaError_t e;
-    if (stencil) {
-      e = allow_smem(k_rows_forward<C, LX, true>, bytes);
-      if (e == cudaSuccess) k_rows_forward<C, LX, true><<<grid, RC::NT, bytes, s>>>(p);
-    } else {
-      e = allow_smem(k_rows_forward<C, LX, false>, bytes);
-      if (e == cudaSuccess) k_rows_forward<C, LX, false><<<grid, RC::NT, bytes, s>>>(p);
-    }
+    auto launch = [&](auto kernel) {
+      e = allow_smem(kernel, bytes);
+      if (e == cudaSuccess) kernel<<<grid, RC::NT, bytes, s>>>(p);
+    };
+    if (stencil) launch(k_rows_forward<C, LX, true>);
+    else launch(k_rows_forward<C, LX, false>);
     rc = e != cudaSuccess ? cuda_fail("k_rows_forward smem", e) : check_launch("k_rows_forward");
   });
   prof_mark(PROF_ROWS_FORWARD, true, s);
@@ -375,7 +405,7 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
   dispatch_len(a.lz, [&]<int LZ>() {
     using CF = ColCfg<C, LZ>;
     const size_t bytes = size_t(2) * CF::CC * CF::LP * sizeof(C);
-    dim3 grid((a.lx + CF::CC - 1) / CF::CC, a.B);
+    dim3 grid((a.lx + CF::CC - 1) / CF::CC, nb);
     cudaError_t e = allow_smem(k_cols<C, LZ>, bytes);
     if (e == cudaSuccess) k_cols<C, LZ><<<grid, CF::NT, bytes, s>>>(p);
     rc = e != cudaSuccess ? cuda_fail("k_cols smem", e) : check_launch("k_cols");
@@ -386,14 +416,42 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
   dispatch_len(a.lx, [&]<int LX>() {
     using RC = RowCfg<C, LX>;
     const size_t bytes = std::max(size_t(2) * RC::ROWS * RC::LP, tile_elems<C, LX>()) * sizeof(C);
-    dim3 grid((a.nz + RC::ROWS - 1) / RC::ROWS, a.B);
-    cudaError_t e = allow_smem(k_rows_inverse<C, LX>, bytes);
-    if (e == cudaSuccess) k_rows_inverse<C, LX><<<grid, RC::NT, bytes, s>>>(p);
+    dim3 grid((a.nz + RC::ROWS - 1) / RC::ROWS, nb);
+    cudaError_t e;
+    auto launch = [&](auto kernel) {
+      e = allow_smem(kernel, bytes);
+      if (e == cudaSuccess) kernel<<<grid, RC::NT, bytes, s>>>(p);
+    };
+    if (a.epi == 1) launch(k_rows_inverse<C, LX, 1>);
+    else if (a.epi == 2) launch(k_rows_inverse<C, LX, 2>);
+    else launch(k_rows_inverse<C, LX, 0>);
     rc = e != cudaSuccess ? cuda_fail("k_rows_inverse smem", e) : check_launch("k_rows_inverse");
   });
   prof_mark(PROF_ROWS_INVERSE, true, s);
+  return rc;
+}
+
+template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
+  if (a.B == 0) return DBI_OK;
+  dbi_grid g{a.nz, a.nx, a.lz, a.lx, a.h};
+  const int chunk = spectral_chunk(&g, a.B, a.precision);
+  int rc = DBI_OK;
+  prof_mark(PROF_OPERATOR, false, s);
+  for (int b0 = 0; b0 < a.B && rc == DBI_OK; b0 += chunk)
+    rc = run_chunk<C>(a, b0, std::min(chunk, a.B - b0), s);
   prof_mark(PROF_OPERATOR, true, s);
   return rc;
+}
+
+int operator_parts(int nz, int lx, int precision) {
+  int rows = 1;
+  auto pick = [&](auto tag) {
+    using C = decltype(tag);
+    dispatch_len(lx, [&]<int LX>() { rows = RowCfg<C, LX>::ROWS; });
+  };
+  if (precision == DBI_C64) pick(float2{});
+  else pick(double2{});
+  return (nz + rows - 1) / rows;
 }
 
 int run_operator(const OpArgs &a, cudaStream_t s) {

@@ -30,7 +30,16 @@ struct OpArgs {
   const double *in_scale;   // device [B]: the input field is multiplied by in_scale[b]
   const double *m_scale;    // device [1]: the contrast (m - ref) is multiplied by m_scale[0]
   const double *out_scale;  // device [B]: the convolution result is multiplied by out_scale[b]
+  // Inner products fused into the last kernel's epilogue (krylov.cu); 0 / NULL for a plain pass.
+  //   epi = 1: partials of <rhat, out> (rhat = krhat); epi = 2: partials of <out, ident>, <out, out>.
+  //   part_out: [B][operator_parts][kRedSlots].
+  int epi;
+  const void *krhat;
+  double *part_out;
 };
+
+// Partials per problem written by the operator kernels (one per CTA row block).
+int operator_parts(int nz, int lx, int precision);
 
 int run_operator(const OpArgs &a, cudaStream_t s);
 
@@ -38,12 +47,13 @@ int run_operator(const OpArgs &a, cudaStream_t s);
 // or real when `real` is set): scale[b] = 2^-e with ||x_b|| in [2^e, 2^(e+1)), 1 for a zero array.
 // If inv is non-NULL, inv[b] = 1 / (scale[b] * (extra ? extra[0] : 1)). part: bytes_partials(B).
 struct Scales {
-  double *scale, *inv, *mscale, *part;
+  double *scale, *inv, *aux, *mscale, *part;
 };
 inline Scales carve_scales(Arena &ar, int B) {
   Scales s;
   s.scale = static_cast<double *>(ar.take(size_t(B) * sizeof(double)));
   s.inv = static_cast<double *>(ar.take(size_t(B) * sizeof(double)));
+  s.aux = static_cast<double *>(ar.take(size_t(B) * sizeof(double)));
   s.mscale = static_cast<double *>(ar.take(256));
   s.part = static_cast<double *>(ar.take(bytes_partials(B)));
   return s;

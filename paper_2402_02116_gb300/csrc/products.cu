@@ -82,14 +82,14 @@ __device__ __forceinline__ void strain(const C *u1, const C *u3, int nz, int nx,
                    csub(at(u3, nz, nx, z, x + 1), at(u3, nz, nx, z, x - 1))), inv2h);
 }
 
-// Re(a b) formed in FP64
-template <typename C> __device__ __forceinline__ double re_mul(C a, C b) {
-  return double(a.x) * double(b.x) - double(a.y) * double(b.y);
-}
-
-template <typename C, typename GOut>
-__global__ void k_imaging(int B, int nf, int nz, int nx, double h, const double *omega, const int *fidx,
-                          const C *ua, const C *ub, const double *src_scale, const KState *st, GOut *g) {
+// Partial images of the problems [c * pb, min(B, (c + 1) * pb)) for chunk c = blockIdx.z, FP64.
+// u_a is stored as src_scale[b] * st[b].scale * (the back-propagated field) and u_b is read times
+// ub_scale[b] (powers of two bringing both near unit norm), so the strain products are formed in
+// FP32 without underflow and accumulated in FP64 with the exact factor 1 / (all three scales).
+template <typename C>
+__global__ void k_imaging_part(int B, int pb, int nf, int nz, int nx, double h, const double *omega,
+                               const int *fidx, const C *ua, const C *ub, const double *src_scale,
+                               const KState *st, const double *ub_scale, double *part) {
   using R = typename RealOf<C>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int z = blockIdx.y;
@@ -97,28 +97,45 @@ __global__ void k_imaging(int B, int nf, int nz, int nx, double h, const double 
   const R inv2h = R(1.0 / (2.0 * h));
   const size_t plane = size_t(nz) * nx, cell = size_t(z) * nx + x;
   double g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0;
-  for (int b = 0; b < B; ++b) {
-    const C *a1 = ua + size_t(b) * 2 * plane, *a3 = a1 + plane;
-    const C *b1 = ub + size_t(b) * 2 * plane, *b3 = b1 + plane;
+  const int b1e = min(B, (int(blockIdx.z) + 1) * pb);
+  for (int b = blockIdx.z * pb; b < b1e; ++b) {
     if (unsigned(fidx[b]) >= unsigned(nf)) continue;
+    const C *a1 = ua + size_t(b) * 2 * plane, *a3 = a1 + plane;
+    const C *c1 = ub + size_t(b) * 2 * plane, *c3 = c1 + plane;
+    const R us = R(ub_scale[b]);
     const double w = omega[fidx[b]];
-    // u_a is stored as src_scale[b] * st[b].scale * (the back-propagated field)
-    const double f = 1.0 / (src_scale[b] * st[b].scale);
+    const double f = 1.0 / (src_scale[b] * st[b].scale * ub_scale[b]);
     C ea1, ea3, ea5, eb1, eb3, eb5;
     strain(a1, a3, nz, nx, z, x, inv2h, ea1, ea3, ea5);
-    strain(b1, b3, nz, nx, z, x, inv2h, eb1, eb3, eb5);
-    // products in FP64: back-propagated fields can be so small that FP32 products underflow
-    g0 += f * w * w * (re_mul(a1[cell], b1[cell]) + re_mul(a3[cell], b3[cell]));
-    g1 -= f * re_mul(ea1, eb1);
-    g2 -= f * (re_mul(ea1, eb3) + re_mul(ea3, eb1));
-    g3 -= f * re_mul(ea3, eb3);
-    g4 -= f * re_mul(ea5, eb5);
+    strain(c1, c3, nz, nx, z, x, R(inv2h * us), eb1, eb3, eb5);
+    const C pa1 = a1[cell], pa3 = a3[cell], pb1 = cscale(c1[cell], us), pb3 = cscale(c3[cell], us);
+    const R rho_t = cmul(pa1, pb1).x + cmul(pa3, pb3).x;
+    const R t11 = cmul(ea1, eb1).x;
+    const R t13 = cmul(ea1, eb3).x + cmul(ea3, eb1).x;
+    const R t33 = cmul(ea3, eb3).x;
+    const R t55 = cmul(ea5, eb5).x;
+    g0 += f * w * w * double(rho_t);
+    g1 -= f * double(t11);
+    g2 -= f * double(t13);
+    g3 -= f * double(t33);
+    g4 -= f * double(t55);
   }
-  g[cell] = GOut(g0);
-  g[plane + cell] = GOut(g1);
-  g[2 * plane + cell] = GOut(g2);
-  g[3 * plane + cell] = GOut(g3);
-  g[4 * plane + cell] = GOut(g4);
+  double *o = part + size_t(blockIdx.z) * 5 * plane + cell;
+  o[0] = g0;
+  o[plane] = g1;
+  o[2 * plane] = g2;
+  o[3 * plane] = g3;
+  o[4 * plane] = g4;
+}
+
+// g = sum of the chunks' partial images, in chunk order.
+template <typename GOut>
+__global__ void k_imaging_sum(size_t n, int nch, const double *part, GOut *g) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    double a = 0.0;
+    for (int c = 0; c < nch; ++c) a += part[size_t(c) * n + i];
+    g[i] = GOut(a);
+  }
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -255,6 +272,7 @@ struct ProdCtx {
   SolverBufs sb;
   void *f1, *f2;  // two fields [B][2][nz][nx]
   Scales sc;      // power-of-two normalisers of the convolution inputs
+  double *img;    // [imaging_chunks(B)][5][nz][nx] FP64 partial images
   dbi_krylov_opts opts;
   const dbi_status *status;
   cudaStream_t s;
@@ -332,16 +350,26 @@ static int adjoint_internal(const ProdCtx &c, const void *u_b, const dbi_receive
   a.in_scale = c.sc.scale;
   if ((rc = run_operator(a, c.s))) return rc;
   if ((rc = solve_background(c, c.f1, c.f2, false))) return rc;
-  dim3 grid((nx + 127) / 128, nz);
+  // u_b normalised per problem for the FP32 strain products
+  if ((rc = pow2_scales(u_b, c.precision, false, B, size_t(2) * nz * nx, c.sc.part, c.sc.aux, nullptr,
+                        nullptr, c.s)))
+    return rc;
+  const int nch = imaging_chunks(B), pb = (B + nch - 1) / nch;
+  dim3 grid((nx + 127) / 128, nz, nch);
   if (c.precision == DBI_C64)
-    k_imaging<float2, GOut><<<grid, 128, 0, c.s>>>(B, c.batch->nf, nz, nx, c.g->h, c.batch->omega, c.batch->fidx,
-                                                   static_cast<const float2 *>(c.f2),
-                                                   static_cast<const float2 *>(u_b), c.sc.scale, c.sb.st, g);
+    k_imaging_part<float2><<<grid, 128, 0, c.s>>>(B, pb, c.batch->nf, nz, nx, c.g->h, c.batch->omega,
+                                                  c.batch->fidx, static_cast<const float2 *>(c.f2),
+                                                  static_cast<const float2 *>(u_b), c.sc.scale, c.sb.st,
+                                                  c.sc.aux, c.img);
   else
-    k_imaging<double2, GOut><<<grid, 128, 0, c.s>>>(B, c.batch->nf, nz, nx, c.g->h, c.batch->omega, c.batch->fidx,
-                                                    static_cast<const double2 *>(c.f2),
-                                                    static_cast<const double2 *>(u_b), c.sc.scale, c.sb.st, g);
-  return check_launch("k_imaging");
+    k_imaging_part<double2><<<grid, 128, 0, c.s>>>(B, pb, c.batch->nf, nz, nx, c.g->h, c.batch->omega,
+                                                   c.batch->fidx, static_cast<const double2 *>(c.f2),
+                                                   static_cast<const double2 *>(u_b), c.sc.scale, c.sb.st,
+                                                   c.sc.aux, c.img);
+  if ((rc = check_launch("k_imaging_part"))) return rc;
+  const size_t nm = size_t(5) * nz * nx;
+  k_imaging_sum<GOut><<<int(std::min<size_t>((nm + 255) / 256, 4096)), 256, 0, c.s>>>(nm, nch, c.img, g);
+  return check_launch("k_imaging_sum");
 }
 
 static int prepare(ProdCtx &c, Arena &ar, const dbi_model *bg, const dbi_batch *batch, const void *Ghat,
@@ -359,6 +387,7 @@ static int prepare(ProdCtx &c, Arena &ar, const dbi_model *bg, const dbi_batch *
   c.f1 = ar.take(bytes_field(c.g, batch->B, precision));
   c.f2 = ar.take(bytes_field(c.g, batch->B, precision));
   c.sc = carve_scales(ar, batch->B);
+  c.img = static_cast<double *>(ar.take(size_t(imaging_chunks(batch->B)) * 5 * c.g->nz * c.g->nx * sizeof(double)));
   c.opts = *opts;
   c.status = status;
   return launch_twiddles(const_cast<void *>(c.tw), precision, c.s);
