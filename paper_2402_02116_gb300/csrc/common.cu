@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -56,6 +57,22 @@ void prof_mark(int stage, bool after, cudaStream_t s) {
   // an end mark only pairs with a begin mark
   if (after != (g_prof.used % 2 == 1)) return;
   cudaEventRecord(g_prof.ev[g_prof.used++], s);
+}
+
+cudaError_t allow_dynamic_smem(const void *kernel, size_t bytes) {
+  constexpr size_t kStaticReserve = 4096;  // static shared arrays of the reductions
+  if (bytes + kStaticReserve <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> raised;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t &have = raised[{kernel, dev}];
+  if (have >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess) have = bytes;
+  return e;
 }
 
 int check_grid(const dbi_grid *g) {

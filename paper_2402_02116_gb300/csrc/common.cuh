@@ -65,6 +65,14 @@ int check_launch(const char *what);
 enum { PROF_NONE = 0, PROF_ROWS_FORWARD = 1, PROF_COLS = 2, PROF_ROWS_INVERSE = 3, PROF_OPERATOR = 4 };
 void prof_mark(int stage, bool after, cudaStream_t s);
 
+// Lets `kernel` take `bytes` of dynamic shared memory on the current device: above 48 KB minus a
+// reserve for the kernel's own static shared arrays, the kernel's limit is raised (once per kernel,
+// device and size).
+cudaError_t allow_dynamic_smem(const void *kernel, size_t bytes);
+template <typename K> inline cudaError_t allow_smem(K kernel, size_t bytes) {
+  return allow_dynamic_smem(reinterpret_cast<const void *>(kernel), bytes);
+}
+
 // Validation shared by the entry points.
 int check_grid(const dbi_grid *g);
 int check_batch(const dbi_batch *b);

@@ -165,10 +165,6 @@ __global__ void k_scale_cast_t(const double2 *W, C *Ghat, int lz, int lx, double
   }
 }
 
-template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-}
 
 static int fft2_fp64(double2 *W, int nmat, int lz, int lx, const double2 *tw, cudaStream_t s) {
   int rc = DBI_OK;

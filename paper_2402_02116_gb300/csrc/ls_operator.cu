@@ -349,11 +349,6 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
   }
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory.
-template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-}
 
 // The three kernels for problems [b0, b0 + nb) of the batch, using the first nb problems' worth of
 // the spectral scratch.

@@ -126,7 +126,9 @@ def test_misfit_512_vti_workload_with_recomputation():
     (phi_k, g_k), (phi_c, g_c) = out
     assert np.isfinite(phi_k) and phi_k > 0
     assert abs(phi_k - phi_c) <= 1e-6 * phi_k
-    assert float(torch.linalg.norm(g_c - g_k) / torch.linalg.norm(g_k)) < 1e-5
+    gk64, gc64 = g_k.double(), g_c.double()  # per-cell gradients are ~1e-25: norms in FP64
+    assert torch.isfinite(gk64).all() and float(gk64.abs().max()) > 0
+    assert float(torch.linalg.norm(gc64 - gk64) / torch.linalg.norm(gk64)) < 1e-5
     # directional derivative: a smooth perturbation of every parameter
     a2 = w.rho0 * w.alpha0 ** 2
     sc = torch.tensor([w.rho0, a2, a2, a2, w.rho0 * w.beta0 ** 2], dtype=torch.float64)

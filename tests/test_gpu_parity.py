@@ -180,6 +180,12 @@ def test_largest_fft_grid():
     u = inputs.seeded_complex((1, 2, 512, 512), 6)
     out = npy(P.apply(P.to_field(u)))
     assert rel(out[0], orc.apply(u[0], w.model, 0)) < TOL[dbi.C64]
+    # the solver's fused kernels on the same grid; the FP64 oracle confirms the residual
+    u0 = P.incident()
+    x, _, relres, code = P.solve(u0, tol=1e-5)
+    assert int(npy(code)[0]) == dbi.CONVERGED
+    x0, b0 = npy(x)[0].astype(np.complex128), npy(u0)[0].astype(np.complex128)
+    assert rel(orc.apply(x0, w.model, 0), b0) < 3e-5
 
 
 def _dbi_setup(precision, seed=31):
