@@ -316,3 +316,38 @@ def test_config2_solve_residual_sampled(config2):
         f = int(w.problem_fidx()[b])
         res = rel(orc.apply(un[b], w.model, f), u0n[b])
         assert res < 3e-5, (b, res, float(npy(relres)[b]))
+
+
+# --- the linear DBI step at full size: 128 x 128, 16 sources x 4 frequencies, 30 CG iterations --
+def test_config3_linear_dbi_step():
+    """Frechet and adjoint products of the 64-problem DBI step pass the dot-product test to 1e-5
+    (complex64), and 30 normal-equation CG iterations with lambda = 1e-3 of the power-iteration
+    estimate of ||J||^2 reduce both the normal residual and the linearised data misfit."""
+    w = inputs.config3_linear_dbi()
+    P = DeviceProblem(w, dbi.C64)
+    u_b, _, _, code = P.forward(tol=1e-6)
+    assert bool((code == dbi.CONVERGED).all())
+    # data residual of the true model against the background
+    Pt = DeviceProblem(w, dbi.C64, model=w.model_true)
+    u_t, _, _, code = Pt.forward(tol=1e-6)
+    assert bool((code == dbi.CONVERGED).all())
+    dd = Pt.sample(u_t) - P.sample(u_b)
+    del u_t, Pt
+    a2 = w.rho0 * w.alpha0 ** 2
+    sc = np.array([w.rho0, a2, a2, a2, w.rho0 * w.beta0 ** 2])[:, None, None]
+    dm = P.to_model(inputs.seeded_real((5, w.nz, w.nx), 31) * sc * 1e-3)
+    R = P.to_field(inputs.seeded_complex((P.B, len(w.rec_cells), 2), 32) * 1e-12)
+    Jd = npy(P.frechet(u_b, dm, tol=1e-7)).astype(np.complex128)
+    g = npy(P.adjoint(u_b, R, tol=1e-7)).astype(np.float64)
+    lhs = np.real(np.vdot(npy(R).astype(np.complex128), Jd))
+    rhs = float(np.sum(npy(dm).astype(np.float64) * g))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    start = inputs.seeded_real((5, w.nz, w.nx), 33)
+    dm_cg, lam, hist = P.normal_cg(u_b, dd, iters=30, lambda_rel=1e-3, power_iters=10, power_start=start,
+                                   tol=1e-6)
+    assert lam > 0 and np.all(np.isfinite(hist))
+    assert hist[-1] < 0.05 * hist[0]
+    pred = P.frechet(u_b, dm_cg, tol=1e-6)
+    r0 = float(torch.linalg.norm(dd.to(torch.complex128)))
+    r1 = float(torch.linalg.norm((dd - pred).to(torch.complex128)))
+    assert r1 < 0.5 * r0, (r1 / r0)
