@@ -48,6 +48,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle sample")
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 plain-path sample")
+    ap.add_argument("--check-every", type=int, default=4,
+                    help="BiCGSTAB iterations between host convergence checks (each check also "
+                         "compacts the launches to the problems still active)")
     ap.add_argument("--sources", type=int, default=32,
                     help="sources per GPU (32 is the benchmark workload; fewer make a smaller batch "
                          "of the same grid for profiler captures)")
@@ -165,10 +168,11 @@ def run_ours(args):
         Ghat, Gspace = dbi.greens_tabulate(P.grid, P.ref, P.omega, dbi.C64)
         u0 = dbi.incident_field(P.grid, P.omega, P.fidx, Gspace, P.src_cells, P.forces)
         u, it_f, _, code_f = dbi.ls_solve(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u0, tol=TOL,
-                                          max_iter=MAX_ITER)
+                                          max_iter=MAX_ITER, check_every=args.check_every)
         r, phi = dbi.data_residual(P.grid, P.omega, P.fidx, P.rec_cells, u, d_obs)
         g, (it_a, _, code_a) = dbi.adjoint_apply(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u, P.rec_cells, r,
-                                                 tol=TOL, max_iter=MAX_ITER, with_status=True)
+                                                 tol=TOL, max_iter=MAX_ITER, check_every=args.check_every,
+                                                 with_status=True)
         reduce_gradient(g, phi)  # sum over ranks (no-op on one GPU)
         return phi, g, it_f, it_a, code_f, code_a
 

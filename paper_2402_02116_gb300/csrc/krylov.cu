@@ -36,9 +36,11 @@ template <typename C> __device__ __forceinline__ C from_z(double2 z) {
   return mk<C>(R(z.x), R(z.y));
 }
 
-// Grid-stride loop over the n elements of problem blockIdx.y (unrolled for memory parallelism).
+// Grid-stride loop over the n elements of problem b (unrolled for memory parallelism).
+// Problem of this CTA: plist[blockIdx.y] when the launch runs a compacted list of problems.
+__device__ __forceinline__ int problem_at(const int *plist, int slot) { return plist ? plist[slot] : slot; }
+
 #define DBI_PROBLEM_LOOP(n)                                                                   \
-  const int b = blockIdx.y;                                                                   \
   const size_t off = size_t(b) * (n);                                                         \
   _Pragma("unroll 4")                                                                         \
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < (n); i += size_t(gridDim.x) * blockDim.x)
@@ -47,6 +49,7 @@ template <typename C> __device__ __forceinline__ C from_z(double2 z) {
 // (a data residual of 1e-12 back-propagates to fields of 1e-21), where FP32 squares underflow.
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_bnorm(size_t n, const C *rhs, double *part) {
+  const int b = blockIdx.y;
   double bb = 0.0;
   DBI_PROBLEM_LOOP(n) {
     const C bi = rhs[off + i];
@@ -68,6 +71,7 @@ __global__ void k_scale(KState *st, const double *part) {
 // x *= scale (inverse = 0) or x /= scale (inverse = 1)
 template <typename C>
 __global__ void k_scale_x(size_t n, const KState *st, C *x, int inverse) {
+  const int b = blockIdx.y;
   using R = typename RealOf<C>::type;
   const double sc = st[blockIdx.y].scale;
   const R f = R(inverse ? 1.0 / sc : sc);
@@ -77,6 +81,7 @@ __global__ void k_scale_x(size_t n, const KState *st, C *x, int inverse) {
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_init(size_t n, const KState *st, const C *rhs, C *v, C *r,
                                                       C *rhat, C *p, C *x, int x_zero, double *part) {
+  const int b = blockIdx.y;
   using A = typename Acc<C>::type;
   using R = typename RealOf<C>::type;
   const R sc = R(st[blockIdx.y].scale);
@@ -123,17 +128,19 @@ __global__ void k_init_state(KState *st, int *active, int *counters, const doubl
 
 template <typename C>
 __global__ void k_zero_flagged(size_t n, const KState *st, C *x) {
+  const int b = blockIdx.y;
   if (!st[blockIdx.y].zero_rhs) return;
   DBI_PROBLEM_LOOP(n) x[off + i] = czero<C>();
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const KState *st, const int *active,
-                                                          int *counters, int parity, const C *r,
-                                                          C *rhat, C *p, const C *v) {
+__global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const int *plist, const KState *st,
+                                                          const int *active, int *counters, int parity,
+                                                          const C *r, C *rhat, C *p, const C *v) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[parity] = 0;
-  if (!active[blockIdx.y]) return;
-  const KState k = st[blockIdx.y];
+  const int b = problem_at(plist, blockIdx.y);
+  if (!active[b]) return;
+  const KState k = st[b];
   if (k.restart) {
     DBI_PROBLEM_LOOP(n) {
       const C ri = r[off + i];
@@ -151,21 +158,22 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const KState
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, KState *st, const int *active,
-                                                          int nparts, const double *partA, const C *r,
-                                                          const C *v, C *s, double *partS) {
+__global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, const int *plist, KState *st,
+                                                          const int *active, int nparts, const double *partA,
+                                                          const C *r, const C *v, C *s, double *partS) {
   using A = typename Acc<C>::type;
-  if (!active[blockIdx.y]) return;
+  const int b = problem_at(plist, blockIdx.y);
+  if (!active[b]) return;
   double sg[2];
-  gather_n<2>(partA + size_t(blockIdx.y) * nparts * kRedSlots, nparts, sg);
-  const KState k = st[blockIdx.y];
+  gather_n<2>(partA + size_t(b) * nparts * kRedSlots, nparts, sg);
+  const KState k = st[b];
   const double2 sigma = make_double2(sg[0], sg[1]);
   const double2 alpha = (sigma.x == 0.0 && sigma.y == 0.0)
                             ? make_double2(0.0, 0.0)
                             : zdiv(make_double2(k.rho_re, k.rho_im), sigma);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st[blockIdx.y].alpha_re = alpha.x;
-    st[blockIdx.y].alpha_im = alpha.y;
+    st[b].alpha_re = alpha.x;
+    st[b].alpha_im = alpha.y;
   }
   const C al = from_z<C>(alpha);
   A ss = 0;
@@ -179,25 +187,27 @@ __global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, KState *st, 
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_update_xr(size_t n, KState *st, const int *active,
-                                                           int nparts, const double *partB, const double *partS,
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(size_t n, const int *plist, KState *st,
+                                                           const int *active, int nparts,
+                                                           const double *partB, const double *partS,
                                                            double tol, const C *p, const C *s,
                                                            const C *t, const C *rhat, C *x, C *r,
                                                            double *partC) {
   using A = typename Acc<C>::type;
-  if (!active[blockIdx.y]) return;
+  const int b = problem_at(plist, blockIdx.y);
+  if (!active[b]) return;
   double q[3], sn[1];
-  gather_n<3>(partB + size_t(blockIdx.y) * nparts * kRedSlots, nparts, q);
-  gather_n<1>(partS + size_t(blockIdx.y) * kRedBlocks * kRedSlots, kRedBlocks, sn);
-  const KState k = st[blockIdx.y];
+  gather_n<3>(partB + size_t(b) * nparts * kRedSlots, nparts, q);
+  gather_n<1>(partS + size_t(b) * kRedBlocks * kRedSlots, kRedBlocks, sn);
+  const KState k = st[b];
   const int half = sn[0] <= tol * tol * k.bnorm2;
   const double2 om = (half || q[2] == 0.0) ? make_double2(0.0, 0.0)
                                            : make_double2(q[0] / q[2], q[1] / q[2]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st[blockIdx.y].om_re = om.x;
-    st[blockIdx.y].om_im = om.y;
-    st[blockIdx.y].half = half;
-    st[blockIdx.y].snorm2 = sn[0];
+    st[b].om_re = om.x;
+    st[b].om_im = om.y;
+    st[b].half = half;
+    st[b].snorm2 = sn[0];
   }
   const C al = from_z<C>(make_double2(k.alpha_re, k.alpha_im));
   const C o = from_z<C>(om);
@@ -217,9 +227,9 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(size_t n, KState *st,
 }
 
 // Convergence test, breakdown restart and beta for the next iteration (one CTA per problem).
-__global__ void k_check(KState *st, int *active, int *counters, int parity, const double *partC,
-                        double tol, int max_iter) {
-  const int b = blockIdx.x;
+__global__ void k_check(const int *plist, KState *st, int *active, int *counters, int parity,
+                        const double *partC, double tol, int max_iter) {
+  const int b = problem_at(plist, blockIdx.x);
   if (!active[b]) return;
   double q[3];
   gather_n<3>(partC + size_t(b) * kRedBlocks * kRedSlots, kRedBlocks, q);
@@ -263,6 +273,33 @@ __global__ void k_check(KState *st, int *active, int *counters, int parity, cons
   atomicAdd(&counters[parity], act);
 }
 
+// plist = the active problems in ascending order, count = how many (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) k_compact(int B, const int *active, int *plist, int *count) {
+  __shared__ int warp_tot[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < B; c0 += blockDim.x) {
+    const int i = c0 + threadIdx.x;
+    const int a = (i < B && active[i]) ? 1 : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, a);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_tot[w];
+    if (a) plist[base + before + __popc(bal & ((1u << lane) - 1u))] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += warp_tot[w];
+      base += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
 __global__ void k_finalize(int B, const KState *st, int *iters, double *relres, int *code) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
@@ -283,6 +320,7 @@ template <> __device__ __forceinline__ double sq64<double2>(double2 v) { return 
 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_sumsq(size_t n, const T *x, double *part) {
+  const int b = blockIdx.y;
   double acc = 0.0;
   DBI_PROBLEM_LOOP(n) acc += sq64<T>(x[off + i]);
   double a[1] = {acc};
@@ -317,7 +355,7 @@ int pow2_scales(const void *x, int precision, bool real, int B, size_t n, double
 
 size_t bytes_solver(const dbi_grid *g, int B, int precision) {
   return 6 * bytes_field(g, B, precision) + align256(size_t(B) * sizeof(KState)) +
-         align256(size_t(B) * sizeof(int)) + 256 + 4 * bytes_partials(B);
+         2 * align256(size_t(B) * sizeof(int)) + 256 + 4 * bytes_partials(B);
 }
 
 SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision) {
@@ -328,6 +366,7 @@ SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision) {
   sb.st = static_cast<KState *>(ar.take(size_t(B) * sizeof(KState)));
   sb.active = static_cast<int *>(ar.take(size_t(B) * sizeof(int)));
   sb.counters = static_cast<int *>(ar.take(256));
+  sb.plist = static_cast<int *>(ar.take(size_t(B) * sizeof(int)));
   sb.partA = static_cast<double *>(ar.take(bytes_partials(B)));
   sb.partS = static_cast<double *>(ar.take(bytes_partials(B)));
   sb.partB = static_cast<double *>(ar.take(bytes_partials(B)));
@@ -375,30 +414,42 @@ static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, voi
     k_zero_flagged<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x);
     if ((rc = check_launch("k_zero_flagged"))) return rc;
   }
-  int remaining = B;
-  if (o.check_every > 0 && (rc = read_counter(sb.counters + 1, s, &remaining))) return rc;
+  // Launches run over the problems still active: at every host check the active problems are
+  // compacted into sb.plist (ascending order) and the grids shrink to them.
+  int nact = B;
+  const int *plist = nullptr;
+  auto compact = [&]() -> int {
+    k_compact<<<1, 1024, 0, s>>>(B, sb.active, sb.plist, sb.counters + 2);
+    int e = check_launch("k_compact");
+    if (e == DBI_OK) e = read_counter(sb.counters + 2, s, &nact);
+    plist = sb.plist;
+    return e;
+  };
+  if (o.check_every > 0 && (rc = compact())) return rc;
   op.active = sb.active;
   op.krhat = rhat;
   const int nparts = operator_parts(op.nz, op.lx, op.precision);
-  for (int it = 0; it < o.max_iter && remaining > 0; ++it) {
+  for (int it = 0; it < o.max_iter && nact > 0; ++it) {
     const int parity = it & 1;
-    k_update_p<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, sb.counters, parity, r, rhat, p, v);
+    const dim3 g2(kRedBlocks, nact);
+    op.plist = plist;
+    op.nb = nact;
+    k_update_p<C><<<g2, kRedThreads, 0, s>>>(n, plist, sb.st, sb.active, sb.counters, parity, r, rhat, p, v);
     if ((rc = check_launch("k_update_p"))) return rc;
     op.epi = 1; op.in = p; op.ident = p; op.out = v; op.part_out = sb.partA;
     if ((rc = run_operator(op, s))) return rc;
-    k_update_s<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, nparts, sb.partA, r, v, sv, sb.partS);
+    k_update_s<C><<<g2, kRedThreads, 0, s>>>(n, plist, sb.st, sb.active, nparts, sb.partA, r, v, sv, sb.partS);
     if ((rc = check_launch("k_update_s"))) return rc;
     op.epi = 2; op.in = sv; op.ident = sv; op.out = t; op.part_out = sb.partB;
     if ((rc = run_operator(op, s))) return rc;
-    k_update_xr<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, sb.active, nparts, sb.partB, sb.partS, o.tol, p,
-                                                 sv, t, rhat, x, r, sb.partC);
+    k_update_xr<C><<<g2, kRedThreads, 0, s>>>(n, plist, sb.st, sb.active, nparts, sb.partB, sb.partS, o.tol,
+                                               p, sv, t, rhat, x, r, sb.partC);
     if ((rc = check_launch("k_update_xr"))) return rc;
-    k_check<<<B, 32, 0, s>>>(sb.st, sb.active, sb.counters, parity, sb.partC, o.tol, o.max_iter);
+    k_check<<<nact, 32, 0, s>>>(plist, sb.st, sb.active, sb.counters, parity, sb.partC, o.tol, o.max_iter);
     if ((rc = check_launch("k_check"))) return rc;
-    if (o.check_every > 0 && ((it + 1) % o.check_every == 0) &&
-        (rc = read_counter(sb.counters + parity, s, &remaining)))
-      return rc;
+    if (o.check_every > 0 && ((it + 1) % o.check_every == 0) && (rc = compact())) return rc;
   }
+  op.plist = nullptr;
   if (unscale) {
     k_scale_x<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x, 1);
     if ((rc = check_launch("k_scale_x"))) return rc;

@@ -21,7 +21,8 @@ struct SolverBufs {
   void *r, *rhat, *p, *v, *s, *t;  // [B][2][nz][nx] complex
   KState *st;                      // [B]
   int *active;                     // [B]
-  int *counters;                   // [2]
+  int *counters;                   // [4]: active counts by iteration parity, compaction count
+  int *plist;                      // [B] active problems, compacted
   double *partA, *partS, *partB, *partC;  // [B][kRedBlocks][kRedSlots]
 };
 

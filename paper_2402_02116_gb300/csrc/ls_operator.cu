@@ -34,6 +34,8 @@ template <typename C> struct OpP {
   const C *Ghat;
   const C *tw;
   const int *active;
+  const int *plist;  // slot -> problem (NULL: problem = s0 + slot)
+  int s0;            // first slot of this launch
   const double *in_scale, *m_scale, *out_scale;
   const C *krhat;
   double *part_out;
@@ -63,6 +65,12 @@ template <typename C, int LZ> struct ColCfg {
 // Transposition tile of the rows kernels: [2][LX][ROWS + 1] (padded against bank conflicts).
 template <typename C, int LX> constexpr size_t tile_elems() {
   return size_t(2) * LX * (RowCfg<C, LX>::ROWS + 1);
+}
+
+// Problem of this CTA's launch slot (blockIdx.y); the spectral scratch is indexed by the slot.
+template <typename C> __device__ __forceinline__ int problem_of(const OpP<C> &p) {
+  const int sl = p.s0 + int(blockIdx.y);
+  return p.plist ? p.plist[sl] : sl;
 }
 
 // Barrier over the threads that share a line: the T threads of one row (rows kernels).
@@ -114,7 +122,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
   using Rl = typename RealOf<C>::type;
   using RC = RowCfg<C, LX>;
   constexpr int ROWS = RC::ROWS, T = RC::T, LP = RC::LP;
-  const int b = blockIdx.y;
+  const int b = problem_of(p), slot = blockIdx.y;
   if ((p.active && !p.active[b]) || unsigned(p.fidx[b]) >= unsigned(p.nf)) return;
   const int z0 = blockIdx.x * ROWS;
   const int nz = p.nz, nx = p.nx;
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) smem[(size_t(c) * LX + t + m * T) * RP + rr] = v[c][m];
   __syncthreads();
-  C *Tb = p.T + size_t(b) * 2 * LX * nz;
+  C *Tb = p.T + size_t(slot) * 2 * LX * nz;
   for (int idx = threadIdx.x; idx < 2 * LX * ROWS; idx += RC::NT) {
     const int r = idx % ROWS, ck = idx / ROWS;  // ck = c * LX + kx
     if (z0 + r < nz) Tb[size_t(ck) * nz + z0 + r] = smem[size_t(ck) * RP + r];
@@ -227,7 +235,7 @@ template <typename C, int LZ>
 __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_cols(OpP<C> p) {
   using CF = ColCfg<C, LZ>;
   constexpr int CC = CF::CC, T = CF::T, LP = CF::LP;
-  const int b = blockIdx.y;
+  const int b = problem_of(p), slot = blockIdx.y;
   if ((p.active && !p.active[b]) || unsigned(p.fidx[b]) >= unsigned(p.nf)) return;
   const int col = threadIdx.x / T, t = threadIdx.x - col * T;
   const int kx = blockIdx.x * CC + col;
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_col
   const bool live = kx < lx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *smem = reinterpret_cast<C *>(smem_raw);
-  C *Tb = p.T + size_t(b) * 2 * lx * nz;
+  C *Tb = p.T + size_t(slot) * 2 * lx * nz;
   const C *c0 = Tb + size_t(kx) * nz, *c1 = Tb + (size_t(lx) + kx) * nz;
   C v[2][8];
 #pragma unroll
@@ -280,14 +288,14 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
   using Rl = typename RealOf<C>::type;
   using RC = RowCfg<C, LX>;
   constexpr int ROWS = RC::ROWS, T = RC::T, LP = RC::LP;
-  const int b = blockIdx.y;
+  const int b = problem_of(p), slot = blockIdx.y;
   if ((p.active && !p.active[b]) || unsigned(p.fidx[b]) >= unsigned(p.nf)) return;
   const int z0 = blockIdx.x * ROWS;
   const int nz = p.nz, nx = p.nx;
   const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *smem = reinterpret_cast<C *>(smem_raw);
-  const C *Tb = p.T + size_t(b) * 2 * LX * nz;
+  const C *Tb = p.T + size_t(slot) * 2 * LX * nz;
   // ROWS consecutive z of every (c, kx) into tile[c][kx][r], then each thread takes its row
   constexpr int RP = ROWS + 1, NLD = 2 * LX * ROWS / RC::NT;
   static_assert((2 * LX * ROWS) % RC::NT == 0, "tile load");
@@ -350,31 +358,31 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
 }
 
 
-// The three kernels for problems [b0, b0 + nb) of the batch, using the first nb problems' worth of
-// the spectral scratch.
-template <typename C> static int run_chunk(const OpArgs &a, int b0, int nb, cudaStream_t s) {
+// The three kernels for launch slots [s0, s0 + nb) (problems plist[slot], or the slots themselves),
+// each slot using its own part of the spectral scratch.
+template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, cudaStream_t s) {
   using Rl = typename RealOf<C>::type;
-  const size_t fo = size_t(b0) * 2 * a.nz * a.nx;  // field offset of the chunk
   OpP<C> p;
   p.nz = a.nz; p.nx = a.nx; p.lz = a.lz; p.lx = a.lx; p.nf = a.nf;
   p.inv2h = Rl(1.0 / (2.0 * a.h));
-  p.omega = a.omega; p.fidx = a.fidx + b0;
+  p.omega = a.omega; p.fidx = a.fidx;
   p.m = static_cast<const Rl *>(a.m);
   for (int i = 0; i < 5; ++i) p.ref[i] = Rl(a.ref[i]);
-  p.in = static_cast<const C *>(a.in) + fo;
-  p.ident = a.ident ? static_cast<const C *>(a.ident) + fo : nullptr;
-  p.out = static_cast<C *>(a.out) + fo;
+  p.in = static_cast<const C *>(a.in);
+  p.ident = static_cast<const C *>(a.ident);
+  p.out = static_cast<C *>(a.out);
   p.T = static_cast<C *>(a.T);
   p.Ghat = static_cast<const C *>(a.Ghat);
   p.tw = static_cast<const C *>(a.tw);
-  p.active = a.active ? a.active + b0 : nullptr;
-  p.in_scale = a.in_scale ? a.in_scale + b0 : nullptr;
+  p.active = a.active;
+  p.plist = a.plist;
+  p.s0 = s0;
+  p.in_scale = a.in_scale;
   p.m_scale = a.m_scale;
-  p.out_scale = a.out_scale ? a.out_scale + b0 : nullptr;
+  p.out_scale = a.out_scale;
   p.part_count = operator_parts(a.nz, a.lx, a.precision);
-  const size_t pk = size_t(b0) * p.part_count * kRedSlots;
-  p.krhat = a.krhat ? static_cast<const C *>(a.krhat) + fo : nullptr;
-  p.part_out = a.part_out ? a.part_out + pk : nullptr;
+  p.krhat = static_cast<const C *>(a.krhat);
+  p.part_out = a.part_out;
   int rc = DBI_OK;
   const bool stencil = a.stencil;
   prof_mark(PROF_ROWS_FORWARD, false, s);
@@ -427,13 +435,14 @@ template <typename C> static int run_chunk(const OpArgs &a, int b0, int nb, cuda
 }
 
 template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
-  if (a.B == 0) return DBI_OK;
+  const int nb = a.plist ? a.nb : a.B;
+  if (nb <= 0) return DBI_OK;
   dbi_grid g{a.nz, a.nx, a.lz, a.lx, a.h};
   const int chunk = spectral_chunk(&g, a.B, a.precision);
   int rc = DBI_OK;
   prof_mark(PROF_OPERATOR, false, s);
-  for (int b0 = 0; b0 < a.B && rc == DBI_OK; b0 += chunk)
-    rc = run_chunk<C>(a, b0, std::min(chunk, a.B - b0), s);
+  for (int s0 = 0; s0 < nb && rc == DBI_OK; s0 += chunk)
+    rc = run_chunk<C>(a, s0, std::min(chunk, nb - s0), s);
   prof_mark(PROF_OPERATOR, true, s);
   return rc;
 }

@@ -26,6 +26,8 @@ struct OpArgs {
   const void *Ghat;     // device [nf][3][lx][lz] complex (column-major)
   const void *tw;       // device twiddle table of the precision
   const int *active;    // device [B] (0 = skip the problem) or NULL
+  const int *plist;     // device [nb]: the problems to run (launch slot -> problem), or NULL
+  int nb;               // launch slots (problems run); B when plist is NULL
   // Exact power-of-two scalings that keep FP32 intermediates in range (each may be NULL):
   const double *in_scale;   // device [B]: the input field is multiplied by in_scale[b]
   const double *m_scale;    // device [1]: the contrast (m - ref) is multiplied by m_scale[0]
