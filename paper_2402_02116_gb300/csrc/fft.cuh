@@ -69,6 +69,30 @@ template <typename C, bool INV> __host__ __device__ __forceinline__ void dft8(C 
   v[3] = hadd(e[3], w3);   v[7] = hsub(e[3], w3);
 }
 
+// 8-point DFT of v[0..3] with v[4..7] = 0 (never read): the first pass of a transform whose
+// input line is zero beyond its first half. Each 4-point DFT of two non-zero inputs a, b gives
+// a + b, a + W4 b, a - b, a - W4 b.
+template <typename C, bool INV> __host__ __device__ __forceinline__ void dft8_half_in(C *v) {
+  using R = typename RealOf<C>::type;
+  const R h = R(0.70710678118654752440);
+  const C me = hmul_mi<C, INV>(v[2]), mo = hmul_mi<C, INV>(v[3]);
+  C e[4] = {hadd(v[0], v[2]), hadd(v[0], me), hsub(v[0], v[2]), hsub(v[0], me)};
+  C o[4] = {hadd(v[1], v[3]), hadd(v[1], mo), hsub(v[1], v[3]), hsub(v[1], mo)};
+  C w1, w2, w3;
+  if (INV) {
+    w1.x = (o[1].x - o[1].y) * h; w1.y = (o[1].x + o[1].y) * h;
+    w3.x = -(o[3].x + o[3].y) * h; w3.y = (o[3].x - o[3].y) * h;
+  } else {
+    w1.x = (o[1].x + o[1].y) * h; w1.y = (o[1].y - o[1].x) * h;
+    w3.x = (o[3].y - o[3].x) * h; w3.y = -(o[3].x + o[3].y) * h;
+  }
+  w2 = hmul_mi<C, INV>(o[2]);
+  v[0] = hadd(e[0], o[0]); v[4] = hsub(e[0], o[0]);
+  v[1] = hadd(e[1], w1);   v[5] = hsub(e[1], w1);
+  v[2] = hadd(e[2], w2);   v[6] = hsub(e[2], w2);
+  v[3] = hadd(e[3], w3);   v[7] = hsub(e[3], w3);
+}
+
 template <typename C, int R, bool INV> __host__ __device__ __forceinline__ void dft(C *v) {
   if constexpr (R == 2) dft2<C, INV>(v);
   else if constexpr (R == 4) dft4<C, INV>(v);

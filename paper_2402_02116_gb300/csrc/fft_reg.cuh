@@ -44,16 +44,19 @@ template <typename C, int L> struct RegFFT {
   __host__ __device__ __forceinline__ static int pad(int i) { return i + (i >> 4); }
 
   // One radix-R pass from registers (pass input in natural order) into a shared-memory line.
-  template <int R, int NS, bool INV>
+  // HIN: the line is zero beyond its first half (first pass only: R = 8, NS = 1, so v[4..7]
+  // are those zeros and are not read).
+  template <int R, int NS, bool INV, bool HIN = false>
   __host__ __device__ __forceinline__ static void pass(const C (&v)[8], C *line, int t,
                                                       const C *__restrict__ tw) {
     constexpr int NB = 8 / R;
+    static_assert(!HIN || (R == 8 && NS == 1), "half-zero input only in a first radix-8 pass");
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = t + i * T;
       C x[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[r] = v[i + r * NB];
+      for (int r = 0; r < R; ++r) x[r] = (HIN && r >= 4) ? v[0] : v[i + r * NB];
       const int k = j % NS;
       if constexpr (NS > 1) {
         C w1 = tw[k * (L / (NS * R)) * TWS];
@@ -63,7 +66,8 @@ template <typename C, int L> struct RegFFT {
 #pragma unroll
         for (int r = 1; r < R; ++r) x[r] = hmul(x[r], w[r]);
       }
-      dft<C, R, INV>(x);
+      if constexpr (HIN) dft8_half_in<C, INV>(x);
+      else dft<C, R, INV>(x);
       const int base = (j - k) * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) line[pad(base + r * NS)] = x[r];
@@ -105,15 +109,17 @@ template <typename C, int L> struct RegFFT {
 // that shares those lines (a barrier over at least the line's T threads).
 template <int N> using IC = std::integral_constant<int, N>;
 
+// HIN: every line is zero beyond its first half (v[l][4..7] = 0 on entry; they are not read).
 template <int L> struct RegPlan {
-  template <typename C, int NLT, bool INV, typename Sync>
+  template <typename C, int NLT, bool INV, bool HIN = false, typename Sync>
   __host__ __device__ __forceinline__ static void run(C (&v)[NLT][8], C *const (&lines)[NLT], int t,
                                                       const C *__restrict__ tw, Sync &&sync) {
     using F = RegFFT<C, L>;
     auto step = [&](auto r_, auto ns_) {
       constexpr int R = decltype(r_)::value, NS = decltype(ns_)::value;
+      constexpr bool H = HIN && NS == 1;
 #pragma unroll
-      for (int l = 0; l < NLT; ++l) F::template pass<R, NS, INV>(v[l], lines[l], t, tw);
+      for (int l = 0; l < NLT; ++l) F::template pass<R, NS, INV, H>(v[l], lines[l], t, tw);
       sync();
 #pragma unroll
       for (int l = 0; l < NLT; ++l) F::gather(v[l], lines[l], t);

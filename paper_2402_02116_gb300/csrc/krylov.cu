@@ -79,8 +79,10 @@ __global__ void k_scale_x(size_t n, const KState *st, C *x, int inverse) {
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_init(size_t n, const KState *st, const C *rhs, C *v, C *r,
-                                                      C *rhat, C *p, C *x, int x_zero, double *part) {
+__global__ void __launch_bounds__(kRedThreads) k_init(size_t n, const KState *st, const C *__restrict__ rhs,
+                                                      C *__restrict__ v, C *__restrict__ r,
+                                                      C *__restrict__ rhat, C *__restrict__ p,
+                                                      C *__restrict__ x, int x_zero, double *part) {
   const int b = blockIdx.y;
   using A = typename Acc<C>::type;
   using R = typename RealOf<C>::type;
@@ -136,7 +138,8 @@ __global__ void k_zero_flagged(size_t n, const KState *st, C *x) {
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const int *plist, const KState *st,
                                                           const int *active, int *counters, int parity,
-                                                          const C *r, C *rhat, C *p, const C *v) {
+                                                          const C *__restrict__ r, C *__restrict__ rhat,
+                                                          C *__restrict__ p, const C *__restrict__ v) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[parity] = 0;
   const int b = problem_at(plist, blockIdx.y);
   if (!active[b]) return;
@@ -160,7 +163,8 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const int *p
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, const int *plist, KState *st,
                                                           const int *active, int nparts, const double *partA,
-                                                          const C *r, const C *v, C *s, double *partS) {
+                                                          const C *__restrict__ r, const C *__restrict__ v,
+                                                          C *__restrict__ s, double *partS) {
   using A = typename Acc<C>::type;
   const int b = problem_at(plist, blockIdx.y);
   if (!active[b]) return;
@@ -190,9 +194,10 @@ template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_update_xr(size_t n, const int *plist, KState *st,
                                                            const int *active, int nparts,
                                                            const double *partB, const double *partS,
-                                                           double tol, const C *p, const C *s,
-                                                           const C *t, const C *rhat, C *x, C *r,
-                                                           double *partC) {
+                                                           double tol, const C *__restrict__ p,
+                                                           const C *__restrict__ s, const C *__restrict__ t,
+                                                           const C *__restrict__ rhat, C *__restrict__ x,
+                                                           C *__restrict__ r, double *partC) {
   using A = typename Acc<C>::type;
   const int b = problem_at(plist, blockIdx.y);
   if (!active[b]) return;

@@ -62,6 +62,11 @@ template <typename C, int LZ> struct ColCfg {
   static constexpr int NT = CC * T;
   static constexpr int LP = RegFFT<C, LZ>::LP;
 };
+// Every line holds its data in its first half: the entry points require lz >= 2 nz - 1 and
+// lx >= 2 nx - 1, so a cell index t + m L/8 < n <= L/2 has m < 4. Points m = 4..7 are zero on
+// input to a forward transform and never needed on output of an inverse one.
+constexpr int kHalf = 4;
+
 // Transposition tile of the rows kernels: [2][LX][ROWS + 1] (padded against bank conflicts).
 template <typename C, int LX> constexpr size_t tile_elems() {
   return size_t(2) * LX * (RowCfg<C, LX>::ROWS + 1);
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
     for (int m = 0; m < 8; ++m) {
       const int x = t + m * T;
       C o1 = czero<C>(), o3 = czero<C>();
-      if (z < nz && x < nx) {
+      if (m < kHalf && z < nz && x < nx) {
         const int r2 = rr + 1;
         o1 = cadd(csub(S(0, r2, x + 1), S(0, r2, x - 1)), csub(S(2, r2 + 1, x), S(2, r2 - 1, x)));
         o3 = cadd(csub(S(2, r2, x + 1), S(2, r2, x - 1)), csub(S(1, r2 + 1, x), S(1, r2 - 1, x)));
@@ -206,13 +211,13 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int x = t + m * T;
-      const bool in = z < nz && x < nx;
+      const bool in = m < kHalf && z < nz && x < nx;
       v[0][m] = in ? cscale(__ldg(u1 + size_t(z) * nx + x), isc) : czero<C>();
       v[1][m] = in ? cscale(__ldg(u3 + size_t(z) * nx + x), isc) : czero<C>();
     }
   }
   C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
-  RegPlan<LX>::template run<C, 2, false>(v, lines, t, p.tw, RowSync<T>{1 + rr});
+  RegPlan<LX>::template run<C, 2, false, true>(v, lines, t, p.tw, RowSync<T>{1 + rr});
   // transpose through shared memory: tile[c][kx][rr], then ROWS consecutive z per kx
   __syncthreads();
   constexpr int RP = ROWS + 1;
@@ -249,12 +254,12 @@ __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_col
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int z = t + m * T;
-    const bool in = live && z < nz;
+    const bool in = m < kHalf && live && z < nz;
     v[0][m] = in ? c0[z] : czero<C>();
     v[1][m] = in ? c1[z] : czero<C>();
   }
   C *const lines[2] = {smem + size_t(col) * LP, smem + size_t(CC + col) * LP};
-  RegPlan<LZ>::template run<C, 2, false>(v, lines, t, p.tw, RowSync<T>{1 + col});
+  RegPlan<LZ>::template run<C, 2, false, true>(v, lines, t, p.tw, RowSync<T>{1 + col});
   if (live) {
     const size_t plane = size_t(lx) * LZ;
     const C *G = p.Ghat + size_t(p.fidx[b]) * 3 * plane + size_t(kx) * LZ;
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_col
   if (live) {
     C *o0 = Tb + size_t(kx) * nz, *o1 = Tb + (size_t(lx) + kx) * nz;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < kHalf; ++m) {
       const int z = t + m * T;
       if (z < nz) {
         o0[z] = v[0][m];
@@ -326,27 +331,35 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // per-thread partials of the fused inner products
   if (z < nz) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < 2; ++c) {
+      // every load of the component first (ident and rhat are read-only here), then the stores
+      C id[kHalf], h[kHalf];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
+      for (int m = 0; m < kHalf; ++m) {
+        const int x = t + m * T;
+        const size_t o = base + size_t(c) * nz * nx + x;
+        id[m] = (p.ident && x < nx) ? __ldg(p.ident + o) : czero<C>();
+        if constexpr (EPI == 1) h[m] = x < nx ? __ldg(p.krhat + o) : czero<C>();
+      }
+#pragma unroll
+      for (int m = 0; m < kHalf; ++m) {
         const int x = t + m * T;
         if (x < nx) {
           const size_t o = base + size_t(c) * nz * nx + x;
           const C r = cscale(v[c][m], osc);
-          const C id = p.ident ? p.ident[o] : czero<C>();
-          const C w = p.ident ? csub(id, r) : r;
+          const C w = p.ident ? csub(id[m], r) : r;
           p.out[o] = w;
           if constexpr (EPI == 1) {  // conj(rhat) w
-            const C h = p.krhat[o];
-            a0 += float(h.x) * float(w.x) + float(h.y) * float(w.y);
-            a1 += float(h.x) * float(w.y) - float(h.y) * float(w.x);
+            a0 += float(h[m].x) * float(w.x) + float(h[m].y) * float(w.y);
+            a1 += float(h[m].x) * float(w.y) - float(h[m].y) * float(w.x);
           } else if constexpr (EPI == 2) {  // conj(w) id and |w|^2
-            a0 += float(w.x) * float(id.x) + float(w.y) * float(id.y);
-            a1 += float(w.x) * float(id.y) - float(w.y) * float(id.x);
+            a0 += float(w.x) * float(id[m].x) + float(w.y) * float(id[m].y);
+            a1 += float(w.x) * float(id[m].y) - float(w.y) * float(id[m].x);
             a2 += float(w.x) * float(w.x) + float(w.y) * float(w.y);
           }
         }
       }
+    }
   }
   if constexpr (EPI == 1) {
     double acc[2] = {double(a0), double(a1)};
