@@ -11,11 +11,18 @@
 // distinct banks; the last pass writes position j + r L/R = t + (i + r 8/R) T, i.e. straight back
 // into the registers in natural order.
 //
-// Forward transforms use exp(-2 pi i jk/L), inverse ones exp(+2 pi i jk/L), unnormalised;
-// each butterfly reads one twiddle from tw[m] = exp(-2 pi i m / 3072) and forms its powers.
+// Forward transforms use exp(-2 pi i jk/L), inverse ones exp(+2 pi i jk/L), unnormalised.
+// A thread's twiddles depend only on t and the pass, so each kernel reads them once from the
+// table tw[m] = exp(-2 pi i m / 3072) into a TwReg (one base twiddle per butterfly of every
+// twiddled pass); each pass forms the powers once and applies them to all the thread's lines.
+//
+// Radix plans: V = 0 puts the radix-8 passes first and a smaller radix last; V = 1 puts the
+// smaller radix first (the two coincide when L is a power of 8). Both are exact orderings of the
+// same factorisation; which one runs faster depends on the length and is measured at run time.
 #pragma once
 
 #include <type_traits>
+#include <utility>
 
 #include "fft.cuh"
 
@@ -34,6 +41,74 @@ __host__ __device__ __forceinline__ void twiddle_powers(C w1, C (&w)[R]) {
   if constexpr (R > 7) w[7] = hmul(w[4], w[3]);
 }
 
+// R-point DFT of x[0 .. R/2) with x[R/2 .. R) = 0 (not read).
+template <typename C, int R, bool INV> __host__ __device__ __forceinline__ void dft_half_in(C *x) {
+  if constexpr (R == 2) {
+    x[1] = x[0];
+  } else if constexpr (R == 4) {
+    const C a = x[0], b = x[1], mb = hmul_mi<C, INV>(b);
+    x[0] = hadd(a, b); x[1] = hadd(a, mb); x[2] = hsub(a, b); x[3] = hsub(a, mb);
+  } else {
+    dft8_half_in<C, INV>(x);
+  }
+}
+
+// Radix sequence of a plan.
+template <int L, int V> struct Radices;
+template <> struct Radices<16, 0> { static constexpr int n = 2, r[2] = {8, 2}; };
+template <> struct Radices<16, 1> { static constexpr int n = 2, r[2] = {2, 8}; };
+template <> struct Radices<32, 0> { static constexpr int n = 2, r[2] = {8, 4}; };
+template <> struct Radices<32, 1> { static constexpr int n = 2, r[2] = {4, 8}; };
+template <> struct Radices<64, 0> { static constexpr int n = 2, r[2] = {8, 8}; };
+template <> struct Radices<64, 1> { static constexpr int n = 2, r[2] = {8, 8}; };
+template <> struct Radices<128, 0> { static constexpr int n = 3, r[3] = {8, 8, 2}; };
+template <> struct Radices<128, 1> { static constexpr int n = 3, r[3] = {2, 8, 8}; };
+template <> struct Radices<256, 0> { static constexpr int n = 3, r[3] = {8, 8, 4}; };
+template <> struct Radices<256, 1> { static constexpr int n = 3, r[3] = {4, 8, 8}; };
+template <> struct Radices<512, 0> { static constexpr int n = 3, r[3] = {8, 8, 8}; };
+template <> struct Radices<512, 1> { static constexpr int n = 3, r[3] = {8, 8, 8}; };
+template <> struct Radices<1024, 0> { static constexpr int n = 4, r[4] = {8, 8, 8, 2}; };
+template <> struct Radices<1024, 1> { static constexpr int n = 4, r[4] = {2, 8, 8, 8}; };
+
+template <int L, int V> struct PlanInfo {
+  using Rd = Radices<L, V>;
+  static constexpr int np = Rd::n;
+  static constexpr int radix(int p) { return Rd::r[p]; }
+  static constexpr int ns(int p) {  // product of the radices before pass p
+    int s = 1;
+    for (int q = 0; q < p; ++q) s *= Rd::r[q];
+    return s;
+  }
+  static constexpr int woff(int p) {  // first base twiddle of pass p in the TwReg
+    int o = 0;
+    for (int q = 1; q < p; ++q) o += 8 / Rd::r[q];
+    return o;
+  }
+  static constexpr int nw = woff(np);  // base twiddles per thread (passes 1 .. np-1)
+};
+
+template <typename C, int L, int V = 0> struct TwReg {
+  static constexpr int NW = PlanInfo<L, V>::nw;
+  C w[NW];
+  // Base twiddles W_{Ns R}^{j mod Ns} of thread t's butterflies j = t + i L/8 in every pass > 0.
+  __host__ __device__ __forceinline__ TwReg(int t, const C *__restrict__ tw) {
+    using P = PlanInfo<L, V>;
+    constexpr int TWS = kTwiddleN / L, T = L / 8;
+    [&]<int... p>(std::integer_sequence<int, p...>) {
+      (
+          [&] {
+            constexpr int q = p + 1, R = P::radix(q), NS = P::ns(q), NB = 8 / R;
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+              const int k = (t + i * T) % NS;
+              w[P::woff(q) + i] = tw[k * (L / (NS * R)) * TWS];
+            }
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, P::np - 1>{});
+  }
+};
+
 template <typename C, int L> struct RegFFT {
   static constexpr int T = L / 8;                 // threads per line
   static constexpr int LP = L + L / 16 + 2;       // padded line length in shared memory
@@ -43,34 +118,36 @@ template <typename C, int L> struct RegFFT {
   // needs the minimum two shared-memory wavefronts per warp (8-byte points).
   __host__ __device__ __forceinline__ static int pad(int i) { return i + (i >> 4); }
 
-  // One radix-R pass from registers (pass input in natural order) into a shared-memory line.
-  // HIN: the line is zero beyond its first half (first pass only: R = 8, NS = 1, so v[4..7]
-  // are those zeros and are not read).
-  template <int R, int NS, bool INV, bool HIN = false>
-  __host__ __device__ __forceinline__ static void pass(const C (&v)[8], C *line, int t,
-                                                      const C *__restrict__ tw) {
+  // The NB = 8/R butterflies of one pass on registers in natural order: twiddle by the powers
+  // wp[i][r] (NS > 1), R-point DFT. HIN (first pass only): v[4..7] are zero and not read.
+  template <int R, int NS, bool INV, bool HIN>
+  __host__ __device__ __forceinline__ static void butterflies(C (&v)[8], const C (&wp)[8 / R][R]) {
     constexpr int NB = 8 / R;
-    static_assert(!HIN || (R == 8 && NS == 1), "half-zero input only in a first radix-8 pass");
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-      const int j = t + i * T;
       C x[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[r] = (HIN && r >= 4) ? v[0] : v[i + r * NB];
-      const int k = j % NS;
+      for (int r = 0; r < R; ++r) x[r] = (HIN && i + r * NB >= 4) ? v[0] : v[i + r * NB];
       if constexpr (NS > 1) {
-        C w1 = tw[k * (L / (NS * R)) * TWS];
-        if (INV) w1.y = -w1.y;
-        C w[R];
-        twiddle_powers<C, R>(w1, w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) x[r] = hmul(x[r], w[r]);
+        for (int r = 1; r < R; ++r) x[r] = hmul(x[r], wp[i][r]);
       }
-      if constexpr (HIN) dft8_half_in<C, INV>(x);
+      if constexpr (HIN) dft_half_in<C, R, INV>(x);
       else dft<C, R, INV>(x);
-      const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) line[pad(base + r * NS)] = x[r];
+      for (int r = 0; r < R; ++r) v[i + r * NB] = x[r];
+    }
+  }
+
+  // Store a pass's outputs (held in v as produced by butterflies()) at their Stockham positions.
+  template <int R, int NS>
+  __host__ __device__ __forceinline__ static void scatter(const C (&v)[8], C *line, int t) {
+    constexpr int NB = 8 / R;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int j = t + i * T, k = j % NS, base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) line[pad(base + r * NS)] = v[i + r * NB];
     }
   }
 
@@ -79,68 +156,51 @@ template <typename C, int L> struct RegFFT {
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = line[pad(t + m * T)];
   }
-
-  // The last pass (NS = L / R): its outputs land in the registers in natural order.
-  template <int R, bool INV>
-  __host__ __device__ __forceinline__ static void last(C (&v)[8], int t, const C *__restrict__ tw) {
-    constexpr int NB = 8 / R, NS = L / R;
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      const int j = t + i * T;
-      C x[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) x[r] = v[i + r * NB];
-      C w1 = tw[j * TWS];  // W_{NS R}^{r j} = W_L^{r j}
-      if (INV) w1.y = -w1.y;
-      C w[R];
-      twiddle_powers<C, R>(w1, w);
-#pragma unroll
-      for (int r = 1; r < R; ++r) x[r] = hmul(x[r], w[r]);
-      dft<C, R, INV>(x);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[i + r * NB] = x[r];
-      (void)NS;
-    }
-  }
 };
 
-// Radix plans (8 values per thread; the product of the radices is L). run() transforms the NLT
-// lines held by the calling thread; sync() must order the shared-memory accesses of every thread
-// that shares those lines (a barrier over at least the line's T threads).
-template <int N> using IC = std::integral_constant<int, N>;
+// Powers of the NB base twiddles of one pass (conjugated for an inverse transform).
+template <typename C, int R, bool INV, int NB>
+__host__ __device__ __forceinline__ void pass_powers(const C *w1, C (&wp)[NB][R]) {
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    C b = w1[i];
+    if (INV) b.y = -b.y;
+    C pw[R];
+    twiddle_powers<C, R>(b, pw);
+#pragma unroll
+    for (int r = 0; r < R; ++r) wp[i][r] = pw[r];
+  }
+}
 
+// run() transforms the NLT lines held by the calling thread; sync() must order the shared-memory
+// accesses of every thread that shares those lines (a barrier over at least the line's T threads).
 // HIN: every line is zero beyond its first half (v[l][4..7] = 0 on entry; they are not read).
-template <int L> struct RegPlan {
+template <int L, int V = 0> struct RegPlan {
   template <typename C, int NLT, bool INV, bool HIN = false, typename Sync>
   __host__ __device__ __forceinline__ static void run(C (&v)[NLT][8], C *const (&lines)[NLT], int t,
-                                                      const C *__restrict__ tw, Sync &&sync) {
+                                                      const TwReg<C, L, V> &tr, Sync &&sync) {
     using F = RegFFT<C, L>;
-    auto step = [&](auto r_, auto ns_) {
-      constexpr int R = decltype(r_)::value, NS = decltype(ns_)::value;
-      constexpr bool H = HIN && NS == 1;
+    using P = PlanInfo<L, V>;
+    [&]<int... p>(std::integer_sequence<int, p...>) {
+      (
+          [&] {
+            constexpr int R = P::radix(p), NS = P::ns(p), NB = 8 / R;
+            constexpr bool H = HIN && p == 0, LAST = p == P::np - 1;
+            C wp[NB][R];
+            if constexpr (NS > 1) pass_powers<C, R, INV, NB>(tr.w + P::woff(p), wp);
 #pragma unroll
-      for (int l = 0; l < NLT; ++l) F::template pass<R, NS, INV, H>(v[l], lines[l], t, tw);
-      sync();
+            for (int l = 0; l < NLT; ++l) F::template butterflies<R, NS, INV, H>(v[l], wp);
+            if constexpr (!LAST) {
 #pragma unroll
-      for (int l = 0; l < NLT; ++l) F::gather(v[l], lines[l], t);
-      sync();
-    };
-    auto fin = [&](auto r_) {
-      constexpr int R = decltype(r_)::value;
+              for (int l = 0; l < NLT; ++l) F::template scatter<R, NS>(v[l], lines[l], t);
+              sync();
 #pragma unroll
-      for (int l = 0; l < NLT; ++l) F::template last<R, INV>(v[l], t, tw);
-    };
-    if constexpr (L == 16) { step(IC<8>{}, IC<1>{}); fin(IC<2>{}); }
-    else if constexpr (L == 32) { step(IC<8>{}, IC<1>{}); fin(IC<4>{}); }
-    else if constexpr (L == 64) { step(IC<8>{}, IC<1>{}); fin(IC<8>{}); }
-    else if constexpr (L == 128) { step(IC<8>{}, IC<1>{}); step(IC<8>{}, IC<8>{}); fin(IC<2>{}); }
-    else if constexpr (L == 256) { step(IC<8>{}, IC<1>{}); step(IC<8>{}, IC<8>{}); fin(IC<4>{}); }
-    else if constexpr (L == 512) { step(IC<8>{}, IC<1>{}); step(IC<8>{}, IC<8>{}); fin(IC<8>{}); }
-    else if constexpr (L == 1024) {
-      step(IC<8>{}, IC<1>{}); step(IC<8>{}, IC<8>{}); step(IC<8>{}, IC<64>{}); fin(IC<2>{});
-    } else {
-      static_assert(L == 16, "unsupported FFT length");
-    }
+              for (int l = 0; l < NLT; ++l) F::gather(v[l], lines[l], t);
+              sync();
+            }
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, P::np>{});
   }
 };
 

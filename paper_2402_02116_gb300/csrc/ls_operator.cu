@@ -46,8 +46,19 @@ template <typename C> struct OpP {
 // components of a row held by each thread. Column kernel: CC columns per CTA, thread (c, t) with c
 // fastest so that a warp reads CC adjacent columns of a row.
 template <typename C> struct Cfg;
-template <> struct Cfg<float2> { static constexpr int rowThreads = 256, colThreads = 256, colMinBlocks = 3; };
-template <> struct Cfg<double2> { static constexpr int rowThreads = 256, colThreads = 256, colMinBlocks = 1; };
+#ifndef DBI_COLS_MIN_BLOCKS
+#define DBI_COLS_MIN_BLOCKS 3
+#endif
+#ifndef DBI_ROWS_INV_MIN_BLOCKS
+#define DBI_ROWS_INV_MIN_BLOCKS 4
+#endif
+template <> struct Cfg<float2> {
+  static constexpr int rowThreads = 256, colThreads = 256;
+  static constexpr int colMinBlocks = DBI_COLS_MIN_BLOCKS, rowInvMinBlocks = DBI_ROWS_INV_MIN_BLOCKS;
+};
+template <> struct Cfg<double2> {
+  static constexpr int rowThreads = 256, colThreads = 256, colMinBlocks = 1, rowInvMinBlocks = 1;
+};
 
 template <typename C, int LX> struct RowCfg {
   static constexpr int T = LX / 8;
@@ -137,6 +148,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
   const size_t plane = size_t(nz) * nx;
   const C *u1 = p.in + size_t(b) * 2 * plane, *u3 = u1 + plane;
   const Rl isc = p.in_scale ? Rl(p.in_scale[b]) : Rl(1);
+  const TwReg<C, LX> tr(t, p.tw);
   C v[2][8];
 
   if constexpr (STENCIL) {
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_forward(OpP<C> p) {
     }
   }
   C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
-  RegPlan<LX>::template run<C, 2, false, true>(v, lines, t, p.tw, RowSync<T>{1 + rr});
+  RegPlan<LX>::template run<C, 2, false, true>(v, lines, t, tr, RowSync<T>{1 + rr});
   // transpose through shared memory: tile[c][kx][rr], then ROWS consecutive z per kx
   __syncthreads();
   constexpr int RP = ROWS + 1;
@@ -250,6 +262,7 @@ __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_col
   C *smem = reinterpret_cast<C *>(smem_raw);
   C *Tb = p.T + size_t(slot) * 2 * lx * nz;
   const C *c0 = Tb + size_t(kx) * nz, *c1 = Tb + (size_t(lx) + kx) * nz;
+  const TwReg<C, LZ> tr(t, p.tw);
   C v[2][8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_col
     v[1][m] = in ? c1[z] : czero<C>();
   }
   C *const lines[2] = {smem + size_t(col) * LP, smem + size_t(CC + col) * LP};
-  RegPlan<LZ>::template run<C, 2, false, true>(v, lines, t, p.tw, RowSync<T>{1 + col});
+  RegPlan<LZ>::template run<C, 2, false, true>(v, lines, t, tr, RowSync<T>{1 + col});
   if (live) {
     const size_t plane = size_t(lx) * LZ;
     const C *G = p.Ghat + size_t(p.fidx[b]) * 3 * plane + size_t(kx) * LZ;
@@ -272,7 +285,7 @@ __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_col
       v[1][m] = cadd(cmul(g13, s1), cmul(g33, s3));
     }
   }
-  RegPlan<LZ>::template run<C, 2, true>(v, lines, t, p.tw, RowSync<T>{1 + col});
+  RegPlan<LZ>::template run<C, 2, true>(v, lines, t, tr, RowSync<T>{1 + col});
   if (live) {
     C *o0 = Tb + size_t(kx) * nz, *o1 = Tb + (size_t(lx) + kx) * nz;
 #pragma unroll
@@ -289,7 +302,7 @@ __global__ void __launch_bounds__(ColCfg<C, LZ>::NT, Cfg<C>::colMinBlocks) k_col
 // Inverse FFT along x of ROWS rows, keep x < nx, out = ident - out_scale * result (or the scaled
 // result when there is no identity term).
 template <typename C, int LX, int EPI>
-__global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
+__global__ void __launch_bounds__(RowCfg<C, LX>::NT, Cfg<C>::rowInvMinBlocks) k_rows_inverse(OpP<C> p) {
   using Rl = typename RealOf<C>::type;
   using RC = RowCfg<C, LX>;
   constexpr int ROWS = RC::ROWS, T = RC::T, LP = RC::LP;
@@ -301,6 +314,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *smem = reinterpret_cast<C *>(smem_raw);
   const C *Tb = p.T + size_t(slot) * 2 * LX * nz;
+  const TwReg<C, LX> tr(t, p.tw);
   // ROWS consecutive z of every (c, kx) into tile[c][kx][r], then each thread takes its row
   constexpr int RP = ROWS + 1, NLD = 2 * LX * ROWS / RC::NT;
   static_assert((2 * LX * ROWS) % RC::NT == 0, "tile load");
@@ -325,7 +339,7 @@ __global__ void __launch_bounds__(RowCfg<C, LX>::NT) k_rows_inverse(OpP<C> p) {
     for (int m = 0; m < 8; ++m) v[c][m] = smem[(size_t(c) * LX + t + m * T) * RP + rr];
   __syncthreads();  // the FFT lines reuse the tile
   C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
-  RegPlan<LX>::template run<C, 2, true>(v, lines, t, p.tw, RowSync<T>{1 + rr});
+  RegPlan<LX>::template run<C, 2, true>(v, lines, t, tr, RowSync<T>{1 + rr});
   const Rl osc = p.out_scale ? Rl(p.out_scale[b]) : Rl(1);
   const size_t base = size_t(b) * 2 * nz * nx + size_t(z) * nx;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // per-thread partials of the fused inner products
