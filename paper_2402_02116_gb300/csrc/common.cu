@@ -31,6 +31,9 @@ int cuda_fail(const char *what, cudaError_t e) {
 
 static std::atomic<unsigned long long> g_launches{0};
 
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 int check_launch(const char *what) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaGetLastError();

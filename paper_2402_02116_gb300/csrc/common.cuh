@@ -60,6 +60,9 @@ void clear_error();
 int cuda_fail(const char *what, cudaError_t e);
 // Checks the last launch and counts it (every kernel launch is followed by exactly one call).
 int check_launch(const char *what);
+// The launch count, and n more launches made by replaying a captured graph.
+unsigned long long launch_count();
+void add_launches(unsigned long long n);
 
 // Event timing of one operator stage on its launching stream (see dbi_profile_begin).
 enum { PROF_NONE = 0, PROF_ROWS_FORWARD = 1, PROF_COLS = 2, PROF_ROWS_INVERSE = 3, PROF_OPERATOR = 4 };

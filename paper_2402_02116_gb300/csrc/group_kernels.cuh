@@ -1,0 +1,201 @@
+// Persistent kernels of the uneven-batch operator: each stage is one launch of `blocks` CTAs that
+// walk the stage's tile space (tile = blockIdx.x, + gridDim.x, ...). A tile belongs to one slot of
+// one member; the member is found by binary search over the members' first tiles, and the FFT
+// length and radix plan of the member select the tile body (op_tiles.cuh) inside the kernel.
+#pragma once
+
+#include "group.cuh"
+#include "op_tiles.cuh"
+
+namespace dbi {
+
+template <typename C> struct GroupP {
+  const GMember *desc;
+  int nm, total;
+  const C *in;
+  const C *ident;
+  C *out;
+  C *T;
+  const C *tw;
+  const int *active;
+  const double *in_scale, *m_scale, *out_scale;
+  const C *krhat;
+  double *part_out;
+  int parts;
+  signed char plan[11];
+};
+
+// Last member whose first tile of `stage` is <= tile (members are in tile order).
+__device__ __forceinline__ int find_member(const GMember *d, int nm, int stage, int tile) {
+  int lo = 0, hi = nm - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d[mid].tile0[stage] <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int ilog2(int L) { return 31 - __clz(L); }
+
+// Tile arguments of slot q of member M (global slot b, table f).
+template <typename C>
+__device__ __forceinline__ TileArgs<C> group_args(const GroupP<C> &g, const GMember &M, int b, int q, int f) {
+  using Rl = typename RealOf<C>::type;
+  TileArgs<C> a;
+  a.nz = M.nz; a.nx = M.nx; a.lz = M.lz; a.lx = M.lx;
+  a.inv2h = Rl(M.inv2h);
+  const double om = M.omega[f];
+  a.w2 = Rl(om * om);
+  a.isc = g.in_scale ? Rl(g.in_scale[b]) : Rl(1);
+  a.osc = g.out_scale ? Rl(g.out_scale[b]) : Rl(1);
+  a.ms = g.m_scale ? Rl(g.m_scale[0]) : Rl(1);
+  a.m = static_cast<const Rl *>(M.m);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) a.ref[i] = Rl(M.ref[i]);
+  const size_t fld = size_t(M.field0) + size_t(q) * 2 * M.nz * M.nx;
+  a.in = g.in + fld;
+  a.ident = g.ident ? g.ident + fld : nullptr;
+  a.out = g.out + fld;
+  a.T = g.T + size_t(M.T0) + size_t(q) * 2 * M.lx * M.nz;
+  a.G = static_cast<const C *>(M.Ghat) + size_t(f) * 3 * M.lx * M.lz;
+  a.tw = g.tw;
+  a.krhat = g.krhat ? g.krhat + fld : nullptr;
+  a.part = g.part_out ? g.part_out + size_t(b) * g.parts * kRedSlots : nullptr;
+  return a;
+}
+
+// Runs body(M, b, q, f, tt) for every tile of `stage` assigned to this CTA whose slot is active.
+template <int STAGE, typename C, typename Body>
+__device__ __forceinline__ void for_tiles(const GroupP<C> &g, Body &&body) {
+  for (int tile = blockIdx.x; tile < g.total; tile += gridDim.x) {
+    const int i = find_member(g.desc, g.nm, STAGE, tile);
+    const GMember &M = g.desc[i];
+    const int rel = tile - M.tile0[STAGE];
+    const int q = rel / M.tiles[STAGE], tt = rel - q * M.tiles[STAGE];
+    const int b = M.slot0 + q;
+    const int f = M.fidx[q];
+    if ((g.active && !g.active[b]) || unsigned(f) >= unsigned(M.nf)) continue;  // uniform per CTA
+    __syncthreads();  // the previous tile's shared-memory reads are complete
+    body(M, b, q, f, tt);
+  }
+}
+
+// One call per (length, plan) body: each body keeps its own register allocation inside the
+// persistent kernel (a tile is microseconds of work, so the call costs nothing measurable).
+template <typename C, int LX, bool STENCIL, int V>
+__device__ __noinline__ void call_rows_forward(const TileArgs<C> &a, int tt, C *smem) {
+  rows_forward_tile<C, LX, STENCIL, V>(a, tt, smem);
+}
+template <typename C, int LZ, int V>
+__device__ __noinline__ void call_cols(const TileArgs<C> &a, int tt, C *smem) {
+  cols_tile<C, LZ, V>(a, tt, smem);
+}
+template <typename C, int LX, int EPI, int V>
+__device__ __noinline__ void call_rows_inverse(const TileArgs<C> &a, int tt, C *smem) {
+  rows_inverse_tile<C, LX, EPI, V>(a, tt, smem);
+}
+
+template <typename C> struct GroupCfg;
+template <> struct GroupCfg<float2> { static constexpr int rowsMinBlocks = 3; };
+template <> struct GroupCfg<double2> { static constexpr int rowsMinBlocks = 1; };
+
+template <typename C, bool STENCIL>
+__global__ void __launch_bounds__(kTileThreads, GroupCfg<C>::rowsMinBlocks) kg_rows_forward(GroupP<C> g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageRowsForward>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    const TileArgs<C> a = group_args(g, M, b, q, f);
+    const int L = M.lx, v = g.plan[ilog2(L)];
+    with_len(L, [&]<int LX>() {
+      if constexpr (LX == 64 || LX == 512) call_rows_forward<C, LX, STENCIL, 0>(a, tt, smem);
+      else if (v) call_rows_forward<C, LX, STENCIL, 1>(a, tt, smem);
+      else call_rows_forward<C, LX, STENCIL, 0>(a, tt, smem);
+    });
+  });
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kTileThreads, Cfg<C>::colMinBlocks) kg_cols(GroupP<C> g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageCols>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    const TileArgs<C> a = group_args(g, M, b, q, f);
+    const int L = M.lz, v = g.plan[ilog2(L)];
+    with_len(L, [&]<int LZ>() {
+      if constexpr (LZ == 64 || LZ == 512) call_cols<C, LZ, 0>(a, tt, smem);
+      else if (v) call_cols<C, LZ, 1>(a, tt, smem);
+      else call_cols<C, LZ, 0>(a, tt, smem);
+    });
+  });
+}
+
+template <typename C, int EPI>
+__global__ void __launch_bounds__(kTileThreads, Cfg<C>::rowInvMinBlocks) kg_rows_inverse(GroupP<C> g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageRowsInverse>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    const TileArgs<C> a = group_args(g, M, b, q, f);
+    const int L = M.lx, v = g.plan[ilog2(L)];
+    with_len(L, [&]<int LX>() {
+      if constexpr (LX == 64 || LX == 512) call_rows_inverse<C, LX, EPI, 0>(a, tt, smem);
+      else if (v) call_rows_inverse<C, LX, EPI, 1>(a, tt, smem);
+      else call_rows_inverse<C, LX, EPI, 0>(a, tt, smem);
+    });
+  });
+}
+
+template <typename C> int run_group_typed(const OpArgs &a, cudaStream_t s) {
+  const GroupLaunch &gl = *a.group;
+  GroupP<C> g;
+  g.desc = gl.desc;
+  g.nm = gl.nm;
+  g.in = static_cast<const C *>(a.in);
+  g.ident = static_cast<const C *>(a.ident);
+  g.out = static_cast<C *>(a.out);
+  g.T = static_cast<C *>(a.T);
+  g.tw = static_cast<const C *>(a.tw);
+  g.active = a.active;
+  g.in_scale = a.in_scale;
+  g.m_scale = a.m_scale;
+  g.out_scale = a.out_scale;
+  g.krhat = static_cast<const C *>(a.krhat);
+  g.part_out = a.part_out;
+  g.parts = gl.parts;
+  for (int i = 0; i < 11; ++i) g.plan[i] = gl.plan[i];
+  auto launch = [&](auto kernel, int stage, size_t smem, const char *what) -> int {
+    g.total = gl.total[stage];
+    if (g.total == 0) return DBI_OK;
+    cudaError_t e = allow_smem(kernel, smem);
+    if (e != cudaSuccess) return cuda_fail(what, e);
+    const int blocks = std::max(1, std::min(gl.blocks[stage], g.total));
+    kernel<<<blocks, kTileThreads, smem, s>>>(g);
+    return check_launch(what);
+  };
+  int rc;
+  if (a.stencil) rc = launch(kg_rows_forward<C, true>, kStageRowsForward, gl.smem[0], "kg_rows_forward");
+  else rc = launch(kg_rows_forward<C, false>, kStageRowsForward, gl.smem[1], "kg_rows_forward");
+  if (rc) return rc;
+  if ((rc = launch(kg_cols<C>, kStageCols, gl.smem[2], "kg_cols"))) return rc;
+  if (a.epi == 1) rc = launch(kg_rows_inverse<C, 1>, kStageRowsInverse, gl.smem[3], "kg_rows_inverse");
+  else if (a.epi == 2) rc = launch(kg_rows_inverse<C, 2>, kStageRowsInverse, gl.smem[3], "kg_rows_inverse");
+  else rc = launch(kg_rows_inverse<C, 0>, kStageRowsInverse, gl.smem[3], "kg_rows_inverse");
+  return rc;
+}
+
+template <typename C> int group_occupancy(int stage, int epi, size_t smem, int *per_sm) {
+  cudaError_t e = cudaSuccess;
+  auto occ = [&](auto kernel) {
+    e = allow_smem(kernel, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, kTileThreads, smem);
+  };
+  if (stage == 0) occ(kg_rows_forward<C, true>);
+  else if (stage == 1) occ(kg_rows_forward<C, false>);
+  else if (stage == 2) occ(kg_cols<C>);
+  else if (epi == 1) occ(kg_rows_inverse<C, 1>);
+  else if (epi == 2) occ(kg_rows_inverse<C, 2>);
+  else occ(kg_rows_inverse<C, 0>);
+  return e == cudaSuccess ? DBI_OK : cuda_fail("cudaOccupancyMaxActiveBlocksPerMultiprocessor", e);
+}
+
+}  // namespace dbi

@@ -15,6 +15,7 @@
 // iterations. A breakdown (rho or omega vanishing) restarts the problem from its iterate.
 #include <cmath>
 
+#include "group.cuh"
 #include "krylov.cuh"
 #include "reduce.cuh"
 
@@ -40,18 +41,18 @@ template <typename C> __device__ __forceinline__ C from_z(double2 z) {
 // Problem of this CTA: plist[blockIdx.y] when the launch runs a compacted list of problems.
 __device__ __forceinline__ int problem_at(const int *plist, int slot) { return plist ? plist[slot] : slot; }
 
-#define DBI_PROBLEM_LOOP(n)                                                                   \
-  const size_t off = size_t(b) * (n);                                                         \
+#define DBI_PROBLEM_LOOP(sp)                                                                  \
+  const size_t off = (sp).offset(b), cnt = (sp).count(b);                                     \
   _Pragma("unroll 4")                                                                         \
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < (n); i += size_t(gridDim.x) * blockDim.x)
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt; i += size_t(gridDim.x) * blockDim.x)
 
 // ||rhs||^2 with every square formed in FP64: the right-hand side may lie far from unit scale
 // (a data residual of 1e-12 back-propagates to fields of 1e-21), where FP32 squares underflow.
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_bnorm(size_t n, const C *rhs, double *part) {
+__global__ void __launch_bounds__(kRedThreads) k_bnorm(Span sp, const C *rhs, double *part) {
   const int b = blockIdx.y;
   double bb = 0.0;
-  DBI_PROBLEM_LOOP(n) {
+  DBI_PROBLEM_LOOP(sp) {
     const C bi = rhs[off + i];
     const double x = bi.x, y = bi.y;
     bb += x * x + y * y;
@@ -70,16 +71,16 @@ __global__ void k_scale(KState *st, const double *part) {
 
 // x *= scale (inverse = 0) or x /= scale (inverse = 1)
 template <typename C>
-__global__ void k_scale_x(size_t n, const KState *st, C *x, int inverse) {
+__global__ void k_scale_x(Span sp, const KState *st, C *x, int inverse) {
   const int b = blockIdx.y;
   using R = typename RealOf<C>::type;
   const double sc = st[blockIdx.y].scale;
   const R f = R(inverse ? 1.0 / sc : sc);
-  DBI_PROBLEM_LOOP(n) x[off + i] = cscale(x[off + i], f);
+  DBI_PROBLEM_LOOP(sp) x[off + i] = cscale(x[off + i], f);
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_init(size_t n, const KState *st, const C *__restrict__ rhs,
+__global__ void __launch_bounds__(kRedThreads) k_init(Span sp, const KState *st, const C *__restrict__ rhs,
                                                       C *__restrict__ v, C *__restrict__ r,
                                                       C *__restrict__ rhat, C *__restrict__ p,
                                                       C *__restrict__ x, int x_zero, double *part) {
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kRedThreads) k_init(size_t n, const KState *st
   using R = typename RealOf<C>::type;
   const R sc = R(st[blockIdx.y].scale);
   A bb = 0, rr = 0;
-  DBI_PROBLEM_LOOP(n) {
+  DBI_PROBLEM_LOOP(sp) {
     const C bi = cscale(rhs[off + i], sc);
     const C ax = x_zero ? czero<C>() : v[off + i];
     const C ri = csub(bi, ax);
@@ -129,14 +130,14 @@ __global__ void k_init_state(KState *st, int *active, int *counters, const doubl
 }
 
 template <typename C>
-__global__ void k_zero_flagged(size_t n, const KState *st, C *x) {
+__global__ void k_zero_flagged(Span sp, const KState *st, C *x) {
   const int b = blockIdx.y;
   if (!st[blockIdx.y].zero_rhs) return;
-  DBI_PROBLEM_LOOP(n) x[off + i] = czero<C>();
+  DBI_PROBLEM_LOOP(sp) x[off + i] = czero<C>();
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const int *plist, const KState *st,
+__global__ void __launch_bounds__(kRedThreads) k_update_p(Span sp, const int *plist, const KState *st,
                                                           const int *active, int *counters, int parity,
                                                           const C *__restrict__ r, C *__restrict__ rhat,
                                                           C *__restrict__ p, const C *__restrict__ v) {
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const int *p
   if (!active[b]) return;
   const KState k = st[b];
   if (k.restart) {
-    DBI_PROBLEM_LOOP(n) {
+    DBI_PROBLEM_LOOP(sp) {
       const C ri = r[off + i];
       rhat[off + i] = ri;
       p[off + i] = ri;
@@ -154,14 +155,14 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(size_t n, const int *p
   }
   const C be = from_z<C>(make_double2(k.beta_re, k.beta_im));
   const C om = from_z<C>(make_double2(k.om_re, k.om_im));
-  DBI_PROBLEM_LOOP(n) {
+  DBI_PROBLEM_LOOP(sp) {
     const C pv = csub(p[off + i], cmul(om, v[off + i]));
     p[off + i] = cadd(r[off + i], cmul(be, pv));
   }
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, const int *plist, KState *st,
+__global__ void __launch_bounds__(kRedThreads) k_update_s(Span sp, const int *plist, KState *st,
                                                           const int *active, int nparts, const double *partA,
                                                           const C *__restrict__ r, const C *__restrict__ v,
                                                           C *__restrict__ s, double *partS) {
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, const int *p
   }
   const C al = from_z<C>(alpha);
   A ss = 0;
-  DBI_PROBLEM_LOOP(n) {
+  DBI_PROBLEM_LOOP(sp) {
     const C si = csub(r[off + i], cmul(al, v[off + i]));
     s[off + i] = si;
     ss += si.x * si.x + si.y * si.y;
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_s(size_t n, const int *p
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_update_xr(size_t n, const int *plist, KState *st,
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(Span sp, const int *plist, KState *st,
                                                            const int *active, int nparts,
                                                            const double *partB, const double *partS,
                                                            double tol, const C *__restrict__ p,
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(size_t n, const int *
   const C al = from_z<C>(make_double2(k.alpha_re, k.alpha_im));
   const C o = from_z<C>(om);
   A re = 0, im = 0, rr = 0;
-  DBI_PROBLEM_LOOP(n) {
+  DBI_PROBLEM_LOOP(sp) {
     const C si = s[off + i];
     x[off + i] = cadd(x[off + i], cadd(cmul(al, p[off + i]), cmul(o, si)));
     const C ri = csub(si, cmul(o, t[off + i]));
@@ -324,10 +325,10 @@ template <> __device__ __forceinline__ double sq64<float2>(float2 v) { return do
 template <> __device__ __forceinline__ double sq64<double2>(double2 v) { return v.x * v.x + v.y * v.y; }
 
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_sumsq(size_t n, const T *x, double *part) {
+__global__ void __launch_bounds__(kRedThreads) k_sumsq(Span sp, const T *x, double *part) {
   const int b = blockIdx.y;
   double acc = 0.0;
-  DBI_PROBLEM_LOOP(n) acc += sq64<T>(x[off + i]);
+  DBI_PROBLEM_LOOP(sp) acc += sq64<T>(x[off + i]);
   double a[1] = {acc};
   block_sum_store<1>(a, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
@@ -343,14 +344,15 @@ __global__ void k_pow2(const double *part, double *scale, double *inv, const dou
 }
 
 int pow2_scales(const void *x, int precision, bool real, int B, size_t n, double *part, double *scale,
-                double *inv, const double *extra, cudaStream_t s) {
+                double *inv, const double *extra, cudaStream_t s, const long long *offs) {
   const dim3 grid(kRedBlocks, B);
+  const Span sp{n, offs};
   if (precision == DBI_C64) {
-    if (real) k_sumsq<float><<<grid, kRedThreads, 0, s>>>(n, static_cast<const float *>(x), part);
-    else k_sumsq<float2><<<grid, kRedThreads, 0, s>>>(n, static_cast<const float2 *>(x), part);
+    if (real) k_sumsq<float><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const float *>(x), part);
+    else k_sumsq<float2><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const float2 *>(x), part);
   } else {
-    if (real) k_sumsq<double><<<grid, kRedThreads, 0, s>>>(n, static_cast<const double *>(x), part);
-    else k_sumsq<double2><<<grid, kRedThreads, 0, s>>>(n, static_cast<const double2 *>(x), part);
+    if (real) k_sumsq<double><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const double *>(x), part);
+    else k_sumsq<double2><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const double2 *>(x), part);
   }
   int rc;
   if ((rc = check_launch("k_sumsq"))) return rc;
@@ -358,14 +360,16 @@ int pow2_scales(const void *x, int precision, bool real, int B, size_t n, double
   return check_launch("k_pow2");
 }
 
+size_t bytes_solver_fields(size_t field_bytes, int B) {
+  return 6 * align256(field_bytes) + align256(size_t(B) * sizeof(KState)) + 2 * align256(size_t(B) * sizeof(int)) +
+         256 + 4 * bytes_partials(B);
+}
 size_t bytes_solver(const dbi_grid *g, int B, int precision) {
-  return 6 * bytes_field(g, B, precision) + align256(size_t(B) * sizeof(KState)) +
-         2 * align256(size_t(B) * sizeof(int)) + 256 + 4 * bytes_partials(B);
+  return bytes_solver_fields(bytes_field(g, B, precision), B);
 }
 
-SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision) {
+SolverBufs carve_solver_fields(Arena &ar, size_t f, int B) {
   SolverBufs sb{};
-  const size_t f = bytes_field(g, B, precision);
   sb.r = ar.take(f); sb.rhat = ar.take(f); sb.p = ar.take(f);
   sb.v = ar.take(f); sb.s = ar.take(f); sb.t = ar.take(f);
   sb.st = static_cast<KState *>(ar.take(size_t(B) * sizeof(KState)));
@@ -378,6 +382,9 @@ SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision) {
   sb.partC = static_cast<double *>(ar.take(bytes_partials(B)));
   return sb;
 }
+SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision) {
+  return carve_solver_fields(ar, bytes_field(g, B, precision), B);
+}
 
 static int read_counter(const int *dev, cudaStream_t s, int *host) {
   cudaError_t e = cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -385,78 +392,135 @@ static int read_counter(const int *dev, cudaStream_t s, int *host) {
   return e == cudaSuccess ? DBI_OK : cuda_fail("reading the active-problem counter", e);
 }
 
+// Owns a capture stream, a captured graph and its executable instance.
+struct GraphChunk {
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~GraphChunk() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
 template <typename C>
 static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, void *x_, bool x_zero,
-                          const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s, bool unscale) {
+                          const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s, bool unscale,
+                          bool use_graph) {
   const int B = op.B;
   if (B == 0) return DBI_OK;
-  const size_t n = size_t(2) * op.nz * op.nx;
+  const bool group = op.group != nullptr;
+  const Span sp{group ? 0 : size_t(2) * op.nz * op.nx, op.offs};
   const C *rhs = static_cast<const C *>(rhs_);
   C *x = static_cast<C *>(x_);
   C *r = static_cast<C *>(sb.r), *rhat = static_cast<C *>(sb.rhat), *p = static_cast<C *>(sb.p);
   C *v = static_cast<C *>(sb.v), *sv = static_cast<C *>(sb.s), *t = static_cast<C *>(sb.t);
   const dim3 grid(kRedBlocks, B);
   int rc;
-  cudaError_t e = cudaMemsetAsync(sb.counters, 0, 2 * sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(sb.counters, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(counters)", e);
+  const int nparts = group ? group_parts(op.group) : operator_parts(op.nz, op.lx, op.precision);
   op.stencil = true;
   op.active = nullptr;
-  k_bnorm<C><<<grid, kRedThreads, 0, s>>>(n, rhs, sb.partA);
+  k_bnorm<C><<<grid, kRedThreads, 0, s>>>(sp, rhs, sb.partA);
   if ((rc = check_launch("k_bnorm"))) return rc;
   k_scale<<<B, 32, 0, s>>>(sb.st, sb.partA);
   if ((rc = check_launch("k_scale"))) return rc;
   if (!x_zero) {  // x0 into the scaled system, v = A x0
-    k_scale_x<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x, 0);
+    k_scale_x<C><<<grid, kRedThreads, 0, s>>>(sp, sb.st, x, 0);
     if ((rc = check_launch("k_scale_x"))) return rc;
     op.in = x; op.ident = x; op.out = v;
     if ((rc = run_operator(op, s))) return rc;
   }
-  k_init<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, rhs, v, r, rhat, p, x, x_zero ? 1 : 0, sb.partA);
+  k_init<C><<<grid, kRedThreads, 0, s>>>(sp, sb.st, rhs, v, r, rhat, p, x, x_zero ? 1 : 0, sb.partA);
   if ((rc = check_launch("k_init"))) return rc;
   k_init_state<<<B, 32, 0, s>>>(sb.st, sb.active, sb.counters, sb.partA, o.tol, o.max_iter);
   if ((rc = check_launch("k_init_state"))) return rc;
   if (!x_zero) {
-    k_zero_flagged<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x);
+    k_zero_flagged<C><<<grid, kRedThreads, 0, s>>>(sp, sb.st, x);
     if ((rc = check_launch("k_zero_flagged"))) return rc;
   }
-  // Launches run over the problems still active: at every host check the active problems are
-  // compacted into sb.plist (ascending order) and the grids shrink to them.
-  int nact = B;
+  // Batches on one grid run their launches over the problems still active: at every host check
+  // the active problems are compacted into sb.plist (ascending order) and the grids shrink to them.
+  // Uneven batches keep every problem in the launches (finished ones return at once).
+  int nact = B;   // problems still active (read back at host checks)
+  int nrun = B;   // launch slots: the compacted active problems, or every problem of an uneven batch
   const int *plist = nullptr;
   auto compact = [&]() -> int {
     k_compact<<<1, 1024, 0, s>>>(B, sb.active, sb.plist, sb.counters + 2);
-    int e = check_launch("k_compact");
-    if (e == DBI_OK) e = read_counter(sb.counters + 2, s, &nact);
+    int e2 = check_launch("k_compact");
+    if (e2 == DBI_OK) e2 = read_counter(sb.counters + 2, s, &nact);
     plist = sb.plist;
-    return e;
+    nrun = nact;
+    return e2;
   };
-  if (o.check_every > 0 && (rc = compact())) return rc;
+  if (!group && o.check_every > 0 && (rc = compact())) return rc;
   op.active = sb.active;
   op.krhat = rhat;
-  const int nparts = operator_parts(op.nz, op.lx, op.precision);
-  for (int it = 0; it < o.max_iter && nact > 0; ++it) {
+  if (group) {  // members write only their own row tiles of the fused-reduction partials: zero the rest
+    e = cudaMemsetAsync(sb.partA, 0, bytes_partials(B), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sb.partB, 0, bytes_partials(B), s);
+    if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(partials)", e);
+  }
+  // One BiCGSTAB iteration of every active problem on stream `st`.
+  auto iterate = [&](int it, cudaStream_t st) -> int {
     const int parity = it & 1;
-    const dim3 g2(kRedBlocks, nact);
+    const dim3 g2(kRedBlocks, nrun);
+    int rc2;
     op.plist = plist;
-    op.nb = nact;
-    k_update_p<C><<<g2, kRedThreads, 0, s>>>(n, plist, sb.st, sb.active, sb.counters, parity, r, rhat, p, v);
-    if ((rc = check_launch("k_update_p"))) return rc;
+    op.nb = nrun;
+    k_update_p<C><<<g2, kRedThreads, 0, st>>>(sp, plist, sb.st, sb.active, sb.counters, parity, r, rhat, p, v);
+    if ((rc2 = check_launch("k_update_p"))) return rc2;
     op.epi = 1; op.in = p; op.ident = p; op.out = v; op.part_out = sb.partA;
-    if ((rc = run_operator(op, s))) return rc;
-    k_update_s<C><<<g2, kRedThreads, 0, s>>>(n, plist, sb.st, sb.active, nparts, sb.partA, r, v, sv, sb.partS);
-    if ((rc = check_launch("k_update_s"))) return rc;
+    if ((rc2 = run_operator(op, st))) return rc2;
+    k_update_s<C><<<g2, kRedThreads, 0, st>>>(sp, plist, sb.st, sb.active, nparts, sb.partA, r, v, sv, sb.partS);
+    if ((rc2 = check_launch("k_update_s"))) return rc2;
     op.epi = 2; op.in = sv; op.ident = sv; op.out = t; op.part_out = sb.partB;
-    if ((rc = run_operator(op, s))) return rc;
-    k_update_xr<C><<<g2, kRedThreads, 0, s>>>(n, plist, sb.st, sb.active, nparts, sb.partB, sb.partS, o.tol,
-                                               p, sv, t, rhat, x, r, sb.partC);
-    if ((rc = check_launch("k_update_xr"))) return rc;
-    k_check<<<nact, 32, 0, s>>>(plist, sb.st, sb.active, sb.counters, parity, sb.partC, o.tol, o.max_iter);
-    if ((rc = check_launch("k_check"))) return rc;
-    if (o.check_every > 0 && ((it + 1) % o.check_every == 0) && (rc = compact())) return rc;
+    if ((rc2 = run_operator(op, st))) return rc2;
+    k_update_xr<C><<<g2, kRedThreads, 0, st>>>(sp, plist, sb.st, sb.active, nparts, sb.partB, sb.partS, o.tol,
+                                                p, sv, t, rhat, x, r, sb.partC);
+    if ((rc2 = check_launch("k_update_xr"))) return rc2;
+    k_check<<<nrun, 32, 0, st>>>(plist, sb.st, sb.active, sb.counters, parity, sb.partC, o.tol, o.max_iter);
+    return check_launch("k_check");
+  };
+  const int K = o.check_every;
+  if (group && use_graph && K > 0) {
+    // Capture K iterations once (on a capture stream of our own: the caller's stream may be the
+    // legacy default stream, which cannot be captured) and replay the graph on the caller's
+    // stream until every problem has stopped; the host reads the active count between replays.
+    GraphChunk gc;
+    if ((e = cudaStreamCreateWithFlags(&gc.cs, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail("cudaStreamCreateWithFlags", e);
+    if ((e = cudaStreamBeginCapture(gc.cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail("cudaStreamBeginCapture", e);
+    int crc = DBI_OK;
+    const unsigned long long before = launch_count();
+    for (int k = 0; k < K && crc == DBI_OK; ++k) crc = iterate(k, gc.cs);
+    const unsigned long long captured = launch_count() - before;  // kernels per replay
+    e = cudaStreamEndCapture(gc.cs, &gc.graph);
+    if (crc) return crc;
+    if (e != cudaSuccess) return cuda_fail("cudaStreamEndCapture", e);
+    if ((e = cudaGraphInstantiate(&gc.exec, gc.graph, 0)) != cudaSuccess) return cuda_fail("cudaGraphInstantiate", e);
+    add_launches(0 - captured);  // capturing launched nothing; every replay below launches them
+    for (int it = 0; it < o.max_iter && nact > 0; it += K) {
+      if ((e = cudaGraphLaunch(gc.exec, s)) != cudaSuccess) return cuda_fail("cudaGraphLaunch", e);
+      add_launches(captured);
+      if ((rc = read_counter(sb.counters + ((K - 1) & 1), s, &nact))) return rc;
+    }
+  } else {
+    for (int it = 0; it < o.max_iter && nact > 0; ++it) {
+      if ((rc = iterate(it, s))) return rc;
+      if (K > 0 && ((it + 1) % K == 0)) {
+        if (!group) rc = compact();
+        else rc = read_counter(sb.counters + (it & 1), s, &nact);
+        if (rc) return rc;
+      }
+    }
   }
   op.plist = nullptr;
   if (unscale) {
-    k_scale_x<C><<<grid, kRedThreads, 0, s>>>(n, sb.st, x, 1);
+    k_scale_x<C><<<grid, kRedThreads, 0, s>>>(sp, sb.st, x, 1);
     if ((rc = check_launch("k_scale_x"))) return rc;
   }
   if (status) {
@@ -467,9 +531,10 @@ static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, voi
 }
 
 int run_bicgstab(OpArgs op, const SolverBufs &sb, const void *rhs, void *x, bool x_zero,
-                 const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s, bool unscale) {
-  return op.precision == DBI_C64 ? bicgstab_typed<float2>(op, sb, rhs, x, x_zero, o, status, s, unscale)
-                                 : bicgstab_typed<double2>(op, sb, rhs, x, x_zero, o, status, s, unscale);
+                 const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s, bool unscale,
+                 bool use_graph) {
+  return op.precision == DBI_C64 ? bicgstab_typed<float2>(op, sb, rhs, x, x_zero, o, status, s, unscale, use_graph)
+                                 : bicgstab_typed<double2>(op, sb, rhs, x, x_zero, o, status, s, unscale, use_graph);
 }
 
 int check_krylov(const dbi_krylov_opts *o) {

@@ -28,12 +28,21 @@ struct SolverBufs {
 
 size_t bytes_solver(const dbi_grid *g, int B, int precision);
 SolverBufs carve_solver(Arena &ar, const dbi_grid *g, int B, int precision);
+// The same for fields of field_bytes bytes in all (uneven batches).
+size_t bytes_solver_fields(size_t field_bytes, int B);
+SolverBufs carve_solver_fields(Arena &ar, size_t field_bytes, int B);
 
 // Solves A x = rhs for every problem of `op` (op.in / op.out / op.ident are set internally).
 // x_zero: the initial guess is zero (x is overwritten without being read). The iteration runs on
 // rhs scaled by a power of two per problem (KState::scale, ||scaled rhs|| in [1, 2)); with
 // unscale = false the returned x stays in that scaled system (x = scale * A^{-1} rhs).
+// Validates Krylov options (tol >= 0, max_iter >= 0, check_every >= 0).
+int check_krylov(const dbi_krylov_opts *o);
+
+// use_graph (uneven batches only): the iterations between two host checks are captured once as
+// a CUDA graph and replayed.
 int run_bicgstab(OpArgs op, const SolverBufs &sb, const void *rhs, void *x, bool x_zero,
-                 const dbi_krylov_opts &opts, const dbi_status *status, cudaStream_t s, bool unscale);
+                 const dbi_krylov_opts &opts, const dbi_status *status, cudaStream_t s, bool unscale,
+                 bool use_graph = false);
 
 }  // namespace dbi

@@ -5,6 +5,20 @@
 
 namespace dbi {
 
+// Per-problem extent of a batched array: problem b holds elements [offset(b), offset(b) +
+// count(b)). A batch on one grid has n elements per problem; an uneven batch passes prefix
+// offsets offs[B + 1] (device memory).
+struct Span {
+  size_t n;
+  const long long *offs;
+  __host__ __device__ __forceinline__ size_t offset(int b) const { return offs ? size_t(offs[b]) : size_t(b) * n; }
+  __host__ __device__ __forceinline__ size_t count(int b) const {
+    return offs ? size_t(offs[b + 1] - offs[b]) : n;
+  }
+};
+
+struct GroupLaunch;  // launch description of an uneven batch (group.cuh)
+
 // One batched pass  out = ident - K(src)  or  out = K(src), where K(src) = h^2 G * src and src
 // is either the contrast source w^2 drho u + div(dC : eps(u)) of `in` (stencil = true) or `in`
 // itself (stencil = false).
@@ -38,6 +52,10 @@ struct OpArgs {
   int epi;
   const void *krhat;
   double *part_out;
+  // Uneven batch: problems on different grids (nz, nx, lz, lx, m, Ghat, omega, ref above are then
+  // unused and come from the group's member descriptors). offs: field offsets per problem.
+  const GroupLaunch *group;
+  const long long *offs;
 };
 
 // Partials per problem written by the operator kernels (one per CTA row block).
@@ -45,9 +63,10 @@ int operator_parts(int nz, int lx, int precision);
 
 int run_operator(const OpArgs &a, cudaStream_t s);
 
-// Per-problem power-of-two normalisers of B arrays of n elements each (complex of the precision,
-// or real when `real` is set): scale[b] = 2^-e with ||x_b|| in [2^e, 2^(e+1)), 1 for a zero array.
-// If inv is non-NULL, inv[b] = 1 / (scale[b] * (extra ? extra[0] : 1)). part: bytes_partials(B).
+// Per-problem power-of-two normalisers of B arrays of n elements each (or of the extents offs
+// gives, when non-NULL; complex of the precision, or real when `real` is set): scale[b] = 2^-e with
+// ||x_b|| in [2^e, 2^(e+1)), 1 for a zero array. If inv is non-NULL, inv[b] = 1 / (scale[b] *
+// (extra ? extra[0] : 1)). part: bytes_partials(B).
 struct Scales {
   double *scale, *inv, *aux, *mscale, *part;
 };
@@ -62,7 +81,7 @@ inline Scales carve_scales(Arena &ar, int B) {
 }
 
 int pow2_scales(const void *x, int precision, bool real, int B, size_t n, double *part, double *scale,
-                double *inv, const double *extra, cudaStream_t s);
+                double *inv, const double *extra, cudaStream_t s, const long long *offs = nullptr);
 
 // Reference values (rho, C11, C13, C33, C55) of the isotropic medium (Eq. 4, Eq. 39).
 inline void reference_values(const dbi_medium &r, double out[5]) {

@@ -16,7 +16,6 @@
 
 namespace dbi {
 
-int check_krylov(const dbi_krylov_opts *o);
 
 // ----------------------------------------------------------------------------------------------
 // receivers

@@ -60,7 +60,19 @@ class CGOpts(ctypes.Structure):
     _fields_ = [("iters", c_int), ("lam", c_double), ("lambda_rel", c_double), ("power_iters", c_int)]
 
 
-# (name, restype, argtypes) of every entry point declared in include/dbi.h
+class GroupMember(ctypes.Structure):
+    _fields_ = [("model", Model), ("Ghat", c_void_p), ("omega", c_void_p), ("nf", c_int), ("B", c_int),
+                ("fidx", c_void_p)]
+
+
+class GroupTuning(ctypes.Structure):
+    _fields_ = [("lengths", c_int * 7), ("plan", c_int * 7), ("plan_ms", (c_double * 2) * 7),
+                ("ctas_per_sm", c_int * 3), ("max_ctas", c_int * 3), ("apply_ms", c_double)]
+
+
+GROUP_GRAPH = 1
+
+# (name, restype, argtypes) of every entry point declared in include/dbi.h and include/dbi_group.h
 SIGNATURES = {
     "dbi_last_error": (ctypes.c_char_p, []),
     "dbi_version": (c_int, []),
@@ -78,6 +90,18 @@ SIGNATURES = {
                          c_size_t, c_void_p]),
     "ls_apply_noalloc": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "dbi_noalloc_scratch_bytes": (c_size_t, []),
+    "dbi_group_create": (c_int, [POINTER(GroupMember), c_int, c_int, POINTER(c_void_p)]),
+    "dbi_group_destroy": (None, [c_void_p]),
+    "dbi_group_slots": (c_int, [c_void_p]),
+    "dbi_group_field_elems": (ctypes.c_longlong, [c_void_p]),
+    "dbi_group_offsets": (c_int, [c_void_p, POINTER(ctypes.c_longlong)]),
+    "dbi_group_workspace_bytes": (c_size_t, [c_void_p, c_int]),
+    "dbi_group_bind": (c_int, [c_void_p, c_void_p, c_size_t, c_int, c_void_p]),
+    "ls_apply_group": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ls_solve_group": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts), POINTER(Status), c_int,
+                               c_void_p]),
+    "dbi_group_tune": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(GroupTuning)]),
+    "dbi_set_radix_plan": (c_int, [c_int, c_int, c_int]),
     "ls_solve": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
                          POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
     "frechet_apply": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, POINTER(Receivers),
@@ -207,6 +231,12 @@ def _status(B, device):
 
 
 PROF_ROWS_FORWARD, PROF_COLS, PROF_ROWS_INVERSE, PROF_OPERATOR = 1, 2, 3, 4
+
+
+def set_radix_plan(precision: int, L: int, plan: int):
+    """Radix plan (0: radix-8 passes first, 1: the smaller radix first) of FFT length L for the
+    single-grid entry points."""
+    _check(load().dbi_set_radix_plan(int(precision), int(L), int(plan)), "dbi_set_radix_plan")
 
 
 def kernel_launches() -> int:

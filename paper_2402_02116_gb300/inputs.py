@@ -229,6 +229,42 @@ def config4_misfit(n=512, n_src=64, nf=6, seed=4) -> Workload:
         krylov_tol=1e-6, seed=seed)
 
 
+def config5_uneven(sizes=(64, 128, 256, 384, 512), n_members=40, max_src=32, max_f=8, f_range=(2.0, 25.0),
+                   h=5.0, seed=5) -> list:
+    """Uneven batch: n_members independent problems, each with a square grid drawn from `sizes`,
+    1..max_src surface sources, 1..max_f frequencies drawn in f_range (sorted), an isotropic
+    (rho 2000, alpha 2000, beta 1155) or VTI background (as config 2) and 1-4 Gaussian anomalies
+    (sigma N/32 .. N/8 cells) of +/-15 % with a random sign per parameter. The FFT grid of each is
+    the smallest power of two >= 2N - 1 (384 cells -> 1024)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_members):
+        n = int(rng.choice(sizes))
+        n_src = int(rng.integers(1, max_src + 1))
+        nf = int(rng.integers(1, max_f + 1))
+        freqs = np.sort(rng.uniform(f_range[0], f_range[1], nf))
+        vti = bool(rng.integers(0, 2))
+        if vti:
+            m_bg = vti_background(n, n)
+            rho0, a0, b0 = isotropic_reference_for(m_bg)
+        else:
+            rho0, a0, b0 = 2000.0, 2000.0, 1155.0
+            m_bg = isotropic_model(n, n, rho0, a0, b0)
+        count = int(rng.integers(1, 5))
+        pert = _random_anomalies(rng, n, n, count, 0.15, (n / 32.0, n / 8.0))
+        model = m_bg * (1.0 + np.clip(pert, -0.15, 0.15))
+        cols = surface_line(n, n_src)
+        L = fft_len(n)
+        out.append(Workload(
+            name=f"{'vti' if vti else 'iso'}{n}x{n}_{n_src}src_{nf}f", nz=n, nx=n, h=h, lz=L, lx=L,
+            rho0=rho0, alpha0=a0, beta0=b0, model=model, freqs_hz=freqs,
+            src_cells=np.stack([np.zeros_like(cols), cols], axis=1),
+            src_force=np.tile([0.0, 1.0], (n_src, 1)),
+            rec_cells=np.array([[0, j] for j in range(0, n, 2)]),
+            krylov_tol=1e-5, seed=seed))
+    return out
+
+
 def fft_len(n: int) -> int:
     """Smallest power of two >= max(16, 2n - 1): an FFT length that holds every offset of n cells."""
     p = 16

@@ -9,13 +9,17 @@ import pytest
 from paper_2402_02116_gb300 import build, dbi
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "dbi.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^(?:const\s+char\s*\*|int|size_t)\s*\**\s*(\w+)\s*\(", text, flags=re.M)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"^(?:const\s+char\s*\*|unsigned\s+long\s+long|long\s+long|int|size_t|void)"
+                                r"\s*\**\s*(\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +31,9 @@ def lib():
 def test_header_declares_the_paper_entry_points():
     names = declared_functions()
     for want in ("greens_tabulate", "ls_apply", "ls_solve", "frechet_apply", "adjoint_apply", "normal_cg",
-                 "incident_field", "green_convolve", "data_residual", "dbi_workspace_bytes", "dbi_last_error"):
+                 "incident_field", "green_convolve", "data_residual", "dbi_workspace_bytes", "dbi_last_error",
+                 "dbi_kernel_launches", "ls_apply_group", "ls_solve_group", "dbi_group_create", "dbi_group_tune",
+                 "dbi_group_destroy"):
         assert want in names
 
 

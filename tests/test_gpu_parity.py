@@ -351,3 +351,22 @@ def test_config3_linear_dbi_step():
     r0 = float(torch.linalg.norm(dd.to(torch.complex128)))
     r1 = float(torch.linalg.norm((dd - pred).to(torch.complex128)))
     assert r1 < 0.5 * r0, (r1 / r0)
+
+
+@pytest.mark.parametrize("L", [16, 32, 128, 256, 1024])
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_second_radix_plan_matches_oracle(L, precision):
+    """The radix order with the smaller radix first (plan 1) gives the same operator."""
+    n = min(L // 2, 24)
+    w = inputs.small_case(nz=n, nx=max(1, n - 3), lz=L, lx=L, vti=True, n_src=2, freqs=(9.0,), seed=L)
+    P = DeviceProblem(w, precision)
+    u = torch.as_tensor(inputs.seeded_complex((P.B, 2, w.nz, w.nx), L + 1)).to(P.device, P.cdt)
+    orc = oracle_for(w)
+    try:
+        dbi.set_radix_plan(precision, L, 1)
+        out = npy(P.apply(u))
+    finally:
+        dbi.set_radix_plan(precision, L, 0)
+    for b in range(P.B):
+        want = orc.apply(npy(u[b]).astype(np.complex128), w.model, 0)
+        assert rel(out[b], want) < TOL[precision], b

@@ -1,0 +1,94 @@
+"""Host-side plan of an uneven batch (include/dbi_group.h): slot and field offsets, workspace
+sizes and argument checks. The plan is built on the host from member descriptors; the device
+pointers are only stored, so placeholder addresses suffice and no GPU is needed."""
+import ctypes
+
+import pytest
+
+from paper_2402_02116_gb300 import build, dbi
+
+FAKE = 0x100000  # placeholder device address (never dereferenced by the planner)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return dbi.load()
+
+
+def member(nz, nx, lz, lx, B, nf=2, h=5.0):
+    m = dbi.GroupMember()
+    m.model.grid = dbi.make_grid(nz, nx, lz, lx, h)
+    m.model.ref = dbi.make_medium(2000.0, 2000.0, 1155.0)
+    m.model.m = FAKE
+    m.Ghat, m.omega, m.fidx = FAKE, FAKE, FAKE
+    m.nf, m.B = nf, B
+    return m
+
+
+def make(lib, specs, precision=dbi.C64):
+    arr = (dbi.GroupMember * len(specs))(*[member(*s) for s in specs])
+    h = ctypes.c_void_p()
+    rc = lib.dbi_group_create(arr, len(specs), precision, ctypes.byref(h))
+    return rc, h
+
+
+def test_offsets_follow_the_members_in_order(lib):
+    specs = [(64, 64, 128, 128, 3), (20, 12, 64, 32, 2), (256, 256, 512, 512, 1), (8, 8, 16, 16, 4)]
+    rc, h = make(lib, specs)
+    assert rc == 0
+    try:
+        slots = sum(s[4] for s in specs)
+        assert lib.dbi_group_slots(h) == slots
+        want = [0]
+        for nz, nx, _, _, B in specs:
+            for _ in range(B):
+                want.append(want[-1] + 2 * nz * nx)
+        assert lib.dbi_group_field_elems(h) == want[-1]
+        offs = (ctypes.c_longlong * (slots + 1))()
+        assert lib.dbi_group_offsets(h, offs) == 0
+        assert list(offs) == want
+        apply_b = lib.dbi_group_workspace_bytes(h, dbi.OP_APPLY)
+        solve_b = lib.dbi_group_workspace_bytes(h, dbi.OP_SOLVE)
+        spectra = sum(2 * B * lx * nz * 8 for nz, nx, lz, lx, B in specs)
+        assert apply_b >= spectra and solve_b >= apply_b + 6 * want[-1] * 8
+        assert lib.dbi_group_workspace_bytes(h, dbi.OP_FRECHET) == 0
+    finally:
+        lib.dbi_group_destroy(h)
+
+
+def test_complex128_plan_needs_more_workspace(lib):
+    specs = [(32, 32, 64, 64, 2), (16, 16, 32, 32, 1)]
+    _, h64 = make(lib, specs, dbi.C64)
+    _, h128 = make(lib, specs, dbi.C128)
+    try:
+        assert lib.dbi_group_workspace_bytes(h128, dbi.OP_SOLVE) > lib.dbi_group_workspace_bytes(h64, dbi.OP_SOLVE)
+    finally:
+        lib.dbi_group_destroy(h64)
+        lib.dbi_group_destroy(h128)
+
+
+def test_bad_members_are_rejected(lib):
+    for specs, code, text in (([(32, 32, 48, 64, 1)], -2, b"power of two"),
+                              ([(40, 32, 64, 64, 1)], -1, b"too small"),
+                              ([(32, 32, 64, 64, 0)], -1, b"B >= 1")):
+        rc, h = make(lib, specs)
+        assert rc == code and not h.value, specs
+        assert text in lib.dbi_last_error()
+    h = ctypes.c_void_p()
+    assert lib.dbi_group_create(None, 0, dbi.C64, ctypes.byref(h)) == -1
+    m = (dbi.GroupMember * 1)(member(8, 8, 16, 16, 1))
+    m[0].Ghat = None
+    assert lib.dbi_group_create(m, 1, dbi.C64, ctypes.byref(h)) == -1
+
+
+def test_unbound_plan_refuses_work(lib):
+    rc, h = make(lib, [(8, 8, 16, 16, 1)])
+    try:
+        assert lib.ls_apply_group(h, FAKE, FAKE * 2, None) == -3
+        assert b"not bound" in lib.dbi_last_error()
+        opts = dbi.KrylovOpts(1e-6, 10, 2, 1)
+        assert lib.ls_solve_group(h, FAKE, FAKE * 2, ctypes.byref(opts), None, 1, None) == -3
+        assert lib.dbi_set_radix_plan(dbi.C64, 48, 1) == -1
+    finally:
+        lib.dbi_group_destroy(h)
