@@ -43,25 +43,23 @@ template <typename C>
 __device__ __forceinline__ TileArgs<C> group_args(const GroupP<C> &g, const GMember &M, int b, int q, int f) {
   using Rl = typename RealOf<C>::type;
   TileArgs<C> a;
-  a.nz = M.nz; a.nx = M.nx; a.lz = M.lz; a.lx = M.lx;
-  a.inv2h = Rl(M.inv2h);
-  const double om = M.omega[f];
-  a.w2 = Rl(om * om);
-  a.isc = g.in_scale ? Rl(g.in_scale[b]) : Rl(1);
-  a.osc = g.out_scale ? Rl(g.out_scale[b]) : Rl(1);
-  a.ms = g.m_scale ? Rl(g.m_scale[0]) : Rl(1);
-  a.m = static_cast<const Rl *>(M.m);
+  a.nz_ = M.nz; a.nx_ = M.nx; a.lz_ = M.lz; a.lx_ = M.lx;
+  a.inv2h_ = Rl(M.inv2h);
+  a.b_ = b; a.f_ = f;
+  a.omega_ = M.omega;
+  a.in_scale_ = g.in_scale; a.out_scale_ = g.out_scale; a.m_scale_ = g.m_scale;
+  a.m_ = static_cast<const Rl *>(M.m);
 #pragma unroll
-  for (int i = 0; i < 5; ++i) a.ref[i] = Rl(M.ref[i]);
+  for (int i = 0; i < 5; ++i) a.ref_[i] = Rl(M.ref[i]);
   const size_t fld = size_t(M.field0) + size_t(q) * 2 * M.nz * M.nx;
-  a.in = g.in + fld;
-  a.ident = g.ident ? g.ident + fld : nullptr;
-  a.out = g.out + fld;
-  a.T = g.T + size_t(M.T0) + size_t(q) * 2 * M.lx * M.nz;
-  a.G = static_cast<const C *>(M.Ghat) + size_t(f) * 3 * M.lx * M.lz;
-  a.tw = g.tw;
-  a.krhat = g.krhat ? g.krhat + fld : nullptr;
-  a.part = g.part_out ? g.part_out + size_t(b) * g.parts * kRedSlots : nullptr;
+  a.in_ = g.in + fld;
+  a.ident_ = g.ident ? g.ident + fld : nullptr;
+  a.out_ = g.out + fld;
+  a.T_ = g.T + size_t(M.T0) + size_t(q) * 2 * M.lx * M.nz;
+  a.G_ = static_cast<const C *>(M.Ghat) + size_t(f) * 3 * M.lx * M.lz;
+  a.tw_ = g.tw;
+  a.krhat_ = g.krhat ? g.krhat + fld : nullptr;
+  a.part_ = g.part_out ? g.part_out + size_t(b) * g.parts * kRedSlots : nullptr;
   return a;
 }
 

@@ -43,38 +43,45 @@ template <typename C> __device__ __forceinline__ int problem_of(const OpP<C> &p)
   return p.plist ? p.plist[sl] : sl;
 }
 
-// The tile arguments of problem b in launch slot `slot`.
-template <typename C> __device__ __forceinline__ TileArgs<C> tile_args(const OpP<C> &p, int b, int slot, int f) {
+// Tile accessor of problem b in launch slot `slot`: every value is read from the kernel's
+// parameters where the tile body uses it (kernel parameters live in constant memory, so they cost
+// no registers until then; a reference to the parameter would force generic loads through its
+// address instead).
+template <typename C> struct BatchTile {
   using Rl = typename RealOf<C>::type;
-  TileArgs<C> a;
-  a.nz = p.nz; a.nx = p.nx; a.lz = p.lz; a.lx = p.lx;
-  a.inv2h = p.inv2h;
-  const double om = p.omega[f];
-  a.w2 = Rl(om * om);
-  a.isc = p.in_scale ? Rl(p.in_scale[b]) : Rl(1);
-  a.osc = p.out_scale ? Rl(p.out_scale[b]) : Rl(1);
-  a.ms = p.m_scale ? Rl(p.m_scale[0]) : Rl(1);
-  a.m = p.m;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) a.ref[i] = p.ref[i];
-  const size_t fld = size_t(b) * 2 * p.nz * p.nx;
-  a.in = p.in + fld;
-  a.ident = p.ident ? p.ident + fld : nullptr;
-  a.out = p.out + fld;
-  a.T = p.T + size_t(slot) * 2 * p.lx * p.nz;
-  a.G = p.Ghat + size_t(f) * 3 * p.lx * p.lz;
-  a.tw = p.tw;
-  a.krhat = p.krhat ? p.krhat + fld : nullptr;
-  a.part = p.part_out ? p.part_out + size_t(b) * p.part_count * kRedSlots : nullptr;
-  return a;
-}
+  OpP<C> p;  // a copy of the kernel parameter: its fields stay parameter reads (no address taken)
+  int b, slot, f;
+  __device__ __forceinline__ size_t fld() const { return size_t(b) * 2 * p.nz * p.nx; }
+  __device__ __forceinline__ int nz() const { return p.nz; }
+  __device__ __forceinline__ int nx() const { return p.nx; }
+  __device__ __forceinline__ int lx() const { return p.lx; }
+  __device__ __forceinline__ Rl inv2h() const { return p.inv2h; }
+  __device__ __forceinline__ Rl ref(int i) const { return p.ref[i]; }
+  __device__ __forceinline__ const Rl *m() const { return p.m; }
+  __device__ __forceinline__ const C *in() const { return p.in + fld(); }
+  __device__ __forceinline__ const C *ident() const { return p.ident ? p.ident + fld() : nullptr; }
+  __device__ __forceinline__ C *out() const { return p.out + fld(); }
+  __device__ __forceinline__ C *T() const { return p.T + size_t(slot) * 2 * p.lx * p.nz; }
+  __device__ __forceinline__ const C *G() const { return p.Ghat + size_t(f) * 3 * p.lx * p.lz; }
+  __device__ __forceinline__ const C *tw() const { return p.tw; }
+  __device__ __forceinline__ const C *krhat() const { return p.krhat + fld(); }
+  __device__ __forceinline__ double *part() const { return p.part_out + size_t(b) * p.part_count * kRedSlots; }
+  __device__ __forceinline__ Rl w2() const {
+    const double om = p.omega[f];
+    return Rl(om * om);
+  }
+  __device__ __forceinline__ Rl isc() const { return p.in_scale ? Rl(p.in_scale[b]) : Rl(1); }
+  __device__ __forceinline__ Rl osc() const { return p.out_scale ? Rl(p.out_scale[b]) : Rl(1); }
+  __device__ __forceinline__ Rl ms() const { return p.m_scale ? Rl(p.m_scale[0]) : Rl(1); }
+};
 
 template <typename C, int LX, bool STENCIL, int V>
 __global__ void __launch_bounds__(kTileThreads) k_rows_forward(OpP<C> p) {
   const int b = problem_of(p), f = p.fidx[b];
   if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  rows_forward_tile<C, LX, STENCIL, V>(tile_args(p, b, blockIdx.y, f), blockIdx.x, reinterpret_cast<C *>(smem_raw));
+  rows_forward_tile<C, LX, STENCIL, V>(BatchTile<C>{p, b, int(blockIdx.y), f}, blockIdx.x,
+                                       reinterpret_cast<C *>(smem_raw));
 }
 
 template <typename C, int LZ, int V>
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(kTileThreads, Cfg<C>::colMinBlocks) k_cols(OpP
   const int b = problem_of(p), f = p.fidx[b];
   if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cols_tile<C, LZ, V>(tile_args(p, b, blockIdx.y, f), blockIdx.x, reinterpret_cast<C *>(smem_raw));
+  cols_tile<C, LZ, V>(BatchTile<C>{p, b, int(blockIdx.y), f}, blockIdx.x, reinterpret_cast<C *>(smem_raw));
 }
 
 template <typename C, int LX, int EPI, int V>
@@ -90,7 +97,8 @@ __global__ void __launch_bounds__(kTileThreads, Cfg<C>::rowInvMinBlocks) k_rows_
   const int b = problem_of(p), f = p.fidx[b];
   if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  rows_inverse_tile<C, LX, EPI, V>(tile_args(p, b, blockIdx.y, f), blockIdx.x, reinterpret_cast<C *>(smem_raw));
+  rows_inverse_tile<C, LX, EPI, V>(BatchTile<C>{p, b, int(blockIdx.y), f}, blockIdx.x,
+                                   reinterpret_cast<C *>(smem_raw));
 }
 
 // Calls f.template operator()<V>() with the radix plan chosen for length L (plans differ only

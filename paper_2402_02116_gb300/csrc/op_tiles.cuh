@@ -89,45 +89,72 @@ template <int T> struct RowSync {
 };
 
 // Everything a tile needs about its problem (one (source, frequency) wavefield on one grid).
+// The tile bodies read it through an accessor with the member functions below: TileArgs holds the
+// values (the persistent kernels build one per tile); the batched kernels of one grid use an
+// accessor that reads its kernel parameters where they are used (ls_operator.cu).
 template <typename C> struct TileArgs {
   using Rl = typename RealOf<C>::type;
-  int nz, nx, lz, lx;
-  Rl inv2h;
-  Rl w2;             // omega^2 of the problem's frequency
-  Rl isc, osc, ms;   // input, output and contrast power-of-two scales
-  const Rl *m;       // [5][nz][nx] model or perturbation
-  Rl ref[5];         // subtracted from m
-  const C *in;       // [2][nz][nx] this problem's input
-  const C *ident;    // [2][nz][nx] identity term or NULL
-  C *out;            // [2][nz][nx]
-  C *T;              // [2][lx][nz] this problem's column-major spectra
-  const C *G;        // [3][lx][lz] Ghat of the problem's frequency (column-major)
-  const C *tw;       // twiddle table
-  const C *krhat;    // [2][nz][nx] shadow residual (EPI 1)
-  double *part;      // [row tiles][kRedSlots] fused inner-product partials (EPI 1, 2)
+  int nz_, nx_, lz_, lx_;
+  Rl inv2h_;
+  int b_, f_;                  // the problem (scale index) and its frequency
+  const double *omega_;        // [nf] angular frequencies
+  const double *in_scale_;     // [B] power-of-two input scales or NULL (1)
+  const double *out_scale_;    // [B] output scales or NULL (1)
+  const double *m_scale_;      // [1] contrast scale or NULL (1)
+  const Rl *m_;                // [5][nz][nx] model or perturbation
+  Rl ref_[5];                  // subtracted from m
+  const C *in_;                // [2][nz][nx] this problem's input
+  const C *ident_;             // [2][nz][nx] identity term or NULL
+  C *out_;                     // [2][nz][nx]
+  C *T_;                       // [2][lx][nz] this problem's column-major spectra
+  const C *G_;                 // [3][lx][lz] Ghat of the problem's frequency (column-major)
+  const C *tw_;                // twiddle table
+  const C *krhat_;             // [2][nz][nx] shadow residual (EPI 1)
+  double *part_;               // [row tiles][kRedSlots] fused inner-product partials (EPI 1, 2)
+  __device__ __forceinline__ int nz() const { return nz_; }
+  __device__ __forceinline__ int nx() const { return nx_; }
+  __device__ __forceinline__ int lx() const { return lx_; }
+  __device__ __forceinline__ Rl inv2h() const { return inv2h_; }
+  __device__ __forceinline__ Rl ref(int i) const { return ref_[i]; }
+  __device__ __forceinline__ const Rl *m() const { return m_; }
+  __device__ __forceinline__ const C *in() const { return in_; }
+  __device__ __forceinline__ const C *ident() const { return ident_; }
+  __device__ __forceinline__ C *out() const { return out_; }
+  __device__ __forceinline__ C *T() const { return T_; }
+  __device__ __forceinline__ const C *G() const { return G_; }
+  __device__ __forceinline__ const C *tw() const { return tw_; }
+  __device__ __forceinline__ const C *krhat() const { return krhat_; }
+  __device__ __forceinline__ double *part() const { return part_; }
+  __device__ __forceinline__ Rl w2() const {
+    const double om = omega_[f_];
+    return Rl(om * om);
+  }
+  __device__ __forceinline__ Rl isc() const { return in_scale_ ? Rl(in_scale_[b_]) : Rl(1); }
+  __device__ __forceinline__ Rl osc() const { return out_scale_ ? Rl(out_scale_[b_]) : Rl(1); }
+  __device__ __forceinline__ Rl ms() const { return m_scale_ ? Rl(m_scale_[0]) : Rl(1); }
 };
 
 // Stress sigma = dC eps at cell (z, x) of D (zero outside D), from the staged u (rows z0 - 2 ..
 // z0 + ROWS + 1 with a zero column on each side; u already multiplied by its input scale).
-template <typename C>
-__device__ __forceinline__ void stress_at(const TileArgs<C> &a, const C *su, int RS, int W, int z0, int z,
-                                          int x, C &s1, C &s3, C &s5) {
+template <typename C, typename A>
+__device__ __forceinline__ void stress_at(const A &a, const C *su, int RS, int W, int z0, int z,
+                                          int x, typename RealOf<C>::type ms, C &s1, C &s3, C &s5) {
   using Rl = typename RealOf<C>::type;
-  const int nz = a.nz, nx = a.nx;
+  const int nz = a.nz(), nx = a.nx();
   if (z < 0 || z >= nz || x < 0 || x >= nx) {
     s1 = s3 = s5 = czero<C>();
     return;
   }
   auto U = [&](int c, int zz, int xx) { return su[(c * RS + (zz - z0 + 2)) * W + xx + 1]; };
-  const Rl f = a.inv2h;
+  const Rl f = a.inv2h();
   const C e1 = cscale(csub(U(0, z, x + 1), U(0, z, x - 1)), f);
   const C e3 = cscale(csub(U(1, z + 1, x), U(1, z - 1, x)), f);
   const C e5 = cscale(cadd(csub(U(0, z + 1, x), U(0, z - 1, x)), csub(U(1, z, x + 1), U(1, z, x - 1))), f);
   const size_t cell = size_t(z) * nx + x, plane = size_t(nz) * nx;
-  const Rl d11 = (__ldg(a.m + 1 * plane + cell) - a.ref[1]) * a.ms;
-  const Rl d13 = (__ldg(a.m + 2 * plane + cell) - a.ref[2]) * a.ms;
-  const Rl d33 = (__ldg(a.m + 3 * plane + cell) - a.ref[3]) * a.ms;
-  const Rl d55 = (__ldg(a.m + 4 * plane + cell) - a.ref[4]) * a.ms;
+  const Rl d11 = (__ldg(a.m() + 1 * plane + cell) - a.ref(1)) * ms;
+  const Rl d13 = (__ldg(a.m() + 2 * plane + cell) - a.ref(2)) * ms;
+  const Rl d33 = (__ldg(a.m() + 3 * plane + cell) - a.ref(3)) * ms;
+  const Rl d55 = (__ldg(a.m() + 4 * plane + cell) - a.ref(4)) * ms;
   s1 = cadd(cscale(e1, d11), cscale(e3, d13));
   s3 = cadd(cscale(e1, d13), cscale(e3, d33));
   s5 = cscale(e5, d55);
@@ -136,18 +163,18 @@ __device__ __forceinline__ void stress_at(const TileArgs<C> &a, const C *su, int
 // Contrast source (or the raw source) of ROWS rows, zero-padded to LX, forward FFT along x.
 //   stencil: stress of rows z0-1 .. z0+ROWS (each computed once, kept in shared memory), then
 //            s1 = w^2 drho u1 + d1 sigma1 + d3 sigma5, s3 = w^2 drho u3 + d1 sigma5 + d3 sigma3.
-template <typename C, int LX, bool STENCIL, int V>
-__device__ __forceinline__ void rows_forward_tile(const TileArgs<C> &a, int tile, C *smem) {
+template <typename C, int LX, bool STENCIL, int V, typename A>
+__device__ __forceinline__ void rows_forward_tile(const A &a, int tile, C *smem) {
   using Rl = typename RealOf<C>::type;
   using RC = RowCfg<C, LX>;
   constexpr int ROWS = RC::ROWS, T = RC::T, LP = RC::LP;
   const int z0 = tile * ROWS;
-  const int nz = a.nz, nx = a.nx;
+  const int nz = a.nz(), nx = a.nx();
   const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
   const size_t plane = size_t(nz) * nx;
-  const C *u1 = a.in, *u3 = u1 + plane;
-  const Rl isc = a.isc;
-  const TwReg<C, LX, V> tr(t, a.tw);
+  const C *u1 = a.in(), *u3 = u1 + plane;
+  const Rl isc = a.isc();
+  const TwReg<C, LX, V> tr(t, a.tw());
   C v[2][8];
 
   if constexpr (STENCIL) {
@@ -180,6 +207,7 @@ __device__ __forceinline__ void rows_forward_tile(const TileArgs<C> &a, int tile
       }
     }
     __syncthreads();
+    const Rl ms = a.ms();
 #pragma unroll UR
     for (int r2 = 0; r2 < ROWS + 2; ++r2) {
       const int zz = z0 - 1 + r2;
@@ -188,7 +216,7 @@ __device__ __forceinline__ void rows_forward_tile(const TileArgs<C> &a, int tile
         const int xx = int(threadIdx.x) - 1 + k * RC::NT;
         if (xx <= nx) {
           C a1, a3, a5;
-          stress_at(a, su, RS, W, z0, zz, xx, a1, a3, a5);
+          stress_at(a, su, RS, W, z0, zz, xx, ms, a1, a3, a5);
           sg[(0 * (ROWS + 2) + r2) * W + xx + 1] = a1;
           sg[(1 * (ROWS + 2) + r2) * W + xx + 1] = a3;
           sg[(2 * (ROWS + 2) + r2) * W + xx + 1] = a5;
@@ -196,6 +224,7 @@ __device__ __forceinline__ void rows_forward_tile(const TileArgs<C> &a, int tile
       }
     }
     __syncthreads();
+    const Rl w2 = a.w2();
     auto S = [&](int c, int r2, int xx) { return sg[(c * (ROWS + 2) + r2) * W + xx + 1]; };
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -205,10 +234,10 @@ __device__ __forceinline__ void rows_forward_tile(const TileArgs<C> &a, int tile
         const int r2 = rr + 1;
         o1 = cadd(csub(S(0, r2, x + 1), S(0, r2, x - 1)), csub(S(2, r2 + 1, x), S(2, r2 - 1, x)));
         o3 = cadd(csub(S(2, r2, x + 1), S(2, r2, x - 1)), csub(S(1, r2 + 1, x), S(1, r2 - 1, x)));
-        o1 = cscale(o1, a.inv2h);
-        o3 = cscale(o3, a.inv2h);
+        o1 = cscale(o1, a.inv2h());
+        o3 = cscale(o3, a.inv2h());
         const size_t cell = size_t(z) * nx + x;
-        const Rl wr = a.w2 * (__ldg(a.m + cell) - a.ref[0]) * a.ms;
+        const Rl wr = w2 * (__ldg(a.m() + cell) - a.ref(0)) * ms;
         o1 = cadd(o1, cscale(su[(0 * RS + rr + 2) * W + x + 1], wr));
         o3 = cadd(o3, cscale(su[(1 * RS + rr + 2) * W + x + 1], wr));
       }
@@ -237,23 +266,23 @@ __device__ __forceinline__ void rows_forward_tile(const TileArgs<C> &a, int tile
   __syncthreads();
   for (int idx = threadIdx.x; idx < 2 * LX * ROWS; idx += RC::NT) {
     const int r = idx % ROWS, ck = idx / ROWS;  // ck = c * LX + kx
-    if (z0 + r < nz) a.T[size_t(ck) * nz + z0 + r] = smem[size_t(ck) * RP + r];
+    if (z0 + r < nz) a.T()[size_t(ck) * nz + z0 + r] = smem[size_t(ck) * RP + r];
   }
 }
 
 // For CC columns kx: forward FFT along z of the nz non-zero rows padded to LZ, 2x2 multiply by
 // Ghat(kz, kx), inverse FFT along z, keep z < nz. Thread (col, t), t fastest: a warp reads a
 // contiguous run of one column; the T threads of a column share a barrier.
-template <typename C, int LZ, int V>
-__device__ __forceinline__ void cols_tile(const TileArgs<C> &a, int tile, C *smem) {
+template <typename C, int LZ, int V, typename A>
+__device__ __forceinline__ void cols_tile(const A &a, int tile, C *smem) {
   using CF = ColCfg<C, LZ>;
   constexpr int CC = CF::CC, T = CF::T, LP = CF::LP;
   const int col = threadIdx.x / T, t = threadIdx.x - col * T;
   const int kx = tile * CC + col;
-  const int nz = a.nz, lx = a.lx;
+  const int nz = a.nz(), lx = a.lx();
   const bool live = kx < lx;
-  const C *c0 = a.T + size_t(kx) * nz, *c1 = a.T + (size_t(lx) + kx) * nz;
-  const TwReg<C, LZ, V> tr(t, a.tw);
+  const C *c0 = a.T() + size_t(kx) * nz, *c1 = a.T() + (size_t(lx) + kx) * nz;
+  const TwReg<C, LZ, V> tr(t, a.tw());
   C v[2][8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
@@ -266,7 +295,7 @@ __device__ __forceinline__ void cols_tile(const TileArgs<C> &a, int tile, C *sme
   RegPlan<LZ, V>::template run<C, 2, false, true>(v, lines, t, tr, RowSync<T>{1 + col});
   if (live) {
     const size_t plane = size_t(lx) * LZ;
-    const C *G = a.G + size_t(kx) * LZ;
+    const C *G = a.G() + size_t(kx) * LZ;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int kz = t + m * T;
@@ -278,7 +307,7 @@ __device__ __forceinline__ void cols_tile(const TileArgs<C> &a, int tile, C *sme
   }
   RegPlan<LZ, V>::template run<C, 2, true>(v, lines, t, tr, RowSync<T>{1 + col});
   if (live) {
-    C *o0 = a.T + size_t(kx) * nz, *o1 = a.T + (size_t(lx) + kx) * nz;
+    C *o0 = a.T() + size_t(kx) * nz, *o1 = a.T() + (size_t(lx) + kx) * nz;
 #pragma unroll
     for (int m = 0; m < kHalf; ++m) {
       const int z = t + m * T;
@@ -292,15 +321,15 @@ __device__ __forceinline__ void cols_tile(const TileArgs<C> &a, int tile, C *sme
 
 // Inverse FFT along x of ROWS rows, keep x < nx, out = ident - osc * result (or the scaled
 // result when there is no identity term).
-template <typename C, int LX, int EPI, int V>
-__device__ __forceinline__ void rows_inverse_tile(const TileArgs<C> &a, int tile, C *smem) {
+template <typename C, int LX, int EPI, int V, typename A>
+__device__ __forceinline__ void rows_inverse_tile(const A &a, int tile, C *smem) {
   using Rl = typename RealOf<C>::type;
   using RC = RowCfg<C, LX>;
   constexpr int ROWS = RC::ROWS, T = RC::T, LP = RC::LP;
   const int z0 = tile * ROWS;
-  const int nz = a.nz, nx = a.nx;
+  const int nz = a.nz(), nx = a.nx();
   const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
-  const TwReg<C, LX, V> tr(t, a.tw);
+  const TwReg<C, LX, V> tr(t, a.tw());
   // ROWS consecutive z of every (c, kx) into tile[c][kx][r], then each thread takes its row
   constexpr int RP = ROWS + 1, NLD = 2 * LX * ROWS / RC::NT;
   static_assert((2 * LX * ROWS) % RC::NT == 0, "tile load");
@@ -309,7 +338,7 @@ __device__ __forceinline__ void rows_inverse_tile(const TileArgs<C> &a, int tile
 #pragma unroll
     for (int i = 0; i < NLD; ++i) {  // all loads in flight before the shared-memory stores
       const int idx = threadIdx.x + i * RC::NT, r = idx % ROWS, ck = idx / ROWS;
-      ld[i] = z0 + r < nz ? a.T[size_t(ck) * nz + z0 + r] : czero<C>();
+      ld[i] = z0 + r < nz ? a.T()[size_t(ck) * nz + z0 + r] : czero<C>();
     }
 #pragma unroll
     for (int i = 0; i < NLD; ++i) {
@@ -326,7 +355,7 @@ __device__ __forceinline__ void rows_inverse_tile(const TileArgs<C> &a, int tile
   __syncthreads();  // the FFT lines reuse the tile
   C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
   RegPlan<LX, V>::template run<C, 2, true>(v, lines, t, tr, RowSync<T>{1 + rr});
-  const Rl osc = a.osc;
+  const Rl osc = a.osc();
   const size_t base = size_t(z) * nx;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // per-thread partials of the fused inner products
   if (z < nz) {
@@ -338,8 +367,8 @@ __device__ __forceinline__ void rows_inverse_tile(const TileArgs<C> &a, int tile
       for (int m = 0; m < kHalf; ++m) {
         const int x = t + m * T;
         const size_t o = base + size_t(c) * nz * nx + x;
-        id[m] = (a.ident && x < nx) ? __ldg(a.ident + o) : czero<C>();
-        if constexpr (EPI == 1) h[m] = x < nx ? __ldg(a.krhat + o) : czero<C>();
+        id[m] = (a.ident() && x < nx) ? __ldg(a.ident() + o) : czero<C>();
+        if constexpr (EPI == 1) h[m] = x < nx ? __ldg(a.krhat() + o) : czero<C>();
       }
 #pragma unroll
       for (int m = 0; m < kHalf; ++m) {
@@ -347,8 +376,8 @@ __device__ __forceinline__ void rows_inverse_tile(const TileArgs<C> &a, int tile
         if (x < nx) {
           const size_t o = base + size_t(c) * nz * nx + x;
           const C r = cscale(v[c][m], osc);
-          const C w = a.ident ? csub(id[m], r) : r;
-          a.out[o] = w;
+          const C w = a.ident() ? csub(id[m], r) : r;
+          a.out()[o] = w;
           if constexpr (EPI == 1) {  // conj(rhat) w
             a0 += float(h[m].x) * float(w.x) + float(h[m].y) * float(w.y);
             a1 += float(h[m].x) * float(w.y) - float(h[m].y) * float(w.x);
@@ -363,10 +392,10 @@ __device__ __forceinline__ void rows_inverse_tile(const TileArgs<C> &a, int tile
   }
   if constexpr (EPI == 1) {
     double acc[2] = {double(a0), double(a1)};
-    block_sum_store<2>(acc, a.part + size_t(tile) * kRedSlots);
+    block_sum_store<2>(acc, a.part() + size_t(tile) * kRedSlots);
   } else if constexpr (EPI == 2) {
     double acc[3] = {double(a0), double(a1), double(a2)};
-    block_sum_store<3>(acc, a.part + size_t(tile) * kRedSlots);
+    block_sum_store<3>(acc, a.part() + size_t(tile) * kRedSlots);
   }
 }
 
