@@ -45,6 +45,8 @@ SHAPES = [
     dict(nz=1, nx=8),                    # one row
     dict(nz=40, nx=24, vti=True),        # several row tiles, VTI background
     dict(nz=64, nx=64, lz=128, lx=128),  # several column tiles
+    dict(nz=21, nx=30, lz=64, lx=512, vti=True),  # 512-long rows (one thread per column), ragged
+    dict(nz=9, nx=256, lz=32, lx=512),   # 512-long rows at full width (nx = 256)
 ]
 
 
