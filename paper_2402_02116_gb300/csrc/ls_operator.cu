@@ -76,7 +76,7 @@ template <typename C> struct BatchTile {
 };
 
 template <typename C, int LX, bool STENCIL, int V>
-__global__ void __launch_bounds__(kTileThreads) k_rows_forward(OpP<C> p) {
+__global__ void __launch_bounds__(kTileThreads, Cfg<C>::rowFwdMinBlocks(LX)) k_rows_forward(OpP<C> p) {
   const int b = problem_of(p), f = p.fidx[b];
   if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -28,12 +28,19 @@ template <typename C> struct Cfg;
 #ifndef DBI_ROWS_INV_MIN_BLOCKS
 #define DBI_ROWS_INV_MIN_BLOCKS 4
 #endif
+#ifndef DBI_ROWS_FWD_MIN_BLOCKS
+#define DBI_ROWS_FWD_MIN_BLOCKS 4
+#endif
 template <> struct Cfg<float2> {
   static constexpr int threads = 256;
   static constexpr int colMinBlocks = DBI_COLS_MIN_BLOCKS, rowInvMinBlocks = DBI_ROWS_INV_MIN_BLOCKS;
+  // rows forward: 4 CTAs per SM up to L = 512 (64 registers); L = 1024 tiles need 99 KB of shared
+  // memory, so only 2 fit and the registers are left free
+  static constexpr int rowFwdMinBlocks(int L) { return L >= 1024 ? 2 : DBI_ROWS_FWD_MIN_BLOCKS; }
 };
 template <> struct Cfg<double2> {
   static constexpr int threads = 256, colMinBlocks = 1, rowInvMinBlocks = 1;
+  static constexpr int rowFwdMinBlocks(int) { return 2; }
 };
 constexpr int kTileThreads = 256;
 
@@ -60,7 +67,10 @@ template <typename C, int LX> constexpr size_t tile_elems() {
 }
 
 // Lengths whose stencil uses the strip form (one column per thread, few rows per tile).
-template <int LX> constexpr bool kStripStencil = LX == 512;
+#ifndef DBI_STRIP_256
+#define DBI_STRIP_256 0  // at L = 256 the strip needs 150 registers and loses to the shared-memory form
+#endif
+template <int LX> constexpr bool kStripStencil = LX == 512 || (LX == 256 && DBI_STRIP_256);
 
 // Shared memory of the strip stencil (bytes): u at ROWS + 2 rows, sigma1 and sigma5 at ROWS rows.
 template <typename C, int LX> inline size_t stencil_strip_smem(int nx) {
