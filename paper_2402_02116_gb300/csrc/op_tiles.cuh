@@ -70,7 +70,12 @@ template <typename C, int LX> constexpr size_t tile_elems() {
 #ifndef DBI_STRIP_256
 #define DBI_STRIP_256 0  // at L = 256 the strip needs 150 registers and loses to the shared-memory form
 #endif
-template <int LX> constexpr bool kStripStencil = LX == 512 || (LX == 256 && DBI_STRIP_256);
+#ifndef DBI_STRIP_1024
+#define DBI_STRIP_1024 1
+#endif
+template <typename C, int LX>
+constexpr bool kStripStencil = LX == 512 || (LX == 1024 && DBI_STRIP_1024 && sizeof(C) == 8) ||
+                               (LX == 256 && DBI_STRIP_256);  // complex128 at 1024 would spill
 
 // Shared memory of the strip stencil (bytes): u at ROWS + 2 rows, sigma1 and sigma5 at ROWS rows.
 template <typename C, int LX> inline size_t stencil_strip_smem(int nx) {
@@ -85,7 +90,7 @@ template <typename C, int LX> inline size_t rows_forward_smem(int nx, bool stenc
   const size_t tile = tile_elems<C, LX>() * sizeof(C);
   size_t sg = 0;
   if (stencil) {
-    if constexpr (kStripStencil<LX>) sg = stencil_strip_smem<C, LX>(nx);
+    if constexpr (kStripStencil<C, LX>) sg = stencil_strip_smem<C, LX>(nx);
     else sg = (size_t(3) * (RC::ROWS + 2) + size_t(2) * (RC::ROWS + 4)) * (nx + 2) * sizeof(C);
   }
   return std::max(std::max(lines, tile), sg);
@@ -183,39 +188,46 @@ __device__ __forceinline__ void stress_at(const A &a, const C *su, int RS, int W
   s5 = cscale(e5, d55);
 }
 
-// Contrast source of the tile's ROWS rows with one thread per column x (the "strip" form, for
-// lengths whose tiles have few rows): the thread keeps its column's u and stress in registers
+// Contrast source of the tile's ROWS rows with KC = L/512 columns per thread (the "strip" form,
+// for lengths whose tiles have few rows): the thread keeps its columns' u and stress in registers
 // along z, so only the x-neighbours go through shared memory (u at the stress rows, sigma1 and
 // sigma5 at the output rows); the sources then pass through shared memory once more into the FFT
-// layout v[c][m] = s_c(z0 + rr, t + m L/8). Needs nx <= blockDim.x (one column per thread).
+// layout v[c][m] = s_c(z0 + rr, t + m L/8). Columns x = threadIdx.x + k blockDim.x, k < KC.
 template <typename C, int LX, typename A>
 __device__ __forceinline__ void stencil_strip(const A &a, int z0, C *smem, C (&v)[2][8]) {
   using Rl = typename RealOf<C>::type;
   using RC = RowCfg<C, LX>;
   constexpr int ROWS = RC::ROWS, T = RC::T, RS = ROWS + 4, RG = ROWS + 2;
+  constexpr int KC = (LX / 2 + kTileThreads - 1) / kTileThreads;  // nx <= L/2 columns
   const int nz = a.nz(), nx = a.nx(), W = nx + 2;
-  const int x = threadIdx.x;  // this thread's column
-  const bool col = x < nx;
   const size_t plane = size_t(nz) * nx;
   const C *u1 = a.in(), *u3 = u1 + plane;
   C *su = smem;                               // [2][RG][W]: u at the stress rows z0 - 1 .. z0 + ROWS
   C *sg = smem + size_t(2) * RG * W;          // [2][ROWS][W]: sigma1, sigma5 at the output rows
   C *so = smem;                               // [2][ROWS][nx]: the sources (reuses su)
-  // u of the column at rows z0 - 2 .. z0 + ROWS + 1 (zero outside D), scaled
+  // u of the columns at rows z0 - 2 .. z0 + ROWS + 1 (zero outside D), scaled
   const Rl isc = a.isc();
-  C U1[RS], U3[RS];
+  C U1[KC][RS], U3[KC][RS];
 #pragma unroll
-  for (int r = 0; r < RS; ++r) {
-    const int zz = z0 - 2 + r;
-    const bool in = col && zz >= 0 && zz < nz;
-    U1[r] = in ? cscale(__ldg(u1 + size_t(zz) * nx + x), isc) : czero<C>();
-    U3[r] = in ? cscale(__ldg(u3 + size_t(zz) * nx + x), isc) : czero<C>();
+  for (int k = 0; k < KC; ++k) {
+    const int x = threadIdx.x + k * kTileThreads;
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+      const int zz = z0 - 2 + r;
+      const bool in = x < nx && zz >= 0 && zz < nz;
+      U1[k][r] = in ? cscale(__ldg(u1 + size_t(zz) * nx + x), isc) : czero<C>();
+      U3[k][r] = in ? cscale(__ldg(u3 + size_t(zz) * nx + x), isc) : czero<C>();
+    }
   }
 #pragma unroll
-  for (int r = 0; r < RG; ++r) {
-    if (col) {
-      su[(0 * RG + r) * W + x + 1] = U1[r + 1];
-      su[(1 * RG + r) * W + x + 1] = U3[r + 1];
+  for (int k = 0; k < KC; ++k) {
+    const int x = threadIdx.x + k * kTileThreads;
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+      if (x < nx) {
+        su[(0 * RG + r) * W + x + 1] = U1[k][r + 1];
+        su[(1 * RG + r) * W + x + 1] = U3[k][r + 1];
+      }
     }
   }
   if (threadIdx.x < 2 * RG) {  // the zero columns x = -1 and x = nx of every staged row
@@ -230,47 +242,55 @@ __device__ __forceinline__ void stencil_strip(const A &a, int z0, C *smem, C (&v
   // stress at rows z0 - 1 .. z0 + ROWS (zero outside D): sigma3, sigma5 kept in registers for the
   // z-derivatives, sigma1 and sigma5 of the output rows stored for the x-derivatives
   const Rl f = a.inv2h(), ms = a.ms();
-  C S3[RG], S5[RG];
+  C S3[KC][RG], S5[KC][RG];
 #pragma unroll
-  for (int r = 0; r < RG; ++r) {
-    const int zz = z0 - 1 + r;
-    C s1 = czero<C>(), s3 = czero<C>(), s5 = czero<C>();
-    if (col && zz >= 0 && zz < nz) {
-      const C *r1 = su + (0 * RG + r) * W + x + 1, *r3 = su + (1 * RG + r) * W + x + 1;
-      const C e1 = cscale(csub(r1[1], r1[-1]), f);
-      const C e3 = cscale(csub(U3[r + 2], U3[r]), f);
-      const C e5 = cscale(cadd(csub(U1[r + 2], U1[r]), csub(r3[1], r3[-1])), f);
-      const size_t cell = size_t(zz) * nx + x;
-      const Rl d11 = (__ldg(a.m() + 1 * plane + cell) - a.ref(1)) * ms;
-      const Rl d13 = (__ldg(a.m() + 2 * plane + cell) - a.ref(2)) * ms;
-      const Rl d33 = (__ldg(a.m() + 3 * plane + cell) - a.ref(3)) * ms;
-      const Rl d55 = (__ldg(a.m() + 4 * plane + cell) - a.ref(4)) * ms;
-      s1 = cadd(cscale(e1, d11), cscale(e3, d13));
-      s3 = cadd(cscale(e1, d13), cscale(e3, d33));
-      s5 = cscale(e5, d55);
-    }
-    S3[r] = s3;
-    S5[r] = s5;
-    if (r >= 1 && r <= ROWS && col) {
-      sg[(0 * ROWS + r - 1) * W + x + 1] = s1;
-      sg[(1 * ROWS + r - 1) * W + x + 1] = s5;
+  for (int k = 0; k < KC; ++k) {
+    const int x = threadIdx.x + k * kTileThreads;
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+      const int zz = z0 - 1 + r;
+      C s1 = czero<C>(), s3 = czero<C>(), s5 = czero<C>();
+      if (x < nx && zz >= 0 && zz < nz) {
+        const C *r1 = su + (0 * RG + r) * W + x + 1, *r3 = su + (1 * RG + r) * W + x + 1;
+        const C e1 = cscale(csub(r1[1], r1[-1]), f);
+        const C e3 = cscale(csub(U3[k][r + 2], U3[k][r]), f);
+        const C e5 = cscale(cadd(csub(U1[k][r + 2], U1[k][r]), csub(r3[1], r3[-1])), f);
+        const size_t cell = size_t(zz) * nx + x;
+        const Rl d11 = (__ldg(a.m() + 1 * plane + cell) - a.ref(1)) * ms;
+        const Rl d13 = (__ldg(a.m() + 2 * plane + cell) - a.ref(2)) * ms;
+        const Rl d33 = (__ldg(a.m() + 3 * plane + cell) - a.ref(3)) * ms;
+        const Rl d55 = (__ldg(a.m() + 4 * plane + cell) - a.ref(4)) * ms;
+        s1 = cadd(cscale(e1, d11), cscale(e3, d13));
+        s3 = cadd(cscale(e1, d13), cscale(e3, d33));
+        s5 = cscale(e5, d55);
+      }
+      S3[k][r] = s3;
+      S5[k][r] = s5;
+      if (r >= 1 && r <= ROWS && x < nx) {
+        sg[(0 * ROWS + r - 1) * W + x + 1] = s1;
+        sg[(1 * ROWS + r - 1) * W + x + 1] = s5;
+      }
     }
   }
   __syncthreads();
   // s1 = w^2 drho u1 + d1 sigma1 + d3 sigma5, s3 = w^2 drho u3 + d1 sigma5 + d3 sigma3
   const Rl w2 = a.w2();
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r) {
-    const int z = z0 + r;
-    if (col && z < nz) {
-      const C *g1 = sg + (0 * ROWS + r) * W + x + 1, *g5 = sg + (1 * ROWS + r) * W + x + 1;
-      C o1 = cadd(csub(g1[1], g1[-1]), csub(S5[r + 2], S5[r]));
-      C o3 = cadd(csub(g5[1], g5[-1]), csub(S3[r + 2], S3[r]));
-      o1 = cscale(o1, f);
-      o3 = cscale(o3, f);
-      const Rl wr = w2 * (__ldg(a.m() + size_t(z) * nx + x) - a.ref(0)) * ms;
-      so[(0 * ROWS + r) * nx + x] = cadd(o1, cscale(U1[r + 2], wr));
-      so[(1 * ROWS + r) * nx + x] = cadd(o3, cscale(U3[r + 2], wr));
+  for (int k = 0; k < KC; ++k) {
+    const int x = threadIdx.x + k * kTileThreads;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const int z = z0 + r;
+      if (x < nx && z < nz) {
+        const C *g1 = sg + (0 * ROWS + r) * W + x + 1, *g5 = sg + (1 * ROWS + r) * W + x + 1;
+        C o1 = cadd(csub(g1[1], g1[-1]), csub(S5[k][r + 2], S5[k][r]));
+        C o3 = cadd(csub(g5[1], g5[-1]), csub(S3[k][r + 2], S3[k][r]));
+        o1 = cscale(o1, f);
+        o3 = cscale(o3, f);
+        const Rl wr = w2 * (__ldg(a.m() + size_t(z) * nx + x) - a.ref(0)) * ms;
+        so[(0 * ROWS + r) * nx + x] = cadd(o1, cscale(U1[k][r + 2], wr));
+        so[(1 * ROWS + r) * nx + x] = cadd(o3, cscale(U3[k][r + 2], wr));
+      }
     }
   }
   __syncthreads();
@@ -302,7 +322,7 @@ __device__ __forceinline__ void rows_forward_tile(const A &a, int tile, C *smem)
   const TwReg<C, LX, V> tr(t, a.tw());
   C v[2][8];
 
-  if constexpr (STENCIL && kStripStencil<LX>) {
+  if constexpr (STENCIL && kStripStencil<C, LX>) {
     stencil_strip<C, LX>(a, z0, smem, v);
   } else if constexpr (STENCIL) {
     const int W = nx + 2;          // rows with one zero column on each side
