@@ -7,9 +7,9 @@
 // the points j + r L/R = t + (i + r 8/R) T of the registers, multiplies them by W_{Ns R}^{r (j mod
 // Ns)} (Ns = product of the earlier radices), takes an R-point DFT and writes position
 // (j - j mod Ns) R + j mod Ns + r Ns of the line (self-sorting Stockham order). Between passes the
-// line goes through shared memory, padded as i + i/16 so that the strided writes of a warp hit
-// distinct banks; the last pass writes position j + r L/R = t + (i + r 8/R) T, i.e. straight back
-// into the registers in natural order.
+// line goes through shared memory, its positions swizzled within 16-point blocks so that the
+// strided writes of a warp hit distinct banks; the last pass writes position j + r L/R = t +
+// (i + r 8/R) T, i.e. straight back into the registers in natural order.
 //
 // Forward transforms use exp(-2 pi i jk/L), inverse ones exp(+2 pi i jk/L), unnormalised.
 // A thread's twiddles depend only on t and the pass, so each kernel reads them once from the
@@ -114,9 +114,15 @@ template <typename C, int L> struct RegFFT {
   static constexpr int LP = L + L / 16 + 2;       // padded line length in shared memory
   static constexpr int TWS = kTwiddleN / L;       // table stride of W_L
 
-  // One padding slot per 16 points: every store and gather pattern of the radix-8 passes then
-  // needs the minimum two shared-memory wavefronts per warp (8-byte points).
-  __host__ __device__ __forceinline__ static int pad(int i) { return i + (i >> 4); }
+  // Position of point i of a line in shared memory: inside each 16-point block, the low four bits
+  // are XORed with the block index (bits 0-2) and with bit 2 of the block index moved to bit 3. A
+  // bijection on every 16-point block, so every access pattern of the radix-8 passes (stride-8
+  // stores, two runs of 8 that are 64 apart, runs of 16 consecutive points) needs the minimum two
+  // wavefronts per warp of 8-byte points, for every length from 128 to 1024.
+  __host__ __device__ __forceinline__ static int pad(int i) {
+    const int h = i >> 4;
+    return (i & ~15) | ((i & 15) ^ ((((h >> 2) & 1) << 3) | (h & 7)));
+  }
 
   // The NB = 8/R butterflies of one pass on registers in natural order: twiddle by the powers
   // wp[i][r] (NS > 1), R-point DFT. HIN (first pass only): v[4..7] are zero and not read.
