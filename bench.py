@@ -10,6 +10,7 @@ the misfit gradient for (rho, C11, C13, C33, C55). The metric counts LS-operator
 second of wall time on the device.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload uneven40     # the 40-problem uneven batch (grids 64^2 .. 512^2)
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own 32 sources x 8 frequencies
 (weak scaling) and the gradients are summed across ranks with one all-reduce per step.
@@ -51,6 +52,10 @@ def parse_args():
     ap.add_argument("--check-every", type=int, default=4,
                     help="BiCGSTAB iterations between host convergence checks (each check also "
                          "compacts the launches to the problems still active)")
+    ap.add_argument("--workload", choices=["vti256", "uneven40"], default="vti256",
+                    help="vti256: the gradient step of the benchmark (default); uneven40: operator "
+                         "passes over the 40-problem uneven batch (persistent launches, autotuned), "
+                         "plus one graph-captured solve")
     ap.add_argument("--sources", type=int, default=32,
                     help="sources per GPU (32 is the benchmark workload; fewer make a smaller batch "
                          "of the same grid for profiler captures)")
@@ -460,10 +465,90 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args):
+    """Operator passes over the 40-problem uneven batch (3074 wavefields on grids of 64^2 .. 512^2),
+    after the autotuner; one step = one pass over every wavefield. Also times one graph-captured
+    BiCGSTAB solve of every wavefield from its incident field."""
+    import torch
+    from paper_2402_02116_gb300 import dbi
+    from paper_2402_02116_gb300.group import UnevenBatch
+    from paper_2402_02116_gb300.problem import DeviceProblem
+    rank, world = 0, 1
+    if args.gpus > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        rank, world = dist.get_rank(), dist.get_world_size()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    from paper_2402_02116_gb300 import build
+    build.build()
+    dbi.load()
+    ws = inputs.config5_uneven()
+    Ps = [DeviceProblem(w, dbi.C64, device=dev) for w in ws]
+    G = UnevenBatch(Ps, dbi.C64)
+    u = G.incident()
+    out = torch.empty_like(u)
+    tuning = G.tune(u)
+    cells = sum(P.B * P.w.nz * P.w.nx for P in Ps)
+    for _ in range(args.warmup):
+        G.apply(u, out=out)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = dbi.kernel_launches()
+    with ClockSampler(gpu_id(dev)) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            G.apply(u, out=out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = dbi.kernel_launches() - launches0
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max * 1e-3)
+    # one graph-captured solve of every wavefield
+    torch.cuda.synchronize()
+    t0 = time.time()
+    _, iters, _, code = G.solve(u, tol=TOL, max_iter=MAX_ITER, check_every=8, graph=True)
+    torch.cuda.synchronize()
+    solve_s = time.time() - t0
+    slot_cells = [P.w.nz * P.w.nx for P in Ps for _ in range(P.B)]
+    useful = sum(2 * int(i) * c for i, c in zip(iters.cpu().tolist(), slot_cells))
+    sizes = sorted({P.w.nz for P in Ps})
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 (fp32 complex operator; fp64 inner products and scalars)",
+        "data": "synthetic (seeded isotropic / VTI models with Gaussian anomalies)",
+        "config": {"workload": "uneven40: 40 problems, square grids " + "/".join(f"{n}^2" for n in sizes)
+                   + ", 1-32 sources x 1-8 frequencies (2-25 Hz) each", "members": len(Ps),
+                   "wavefields": G.slots, "cells_per_pass": cells, "step": "one operator pass over every "
+                   "wavefield (3 persistent launches + input scaling)",
+                   "l2": f"inputs larger than L2: {cells * 16 / 1e9:.1f} GB per field"},
+        "autotuner": tuning, "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
+        "clocks": clk.summary(),
+        "solve": {"seconds": solve_s, "all_converged": bool((code == dbi.CONVERGED).all()),
+                  "iterations_mean": float(iters.float().mean()), "iterations_max": int(iters.max()),
+                  "useful_cell_applies_per_s": useful / solve_s, "graph_captured": True},
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven40":
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -46,27 +46,31 @@ __device__ __forceinline__ int problem_at(const int *plist, int slot) { return p
   _Pragma("unroll 4")                                                                         \
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt; i += size_t(gridDim.x) * blockDim.x)
 
-// ||rhs||^2 with every square formed in FP64: the right-hand side may lie far from unit scale
-// (a data residual of 1e-12 back-propagates to fields of 1e-21), where FP32 squares underflow.
-template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_bnorm(Span sp, const C *rhs, double *part) {
+// Largest |component| of every problem's array (real and imaginary parts of complex values):
+// comparisons only, so nothing underflows whatever the scale of the values (a data residual of
+// 1e-12 back-propagates to fields of 1e-21, whose squares would underflow FP32).
+template <typename T> __device__ __forceinline__ double absmax(T v);
+template <> __device__ __forceinline__ double absmax<float>(float v) { return fabsf(v); }
+template <> __device__ __forceinline__ double absmax<double>(double v) { return fabs(v); }
+template <> __device__ __forceinline__ double absmax<float2>(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
+template <> __device__ __forceinline__ double absmax<double2>(double2 v) { return fmax(fabs(v.x), fabs(v.y)); }
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_absmax(Span sp, const T *x, double *part) {
   const int b = blockIdx.y;
-  double bb = 0.0;
-  DBI_PROBLEM_LOOP(sp) {
-    const C bi = rhs[off + i];
-    const double x = bi.x, y = bi.y;
-    bb += x * x + y * y;
-  }
-  double acc[1] = {bb};
-  block_sum_store<1>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+  double m = 0.0;
+  DBI_PROBLEM_LOOP(sp) m = fmax(m, absmax<T>(x[off + i]));
+  block_max_store(m, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
 
-// Power-of-two scale per problem that brings ||rhs|| into [1, 2); the solver iterates on the
+// 2^-e with m in [2^e, 2^(e+1)), or 1 when m = 0.
+__device__ __forceinline__ double pow2_below(double m) { return m > 0.0 ? ldexp(1.0, -ilogb(m)) : 1.0; }
+
+// Power-of-two scale per problem that brings max |rhs| into [1, 2); the solver iterates on the
 // scaled system (exact in any precision) and unscales the solution at the end.
 __global__ void k_scale(KState *st, const double *part) {
-  double s[1];
-  gather_n<1>(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, kRedBlocks, s);
-  if (threadIdx.x == 0) st[blockIdx.x].scale = s[0] > 0.0 ? ldexp(1.0, -ilogb(sqrt(s[0]))) : 1.0;
+  const double m = gather_max(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, kRedBlocks);
+  if (threadIdx.x == 0) st[blockIdx.x].scale = pow2_below(m);
 }
 
 // x *= scale (inverse = 0) or x /= scale (inverse = 1)
@@ -318,26 +322,10 @@ __global__ void k_finalize(int B, const KState *st, int *iters, double *relres, 
 // ---------------------------------------------------------------------------------------------
 // power-of-two normalisers
 // ---------------------------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ double sq64(T v);
-template <> __device__ __forceinline__ double sq64<float>(float v) { return double(v) * double(v); }
-template <> __device__ __forceinline__ double sq64<double>(double v) { return v * v; }
-template <> __device__ __forceinline__ double sq64<float2>(float2 v) { return double(v.x) * v.x + double(v.y) * v.y; }
-template <> __device__ __forceinline__ double sq64<double2>(double2 v) { return v.x * v.x + v.y * v.y; }
-
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_sumsq(Span sp, const T *x, double *part) {
-  const int b = blockIdx.y;
-  double acc = 0.0;
-  DBI_PROBLEM_LOOP(sp) acc += sq64<T>(x[off + i]);
-  double a[1] = {acc};
-  block_sum_store<1>(a, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
-}
-
 __global__ void k_pow2(const double *part, double *scale, double *inv, const double *extra) {
-  double s[1];
-  gather_n<1>(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, kRedBlocks, s);
+  const double m = gather_max(part + size_t(blockIdx.x) * kRedBlocks * kRedSlots, kRedBlocks);
   if (threadIdx.x == 0) {
-    const double sc = s[0] > 0.0 ? ldexp(1.0, -ilogb(sqrt(s[0]))) : 1.0;
+    const double sc = pow2_below(m);
     scale[blockIdx.x] = sc;
     if (inv) inv[blockIdx.x] = 1.0 / (sc * (extra ? extra[0] : 1.0));
   }
@@ -348,14 +336,14 @@ int pow2_scales(const void *x, int precision, bool real, int B, size_t n, double
   const dim3 grid(kRedBlocks, B);
   const Span sp{n, offs};
   if (precision == DBI_C64) {
-    if (real) k_sumsq<float><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const float *>(x), part);
-    else k_sumsq<float2><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const float2 *>(x), part);
+    if (real) k_absmax<float><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const float *>(x), part);
+    else k_absmax<float2><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const float2 *>(x), part);
   } else {
-    if (real) k_sumsq<double><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const double *>(x), part);
-    else k_sumsq<double2><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const double2 *>(x), part);
+    if (real) k_absmax<double><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const double *>(x), part);
+    else k_absmax<double2><<<grid, kRedThreads, 0, s>>>(sp, static_cast<const double2 *>(x), part);
   }
   int rc;
-  if ((rc = check_launch("k_sumsq"))) return rc;
+  if ((rc = check_launch("k_absmax"))) return rc;
   k_pow2<<<B, 32, 0, s>>>(part, scale, inv, extra);
   return check_launch("k_pow2");
 }
@@ -423,8 +411,8 @@ static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, voi
   const int nparts = group ? group_parts(op.group) : operator_parts(op.nz, op.lx, op.precision);
   op.stencil = true;
   op.active = nullptr;
-  k_bnorm<C><<<grid, kRedThreads, 0, s>>>(sp, rhs, sb.partA);
-  if ((rc = check_launch("k_bnorm"))) return rc;
+  k_absmax<C><<<grid, kRedThreads, 0, s>>>(sp, rhs, sb.partA);
+  if ((rc = check_launch("k_absmax"))) return rc;
   k_scale<<<B, 32, 0, s>>>(sb.st, sb.partA);
   if ((rc = check_launch("k_scale"))) return rc;
   if (!x_zero) {  // x0 into the scaled system, v = A x0

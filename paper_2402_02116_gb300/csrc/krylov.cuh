@@ -34,7 +34,7 @@ SolverBufs carve_solver_fields(Arena &ar, size_t field_bytes, int B);
 
 // Solves A x = rhs for every problem of `op` (op.in / op.out / op.ident are set internally).
 // x_zero: the initial guess is zero (x is overwritten without being read). The iteration runs on
-// rhs scaled by a power of two per problem (KState::scale, ||scaled rhs|| in [1, 2)); with
+// rhs scaled by a power of two per problem (KState::scale, max |scaled rhs| in [1, 2)); with
 // unscale = false the returned x stays in that scaled system (x = scale * A^{-1} rhs).
 // Validates Krylov options (tol >= 0, max_iter >= 0, check_every >= 0).
 int check_krylov(const dbi_krylov_opts *o);

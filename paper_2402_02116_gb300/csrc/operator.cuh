@@ -64,9 +64,9 @@ int operator_parts(int nz, int lx, int precision);
 int run_operator(const OpArgs &a, cudaStream_t s);
 
 // Per-problem power-of-two normalisers of B arrays of n elements each (or of the extents offs
-// gives, when non-NULL; complex of the precision, or real when `real` is set): scale[b] = 2^-e with
-// ||x_b|| in [2^e, 2^(e+1)), 1 for a zero array. If inv is non-NULL, inv[b] = 1 / (scale[b] *
-// (extra ? extra[0] : 1)). part: bytes_partials(B).
+// gives, when non-NULL; complex of the precision, or real when `real` is set): scale[b] = 2^-e
+// with max |x_b| (largest real or imaginary part) in [2^e, 2^(e+1)), 1 for a zero array. If inv is
+// non-NULL, inv[b] = 1 / (scale[b] * (extra ? extra[0] : 1)). part: bytes_partials(B).
 struct Scales {
   double *scale, *inv, *aux, *mscale, *part;
 };

@@ -55,4 +55,36 @@ template <int NS> __device__ __forceinline__ void gather_n(const double *part, i
   __syncthreads();
 }
 
+// Maximum of v over the CTA; thread 0 stores it to out[0]. Every thread of the CTA must call it.
+__device__ __forceinline__ void block_max_store(double v, double *out) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) a = fmax(a, sh[w]);
+    out[0] = a;
+  }
+  __syncthreads();
+}
+
+// Maximum of slot 0 of `count` partials (stride kRedSlots); every thread of the CTA gets it.
+__device__ __forceinline__ double gather_max(const double *part, int count) {
+  __shared__ double sh;
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < count; i += 32) a = fmax(a, part[i * kRedSlots]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, off));
+    if (threadIdx.x == 0) sh = a;
+  }
+  __syncthreads();
+  const double r = sh;
+  __syncthreads();
+  return r;
+}
+
 }  // namespace dbi
