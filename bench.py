@@ -252,7 +252,7 @@ def run_ours(args):
     if (w.nz, w.nx, w.lz, w.lx) == (256, 256, 512, 512):
         per_launch_problems = rank_applies / max(cols_launches, 1)
         roof["traffic"] = COLS_DRAM_BYTES_PER_PROBLEM * per_launch_problems
-        roof["traffic_note"] = ("ncu dram bytes of k_cols, 4.21 MB per problem (64-problem capture), "
+        roof["traffic_note"] = ("ncu dram bytes of k_cols, 4.35 MB per problem (64-problem capture), "
                                 f"x {per_launch_problems:.1f} problems per timed launch")
     else:
         roof["traffic"] = None
@@ -369,7 +369,7 @@ def plain_c128_sample(w, dev, cells, value_c64):
 # ---------------------------------------------------------------------------------------------
 # roofline arithmetic of the column pass (per D-cell per operator pass)
 # ---------------------------------------------------------------------------------------------
-COLS_DRAM_BYTES_PER_PROBLEM = 4.21e6
+COLS_DRAM_BYTES_PER_PROBLEM = 4.35e6
 
 
 def cols_bytes_per_cell_apply(w):
