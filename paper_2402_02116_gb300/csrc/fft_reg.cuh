@@ -7,8 +7,8 @@
 // the points j + r L/R = t + (i + r 8/R) T of the registers, multiplies them by W_{Ns R}^{r (j mod
 // Ns)} (Ns = product of the earlier radices), takes an R-point DFT and writes position
 // (j - j mod Ns) R + j mod Ns + r Ns of the line (self-sorting Stockham order). Between passes the
-// line goes through shared memory, its positions swizzled within 16-point blocks so that the
-// strided writes of a warp hit distinct banks; the last pass writes position j + r L/R = t +
+// line goes through shared memory, laid out so that the strided writes of a warp hit distinct banks
+// (padding or an XOR swizzle, per exchange); the last pass writes position j + r L/R = t +
 // (i + r 8/R) T, i.e. straight back into the registers in natural order.
 //
 // Forward transforms use exp(-2 pi i jk/L), inverse ones exp(+2 pi i jk/L), unnormalised.
@@ -87,6 +87,18 @@ template <int L, int V> struct PlanInfo {
   static constexpr int nw = woff(np);  // base twiddles per thread (passes 1 .. np-1)
 };
 
+// Line layout of exchange p (after pass p) of each plan: the cheapest layout (RegFFT::pad) whose
+// stores and loads need the minimum shared-memory wavefronts, found by counting the wavefronts of
+// every access of every layout for each plan (one line per warp from L = 256; two or more below).
+template <int L, int V> constexpr int layout_of(int p) {
+  if constexpr (L == 16) return 0;
+  else if constexpr (L == 32) return V == 0 ? 1 : 0;
+  else if constexpr (L == 64) return 1;
+  else if constexpr (L == 128 || L == 256) return (p == 1 && V == 0) ? 2 : 1;
+  else if constexpr (L == 512) return p == 0 ? 1 : 2;
+  else return p == 0 ? 1 : (p == 1 ? (V == 0 ? 2 : 1) : 0);
+}
+
 template <typename C, int L, int V = 0> struct TwReg {
   static constexpr int NW = PlanInfo<L, V>::nw;
   C w[NW];
@@ -114,14 +126,20 @@ template <typename C, int L> struct RegFFT {
   static constexpr int LP = L + L / 16 + 2;       // padded line length in shared memory
   static constexpr int TWS = kTwiddleN / L;       // table stride of W_L
 
-  // Position of point i of a line in shared memory: inside each 16-point block, the low four bits
-  // are XORed with the block index (bits 0-2) and with bit 2 of the block index moved to bit 3. A
-  // bijection on every 16-point block, so every access pattern of the radix-8 passes (stride-8
-  // stores, two runs of 8 that are 64 apart, runs of 16 consecutive points) needs the minimum two
-  // wavefronts per warp of 8-byte points, for every length from 128 to 1024.
-  __host__ __device__ __forceinline__ static int pad(int i) {
-    const int h = i >> 4;
-    return (i & ~15) | ((i & 15) ^ ((((h >> 2) & 1) << 3) | (h & 7)));
+  // Position of point i of a line in shared memory, by layout (chosen per exchange, see
+  // Layouts): 0 = i; 1 = i + i/16 (one padding slot per 16 points); 2 = inside each 16-point
+  // block, the low four bits XORed with the block index (bits 0-2) and with bit 2 of the block
+  // index moved to bit 3 (a bijection on every block). Each exchange takes the cheapest layout
+  // under which its stores and loads need the minimum two wavefronts per warp of 8-byte points.
+  template <int LAY> __host__ __device__ __forceinline__ static int pad(int i) {
+    if constexpr (LAY == 0) {
+      return i;
+    } else if constexpr (LAY == 1) {
+      return i + (i >> 4);
+    } else {
+      const int h = i >> 4;
+      return (i & ~15) | ((i & 15) ^ ((((h >> 2) & 1) << 3) | (h & 7)));
+    }
   }
 
   // The NB = 8/R butterflies of one pass on registers in natural order: twiddle by the powers
@@ -146,21 +164,21 @@ template <typename C, int L> struct RegFFT {
   }
 
   // Store a pass's outputs (held in v as produced by butterflies()) at their Stockham positions.
-  template <int R, int NS>
+  template <int R, int NS, int LAY>
   __host__ __device__ __forceinline__ static void scatter(const C (&v)[8], C *line, int t) {
     constexpr int NB = 8 / R;
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = t + i * T, k = j % NS, base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) line[pad(base + r * NS)] = v[i + r * NB];
+      for (int r = 0; r < R; ++r) line[pad<LAY>(base + r * NS)] = v[i + r * NB];
     }
   }
 
   // Load the next pass's input (natural order) from a shared-memory line.
-  __host__ __device__ __forceinline__ static void gather(C (&v)[8], const C *line, int t) {
+  template <int LAY> __host__ __device__ __forceinline__ static void gather(C (&v)[8], const C *line, int t) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = line[pad(t + m * T)];
+    for (int m = 0; m < 8; ++m) v[m] = line[pad<LAY>(t + m * T)];
   }
 };
 
@@ -198,10 +216,12 @@ template <int L, int V = 0> struct RegPlan {
             for (int l = 0; l < NLT; ++l) F::template butterflies<R, NS, INV, H>(v[l], wp);
             if constexpr (!LAST) {
 #pragma unroll
-              for (int l = 0; l < NLT; ++l) F::template scatter<R, NS>(v[l], lines[l], t);
+              constexpr int LAY = layout_of<L, V>(p);
+#pragma unroll
+              for (int l = 0; l < NLT; ++l) F::template scatter<R, NS, LAY>(v[l], lines[l], t);
               sync();
 #pragma unroll
-              for (int l = 0; l < NLT; ++l) F::gather(v[l], lines[l], t);
+              for (int l = 0; l < NLT; ++l) F::template gather<LAY>(v[l], lines[l], t);
               sync();
             }
           }(),
