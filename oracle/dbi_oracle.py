@@ -212,6 +212,75 @@ def convolve_fft(s, G_hat, h):
 
 
 # ---------------------------------------------------------------------------------------------
+# Paper-literal form: the derivative on the Green's tensor (Eq. 9)
+# ---------------------------------------------------------------------------------------------
+# Eq. 9 integrates the stress term by parts so that the derivative falls on G: the operator is
+#   A u = u - [ w^2 G * (drho u) + (grad G) * sigma ],  (grad G * sigma)_i = sum_jk d_k G_ij sigma_jk,
+# sigma = dC : eps(u) (the sign: grad_x' G(x - x') = -(grad G)(x - x')). The derivatives of G are
+# the central differences of the lattice G_h, (D_k G)(y) = [G_h(y + h e_k) - G_h(y - h e_k)] / 2h,
+# which needs G_h one ring beyond the (2N-1)^2 offsets. For stress that vanishes on the outer ring
+# of D this equals the form above term by term (summation by parts); it differs next to the
+# boundary of D.
+def green_derivative_lattice(nz, nx, h, omega, alpha, beta, rho) -> np.ndarray:
+    """(D_k G_h) on the (2nz-1) x (2nx-1) offsets: [6][dz+nz-1][dx+nx-1] holding D1 G11, D1 G13,
+    D1 G33, D3 G11, D3 G13, D3 G33 (D1 along x1, the last axis; D3 along x3)."""
+    Ge = green_lattice(nz + 1, nx + 1, h, omega, alpha, beta, rho)  # offsets -nz..nz, -nx..nx
+    d1g = (Ge[:, 1:-1, 2:] - Ge[:, 1:-1, :-2]) / (2.0 * h)
+    d3g = (Ge[:, 2:, 1:-1] - Ge[:, :-2, 1:-1]) / (2.0 * h)
+    return np.concatenate([d1g, d3g]).astype(np.complex128)
+
+
+def form_k_sources(u, dmodel, omega, h):
+    """The five fields convolved in Eq. 9: w^2 drho u1, w^2 drho u3, sigma1, sigma5, sigma3."""
+    s = omega * omega * dmodel[0] * u
+    sig = stress(strain(u, h), dmodel)
+    return np.stack([s[0], s[1], sig[0], sig[2], sig[1]])
+
+
+# Rows of the 2 x 5 kernel of Eq. 9 over the sources (s1, s3, sigma1, sigma5, sigma3), as
+# (table, index) pairs summed per entry: table "G" = green_lattice, "D" = green_derivative_lattice.
+FORM_K_KERNEL = (
+    ((("G", 0),), (("G", 1),), (("D", 0),), (("D", 3), ("D", 1)), (("D", 4),)),
+    ((("G", 1),), (("G", 2),), (("D", 1),), (("D", 4), ("D", 2)), (("D", 5),)),
+)
+
+
+def form_k_direct(src, G_lat, DG_lat, h):
+    """h^2 sum_{x' in D} K(x - x') src(x') for the 2 x 5 kernel of Eq. 9, summed directly."""
+    _, nz, nx = src.shape
+    out = np.zeros((2, nz, nx), dtype=np.complex128)
+    tables = {"G": G_lat, "D": DG_lat}
+    for izp in range(nz):
+        for ixp in range(nx):
+            sl = (slice(nz - 1 - izp, 2 * nz - 1 - izp), slice(nx - 1 - ixp, 2 * nx - 1 - ixp))
+            for i in range(2):
+                for c in range(5):
+                    ker = sum(tables[t][k][sl] for t, k in FORM_K_KERNEL[i][c])
+                    out[i] += ker * src[c, izp, ixp]
+    return h * h * out
+
+
+def form_k_spectra(G_lat, DG_lat, lz, lx):
+    """FFTs of the circulant embeddings of the nine distinct kernel entries, as [2][5] spectra."""
+    G_hat = green_spectrum(G_lat, lz, lx)
+    D_hat = np.concatenate([green_spectrum(DG_lat[0:3], lz, lx), green_spectrum(DG_lat[3:6], lz, lx)])
+    tables = {"G": G_hat, "D": D_hat}
+    return [[sum(tables[t][k] for t, k in FORM_K_KERNEL[i][c]) for c in range(5)] for i in range(2)]
+
+
+def form_k_fft(src, K_hat, h):
+    """The same convolution by Eq. 12 on the zero-padded grid."""
+    _, nz, nx = src.shape
+    lz, lx = K_hat[0][0].shape
+    sp = np.zeros((5, lz, lx), dtype=np.complex128)
+    sp[:, :nz, :nx] = src
+    S = np.fft.fft2(sp, axes=(-2, -1))
+    O = np.stack([sum(K_hat[i][c] * S[c] for c in range(5)) for i in range(2)])
+    o = np.fft.ifft2(O, axes=(-2, -1))
+    return h * h * o[:, :nz, :nx]
+
+
+# ---------------------------------------------------------------------------------------------
 # Krylov solver
 # ---------------------------------------------------------------------------------------------
 def bicgstab(apply, b, tol=1e-12, maxiter=2000, x0=None):
@@ -286,6 +355,21 @@ class LSOracle:
     def apply(self, u, model, f):
         dmod = contrast(model, self.rho0, self.alpha0, self.beta0)
         return u - self.convolve(contrast_source(u, dmod, self.omegas[f], self.h), f)
+
+    # --- Eq. 9 (derivatives on G): A_K u = u - [w^2 G * (drho u) + (grad G) * sigma] -----------
+    def apply_k(self, u, model, f):
+        if not hasattr(self, "K_hat"):
+            self.K_hat = [form_k_spectra(G, green_derivative_lattice(self.nz, self.nx, self.h, w, self.alpha0,
+                                                                     self.beta0, self.rho0), self.lz, self.lx)
+                          for G, w in zip(self.G_lat, self.omegas)]
+        dmod = contrast(model, self.rho0, self.alpha0, self.beta0)
+        return u - form_k_fft(form_k_sources(u, dmod, self.omegas[f], self.h), self.K_hat[f], self.h)
+
+    def solve_k(self, rhs, model, f, tol=1e-12, maxiter=3000):
+        shape = rhs.shape
+        x, _ = bicgstab(lambda v: self.apply_k(v.reshape(shape), model, f).ravel(), rhs.ravel(), tol=tol,
+                        maxiter=maxiter)
+        return x.reshape(shape)
 
     # --- Eq. 7: incident field of a point force f at cell x_s: u0(x) = G_h(x - x_s) f ------------
     def incident(self, f, src_cell, force):
