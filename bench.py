@@ -11,6 +11,7 @@ second of wall time on the device.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --workload uneven40     # the 40-problem uneven batch (grids 64^2 .. 512^2)
+    python bench.py --workload formk256     # operator passes in the paper-literal form of Eq. 9
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own 32 sources x 8 frequencies
 (weak scaling) and the gradients are summed across ranks with one all-reduce per step.
@@ -52,10 +53,12 @@ def parse_args():
     ap.add_argument("--check-every", type=int, default=4,
                     help="BiCGSTAB iterations between host convergence checks (each check also "
                          "compacts the launches to the problems still active)")
-    ap.add_argument("--workload", choices=["vti256", "uneven40"], default="vti256",
+    ap.add_argument("--workload", choices=["vti256", "uneven40", "formk256"], default="vti256",
                     help="vti256: the gradient step of the benchmark (default); uneven40: operator "
                          "passes over the 40-problem uneven batch (persistent launches, autotuned), "
-                         "plus one graph-captured solve")
+                         "plus one graph-captured solve; formk256: operator passes over the 256^2 "
+                         "batch in the paper-literal form (derivatives on G, Eq. 9) beside the "
+                         "divergence form")
     ap.add_argument("--sources", type=int, default=32,
                     help="sources per GPU (32 is the benchmark workload; fewer make a smaller batch "
                          "of the same grid for profiler captures)")
@@ -543,12 +546,106 @@ def run_uneven(args):
         dist.destroy_process_group()
 
 
+def formk_cols_bytes_per_cell_apply(w):
+    """Compulsory bytes of kk_cols: the five row-transformed sources [5][nz][lx] read and the two
+    outputs [2][nz][lx] written (complex64), plus Ghat [3][lz][lx] and the derivative tables
+    [6][lz][lx] read once per frequency and shared by its sources."""
+    t = 7 * w.nz * w.lx * 8
+    g = 9 * w.lz * w.lx * 8 * w.nf / w.n_problems
+    return (t + g) / (w.nz * w.nx)
+
+
+def formk_cols_flops_per_cell_apply(w):
+    """Nominal flops of kk_cols: 5 L log2 L per complex FFT of length lz (five forward, two
+    inverse per column, lx columns) plus the 2 x 5 complex multiply-accumulate (10 products and
+    10 sums, 80 flops) at each of the lz x lx wavenumbers."""
+    fft = 7 * w.lx * 5 * w.lz * math.log2(w.lz)
+    return (fft + 80 * w.lz * w.lx) / (w.nz * w.nx)
+
+
+def run_formk(args):
+    """Operator passes over the 256 x 256 VTI batch (32 sources x 8 frequencies) in the
+    paper-literal form of Eq. 9 (ls_apply_k: five sources, the 2 x 5 kernel of G and its central
+    differences), one step = one pass over the 256 wavefields; the divergence form (ls_apply) is
+    timed the same way on the same inputs, and the two results are compared."""
+    import torch
+    from paper_2402_02116_gb300 import build, dbi
+    from paper_2402_02116_gb300.problem import DeviceProblem
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    build.build()
+    dbi.load()
+    w = workload(0, 1, args.sources)
+    P = DeviceProblem(w, dbi.C64, device=dev)
+    u = P.incident()
+    out = torch.empty_like(u)
+    cells = w.nz * w.nx * P.B
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, stage):
+        for _ in range(args.warmup):
+            fn()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = dbi.kernel_launches()
+        dbi.profile_begin(stage)
+        with ClockSampler(gpu_id(dev)) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        stage_ms, stage_launches = dbi.profile_end()
+        return ev0.elapsed_time(ev1), dbi.kernel_launches() - n0, stage_ms, stage_launches, clk.summary()
+
+    Dhat = P.Dhat
+    ms_k, launches_k, cols_ms, cols_launches, clocks = timed(
+        lambda: dbi.ls_apply_k(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, Dhat, u, out=out), dbi.PROF_COLS)
+    a_k = out.clone()
+    out_s = torch.empty_like(u)
+    ms_s, launches_s, _, _, clocks_s = timed(
+        lambda: dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u, out=out_s), dbi.PROF_OPERATOR)
+    diff = float(torch.linalg.norm(a_k - out_s) / torch.linalg.norm(out_s - u))
+    value = cells * args.steps / (ms_k * 1e-3)
+    peaks = load_peaks()
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6
+    cols_s = cols_ms * 1e-3
+    flops = formk_cols_flops_per_cell_apply(w) * cells * args.steps
+    algo_bytes = formk_cols_bytes_per_cell_apply(w) * cells * args.steps
+    roof = {"bound": "alu", "achieved": flops / cols_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured median)",
+            "traffic": None, "kernel": "kk_cols (five forward column FFTs, 2 x 5 kernel, two inverse)",
+            "hbm_frac_of_algorithmic_bytes": algo_bytes / cols_s / (peaks.get("hbm_gbs", 6800.0) * 1e9),
+            "launches_timed": cols_launches, "avg_launch_ms": cols_ms / max(cols_launches, 1),
+            "share_of_step_time": cols_ms / ms_k if ms_k > 0 else None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_k / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 (fp32 complex operator)", "data": "synthetic (seeded VTI model with layers and anomalies)",
+        "config": {"workload": f"formk: {w.name}, one operator pass over every wavefield in the paper-literal "
+                               "form of Eq. 9 (derivatives on G)", "nz": w.nz, "nx": w.nx, "lz": w.lz, "lx": w.lx,
+                   "wavefields": P.B, "l2": f"inputs larger than L2: {cells * 16 / 1e9:.2f} GB per field"},
+        "roofline": roof, "gpu_launches": int(launches_k), "gpu_launches_per_step": launches_k / args.steps,
+        "clocks": clocks,
+        "divergence_form": {"value": cells * args.steps / (ms_s * 1e-3), "ms_per_step": ms_s / args.steps,
+                            "gpu_launches_per_step": launches_s / args.steps, "clocks": clocks_s},
+        "form_difference": {"relative_to_scattered_field": diff,
+                            "note": "||A_K u0 - A_S u0|| / ||A_S u0 - u0|| over the batch: the boundary layer "
+                                    "the divergence form leaves out where the contrast reaches the edge of D"},
+    }
+    print(json.dumps(result), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "uneven40":
         run_uneven(args)
+    elif args.workload == "formk256":
+        run_formk(args)
     else:
         run_ours(args)
 

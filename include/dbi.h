@@ -58,7 +58,10 @@ enum dbi_op {
   DBI_OP_SOLVE = 3,
   DBI_OP_FRECHET = 4,
   DBI_OP_ADJOINT = 5,
-  DBI_OP_NORMAL_CG = 6
+  DBI_OP_NORMAL_CG = 6,
+  DBI_OP_GREENS_K = 7, /* greens_tabulate_k (B counts frequencies) */
+  DBI_OP_APPLY_K = 8,  /* ls_apply_k */
+  DBI_OP_SOLVE_K = 9   /* ls_solve_k */
 };
 
 typedef struct dbi_grid {
@@ -174,6 +177,40 @@ int ls_apply(const dbi_model *model, const dbi_batch *batch, const void *Ghat, c
 int ls_solve(const dbi_model *model, const dbi_batch *batch, const void *Ghat, const void *rhs,
              void *u, const dbi_krylov_opts *opts, const dbi_status *status, int precision,
              void *work, size_t work_bytes, dbi_stream stream);
+
+/*
+ * greens_tabulate_k -- the derivative tables of the paper-literal form of the LS equation (Eq. 9,
+ *   the gradient acting on the Green's tensor instead of on the stress): central differences
+ *   (D_k G)(y) = [G_h(y + h e_k) - G_h(y - h e_k)] / 2h of the same lattice G_h as greens_tabulate
+ *   (self cell = disk average), at every offset |dz| < nz, |dx| < nx, placed at slot d mod L and
+ *   transformed by the FP64 2D FFT. Six entries per frequency, the kernel entries of the stress
+ *   components: e = D1G11, D1G13 (sigma11), D3G11 + D1G13, D3G13 + D1G33 (sigma13),
+ *   D3G13, D3G33 (sigma33).
+ *   omega device [nf]. Dhat device [nf][6][lx][lz] complex out, h^2 / (lz lx) * FFT, stored
+ *   column-major like Ghat. Work: DBI_OP_GREENS_K bytes (B = nf).
+ */
+int greens_tabulate_k(const dbi_grid *g, const dbi_medium *ref, const double *omega, int nf,
+                      int precision, void *Dhat, void *work, size_t work_bytes, dbi_stream stream);
+
+/*
+ * ls_apply_k -- out = u - h^2 [ G * (w^2 drho u) + sum_jk (D_k G_ij) * sigma_jk ], sigma = dC : eps(u)
+ *   (Eq. 9 discretised with the quadrature of Eq. 10 and evaluated by Eq. 12), eps by central
+ *   differences of u (zero outside D). Equals ls_apply exactly when dC vanishes on the outer ring
+ *   of cells of D (summation by parts); otherwise the two differ by the convolution of G with the
+ *   ring's boundary sources. Ghat from greens_tabulate, Dhat from greens_tabulate_k (same grid,
+ *   medium, frequencies, precision). u, out: device [B][2][nz][nx] complex (distinct).
+ *   Work: DBI_OP_APPLY_K bytes.
+ */
+int ls_apply_k(const dbi_model *model, const dbi_batch *batch, const void *Ghat, const void *Dhat,
+               const void *u, void *out, int precision, void *work, size_t work_bytes, dbi_stream stream);
+
+/*
+ * ls_solve_k -- ls_solve with the operator of ls_apply_k (BiCGSTAB, same options, status and
+ *   FP64 scalars). Work: DBI_OP_SOLVE_K bytes.
+ */
+int ls_solve_k(const dbi_model *model, const dbi_batch *batch, const void *Ghat, const void *Dhat,
+               const void *rhs, void *u, const dbi_krylov_opts *opts, const dbi_status *status,
+               int precision, void *work, size_t work_bytes, dbi_stream stream);
 
 /*
  * frechet_apply -- d = J dm (Eq. 20, 26-31): the virtual source w^2 dm_rho u_b + div(dC(dm) :

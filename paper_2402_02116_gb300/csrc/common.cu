@@ -232,6 +232,13 @@ extern "C" size_t dbi_workspace_bytes(const dbi_grid *g, int B, int precision, i
              imaging_chunks(B) * model +
              align256(4097 * sizeof(double));
     }
+    case DBI_OP_GREENS_K:  // B counts frequencies here
+      return align256(size_t(kTwiddleN) * sizeof(double2)) +
+             align256(size_t(B) * 6 * g->lz * g->lx * sizeof(double2));
+    case DBI_OP_APPLY_K:  // spectra of the five sources and of the two outputs
+      return tw + bytes_spectral_k(g, B, precision) + bytes_scales(B);
+    case DBI_OP_SOLVE_K:
+      return tw + bytes_spectral_k(g, B, precision) + bytes_solver(g, B, precision);
     default:
       return 0;
   }

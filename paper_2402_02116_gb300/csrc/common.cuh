@@ -100,6 +100,10 @@ struct Arena {
 // Sizes of the buffers each operation carves out of the work buffer (see workspace.cu).
 size_t bytes_twiddles(int precision);
 size_t bytes_spectral(const dbi_grid *g, int B, int precision);
+// Spectral scratch of the paper-literal form (Eq. 9): five source spectra and two output spectra.
+inline size_t bytes_spectral_k(const dbi_grid *g, int B, int precision) {
+  return align256(size_t(B) * 7 * g->lx * g->nz * (precision == DBI_C64 ? 8 : 16));
+}
 // Problems per operator pass: the three operator kernels run chunk by chunk over the batch; by
 // default one chunk holds the whole batch (DBI_SPECTRAL_CHUNK_MB bounds the scratch per chunk).
 int spectral_chunk(const dbi_grid *g, int B, int precision);

@@ -215,9 +215,87 @@ __global__ void k_incident(int B, int nf, int nz, int nx, int lz, int lx, const 
   u0[o + size_t(nz) * nx] = cadd(cscale(g13, f1), cscale(g33, f3));
 }
 
+// Derivative tables of the paper-literal form (Eq. 9): central differences of the lattice G_h,
+// (D_k G)(y) = [G_h(y + h e_k) - G_h(y - h e_k)] / 2h (G_h(0) = the self-cell mean), at every
+// offset |dz| < nz, |dx| < nx, combined into the six entries the kernel of Eq. 9 needs over the
+// stress components: [f][e][kz slot][kx slot] with e = D1G11, D1G13 (sigma1), D3G11 + D1G13,
+// D3G13 + D1G33 (sigma5), D3G13, D3G33 (sigma3). One thread per offset; gap slots zeroed before.
+__device__ __forceinline__ void green_at(int dz, int dx, double h, double w, double alpha, double beta,
+                                         double rho, double2 &g11, double2 &g13, double2 &g33) {
+  if (dz == 0 && dx == 0) {
+    g11 = g33 = green_self(h, w, alpha, beta, rho);
+    g13 = make_double2(0.0, 0.0);
+  } else {
+    green_offset(dx * h, dz * h, w, alpha, beta, rho, g11, g13, g33);
+  }
+}
+
+__global__ void k_green_deriv(int nz, int nx, int lz, int lx, double h, const double *omega, double rho,
+                              double alpha, double beta, double2 *W) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;  // dx + nx - 1
+  const int dz = int(blockIdx.y) - (nz - 1);
+  const int f = blockIdx.z;
+  if (ix >= 2 * nx - 1) return;
+  const int dx = ix - (nx - 1);
+  const double w = omega[f];
+  double2 xp[3], xm[3], zp[3], zm[3];
+  green_at(dz, dx + 1, h, w, alpha, beta, rho, xp[0], xp[1], xp[2]);
+  green_at(dz, dx - 1, h, w, alpha, beta, rho, xm[0], xm[1], xm[2]);
+  green_at(dz + 1, dx, h, w, alpha, beta, rho, zp[0], zp[1], zp[2]);
+  green_at(dz - 1, dx, h, w, alpha, beta, rho, zm[0], zm[1], zm[2]);
+  const double i2h = 1.0 / (2.0 * h);
+  double2 d1[3], d3[3];
+  for (int c = 0; c < 3; ++c) {
+    d1[c] = make_double2((xp[c].x - xm[c].x) * i2h, (xp[c].y - xm[c].y) * i2h);
+    d3[c] = make_double2((zp[c].x - zm[c].x) * i2h, (zp[c].y - zm[c].y) * i2h);
+  }
+  const double2 e[6] = {d1[0], d1[1], make_double2(d3[0].x + d1[1].x, d3[0].y + d1[1].y),
+                        make_double2(d3[1].x + d1[2].x, d3[1].y + d1[2].y), d3[1], d3[2]};
+  const size_t plane = size_t(lz) * lx;
+  const size_t cell = size_t(dz < 0 ? dz + lz : dz) * lx + (dx < 0 ? dx + lx : dx);
+  for (int k = 0; k < 6; ++k) W[(size_t(f) * 6 + k) * plane + cell] = e[k];
+}
+
 }  // namespace dbi
 
 using namespace dbi;
+
+extern "C" int greens_tabulate_k(const dbi_grid *g, const dbi_medium *ref, const double *omega, int nf,
+                                 int precision, void *Dhat, void *work, size_t work_bytes, dbi_stream stream) {
+  clear_error();
+  int rc;
+  if ((rc = check_grid(g)) || (rc = check_precision(precision))) return rc;
+  if (!ref || !(ref->rho0 > 0) || !(ref->alpha0 > 0) || !(ref->beta0 > 0) || !(ref->alpha0 > ref->beta0)) {
+    set_error("reference medium needs rho0 > 0 and alpha0 > beta0 > 0");
+    return DBI_ERR_ARG;
+  }
+  if (nf < 1 || !omega || !Dhat) { set_error("need nf >= 1, omega and Dhat"); return DBI_ERR_ARG; }
+  const size_t need = dbi_workspace_bytes(g, nf, precision, DBI_OP_GREENS_K);
+  if (!work || work_bytes < need) {
+    set_error("work buffer of %zu bytes, need %zu", work_bytes, need);
+    return DBI_ERR_WORKSPACE;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Arena ar(work, work_bytes);
+  double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
+  const size_t tab = size_t(nf) * 6 * g->lz * g->lx;
+  double2 *W = static_cast<double2 *>(ar.take(tab * sizeof(double2)));
+  if ((rc = launch_twiddles(tw, DBI_C128, s))) return rc;
+  cudaError_t e = cudaMemsetAsync(W, 0, tab * sizeof(double2), s);
+  if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(derivative table)", e);
+  dim3 grid((2 * g->nx - 1 + 127) / 128, 2 * g->nz - 1, nf);
+  k_green_deriv<<<grid, 128, 0, s>>>(g->nz, g->nx, g->lz, g->lx, g->h, omega, ref->rho0, ref->alpha0,
+                                     ref->beta0, W);
+  if ((rc = check_launch("k_green_deriv"))) return rc;
+  if ((rc = fft2_fp64(W, 6 * nf, g->lz, g->lx, tw, s))) return rc;
+  const double scale = g->h * g->h / (double(g->lz) * double(g->lx));
+  const dim3 tgrid((g->lx + 31) / 32, (g->lz + 31) / 32, 6 * nf), tblock(32, 8);
+  if (precision == DBI_C64)
+    k_scale_cast_t<float2><<<tgrid, tblock, 0, s>>>(W, static_cast<float2 *>(Dhat), g->lz, g->lx, scale);
+  else
+    k_scale_cast_t<double2><<<tgrid, tblock, 0, s>>>(W, static_cast<double2 *>(Dhat), g->lz, g->lx, scale);
+  return check_launch("k_scale_cast_t");
+}
 
 extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const double *omega,
                                int nf, int precision, void *Ghat, void *Gspace, void *work,

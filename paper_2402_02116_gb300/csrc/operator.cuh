@@ -38,6 +38,8 @@ struct OpArgs {
   void *out;            // device [B][2][nz][nx] complex
   void *T;              // device [B][2][lx][nz] complex scratch (column-major spectra)
   const void *Ghat;     // device [nf][3][lx][lz] complex (column-major)
+  const void *Dhat;     // device [nf][6][lx][lz] derivative tables: the paper-literal form (Eq. 9)
+                        // replaces the stencil pass (form_k.cu; T then holds [B][7][lx][nz])
   const void *tw;       // device twiddle table of the precision
   const int *active;    // device [B] (0 = skip the problem) or NULL
   const int *plist;     // device [nb]: the problems to run (launch slot -> problem), or NULL
@@ -62,6 +64,7 @@ struct OpArgs {
 int operator_parts(int nz, int lx, int precision);
 
 int run_operator(const OpArgs &a, cudaStream_t s);
+int run_form_k(const OpArgs &a, cudaStream_t s);
 
 // Per-problem power-of-two normalisers of B arrays of n elements each (or of the extents offs
 // gives, when non-NULL; complex of the precision, or real when `real` is set): scale[b] = 2^-e

@@ -21,6 +21,7 @@ from . import build as _build
 
 C64, C128 = 0, 1
 OP_GREENS, OP_CONVOLVE, OP_APPLY, OP_SOLVE, OP_FRECHET, OP_ADJOINT, OP_NORMAL_CG = range(7)
+OP_GREENS_K, OP_APPLY_K, OP_SOLVE_K = 7, 8, 9
 CONVERGED, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 
 
@@ -104,6 +105,12 @@ SIGNATURES = {
     "dbi_set_radix_plan": (c_int, [c_int, c_int, c_int]),
     "ls_solve": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
                          POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
+    "greens_tabulate_k": (c_int, [POINTER(Grid), POINTER(Medium), c_void_p, c_int, c_int, c_void_p, c_void_p,
+                                  c_size_t, c_void_p]),
+    "ls_apply_k": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                           c_void_p, c_size_t, c_void_p]),
+    "ls_solve_k": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p,
+                           POINTER(KrylovOpts), POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
     "frechet_apply": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, POINTER(Receivers),
                               c_void_p, c_void_p, POINTER(KrylovOpts), POINTER(Status), c_int, c_void_p,
                               c_size_t, c_void_p]),
@@ -353,6 +360,49 @@ def ls_solve(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, tol=1e
     _check(load().ls_solve(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(rhs), _ptr(u),
                            ctypes.byref(opts), ctypes.byref(st), precision, _ptr(work), n,
                            _stream(rhs.device)), "ls_solve")
+    return u, iters, relres, code
+
+
+def greens_tabulate_k(grid: Grid, ref: Medium, omega: torch.Tensor, precision: int = C64):
+    """Dhat [nf][6][lx][lz]: h^2/(lz lx) FFT of the central differences of G_h combined per stress
+    component (D1G11, D1G13, D3G11 + D1G13, D3G13 + D1G33, D3G13, D3G33), column-major (Eq. 9)."""
+    _need_cuda(omega)
+    dev = omega.device
+    nf = int(omega.numel())
+    Dhat = torch.empty((nf, 6, grid.lx, grid.lz), dtype=complex_dtype(precision), device=dev)
+    work, n = _work(grid, nf, precision, OP_GREENS_K, dev)
+    _check(load().greens_tabulate_k(ctypes.byref(grid), ctypes.byref(ref), _ptr(omega), nf, precision,
+                                    _ptr(Dhat), _ptr(work), n, _stream(dev)), "greens_tabulate_k")
+    return Dhat
+
+
+def ls_apply_k(grid: Grid, ref: Medium, m, omega, fidx, Ghat, Dhat, u, out=None):
+    """A u in the paper-literal form of Eq. 9 (the gradient on the Green's tensor)."""
+    precision = _precision(u)
+    _need_cuda(Ghat, Dhat, u)
+    model = _model(grid, ref, m, precision)
+    batch = _batch(omega, fidx)
+    out = torch.empty_like(u) if out is None else out
+    work, n = _work(grid, batch.B, precision, OP_APPLY_K, u.device)
+    _check(load().ls_apply_k(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(Dhat), _ptr(u),
+                             _ptr(out), precision, _ptr(work), n, _stream(u.device)), "ls_apply_k")
+    return out
+
+
+def ls_solve_k(grid: Grid, ref: Medium, m, omega, fidx, Ghat, Dhat, rhs, u0=None, tol=1e-6, max_iter=1000,
+               check_every=8):
+    """Solve A u = rhs with the operator of ls_apply_k; returns (u, iters, relres, code)."""
+    precision = _precision(rhs)
+    _need_cuda(Ghat, Dhat, rhs)
+    model = _model(grid, ref, m, precision)
+    batch = _batch(omega, fidx)
+    u = torch.empty_like(rhs) if u0 is None else u0.clone()
+    work, n = _work(grid, batch.B, precision, OP_SOLVE_K, rhs.device)
+    (iters, relres, code), st = _status(batch.B, rhs.device)
+    opts = _kopts(tol, max_iter, check_every, zero_guess=u0 is None)
+    _check(load().ls_solve_k(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(Dhat), _ptr(rhs),
+                             _ptr(u), ctypes.byref(opts), ctypes.byref(st), precision, _ptr(work), n,
+                             _stream(rhs.device)), "ls_solve_k")
     return u, iters, relres, code
 
 

@@ -66,6 +66,22 @@ class DeviceProblem:
         u, iters, relres, code = self.solve(self.incident(), m=m, tol=tol, max_iter=max_iter)
         return u, iters, relres, code
 
+    # paper-literal form of Eq. 9 (derivative tables tabulated on first use)
+    @property
+    def Dhat(self):
+        if getattr(self, "_Dhat", None) is None:
+            self._Dhat = dbi.greens_tabulate_k(self.grid, self.ref, self.omega, self.precision)
+        return self._Dhat
+
+    def apply_k(self, u, m=None):
+        return dbi.ls_apply_k(self.grid, self.ref, self.m if m is None else m, self.omega, self.fidx, self.Ghat,
+                              self.Dhat, u)
+
+    def solve_k(self, rhs, m=None, tol=None, max_iter=2000, check_every=8, u0=None):
+        tol = self.w.krylov_tol if tol is None else tol
+        return dbi.ls_solve_k(self.grid, self.ref, self.m if m is None else m, self.omega, self.fidx, self.Ghat,
+                              self.Dhat, rhs, u0=u0, tol=tol, max_iter=max_iter, check_every=check_every)
+
     def sample(self, u):
         d, _ = dbi.data_residual(self.grid, self.omega, self.fidx, self.rec_cells, u,
                                  torch.zeros((self.B, self.rec_cells.shape[0], 2), dtype=self.cdt, device=self.device))
