@@ -78,17 +78,18 @@ template <typename C> struct KTile {
   __device__ __forceinline__ Rl ms() const { return p.m_scale ? Rl(p.m_scale[0]) : Rl(1); }
 };
 
-// Shared memory of kk_rows_forward: staged u [2][ROWS + 2][nx + 2], one FFT line per row, one
-// transposition tile [LX][ROWS + 1].
+// Shared memory of kk_rows_forward: staged u [2][ROWS + 2][nx + 2], then one region that holds
+// the FFT lines of two sources [2][ROWS][LP] and, after the transform, their transposition tile
+// [2][LX][ROWS + 1].
 template <typename C, int LX> inline size_t kk_rows_forward_smem(int nx) {
   using RC = RowCfg<C, LX>;
-  return (size_t(2) * (RC::ROWS + 2) * (nx + 2) + size_t(RC::ROWS) * RC::LP + size_t(LX) * (RC::ROWS + 1)) *
-         sizeof(C);
+  const size_t region = std::max(size_t(2) * RC::ROWS * RC::LP, size_t(2) * LX * (RC::ROWS + 1));
+  return (size_t(2) * (RC::ROWS + 2) * (nx + 2) + region) * sizeof(C);
 }
 
 // The five sources of ROWS rows (w^2 drho u1, w^2 drho u3, sigma1, sigma5, sigma3 with
-// sigma = dC : eps(u)), one after another: zero-padded to LX, forward FFT along x, transposed
-// into T5[slot][c][kx][z].
+// sigma = dC : eps(u)), two at a time ((s1, s3), (sigma1, sigma5), sigma3): zero-padded to LX,
+// forward FFT along x, transposed into T5[slot][c][kx][z].
 template <typename C, int LX>
 __global__ void __launch_bounds__(kTileThreads) kk_rows_forward(KP<C> p) {
   using Rl = typename RealOf<C>::type;
@@ -99,9 +100,8 @@ __global__ void __launch_bounds__(kTileThreads) kk_rows_forward(KP<C> p) {
   const int z0 = blockIdx.x * ROWS, nz = p.nz, nx = p.nx, W = nx + 2;
   const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *su = reinterpret_cast<C *>(smem_raw);     // [2][RG][W]: u at rows z0 - 1 .. z0 + ROWS
-  C *lines = su + size_t(2) * RG * W;          // [ROWS][LP]
-  C *tile = lines + size_t(ROWS) * LP;         // [LX][RP]
+  C *su = reinterpret_cast<C *>(smem_raw);  // [2][RG][W]: u at rows z0 - 1 .. z0 + ROWS
+  C *R = su + size_t(2) * RG * W;           // FFT lines, then the transposition tile
   const size_t plane = size_t(nz) * nx;
   const C *u = p.in + size_t(b) * 2 * plane;
   const Rl isc = p.in_scale ? Rl(p.in_scale[b]) : Rl(1);
@@ -115,53 +115,66 @@ __global__ void __launch_bounds__(kTileThreads) kk_rows_forward(KP<C> p) {
   const double om = p.omega[f];
   const Rl w2 = Rl(om * om);
   auto U = [&](int c, int dz, int dx, int x) { return su[(c * RG + rr + 1 + dz) * W + x + 1 + dx]; };
+  auto dm = [&](int q, size_t cell) { return (__ldg(p.m + q * plane + cell) - p.ref[q]) * ms; };
+  // source c at column x of this thread's row (inside D)
+  auto source = [&](int c, int x) -> C {
+    const size_t cell = size_t(z) * nx + x;
+    if (c < 2) return cscale(U(c, 0, 0, x), w2 * dm(0, cell));
+    if (c == 3) {
+      const C e5 = cadd(csub(U(0, 1, 0, x), U(0, -1, 0, x)), csub(U(1, 0, 1, x), U(1, 0, -1, x)));
+      return cscale(e5, fh * dm(4, cell));
+    }
+    const C e1 = cscale(csub(U(0, 0, 1, x), U(0, 0, -1, x)), fh);
+    const C e3 = cscale(csub(U(1, 1, 0, x), U(1, -1, 0, x)), fh);
+    const Rl d13 = dm(2, cell);
+    return c == 2 ? cadd(cscale(e1, dm(1, cell)), cscale(e3, d13)) : cadd(cscale(e1, d13), cscale(e3, dm(3, cell)));
+  };
   const TwReg<C, LX> tr(t, p.tw);
   C *Tb = p.T5 + size_t(slot) * 5 * LX * nz;
-#pragma unroll 1
-  for (int c = 0; c < 5; ++c) {
-    C v[1][8];
+  auto pass = [&]<int NL>(int c0) {
+    C v[NL][8];
 #pragma unroll
-    for (int mm = 0; mm < 8; ++mm) {
-      const int x = t + mm * T;
-      C val = czero<C>();
-      if (mm < kHalf && z < nz && x < nx) {
-        const size_t cell = size_t(z) * nx + x;
-        if (c < 2) {
-          val = cscale(U(c, 0, 0, x), w2 * (__ldg(p.m + cell) - p.ref[0]) * ms);
-        } else {
-          const C e1 = cscale(csub(U(0, 0, 1, x), U(0, 0, -1, x)), fh);
-          const C e3 = cscale(csub(U(1, 1, 0, x), U(1, -1, 0, x)), fh);
-          if (c == 3) {
-            const C e5 = cscale(cadd(csub(U(0, 1, 0, x), U(0, -1, 0, x)), csub(U(1, 0, 1, x), U(1, 0, -1, x))), fh);
-            val = cscale(e5, (__ldg(p.m + 4 * plane + cell) - p.ref[4]) * ms);
-          } else {
-            const Rl d13 = (__ldg(p.m + 2 * plane + cell) - p.ref[2]) * ms;
-            const Rl dd = c == 2 ? (__ldg(p.m + 1 * plane + cell) - p.ref[1]) * ms
-                                 : (__ldg(p.m + 3 * plane + cell) - p.ref[3]) * ms;
-            val = c == 2 ? cadd(cscale(e1, dd), cscale(e3, d13)) : cadd(cscale(e1, d13), cscale(e3, dd));
-          }
-        }
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+      for (int mm = 0; mm < 8; ++mm) {
+        const int x = t + mm * T;
+        v[l][mm] = (mm < kHalf && z < nz && x < nx) ? source(c0 + l, x) : czero<C>();
       }
-      v[0][mm] = val;
-    }
-    C *const ln[1] = {lines + size_t(rr) * LP};
-    RegPlan<LX>::template run<C, 1, false, true>(v, ln, t, tr, RowSync<T>{1 + rr});
-    __syncthreads();  // the previous source's tile has been stored
+    C *ln[NL];
 #pragma unroll
-    for (int mm = 0; mm < 8; ++mm) tile[size_t(t + mm * T) * RP + rr] = v[0][mm];
+    for (int l = 0; l < NL; ++l) ln[l] = R + size_t(l * ROWS + rr) * LP;
+    RegPlan<LX>::template run<C, NL, false, true>(v, reinterpret_cast<C *const(&)[NL]>(ln), t, tr,
+                                                  RowSync<T>{1 + rr});
+    __syncthreads();  // every row is done with its lines: the region becomes the tile
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+      for (int mm = 0; mm < 8; ++mm) R[(size_t(l) * LX + t + mm * T) * RP + rr] = v[l][mm];
     __syncthreads();
-    C *Tc = Tb + size_t(c) * LX * nz;
-    for (int idx = threadIdx.x; idx < LX * ROWS; idx += kTileThreads) {
-      const int r = idx % ROWS, kx = idx / ROWS;
-      if (z0 + r < nz) Tc[size_t(kx) * nz + z0 + r] = tile[size_t(kx) * RP + r];
+    C *Tc = Tb + size_t(c0) * LX * nz;
+    for (int idx = threadIdx.x; idx < NL * LX * ROWS; idx += kTileThreads) {
+      const int r = idx % ROWS, ck = idx / ROWS;  // ck = l * LX + kx
+      if (z0 + r < nz) Tc[size_t(ck) * nz + z0 + r] = R[size_t(ck) * RP + r];
     }
-  }
+    __syncthreads();  // the tile has been stored before the next lines overwrite it
+  };
+  pass.template operator()<2>(0);
+  pass.template operator()<2>(2);
+  pass.template operator()<1>(4);
 }
 
-// For CC columns kx: each source's column, forward FFT along z, times its two kernel entries,
-// summed into the two outputs; inverse FFT of the sums; keep z < nz -> T2[slot][i][kx][z].
+// For CC columns kx: the sources' columns (two at a time in complex64), forward FFT along z, times their two
+// kernel entries, summed into the two outputs; inverse FFT of the sums; keep z < nz ->
+// T2[slot][i][kx][z].
+// Lines per forward column FFT: complex64 may pair the sources (two CTAs per SM either way);
+// complex128 transforms one line at a time (two would not fit in the register file).
+#ifndef DBI_KCOLS_LINES
+#define DBI_KCOLS_LINES 2
+#endif
+template <typename C> constexpr int kKColsLines = sizeof(C) == 8 ? DBI_KCOLS_LINES : 1;
+
 template <typename C, int LZ>
-__global__ void __launch_bounds__(kTileThreads) kk_cols(KP<C> p) {
+__global__ void __launch_bounds__(kTileThreads, sizeof(C) == 8 ? 2 : 1) kk_cols(KP<C> p) {
   using CF = ColCfg<C, LZ>;
   constexpr int CC = CF::CC, T = CF::T, LP = CF::LP;
   const int b = kproblem(p), f = p.fidx[b], slot = blockIdx.y;
@@ -182,27 +195,57 @@ __global__ void __launch_bounds__(kTileThreads) kk_cols(KP<C> p) {
 #pragma unroll
   for (int mm = 0; mm < 8; ++mm) acc[0][mm] = acc[1][mm] = czero<C>();
   const C *Tb = p.T5 + size_t(slot) * 5 * lx * nz;
-#pragma unroll 1
-  for (int c = 0; c < 5; ++c) {
-    const C *src = Tb + (size_t(c) * lx + kx) * nz;
-    C v[1][8];
+  C *const lines[2] = {smem + size_t(col) * LP, smem + size_t(CC + col) * LP};
+  auto pass = [&]<int NL>(int c0) {
+    C v[NL][8];
 #pragma unroll
-    for (int mm = 0; mm < 8; ++mm) {
-      const int z = t + mm * T;
-      v[0][mm] = (mm < kHalf && live && z < nz) ? src[z] : czero<C>();
-    }
-    C *const ln[1] = {smem + size_t(col) * LP};
-    RegPlan<LZ>::template run<C, 1, false, true>(v, ln, t, tr, RowSync<T>{1 + col});
-    if (live) {
+    for (int l = 0; l < NL; ++l) {
+      const C *src = Tb + (size_t(c0 + l) * lx + kx) * nz;
 #pragma unroll
       for (int mm = 0; mm < 8; ++mm) {
-        const int kz = t + mm * T;
-        acc[0][mm] = cadd(acc[0][mm], cmul(__ldg(e0[c] + kz), v[0][mm]));
-        acc[1][mm] = cadd(acc[1][mm], cmul(__ldg(e1[c] + kz), v[0][mm]));
+        const int z = t + mm * T;
+        v[l][mm] = (mm < kHalf && live && z < nz) ? src[z] : czero<C>();
+      }
+    }
+    RegPlan<LZ>::template run<C, NL, false, true>(v, reinterpret_cast<C *const(&)[NL]>(lines), t, tr,
+                                                  RowSync<T>{1 + col});
+    if (live) {
+#pragma unroll
+      for (int l = 0; l < NL; ++l)
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+          const int kz = t + mm * T;
+          acc[0][mm] = cadd(acc[0][mm], cmul(__ldg(e0[c0 + l] + kz), v[l][mm]));
+          acc[1][mm] = cadd(acc[1][mm], cmul(__ldg(e1[c0 + l] + kz), v[l][mm]));
+        }
+    }
+  };
+  if constexpr (kKColsLines<C> == 2) {
+    pass.template operator()<2>(0);
+    pass.template operator()<2>(2);
+    pass.template operator()<1>(4);
+  } else {
+#pragma unroll 1
+    for (int c = 0; c < 5; ++c) {
+      const C *src = Tb + (size_t(c) * lx + kx) * nz;
+      C v[1][8];
+#pragma unroll
+      for (int mm = 0; mm < 8; ++mm) {
+        const int z = t + mm * T;
+        v[0][mm] = (mm < kHalf && live && z < nz) ? src[z] : czero<C>();
+      }
+      C *const ln[1] = {lines[0]};
+      RegPlan<LZ>::template run<C, 1, false, true>(v, ln, t, tr, RowSync<T>{1 + col});
+      if (live) {
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+          const int kz = t + mm * T;
+          acc[0][mm] = cadd(acc[0][mm], cmul(__ldg(e0[c] + kz), v[0][mm]));
+          acc[1][mm] = cadd(acc[1][mm], cmul(__ldg(e1[c] + kz), v[0][mm]));
+        }
       }
     }
   }
-  C *const lines[2] = {smem + size_t(col) * LP, smem + size_t(CC + col) * LP};
   RegPlan<LZ>::template run<C, 2, true>(acc, lines, t, tr, RowSync<T>{1 + col});
   if (live) {
     C *o = p.T2 + size_t(slot) * 2 * lx * nz;
