@@ -613,9 +613,16 @@ def run_formk(args):
     cols_s = cols_ms * 1e-3
     flops = formk_cols_flops_per_cell_apply(w) * cells * args.steps
     algo_bytes = formk_cols_bytes_per_cell_apply(w) * cells * args.steps
+    # DRAM bytes per launch from one ncu capture of kk_cols over 32 wavefields of this grid (8
+    # frequencies): 373.98 MB, of which the nine kernel tables are 151 MB; the rest grows with the
+    # wavefields a launch processes
+    traffic = None
+    if (w.nz, w.nx, w.lz, w.lx, w.nf) == (256, 256, 512, 512, 8):
+        tables = 9 * w.lz * w.lx * 8 * w.nf
+        traffic = tables + (373.98e6 - tables) / 32 * cells * args.steps / (w.nz * w.nx) / max(cols_launches, 1)
     roof = {"bound": "alu", "achieved": flops / cols_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
             "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured median)",
-            "traffic": None, "kernel": "kk_cols (five forward column FFTs, 2 x 5 kernel, two inverse)",
+            "traffic": traffic, "kernel": "kk_cols (five forward column FFTs, 2 x 5 kernel, two inverse)",
             "hbm_frac_of_algorithmic_bytes": algo_bytes / cols_s / (peaks.get("hbm_gbs", 6800.0) * 1e9),
             "launches_timed": cols_launches, "avg_launch_ms": cols_ms / max(cols_launches, 1),
             "share_of_step_time": cols_ms / ms_k if ms_k > 0 else None}
