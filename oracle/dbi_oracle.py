@@ -21,7 +21,8 @@ leaves unstated):
   * LS operator (Eq. 10, 11): A u = u - h^2 sum_x' G_h(x - x') s(x'),
     s = w^2 drho u + div(dC : eps(u)).
   * Convolution by FFT on a zero-padded lz x lx grid (Eq. 12), lz >= 2 nz - 1, lx >= 2 nx - 1.
-  * Krylov: BiCGSTAB with <a, b> = sum conj(a) b, x0 = 0, shadow residual r0.
+  * Krylov: BiCGSTAB with <a, b> = sum conj(a) b, x0 = 0, shadow residual r0; and restarted
+    GMRES(m), the solver of the paper's experiments (restart length unstated: m = 30 by default).
   * Frechet (Eq. 20, 26-31): J dm = P A_b^{-1} G (w^2 dm_rho u_b + div(dC(dm) : eps(u_b))), the two
     virtual sources Y and M of Eq. 26 merged into one source by linearity.
   * Adjoint (Eq. 25, 32-35): u_a = A_b^{-1} G P^T conj(r);
@@ -330,6 +331,86 @@ def bicgstab(apply, b, tol=1e-12, maxiter=2000, x0=None):
 
 # ---------------------------------------------------------------------------------------------
 # The LS problem on one grid with a set of frequencies
+def givens(a, b):
+    """Complex plane rotation [[c, s], [-conj(s), c]] (c real) that maps (a, b) to (r, 0)."""
+    if b == 0:
+        return 1.0, 0.0 + 0.0j, a
+    if a == 0:
+        return 0.0, np.conj(b) / abs(b), abs(b)
+    t = math.hypot(abs(a), abs(b))
+    phase = a / abs(a)
+    return abs(a) / t, phase * np.conj(b) / t, phase * t
+
+
+def gmres(apply, b, restart=30, tol=1e-12, maxiter=2000, x0=None):
+    """Restarted GMRES(m) (Saad and Schultz 1986), <a, b> = sum conj(a) b.
+
+    One cycle from x0 with r0 = b - A x0, beta = ||r0||: Arnoldi with modified Gram-Schmidt builds
+    the orthonormal basis v_1 = r0 / beta, v_2, ... of the Krylov space and the Hessenberg matrix
+    H with A V_k = V_(k+1) H_k; the iterate x0 + V_k y minimises ||beta e_1 - H_k y||, which equals
+    ||b - A x|| over x0 + span(V_k). Plane rotations reduce H_k to triangular form as it grows, so
+    the minimal residual after k steps is the last entry |g_(k+1)| of the rotated right-hand side.
+    A cycle stops after `restart` steps, when |g_(k+1)| <= tol ||b||, or when the new basis
+    vector vanishes (the solution lies in the space built so far); then y is found by back
+    substitution, x = x0 + V_k y, and the next cycle starts from x.
+
+    Returns (x, info): iters = Arnoldi steps (operator applications inside the cycles), relres =
+    the true relative residual of the returned x, resvec = the minimal residual after every step
+    (relative to ||b||), converged."""
+    x = np.zeros_like(b) if x0 is None else x0.astype(np.complex128).copy()
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros_like(b), dict(iters=0, relres=0.0, resvec=[], converged=True)
+    it = 0
+    resvec = []
+    converged = False
+    while True:
+        r = b - apply(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * bnorm:
+            converged = True
+            break
+        if it >= maxiter:
+            break
+        V = [r / beta]
+        H = np.zeros((restart + 1, restart), dtype=np.complex128)
+        cs = np.zeros(restart)
+        sn = np.zeros(restart, dtype=np.complex128)
+        g = np.zeros(restart + 1, dtype=np.complex128)
+        g[0] = beta
+        k = 0
+        for j in range(restart):
+            if it >= maxiter:
+                break
+            w = apply(V[j])
+            it += 1
+            for i in range(j + 1):
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            hn = np.linalg.norm(w)
+            H[j + 1, j] = hn
+            for i in range(j):  # earlier rotations on the new column
+                hi, hi1 = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * hi + sn[i] * hi1
+                H[i + 1, j] = -np.conj(sn[i]) * hi + cs[i] * hi1
+            cs[j], sn[j], H[j, j] = givens(H[j, j], H[j + 1, j])
+            H[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(sn[j]) * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            resvec.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) <= tol * bnorm or hn == 0.0:
+                break
+            V.append(w / hn)
+        y = np.zeros(k, dtype=np.complex128)
+        for i in range(k - 1, -1, -1):  # back substitution with the triangular H
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        for i in range(k):
+            x = x + y[i] * V[i]
+    relres = np.linalg.norm(b - apply(x)) / bnorm
+    return x, dict(iters=it, relres=float(relres), resvec=resvec, converged=bool(converged))
+
+
 # ---------------------------------------------------------------------------------------------
 class LSOracle:
     """Discrete LS operator, forward solves and distorted-Born products for one grid.
@@ -384,6 +465,13 @@ class LSOracle:
         shape = rhs.shape
         return bicgstab(lambda v: self.apply(v.reshape(shape), model, f).reshape(-1),
                         rhs.reshape(-1), tol=tol, maxiter=maxiter)[0].reshape(shape)
+
+    def solve_gmres(self, rhs, model, f, restart=30, tol=1e-12, maxiter=3000):
+        """A u = rhs by GMRES(restart), the paper's Krylov solver; returns (u, info)."""
+        shape = rhs.shape
+        x, info = gmres(lambda v: self.apply(v.reshape(shape), model, f).reshape(-1), rhs.reshape(-1),
+                        restart=restart, tol=tol, maxiter=maxiter)
+        return x.reshape(shape), info
 
     def solve_info(self, rhs, model, f, tol=1e-12, maxiter=3000):
         shape = rhs.shape
