@@ -12,6 +12,7 @@ second of wall time on the device.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --workload uneven40     # the 40-problem uneven batch (grids 64^2 .. 512^2)
     python bench.py --workload formk256     # operator passes in the paper-literal form of Eq. 9
+    python bench.py --workload gmres256     # batched forward solves by GMRES(30) beside BiCGSTAB
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own 32 sources x 8 frequencies
 (weak scaling) and the gradients are summed across ranks with one all-reduce per step.
@@ -53,12 +54,14 @@ def parse_args():
     ap.add_argument("--check-every", type=int, default=4,
                     help="BiCGSTAB iterations between host convergence checks (each check also "
                          "compacts the launches to the problems still active)")
-    ap.add_argument("--workload", choices=["vti256", "uneven40", "formk256"], default="vti256",
+    ap.add_argument("--workload", choices=["vti256", "uneven40", "formk256", "gmres256"], default="vti256",
                     help="vti256: the gradient step of the benchmark (default); uneven40: operator "
                          "passes over the 40-problem uneven batch (persistent launches, autotuned), "
                          "plus one graph-captured solve; formk256: operator passes over the 256^2 "
                          "batch in the paper-literal form (derivatives on G, Eq. 9) beside the "
-                         "divergence form")
+                         "divergence form; gmres256: batched forward solves of the 256^2 batch by "
+                         "restarted GMRES beside BiCGSTAB")
+    ap.add_argument("--restart", type=int, default=30, help="GMRES restart length (gmres256)")
     ap.add_argument("--sources", type=int, default=32,
                     help="sources per GPU (32 is the benchmark workload; fewer make a smaller batch "
                          "of the same grid for profiler captures)")
@@ -645,6 +648,68 @@ def run_formk(args):
     print(json.dumps(result), flush=True)
 
 
+def run_gmres(args):
+    """Forward solves of the 256 x 256 VTI batch (32 sources x 8 frequencies) to 1e-5 from the
+    incident fields, one step = one batched solve: restarted GMRES (the paper's solver) and then
+    BiCGSTAB on the same right-hand sides. The metric counts the operator passes each solver made
+    (Arnoldi steps for GMRES, two per iteration for BiCGSTAB) times the cells, per second."""
+    import torch
+    from paper_2402_02116_gb300 import build, dbi
+    from paper_2402_02116_gb300.problem import DeviceProblem
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    build.build()
+    dbi.load()
+    w = workload(0, 1, args.sources)
+    P = DeviceProblem(w, dbi.C64, device=dev)
+    u0 = P.incident()
+    cells = w.nz * w.nx
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = dbi.kernel_launches()
+        dbi.profile_begin(dbi.PROF_OPERATOR)
+        with ClockSampler(gpu_id(dev)) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            outs = [fn() for _ in range(args.steps)]
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        op_ms, op_n = dbi.profile_end()
+        return ev0.elapsed_time(ev1), dbi.kernel_launches() - n0, op_ms, op_n, clk.summary(), outs[-1]
+
+    ms_g, launches_g, op_ms_g, op_n_g, clocks, (u_g, it_g, rr_g, code_g) = timed(
+        lambda: P.solve_gmres(u0, restart=args.restart, tol=TOL, max_iter=MAX_ITER, check_every=args.check_every))
+    ms_b, launches_b, op_ms_b, _, clocks_b, (u_b, it_b, rr_b, code_b) = timed(
+        lambda: P.solve(u0, tol=TOL, max_iter=MAX_ITER, check_every=args.check_every))
+    passes_g = int(it_g.sum()) + int(((it_g + args.restart - 1) // args.restart).sum())  # + restart residuals
+    passes_b = 2 * int(it_b.sum())
+    value = passes_g * cells * args.steps / (ms_g * 1e-3)
+    agree = float(torch.linalg.norm(u_g - u_b) / torch.linalg.norm(u_b))
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_g / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 (fp32 complex operator and basis; fp64 Hessenberg, rotations, reductions)",
+        "data": "synthetic (seeded VTI model with layers and anomalies)",
+        "config": {"workload": f"gmres: {w.name}, one batched forward solve to {TOL:g} by GMRES({args.restart})",
+                   "nz": w.nz, "nx": w.nx, "lz": w.lz, "lx": w.lx, "wavefields": P.B,
+                   "l2": f"inputs larger than L2: {P.B * cells * 16 / 1e9:.2f} GB per field"},
+        "gpu_launches": int(launches_g), "gpu_launches_per_step": launches_g / args.steps, "clocks": clocks,
+        "gmres": {"solve_ms": ms_g / args.steps, "arnoldi_steps_mean": float(it_g.float().mean()),
+                  "arnoldi_steps_max": int(it_g.max()), "operator_passes": passes_g,
+                  "operator_share": op_ms_g / ms_g, "all_converged": bool((code_g == dbi.CONVERGED).all())},
+        "bicgstab": {"solve_ms": ms_b / args.steps, "iterations_mean": float(it_b.float().mean()),
+                     "operator_passes": passes_b, "operator_share": op_ms_b / ms_b,
+                     "cell_applies_per_s": passes_b * cells * args.steps / (ms_b * 1e-3),
+                     "all_converged": bool((code_b == dbi.CONVERGED).all()), "clocks": clocks_b},
+        "solutions_relative_difference": agree,
+    }
+    print(json.dumps(result), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -653,6 +718,8 @@ def main():
         run_uneven(args)
     elif args.workload == "formk256":
         run_formk(args)
+    elif args.workload == "gmres256":
+        run_gmres(args)
     else:
         run_ours(args)
 

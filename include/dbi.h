@@ -179,6 +179,29 @@ int ls_solve(const dbi_model *model, const dbi_batch *batch, const void *Ghat, c
              void *work, size_t work_bytes, dbi_stream stream);
 
 /*
+ * dbi_gmres_workspace_bytes -- work-buffer size of ls_solve_gmres for B problems on grid g with
+ *   restart length `restart` (1..64): the operator scratch plus restart + 1 basis vectors per
+ *   problem. Returns 0 for invalid arguments.
+ */
+size_t dbi_gmres_workspace_bytes(const dbi_grid *g, int B, int precision, int restart);
+
+/*
+ * ls_solve_gmres -- solves A u = rhs (Eq. 11) for every problem by restarted GMRES(restart), the
+ *   Krylov method of the paper's experiments: Arnoldi basis by classical Gram-Schmidt with one
+ *   re-orthogonalisation, complex plane rotations on the Hessenberg matrix, minimal-residual
+ *   iterate at the end of each cycle. Basis vectors in the precision's complex type; Hessenberg
+ *   matrix, rotations, inner products and norms in FP64. A problem stops when the minimal
+ *   residual of its cycle is <= opts->tol ||rhs||, when its new basis vector vanishes, or after
+ *   opts->max_iter Arnoldi steps in all. rhs, u: device [B][2][nz][nx] complex (distinct); u holds
+ *   the initial guess unless opts->zero_guess. status: iters = Arnoldi steps (operator passes
+ *   inside the cycles), relres = the last minimal residual / ||rhs||, code. Synchronises the
+ *   stream every opts->check_every steps and at every restart. Work: dbi_gmres_workspace_bytes.
+ */
+int ls_solve_gmres(const dbi_model *model, const dbi_batch *batch, const void *Ghat, const void *rhs,
+                   void *u, const dbi_krylov_opts *opts, int restart, const dbi_status *status,
+                   int precision, void *work, size_t work_bytes, dbi_stream stream);
+
+/*
  * greens_tabulate_k -- the derivative tables of the paper-literal form of the LS equation (Eq. 9,
  *   the gradient acting on the Green's tensor instead of on the stress): central differences
  *   (D_k G)(y) = [G_h(y + h e_k) - G_h(y - h e_k)] / 2h of the same lattice G_h as greens_tabulate

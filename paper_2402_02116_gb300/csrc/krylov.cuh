@@ -39,6 +39,9 @@ SolverBufs carve_solver_fields(Arena &ar, size_t field_bytes, int B);
 // Validates Krylov options (tol >= 0, max_iter >= 0, check_every >= 0).
 int check_krylov(const dbi_krylov_opts *o);
 
+// plist = the problems b < B with active[b] != 0 in ascending order, *count = how many (device).
+int compact_active(int B, const int *active, int *plist, int *count, cudaStream_t s);
+
 // use_graph (uneven batches only): the iterations between two host checks are captured once as
 // a CUDA graph and replayed.
 int run_bicgstab(OpArgs op, const SolverBufs &sb, const void *rhs, void *x, bool x_zero,

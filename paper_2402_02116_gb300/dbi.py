@@ -105,6 +105,9 @@ SIGNATURES = {
     "dbi_set_radix_plan": (c_int, [c_int, c_int, c_int]),
     "ls_solve": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
                          POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
+    "dbi_gmres_workspace_bytes": (c_size_t, [POINTER(Grid), c_int, c_int, c_int]),
+    "ls_solve_gmres": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
+                               c_int, POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
     "greens_tabulate_k": (c_int, [POINTER(Grid), POINTER(Medium), c_void_p, c_int, c_int, c_void_p, c_void_p,
                                   c_size_t, c_void_p]),
     "ls_apply_k": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p, c_int,
@@ -360,6 +363,31 @@ def ls_solve(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, tol=1e
     _check(load().ls_solve(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(rhs), _ptr(u),
                            ctypes.byref(opts), ctypes.byref(st), precision, _ptr(work), n,
                            _stream(rhs.device)), "ls_solve")
+    return u, iters, relres, code
+
+
+def gmres_workspace_bytes(grid: Grid, B: int, precision: int, restart: int) -> int:
+    return int(load().dbi_gmres_workspace_bytes(ctypes.byref(grid), B, precision, restart))
+
+
+def ls_solve_gmres(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, restart=30, tol=1e-6,
+                   max_iter=1000, check_every=8):
+    """Solve A u = rhs by restarted GMRES(restart); returns (u, iters, relres, code), iters in Arnoldi
+    steps (operator passes inside the cycles)."""
+    precision = _precision(rhs)
+    _need_cuda(Ghat, rhs)
+    model = _model(grid, ref, m, precision)
+    batch = _batch(omega, fidx)
+    u = torch.empty_like(rhs) if u0 is None else u0.clone()
+    n = gmres_workspace_bytes(grid, batch.B, precision, restart)
+    if n == 0 and batch.B > 0:
+        raise DBIError(f"invalid GMRES workspace query (restart {restart})")
+    work = torch.empty(max(n, 1), dtype=torch.uint8, device=rhs.device)
+    (iters, relres, code), st = _status(batch.B, rhs.device)
+    opts = _kopts(tol, max_iter, check_every, zero_guess=u0 is None)
+    _check(load().ls_solve_gmres(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(rhs), _ptr(u),
+                                 ctypes.byref(opts), int(restart), ctypes.byref(st), precision, _ptr(work), n,
+                                 _stream(rhs.device)), "ls_solve_gmres")
     return u, iters, relres, code
 
 

@@ -66,6 +66,11 @@ class DeviceProblem:
         u, iters, relres, code = self.solve(self.incident(), m=m, tol=tol, max_iter=max_iter)
         return u, iters, relres, code
 
+    def solve_gmres(self, rhs, m=None, restart=30, tol=None, max_iter=2000, check_every=8, u0=None):
+        tol = self.w.krylov_tol if tol is None else tol
+        return dbi.ls_solve_gmres(self.grid, self.ref, self.m if m is None else m, self.omega, self.fidx, self.Ghat,
+                                  rhs, u0=u0, restart=restart, tol=tol, max_iter=max_iter, check_every=check_every)
+
     # paper-literal form of Eq. 9 (derivative tables tabulated on first use)
     @property
     def Dhat(self):
