@@ -685,7 +685,8 @@ def run_gmres(args):
         lambda: P.solve_gmres(u0, restart=args.restart, tol=TOL, max_iter=MAX_ITER, check_every=args.check_every))
     ms_b, launches_b, op_ms_b, _, clocks_b, (u_b, it_b, rr_b, code_b) = timed(
         lambda: P.solve(u0, tol=TOL, max_iter=MAX_ITER, check_every=args.check_every))
-    passes_g = int(it_g.sum()) + int(((it_g + args.restart - 1) // args.restart).sum())  # + restart residuals
+    # Arnoldi steps plus the residual pass of every restart (the first cycle starts from x = 0)
+    passes_g = int(it_g.sum()) + int(((it_g - 1).clamp(min=0) // args.restart).sum())
     passes_b = 2 * int(it_b.sum())
     value = passes_g * cells * args.steps / (ms_g * 1e-3)
     agree = float(torch.linalg.norm(u_g - u_b) / torch.linalg.norm(u_b))

@@ -4,12 +4,19 @@
 // A cycle (Saad and Schultz's GMRES, <a, b> = sum conj(a) b) from the iterate x:
 //   v_0 = (b - A x) / beta, beta = ||b - A x||      operator + k_gm_residual, k_gm_begin, k_gm_scale_v
 //   step j = 0 .. m-1 (every problem still active):
-//     w = A v_j                                      operator, written into the slot of v_(j+1)
-//     two rounds of classical Gram-Schmidt           k_gm_dots (h_i = <v_i, w>), k_gm_hsum,
-//       (the second one re-orthogonalises)           k_gm_update (w -= sum h_i v_i, ||w||^2)
+//     w = K v_j (A = I - K)                          operator without its identity term, into the
+//                                                     slot of v_(j+1); then column j of H for A is
+//                                                     e_j - <V, K v_j> and v_(j+1) = -w' / ||w'||
+//     classical Gram-Schmidt                          k_gm_dots (h_i = <v_i, w>, ||w||^2), k_gm_hsum,
+//                                                     k_gm_update (w -= sum h_i v_i, ||w||^2)
+//     a second round where the first one removed     k_gm_need2, then the same three kernels
+//       more than half of the norm (Kahan-Parlett: ||w'|| < 0.7 ||w||; "twice is enough").
+//       Orthogonalising K v_j rather than A v_j = v_j - K v_j (the same Krylov space) keeps the
+//       first round from cancelling the v_j component that dominates A v_j, so the second round
+//       is rarely needed.
 //     h_(j+1,j) = ||w||, plane rotations on the new Hessenberg column, the minimal residual
 //       |g_(j+1)|, convergence and iteration limits   k_gm_close
-//     v_(j+1) = w / h_(j+1,j)                        k_gm_scale_v
+//     v_(j+1) = -w' / h_(j+1,j)                      k_gm_scale_v
 //   y from the triangular system R y = g, x += V y   k_gm_solve_y, k_gm_update_x
 // The basis vectors are stored in the precision of the operator; the Hessenberg matrix, the
 // rotations, every inner product and norm are FP64 and every reduction is two-stage and
@@ -31,13 +38,18 @@ constexpr int kDotGroups = kGmresMaxRestart / kDotGroup;
 struct GState {
   double bnorm2;  // ||scaled rhs||^2
   double res;     // minimal residual |g_(k+1)| of the current cycle (scaled system)
-  double hn_inv;  // 1 / h_(j+1,j) of the last step (1 / beta at the start of a cycle)
+  double hn_inv;  // -1 / h_(j+1,j) of the last step (1 / beta at the start of a cycle)
   int iters;      // Arnoldi steps so far
   int code;
   int k;          // steps of the current cycle
   int kx;         // steps of the finished cycle to fold into x
-  int incycle, zero_rhs, pad[2];
+  int incycle, zero_rhs;
+  double wpre2;  // ||A v_j||^2 before the Gram-Schmidt rounds
+  int need2;     // this step re-orthogonalises
+  int pad;
 };
+
+constexpr int kDotSlots = 2 * kDotGroup + 2;  // per partial: 8 complex inner products, ||w||^2, pad
 
 struct GmresBufs {
   void *V;         // [m + 1][B][n] basis vectors
@@ -49,7 +61,7 @@ struct GmresBufs {
   double2 *hc;     // [B][m + 1] coefficients of the current Gram-Schmidt round
   double2 *y;      // [B][m] cycle solution
   double *scale;   // [B] power-of-two scale of the system
-  double *partD;   // [B][kDotGroups][kRedBlocks][2 kDotGroup] inner-product partials
+  double *partD;   // [B][kDotGroups][kRedBlocks][kDotSlots] inner-product partials
   double *partN;   // [B][kRedBlocks][kRedSlots] norm partials
   int *active, *plist, *count;
 };
@@ -60,7 +72,7 @@ size_t gmres_bytes(const dbi_grid *g, int B, int precision, int m) {
                        2 * align256(size_t(B) * (m + 1) * sizeof(double2)) +
                        align256(size_t(B) * m * sizeof(double)) + 2 * align256(size_t(B) * m * sizeof(double2)) +
                        align256(size_t(B) * sizeof(double));
-  const size_t parts = align256(size_t(B) * kDotGroups * kRedBlocks * 2 * kDotGroup * sizeof(double)) +
+  const size_t parts = align256(size_t(B) * kDotGroups * kRedBlocks * kDotSlots * sizeof(double)) +
                        bytes_partials(B);
   return size_t(m + 1) * f + small + parts + 2 * align256(size_t(B) * sizeof(int)) + 256;
 }
@@ -77,7 +89,7 @@ static GmresBufs carve_gmres(Arena &ar, const dbi_grid *g, int B, int precision,
   gb.sn = static_cast<double2 *>(ar.take(size_t(B) * m * sizeof(double2)));
   gb.y = static_cast<double2 *>(ar.take(size_t(B) * m * sizeof(double2)));
   gb.scale = static_cast<double *>(ar.take(size_t(B) * sizeof(double)));
-  gb.partD = static_cast<double *>(ar.take(size_t(B) * kDotGroups * kRedBlocks * 2 * kDotGroup * sizeof(double)));
+  gb.partD = static_cast<double *>(ar.take(size_t(B) * kDotGroups * kRedBlocks * kDotSlots * sizeof(double)));
   gb.partN = static_cast<double *>(ar.take(bytes_partials(B)));
   gb.active = static_cast<int *>(ar.take(size_t(B) * sizeof(int)));
   gb.plist = static_cast<int *>(ar.take(size_t(B) * sizeof(int)));
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(kRedThreads) k_gm_residual(Span sp, const int 
     bb += bi.x * bi.x + bi.y * bi.y;
     rr += ri.x * ri.x + ri.y * ri.y;
   }
-  double acc[2] = {double(bb), double(rr)};
+  A acc[2] = {bb, rr};
   block_sum_store<2>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
 
@@ -172,80 +184,114 @@ __global__ void __launch_bounds__(kRedThreads) k_gm_scale_v(Span sp, const int *
   DBI_PROBLEM_LOOP(sp) v[off + i] = cscale(v[off + i], f);
 }
 
-// Partials of h_i = <v_i, w> for the basis vectors i of group blockIdx.z (i <= j), w = v_(j+1).
+// Partials of h_i = <v_i, w> for the basis vectors i of group blockIdx.z (i <= j), w = v_(j+1),
+// and (group 0 of round 0) of ||w||^2. Round 1 runs only for the problems that re-orthogonalise.
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_gm_dots(Span sp, const int *plist, const int *active,
-                                                         const C *__restrict__ V, size_t vstride, int j,
-                                                         double *partD) {
+                                                         const GState *st, const C *__restrict__ V,
+                                                         size_t vstride, int j, int round, double *partD) {
   using A = typename Acc<C>::type;
   const int b = problem_at(plist, blockIdx.y);
-  if (!active[b]) return;
+  if (!active[b] || (round == 1 && !st[b].need2)) return;
   const int i0 = blockIdx.z * kDotGroup;
   const int nv = min(kDotGroup, j + 1 - i0);
+  const bool norm = round == 0 && blockIdx.z == 0;
   const C *w = V + size_t(j + 1) * vstride;
-  A re[kDotGroup], im[kDotGroup];
+  A re[kDotGroup], im[kDotGroup], ww = 0;
 #pragma unroll
   for (int q = 0; q < kDotGroup; ++q) re[q] = im[q] = 0;
   DBI_PROBLEM_LOOP(sp) {
     const C wi = w[off + i];
+    C v[kDotGroup];
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) v[q] = q < nv ? V[size_t(i0 + q) * vstride + off + i] : czero<C>();
 #pragma unroll
     for (int q = 0; q < kDotGroup; ++q) {
-      if (q < nv) {
-        const C vi = V[size_t(i0 + q) * vstride + off + i];
-        re[q] += vi.x * wi.x + vi.y * wi.y;  // conj(v) w
-        im[q] += vi.x * wi.y - vi.y * wi.x;
-      }
+      re[q] += v[q].x * wi.x + v[q].y * wi.y;  // conj(v) w
+      im[q] += v[q].x * wi.y - v[q].y * wi.x;
     }
+    if (norm) ww += wi.x * wi.x + wi.y * wi.y;
   }
-  double acc[2 * kDotGroup];
+  A acc[kDotSlots];
 #pragma unroll
   for (int q = 0; q < kDotGroup; ++q) {
-    acc[2 * q] = double(re[q]);
-    acc[2 * q + 1] = double(im[q]);
+    acc[2 * q] = re[q];
+    acc[2 * q + 1] = im[q];
   }
-  block_sum_store<2 * kDotGroup>(
-      acc, partD + ((size_t(b) * kDotGroups + blockIdx.z) * kRedBlocks + blockIdx.x) * (2 * kDotGroup));
+  acc[2 * kDotGroup] = ww;
+  acc[2 * kDotGroup + 1] = 0;
+  block_sum_store<kDotSlots>(acc, partD + ((size_t(b) * kDotGroups + blockIdx.z) * kRedBlocks + blockIdx.x) * kDotSlots);
 }
 
-// h_i (i <= j) from the partials, in a fixed order; hc[b][i] = h_i and column j of H gets h
-// (round 0) or h added (round 1). One CTA of 2 kGmresMaxRestart threads per problem.
-__global__ void k_gm_hsum(const int *plist, const int *active, const double *partD, double2 *hc, double2 *H,
-                          int j, int round, int m) {
+// h_i = <v_i, K v_j> (i <= j) from the partials, in a fixed order; hc[b][i] = h_i and column j
+// of the Hessenberg matrix of A = I - K gets delta_ij - h_i (round 0) or -h_i more (round 1);
+// round 0 also stores ||K v_j||^2. One CTA of 2 kGmresMaxRestart + 32 threads per problem.
+__global__ void k_gm_hsum(const int *plist, const int *active, GState *st, const double *partD, double2 *hc,
+                          double2 *H, int j, int round, int m) {
   const int b = problem_at(plist, blockIdx.x);
-  if (!active[b]) return;
-  const int t = threadIdx.x, i = t >> 1, comp = t & 1;
+  if (!active[b] || (round == 1 && !st[b].need2)) return;
+  const int t = threadIdx.x;
+  if (t == 2 * kGmresMaxRestart) {
+    if (round == 0) {
+      const double *p = partD + size_t(b) * kDotGroups * kRedBlocks * kDotSlots + 2 * kDotGroup;
+      double a = 0.0;
+      for (int blk = 0; blk < kRedBlocks; ++blk) a += p[size_t(blk) * kDotSlots];
+      st[b].wpre2 = a;
+    }
+    return;
+  }
+  const int i = t >> 1, comp = t & 1;
   if (i > j) return;
-  const double *p = partD + (size_t(b) * kDotGroups + i / kDotGroup) * kRedBlocks * (2 * kDotGroup) +
-                    2 * (i % kDotGroup) + comp;
+  const double *p = partD + (size_t(b) * kDotGroups + i / kDotGroup) * kRedBlocks * kDotSlots + 2 * (i % kDotGroup) +
+                    comp;
   double a = 0.0;
-  for (int blk = 0; blk < kRedBlocks; ++blk) a += p[size_t(blk) * (2 * kDotGroup)];
+  for (int blk = 0; blk < kRedBlocks; ++blk) a += p[size_t(blk) * kDotSlots];
   double *h = reinterpret_cast<double *>(hc + size_t(b) * (m + 1) + i) + comp;
   *h = a;
   double *Hij = reinterpret_cast<double *>(H + (size_t(b) * (m + 1) + i) * m + j) + comp;
-  *Hij = round == 0 ? a : *Hij + a;
+  *Hij = round == 0 ? ((i == j && comp == 0) ? 1.0 : 0.0) - a : *Hij - a;
 }
 
-// w -= sum_(i <= j) h_i v_i, partials of ||w||^2.
+// w -= sum_(i <= j) h_i v_i, partials of ||w||^2. The basis vectors are read eight at a time so
+// that their loads are in flight together.
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_gm_update(Span sp, const int *plist, const int *active,
-                                                           C *__restrict__ V, size_t vstride, int j,
-                                                           const double2 *hc, int m, double *partN) {
+                                                           const GState *st, C *__restrict__ V, size_t vstride,
+                                                           int j, int round, const double2 *hc, int m,
+                                                           double *partN) {
   using A = typename Acc<C>::type;
-  __shared__ C h[kGmresMaxRestart + 1];
+  __shared__ C h[kGmresMaxRestart + kDotGroup];
   const int b = problem_at(plist, blockIdx.y);
-  if (!active[b]) return;
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = from_z<C>(hc[size_t(b) * (m + 1) + i]);
+  if (!active[b] || (round == 1 && !st[b].need2)) return;
+  for (int i = threadIdx.x; i < kGmresMaxRestart + kDotGroup; i += blockDim.x)
+    h[i] = i <= j ? from_z<C>(hc[size_t(b) * (m + 1) + i]) : czero<C>();
   __syncthreads();
   C *w = V + size_t(j + 1) * vstride;
   A ww = 0;
   DBI_PROBLEM_LOOP(sp) {
     C wi = w[off + i];
-    for (int q = 0; q <= j; ++q) wi = csub(wi, cmul(h[q], V[size_t(q) * vstride + off + i]));
+    for (int q0 = 0; q0 <= j; q0 += kDotGroup) {
+      C v[kDotGroup];
+#pragma unroll
+      for (int u = 0; u < kDotGroup; ++u)
+        v[u] = q0 + u <= j ? V[size_t(q0 + u) * vstride + off + i] : czero<C>();
+#pragma unroll
+      for (int u = 0; u < kDotGroup; ++u) wi = csub(wi, cmul(h[q0 + u], v[u]));
+    }
     w[off + i] = wi;
     ww += wi.x * wi.x + wi.y * wi.y;
   }
-  double acc[1] = {double(ww)};
+  A acc[1] = {ww};
   block_sum_store<1>(acc, partN + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+}
+
+// After the first round: re-orthogonalise when ||w'||^2 < 0.49 ||w||^2 (one CTA per problem).
+__global__ void k_gm_need2(const int *plist, const int *active, GState *st, const double *partN) {
+  const int b = problem_at(plist, blockIdx.x);
+  if (!active[b]) return;
+  double s[1];
+  gather_n<1>(partN + size_t(b) * kRedBlocks * kRedSlots, kRedBlocks, s);
+  if (threadIdx.x == 0) st[b].need2 = s[0] < 0.49 * st[b].wpre2;
 }
 
 // End of step j (one CTA per problem): h_(j+1,j) = ||w||, the earlier rotations on column j, a
@@ -295,7 +341,7 @@ __global__ void k_gm_close(const int *plist, int *active, GState *st, double2 *H
   k.res = hypot(gb[j + 1].x, gb[j + 1].y);
   k.iters += 1;
   k.k = j + 1;
-  k.hn_inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  k.hn_inv = hn > 0.0 ? -1.0 / hn : 0.0;  // v_(j+1) = (A v_j - sum H_ij v_i) / hn = -w' / hn
   int act = 1;
   if (k.res <= tol * sqrt(k.bnorm2) || hn <= 1e-14 * t) {
     k.code = DBI_CONVERGED;
@@ -335,15 +381,22 @@ template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_gm_update_x(Span sp, const GState *st, const C *__restrict__ V,
                                                              size_t vstride, const double2 *y, int m,
                                                              C *__restrict__ x) {
-  __shared__ C c[kGmresMaxRestart];
+  __shared__ C c[kGmresMaxRestart + kDotGroup];
   const int b = blockIdx.y;
   const int kx = st[b].kx;
   if (kx == 0) return;
-  for (int i = threadIdx.x; i < kx; i += blockDim.x) c[i] = from_z<C>(y[size_t(b) * m + i]);
+  for (int i = threadIdx.x; i < kGmresMaxRestart + kDotGroup; i += blockDim.x)
+    c[i] = i < kx ? from_z<C>(y[size_t(b) * m + i]) : czero<C>();
   __syncthreads();
   DBI_PROBLEM_LOOP(sp) {
     C xi = x[off + i];
-    for (int q = 0; q < kx; ++q) xi = cadd(xi, cmul(c[q], V[size_t(q) * vstride + off + i]));
+    for (int q0 = 0; q0 < kx; q0 += kDotGroup) {
+      C v[kDotGroup];
+#pragma unroll
+      for (int u = 0; u < kDotGroup; ++u) v[u] = q0 + u < kx ? V[size_t(q0 + u) * vstride + off + i] : czero<C>();
+#pragma unroll
+      for (int u = 0; u < kDotGroup; ++u) xi = cadd(xi, cmul(c[q0 + u], v[u]));
+    }
     x[off + i] = xi;
   }
 }
@@ -423,15 +476,21 @@ static int gmres_typed(OpArgs op, const GmresBufs &gb, int m, const void *rhs_, 
     for (int j = 0; j < m; ++j) {
       const dim3 g2(kRedBlocks, nrun);
       op.plist = plist; op.nb = nrun; op.active = gb.active;
-      op.in = Vj(j); op.ident = Vj(j); op.out = Vj(j + 1);
+      op.in = Vj(j); op.ident = nullptr; op.out = Vj(j + 1);  // K v_j
       if ((rc = run_operator(op, s))) return rc;
       for (int round = 0; round < 2; ++round) {
+        if (round == 1) {
+          k_gm_need2<<<nrun, 32, 0, s>>>(plist, gb.active, gb.st, gb.partN);
+          if ((rc = check_launch("k_gm_need2"))) return rc;
+        }
         const dim3 g3(kRedBlocks, nrun, (j + 1 + kDotGroup - 1) / kDotGroup);
-        k_gm_dots<C><<<g3, kRedThreads, 0, s>>>(sp, plist, gb.active, V, vstride, j, gb.partD);
+        k_gm_dots<C><<<g3, kRedThreads, 0, s>>>(sp, plist, gb.active, gb.st, V, vstride, j, round, gb.partD);
         if ((rc = check_launch("k_gm_dots"))) return rc;
-        k_gm_hsum<<<nrun, 2 * kGmresMaxRestart, 0, s>>>(plist, gb.active, gb.partD, gb.hc, gb.H, j, round, m);
+        k_gm_hsum<<<nrun, 2 * kGmresMaxRestart + 32, 0, s>>>(plist, gb.active, gb.st, gb.partD, gb.hc, gb.H, j,
+                                                             round, m);
         if ((rc = check_launch("k_gm_hsum"))) return rc;
-        k_gm_update<C><<<g2, kRedThreads, 0, s>>>(sp, plist, gb.active, V, vstride, j, gb.hc, m, gb.partN);
+        k_gm_update<C><<<g2, kRedThreads, 0, s>>>(sp, plist, gb.active, gb.st, V, vstride, j, round, gb.hc, m,
+                                                  gb.partN);
         if ((rc = check_launch("k_gm_update"))) return rc;
       }
       k_gm_close<<<nrun, 32, 0, s>>>(plist, gb.active, gb.st, gb.H, gb.g, gb.cs, gb.sn, gb.partN, j, m, o.tol,

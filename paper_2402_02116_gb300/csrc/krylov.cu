@@ -25,18 +25,19 @@ namespace dbi {
 // Largest |component| of every problem's array (real and imaginary parts of complex values):
 // comparisons only, so nothing underflows whatever the scale of the values (a data residual of
 // 1e-12 back-propagates to fields of 1e-21, whose squares would underflow FP32).
-template <typename T> __device__ __forceinline__ double absmax(T v);
-template <> __device__ __forceinline__ double absmax<float>(float v) { return fabsf(v); }
-template <> __device__ __forceinline__ double absmax<double>(double v) { return fabs(v); }
-template <> __device__ __forceinline__ double absmax<float2>(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
-template <> __device__ __forceinline__ double absmax<double2>(double2 v) { return fmax(fabs(v.x), fabs(v.y)); }
+// The running maximum stays in the element's real type (FP32 comparisons for complex64 data);
+// only the CTA's result is widened to FP64.
+__device__ __forceinline__ float absmax(float v) { return fabsf(v); }
+__device__ __forceinline__ double absmax(double v) { return fabs(v); }
+__device__ __forceinline__ float absmax(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
+__device__ __forceinline__ double absmax(double2 v) { return fmax(fabs(v.x), fabs(v.y)); }
 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_absmax(Span sp, const T *x, double *part) {
   const int b = blockIdx.y;
-  double m = 0.0;
-  DBI_PROBLEM_LOOP(sp) m = fmax(m, absmax<T>(x[off + i]));
-  block_max_store(m, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
+  decltype(absmax(T{})) m = 0;
+  DBI_PROBLEM_LOOP(sp) m = fmax(m, absmax(x[off + i]));
+  block_max_store(double(m), part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
 
 // Power-of-two scale per problem that brings max |rhs| into [1, 2); the solver iterates on the
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kRedThreads) k_init(Span sp, const KState *st,
     bb += bi.x * bi.x + bi.y * bi.y;
     rr += ri.x * ri.x + ri.y * ri.y;
   }
-  double acc[2] = {double(bb), double(rr)};
+  A acc[2] = {bb, rr};
   block_sum_store<2>(acc, part + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
 
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_s(Span sp, const int *pl
     s[off + i] = si;
     ss += si.x * si.x + si.y * si.y;
   }
-  double acc[1] = {double(ss)};
+  A acc[1] = {ss};
   block_sum_store<1>(acc, partS + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
 
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(Span sp, const int *p
     im += h.x * ri.y - h.y * ri.x;
     rr += ri.x * ri.x + ri.y * ri.y;
   }
-  double acc[3] = {double(re), double(im), double(rr)};
+  A acc[3] = {re, im, rr};
   block_sum_store<3>(acc, partC + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
 

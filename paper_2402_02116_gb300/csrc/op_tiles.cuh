@@ -504,7 +504,9 @@ __device__ __forceinline__ void rows_inverse_tile(const A &a, int tile, C *smem)
   RegPlan<LX, V>::template run<C, 2, true>(v, lines, t, tr, RowSync<T>{1 + rr});
   const Rl osc = a.osc();
   const size_t base = size_t(z) * nx;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // per-thread partials of the fused inner products
+  // per-thread partials of the fused inner products: FP32 for complex64, FP64 for complex128
+  using PA = typename RealOf<C>::type;
+  PA a0 = 0, a1 = 0, a2 = 0;
   if (z < nz) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -526,22 +528,22 @@ __device__ __forceinline__ void rows_inverse_tile(const A &a, int tile, C *smem)
           const C w = a.ident() ? csub(id[m], r) : r;
           a.out()[o] = w;
           if constexpr (EPI == 1) {  // conj(rhat) w
-            a0 += float(h[m].x) * float(w.x) + float(h[m].y) * float(w.y);
-            a1 += float(h[m].x) * float(w.y) - float(h[m].y) * float(w.x);
+            a0 += h[m].x * w.x + h[m].y * w.y;
+            a1 += h[m].x * w.y - h[m].y * w.x;
           } else if constexpr (EPI == 2) {  // conj(w) id and |w|^2
-            a0 += float(w.x) * float(id[m].x) + float(w.y) * float(id[m].y);
-            a1 += float(w.x) * float(id[m].y) - float(w.y) * float(id[m].x);
-            a2 += float(w.x) * float(w.x) + float(w.y) * float(w.y);
+            a0 += w.x * id[m].x + w.y * id[m].y;
+            a1 += w.x * id[m].y - w.y * id[m].x;
+            a2 += w.x * w.x + w.y * w.y;
           }
         }
       }
     }
   }
   if constexpr (EPI == 1) {
-    double acc[2] = {double(a0), double(a1)};
+    PA acc[2] = {a0, a1};
     block_sum_store<2>(acc, a.part() + size_t(tile) * kRedSlots);
   } else if constexpr (EPI == 2) {
-    double acc[3] = {double(a0), double(a1), double(a2)};
+    PA acc[3] = {a0, a1, a2};
     block_sum_store<3>(acc, a.part() + size_t(tile) * kRedSlots);
   }
 }

@@ -10,26 +10,26 @@
 namespace dbi {
 
 // Sum NS values over the CTA (blockDim.x a multiple of 32, at most 1024) in a fixed order;
-// thread 0 stores the sums to out[0..NS). Every thread of the CTA must call it.
-template <int NS> __device__ __forceinline__ void block_sum_store(double (&v)[NS], double *out) {
+// thread 0 stores the sums to out[0..NS). Every thread of the CTA must call it. The warp stage
+// adds in the type of the per-thread sums (float for complex64 work: FP64 arithmetic runs at a
+// small fraction of the FP32 rate on this GPU, and a CTA-wide FP64 shuffle tree per partial cost
+// more than the memory pass it reduces); the CTA stage adds the warp sums in FP64.
+template <int NS, typename T> __device__ __forceinline__ void block_sum_store(T (&v)[NS], double *out) {
   __shared__ double sh[NS][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    double a = v[k];
+    T a = v[k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) sh[k][warp] = a;
+    if (lane == 0) sh[k][warp] = double(a);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < NS) {  // one thread per value: the warp sums in order
     const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      double a = 0.0;
-      for (int w = 0; w < nw; ++w) a += sh[k][w];
-      out[k] = a;
-    }
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += sh[threadIdx.x][w];
+    out[threadIdx.x] = a;
   }
   __syncthreads();
 }
