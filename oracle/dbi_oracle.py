@@ -38,7 +38,8 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.special import hankel2
+from scipy.integrate import quad_vec
+from scipy.special import hankel2, sici
 
 # Parameter order: rho, C11, C13, C33, C55.
 N_PARAMS = 5
@@ -121,6 +122,112 @@ def green_lattice(nz, nx, h, omega, alpha, beta, rho) -> np.ndarray:
     G13 = np.where(origin, s13, G13)
     G33 = np.where(origin, s33, G33)
     return np.stack([G11, G13, G33]).astype(np.complex128)
+
+
+# ---------------------------------------------------------------------------------------------
+# Homogeneous VTI reference: Green's tensor by its spectral representation (not in the paper)
+# ---------------------------------------------------------------------------------------------
+def christoffel_2d(n1, n3, c11, c13, c33, c55):
+    """Gamma_ik(n) = C_ijkl n_j n_l of the 2D VTI stiffness: entries (11, 13, 33)."""
+    return (c11 * n1 * n1 + c55 * n3 * n3, (c13 + c55) * n1 * n3, c55 * n1 * n1 + c33 * n3 * n3)
+
+
+def spectral_radial(x):
+    """J(a, s) = int_0^inf k cos(k s) / (k^2 - a^2) dk for a -> a - i0 (outgoing waves under
+    exp(+i w t)), as a function of x = a s > 0: -cos x Ci(x) - sin x Si(x) - (i pi / 2) cos x."""
+    si_x, ci_x = sici(x)
+    return -np.cos(x) * ci_x - np.sin(x) * si_x - 0.5j * np.pi * np.cos(x)
+
+
+def _modes(theta, rho, omega, c11, c13, c33, c55):
+    """Eigenvalues lambda_m of Gamma(n_theta), their projectors P_m (as 11, 13, 33 entries) and the
+    wavenumbers k_m = w sqrt(rho / lambda_m), m = qP, qSV."""
+    n1, n3 = np.cos(theta), np.sin(theta)
+    g11, g13, g33 = christoffel_2d(n1, n3, c11, c13, c33, c55)
+    mean, half = 0.5 * (g11 + g33), 0.5 * (g11 - g33)
+    rad = np.hypot(half, g13)
+    out = []
+    for lam, other in ((mean + rad, mean - rad), (mean - rad, mean + rad)):
+        d = lam - other
+        P = ((g11 - other) / d, g13 / d, (g33 - other) / d)
+        out.append((lam, P, omega * np.sqrt(rho / lam)))
+    return out
+
+
+def green_vti_2d(y1, y3, omega, rho, c11, c13, c33, c55, epsabs=1e-15, epsrel=1e-12):
+    """2D Green's tensor of a homogeneous VTI medium at the offset y = (y1, y3) != 0, from
+    (Gamma(k) - rho w^2)^-1 inverted over k in polar coordinates (the plane-wave decomposition
+    over slowness directions of anisotropic elastodynamics):
+
+        G(y) = 1 / (2 pi^2) int_0^pi sum_m P_m(theta) / lambda_m(theta) J(k_m(theta), |n_theta . y|) dtheta
+
+    with Gamma(n) = sum_m lambda_m P_m. Integrated by scipy's adaptive quadrature over
+    psi = theta - phi in (-pi/2, pi/2) (phi the direction of y), so the logarithmic singularity of J
+    at n . y = 0 sits at the ends. Returns (G11, G13, G33)."""
+    r = math.hypot(y1, y3)
+    phi = math.atan2(y3, y1)
+
+    def integrand(psi):
+        theta = phi + psi
+        s = r * math.cos(psi)
+        v = np.zeros(6)
+        for lam, P, k in _modes(theta, rho, omega, c11, c13, c33, c55):
+            j = spectral_radial(k * s) / lam
+            for c in range(3):
+                v[2 * c] += (P[c] * j).real
+                v[2 * c + 1] += (P[c] * j).imag
+        return v
+
+    val, _ = quad_vec(integrand, -0.5 * math.pi, 0.5 * math.pi, epsabs=epsabs, epsrel=epsrel, limit=2000)
+    g = (val[0::2] + 1j * val[1::2]) / (2.0 * math.pi * math.pi)
+    return g[0], g[1], g[2]
+
+
+def green_vti_self_cell(h, omega, rho, c11, c13, c33, c55):
+    """Mean of the VTI Green's tensor over the disk of area h^2 (radius a = h / sqrt(pi)): the
+    spectral representation with J replaced by its disk mean
+    D(k) = 4 / (pi a^2) int_0^a J(k, s) sqrt(a^2 - s^2) ds (a function of n . y only)."""
+    a = h / math.sqrt(math.pi)
+
+    def disk_mean(k):
+        def f(t):  # s = a t
+            j = spectral_radial(k * a * t) * math.sqrt(1.0 - t * t)
+            return np.array([j.real, j.imag])
+        v, _ = quad_vec(f, 0.0, 1.0, epsabs=1e-15, epsrel=1e-12, limit=500)
+        return (4.0 / math.pi) * (v[0] + 1j * v[1])
+
+    def integrand(theta):
+        v = np.zeros(6)
+        for lam, P, k in _modes(theta, rho, omega, c11, c13, c33, c55):
+            d = disk_mean(k) / lam
+            for c in range(3):
+                v[2 * c] += (P[c] * d).real
+                v[2 * c + 1] += (P[c] * d).imag
+        return v
+
+    val, _ = quad_vec(integrand, 0.0, math.pi, epsabs=1e-15, epsrel=1e-11, limit=200)
+    g = (val[0::2] + 1j * val[1::2]) / (2.0 * math.pi * math.pi)
+    return g[0], g[1], g[2]
+
+
+def green_lattice_vti(nz, nx, h, omega, rho, c11, c13, c33, c55) -> np.ndarray:
+    """G_h of the VTI reference on the (2nz-1) x (2nx-1) offset lattice ([c][dz+nz-1][dx+nx-1], as
+    green_lattice). Only the quadrant dz, dx >= 0 is integrated: the mirror symmetries of a VTI
+    medium make G11, G33 even and G13 odd in each of x1 and x3."""
+    out = np.zeros((3, 2 * nz - 1, 2 * nx - 1), dtype=np.complex128)
+    for dz in range(nz):
+        for dx in range(nx):
+            if dz == 0 and dx == 0:
+                g = green_vti_self_cell(h, omega, rho, c11, c13, c33, c55)
+            else:
+                g = green_vti_2d(dx * h, dz * h, omega, rho, c11, c13, c33, c55)
+            for sz in ((1, -1) if dz else (1,)):
+                for sx in ((1, -1) if dx else (1,)):
+                    iz, ix = nz - 1 + sz * dz, nx - 1 + sx * dx
+                    out[0, iz, ix] = g[0]
+                    out[1, iz, ix] = g[1] * sz * sx
+                    out[2, iz, ix] = g[2]
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -418,12 +525,19 @@ class LSOracle:
     nz, nx, h: grid; lz, lx: FFT grid; rho0, alpha0, beta0: reference medium; omegas: angular
     frequencies (rad/s). method = "fft" (Eq. 12) or "direct" (plain O(N^4) sum)."""
 
-    def __init__(self, nz, nx, h, lz, lx, rho0, alpha0, beta0, omegas, method="fft"):
+    def __init__(self, nz, nx, h, lz, lx, rho0, alpha0, beta0, omegas, method="fft", ref_vti=None):
         self.nz, self.nx, self.h, self.lz, self.lx = nz, nx, float(h), lz, lx
         self.rho0, self.alpha0, self.beta0 = float(rho0), float(alpha0), float(beta0)
         self.omegas = np.asarray(omegas, dtype=np.float64)
         self.method = method
-        self.G_lat = [green_lattice(nz, nx, h, w, alpha0, beta0, rho0) for w in self.omegas]
+        # reference (rho, C11, C13, C33, C55): isotropic from (rho0, alpha0, beta0), or the
+        # homogeneous VTI medium ref_vti with its spectral Green's tensor
+        if ref_vti is None:
+            self.ref = reference_params(rho0, alpha0, beta0)
+            self.G_lat = [green_lattice(nz, nx, h, w, alpha0, beta0, rho0) for w in self.omegas]
+        else:
+            self.ref = np.asarray(ref_vti, dtype=np.float64)
+            self.G_lat = [green_lattice_vti(nz, nx, h, w, *self.ref) for w in self.omegas]
         self.G_hat = [green_spectrum(G, lz, lx) for G in self.G_lat]
 
     # --- Eq. 6 / Eq. 12 convolution --------------------------------------------------------
@@ -434,7 +548,7 @@ class LSOracle:
 
     # --- Eq. 10: A u = u - K(w^2 drho u + div(dC : grad u)) ------------------------------------
     def apply(self, u, model, f):
-        dmod = contrast(model, self.rho0, self.alpha0, self.beta0)
+        dmod = np.asarray(model, dtype=np.float64) - self.ref[:, None, None]
         return u - self.convolve(contrast_source(u, dmod, self.omegas[f], self.h), f)
 
     # --- Eq. 9 (derivatives on G): A_K u = u - [w^2 G * (drho u) + (grad G) * sigma] -----------
