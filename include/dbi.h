@@ -72,6 +72,9 @@ typedef struct dbi_grid {
 
 typedef struct dbi_medium {
   double rho0, alpha0, beta0; /* homogeneous isotropic reference (kg/m^3, m/s, m/s) */
+  /* homogeneous VTI reference stiffness (Pa), used instead of alpha0, beta0 when c11 > 0 (an
+   * extension: the paper's reference is isotropic); all zero for an isotropic reference */
+  double c11, c13, c33, c55;
 } dbi_medium;
 
 typedef struct dbi_model {

@@ -154,7 +154,7 @@ def _modes(theta, rho, omega, c11, c13, c33, c55):
     return out
 
 
-def green_vti_2d(y1, y3, omega, rho, c11, c13, c33, c55, epsabs=1e-15, epsrel=1e-12):
+def green_vti_2d(y1, y3, omega, rho, c11, c13, c33, c55, epsabs=1e-16, epsrel=1e-13):
     """2D Green's tensor of a homogeneous VTI medium at the offset y = (y1, y3) != 0, from
     (Gamma(k) - rho w^2)^-1 inverted over k in polar coordinates (the plane-wave decomposition
     over slowness directions of anisotropic elastodynamics):
@@ -163,7 +163,8 @@ def green_vti_2d(y1, y3, omega, rho, c11, c13, c33, c55, epsabs=1e-15, epsrel=1e
 
     with Gamma(n) = sum_m lambda_m P_m. Integrated by scipy's adaptive quadrature over
     psi = theta - phi in (-pi/2, pi/2) (phi the direction of y), so the logarithmic singularity of J
-    at n . y = 0 sits at the ends. Returns (G11, G13, G33)."""
+    at n . y = 0 sits at the ends. The integrand is scaled by C55 to order one, so that the absolute
+    tolerance is relative to the integral's size. Returns (G11, G13, G33)."""
     r = math.hypot(y1, y3)
     phi = math.atan2(y3, y1)
 
@@ -172,14 +173,14 @@ def green_vti_2d(y1, y3, omega, rho, c11, c13, c33, c55, epsabs=1e-15, epsrel=1e
         s = r * math.cos(psi)
         v = np.zeros(6)
         for lam, P, k in _modes(theta, rho, omega, c11, c13, c33, c55):
-            j = spectral_radial(k * s) / lam
+            j = spectral_radial(k * s) * (c55 / lam)
             for c in range(3):
                 v[2 * c] += (P[c] * j).real
                 v[2 * c + 1] += (P[c] * j).imag
         return v
 
     val, _ = quad_vec(integrand, -0.5 * math.pi, 0.5 * math.pi, epsabs=epsabs, epsrel=epsrel, limit=2000)
-    g = (val[0::2] + 1j * val[1::2]) / (2.0 * math.pi * math.pi)
+    g = (val[0::2] + 1j * val[1::2]) / (2.0 * math.pi * math.pi * c55)
     return g[0], g[1], g[2]
 
 
@@ -199,14 +200,14 @@ def green_vti_self_cell(h, omega, rho, c11, c13, c33, c55):
     def integrand(theta):
         v = np.zeros(6)
         for lam, P, k in _modes(theta, rho, omega, c11, c13, c33, c55):
-            d = disk_mean(k) / lam
+            d = disk_mean(k) * (c55 / lam)
             for c in range(3):
                 v[2 * c] += (P[c] * d).real
                 v[2 * c + 1] += (P[c] * d).imag
         return v
 
     val, _ = quad_vec(integrand, 0.0, math.pi, epsabs=1e-15, epsrel=1e-11, limit=200)
-    g = (val[0::2] + 1j * val[1::2]) / (2.0 * math.pi * math.pi)
+    g = (val[0::2] + 1j * val[1::2]) / (2.0 * math.pi * math.pi * c55)
     return g[0], g[1], g[2]
 
 
@@ -662,10 +663,10 @@ class LSOracle:
 
     # --- normal equation (Eq. 23, 24) ------------------------------------------------------
     def param_scale(self):
-        """Scale of the relative unknowns: rho0, and rho0 alpha0^2 for C11, C13, C33; rho0 beta0^2
-        for C55."""
-        a2 = self.rho0 * self.alpha0 ** 2
-        return np.array([self.rho0, a2, a2, a2, self.rho0 * self.beta0 ** 2])
+        """Scale of the relative unknowns: the reference rho, C11 (for C11 and C13), C33, C55 (for an
+        isotropic reference: rho0, rho0 alpha0^2 three times, rho0 beta0^2)."""
+        r = self.ref
+        return np.array([r[0], r[1], r[1], r[3], r[4]])
 
     def normal_cg(self, model_b, U_b, fidx, dd, rec_cells, iters=30, lam=None, lam_rel=1e-3,
                   power_start=None, power_iters=10, tol=1e-12):

@@ -265,6 +265,10 @@ extern "C" int greens_tabulate_k(const dbi_grid *g, const dbi_medium *ref, const
   clear_error();
   int rc;
   if ((rc = check_grid(g)) || (rc = check_precision(precision))) return rc;
+  if (ref && reference_is_vti(*ref)) {
+    set_error("the derivative tables are tabulated for an isotropic reference only");
+    return DBI_ERR_ARG;
+  }
   if (!ref || !(ref->rho0 > 0) || !(ref->alpha0 > 0) || !(ref->beta0 > 0) || !(ref->alpha0 > ref->beta0)) {
     set_error("reference medium needs rho0 > 0 and alpha0 > beta0 > 0");
     return DBI_ERR_ARG;
@@ -297,13 +301,24 @@ extern "C" int greens_tabulate_k(const dbi_grid *g, const dbi_medium *ref, const
   return check_launch("k_scale_cast_t");
 }
 
+// A homogeneous VTI reference must be elastically stable: rho, C11, C33, C55 > 0, C11 C33 > C13^2.
+static int check_vti(const dbi_medium *r) {
+  if (!(r->rho0 > 0) || !(r->c11 > 0) || !(r->c33 > 0) || !(r->c55 > 0) || !(r->c11 * r->c33 > r->c13 * r->c13)) {
+    set_error("VTI reference needs rho0, C11, C33, C55 > 0 and C11 C33 > C13^2");
+    return DBI_ERR_ARG;
+  }
+  return DBI_OK;
+}
+
 extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const double *omega,
                                int nf, int precision, void *Ghat, void *Gspace, void *work,
                                size_t work_bytes, dbi_stream stream) {
   clear_error();
   int rc;
   if ((rc = check_grid(g)) || (rc = check_precision(precision))) return rc;
-  if (!ref || !(ref->rho0 > 0) || !(ref->alpha0 > 0) || !(ref->beta0 > 0) || !(ref->alpha0 > ref->beta0)) {
+  const bool vti = ref && reference_is_vti(*ref);
+  if (vti && (rc = check_vti(ref))) return rc;
+  if (!vti && (!ref || !(ref->rho0 > 0) || !(ref->alpha0 > 0) || !(ref->beta0 > 0) || !(ref->alpha0 > ref->beta0))) {
     set_error("reference medium needs rho0 > 0 and alpha0 > beta0 > 0");
     return DBI_ERR_ARG;
   }
@@ -324,13 +339,17 @@ extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const d
     e = cudaMemsetAsync(Gspace, 0, tab * (precision == DBI_C64 ? sizeof(float2) : sizeof(double2)), s);
   if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(Green table)", e);
   dim3 grid((g->nx + 127) / 128, g->nz, nf);
-  if (precision == DBI_C64)
-    k_green_space<float2><<<grid, 128, 0, s>>>(g->nz, g->nx, g->lz, g->lx, g->h, omega, ref->rho0,
-                                               ref->alpha0, ref->beta0, W, static_cast<float2 *>(Gspace));
-  else
-    k_green_space<double2><<<grid, 128, 0, s>>>(g->nz, g->nx, g->lz, g->lx, g->h, omega, ref->rho0,
-                                                ref->alpha0, ref->beta0, W, static_cast<double2 *>(Gspace));
-  if ((rc = check_launch("k_green_space"))) return rc;
+  if (vti) {
+    if ((rc = launch_green_vti(g, *ref, omega, nf, W, Gspace, precision, s))) return rc;
+  } else {
+    if (precision == DBI_C64)
+      k_green_space<float2><<<grid, 128, 0, s>>>(g->nz, g->nx, g->lz, g->lx, g->h, omega, ref->rho0,
+                                                 ref->alpha0, ref->beta0, W, static_cast<float2 *>(Gspace));
+    else
+      k_green_space<double2><<<grid, 128, 0, s>>>(g->nz, g->nx, g->lz, g->lx, g->h, omega, ref->rho0,
+                                                  ref->alpha0, ref->beta0, W, static_cast<double2 *>(Gspace));
+    if ((rc = check_launch("k_green_space"))) return rc;
+  }
   if ((rc = fft2_fp64(W, 3 * nf, g->lz, g->lx, tw, s))) return rc;
   const double scale = g->h * g->h / (double(g->lz) * double(g->lx));
   const dim3 tgrid((g->lx + 31) / 32, (g->lz + 31) / 32, 3 * nf), tblock(32, 8);

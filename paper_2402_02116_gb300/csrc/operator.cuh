@@ -83,11 +83,22 @@ inline Scales carve_scales(Arena &ar, int B) {
   return s;
 }
 
+// Green's tensor of a homogeneous VTI reference on the offsets |dz| < nz, |dx| < nx (greens_vti.cu):
+// FP64 values at slot (dz mod lz, dx mod lx) of W [nf][3][lz][lx] (and of Gspace when non-NULL).
+int launch_green_vti(const dbi_grid *g, const dbi_medium &ref, const double *omega, int nf, double2 *W,
+                     void *Gspace, int precision, cudaStream_t s);
+
 int pow2_scales(const void *x, int precision, bool real, int B, size_t n, double *part, double *scale,
                 double *inv, const double *extra, cudaStream_t s, const long long *offs = nullptr);
 
-// Reference values (rho, C11, C13, C33, C55) of the isotropic medium (Eq. 4, Eq. 39).
+// Reference values (rho, C11, C13, C33, C55) of the homogeneous reference medium (Eq. 4, Eq. 39):
+// the VTI stiffness when given, else the isotropic one.
+inline bool reference_is_vti(const dbi_medium &r) { return r.c11 > 0.0; }
 inline void reference_values(const dbi_medium &r, double out[5]) {
+  if (reference_is_vti(r)) {
+    out[0] = r.rho0; out[1] = r.c11; out[2] = r.c13; out[3] = r.c33; out[4] = r.c55;
+    return;
+  }
   const double a2 = r.alpha0 * r.alpha0, b2 = r.beta0 * r.beta0;
   out[0] = r.rho0;
   out[1] = r.rho0 * a2;

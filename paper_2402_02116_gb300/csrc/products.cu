@@ -504,9 +504,9 @@ extern "C" int normal_cg(const dbi_model *background, const dbi_batch *batch, co
   double *hist = static_cast<double *>(ar.take(size_t(cg->iters + 1) * sizeof(double)));
   void *dvec = ar.take(size_t(batch->B) * g->nz * g->nx * 2 * (precision == DBI_C64 ? sizeof(float2) : sizeof(double2)));
   cudaStream_t s = c.s;
-  const double a2 = background->ref.rho0 * background->ref.alpha0 * background->ref.alpha0;
-  const double S[5] = {background->ref.rho0, a2, a2, a2,
-                       background->ref.rho0 * background->ref.beta0 * background->ref.beta0};
+  double rv[5];
+  reference_values(background->ref, rv);
+  const double S[5] = {rv[0], rv[1], rv[1], rv[3], rv[4]};  // C13 takes the scale of C11
   const int mblocks = int(std::min<size_t>((nm + 255) / 256, 4096));
 
   // q = S adjoint(frechet(S p)) in FP64 model space

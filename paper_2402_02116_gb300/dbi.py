@@ -34,7 +34,8 @@ class Grid(ctypes.Structure):
 
 
 class Medium(ctypes.Structure):
-    _fields_ = [("rho0", c_double), ("alpha0", c_double), ("beta0", c_double)]
+    _fields_ = [("rho0", c_double), ("alpha0", c_double), ("beta0", c_double),
+                ("c11", c_double), ("c13", c_double), ("c33", c_double), ("c55", c_double)]
 
 
 class Model(ctypes.Structure):
@@ -192,7 +193,15 @@ def make_grid(nz, nx, lz, lx, h) -> Grid:
 
 
 def make_medium(rho0, alpha0, beta0) -> Medium:
-    return Medium(float(rho0), float(alpha0), float(beta0))
+    return Medium(float(rho0), float(alpha0), float(beta0), 0.0, 0.0, 0.0, 0.0)
+
+
+def make_medium_vti(rho0, c11, c13, c33, c55) -> Medium:
+    """A homogeneous VTI reference (its Green's tensor is tabulated from the spectral
+    representation); alpha0, beta0 are filled with the mean P and the S velocity for reference."""
+    a0 = ((c11 + c33) / (2.0 * rho0)) ** 0.5
+    b0 = (c55 / rho0) ** 0.5
+    return Medium(float(rho0), float(a0), float(b0), float(c11), float(c13), float(c33), float(c55))
 
 
 def workspace_bytes(grid: Grid, B: int, precision: int, op: int) -> int:

@@ -43,6 +43,7 @@ class Workload:
     src_force: np.ndarray  # [n_src][2] float (f1, f3)
     rec_cells: np.ndarray  # [n_rec][2] int (iz, ix)
     model_true: np.ndarray | None = None  # for inversion workloads: the model that made the data
+    ref_vti: tuple | None = None  # (rho, C11, C13, C33, C55) of a homogeneous VTI reference, or None
     krylov_tol: float = 1e-5
     seed: int = 0
 

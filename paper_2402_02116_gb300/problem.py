@@ -26,7 +26,8 @@ class DeviceProblem:
         self.rdt = dbi.real_dtype(precision)
         self.cdt = dbi.complex_dtype(precision)
         self.grid = dbi.make_grid(w.nz, w.nx, w.lz, w.lx, w.h)
-        self.ref = dbi.make_medium(w.rho0, w.alpha0, w.beta0)
+        self.ref = (dbi.make_medium_vti(*w.ref_vti) if getattr(w, "ref_vti", None) is not None
+                    else dbi.make_medium(w.rho0, w.alpha0, w.beta0))
         dev = self.device
         self.omega = torch.tensor(np.asarray(w.omegas, dtype=np.float64), device=dev)
         self.fidx = torch.tensor(w.problem_fidx(), dtype=torch.int32, device=dev)

@@ -66,6 +66,14 @@ def test_argument_errors_are_reported_without_a_gpu(lib):
     bad_ref = dbi.make_medium(2000.0, 1000.0, 1155.0)  # alpha0 < beta0
     rc = lib.greens_tabulate(ctypes.byref(g), ctypes.byref(bad_ref), None, 1, 0, None, None, None, 0, None)
     assert rc == -1
+    unstable = dbi.make_medium_vti(2200.0, 1.0e10, 2.0e10, 1.0e10, 3.0e9)  # C11 C33 < C13^2
+    rc = lib.greens_tabulate(ctypes.byref(g), ctypes.byref(unstable), None, 1, 0, None, None, None, 0, None)
+    assert rc == -1 and b"VTI" in lib.dbi_last_error()
+    vti = dbi.make_medium_vti(2200.0, 1.65e10, 5.6e9, 1.375e10, 4.58e9)
+    rc = lib.greens_tabulate_k(ctypes.byref(g), ctypes.byref(vti), None, 1, 0, None, None, 0, None)
+    assert rc == -1 and b"isotropic" in lib.dbi_last_error()
+    rc = lib.dbi_gmres_workspace_bytes(ctypes.byref(g), 4, 0, 65)
+    assert rc == 0
     model = dbi.Model(g, ref, None)
     batch = dbi.Batch(2, 1, None, None)
     rc = lib.ls_apply(ctypes.byref(model), ctypes.byref(batch), None, None, None, 0, None, 0, None)
