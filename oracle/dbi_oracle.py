@@ -211,7 +211,7 @@ def green_vti_self_cell(h, omega, rho, c11, c13, c33, c55):
     return g[0], g[1], g[2]
 
 
-def green_lattice_vti(nz, nx, h, omega, rho, c11, c13, c33, c55) -> np.ndarray:
+def green_lattice_vti(nz, nx, h, omega, rho, c11, c13, c33, c55, epsrel=1e-13) -> np.ndarray:
     """G_h of the VTI reference on the (2nz-1) x (2nx-1) offset lattice ([c][dz+nz-1][dx+nx-1], as
     green_lattice). Only the quadrant dz, dx >= 0 is integrated: the mirror symmetries of a VTI
     medium make G11, G33 even and G13 odd in each of x1 and x3."""
@@ -221,7 +221,8 @@ def green_lattice_vti(nz, nx, h, omega, rho, c11, c13, c33, c55) -> np.ndarray:
             if dz == 0 and dx == 0:
                 g = green_vti_self_cell(h, omega, rho, c11, c13, c33, c55)
             else:
-                g = green_vti_2d(dx * h, dz * h, omega, rho, c11, c13, c33, c55)
+                g = green_vti_2d(dx * h, dz * h, omega, rho, c11, c13, c33, c55, epsabs=1e-3 * epsrel,
+                                 epsrel=epsrel)
             for sz in ((1, -1) if dz else (1,)):
                 for sx in ((1, -1) if dx else (1,)):
                     iz, ix = nz - 1 + sz * dz, nx - 1 + sx * dx
@@ -526,7 +527,8 @@ class LSOracle:
     nz, nx, h: grid; lz, lx: FFT grid; rho0, alpha0, beta0: reference medium; omegas: angular
     frequencies (rad/s). method = "fft" (Eq. 12) or "direct" (plain O(N^4) sum)."""
 
-    def __init__(self, nz, nx, h, lz, lx, rho0, alpha0, beta0, omegas, method="fft", ref_vti=None):
+    def __init__(self, nz, nx, h, lz, lx, rho0, alpha0, beta0, omegas, method="fft", ref_vti=None,
+                 vti_epsrel=1e-13):
         self.nz, self.nx, self.h, self.lz, self.lx = nz, nx, float(h), lz, lx
         self.rho0, self.alpha0, self.beta0 = float(rho0), float(alpha0), float(beta0)
         self.omegas = np.asarray(omegas, dtype=np.float64)
@@ -538,7 +540,7 @@ class LSOracle:
             self.G_lat = [green_lattice(nz, nx, h, w, alpha0, beta0, rho0) for w in self.omegas]
         else:
             self.ref = np.asarray(ref_vti, dtype=np.float64)
-            self.G_lat = [green_lattice_vti(nz, nx, h, w, *self.ref) for w in self.omegas]
+            self.G_lat = [green_lattice_vti(nz, nx, h, w, *self.ref, epsrel=vti_epsrel) for w in self.omegas]
         self.G_hat = [green_spectrum(G, lz, lx) for G in self.G_lat]
 
     # --- Eq. 6 / Eq. 12 convolution --------------------------------------------------------

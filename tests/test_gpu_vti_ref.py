@@ -55,7 +55,7 @@ def test_isotropic_stiffness_reproduces_the_closed_form_tables():
 def test_vti_tables_match_the_oracle(precision):
     w = with_vti_reference(inputs.small_case(nz=6, nx=5, vti=True, freqs=(11.0,)))
     P = DeviceProblem(w, precision)
-    lat = O.green_lattice_vti(w.nz, w.nx, w.h, w.omegas[0], *w.ref_vti)
+    lat = O.green_lattice_vti(w.nz, w.nx, w.h, w.omegas[0], *w.ref_vti, epsrel=1e-12)
     tol = 1e-9 if precision == dbi.C128 else 1e-6
     assert rel(npy(P.Gspace[0]), O.embed_circulant(lat, w.lz, w.lx)) < tol
     Gh = O.green_spectrum(lat, w.lz, w.lx) * w.h * w.h / (w.lz * w.lx)
@@ -79,7 +79,8 @@ def test_far_offsets_match_the_oracle():
 def test_apply_and_solve_with_a_vti_reference(precision):
     w = with_vti_reference(inputs.small_case(nz=7, nx=6, vti=True, freqs=(9.0,), n_src=2))
     P = DeviceProblem(w, precision)
-    orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas, ref_vti=w.ref_vti)
+    orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas, ref_vti=w.ref_vti,
+                     vti_epsrel=1e-12)
     ud = P.to_field(inputs.seeded_complex((P.B, 2, w.nz, w.nx), 12))
     u = npy(ud).astype(np.complex128)
     got = npy(P.apply(ud))

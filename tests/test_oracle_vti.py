@@ -52,7 +52,7 @@ def test_vti_tensor_solves_the_wave_equation():
     y0 = (40.0, 25.0)
 
     def G(y1, y3, params):
-        g11, g13, g33 = O.green_vti_2d(y1, y3, w, *params)
+        g11, g13, g33 = O.green_vti_2d(y1, y3, w, *params, epsabs=1e-13, epsrel=1e-10)
         return np.array([[g11, g13], [g13, g33]])
 
     def residual(d, params=(rho, c11, c13, c33, c55)):
@@ -93,7 +93,8 @@ def test_ls_operator_with_an_isotropic_vti_reference():
     nz, nx, h = 6, 5, 10.0
     w = [2 * np.pi * 9.0]
     iso = O.LSOracle(nz, nx, h, 2 * nz, 2 * nx, RHO, ALPHA, BETA, w)
-    vti = O.LSOracle(nz, nx, h, 2 * nz, 2 * nx, RHO, ALPHA, BETA, w, ref_vti=O.reference_params(RHO, ALPHA, BETA))
+    vti = O.LSOracle(nz, nx, h, 2 * nz, 2 * nx, RHO, ALPHA, BETA, w, ref_vti=O.reference_params(RHO, ALPHA, BETA),
+                     vti_epsrel=1e-11)
     assert np.abs(vti.G_lat[0] - iso.G_lat[0]).max() <= 1e-9 * np.abs(iso.G_lat[0]).max()
     rng = np.random.default_rng(4)
     model = O.reference_params(RHO, ALPHA, BETA)[:, None, None] * (1 + 0.1 * rng.standard_normal((5, nz, nx)))
@@ -107,7 +108,8 @@ def test_zero_contrast_against_a_vti_reference():
     point source vanishes."""
     ref = vti_params()
     nz, nx = 5, 4
-    orc = O.LSOracle(nz, nx, 5.0, 2 * nz, 2 * nx, ref[0], 2500.0, 1443.0, [2 * np.pi * 8.0], ref_vti=ref)
+    orc = O.LSOracle(nz, nx, 5.0, 2 * nz, 2 * nx, ref[0], 2500.0, 1443.0, [2 * np.pi * 8.0], ref_vti=ref,
+                     vti_epsrel=1e-9)
     model = np.broadcast_to(np.asarray(ref)[:, None, None], (5, nz, nx))
     u0 = orc.incident(0, (0, 2), (0.0, 1.0))
     assert np.array_equal(orc.apply(u0, model, 0), u0)
