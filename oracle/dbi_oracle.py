@@ -163,8 +163,9 @@ def green_vti_2d(y1, y3, omega, rho, c11, c13, c33, c55, epsabs=1e-16, epsrel=1e
 
     with Gamma(n) = sum_m lambda_m P_m. Integrated by scipy's adaptive quadrature over
     psi = theta - phi in (-pi/2, pi/2) (phi the direction of y), so the logarithmic singularity of J
-    at n . y = 0 sits at the ends. The integrand is scaled by C55 to order one, so that the absolute
-    tolerance is relative to the integral's size. Returns (G11, G13, G33)."""
+    at n . y = 0 sits at the ends, with breakpoints every few radians of the largest phase k r. The
+    integrand is scaled by C55 to order one, so that the absolute tolerance is relative to the
+    integral's size; a quadrature that runs out of subdivisions raises. Returns (G11, G13, G33)."""
     r = math.hypot(y1, y3)
     phi = math.atan2(y3, y1)
 
@@ -179,7 +180,13 @@ def green_vti_2d(y1, y3, omega, rho, c11, c13, c33, c55, epsabs=1e-16, epsrel=1e
                 v[2 * c + 1] += (P[c] * j).imag
         return v
 
-    val, _ = quad_vec(integrand, -0.5 * math.pi, 0.5 * math.pi, epsabs=epsabs, epsrel=epsrel, limit=2000)
+    lam_min = min(m[0] for t in np.linspace(0.0, math.pi, 721) for m in _modes(t, rho, omega, c11, c13, c33, c55))
+    pieces = max(4, int(math.ceil(omega * math.sqrt(rho / lam_min) * r / 4.0)))
+    points = list(np.linspace(-0.5 * math.pi, 0.5 * math.pi, pieces + 1)[1:-1])
+    val, _, info = quad_vec(integrand, -0.5 * math.pi, 0.5 * math.pi, epsabs=epsabs, epsrel=epsrel,
+                            limit=20000, points=points, full_output=True)
+    if info.status == 1:  # subdivision limit (status 2, rounding at the tolerance, is accepted)
+        raise RuntimeError(f"VTI Green's tensor quadrature did not converge at y = ({y1}, {y3}): {info.message}")
     g = (val[0::2] + 1j * val[1::2]) / (2.0 * math.pi * math.pi * c55)
     return g[0], g[1], g[2]
 
