@@ -5,3 +5,4 @@ It shares no code with the CUDA library and imports nothing from it.
 """
 from .dbi_oracle import *  # noqa: F401,F403
 from .dbi_oracle import LSOracle, normalized_error  # noqa: F401
+from . import dbi_oracle3d as o3d  # noqa: F401

@@ -1,0 +1,138 @@
+"""Pins of the 3D oracle (CPU only): the closed-form tensor against its potential representation
+G = [k_s^2 g_s I + grad grad (g_s - g_p)] / (rho w^2) differentiated numerically, the elastic wave
+equation by finite differences (residual O(d^2)), the self-cell ball mean against a quadrature of
+the closed form, the direct sum against the FFT convolution, zero contrast, the Born series
+against the solve, and reciprocity of the discrete responses."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+o3 = O.o3d
+RHO, ALPHA, BETA = 2000.0, 2000.0, 1155.0
+
+
+def G_full(y, w):
+    comps = o3.green_3d(y[0], y[1], y[2], w, ALPHA, BETA, RHO)
+    return np.array([[c.item() if np.ndim(c) else c for c in row] for row in o3._full(comps)])
+
+
+@pytest.mark.parametrize("y", [(12.0, -7.0, 20.0), (40.0, 3.0, -5.0), (0.0, 0.0, 15.0)])
+def test_closed_form_equals_the_potential_representation(y):
+    w = 2 * np.pi * 10.0
+    ks, kp = w / BETA, w / ALPHA
+    F = lambda p: (np.exp(-1j * ks * np.linalg.norm(p)) - np.exp(-1j * kp * np.linalg.norm(p))) / (4 * math.pi * np.linalg.norm(p))
+    d = 1e-3
+    y = np.array(y)
+    E = np.eye(3)
+    H = np.empty((3, 3), dtype=complex)
+    for i in range(3):
+        for j in range(3):
+            H[i, j] = (F(y + d * E[i] + d * E[j]) - F(y + d * E[i] - d * E[j]) - F(y - d * E[i] + d * E[j])
+                       + F(y - d * E[i] - d * E[j])) / (4 * d * d)
+    r = np.linalg.norm(y)
+    gs = np.exp(-1j * ks * r) / (4 * math.pi * r)
+    want = (ks * ks * gs * np.eye(3) + H) / (RHO * w * w)
+    got = G_full(y, w)
+    assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max()
+
+
+def test_wave_equation_by_finite_differences():
+    """mu Lap G + (lambda + mu) grad div G + rho w^2 G = 0 away from the source, O(d^2)."""
+    w = 2 * np.pi * 12.0
+    mu, lam = RHO * BETA ** 2, RHO * (ALPHA ** 2 - 2 * BETA ** 2)
+    y0 = np.array([30.0, -20.0, 25.0])
+    E = np.eye(3)
+
+    def residual(d):
+        G = lambda p: G_full(p, w)
+        g0 = G(y0)
+        lap = sum(G(y0 + d * E[k]) - 2 * g0 + G(y0 - d * E[k]) for k in range(3)) / d ** 2
+        # (grad div G)_i m = sum_j d_i d_j G_jm
+        gd = np.zeros((3, 3), dtype=complex)
+        for i in range(3):
+            for j in range(3):
+                dij = (G(y0 + d * E[i] + d * E[j]) - G(y0 + d * E[i] - d * E[j]) - G(y0 - d * E[i] + d * E[j])
+                       + G(y0 - d * E[i] - d * E[j])) / (4 * d * d)
+                gd[i] += dij[j]
+        r = mu * lap + (lam + mu) * gd + RHO * w * w * g0
+        return np.abs(r).max() / (RHO * w * w * np.abs(g0).max())
+
+    r1, r2 = residual(1.0), residual(0.5)
+    assert r1 < 2e-3 and 3.5 < r1 / r2 < 4.5
+
+
+def test_self_cell_against_a_ball_quadrature():
+    """The ball mean by quadrature of the closed form: the 6-point octahedral rule is exact on the
+    sphere for the quadratic angular dependence (the 1/r^3 near-field part averages to zero at
+    every radius), Gauss-Legendre in r."""
+    h, w = 10.0, 2 * np.pi * 15.0
+    a = h * (3 / (4 * math.pi)) ** (1 / 3)
+    x, wt = np.polynomial.legendre.leggauss(40)
+    r = 0.5 * a * (x + 1)
+    wr = 0.5 * a * wt
+    dirs = np.vstack([np.eye(3), -np.eye(3)])
+    acc = np.zeros((3, 3), dtype=complex)
+    for rk, wk in zip(r, wr):
+        ang = sum(G_full(rk * d, w) for d in dirs) / 6.0
+        acc += wk * rk * rk * ang
+    mean = 3.0 / a ** 3 * acc
+    s = o3.green_3d_self_cell(h, w, ALPHA, BETA, RHO)
+    assert abs(mean[0, 0] - s) <= 1e-10 * abs(s)
+    assert np.abs(mean - s * np.eye(3)).max() <= 1e-10 * abs(s)
+
+
+def test_direct_sum_equals_fft():
+    nz, ny, nx, h = 3, 2, 4, 10.0
+    w = 2 * np.pi * 9.0
+    G = o3.green_lattice_3d(nz, ny, nx, h, w, ALPHA, BETA, RHO)
+    rng = np.random.default_rng(3)
+    s = rng.standard_normal((3, nz, ny, nx)) + 1j * rng.standard_normal((3, nz, ny, nx))
+    direct = o3.convolve_direct_3d(s, G, h)
+    for L in ((2 * nz, 2 * ny, 2 * nx), (8, 4, 16)):
+        fft = o3.convolve_fft_3d(s, o3.green_spectrum_3d(G, *L), h)
+        assert np.linalg.norm(fft - direct) <= 1e-12 * np.linalg.norm(direct)
+
+
+def case(nz=4, ny=3, nx=5, amp=0.1, seed=2):
+    rng = np.random.default_rng(seed)
+    ref = o3.reference_params_3d(RHO, ALPHA, BETA)
+    model = ref[:, None, None, None] * (1 + amp * (2 * rng.random((6, nz, ny, nx)) - 1))
+    orc = o3.LSOracle3D(nz, ny, nx, 10.0, 2 * nz, 2 * ny, 2 * nx, RHO, ALPHA, BETA, [2 * np.pi * 10.0])
+    return orc, model, ref
+
+
+def test_zero_contrast_is_the_identity():
+    orc, _, ref = case()
+    model = np.broadcast_to(ref[:, None, None, None], (6, 4, 3, 5))
+    u = orc.incident(0, (1, 1, 2), (0.0, 0.3, 1.0))
+    assert np.array_equal(orc.apply(u, model, 0), u)
+
+
+def test_born_series_equals_the_solve():
+    orc, model, ref = case(amp=0.01)
+    u0 = orc.incident(0, (0, 1, 2), (0.2, 0.0, 1.0))
+    u, info = orc.solve(u0, model, 0, tol=1e-13)
+    dm = model - ref[:, None, None, None]
+    K = lambda v: orc.convolve(o3.contrast_source_3d(v, dm, orc.omegas[0], orc.h), 0)
+    term, series = u0, u0.copy()
+    for _ in range(40):
+        term = K(term)
+        series = series + term
+    assert np.linalg.norm(series - u) <= 1e-10 * np.linalg.norm(u)
+
+
+def test_reciprocity():
+    """The discrete response at cell r, component i, to a unit force at s along j equals the
+    response at s, component j, to a force at r along i (the contrast operator is real symmetric
+    and G_h complex symmetric)."""
+    orc, model, _ = case(amp=0.2)
+    s, r = (0, 1, 1), (3, 2, 4)
+    for i, j in ((0, 2), (1, 1), (2, 0)):
+        fj, fi = np.eye(3)[j], np.eye(3)[i]
+        u_s, _ = orc.solve(orc.incident(0, s, fj), model, 0, tol=1e-13)
+        u_r, _ = orc.solve(orc.incident(0, r, fi), model, 0, tol=1e-13)
+        a, b = u_s[i][r], u_r[j][s]
+        assert abs(a - b) <= 1e-10 * abs(a), (i, j)
