@@ -204,6 +204,52 @@ int ls_solve_gmres(const dbi_model *model, const dbi_batch *batch, const void *G
                    void *u, const dbi_krylov_opts *opts, int restart, const dbi_status *status,
                    int precision, void *work, size_t work_bytes, dbi_stream stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * 3D extension (the paper's 3D examples and Eq. A-1): fields [B][3][nz][ny][nx] complex
+ * (u1, u2, u3 along x1, x2, x3; x3 the depth), models [6][nz][ny][nx] real
+ * (rho, C11, C13, C33, C55, C66 of a VTI medium; C12 = C11 - 2 C66, C44 = C55), cubic cells of
+ * side h, an isotropic reference. Tables [nf][6][lz][ly][lx] (components 11, 12, 13, 22, 23, 33).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct dbi_grid3 {
+  int nz, ny, nx; /* cells */
+  int lz, ly, lx; /* FFT grid, powers of two in [16, 1024], each >= 2 n - 1 */
+  double h;
+} dbi_grid3;
+
+typedef struct dbi_model3 {
+  dbi_grid3 grid;
+  dbi_medium ref; /* isotropic (rho0, alpha0, beta0) */
+  const void *m;  /* device [6][nz][ny][nx] real of the precision */
+} dbi_model3;
+
+/* dbi_workspace_bytes_3d -- work-buffer size for op DBI_OP_GREENS (B = nf), DBI_OP_APPLY or
+ * DBI_OP_SOLVE (GMRES with `restart`); 0 for invalid arguments. */
+size_t dbi_workspace_bytes_3d(const dbi_grid3 *g, int B, int precision, int op, int restart);
+
+/* greens_tabulate_3d -- the 3D isotropic Green's tensor (Eq. A-1, written for the exp(+i w t)
+ * convention of the 2D tensor, i.e. its complex conjugate; outgoing exp(-i k r)) at the offsets
+ * |d| < n, the self cell as the mean over the ball of volume h^3, FP64 3D FFT, scaled by
+ * h^3 / (lz ly lx) into Ghat (natural [kz][ky][kx] order); Gspace (may be NULL) the spatial table. */
+int greens_tabulate_3d(const dbi_grid3 *g, const dbi_medium *ref, const double *omega, int nf,
+                       int precision, void *Ghat, void *Gspace, void *work, size_t work_bytes,
+                       dbi_stream stream);
+
+/* incident_field_3d -- u0(x) = G_h(x - x_s) f (Eq. 7 in 3D). src_cells device [B][3] (iz, iy, ix),
+ * forces device [B][3] double (f1, f2, f3), u0 device [B][3][nz][ny][nx] out. */
+int incident_field_3d(const dbi_grid3 *g, const dbi_batch *batch, const void *Gspace,
+                      const int *src_cells, const double *forces, void *u0, int precision,
+                      dbi_stream stream);
+
+/* ls_apply_3d -- out = A u = u - h^3 G * (w^2 drho u + div(dC : eps(u))) in 3D (central
+ * differences, fields zero outside the grid). Work: dbi_workspace_bytes_3d(..., DBI_OP_APPLY). */
+int ls_apply_3d(const dbi_model3 *model, const dbi_batch *batch, const void *Ghat, const void *u,
+                void *out, int precision, void *work, size_t work_bytes, dbi_stream stream);
+
+/* ls_solve_3d -- A u = rhs in 3D by restarted GMRES(restart) (as ls_solve_gmres). */
+int ls_solve_3d(const dbi_model3 *model, const dbi_batch *batch, const void *Ghat, const void *rhs,
+                void *u, const dbi_krylov_opts *opts, int restart, const dbi_status *status,
+                int precision, void *work, size_t work_bytes, dbi_stream stream);
+
 /*
  * greens_tabulate_k -- the derivative tables of the paper-literal form of the LS equation (Eq. 9,
  *   the gradient acting on the Green's tensor instead of on the stress): central differences

@@ -31,7 +31,6 @@
 
 namespace dbi {
 
-constexpr int kGmresMaxRestart = 64;
 constexpr int kDotGroup = 8;  // basis vectors per CTA of the inner-product pass
 constexpr int kDotGroups = kGmresMaxRestart / kDotGroup;
 
@@ -66,8 +65,8 @@ struct GmresBufs {
   int *active, *plist, *count;
 };
 
-size_t gmres_bytes(const dbi_grid *g, int B, int precision, int m) {
-  const size_t f = bytes_field(g, B, precision);
+// f: bytes of one field of the whole batch (B problems), 256-aligned.
+size_t gmres_bytes_fields(size_t f, int B, int m) {
   const size_t small = align256(size_t(B) * sizeof(GState)) + align256(size_t(B) * (m + 1) * m * sizeof(double2)) +
                        2 * align256(size_t(B) * (m + 1) * sizeof(double2)) +
                        align256(size_t(B) * m * sizeof(double)) + 2 * align256(size_t(B) * m * sizeof(double2)) +
@@ -77,9 +76,8 @@ size_t gmres_bytes(const dbi_grid *g, int B, int precision, int m) {
   return size_t(m + 1) * f + small + parts + 2 * align256(size_t(B) * sizeof(int)) + 256;
 }
 
-static GmresBufs carve_gmres(Arena &ar, const dbi_grid *g, int B, int precision, int m) {
+static GmresBufs carve_gmres(Arena &ar, size_t f, int B, int m) {
   GmresBufs gb{};
-  const size_t f = bytes_field(g, B, precision);
   gb.V = ar.take(size_t(m + 1) * f);
   gb.st = static_cast<GState *>(ar.take(size_t(B) * sizeof(GState)));
   gb.H = static_cast<double2 *>(ar.take(size_t(B) * (m + 1) * m * sizeof(double2)));
@@ -420,7 +418,7 @@ template <typename C>
 static int gmres_typed(OpArgs op, const GmresBufs &gb, int m, const void *rhs_, void *x_, bool x_zero,
                        const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s) {
   const int B = op.B;
-  const size_t n = size_t(2) * op.nz * op.nx;
+  const size_t n = field_elems(op);
   const Span sp{n, nullptr};
   const size_t vstride = size_t(B) * n;
   const C *rhs = static_cast<const C *>(rhs_);
@@ -520,8 +518,9 @@ static int gmres_typed(OpArgs op, const GmresBufs &gb, int m, const void *rhs_, 
   return DBI_OK;
 }
 
-static int run_gmres(const OpArgs &op, const GmresBufs &gb, int m, const void *rhs, void *x, bool x_zero,
-                     const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s) {
+int run_gmres(const OpArgs &op, Arena &ar, size_t field_bytes, int m, const void *rhs, void *x, bool x_zero,
+              const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s) {
+  const GmresBufs gb = carve_gmres(ar, field_bytes, op.B, m);
   return op.precision == DBI_C64 ? gmres_typed<float2>(op, gb, m, rhs, x, x_zero, o, status, s)
                                  : gmres_typed<double2>(op, gb, m, rhs, x, x_zero, o, status, s);
 }
@@ -533,7 +532,8 @@ using namespace dbi;
 extern "C" size_t dbi_gmres_workspace_bytes(const dbi_grid *g, int B, int precision, int restart) {
   if (!g || check_grid(g) || check_precision(precision) || B < 0 || restart < 1 || restart > kGmresMaxRestart)
     return 0;
-  return bytes_twiddles(precision) + bytes_spectral(g, B, precision) + gmres_bytes(g, B, precision, restart);
+  return bytes_twiddles(precision) + bytes_spectral(g, B, precision) +
+         gmres_bytes_fields(bytes_field(g, B, precision), B, restart);
 }
 
 extern "C" int ls_solve_gmres(const dbi_model *model, const dbi_batch *batch, const void *Ghat, const void *rhs,
@@ -562,12 +562,12 @@ extern "C" int ls_solve_gmres(const dbi_model *model, const dbi_batch *batch, co
   Arena ar(work, work_bytes);
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral(g, batch->B, precision));
-  GmresBufs gb = carve_gmres(ar, g, batch->B, precision, restart);
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   OpArgs a{};
   a.precision = precision; a.nz = g->nz; a.nx = g->nx; a.lz = g->lz; a.lx = g->lx; a.h = g->h;
   a.B = batch->B; a.nf = batch->nf; a.omega = batch->omega; a.fidx = batch->fidx;
   a.m = model->m; reference_values(model->ref, a.ref);
   a.T = T; a.Ghat = Ghat; a.tw = tw;
-  return run_gmres(a, gb, restart, rhs, u, opts->zero_guess != 0, *opts, status, s);
+  return run_gmres(a, ar, bytes_field(g, batch->B, precision), restart, rhs, u, opts->zero_guess != 0, *opts,
+                   status, s);
 }

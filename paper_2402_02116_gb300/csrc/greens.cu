@@ -166,26 +166,34 @@ __global__ void k_scale_cast_t(const double2 *W, C *Ghat, int lz, int lx, double
 }
 
 
-static int fft2_fp64(double2 *W, int nmat, int lz, int lx, const double2 *tw, cudaStream_t s) {
-  int rc = DBI_OK;
-  dispatch_len(lx, [&]<int L>() {
-    constexpr int NL = 2048 / L > 0 ? 2048 / L : 1, LS = L + 1, NT = NL * L / 8;
+int fft_rows_fp64(double2 *W, long nlines, int L, const double2 *tw, cudaStream_t s) {
+  int rc = DBI_ERR_UNSUPPORTED;
+  dispatch_len(L, [&]<int LL>() {
+    constexpr int NL = 2048 / LL > 0 ? 2048 / LL : 1, LS = LL + 1, NT = NL * LL / 8;
     const size_t bytes = size_t(NL) * LS * sizeof(double2);
-    const long nlines = long(nmat) * lz;
-    cudaError_t e = allow_smem(k_fft_rows64<L>, bytes);
-    if (e == cudaSuccess) k_fft_rows64<L><<<unsigned((nlines + NL - 1) / NL), NT, bytes, s>>>(W, nlines, tw);
+    cudaError_t e = allow_smem(k_fft_rows64<LL>, bytes);
+    if (e == cudaSuccess) k_fft_rows64<LL><<<unsigned((nlines + NL - 1) / NL), NT, bytes, s>>>(W, nlines, tw);
     rc = e != cudaSuccess ? cuda_fail("k_fft_rows64 smem", e) : check_launch("k_fft_rows64");
   });
-  if (rc) return rc;
-  dispatch_len(lz, [&]<int L>() {
-    constexpr int CC = 2048 / L > 0 ? 2048 / L : 1, LS = L + 1, NT = CC * L / 8;
+  return rc;
+}
+
+int fft_cols_fp64(double2 *W, int nmat, int L, int width, const double2 *tw, cudaStream_t s) {
+  int rc = DBI_ERR_UNSUPPORTED;
+  dispatch_len(L, [&]<int LL>() {
+    constexpr int CC = 2048 / LL > 0 ? 2048 / LL : 1, LS = LL + 1, NT = CC * LL / 8;
     const size_t bytes = size_t(CC) * LS * sizeof(double2);
-    cudaError_t e = allow_smem(k_fft_cols64<L>, bytes);
-    dim3 grid((lx + CC - 1) / CC, nmat);
-    if (e == cudaSuccess) k_fft_cols64<L><<<grid, NT, bytes, s>>>(W, lx, tw);
+    cudaError_t e = allow_smem(k_fft_cols64<LL>, bytes);
+    dim3 grid((width + CC - 1) / CC, nmat);
+    if (e == cudaSuccess) k_fft_cols64<LL><<<grid, NT, bytes, s>>>(W, width, tw);
     rc = e != cudaSuccess ? cuda_fail("k_fft_cols64 smem", e) : check_launch("k_fft_cols64");
   });
   return rc;
+}
+
+static int fft2_fp64(double2 *W, int nmat, int lz, int lx, const double2 *tw, cudaStream_t s) {
+  int rc = fft_rows_fp64(W, long(nmat) * lz, lx, tw, s);
+  return rc ? rc : fft_cols_fp64(W, nmat, lz, lx, tw, s);
 }
 
 // Problems whose source cell or frequency index is out of range get u0 = 0.

@@ -39,6 +39,13 @@ SolverBufs carve_solver_fields(Arena &ar, size_t field_bytes, int B);
 // Validates Krylov options (tol >= 0, max_iter >= 0, check_every >= 0).
 int check_krylov(const dbi_krylov_opts *o);
 
+// Restarted GMRES(m) (gmres.cu) on the operator `op` (2D or 3D): the basis and the cycle state are
+// carved from `ar`; field_bytes = bytes of one field of the whole batch (256-aligned).
+constexpr int kGmresMaxRestart = 64;
+size_t gmres_bytes_fields(size_t field_bytes, int B, int m);
+int run_gmres(const OpArgs &op, Arena &ar, size_t field_bytes, int m, const void *rhs, void *x, bool x_zero,
+              const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s);
+
 // plist = the problems b < B with active[b] != 0 in ascending order, *count = how many (device).
 int compact_active(int B, const int *active, int *plist, int *count, cudaStream_t s);
 

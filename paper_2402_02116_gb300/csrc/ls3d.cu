@@ -1,0 +1,647 @@
+// 3D LS operator (the paper's 3D extension: Eq. A-1 and its 3D VTI example), batched over
+// (source, frequency) problems on one grid [nz][ny][nx] of cubic cells:
+//   A u = u - h^3 G * (w^2 drho u + div(dC : eps(u))),   u = (u1, u2, u3), x3 the depth,
+// with the 3D VTI contrast (rho, C11, C13, C33, C55 = C44, C66; C12 = C11 - 2 C66) against an
+// isotropic reference, central differences with fields zero outside the grid, and the isotropic
+// 3D Green's tensor written for the exp(+i w t) convention of the 2D tensor (the complex conjugate
+// of Eq. A-1 as printed). Kernels per operator pass:
+//   k3_stress       sigma = dC : eps(u)  (6 Voigt components)              -> T2
+//   k3_source       w^2 drho u + div sigma                                 -> T rows (x < nx)
+//   k3_fft_x        forward FFT along x of every row, zero-padded to lx    (in place in T)
+//   k3_fft_y        forward FFT along y (rows y >= ny read as zero)        (in place)
+//   k3_fft_z_mul    per (ky, kx) column: forward FFT along z of the three components, the
+//                   symmetric 3 x 3 Ghat product, inverse FFT along z      (in place, z < nz kept)
+//   k3_fft_y        inverse, y < ny kept
+//   k3_fft_x_epi    inverse FFT along x, x < nx kept, out = ident - result
+// The FFTs are the shared-memory Stockham transforms of fft.cuh. Ghat [nf][6][lz][ly][lx]
+// (components 11, 12, 13, 22, 23, 33) carries h^3 / (lz ly lx).
+#include <algorithm>
+#include <cmath>
+
+#include "fft.cuh"
+#include "krylov.cuh"
+
+namespace dbi {
+
+struct Ref6 {  // reference values (rho, C11, C13, C33, C55, C66) subtracted from the model
+  double v[6];
+};
+
+// Problem of a launch slot, or -1 when it is out of range or inactive.
+__device__ __forceinline__ int slot_problem(const int *plist, const int *active, int slot) {
+  const int b = plist ? plist[slot] : slot;
+  return (active && !active[b]) ? -1 : b;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(128) k3_stress(int nz, int ny, int nx, typename RealOf<C>::type inv2h,
+                                                 const typename RealOf<C>::type *m, Ref6 ref,
+                                                 const C *u, const double *in_scale, const int *plist,
+                                                 const int *active, C *sig) {
+  using R = typename RealOf<C>::type;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int zy = blockIdx.y, z = zy / ny, y = zy - z * ny, slot = blockIdx.z;
+  if (x >= nx) return;
+  const int b = slot_problem(plist, active, slot);
+  if (b < 0) return;
+  const size_t cells = size_t(nz) * ny * nx, cell = (size_t(z) * ny + y) * nx + x;
+  const C *ub = u + size_t(b) * 3 * cells;
+  const R sc = in_scale ? R(in_scale[b]) : R(1);
+  auto U = [&](int c, int dz, int dy, int dx) -> C {
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) return czero<C>();
+    return ub[c * cells + (size_t(zz) * ny + yy) * nx + xx];
+  };
+  // d u_c / d x_k (k = 0: x, 1: y, 2: z)
+  auto D = [&](int c, int k) -> C {
+    const C p = U(c, k == 2, k == 1, k == 0), q = U(c, -(k == 2), -(k == 1), -(k == 0));
+    return cscale(csub(p, q), inv2h * sc);
+  };
+  const C e1 = D(0, 0), e2 = D(1, 1), e3 = D(2, 2);
+  const C e4 = cadd(D(1, 2), D(2, 1)), e5 = cadd(D(0, 2), D(2, 0)), e6 = cadd(D(0, 1), D(1, 0));
+  auto dm = [&](int p) { return R(double(m[p * cells + cell]) - ref.v[p]); };
+  const R c11 = dm(1), c13 = dm(2), c33 = dm(3), c55 = dm(4), c66 = dm(5), c12 = c11 - R(2) * c66;
+  C *sb = sig + size_t(slot) * 6 * cells + cell;
+  sb[0] = cadd(cadd(cscale(e1, c11), cscale(e2, c12)), cscale(e3, c13));
+  sb[cells] = cadd(cadd(cscale(e1, c12), cscale(e2, c11)), cscale(e3, c13));
+  sb[2 * cells] = cadd(cscale(cadd(e1, e2), c13), cscale(e3, c33));
+  sb[3 * cells] = cscale(e4, c55);
+  sb[4 * cells] = cscale(e5, c55);
+  sb[5 * cells] = cscale(e6, c66);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(128) k3_source(int nz, int ny, int nx, int ly, int lx, int nf,
+                                                 typename RealOf<C>::type inv2h, const typename RealOf<C>::type *m,
+                                                 Ref6 ref, const C *u, const double *in_scale,
+                                                 const double *omega, const int *fidx, const int *plist,
+                                                 const int *active, const C *sig, C *T) {
+  using R = typename RealOf<C>::type;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int zy = blockIdx.y, z = zy / ny, y = zy - z * ny, slot = blockIdx.z;
+  if (x >= nx) return;
+  const int b = slot_problem(plist, active, slot);
+  if (b < 0 || unsigned(fidx[b]) >= unsigned(nf)) return;
+  const size_t cells = size_t(nz) * ny * nx, cell = (size_t(z) * ny + y) * nx + x;
+  const C *sb = sig + size_t(slot) * 6 * cells;
+  auto S = [&](int k, int dz, int dy, int dx) -> C {
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) return czero<C>();
+    return sb[k * cells + (size_t(zz) * ny + yy) * nx + xx];
+  };
+  // d sigma_k / d x_a (Voigt k: 0 s11, 1 s22, 2 s33, 3 s23, 4 s13, 5 s12)
+  auto D = [&](int k, int a) -> C {
+    return cscale(csub(S(k, a == 2, a == 1, a == 0), S(k, -(a == 2), -(a == 1), -(a == 0))), inv2h);
+  };
+  const double w = omega[fidx[b]];
+  const R sc = in_scale ? R(in_scale[b]) : R(1);
+  const R wr = R(w * w * (double(m[cell]) - ref.v[0])) * sc;
+  const C *ub = u + size_t(b) * 3 * cells;
+  const C d0 = cadd(cadd(D(0, 0), D(5, 1)), D(4, 2));
+  const C d1 = cadd(cadd(D(5, 0), D(1, 1)), D(3, 2));
+  const C d2 = cadd(cadd(D(4, 0), D(3, 1)), D(2, 2));
+  const C dv[3] = {d0, d1, d2};
+  C *Tb = T + size_t(slot) * 3 * nz * ly * lx;
+  for (int c = 0; c < 3; ++c)
+    Tb[((size_t(c) * nz + z) * ly + y) * lx + x] = cadd(dv[c], cscale(ub[c * cells + cell], wr));
+}
+
+// Forward FFT along x of the rows (slot, c, z, y < ny) of T: points x < nx read, the rest zero.
+template <typename C, int LX>
+__global__ void __launch_bounds__(256) k3_fft_x(int nb, int nz, int ny, int nx, int ly, const int *plist,
+                                                const int *active, const C *tw, C *T) {
+  constexpr int NL = 2048 / LX, LS = LX + 1, NT = NL * LX / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *s = reinterpret_cast<C *>(smem_raw);
+  const long rows = long(nb) * 3 * nz * ny, r0 = long(blockIdx.x) * NL;
+  auto row_ptr = [&](long r, bool &live) -> C * {
+    const long per = long(3) * nz * ny;
+    const int slot = int(r / per);
+    const long rem = r - slot * per;
+    const int cz = int(rem / ny), y = int(rem - long(cz) * ny);
+    live = r < rows && slot_problem(plist, active, slot) >= 0;
+    return T + ((size_t(slot) * 3 * nz + cz) * ly + y) * LX;
+  };
+  for (int idx = threadIdx.x; idx < NL * LX; idx += NT) {
+    const int l = idx / LX, k = idx - l * LX;
+    bool live;
+    const C *p = row_ptr(r0 + l, live);
+    s[l * LS + k] = (live && k < nx) ? p[k] : czero<C>();
+  }
+  __syncthreads();
+  Plan<LX>::template run<C, NL, LS, NT, false>(s, tw);
+  for (int idx = threadIdx.x; idx < NL * LX; idx += NT) {
+    const int l = idx / LX, k = idx - l * LX;
+    bool live;
+    C *p = row_ptr(r0 + l, live);
+    if (live) p[k] = s[l * LS + k];
+  }
+}
+
+// FFT along y of the planes (slot, c, z) [ly][lx], CC columns per CTA. Forward: rows y >= ny read
+// as zero, all ly written; inverse: all read, y < ny written.
+template <typename C, int LY, bool INV>
+__global__ void __launch_bounds__(256) k3_fft_y(int nz, int ny, int lx, const int *plist, const int *active,
+                                                const C *tw, C *T) {
+  constexpr int CC = 2048 / LY, LS = LY + 1, NT = CC * LY / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *s = reinterpret_cast<C *>(smem_raw);
+  const int plane = blockIdx.y, slot = plane / (3 * nz);
+  if (slot_problem(plist, active, slot) < 0) return;  // uniform over the CTA
+  C *M = T + size_t(plane) * LY * lx;
+  const int c0 = blockIdx.x * CC;
+  for (int idx = threadIdx.x; idx < CC * LY; idx += NT) {
+    const int y = idx / CC, j = idx - y * CC;
+    s[j * LS + y] = (c0 + j < lx && (INV || y < ny)) ? M[size_t(y) * lx + c0 + j] : czero<C>();
+  }
+  __syncthreads();
+  Plan<LY>::template run<C, CC, LS, NT, INV>(s, tw);
+  for (int idx = threadIdx.x; idx < CC * LY; idx += NT) {
+    const int y = idx / CC, j = idx - y * CC;
+    if (c0 + j < lx && (!INV || y < ny)) M[size_t(y) * lx + c0 + j] = s[j * LS + y];
+  }
+}
+
+// Per (ky, kx) column q of a slot: the three components' z-lines (z < nz, zero-padded to LZ),
+// forward FFT, out_i = sum_j Ghat_ij(kz, q) v_j, inverse FFT, z < nz written back.
+template <typename C, int LZ> struct ZCfg {
+  static constexpr int CC = 512 / LZ > 0 ? 512 / LZ : 1;
+  static constexpr int NL = 3 * CC, LS = LZ + 1, NT = NL * LZ / 8;
+};
+template <typename C, int LZ>
+__global__ void __launch_bounds__(ZCfg<C, LZ>::NT) k3_fft_z_mul(int nz, int nf, size_t plane, const int *plist,
+                                                                const int *active, const int *fidx, const C *Ghat,
+                                                                const C *tw, C *T) {
+  using Z = ZCfg<C, LZ>;
+  constexpr int CC = Z::CC, NL = Z::NL, LS = Z::LS, NT = Z::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *s = reinterpret_cast<C *>(smem_raw);
+  const int slot = blockIdx.y;
+  const int b = slot_problem(plist, active, slot);
+  if (b < 0 || unsigned(fidx[b]) >= unsigned(nf)) return;
+  C *Tb = T + size_t(slot) * 3 * nz * plane;
+  const size_t q0 = size_t(blockIdx.x) * CC;
+  for (int idx = threadIdx.x; idx < NL * LZ; idx += NT) {
+    const int z = idx / NL, l = idx - z * NL, c = l / CC, j = l - c * CC;
+    s[l * LS + z] = (z < nz && q0 + j < plane) ? Tb[(size_t(c) * nz + z) * plane + q0 + j] : czero<C>();
+  }
+  __syncthreads();
+  Plan<LZ>::template run<C, NL, LS, NT, false>(s, tw);
+  const C *G = Ghat + size_t(fidx[b]) * 6 * LZ * plane;
+  for (int idx = threadIdx.x; idx < CC * LZ; idx += NT) {
+    const int kz = idx / CC, j = idx - kz * CC;
+    if (q0 + j >= plane) continue;
+    const size_t o = size_t(kz) * plane + q0 + j;
+    const C g11 = G[o], g12 = G[LZ * plane + o], g13 = G[2 * LZ * plane + o];
+    const C g22 = G[3 * LZ * plane + o], g23 = G[4 * LZ * plane + o], g33 = G[5 * LZ * plane + o];
+    const C v1 = s[j * LS + kz], v2 = s[(CC + j) * LS + kz], v3 = s[(2 * CC + j) * LS + kz];
+    s[j * LS + kz] = cadd(cadd(cmul(g11, v1), cmul(g12, v2)), cmul(g13, v3));
+    s[(CC + j) * LS + kz] = cadd(cadd(cmul(g12, v1), cmul(g22, v2)), cmul(g23, v3));
+    s[(2 * CC + j) * LS + kz] = cadd(cadd(cmul(g13, v1), cmul(g23, v2)), cmul(g33, v3));
+  }
+  __syncthreads();
+  Plan<LZ>::template run<C, NL, LS, NT, true>(s, tw);
+  for (int idx = threadIdx.x; idx < NL * nz; idx += NT) {
+    const int z = idx / NL, l = idx - z * NL, c = l / CC, j = l - c * CC;
+    if (q0 + j < plane) Tb[(size_t(c) * nz + z) * plane + q0 + j] = s[l * LS + z];
+  }
+}
+
+// Inverse FFT along x of the rows (slot, c, z, y < ny); out = ident - osc result (x < nx).
+template <typename C, int LX>
+__global__ void __launch_bounds__(256) k3_fft_x_epi(int nb, int nz, int ny, int nx, int ly, const int *plist,
+                                                    const int *active, const C *tw, const C *T, const C *ident,
+                                                    const double *out_scale, C *out) {
+  using R = typename RealOf<C>::type;
+  constexpr int NL = 2048 / LX, LS = LX + 1, NT = NL * LX / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *s = reinterpret_cast<C *>(smem_raw);
+  const long per = long(3) * nz * ny, rows = long(nb) * per, r0 = long(blockIdx.x) * NL;
+  const size_t cells = size_t(nz) * ny * nx;
+  for (int idx = threadIdx.x; idx < NL * LX; idx += NT) {
+    const int l = idx / LX, k = idx - l * LX;
+    const long r = r0 + l;
+    const int slot = int(r / per);
+    const long rem = r - slot * per;
+    const int cz = int(rem / ny), y = int(rem - long(cz) * ny);
+    const bool live = r < rows && slot_problem(plist, active, slot) >= 0;
+    s[l * LS + k] = live ? T[((size_t(slot) * 3 * nz + cz) * ly + y) * LX + k] : czero<C>();
+  }
+  __syncthreads();
+  Plan<LX>::template run<C, NL, LS, NT, true>(s, tw);
+  for (int idx = threadIdx.x; idx < NL * LX; idx += NT) {
+    const int l = idx / LX, k = idx - l * LX;
+    const long r = r0 + l;
+    if (r >= rows || k >= nx) continue;
+    const int slot = int(r / per);
+    const int b = slot_problem(plist, active, slot);
+    if (b < 0) continue;
+    const long rem = r - slot * per;
+    const int cz = int(rem / ny), y = int(rem - long(cz) * ny);
+    const size_t o = size_t(b) * 3 * cells + (size_t(cz) * ny + y) * nx + k;  // cz = c nz + z
+    const C v = cscale(s[l * LS + k], out_scale ? R(out_scale[b]) : R(1));
+    out[o] = ident ? csub(ident[o], v) : v;
+  }
+}
+
+template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
+  using R = typename RealOf<C>::type;
+  const int nb = a.plist ? a.nb : a.B;
+  if (nb <= 0) return DBI_OK;
+  const R inv2h = R(1.0 / (2.0 * a.h));
+  const R *m = static_cast<const R *>(a.m);
+  const C *in = static_cast<const C *>(a.in), *tw = static_cast<const C *>(a.tw);
+  C *T = static_cast<C *>(a.T), *sig = static_cast<C *>(a.T2);
+  Ref6 ref;
+  for (int i = 0; i < 6; ++i) ref.v[i] = a.ref[i];
+  int rc;
+  const dim3 cg((a.nx + 127) / 128, a.nz * a.ny, nb);
+  k3_stress<C><<<cg, 128, 0, s>>>(a.nz, a.ny, a.nx, inv2h, m, ref, in, a.in_scale, a.plist, a.active, sig);
+  if ((rc = check_launch("k3_stress"))) return rc;
+  k3_source<C><<<cg, 128, 0, s>>>(a.nz, a.ny, a.nx, a.ly, a.lx, a.nf, inv2h, m, ref, in, a.in_scale, a.omega,
+                                  a.fidx, a.plist, a.active, sig, T);
+  if ((rc = check_launch("k3_source"))) return rc;
+  rc = DBI_ERR_UNSUPPORTED;
+  dispatch_len(a.lx, [&]<int LX>() {
+    constexpr int NL = 2048 / LX, NT = NL * LX / 8;
+    const size_t bytes = size_t(NL) * (LX + 1) * sizeof(C);
+    const long rows = long(nb) * 3 * a.nz * a.ny;
+    cudaError_t e = allow_smem(k3_fft_x<C, LX>, bytes);
+    if (e == cudaSuccess)
+      k3_fft_x<C, LX><<<unsigned((rows + NL - 1) / NL), NT, bytes, s>>>(nb, a.nz, a.ny, a.nx, a.ly, a.plist,
+                                                                       a.active, tw, T);
+    rc = e != cudaSuccess ? cuda_fail("k3_fft_x smem", e) : check_launch("k3_fft_x");
+  });
+  if (rc) return rc;
+  auto fft_y = [&](auto inv_tag) {
+    constexpr bool INV = decltype(inv_tag)::value;
+    rc = DBI_ERR_UNSUPPORTED;
+    dispatch_len(a.ly, [&]<int LY>() {
+      constexpr int CC = 2048 / LY, NT = CC * LY / 8;
+      const size_t bytes = size_t(CC) * (LY + 1) * sizeof(C);
+      cudaError_t e = allow_smem(k3_fft_y<C, LY, INV>, bytes);
+      const dim3 grid((a.lx + CC - 1) / CC, nb * 3 * a.nz);
+      if (e == cudaSuccess) k3_fft_y<C, LY, INV><<<grid, NT, bytes, s>>>(a.nz, a.ny, a.lx, a.plist, a.active, tw, T);
+      rc = e != cudaSuccess ? cuda_fail("k3_fft_y smem", e) : check_launch("k3_fft_y");
+    });
+    return rc;
+  };
+  if ((rc = fft_y(std::false_type{}))) return rc;
+  rc = DBI_ERR_UNSUPPORTED;
+  dispatch_len(a.lz, [&]<int LZ>() {
+    using Z = ZCfg<C, LZ>;
+    const size_t bytes = size_t(Z::NL) * Z::LS * sizeof(C);
+    const size_t plane = size_t(a.ly) * a.lx;
+    cudaError_t e = allow_smem(k3_fft_z_mul<C, LZ>, bytes);
+    const dim3 grid(unsigned((plane + Z::CC - 1) / Z::CC), nb);
+    if (e == cudaSuccess)
+      k3_fft_z_mul<C, LZ><<<grid, Z::NT, bytes, s>>>(a.nz, a.nf, plane, a.plist, a.active, a.fidx,
+                                                     static_cast<const C *>(a.Ghat), tw, T);
+    rc = e != cudaSuccess ? cuda_fail("k3_fft_z_mul smem", e) : check_launch("k3_fft_z_mul");
+  });
+  if (rc) return rc;
+  if ((rc = fft_y(std::true_type{}))) return rc;
+  rc = DBI_ERR_UNSUPPORTED;
+  dispatch_len(a.lx, [&]<int LX>() {
+    constexpr int NL = 2048 / LX, NT = NL * LX / 8;
+    const size_t bytes = size_t(NL) * (LX + 1) * sizeof(C);
+    const long rows = long(nb) * 3 * a.nz * a.ny;
+    cudaError_t e = allow_smem(k3_fft_x_epi<C, LX>, bytes);
+    if (e == cudaSuccess)
+      k3_fft_x_epi<C, LX><<<unsigned((rows + NL - 1) / NL), NT, bytes, s>>>(
+          nb, a.nz, a.ny, a.nx, a.ly, a.plist, a.active, tw, T, static_cast<const C *>(a.ident), a.out_scale,
+          static_cast<C *>(a.out));
+    rc = e != cudaSuccess ? cuda_fail("k3_fft_x_epi smem", e) : check_launch("k3_fft_x_epi");
+  });
+  return rc;
+}
+
+int run_operator_3d(const OpArgs &a, cudaStream_t s) {
+  if (a.epi != 0) {
+    set_error("the 3D operator has no fused inner products (use GMRES)");
+    return DBI_ERR_UNSUPPORTED;
+  }
+  return a.precision == DBI_C64 ? run3_typed<float2>(a, s) : run3_typed<double2>(a, s);
+}
+
+}  // namespace dbi
+
+// ---------------------------------------------------------------------------------------------
+// 3D Green's tables and incident fields
+// ---------------------------------------------------------------------------------------------
+namespace dbi {
+
+// G_ij at offset y != 0 (components 11, 12, 13, 22, 23, 33): with g = y / r,
+// D_c = exp(-i k_c r) / (4 pi rho c^2 r), Q_c = q + q^2, q = 1 / (i k_c r),
+// G = D_p [g g^T + (3 g g^T - I) Q_p] - D_s [(g g^T - I) + (3 g g^T - I) Q_s].
+__device__ void green3_offset(double y1, double y2, double y3, double w, double alpha, double beta, double rho,
+                              double2 g[6]) {
+  const double r = sqrt(y1 * y1 + y2 * y2 + y3 * y3);
+  const double gm[3] = {y1 / r, y2 / r, y3 / r};
+  double2 Dc[2], Qc[2];
+  const double cs[2] = {alpha, beta};
+  for (int m = 0; m < 2; ++m) {
+    const double k = w / cs[m], kr = k * r, f = 1.0 / (4.0 * M_PI * rho * cs[m] * cs[m] * r);
+    double sn, cn;
+    sincos(kr, &sn, &cn);
+    Dc[m] = make_double2(cn * f, -sn * f);
+    Qc[m] = make_double2(-1.0 / (kr * kr), -1.0 / kr);  // -i / (k r) - 1 / (k r)^2
+  }
+  const int I[6] = {0, 0, 0, 1, 1, 2}, J[6] = {0, 1, 2, 1, 2, 2};
+  for (int e = 0; e < 6; ++e) {
+    const double gg = gm[I[e]] * gm[J[e]], d = I[e] == J[e] ? 1.0 : 0.0, t3 = 3.0 * gg - d;
+    // P-part: Dp (gg + t3 Qp); S-part: Ds ((gg - d) + t3 Qs)
+    const double2 ap = make_double2(gg + t3 * Qc[0].x, t3 * Qc[0].y);
+    const double2 as = make_double2(gg - d + t3 * Qc[1].x, t3 * Qc[1].y);
+    const double2 p = make_double2(Dc[0].x * ap.x - Dc[0].y * ap.y, Dc[0].x * ap.y + Dc[0].y * ap.x);
+    const double2 q = make_double2(Dc[1].x * as.x - Dc[1].y * as.y, Dc[1].x * as.y + Dc[1].y * as.x);
+    g[e] = make_double2(p.x - q.x, p.y - q.y);
+  }
+}
+
+// Mean of G over the ball of volume h^3: delta_ij (2 k_s^2 <g_s> + k_p^2 <g_p>) / (3 rho w^2),
+// <g_c> = 3 (exp(-i k a)(1 + i k a) - 1) / (4 pi a^3 k^2), a = h (3 / (4 pi))^(1/3).
+__device__ double2 green3_self(double h, double w, double alpha, double beta, double rho) {
+  const double a = h * cbrt(3.0 / (4.0 * M_PI));
+  double2 tot = make_double2(0.0, 0.0);
+  const double cs[2] = {alpha, beta}, wt[2] = {1.0, 2.0};
+  for (int m = 0; m < 2; ++m) {
+    const double k = w / cs[m], ka = k * a;
+    double sn, cn;
+    sincos(ka, &sn, &cn);
+    // exp(-i k a)(1 + i k a) - 1 = (cos ka + ka sin ka - 1) + i (ka cos ka - sin ka)
+    const double f = 3.0 / (4.0 * M_PI * a * a * a * k * k) * wt[m] * k * k;
+    tot.x += f * (cn + ka * sn - 1.0);
+    tot.y += f * (ka * cn - sn);
+  }
+  const double d = 1.0 / (3.0 * rho * w * w);
+  return make_double2(tot.x * d, tot.y * d);
+}
+
+// One thread per offset (dz, dy, dx) >= 0, mirrored into the octant slots: the diagonal
+// components are even in every coordinate, G_12 odd in x and y, G_13 in x and z, G_23 in y and z.
+template <typename C>
+__global__ void k3_green_space(int nz, int ny, int nx, int lz, int ly, int lx, double h, const double *omega,
+                               double rho, double alpha, double beta, double2 *W, C *Gspace) {
+  using R = typename RealOf<C>::type;
+  const int dx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int dzy = blockIdx.y, dz = dzy / ny, dy = dzy - dz * ny, f = blockIdx.z;
+  if (dx >= nx) return;
+  double2 g[6];
+  if (dz == 0 && dy == 0 && dx == 0) {
+    const double2 sv = green3_self(h, omega[f], alpha, beta, rho);
+    for (int e = 0; e < 6; ++e) g[e] = (e == 0 || e == 3 || e == 5) ? sv : make_double2(0.0, 0.0);
+  } else {
+    green3_offset(dx * h, dy * h, dz * h, omega[f], alpha, beta, rho, g);
+  }
+  const size_t vol = size_t(lz) * ly * lx;
+  for (int sz = 0; sz < 2; ++sz) {
+    if (sz && dz == 0) continue;
+    for (int sy = 0; sy < 2; ++sy) {
+      if (sy && dy == 0) continue;
+      for (int sx = 0; sx < 2; ++sx) {
+        if (sx && dx == 0) continue;
+        const size_t cell = (size_t(sz ? lz - dz : dz) * ly + (sy ? ly - dy : dy)) * lx + (sx ? lx - dx : dx);
+        const int sg[6] = {1, (sx ^ sy) ? -1 : 1, (sx ^ sz) ? -1 : 1, 1, (sy ^ sz) ? -1 : 1, 1};
+        for (int e = 0; e < 6; ++e) {
+          const double2 v = make_double2(sg[e] * g[e].x, sg[e] * g[e].y);
+          W[(size_t(f) * 6 + e) * vol + cell] = v;
+          if (Gspace) Gspace[(size_t(f) * 6 + e) * vol + cell] = mk<C>(R(v.x), R(v.y));
+        }
+      }
+    }
+  }
+}
+
+template <typename C>
+__global__ void k3_scale_cast(const double2 *W, C *Ghat, size_t n, double scale) {
+  using R = typename RealOf<C>::type;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+    Ghat[i] = mk<C>(R(W[i].x * scale), R(W[i].y * scale));
+}
+
+// u0[b][i] = sum_j G_ij(x - x_s) f_j; problems with an out-of-range source or frequency get 0.
+template <typename C>
+__global__ void k3_incident(int nf, int nz, int ny, int nx, int lz, int ly, int lx, const int *fidx,
+                            const C *Gspace, const int *src, const double *forces, C *u0) {
+  using R = typename RealOf<C>::type;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int zy = blockIdx.y, z = zy / ny, y = zy - z * ny, b = blockIdx.z;
+  if (x >= nx) return;
+  const size_t cells = size_t(nz) * ny * nx, cell = (size_t(z) * ny + y) * nx + x;
+  C *o = u0 + size_t(b) * 3 * cells + cell;
+  const int zs = src[3 * b], ys = src[3 * b + 1], xs = src[3 * b + 2];
+  if (zs < 0 || zs >= nz || ys < 0 || ys >= ny || xs < 0 || xs >= nx || unsigned(fidx[b]) >= unsigned(nf)) {
+    for (int c = 0; c < 3; ++c) o[c * cells] = czero<C>();
+    return;
+  }
+  const int dz = (z - zs + lz) % lz, dy = (y - ys + ly) % ly, dx = (x - xs + lx) % lx;
+  const size_t vol = size_t(lz) * ly * lx, slot = (size_t(dz) * ly + dy) * lx + dx;
+  const C *G = Gspace + size_t(fidx[b]) * 6 * vol + slot;
+  const C g[6] = {G[0], G[vol], G[2 * vol], G[3 * vol], G[4 * vol], G[5 * vol]};
+  const R f1 = R(forces[3 * b]), f2 = R(forces[3 * b + 1]), f3 = R(forces[3 * b + 2]);
+  o[0] = cadd(cadd(cscale(g[0], f1), cscale(g[1], f2)), cscale(g[2], f3));
+  o[cells] = cadd(cadd(cscale(g[1], f1), cscale(g[3], f2)), cscale(g[4], f3));
+  o[2 * cells] = cadd(cadd(cscale(g[2], f1), cscale(g[4], f2)), cscale(g[5], f3));
+}
+
+static bool len_ok(int L) { return L >= 16 && L <= 1024 && (L & (L - 1)) == 0; }
+
+static int check_grid3(const dbi_grid3 *g) {
+  if (!g) { set_error("grid is NULL"); return DBI_ERR_ARG; }
+  if (g->nz < 1 || g->ny < 1 || g->nx < 1 || !(g->h > 0) || size_t(g->nz) * g->ny > 65535) {
+    set_error("3D grid needs nz, ny, nx >= 1, nz ny <= 65535 and h > 0");
+    return DBI_ERR_ARG;
+  }
+  if (!len_ok(g->lz) || !len_ok(g->ly) || !len_ok(g->lx)) {
+    set_error("FFT grid %d x %d x %d: each side must be a power of two in [16, 1024]", g->lz, g->ly, g->lx);
+    return DBI_ERR_UNSUPPORTED;
+  }
+  if (g->lz < 2 * g->nz - 1 || g->ly < 2 * g->ny - 1 || g->lx < 2 * g->nx - 1) {
+    set_error("FFT grid too small for the cells (need >= 2n - 1 on every side)");
+    return DBI_ERR_ARG;
+  }
+  return DBI_OK;
+}
+
+static size_t csize3(int precision) { return precision == DBI_C64 ? sizeof(float2) : sizeof(double2); }
+static size_t bytes_field3(const dbi_grid3 *g, int B, int precision) {
+  return align256(size_t(B) * 3 * g->nz * g->ny * g->nx * csize3(precision));
+}
+static size_t bytes_spec3(const dbi_grid3 *g, int B, int precision) {
+  return align256(size_t(B) * 3 * g->nz * g->ly * g->lx * csize3(precision));
+}
+static size_t bytes_sig3(const dbi_grid3 *g, int B, int precision) {
+  return align256(size_t(B) * 6 * g->nz * g->ny * g->nx * csize3(precision));
+}
+
+}  // namespace dbi
+
+using namespace dbi;
+
+extern "C" size_t dbi_workspace_bytes_3d(const dbi_grid3 *g, int B, int precision, int op, int restart) {
+  if (check_grid3(g) || check_precision(precision) || B < 0) return 0;
+  const size_t tw = bytes_twiddles(precision);
+  switch (op) {
+    case DBI_OP_GREENS:  // B counts frequencies
+      return align256(size_t(kTwiddleN) * sizeof(double2)) +
+             align256(size_t(B) * 6 * g->lz * g->ly * g->lx * sizeof(double2));
+    case DBI_OP_APPLY:
+      return tw + bytes_spec3(g, B, precision) + bytes_sig3(g, B, precision) + bytes_scales(B);
+    case DBI_OP_SOLVE:
+      if (restart < 1 || restart > kGmresMaxRestart) return 0;
+      return tw + bytes_spec3(g, B, precision) + bytes_sig3(g, B, precision) +
+             gmres_bytes_fields(bytes_field3(g, B, precision), B, restart);
+    default:
+      return 0;
+  }
+}
+
+extern "C" int greens_tabulate_3d(const dbi_grid3 *g, const dbi_medium *ref, const double *omega, int nf,
+                                  int precision, void *Ghat, void *Gspace, void *work, size_t work_bytes,
+                                  dbi_stream stream) {
+  clear_error();
+  int rc;
+  if ((rc = check_grid3(g)) || (rc = check_precision(precision))) return rc;
+  if (!ref || reference_is_vti(*ref) || !(ref->rho0 > 0) || !(ref->alpha0 > ref->beta0) || !(ref->beta0 > 0)) {
+    set_error("the 3D reference must be isotropic with rho0 > 0 and alpha0 > beta0 > 0");
+    return DBI_ERR_ARG;
+  }
+  if (nf < 1 || !omega || !Ghat) { set_error("need nf >= 1, omega and Ghat"); return DBI_ERR_ARG; }
+  const size_t need = dbi_workspace_bytes_3d(g, nf, precision, DBI_OP_GREENS, 1);
+  if (!work || work_bytes < need) {
+    set_error("work buffer of %zu bytes, need %zu", work_bytes, need);
+    return DBI_ERR_WORKSPACE;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Arena ar(work, work_bytes);
+  double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
+  const size_t vol = size_t(g->lz) * g->ly * g->lx, tab = size_t(nf) * 6 * vol;
+  double2 *W = static_cast<double2 *>(ar.take(tab * sizeof(double2)));
+  if ((rc = launch_twiddles(tw, DBI_C128, s))) return rc;
+  cudaError_t e = cudaMemsetAsync(W, 0, tab * sizeof(double2), s);
+  if (e == cudaSuccess && Gspace) e = cudaMemsetAsync(Gspace, 0, tab * csize3(precision), s);
+  if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(3D Green table)", e);
+  const dim3 grid((g->nx + 127) / 128, g->nz * g->ny, nf);
+  if (precision == DBI_C64)
+    k3_green_space<float2><<<grid, 128, 0, s>>>(g->nz, g->ny, g->nx, g->lz, g->ly, g->lx, g->h, omega, ref->rho0,
+                                                ref->alpha0, ref->beta0, W, static_cast<float2 *>(Gspace));
+  else
+    k3_green_space<double2><<<grid, 128, 0, s>>>(g->nz, g->ny, g->nx, g->lz, g->ly, g->lx, g->h, omega,
+                                                 ref->rho0, ref->alpha0, ref->beta0, W,
+                                                 static_cast<double2 *>(Gspace));
+  if ((rc = check_launch("k3_green_space"))) return rc;
+  // FP64 3D FFT: x (rows), y (columns of the [ly][lx] planes), z (columns of [lz][ly lx])
+  if ((rc = fft_rows_fp64(W, long(nf) * 6 * g->lz * g->ly, g->lx, tw, s))) return rc;
+  if ((rc = fft_cols_fp64(W, nf * 6 * g->lz, g->ly, g->lx, tw, s))) return rc;
+  if ((rc = fft_cols_fp64(W, nf * 6, g->lz, g->ly * g->lx, tw, s))) return rc;
+  const double scale = g->h * g->h * g->h / (double(g->lz) * g->ly * g->lx);
+  const int blocks = int(std::min<size_t>((tab + 255) / 256, 8192));
+  if (precision == DBI_C64) k3_scale_cast<float2><<<blocks, 256, 0, s>>>(W, static_cast<float2 *>(Ghat), tab, scale);
+  else k3_scale_cast<double2><<<blocks, 256, 0, s>>>(W, static_cast<double2 *>(Ghat), tab, scale);
+  return check_launch("k3_scale_cast");
+}
+
+extern "C" int incident_field_3d(const dbi_grid3 *g, const dbi_batch *batch, const void *Gspace,
+                                 const int *src_cells, const double *forces, void *u0, int precision,
+                                 dbi_stream stream) {
+  clear_error();
+  int rc;
+  if ((rc = check_grid3(g)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
+  if (batch->B == 0) return DBI_OK;
+  if (!Gspace || !src_cells || !forces || !u0) { set_error("NULL Gspace, sources, forces or u0"); return DBI_ERR_ARG; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const dim3 grid((g->nx + 127) / 128, g->nz * g->ny, batch->B);
+  if (precision == DBI_C64)
+    k3_incident<float2><<<grid, 128, 0, s>>>(batch->nf, g->nz, g->ny, g->nx, g->lz, g->ly, g->lx, batch->fidx,
+                                             static_cast<const float2 *>(Gspace), src_cells, forces,
+                                             static_cast<float2 *>(u0));
+  else
+    k3_incident<double2><<<grid, 128, 0, s>>>(batch->nf, g->nz, g->ny, g->nx, g->lz, g->ly, g->lx, batch->fidx,
+                                              static_cast<const double2 *>(Gspace), src_cells, forces,
+                                              static_cast<double2 *>(u0));
+  return check_launch("k3_incident");
+}
+
+static int check_model3(const dbi_model3 *model, const dbi_batch *batch, int precision) {
+  int rc;
+  if (!model) { set_error("model is NULL"); return DBI_ERR_ARG; }
+  if ((rc = check_grid3(&model->grid)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
+  if (reference_is_vti(model->ref)) {
+    set_error("the 3D reference must be isotropic");
+    return DBI_ERR_ARG;
+  }
+  return DBI_OK;
+}
+
+static OpArgs args3(const dbi_model3 *model, const dbi_batch *batch, const void *Ghat, int precision, void *T,
+                    void *T2, void *tw) {
+  const dbi_grid3 *g = &model->grid;
+  OpArgs a{};
+  a.precision = precision;
+  a.nz = g->nz; a.ny = g->ny; a.nx = g->nx; a.lz = g->lz; a.ly = g->ly; a.lx = g->lx; a.h = g->h;
+  a.B = batch->B; a.nf = batch->nf; a.omega = batch->omega; a.fidx = batch->fidx;
+  a.m = model->m;
+  reference_values(model->ref, a.ref);
+  a.ref[5] = model->ref.rho0 * model->ref.beta0 * model->ref.beta0;  // C66
+  a.stencil = true; a.T = T; a.T2 = T2; a.Ghat = Ghat; a.tw = tw;
+  return a;
+}
+
+extern "C" int ls_apply_3d(const dbi_model3 *model, const dbi_batch *batch, const void *Ghat, const void *u,
+                           void *out, int precision, void *work, size_t work_bytes, dbi_stream stream) {
+  clear_error();
+  int rc = check_model3(model, batch, precision);
+  if (rc || batch->B == 0) return rc;
+  if (!Ghat || !u || !out || !model->m) { set_error("NULL model->m, Ghat, input or output"); return DBI_ERR_ARG; }
+  if (u == out) { set_error("input and output must be distinct buffers"); return DBI_ERR_ARG; }
+  const dbi_grid3 *g = &model->grid;
+  const size_t need = dbi_workspace_bytes_3d(g, batch->B, precision, DBI_OP_APPLY, 1);
+  if (!work || work_bytes < need) {
+    set_error("work buffer of %zu bytes, need %zu", work_bytes, need);
+    return DBI_ERR_WORKSPACE;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Arena ar(work, work_bytes);
+  void *tw = ar.take(bytes_twiddles(precision));
+  void *T = ar.take(bytes_spec3(g, batch->B, precision));
+  void *T2 = ar.take(bytes_sig3(g, batch->B, precision));
+  Scales sc = carve_scales(ar, batch->B);
+  if ((rc = launch_twiddles(tw, precision, s))) return rc;
+  const size_t n = size_t(3) * g->nz * g->ny * g->nx;
+  if ((rc = pow2_scales(u, precision, false, batch->B, n, sc.part, sc.scale, sc.inv, nullptr, s))) return rc;
+  OpArgs a = args3(model, batch, Ghat, precision, T, T2, tw);
+  a.in = u; a.ident = u; a.out = out;
+  a.in_scale = sc.scale; a.out_scale = sc.inv;
+  return run_operator(a, s);
+}
+
+extern "C" int ls_solve_3d(const dbi_model3 *model, const dbi_batch *batch, const void *Ghat, const void *rhs,
+                           void *u, const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
+                           void *work, size_t work_bytes, dbi_stream stream) {
+  clear_error();
+  int rc = check_model3(model, batch, precision);
+  if (rc || (rc = check_krylov(opts))) return rc;
+  if (restart < 1 || restart > kGmresMaxRestart) {
+    set_error("restart length %d outside [1, %d]", restart, kGmresMaxRestart);
+    return DBI_ERR_ARG;
+  }
+  if (batch->B == 0) return DBI_OK;
+  if (!Ghat || !rhs || !u || !model->m) { set_error("NULL model->m, Ghat, rhs or u"); return DBI_ERR_ARG; }
+  if (rhs == u) { set_error("rhs and u must be distinct buffers"); return DBI_ERR_ARG; }
+  const dbi_grid3 *g = &model->grid;
+  const size_t need = dbi_workspace_bytes_3d(g, batch->B, precision, DBI_OP_SOLVE, restart);
+  if (!work || work_bytes < need) {
+    set_error("work buffer of %zu bytes, need %zu", work_bytes, need);
+    return DBI_ERR_WORKSPACE;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Arena ar(work, work_bytes);
+  void *tw = ar.take(bytes_twiddles(precision));
+  void *T = ar.take(bytes_spec3(g, batch->B, precision));
+  void *T2 = ar.take(bytes_sig3(g, batch->B, precision));
+  if ((rc = launch_twiddles(tw, precision, s))) return rc;
+  OpArgs a = args3(model, batch, Ghat, precision, T, T2, tw);
+  return run_gmres(a, ar, bytes_field3(g, batch->B, precision), restart, rhs, u, opts->zero_guess != 0, *opts,
+                   status, s);
+}

@@ -213,6 +213,7 @@ int operator_parts(int nz, int lx, int precision) {
 }
 
 int run_operator(const OpArgs &a, cudaStream_t s) {
+  if (a.ny > 0) return run_operator_3d(a, s);
   if (a.group) return run_group_operator(a, s);
   if (a.Dhat) return run_form_k(a, s);
   return a.precision == DBI_C64 ? run_typed<float2>(a, s) : run_typed<double2>(a, s);

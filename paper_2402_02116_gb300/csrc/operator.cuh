@@ -31,7 +31,7 @@ struct OpArgs {
   const double *omega;  // device [nf]
   const int *fidx;      // device [B]
   const void *m;        // device [5][nz][nx] real (stencil mode): model or perturbation
-  double ref[5];        // subtracted from m per cell (the reference medium, or zeros)
+  double ref[6];        // subtracted from m per cell (the reference medium, or zeros; [5]: C66 in 3D)
   bool stencil;
   const void *in;       // device [B][2][nz][nx] complex
   const void *ident;    // device [B][2][nz][nx] complex or NULL
@@ -58,6 +58,10 @@ struct OpArgs {
   // unused and come from the group's member descriptors). offs: field offsets per problem.
   const GroupLaunch *group;
   const long long *offs;
+  // 3D grids (ls3d.cu): ny > 0; fields [B][3][nz][ny][nx], m [6][nz][ny][nx]; T holds the spectra
+  // [B][3][nz][ly][lx] and T2 the stress [B][6][nz][ny][nx]; Ghat [nf][6][lz][ly][lx].
+  int ny, ly;
+  void *T2;
 };
 
 // Partials per problem written by the operator kernels (one per CTA row block).
@@ -65,6 +69,17 @@ int operator_parts(int nz, int lx, int precision);
 
 int run_operator(const OpArgs &a, cudaStream_t s);
 int run_form_k(const OpArgs &a, cudaStream_t s);
+int run_operator_3d(const OpArgs &a, cudaStream_t s);
+
+// Field elements per problem: 2 nz nx in 2D, 3 nz ny nx in 3D.
+inline size_t field_elems(const OpArgs &a) {
+  return a.ny > 0 ? size_t(3) * a.nz * a.ny * a.nx : size_t(2) * a.nz * a.nx;
+}
+
+// In-place FP64 FFTs of the Green's tables (greens.cu): nlines contiguous lines of length L, or
+// the columns of nmat row-major [L][width] matrices.
+int fft_rows_fp64(double2 *W, long nlines, int L, const double2 *tw, cudaStream_t s);
+int fft_cols_fp64(double2 *W, int nmat, int L, int width, const double2 *tw, cudaStream_t s);
 
 // Per-problem power-of-two normalisers of B arrays of n elements each (or of the extents offs
 // gives, when non-NULL; complex of the precision, or real when `real` is set): scale[b] = 2^-e

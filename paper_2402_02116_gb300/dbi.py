@@ -42,6 +42,15 @@ class Model(ctypes.Structure):
     _fields_ = [("grid", Grid), ("ref", Medium), ("m", c_void_p)]
 
 
+class Grid3(ctypes.Structure):
+    _fields_ = [("nz", c_int), ("ny", c_int), ("nx", c_int), ("lz", c_int), ("ly", c_int), ("lx", c_int),
+                ("h", c_double)]
+
+
+class Model3(ctypes.Structure):
+    _fields_ = [("grid", Grid3), ("ref", Medium), ("m", c_void_p)]
+
+
 class Batch(ctypes.Structure):
     _fields_ = [("B", c_int), ("nf", c_int), ("omega", c_void_p), ("fidx", c_void_p)]
 
@@ -109,6 +118,15 @@ SIGNATURES = {
     "dbi_gmres_workspace_bytes": (c_size_t, [POINTER(Grid), c_int, c_int, c_int]),
     "ls_solve_gmres": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
                                c_int, POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
+    "dbi_workspace_bytes_3d": (c_size_t, [POINTER(Grid3), c_int, c_int, c_int, c_int]),
+    "greens_tabulate_3d": (c_int, [POINTER(Grid3), POINTER(Medium), c_void_p, c_int, c_int, c_void_p, c_void_p,
+                                   c_void_p, c_size_t, c_void_p]),
+    "incident_field_3d": (c_int, [POINTER(Grid3), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                  c_void_p]),
+    "ls_apply_3d": (c_int, [POINTER(Model3), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                            c_size_t, c_void_p]),
+    "ls_solve_3d": (c_int, [POINTER(Model3), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
+                            c_int, POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
     "greens_tabulate_k": (c_int, [POINTER(Grid), POINTER(Medium), c_void_p, c_int, c_int, c_void_p, c_void_p,
                                   c_size_t, c_void_p]),
     "ls_apply_k": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p, c_int,
@@ -397,6 +415,86 @@ def ls_solve_gmres(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, 
     _check(load().ls_solve_gmres(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(rhs), _ptr(u),
                                  ctypes.byref(opts), int(restart), ctypes.byref(st), precision, _ptr(work), n,
                                  _stream(rhs.device)), "ls_solve_gmres")
+    return u, iters, relres, code
+
+
+# ---------------------------------------------------------------------------------------------
+# 3D extension
+# ---------------------------------------------------------------------------------------------
+def make_grid3(nz, ny, nx, lz, ly, lx, h) -> Grid3:
+    return Grid3(int(nz), int(ny), int(nx), int(lz), int(ly), int(lx), float(h))
+
+
+def workspace_bytes_3d(grid: Grid3, B: int, precision: int, op: int, restart: int = 30) -> int:
+    return int(load().dbi_workspace_bytes_3d(ctypes.byref(grid), int(B), int(precision), int(op), int(restart)))
+
+
+def _work3(grid, B, precision, op, device, restart=30):
+    n = workspace_bytes_3d(grid, B, precision, op, restart)
+    if n == 0:
+        raise DBIError("invalid 3D grid, precision or restart for the workspace query")
+    return torch.empty(n, dtype=torch.uint8, device=device), n
+
+
+def _model3(grid, ref, m, precision) -> Model3:
+    if m.dtype != real_dtype(precision):
+        raise DBIError(f"model must be {real_dtype(precision)} for this precision, got {m.dtype}")
+    _need_cuda(m)
+    if tuple(m.shape) != (6, grid.nz, grid.ny, grid.nx):
+        raise DBIError(f"model shape {tuple(m.shape)} != (6, {grid.nz}, {grid.ny}, {grid.nx})")
+    return Model3(grid, ref, m.data_ptr())
+
+
+def greens_tabulate_3d(grid: Grid3, ref: Medium, omega: torch.Tensor, precision: int = C64, with_space=True):
+    """Ghat [nf][6][lz][ly][lx] (h^3 / (lz ly lx) FFT(G)) and, if asked, Gspace of the same shape."""
+    _need_cuda(omega)
+    dev = omega.device
+    nf = int(omega.numel())
+    cd = complex_dtype(precision)
+    Ghat = torch.empty((nf, 6, grid.lz, grid.ly, grid.lx), dtype=cd, device=dev)
+    Gspace = torch.empty_like(Ghat) if with_space else None
+    work, n = _work3(grid, nf, precision, OP_GREENS, dev)
+    _check(load().greens_tabulate_3d(ctypes.byref(grid), ctypes.byref(ref), _ptr(omega), nf, precision, _ptr(Ghat),
+                                     _ptr(Gspace), _ptr(work), n, _stream(dev)), "greens_tabulate_3d")
+    return Ghat, Gspace
+
+
+def incident_field_3d(grid: Grid3, omega, fidx, Gspace, src_cells, forces):
+    precision = _precision(Gspace)
+    _need_cuda(Gspace, src_cells, forces)
+    batch = _batch(omega, fidx)
+    u0 = torch.empty((batch.B, 3, grid.nz, grid.ny, grid.nx), dtype=Gspace.dtype, device=Gspace.device)
+    _check(load().incident_field_3d(ctypes.byref(grid), ctypes.byref(batch), _ptr(Gspace), _ptr(src_cells),
+                                    _ptr(forces), _ptr(u0), precision, _stream(Gspace.device)), "incident_field_3d")
+    return u0
+
+
+def ls_apply_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, u, out=None):
+    precision = _precision(u)
+    _need_cuda(Ghat, u)
+    model = _model3(grid, ref, m, precision)
+    batch = _batch(omega, fidx)
+    out = torch.empty_like(u) if out is None else out
+    work, n = _work3(grid, batch.B, precision, OP_APPLY, u.device)
+    _check(load().ls_apply_3d(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u), _ptr(out), precision,
+                              _ptr(work), n, _stream(u.device)), "ls_apply_3d")
+    return out
+
+
+def ls_solve_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, restart=30, tol=1e-6, max_iter=1000,
+                check_every=8):
+    """A u = rhs in 3D by GMRES(restart); returns (u, iters, relres, code)."""
+    precision = _precision(rhs)
+    _need_cuda(Ghat, rhs)
+    model = _model3(grid, ref, m, precision)
+    batch = _batch(omega, fidx)
+    u = torch.empty_like(rhs) if u0 is None else u0.clone()
+    work, n = _work3(grid, batch.B, precision, OP_SOLVE, rhs.device, restart)
+    (iters, relres, code), st = _status(batch.B, rhs.device)
+    opts = _kopts(tol, max_iter, check_every, zero_guess=u0 is None)
+    _check(load().ls_solve_3d(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(rhs), _ptr(u),
+                              ctypes.byref(opts), int(restart), ctypes.byref(st), precision, _ptr(work), n,
+                              _stream(rhs.device)), "ls_solve_3d")
     return u, iters, relres, code
 
 

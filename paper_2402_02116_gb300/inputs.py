@@ -315,3 +315,115 @@ CONFIGS = {
     "c3": config3_linear_dbi,
     "c4": config4_misfit,
 }
+
+
+# ---------------------------------------------------------------------------------------------
+# 3D workloads (the paper's 3D extension): fields [3][nz][ny][nx], models [6][nz][ny][nx] of
+# (rho, C11, C13, C33, C55, C66); isotropic reference
+# ---------------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Workload3D:
+    name: str
+    nz: int
+    ny: int
+    nx: int
+    h: float
+    lz: int
+    ly: int
+    lx: int
+    rho0: float
+    alpha0: float
+    beta0: float
+    model: np.ndarray      # [6][nz][ny][nx]
+    freqs_hz: np.ndarray
+    src_cells: np.ndarray  # [n_src][3] (iz, iy, ix)
+    src_force: np.ndarray  # [n_src][3]
+    rec_cells: np.ndarray  # [n_rec][3]
+    krylov_tol: float = 1e-5
+    seed: int = 0
+
+    @property
+    def omegas(self) -> np.ndarray:
+        return 2.0 * np.pi * np.asarray(self.freqs_hz, dtype=np.float64)
+
+    @property
+    def nf(self) -> int:
+        return int(len(self.freqs_hz))
+
+    @property
+    def n_src(self) -> int:
+        return int(self.src_cells.shape[0])
+
+    @property
+    def n_problems(self) -> int:
+        return self.n_src * self.nf
+
+    def problem_fidx(self) -> np.ndarray:
+        return np.repeat(np.arange(self.nf, dtype=np.int32), self.n_src)
+
+    def problem_src(self) -> np.ndarray:
+        return np.tile(np.arange(self.n_src, dtype=np.int64), self.nf)
+
+
+def vti_background_3d(nz, ny, nx, rho=2200.0, alpha_v=2500.0, eps_ratio=1.2, delta=0.1) -> np.ndarray:
+    """The 2D VTI background extended along y with C66 = C55 (as the paper's modified 3D model)."""
+    m2 = vti_background(1, 1, rho, alpha_v, eps_ratio, delta)
+    vals = [float(m2[p, 0, 0]) for p in range(5)] + [float(m2[4, 0, 0])]
+    return np.broadcast_to(np.asarray(vals)[:, None, None, None], (6, nz, ny, nx)).copy()
+
+
+def _surface_grid(ny, nx, count):
+    k = int(round(math.sqrt(count)))
+    ys, xs = surface_line(ny, k), surface_line(nx, max(1, count // k))
+    return np.array([[0, y, x] for y in ys for x in xs][:count], dtype=np.int64)
+
+
+def small_case_3d(nz=4, ny=3, nx=5, h=10.0, seed=21, n_src=2, freqs=(8.0,), amp=0.1, lz=None, ly=None,
+                  lx=None) -> Workload3D:
+    """A small 3D case: isotropic reference (2000, 2000, 1155), the medium perturbed by +-amp per
+    parameter and cell, vertical point forces on the surface."""
+    rng = np.random.default_rng(seed)
+    rho0, a0, b0 = 2000.0, 2000.0, 1155.0
+    a2, b2 = a0 * a0, b0 * b0
+    ref = np.array([rho0, rho0 * a2, rho0 * (a2 - 2 * b2), rho0 * a2, rho0 * b2, rho0 * b2])
+    model = ref[:, None, None, None] * (1.0 + amp * (2.0 * rng.random((6, nz, ny, nx)) - 1.0))
+    src = _surface_grid(ny, nx, n_src)
+    return Workload3D(
+        name=f"small3d_{nz}x{ny}x{nx}", nz=nz, ny=ny, nx=nx, h=h,
+        lz=lz or fft_len(nz), ly=ly or fft_len(ny), lx=lx or fft_len(nx), rho0=rho0, alpha0=a0, beta0=b0,
+        model=model, freqs_hz=np.asarray(freqs, dtype=np.float64), src_cells=src,
+        src_force=np.tile([0.0, 0.3, 1.0], (len(src), 1)),
+        rec_cells=np.array([[0, y, x] for y in range(0, ny, 2) for x in range(0, nx, 2)], dtype=np.int64),
+        krylov_tol=1e-10, seed=seed)
+
+
+def hess3d_like(nz=32, ny=40, nx=80, h=25.0, n_src=16, freqs=(3.0, 5.0, 7.0, 9.0), seed=6) -> Workload3D:
+    """The size of the paper's modified 3D VTI example (2000 m x 1000 m x 800 m at h = 25 m:
+    80 x 40 x 32 cells): the VTI background extended along y (C66 = C55), three horizontal layers
+    and four Gaussian anomalies of +-15 % per parameter; isotropic reference; vertical forces on a
+    4 x 4 surface grid; receivers on every 2nd surface cell. (The paper's Hess model itself is not
+    available.)"""
+    rng = np.random.default_rng(seed)
+    m_bg = vti_background_3d(nz, ny, nx)
+    pert = np.zeros((6, nz, ny, nx))
+    bounds = np.sort(rng.integers(nz // 5, nz, size=3))
+    for k, z0 in enumerate(bounds):
+        pert[:, z0:] += rng.uniform(-0.15, 0.15, size=(6, 1, 1, 1)) / (k + 1)
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for _ in range(4):
+        c = rng.uniform([nz * 0.2, ny * 0.2, nx * 0.2], [nz * 0.8, ny * 0.8, nx * 0.8])
+        sig = rng.uniform(3.0, 8.0)
+        bump = np.exp(-((iz - c[0]) ** 2 + (iy - c[1]) ** 2 + (ix - c[2]) ** 2) / (2 * sig * sig))
+        pert += rng.choice([-0.15, 0.15], size=(6, 1, 1, 1)) * bump
+    model = m_bg * (1.0 + np.clip(pert, -0.15, 0.15))
+    rho = float(m_bg[0, 0, 0, 0])
+    a0 = math.sqrt(0.5 * (m_bg[1, 0, 0, 0] + m_bg[3, 0, 0, 0]) / rho)
+    b0 = math.sqrt(m_bg[4, 0, 0, 0] / rho)
+    src = _surface_grid(ny, nx, n_src)
+    return Workload3D(
+        name=f"hess3d_like_{nz}x{ny}x{nx}_{n_src}src_{len(freqs)}f", nz=nz, ny=ny, nx=nx, h=h,
+        lz=fft_len(nz), ly=fft_len(ny), lx=fft_len(nx), rho0=rho, alpha0=a0, beta0=b0, model=model,
+        freqs_hz=np.asarray(freqs, dtype=np.float64), src_cells=src,
+        src_force=np.tile([0.0, 0.0, 1.0], (len(src), 1)),
+        rec_cells=np.array([[0, y, x] for y in range(0, ny, 2) for x in range(0, nx, 2)], dtype=np.int64),
+        krylov_tol=1e-5, seed=seed)

@@ -113,3 +113,43 @@ class DeviceProblem:
         return dbi.normal_cg(self.grid, self.ref, self.m if m_b is None else m_b, self.omega, self.fidx,
                              self.Ghat, u_b, self.rec_cells, dd, iters=iters, lam=lam, lambda_rel=lambda_rel,
                              power_iters=power_iters, power_start=ps, tol=tol, max_iter=max_iter)
+
+
+class DeviceProblem3D:
+    """A 3D workload (inputs.Workload3D) copied to the device once; forwards to the 3D entry points."""
+
+    def __init__(self, w, precision: int = dbi.C64, device="cuda", model=None, with_space=True):
+        self.w = w
+        self.precision = precision
+        self.device = torch.device(device)
+        self.rdt = dbi.real_dtype(precision)
+        self.cdt = dbi.complex_dtype(precision)
+        self.grid = dbi.make_grid3(w.nz, w.ny, w.nx, w.lz, w.ly, w.lx, w.h)
+        self.ref = dbi.make_medium(w.rho0, w.alpha0, w.beta0)
+        dev = self.device
+        self.omega = torch.tensor(np.asarray(w.omegas, dtype=np.float64), device=dev)
+        self.fidx = torch.tensor(w.problem_fidx(), dtype=torch.int32, device=dev)
+        srcs = w.problem_src()
+        self.src_cells = torch.tensor(np.asarray(w.src_cells)[srcs], dtype=torch.int32, device=dev).contiguous()
+        self.forces = torch.tensor(np.asarray(w.src_force, dtype=np.float64)[srcs], device=dev).contiguous()
+        self.m = torch.as_tensor(np.asarray(w.model if model is None else model, dtype=np.float64)).to(
+            dev, self.rdt).contiguous()
+        self.Ghat, self.Gspace = dbi.greens_tabulate_3d(self.grid, self.ref, self.omega, precision, with_space)
+
+    @property
+    def B(self) -> int:
+        return int(self.fidx.numel())
+
+    def to_field(self, arr) -> torch.Tensor:
+        return torch.as_tensor(np.asarray(arr)).to(self.device, self.cdt).contiguous()
+
+    def incident(self):
+        return dbi.incident_field_3d(self.grid, self.omega, self.fidx, self.Gspace, self.src_cells, self.forces)
+
+    def apply(self, u):
+        return dbi.ls_apply_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u)
+
+    def solve(self, rhs, restart=30, tol=None, max_iter=2000, check_every=8, u0=None):
+        tol = self.w.krylov_tol if tol is None else tol
+        return dbi.ls_solve_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, rhs, u0=u0,
+                               restart=restart, tol=tol, max_iter=max_iter, check_every=check_every)
