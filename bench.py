@@ -13,6 +13,7 @@ second of wall time on the device.
     python bench.py --workload uneven40     # the 40-problem uneven batch (grids 64^2 .. 512^2)
     python bench.py --workload formk256     # operator passes in the paper-literal form of Eq. 9
     python bench.py --workload gmres256     # batched forward solves by GMRES(30) beside BiCGSTAB
+    python bench.py --workload hess3d       # 3D operator passes and GMRES solves, 80 x 40 x 32 cells
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own 32 sources x 8 frequencies
 (weak scaling) and the gradients are summed across ranks with one all-reduce per step.
@@ -21,6 +22,7 @@ With N > 1 (torchrun, one rank per GPU) every rank runs its own 32 sources x 8 f
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -54,13 +56,15 @@ def parse_args():
     ap.add_argument("--check-every", type=int, default=4,
                     help="BiCGSTAB iterations between host convergence checks (each check also "
                          "compacts the launches to the problems still active)")
-    ap.add_argument("--workload", choices=["vti256", "uneven40", "formk256", "gmres256"], default="vti256",
+    ap.add_argument("--workload", choices=["vti256", "uneven40", "formk256", "gmres256", "hess3d"],
+                    default="vti256",
                     help="vti256: the gradient step of the benchmark (default); uneven40: operator "
                          "passes over the 40-problem uneven batch (persistent launches, autotuned), "
                          "plus one graph-captured solve; formk256: operator passes over the 256^2 "
                          "batch in the paper-literal form (derivatives on G, Eq. 9) beside the "
                          "divergence form; gmres256: batched forward solves of the 256^2 batch by "
-                         "restarted GMRES beside BiCGSTAB")
+                         "restarted GMRES beside BiCGSTAB; hess3d: 3D operator passes and GMRES "
+                         "solves on 80 x 40 x 32 cells (16 sources x 4 frequencies)")
     ap.add_argument("--restart", type=int, default=30, help="GMRES restart length (gmres256)")
     ap.add_argument("--sources", type=int, default=32,
                     help="sources per GPU (32 is the benchmark workload; fewer make a smaller batch "
@@ -711,6 +715,86 @@ def run_gmres(args):
     print(json.dumps(result), flush=True)
 
 
+def run_hess3d(args):
+    """3D extension at the size of the paper's modified 3D VTI example (80 x 40 x 32 cells of 25 m,
+    FFT grid 256 x 128 x 64), 16 surface sources x 4 frequencies = 64 wavefields, complex64: one
+    step = one 3D operator pass over every wavefield; one GMRES(30) solve of the batch to 1e-5 is
+    timed after the steps."""
+    import torch
+    from paper_2402_02116_gb300 import build, dbi
+    from paper_2402_02116_gb300.problem import DeviceProblem3D
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    build.build()
+    dbi.load()
+    w = inputs.hess3d_like()
+    P = DeviceProblem3D(w, dbi.C64, device=dev)
+    u = P.incident()
+    out = torch.empty_like(u)
+    cells = w.nz * w.ny * w.nx * P.B
+    work, nbytes = dbi._work3(P.grid, P.B, dbi.C64, dbi.OP_APPLY, dev)
+    model = dbi._model3(P.grid, P.ref, P.m, dbi.C64)
+    batch = dbi._batch(P.omega, P.fidx)
+    lib = dbi.load()
+
+    def step():
+        dbi._check(lib.ls_apply_3d(ctypes.byref(model), ctypes.byref(batch), dbi._ptr(P.Ghat), dbi._ptr(u),
+                                   dbi._ptr(out), dbi.C64, dbi._ptr(work), nbytes, dbi._stream(dev)), "ls_apply_3d")
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = dbi.kernel_launches()
+    dbi.profile_begin(dbi.PROF_COLS)
+    with ClockSampler(gpu_id(dev)) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    z_ms, z_launches = dbi.profile_end()
+    ms = ev0.elapsed_time(ev1)
+    launches = dbi.kernel_launches() - n0
+    torch.cuda.synchronize()
+    t0 = time.time()
+    _, iters, _, code = P.solve(u, restart=30, tol=1e-5, max_iter=2000)
+    torch.cuda.synchronize()
+    solve_s = time.time() - t0
+    clocks = clk.summary()
+    peaks = load_peaks()
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6
+    # the z pass: per (ky, kx) column of every wavefield three forward and three inverse FFTs of
+    # length lz (5 L log2 L flops each) and the symmetric 3 x 3 complex product (66 flops) per kz
+    cols = P.B * w.ly * w.lx
+    z_flops = cols * (6 * 5 * w.lz * math.log2(w.lz) + 66 * w.lz) * args.steps
+    z_bytes = (P.B * 2 * 3 * w.nz * w.ly * w.lx * 8 + w.nf * 6 * w.lz * w.ly * w.lx * 8) * args.steps
+    z_s = z_ms * 1e-3
+    roof = {"bound": "alu", "achieved": z_flops / z_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured median)", "traffic": None,
+            "kernel": "k3_fft_z_mul (z-line FFTs of the three components, 3 x 3 kernel, inverse)",
+            "hbm_frac_of_algorithmic_bytes": z_bytes / z_s / (peaks.get("hbm_gbs", 6800.0) * 1e9),
+            "launches_timed": z_launches, "avg_launch_ms": z_ms / max(z_launches, 1),
+            "share_of_step_time": z_ms / ms if ms > 0 else None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    result = {
+        "metric": METRIC, "value": cells * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 (fp32 complex operator)",
+        "data": "synthetic (seeded 3D VTI model with layers and anomalies, the size of the paper's 3D example)",
+        "config": {"workload": f"3d: {w.name}, one operator pass over every wavefield", "nz": w.nz, "ny": w.ny,
+                   "nx": w.nx, "lz": w.lz, "ly": w.ly, "lx": w.lx, "wavefields": P.B,
+                   "l2": f"spectra larger than L2: {P.B * 3 * w.nz * w.ly * w.lx * 8 / 1e9:.2f} GB per pass"},
+        "roofline": roof, "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
+        "clocks": clocks,
+        "gmres_solve": {"seconds": solve_s, "all_converged": bool((code == dbi.CONVERGED).all()),
+                        "arnoldi_steps_mean": float(iters.float().mean()), "arnoldi_steps_max": int(iters.max())},
+    }
+    print(json.dumps(result), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -721,6 +805,8 @@ def main():
         run_formk(args)
     elif args.workload == "gmres256":
         run_gmres(args)
+    elif args.workload == "hess3d":
+        run_hess3d(args)
     else:
         run_ours(args)
 

@@ -255,6 +255,7 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
   Ref6 ref;
   for (int i = 0; i < 6; ++i) ref.v[i] = a.ref[i];
   int rc;
+  prof_mark(PROF_OPERATOR, false, s);
   const dim3 cg((a.nx + 127) / 128, a.nz * a.ny, nb);
   k3_stress<C><<<cg, 128, 0, s>>>(a.nz, a.ny, a.nx, inv2h, m, ref, in, a.in_scale, a.plist, a.active, sig);
   if ((rc = check_launch("k3_stress"))) return rc;
@@ -287,6 +288,7 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
     return rc;
   };
   if ((rc = fft_y(std::false_type{}))) return rc;
+  prof_mark(PROF_COLS, false, s);
   rc = DBI_ERR_UNSUPPORTED;
   dispatch_len(a.lz, [&]<int LZ>() {
     using Z = ZCfg<C, LZ>;
@@ -299,6 +301,7 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
                                                      static_cast<const C *>(a.Ghat), tw, T);
     rc = e != cudaSuccess ? cuda_fail("k3_fft_z_mul smem", e) : check_launch("k3_fft_z_mul");
   });
+  prof_mark(PROF_COLS, true, s);
   if (rc) return rc;
   if ((rc = fft_y(std::true_type{}))) return rc;
   rc = DBI_ERR_UNSUPPORTED;
@@ -313,6 +316,7 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
           static_cast<C *>(a.out));
     rc = e != cudaSuccess ? cuda_fail("k3_fft_x_epi smem", e) : check_launch("k3_fft_x_epi");
   });
+  prof_mark(PROF_OPERATOR, true, s);
   return rc;
 }
 
