@@ -138,12 +138,16 @@ __global__ void __launch_bounds__(256) k3_fft_x(int nb, int nz, int ny, int nx, 
   }
 }
 
-// FFT along y of the planes (slot, c, z) [ly][lx], CC columns per CTA. Forward: rows y >= ny read
+// FFT along y of the planes (slot, c, z) [ly][lx], CC columns per CTA (512-byte runs of a row in
+// complex64). Forward: rows y >= ny read
 // as zero, all ly written; inverse: all read, y < ny written.
+template <typename C, int LY> struct YCfg {
+  static constexpr int CC = 4096 / LY, LS = LY + 1, NT = CC * LY / 8;  // 512 threads
+};
 template <typename C, int LY, bool INV>
-__global__ void __launch_bounds__(256) k3_fft_y(int nz, int ny, int lx, const int *plist, const int *active,
+__global__ void __launch_bounds__(512) k3_fft_y(int nz, int ny, int lx, const int *plist, const int *active,
                                                 const C *tw, C *T) {
-  constexpr int CC = 2048 / LY, LS = LY + 1, NT = CC * LY / 8;
+  constexpr int CC = YCfg<C, LY>::CC, LS = YCfg<C, LY>::LS, NT = YCfg<C, LY>::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *s = reinterpret_cast<C *>(smem_raw);
   const int plane = blockIdx.y, slot = plane / (3 * nz);
@@ -164,8 +168,10 @@ __global__ void __launch_bounds__(256) k3_fft_y(int nz, int ny, int lx, const in
 
 // Per (ky, kx) column q of a slot: the three components' z-lines (z < nz, zero-padded to LZ),
 // forward FFT, out_i = sum_j Ghat_ij(kz, q) v_j, inverse FFT, z < nz written back.
+// CC columns per CTA (up to 32: 256-byte runs of each (component, z) row in complex64), 768
+// threads from LZ = 64 up.
 template <typename C, int LZ> struct ZCfg {
-  static constexpr int CC = 512 / LZ > 0 ? 512 / LZ : 1;
+  static constexpr int CC = 2048 / LZ < 32 ? 2048 / LZ : 32;
   static constexpr int NL = 3 * CC, LS = LZ + 1, NT = NL * LZ / 8;
 };
 template <typename C, int LZ>
@@ -278,7 +284,7 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
     constexpr bool INV = decltype(inv_tag)::value;
     rc = DBI_ERR_UNSUPPORTED;
     dispatch_len(a.ly, [&]<int LY>() {
-      constexpr int CC = 2048 / LY, NT = CC * LY / 8;
+      constexpr int CC = YCfg<C, LY>::CC, NT = YCfg<C, LY>::NT;
       const size_t bytes = size_t(CC) * (LY + 1) * sizeof(C);
       cudaError_t e = allow_smem(k3_fft_y<C, LY, INV>, bytes);
       const dim3 grid((a.lx + CC - 1) / CC, nb * 3 * a.nz);
