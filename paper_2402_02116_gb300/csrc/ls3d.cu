@@ -138,14 +138,13 @@ __global__ void __launch_bounds__(256) k3_fft_x(int nb, int nz, int ny, int nx, 
   }
 }
 
-// FFT along y of the planes (slot, c, z) [ly][lx], CC columns per CTA (512-byte runs of a row in
-// complex64). Forward: rows y >= ny read
+// FFT along y of the planes (slot, c, z) [ly][lx], CC columns per CTA. Forward: rows y >= ny read
 // as zero, all ly written; inverse: all read, y < ny written.
 template <typename C, int LY> struct YCfg {
-  static constexpr int CC = 4096 / LY, LS = LY + 1, NT = CC * LY / 8;  // 512 threads
+  static constexpr int CC = 2048 / LY, LS = LY + 1, NT = CC * LY / 8;  // 256 threads
 };
 template <typename C, int LY, bool INV>
-__global__ void __launch_bounds__(512) k3_fft_y(int nz, int ny, int lx, const int *plist, const int *active,
+__global__ void __launch_bounds__(256) k3_fft_y(int nz, int ny, int lx, const int *plist, const int *active,
                                                 const C *tw, C *T) {
   constexpr int CC = YCfg<C, LY>::CC, LS = YCfg<C, LY>::LS, NT = YCfg<C, LY>::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -168,14 +167,16 @@ __global__ void __launch_bounds__(512) k3_fft_y(int nz, int ny, int lx, const in
 
 // Per (ky, kx) column q of a slot: the three components' z-lines (z < nz, zero-padded to LZ),
 // forward FFT, out_i = sum_j Ghat_ij(kz, q) v_j, inverse FFT, z < nz written back.
-// CC columns per CTA (up to 32: 256-byte runs of each (component, z) row in complex64), 768
-// threads from LZ = 64 up.
+// CC = 512 / LZ columns per CTA (192 threads up to LZ = 512): small CTAs, several per SM. Wider
+// tiles (32 columns, 768 threads) gave longer row runs but fewer resident warps and were 60 %
+// slower at LZ = 64.
 template <typename C, int LZ> struct ZCfg {
-  static constexpr int CC = 2048 / LZ < 32 ? 2048 / LZ : 32;
+  static constexpr int CC = 512 / LZ > 0 ? 512 / LZ : 1;
   static constexpr int NL = 3 * CC, LS = LZ + 1, NT = NL * LZ / 8;
+  static constexpr int MIN_BLOCKS = sizeof(C) == 8 ? (NT <= 192 ? 8 : 4) : 1;  // complex128 would spill
 };
 template <typename C, int LZ>
-__global__ void __launch_bounds__(ZCfg<C, LZ>::NT) k3_fft_z_mul(int nz, int nf, size_t plane, const int *plist,
+__global__ void __launch_bounds__(ZCfg<C, LZ>::NT, ZCfg<C, LZ>::MIN_BLOCKS) k3_fft_z_mul(int nz, int nf, size_t plane, const int *plist,
                                                                 const int *active, const int *fidx, const C *Ghat,
                                                                 const C *tw, C *T) {
   using Z = ZCfg<C, LZ>;
