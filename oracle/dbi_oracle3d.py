@@ -235,3 +235,58 @@ class LSOracle3D:
         else:
             x, info = bicgstab(op, rhs.reshape(-1), tol=tol, maxiter=maxiter)
         return x.reshape(shape), info
+
+
+# ---------------------------------------------------------------------------------------------
+# Distorted-Born products in 3D (Eq. 20, 25-35 with the 3D VTI stiffness)
+# ---------------------------------------------------------------------------------------------
+def imaging_3d(u_a, u_b, omega, h):
+    """Pointwise imaging (real part) for (rho, C11, C13, C33, C55, C66): rho: Re(w^2 u_a . u_b);
+    C_p: -Re(eps(u_a)^T B_p eps(u_b)) with B_p = dC/dp of the 3D VTI Voigt matrix (C12 = C11 - 2 C66,
+    C44 = C55): B_C11 = E11 + E22 + E12 + E21, B_C13 = E13 + E31 + E23 + E32, B_C33 = E33,
+    B_C55 = E44 + E55, B_C66 = E66 - 2 (E12 + E21)."""
+    a = strain_3d(u_a, h)
+    b = strain_3d(u_b, h)
+    g = np.empty((N_PARAMS_3D,) + u_a.shape[1:])
+    g[0] = np.real(omega * omega * (u_a[0] * u_b[0] + u_a[1] * u_b[1] + u_a[2] * u_b[2]))
+    g[1] = -np.real((a[0] + a[1]) * (b[0] + b[1]))
+    g[2] = -np.real((a[0] + a[1]) * b[2] + a[2] * (b[0] + b[1]))
+    g[3] = -np.real(a[2] * b[2])
+    g[4] = -np.real(a[3] * b[3] + a[4] * b[4])
+    g[5] = -np.real(a[5] * b[5] - 2.0 * (a[0] * b[1] + a[1] * b[0]))
+    return g
+
+
+def sample_3d(u, rec_cells):
+    """P u: the three components at the receiver cells, [n_rec][3]."""
+    return np.stack([u[:, iz, iy, ix] for iz, iy, ix in rec_cells])
+
+
+def inject_3d(q, rec_cells, shape):
+    """P^T q: a field holding q[r] at receiver cell r (summed where receivers coincide)."""
+    out = np.zeros((3,) + tuple(shape), dtype=np.complex128)
+    for k, (iz, iy, ix) in enumerate(rec_cells):
+        out[:, iz, iy, ix] += q[k]
+    return out
+
+
+def frechet_3d(orc, model_b, U_b, fidx, dm, rec_cells, tol=1e-12):
+    """J dm for every problem: the virtual source w^2 dm_rho u_b + div(dC(dm) : eps(u_b)) convolved
+    with G, solved in the background, sampled at the receivers."""
+    D = np.zeros((len(fidx), len(rec_cells), 3), dtype=np.complex128)
+    for b, f in enumerate(fidx):
+        src = contrast_source_3d(U_b[b], dm, orc.omegas[f], orc.h)
+        du, _ = orc.solve(orc.convolve(src, f), model_b, f, tol=tol)
+        D[b] = sample_3d(du, rec_cells)
+    return D
+
+
+def adjoint_3d(orc, model_b, U_b, fidx, R, rec_cells, tol=1e-12):
+    """Re J^H R summed over the problems: conj(R) injected at the receivers, convolved with G,
+    solved in the background (the conjugate-source form of Eq. 33-35) and imaged against u_b."""
+    g = np.zeros((N_PARAMS_3D, orc.nz, orc.ny, orc.nx))
+    for b, f in enumerate(fidx):
+        q = inject_3d(np.conj(R[b]), rec_cells, (orc.nz, orc.ny, orc.nx))
+        ua, _ = orc.solve(orc.convolve(q, f), model_b, f, tol=tol)
+        g += imaging_3d(ua, U_b[b], orc.omegas[f], orc.h)
+    return g

@@ -2,7 +2,8 @@
 G = [k_s^2 g_s I + grad grad (g_s - g_p)] / (rho w^2) differentiated numerically, the elastic wave
 equation by finite differences (residual O(d^2)), the self-cell ball mean against a quadrature of
 the closed form, the direct sum against the FFT convolution, zero contrast, the Born series
-against the solve, and reciprocity of the discrete responses."""
+against the solve, reciprocity of the discrete responses, and the 3D Frechet and adjoint products
+(the dot test, and the Frechet product against central differences of the forward map)."""
 import math
 
 import numpy as np
@@ -136,3 +137,43 @@ def test_reciprocity():
         u_r, _ = orc.solve(orc.incident(0, r, fi), model, 0, tol=1e-13)
         a, b = u_s[i][r], u_r[j][s]
         assert abs(a - b) <= 1e-10 * abs(a), (i, j)
+
+
+def products_case():
+    orc, model, ref = case(nz=4, ny=3, nx=5, amp=0.1, seed=8)
+    rng = np.random.default_rng(9)
+    srcs = [(0, 1, 2), (0, 0, 4)]
+    forces = [(0.0, 0.0, 1.0), (0.3, 0.0, 1.0)]
+    fidx = [0, 0]
+    U_b = np.stack([orc.solve(orc.incident(0, s, fv), model, 0, tol=1e-13)[0] for s, fv in zip(srcs, forces)])
+    rec = [(0, y, x) for y in range(3) for x in range(0, 5, 2)]
+    return orc, model, ref, rng, fidx, U_b, rec, srcs, forces
+
+
+def test_frechet_adjoint_dot_product():
+    """<J dm, r>_Re = <dm, Re J^H r> for real dm: the imaging of every parameter is the exact adjoint
+    of its virtual source (a wrong B matrix, sign or conjugation breaks it)."""
+    orc, model, ref, rng, fidx, U_b, rec, _, _ = products_case()
+    dm = ref[:, None, None, None] * 0.01 * rng.standard_normal((6, 4, 3, 5))
+    r = rng.standard_normal((2, len(rec), 3)) + 1j * rng.standard_normal((2, len(rec), 3))
+    Jdm = o3.frechet_3d(orc, model, U_b, fidx, dm, rec, tol=1e-13)
+    g = o3.adjoint_3d(orc, model, U_b, fidx, r, rec, tol=1e-13)
+    lhs = float(np.real(np.vdot(r, Jdm)))
+    rhs = float(np.sum(dm * g))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+def test_frechet_equals_the_derivative_of_the_forward_map():
+    """J dm against the central difference of d(m) = P A(m)^-1 u0 (step 1e-4 of the perturbation):
+    the operator is affine in the model, so the difference is exact up to O(step^2)."""
+    orc, model, ref, rng, fidx, U_b, rec, srcs, forces = products_case()
+    dm = ref[:, None, None, None] * 0.05 * rng.standard_normal((6, 4, 3, 5))
+    Jdm = o3.frechet_3d(orc, model, U_b, fidx, dm, rec, tol=1e-13)
+    eps = 1e-4
+
+    def data(m):
+        return np.stack([o3.sample_3d(orc.solve(orc.incident(0, s, fv), m, 0, tol=1e-14)[0], rec)
+                         for s, fv in zip(srcs, forces)])
+
+    fd = (data(model + eps * dm) - data(model - eps * dm)) / (2 * eps)
+    assert np.linalg.norm(fd - Jdm) <= 1e-6 * np.linalg.norm(Jdm)
