@@ -245,6 +245,29 @@ int incident_field_3d(const dbi_grid3 *g, const dbi_batch *batch, const void *Gs
 int ls_apply_3d(const dbi_model3 *model, const dbi_batch *batch, const void *Ghat, const void *u,
                 void *out, int precision, void *work, size_t work_bytes, dbi_stream stream);
 
+/* dbi_products_workspace_bytes_3d -- work-buffer size of frechet_apply_3d / adjoint_apply_3d. */
+size_t dbi_products_workspace_bytes_3d(const dbi_grid3 *g, int B, int precision, int restart);
+
+/* frechet_apply_3d -- d = J dm in 3D (Eq. 20, 26-31): the virtual source
+ * w^2 dm_rho u_b + div(dC(dm) : eps(u_b)) convolved with G, solved in the background by
+ * GMRES(restart), sampled at the receivers. u_b device [B][3][nz][ny][nx]; rec_cells device
+ * [n_rec][3] int (iz, iy, ix); dm device [6][nz][ny][nx] real of the precision; d device
+ * [B][n_rec][3] complex out. */
+int frechet_apply_3d(const dbi_model3 *background, const dbi_batch *batch, const void *Ghat,
+                     const void *u_b, const int *rec_cells, int n_rec, const void *dm, void *d,
+                     const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
+                     void *work, size_t work_bytes, dbi_stream stream);
+
+/* adjoint_apply_3d -- g = Re J^H r summed over the problems (Eq. 25, 32-35 in 3D): conj(r)
+ * injected at the receivers, convolved with G, solved in the background, imaged against u_b:
+ * g_rho = sum Re(w^2 u_a . u_b), g_p = -sum Re(eps(u_a)^T B_p eps(u_b)) with the derivatives B_p
+ * of the 3D VTI stiffness (C11, C13, C33, C55, C66). r device [B][n_rec][3] complex; g device
+ * [6][nz][ny][nx] real of the precision out (FP64 accumulation). */
+int adjoint_apply_3d(const dbi_model3 *background, const dbi_batch *batch, const void *Ghat,
+                     const void *u_b, const int *rec_cells, int n_rec, const void *r, void *g,
+                     const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
+                     void *work, size_t work_bytes, dbi_stream stream);
+
 /* ls_solve_3d -- A u = rhs in 3D by restarted GMRES(restart) (as ls_solve_gmres). */
 int ls_solve_3d(const dbi_model3 *model, const dbi_batch *batch, const void *Ghat, const void *rhs,
                 void *u, const dbi_krylov_opts *opts, int restart, const dbi_status *status,

@@ -13,7 +13,8 @@
 //                   symmetric 3 x 3 Ghat product, inverse FFT along z      (in place, z < nz kept)
 //   k3_fft_y        inverse, y < ny kept
 //   k3_fft_x_epi    inverse FFT along x, x < nx kept, out = ident - result
-// The FFTs are the shared-memory Stockham transforms of fft.cuh. Ghat [nf][6][lz][ly][lx]
+// Without the stencil (plain convolution of the input, for the adjoint source) k3_copy_source
+// replaces the first two kernels. The FFTs are the shared-memory Stockham transforms of fft.cuh. Ghat [nf][6][lz][ly][lx]
 // (components 11, 12, 13, 22, 23, 33) carries h^3 / (lz ly lx).
 #include <algorithm>
 #include <cmath>
@@ -104,6 +105,24 @@ __global__ void __launch_bounds__(128) k3_source(int nz, int ny, int nx, int ly,
   C *Tb = T + size_t(slot) * 3 * nz * ly * lx;
   for (int c = 0; c < 3; ++c)
     Tb[((size_t(c) * nz + z) * ly + y) * lx + x] = cadd(dv[c], cscale(ub[c * cells + cell], wr));
+}
+
+// Plain convolution (no stencil): the input itself, times its scale, as the source rows of T.
+template <typename C>
+__global__ void __launch_bounds__(128) k3_copy_source(int nz, int ny, int nx, int ly, int lx, const C *u,
+                                                      const double *in_scale, const int *plist, const int *active,
+                                                      C *T) {
+  using R = typename RealOf<C>::type;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int zy = blockIdx.y, z = zy / ny, y = zy - z * ny, slot = blockIdx.z;
+  if (x >= nx) return;
+  const int b = slot_problem(plist, active, slot);
+  if (b < 0) return;
+  const size_t cells = size_t(nz) * ny * nx, cell = (size_t(z) * ny + y) * nx + x;
+  const R sc = in_scale ? R(in_scale[b]) : R(1);
+  C *Tb = T + size_t(slot) * 3 * nz * ly * lx;
+  for (int c = 0; c < 3; ++c)
+    Tb[((size_t(c) * nz + z) * ly + y) * lx + x] = cscale(u[size_t(b) * 3 * cells + c * cells + cell], sc);
 }
 
 // Forward FFT along x of the rows (slot, c, z, y < ny) of T: points x < nx read, the rest zero.
@@ -264,11 +283,16 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
   int rc;
   prof_mark(PROF_OPERATOR, false, s);
   const dim3 cg((a.nx + 127) / 128, a.nz * a.ny, nb);
-  k3_stress<C><<<cg, 128, 0, s>>>(a.nz, a.ny, a.nx, inv2h, m, ref, in, a.in_scale, a.plist, a.active, sig);
-  if ((rc = check_launch("k3_stress"))) return rc;
-  k3_source<C><<<cg, 128, 0, s>>>(a.nz, a.ny, a.nx, a.ly, a.lx, a.nf, inv2h, m, ref, in, a.in_scale, a.omega,
-                                  a.fidx, a.plist, a.active, sig, T);
-  if ((rc = check_launch("k3_source"))) return rc;
+  if (a.stencil) {
+    k3_stress<C><<<cg, 128, 0, s>>>(a.nz, a.ny, a.nx, inv2h, m, ref, in, a.in_scale, a.plist, a.active, sig);
+    if ((rc = check_launch("k3_stress"))) return rc;
+    k3_source<C><<<cg, 128, 0, s>>>(a.nz, a.ny, a.nx, a.ly, a.lx, a.nf, inv2h, m, ref, in, a.in_scale, a.omega,
+                                    a.fidx, a.plist, a.active, sig, T);
+    if ((rc = check_launch("k3_source"))) return rc;
+  } else {
+    k3_copy_source<C><<<cg, 128, 0, s>>>(a.nz, a.ny, a.nx, a.ly, a.lx, in, a.in_scale, a.plist, a.active, T);
+    if ((rc = check_launch("k3_copy_source"))) return rc;
+  }
   rc = DBI_ERR_UNSUPPORTED;
   dispatch_len(a.lx, [&]<int LX>() {
     constexpr int NL = 2048 / LX, NT = NL * LX / 8;
@@ -655,4 +679,227 @@ extern "C" int ls_solve_3d(const dbi_model3 *model, const dbi_batch *batch, cons
   OpArgs a = args3(model, batch, Ghat, precision, T, T2, tw);
   return run_gmres(a, ar, bytes_field3(g, batch->B, precision), restart, rhs, u, opts->zero_guess != 0, *opts,
                    status, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Distorted-Born products in 3D (Eq. 20, 25-35 with the 3D VTI stiffness)
+// ---------------------------------------------------------------------------------------------
+namespace dbi {
+
+// d[b][r][c] = u[b][c] at receiver cell r (P u); out-of-range receivers give 0.
+template <typename C>
+__global__ void k3_sample(int B, int nz, int ny, int nx, int n_rec, const int *rec, const C *u, C *d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * n_rec) return;
+  const int b = i / n_rec, r = i - b * n_rec;
+  const int iz = rec[3 * r], iy = rec[3 * r + 1], ix = rec[3 * r + 2];
+  const bool in = iz >= 0 && iz < nz && iy >= 0 && iy < ny && ix >= 0 && ix < nx;
+  const size_t cells = size_t(nz) * ny * nx, cell = (size_t(iz) * ny + iy) * nx + ix;
+  for (int c = 0; c < 3; ++c)
+    d[size_t(i) * 3 + c] = in ? u[size_t(b) * 3 * cells + c * cells + cell] : czero<C>();
+}
+
+// q[b] = P^T conj(r[b]): conj(r) added at the receiver cells of a zeroed field (receivers that
+// share a cell are summed).
+template <typename C>
+__global__ void k3_inject_conj(int B, int nz, int ny, int nx, int n_rec, const int *rec, const C *r, C *q) {
+  using R = typename RealOf<C>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * n_rec) return;
+  const int b = i / n_rec, k = i - b * n_rec;
+  const int iz = rec[3 * k], iy = rec[3 * k + 1], ix = rec[3 * k + 2];
+  if (iz < 0 || iz >= nz || iy < 0 || iy >= ny || ix < 0 || ix >= nx) return;
+  const size_t cells = size_t(nz) * ny * nx, cell = (size_t(iz) * ny + iy) * nx + ix;
+  for (int c = 0; c < 3; ++c) {
+    const C v = r[size_t(i) * 3 + c];
+    R *o = reinterpret_cast<R *>(q + size_t(b) * 3 * cells + c * cells + cell);
+    atomicAdd(o, v.x);
+    atomicAdd(o + 1, -v.y);
+  }
+}
+
+// g[p][cell] = sum_b imaging of problem b (FP64 accumulation in problem order): rho:
+// Re(w^2 u_a . u_b); C_p: -Re(eps(u_a)^T B_p eps(u_b)), B_C11 = E11 + E22 + E12 + E21,
+// B_C13 = E13 + E31 + E23 + E32, B_C33 = E33, B_C55 = E44 + E55, B_C66 = E66 - 2 (E12 + E21).
+template <typename C>
+__global__ void __launch_bounds__(128) k3_imaging(int B, int nf, int nz, int ny, int nx, double h, const double *omega,
+                                                  const int *fidx, const C *ua, const C *ub,
+                                                  typename RealOf<C>::type *g) {
+  using R = typename RealOf<C>::type;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int zy = blockIdx.y, z = zy / ny, y = zy - z * ny;
+  if (x >= nx) return;
+  const size_t cells = size_t(nz) * ny * nx, cell = (size_t(z) * ny + y) * nx + x;
+  const R inv2h = R(1.0 / (2.0 * h));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < B; ++b) {
+    if (unsigned(fidx[b]) >= unsigned(nf)) continue;
+    const double w = omega[fidx[b]];
+    C ea[6], eb[6];
+    for (int side = 0; side < 2; ++side) {
+      const C *u = (side ? ub : ua) + size_t(b) * 3 * cells;
+      auto U = [&](int c, int dz, int dy, int dx) -> C {
+        const int zz = z + dz, yy = y + dy, xx = x + dx;
+        if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) return czero<C>();
+        return u[c * cells + (size_t(zz) * ny + yy) * nx + xx];
+      };
+      auto D = [&](int c, int k) -> C {
+        return cscale(csub(U(c, k == 2, k == 1, k == 0), U(c, -(k == 2), -(k == 1), -(k == 0))), inv2h);
+      };
+      C *e = side ? eb : ea;
+      e[0] = D(0, 0); e[1] = D(1, 1); e[2] = D(2, 2);
+      e[3] = cadd(D(1, 2), D(2, 1)); e[4] = cadd(D(0, 2), D(2, 0)); e[5] = cadd(D(0, 1), D(1, 0));
+    }
+    auto re = [](C a, C b) { return double(a.x) * double(b.x) - double(a.y) * double(b.y); };  // Re(a b)
+    const C *pa = ua + size_t(b) * 3 * cells + cell, *pb = ub + size_t(b) * 3 * cells + cell;
+    acc[0] += w * w * (re(pa[0], pb[0]) + re(pa[cells], pb[cells]) + re(pa[2 * cells], pb[2 * cells]));
+    const C a12 = cadd(ea[0], ea[1]), b12 = cadd(eb[0], eb[1]);
+    acc[1] -= re(a12, b12);
+    acc[2] -= re(a12, eb[2]) + re(ea[2], b12);
+    acc[3] -= re(ea[2], eb[2]);
+    acc[4] -= re(ea[3], eb[3]) + re(ea[4], eb[4]);
+    acc[5] -= re(ea[5], eb[5]) - 2.0 * (re(ea[0], eb[1]) + re(ea[1], eb[0]));
+  }
+  for (int p = 0; p < 6; ++p) g[p * cells + cell] = R(acc[p]);
+}
+
+}  // namespace dbi
+
+static size_t bytes_products3(const dbi_grid3 *g, int B, int precision, int restart) {
+  return bytes_twiddles(precision) + bytes_spec3(g, B, precision) + bytes_sig3(g, B, precision) +
+         bytes_scales(B) + 2 * bytes_field3(g, B, precision) + gmres_bytes_fields(bytes_field3(g, B, precision), B, restart);
+}
+
+extern "C" size_t dbi_products_workspace_bytes_3d(const dbi_grid3 *g, int B, int precision, int restart) {
+  if (check_grid3(g) || check_precision(precision) || B < 0 || restart < 1 || restart > kGmresMaxRestart) return 0;
+  return bytes_products3(g, B, precision, restart);
+}
+
+namespace {
+struct Prod3 {
+  OpArgs op;
+  Arena *ar;
+  void *src, *sol;
+  Scales sc;
+  cudaStream_t s;
+};
+}  // namespace
+
+// Common front of the 3D products: validation, workspace carving, twiddles.
+static int prepare3(const dbi_model3 *bg, const dbi_batch *batch, const void *Ghat, const void *u_b,
+                    const int *rec, int n_rec, const dbi_krylov_opts *opts, int restart, int precision, void *work,
+                    size_t work_bytes, dbi_stream stream, Arena &ar, Prod3 &p) {
+  int rc = check_model3(bg, batch, precision);
+  if (rc || (rc = check_krylov(opts))) return rc;
+  if (restart < 1 || restart > kGmresMaxRestart) {
+    set_error("restart length %d outside [1, %d]", restart, kGmresMaxRestart);
+    return DBI_ERR_ARG;
+  }
+  if (batch->B > 0 && (!Ghat || !u_b || !bg->m || !rec || n_rec < 1)) {
+    set_error("NULL model->m, Ghat, background fields or receivers");
+    return DBI_ERR_ARG;
+  }
+  const dbi_grid3 *g = &bg->grid;
+  const size_t need = bytes_products3(g, batch->B, precision, restart);
+  if (batch->B > 0 && (!work || work_bytes < need)) {
+    set_error("work buffer of %zu bytes, need %zu", work_bytes, need);
+    return DBI_ERR_WORKSPACE;
+  }
+  if (batch->B == 0) return DBI_OK;
+  p.s = reinterpret_cast<cudaStream_t>(stream);
+  void *tw = ar.take(bytes_twiddles(precision));
+  void *T = ar.take(bytes_spec3(g, batch->B, precision));
+  void *T2 = ar.take(bytes_sig3(g, batch->B, precision));
+  p.sc = carve_scales(ar, batch->B);
+  p.src = ar.take(bytes_field3(g, batch->B, precision));
+  p.sol = ar.take(bytes_field3(g, batch->B, precision));
+  p.ar = &ar;
+  if ((rc = launch_twiddles(tw, precision, p.s))) return rc;
+  p.op = args3(bg, batch, Ghat, precision, T, T2, tw);
+  return DBI_OK;
+}
+
+extern "C" int frechet_apply_3d(const dbi_model3 *background, const dbi_batch *batch, const void *Ghat,
+                                const void *u_b, const int *rec_cells, int n_rec, const void *dm, void *d,
+                                const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
+                                void *work, size_t work_bytes, dbi_stream stream) {
+  clear_error();
+  Arena ar(work, work_bytes);
+  Prod3 p{};
+  int rc = prepare3(background, batch, Ghat, u_b, rec_cells, n_rec, opts, restart, precision, work, work_bytes,
+                    stream, ar, p);
+  if (rc || batch->B == 0) return rc;
+  if (!dm || !d) { set_error("NULL dm or d"); return DBI_ERR_ARG; }
+  const dbi_grid3 *g = &background->grid;
+  const size_t n = size_t(3) * g->nz * g->ny * g->nx;
+  // virtual source convolved: G * (w^2 dm_rho u_b + div(dC(dm) : eps(u_b))): the operator with the
+  // perturbation as the model, a zero reference and no identity term
+  if ((rc = pow2_scales(u_b, precision, false, batch->B, n, p.sc.part, p.sc.scale, p.sc.inv, nullptr, p.s))) return rc;
+  OpArgs a = p.op;
+  a.m = dm;
+  for (int i = 0; i < 6; ++i) a.ref[i] = 0.0;
+  a.in = u_b; a.ident = nullptr; a.out = p.src;
+  a.in_scale = p.sc.scale; a.out_scale = p.sc.inv;
+  if ((rc = run_operator(a, p.s))) return rc;
+  // du = A_b^-1 src
+  if ((rc = run_gmres(p.op, ar, bytes_field3(g, batch->B, precision), restart, p.src, p.sol, true, *opts, status,
+                      p.s)))
+    return rc;
+  const int tot = batch->B * n_rec;
+  if (precision == DBI_C64)
+    k3_sample<float2><<<(tot + 127) / 128, 128, 0, p.s>>>(batch->B, g->nz, g->ny, g->nx, n_rec, rec_cells,
+                                                          static_cast<const float2 *>(p.sol), static_cast<float2 *>(d));
+  else
+    k3_sample<double2><<<(tot + 127) / 128, 128, 0, p.s>>>(batch->B, g->nz, g->ny, g->nx, n_rec, rec_cells,
+                                                           static_cast<const double2 *>(p.sol),
+                                                           static_cast<double2 *>(d));
+  return check_launch("k3_sample");
+}
+
+extern "C" int adjoint_apply_3d(const dbi_model3 *background, const dbi_batch *batch, const void *Ghat,
+                                const void *u_b, const int *rec_cells, int n_rec, const void *r, void *g_out,
+                                const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
+                                void *work, size_t work_bytes, dbi_stream stream) {
+  clear_error();
+  Arena ar(work, work_bytes);
+  Prod3 p{};
+  int rc = prepare3(background, batch, Ghat, u_b, rec_cells, n_rec, opts, restart, precision, work, work_bytes,
+                    stream, ar, p);
+  if (rc || batch->B == 0) return rc;
+  if (!r || !g_out) { set_error("NULL r or g"); return DBI_ERR_ARG; }
+  const dbi_grid3 *g = &background->grid;
+  const size_t n = size_t(3) * g->nz * g->ny * g->nx;
+  const int tot = batch->B * n_rec;
+  cudaError_t e = cudaMemsetAsync(p.sol, 0, bytes_field3(g, batch->B, precision), p.s);
+  if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(adjoint source)", e);
+  if (precision == DBI_C64)
+    k3_inject_conj<float2><<<(tot + 127) / 128, 128, 0, p.s>>>(batch->B, g->nz, g->ny, g->nx, n_rec, rec_cells,
+                                                               static_cast<const float2 *>(r),
+                                                               static_cast<float2 *>(p.sol));
+  else
+    k3_inject_conj<double2><<<(tot + 127) / 128, 128, 0, p.s>>>(batch->B, g->nz, g->ny, g->nx, n_rec, rec_cells,
+                                                                static_cast<const double2 *>(r),
+                                                                static_cast<double2 *>(p.sol));
+  if ((rc = check_launch("k3_inject_conj"))) return rc;
+  // src = G * q (plain convolution), then u_a = A_b^-1 src
+  if ((rc = pow2_scales(p.sol, precision, false, batch->B, n, p.sc.part, p.sc.scale, p.sc.inv, nullptr, p.s)))
+    return rc;
+  OpArgs a = p.op;
+  a.stencil = false;
+  a.in = p.sol; a.ident = nullptr; a.out = p.src;
+  a.in_scale = p.sc.scale; a.out_scale = p.sc.inv;
+  if ((rc = run_operator(a, p.s))) return rc;
+  if ((rc = run_gmres(p.op, ar, bytes_field3(g, batch->B, precision), restart, p.src, p.sol, true, *opts, status,
+                      p.s)))
+    return rc;
+  const dim3 grid((g->nx + 127) / 128, g->nz * g->ny);
+  if (precision == DBI_C64)
+    k3_imaging<float2><<<grid, 128, 0, p.s>>>(batch->B, batch->nf, g->nz, g->ny, g->nx, g->h, batch->omega,
+                                              batch->fidx, static_cast<const float2 *>(p.sol),
+                                              static_cast<const float2 *>(u_b), static_cast<float *>(g_out));
+  else
+    k3_imaging<double2><<<grid, 128, 0, p.s>>>(batch->B, batch->nf, g->nz, g->ny, g->nx, g->h, batch->omega,
+                                               batch->fidx, static_cast<const double2 *>(p.sol),
+                                               static_cast<const double2 *>(u_b), static_cast<double *>(g_out));
+  return check_launch("k3_imaging");
 }

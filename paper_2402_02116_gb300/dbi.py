@@ -127,6 +127,13 @@ SIGNATURES = {
                             c_size_t, c_void_p]),
     "ls_solve_3d": (c_int, [POINTER(Model3), POINTER(Batch), c_void_p, c_void_p, c_void_p, POINTER(KrylovOpts),
                             c_int, POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
+    "dbi_products_workspace_bytes_3d": (c_size_t, [POINTER(Grid3), c_int, c_int, c_int]),
+    "frechet_apply_3d": (c_int, [POINTER(Model3), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                                 c_void_p, POINTER(KrylovOpts), c_int, POINTER(Status), c_int, c_void_p, c_size_t,
+                                 c_void_p]),
+    "adjoint_apply_3d": (c_int, [POINTER(Model3), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                                 c_void_p, POINTER(KrylovOpts), c_int, POINTER(Status), c_int, c_void_p, c_size_t,
+                                 c_void_p]),
     "greens_tabulate_k": (c_int, [POINTER(Grid), POINTER(Medium), c_void_p, c_int, c_int, c_void_p, c_void_p,
                                   c_size_t, c_void_p]),
     "ls_apply_k": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p, c_int,
@@ -496,6 +503,42 @@ def ls_solve_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, re
                               ctypes.byref(opts), int(restart), ctypes.byref(st), precision, _ptr(work), n,
                               _stream(rhs.device)), "ls_solve_3d")
     return u, iters, relres, code
+
+
+def _products3(name, grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, x, out, tol, max_iter, restart,
+               check_every):
+    precision = _precision(u_b)
+    _need_cuda(Ghat, u_b, rec_cells, x)
+    if rec_cells.dtype != torch.int32 or rec_cells.dim() != 2 or rec_cells.shape[1] != 3:
+        raise DBIError("rec_cells must be int32 [n_rec][3]")
+    model = _model3(grid, ref, m_b, precision)
+    batch = _batch(omega, fidx)
+    n = int(load().dbi_products_workspace_bytes_3d(ctypes.byref(grid), batch.B, precision, int(restart)))
+    if n == 0:
+        raise DBIError("invalid 3D grid, precision or restart for the workspace query")
+    work = torch.empty(n, dtype=torch.uint8, device=u_b.device)
+    (iters, relres, code), st = _status(batch.B, u_b.device)
+    opts = _kopts(tol, max_iter, check_every, zero_guess=True)
+    _check(getattr(load(), name)(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u_b), _ptr(rec_cells),
+                                 int(rec_cells.shape[0]), _ptr(x), _ptr(out), ctypes.byref(opts), int(restart),
+                                 ctypes.byref(st), precision, _ptr(work), n, _stream(u_b.device)), name)
+    return out, (iters, relres, code)
+
+
+def frechet_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, dm, tol=1e-6,
+                     max_iter=1000, restart=30, check_every=8):
+    """J dm in 3D: [B][n_rec][3] complex data perturbations (and the solves' status)."""
+    d = torch.empty((u_b.shape[0], rec_cells.shape[0], 3), dtype=u_b.dtype, device=u_b.device)
+    return _products3("frechet_apply_3d", grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, dm, d, tol, max_iter,
+                      restart, check_every)
+
+
+def adjoint_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, r, tol=1e-6,
+                     max_iter=1000, restart=30, check_every=8):
+    """Re J^H r in 3D summed over the problems: [6][nz][ny][nx] real (and the solves' status)."""
+    g = torch.empty((6, grid.nz, grid.ny, grid.nx), dtype=real_dtype(_precision(u_b)), device=u_b.device)
+    return _products3("adjoint_apply_3d", grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, r, g, tol, max_iter,
+                      restart, check_every)
 
 
 def greens_tabulate_k(grid: Grid, ref: Medium, omega: torch.Tensor, precision: int = C64):

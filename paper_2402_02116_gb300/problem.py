@@ -134,6 +134,7 @@ class DeviceProblem3D:
         self.forces = torch.tensor(np.asarray(w.src_force, dtype=np.float64)[srcs], device=dev).contiguous()
         self.m = torch.as_tensor(np.asarray(w.model if model is None else model, dtype=np.float64)).to(
             dev, self.rdt).contiguous()
+        self.rec_cells = torch.tensor(np.asarray(w.rec_cells), dtype=torch.int32, device=dev).contiguous()
         self.Ghat, self.Gspace = dbi.greens_tabulate_3d(self.grid, self.ref, self.omega, precision, with_space)
 
     @property
@@ -148,6 +149,19 @@ class DeviceProblem3D:
 
     def apply(self, u):
         return dbi.ls_apply_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u)
+
+    def to_model(self, arr) -> torch.Tensor:
+        return torch.as_tensor(np.asarray(arr, dtype=np.float64)).to(self.device, self.rdt).contiguous()
+
+    def frechet(self, u_b, dm, tol=None, max_iter=2000, restart=30):
+        tol = self.w.krylov_tol if tol is None else tol
+        return dbi.frechet_apply_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u_b,
+                                    self.rec_cells, dm, tol=tol, max_iter=max_iter, restart=restart)
+
+    def adjoint(self, u_b, r, tol=None, max_iter=2000, restart=30):
+        tol = self.w.krylov_tol if tol is None else tol
+        return dbi.adjoint_apply_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u_b,
+                                    self.rec_cells, r, tol=tol, max_iter=max_iter, restart=restart)
 
     def solve(self, rhs, restart=30, tol=None, max_iter=2000, check_every=8, u0=None):
         tol = self.w.krylov_tol if tol is None else tol

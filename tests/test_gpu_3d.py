@@ -108,3 +108,32 @@ def test_hess3d_sized_batch():
         x = npy(u[q]).astype(np.complex128)
         r = np.linalg.norm(orc.apply(x, w.model, fidx[q]) - npy(u0[q])) / np.linalg.norm(npy(u0[q]))
         assert r < 3e-5, (q, r)
+
+
+@pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
+def test_frechet_and_adjoint_match_oracle(precision):
+    w = inputs.small_case_3d(nz=4, ny=3, nx=5, freqs=(9.0,), n_src=2, amp=0.1, seed=31)
+    P = DeviceProblem3D(w, precision)
+    tol = 1e-12 if precision == dbi.C128 else 1e-7
+    U_b, _, _, code = P.solve(P.incident(), tol=tol, max_iter=500)
+    assert bool((code == dbi.CONVERGED).all())
+    rng = np.random.default_rng(5)
+    ref = o3.reference_params_3d(w.rho0, w.alpha0, w.beta0)
+    dm = ref[:, None, None, None] * 0.01 * rng.standard_normal((6, w.nz, w.ny, w.nx))
+    r = rng.standard_normal((P.B, len(w.rec_cells), 3)) + 1j * rng.standard_normal((P.B, len(w.rec_cells), 3))
+    d, (it, _, cd) = P.frechet(U_b, P.to_model(dm), tol=tol)
+    g, (it2, _, cd2) = P.adjoint(U_b, P.to_field(r), tol=tol)
+    assert bool((cd == dbi.CONVERGED).all()) and bool((cd2 == dbi.CONVERGED).all())
+    orc = oracle_for(w)
+    Ub = npy(U_b).astype(np.complex128)
+    fidx = list(w.problem_fidx())
+    rec = [tuple(c) for c in w.rec_cells]
+    want_d = o3.frechet_3d(orc, w.model, Ub, fidx, dm, rec, tol=1e-13)
+    want_g = o3.adjoint_3d(orc, w.model, Ub, fidx, npy(P.to_field(r)).astype(np.complex128), rec, tol=1e-13)
+    t = 1e-8 if precision == dbi.C128 else 1e-4
+    assert rel(npy(d), want_d) < t
+    assert rel(npy(g), want_g) < t
+    # the GPU's own dot test
+    lhs = float(np.real(np.vdot(npy(P.to_field(r)).astype(np.complex128), npy(d).astype(np.complex128))))
+    rhs = float(np.sum(dm * npy(g)))
+    assert abs(lhs - rhs) <= (1e-9 if precision == dbi.C128 else 1e-4) * abs(lhs)
