@@ -602,6 +602,11 @@ static int check_model3(const dbi_model3 *model, const dbi_batch *batch, int pre
   int rc;
   if (!model) { set_error("model is NULL"); return DBI_ERR_ARG; }
   if ((rc = check_grid3(&model->grid)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
+  if (size_t(batch->B) * 3 * model->grid.nz > 65535) {  // grid.y of the y-line pass: (problem, component, z)
+    set_error("3D batch too large: B * 3 * nz = %zu exceeds 65535 (split the batch)",
+              size_t(batch->B) * 3 * model->grid.nz);
+    return DBI_ERR_UNSUPPORTED;
+  }
   if (reference_is_vti(model->ref)) {
     set_error("the 3D reference must be isotropic");
     return DBI_ERR_ARG;
