@@ -189,10 +189,14 @@ __global__ void __launch_bounds__(256) k3_fft_y(int nz, int ny, int lx, const in
 // CC = 512 / LZ columns per CTA (192 threads up to LZ = 512): small CTAs, several per SM. Wider
 // tiles (32 columns, 768 threads) gave longer row runs but fewer resident warps and were 60 %
 // slower at LZ = 64.
+#ifndef DBI_3D_ZCOLS
+#define DBI_3D_ZCOLS 512
+#endif
 template <typename C, int LZ> struct ZCfg {
-  static constexpr int CC = 512 / LZ > 0 ? 512 / LZ : 1;
+  static constexpr int CC = DBI_3D_ZCOLS / LZ > 0 ? DBI_3D_ZCOLS / LZ : 1;
   static constexpr int NL = 3 * CC, LS = LZ + 1, NT = NL * LZ / 8;
-  static constexpr int MIN_BLOCKS = sizeof(C) == 8 ? (NT <= 192 ? 8 : 4) : 1;  // complex128 would spill
+  // 40 registers for complex64 (8 CTAs of 192 threads per SM); complex128 would spill
+  static constexpr int MIN_BLOCKS = sizeof(C) == 8 ? (NT <= 192 ? 8 : (NT <= 384 ? 4 : 2)) : 1;
 };
 template <typename C, int LZ>
 __global__ void __launch_bounds__(ZCfg<C, LZ>::NT, ZCfg<C, LZ>::MIN_BLOCKS) k3_fft_z_mul(int nz, int nf, size_t plane, const int *plist,
