@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256) k3_fft_y(int nz, int ny, int lx, const in
 // tiles (32 columns, 768 threads) gave longer row runs but fewer resident warps and were 60 %
 // slower at LZ = 64.
 #ifndef DBI_3D_ZCOLS
-#define DBI_3D_ZCOLS 512
+#define DBI_3D_ZCOLS 1024
 #endif
 template <typename C, int LZ> struct ZCfg {
   static constexpr int CC = DBI_3D_ZCOLS / LZ > 0 ? DBI_3D_ZCOLS / LZ : 1;
