@@ -268,6 +268,22 @@ int adjoint_apply_3d(const dbi_model3 *background, const dbi_batch *batch, const
                      const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
                      void *work, size_t work_bytes, dbi_stream stream);
 
+/* dbi_normal_cg_workspace_bytes_3d -- work-buffer size of normal_cg_3d. */
+size_t dbi_normal_cg_workspace_bytes_3d(const dbi_grid3 *g, int B, int precision, int restart, int n_rec,
+                                        int iters);
+
+/* normal_cg_3d -- the Tikhonov normal equation (Eq. 23, 24) in 3D, as normal_cg: CG on the
+ * relative unknowns x_p = dm_p / s_p, s = (rho0, rho0 alpha0^2 for C11, C13 and C33,
+ * rho0 beta0^2 for C55 and C66), (Re J~^H J~ + lambda I) x = Re J~^H dd from x = 0, every product
+ * through frechet_apply_3d / adjoint_apply_3d (GMRES(restart) solves). dd device [B][n_rec][3];
+ * power_start device [6][nz][ny][nx] real (when lambda is estimated); dm device [6][nz][ny][nx]
+ * real out; lambda_out, hist_out (iters + 1 norms of the normal residual) host. */
+int normal_cg_3d(const dbi_model3 *background, const dbi_batch *batch, const void *Ghat, const void *u_b,
+                 const int *rec_cells, int n_rec, const void *dd, const dbi_cg_opts *cg,
+                 const void *power_start, void *dm, double *lambda_out, double *hist_out,
+                 const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
+                 void *work, size_t work_bytes, dbi_stream stream);
+
 /* ls_solve_3d -- A u = rhs in 3D by restarted GMRES(restart) (as ls_solve_gmres). */
 int ls_solve_3d(const dbi_model3 *model, const dbi_batch *batch, const void *Ghat, const void *rhs,
                 void *u, const dbi_krylov_opts *opts, int restart, const dbi_status *status,

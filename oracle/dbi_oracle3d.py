@@ -290,3 +290,43 @@ def adjoint_3d(orc, model_b, U_b, fidx, R, rec_cells, tol=1e-12):
         ua, _ = orc.solve(orc.convolve(q, f), model_b, f, tol=tol)
         g += imaging_3d(ua, U_b[b], orc.omegas[f], orc.h)
     return g
+
+
+def param_scale_3d(rho0, alpha0, beta0):
+    """Scale of the relative unknowns: rho0; rho0 alpha0^2 for C11, C13, C33; rho0 beta0^2 for C55, C66."""
+    a2, b2 = rho0 * alpha0 ** 2, rho0 * beta0 ** 2
+    return np.array([rho0, a2, a2, a2, b2, b2])
+
+
+def normal_cg_3d(orc, model_b, U_b, fidx, dd, rec_cells, iters=30, lam=None, lam_rel=1e-3, power_start=None,
+                 power_iters=10, tol=1e-12):
+    """Tikhonov normal equation (Re J~^H J~ + lambda I) x = Re J~^H dd on relative unknowns, as the
+    2D oracle's normal_cg; returns (dm, lambda, history of ||normal residual||)."""
+    sc = param_scale_3d(orc.rho0, orc.alpha0, orc.beta0)[:, None, None, None]
+
+    def H(x):
+        return sc * adjoint_3d(orc, model_b, U_b, fidx, frechet_3d(orc, model_b, U_b, fidx, sc * x, rec_cells, tol),
+                               rec_cells, tol)
+
+    if lam is None:
+        v = np.array(power_start, dtype=np.float64)
+        v = v / np.sqrt(np.sum(v * v))
+        for _ in range(power_iters):
+            w = H(v)
+            v = w / np.sqrt(np.sum(w * w))
+        lam = lam_rel * float(np.sum(v * H(v)))
+    r = sc * adjoint_3d(orc, model_b, U_b, fidx, dd, rec_cells, tol)
+    x = np.zeros_like(r)
+    p = r.copy()
+    rr = float(np.sum(r * r))
+    hist = [math.sqrt(rr)]
+    for _ in range(iters):
+        q = H(p) + lam * p
+        alpha = rr / float(np.sum(p * q))
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = float(np.sum(r * r))
+        hist.append(math.sqrt(rr_new))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return sc * x, lam, hist

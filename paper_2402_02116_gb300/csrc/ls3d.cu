@@ -19,8 +19,11 @@
 #include <algorithm>
 #include <cmath>
 
+#include <vector>
+
 #include "fft.cuh"
 #include "krylov.cuh"
+#include "mspace.cuh"
 
 namespace dbi {
 
@@ -730,10 +733,9 @@ __global__ void k3_inject_conj(int B, int nz, int ny, int nx, int n_rec, const i
 // g[p][cell] = sum_b imaging of problem b (FP64 accumulation in problem order): rho:
 // Re(w^2 u_a . u_b); C_p: -Re(eps(u_a)^T B_p eps(u_b)), B_C11 = E11 + E22 + E12 + E21,
 // B_C13 = E13 + E31 + E23 + E32, B_C33 = E33, B_C55 = E44 + E55, B_C66 = E66 - 2 (E12 + E21).
-template <typename C>
+template <typename C, typename GOut>
 __global__ void __launch_bounds__(128) k3_imaging(int B, int nf, int nz, int ny, int nx, double h, const double *omega,
-                                                  const int *fidx, const C *ua, const C *ub,
-                                                  typename RealOf<C>::type *g) {
+                                                  const int *fidx, const C *ua, const C *ub, GOut *g) {
   using R = typename RealOf<C>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int zy = blockIdx.y, z = zy / ny, y = zy - z * ny;
@@ -769,7 +771,7 @@ __global__ void __launch_bounds__(128) k3_imaging(int B, int nf, int nz, int ny,
     acc[4] -= re(ea[3], eb[3]) + re(ea[4], eb[4]);
     acc[5] -= re(ea[5], eb[5]) - 2.0 * (re(ea[0], eb[1]) + re(ea[1], eb[0]));
   }
-  for (int p = 0; p < 6; ++p) g[p * cells + cell] = R(acc[p]);
+  for (int p = 0; p < 6; ++p) g[p * cells + cell] = GOut(acc[p]);
 }
 
 }  // namespace dbi
@@ -784,20 +786,95 @@ extern "C" size_t dbi_products_workspace_bytes_3d(const dbi_grid3 *g, int B, int
   return bytes_products3(g, B, precision, restart);
 }
 
-namespace {
-struct Prod3 {
+namespace dbi {
+
+// Everything the 3D products share: the background operator, two field buffers, scales, and the
+// region the GMRES solves carve their basis from (afresh for every solve).
+struct Ctx3 {
   OpArgs op;
-  Arena *ar;
+  const dbi_grid3 *g;
+  const dbi_batch *batch;
   void *src, *sol;
   Scales sc;
+  void *gm_base;
+  size_t gm_bytes, fbytes;
+  int restart, precision;
+  dbi_krylov_opts opts;
+  const dbi_status *status;
   cudaStream_t s;
 };
-}  // namespace
 
-// Common front of the 3D products: validation, workspace carving, twiddles.
+static int solve3(const Ctx3 &c, const void *rhs, void *x) {
+  Arena ar(c.gm_base, c.gm_bytes);
+  return run_gmres(c.op, ar, c.fbytes, c.restart, rhs, x, true, c.opts, c.status, c.s);
+}
+
+// d = P A_b^-1 G (w^2 dm_rho u_b + div(dC(dm) : eps(u_b)))
+static int frechet3(const Ctx3 &c, const void *u_b, const int *rec, int n_rec, const void *dm, void *d) {
+  const dbi_grid3 *g = c.g;
+  const int B = c.batch->B;
+  const size_t n = size_t(3) * g->nz * g->ny * g->nx;
+  int rc;
+  if ((rc = pow2_scales(u_b, c.precision, false, B, n, c.sc.part, c.sc.scale, c.sc.inv, nullptr, c.s))) return rc;
+  OpArgs a = c.op;  // the perturbation as the model, a zero reference, no identity term
+  a.m = dm;
+  for (int i = 0; i < 6; ++i) a.ref[i] = 0.0;
+  a.in = u_b; a.ident = nullptr; a.out = c.src;
+  a.in_scale = c.sc.scale; a.out_scale = c.sc.inv;
+  if ((rc = run_operator(a, c.s)) || (rc = solve3(c, c.src, c.sol))) return rc;
+  const int tot = B * n_rec;
+  if (c.precision == DBI_C64)
+    k3_sample<float2><<<(tot + 127) / 128, 128, 0, c.s>>>(B, g->nz, g->ny, g->nx, n_rec, rec,
+                                                          static_cast<const float2 *>(c.sol), static_cast<float2 *>(d));
+  else
+    k3_sample<double2><<<(tot + 127) / 128, 128, 0, c.s>>>(B, g->nz, g->ny, g->nx, n_rec, rec,
+                                                           static_cast<const double2 *>(c.sol),
+                                                           static_cast<double2 *>(d));
+  return check_launch("k3_sample");
+}
+
+// g = Re J^H r (GOut: the precision's real type, or double for the normal equation)
+template <typename GOut>
+static int adjoint3(const Ctx3 &c, const void *u_b, const int *rec, int n_rec, const void *r, GOut *gout) {
+  const dbi_grid3 *g = c.g;
+  const int B = c.batch->B;
+  const size_t n = size_t(3) * g->nz * g->ny * g->nx;
+  const int tot = B * n_rec;
+  int rc;
+  cudaError_t e = cudaMemsetAsync(c.sol, 0, c.fbytes, c.s);
+  if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(adjoint source)", e);
+  if (c.precision == DBI_C64)
+    k3_inject_conj<float2><<<(tot + 127) / 128, 128, 0, c.s>>>(B, g->nz, g->ny, g->nx, n_rec, rec,
+                                                               static_cast<const float2 *>(r),
+                                                               static_cast<float2 *>(c.sol));
+  else
+    k3_inject_conj<double2><<<(tot + 127) / 128, 128, 0, c.s>>>(B, g->nz, g->ny, g->nx, n_rec, rec,
+                                                                static_cast<const double2 *>(r),
+                                                                static_cast<double2 *>(c.sol));
+  if ((rc = check_launch("k3_inject_conj"))) return rc;
+  if ((rc = pow2_scales(c.sol, c.precision, false, B, n, c.sc.part, c.sc.scale, c.sc.inv, nullptr, c.s))) return rc;
+  OpArgs a = c.op;  // plain convolution of the injected residual
+  a.stencil = false;
+  a.in = c.sol; a.ident = nullptr; a.out = c.src;
+  a.in_scale = c.sc.scale; a.out_scale = c.sc.inv;
+  if ((rc = run_operator(a, c.s)) || (rc = solve3(c, c.src, c.sol))) return rc;
+  const dim3 grid((g->nx + 127) / 128, g->nz * g->ny);
+  if (c.precision == DBI_C64)
+    k3_imaging<float2, GOut><<<grid, 128, 0, c.s>>>(B, c.batch->nf, g->nz, g->ny, g->nx, g->h, c.batch->omega,
+                                                    c.batch->fidx, static_cast<const float2 *>(c.sol),
+                                                    static_cast<const float2 *>(u_b), gout);
+  else
+    k3_imaging<double2, GOut><<<grid, 128, 0, c.s>>>(B, c.batch->nf, g->nz, g->ny, g->nx, g->h, c.batch->omega,
+                                                     c.batch->fidx, static_cast<const double2 *>(c.sol),
+                                                     static_cast<const double2 *>(u_b), gout);
+  return check_launch("k3_imaging");
+}
+
+// Validation and carving common to the 3D products (extra_bytes: what the caller carves after).
 static int prepare3(const dbi_model3 *bg, const dbi_batch *batch, const void *Ghat, const void *u_b,
-                    const int *rec, int n_rec, const dbi_krylov_opts *opts, int restart, int precision, void *work,
-                    size_t work_bytes, dbi_stream stream, Arena &ar, Prod3 &p) {
+                    const int *rec, int n_rec, const dbi_krylov_opts *opts, int restart, const dbi_status *status,
+                    int precision, void *work, size_t work_bytes, size_t extra_bytes, dbi_stream stream, Arena &ar,
+                    Ctx3 &c) {
   int rc = check_model3(bg, batch, precision);
   if (rc || (rc = check_krylov(opts))) return rc;
   if (restart < 1 || restart > kGmresMaxRestart) {
@@ -809,24 +886,34 @@ static int prepare3(const dbi_model3 *bg, const dbi_batch *batch, const void *Gh
     return DBI_ERR_ARG;
   }
   const dbi_grid3 *g = &bg->grid;
-  const size_t need = bytes_products3(g, batch->B, precision, restart);
+  const size_t need = bytes_products3(g, batch->B, precision, restart) + extra_bytes;
   if (batch->B > 0 && (!work || work_bytes < need)) {
     set_error("work buffer of %zu bytes, need %zu", work_bytes, need);
     return DBI_ERR_WORKSPACE;
   }
   if (batch->B == 0) return DBI_OK;
-  p.s = reinterpret_cast<cudaStream_t>(stream);
+  c.g = g;
+  c.batch = batch;
+  c.precision = precision;
+  c.restart = restart;
+  c.opts = *opts;
+  c.status = status;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spec3(g, batch->B, precision));
   void *T2 = ar.take(bytes_sig3(g, batch->B, precision));
-  p.sc = carve_scales(ar, batch->B);
-  p.src = ar.take(bytes_field3(g, batch->B, precision));
-  p.sol = ar.take(bytes_field3(g, batch->B, precision));
-  p.ar = &ar;
-  if ((rc = launch_twiddles(tw, precision, p.s))) return rc;
-  p.op = args3(bg, batch, Ghat, precision, T, T2, tw);
+  c.sc = carve_scales(ar, batch->B);
+  c.fbytes = bytes_field3(g, batch->B, precision);
+  c.src = ar.take(c.fbytes);
+  c.sol = ar.take(c.fbytes);
+  c.gm_bytes = gmres_bytes_fields(c.fbytes, batch->B, restart);
+  c.gm_base = ar.take(c.gm_bytes);
+  if ((rc = launch_twiddles(tw, precision, c.s))) return rc;
+  c.op = args3(bg, batch, Ghat, precision, T, T2, tw);
   return DBI_OK;
 }
+
+}  // namespace dbi
 
 extern "C" int frechet_apply_3d(const dbi_model3 *background, const dbi_batch *batch, const void *Ghat,
                                 const void *u_b, const int *rec_cells, int n_rec, const void *dm, void *d,
@@ -834,35 +921,12 @@ extern "C" int frechet_apply_3d(const dbi_model3 *background, const dbi_batch *b
                                 void *work, size_t work_bytes, dbi_stream stream) {
   clear_error();
   Arena ar(work, work_bytes);
-  Prod3 p{};
-  int rc = prepare3(background, batch, Ghat, u_b, rec_cells, n_rec, opts, restart, precision, work, work_bytes,
-                    stream, ar, p);
+  Ctx3 c{};
+  int rc = prepare3(background, batch, Ghat, u_b, rec_cells, n_rec, opts, restart, status, precision, work,
+                    work_bytes, 0, stream, ar, c);
   if (rc || batch->B == 0) return rc;
   if (!dm || !d) { set_error("NULL dm or d"); return DBI_ERR_ARG; }
-  const dbi_grid3 *g = &background->grid;
-  const size_t n = size_t(3) * g->nz * g->ny * g->nx;
-  // virtual source convolved: G * (w^2 dm_rho u_b + div(dC(dm) : eps(u_b))): the operator with the
-  // perturbation as the model, a zero reference and no identity term
-  if ((rc = pow2_scales(u_b, precision, false, batch->B, n, p.sc.part, p.sc.scale, p.sc.inv, nullptr, p.s))) return rc;
-  OpArgs a = p.op;
-  a.m = dm;
-  for (int i = 0; i < 6; ++i) a.ref[i] = 0.0;
-  a.in = u_b; a.ident = nullptr; a.out = p.src;
-  a.in_scale = p.sc.scale; a.out_scale = p.sc.inv;
-  if ((rc = run_operator(a, p.s))) return rc;
-  // du = A_b^-1 src
-  if ((rc = run_gmres(p.op, ar, bytes_field3(g, batch->B, precision), restart, p.src, p.sol, true, *opts, status,
-                      p.s)))
-    return rc;
-  const int tot = batch->B * n_rec;
-  if (precision == DBI_C64)
-    k3_sample<float2><<<(tot + 127) / 128, 128, 0, p.s>>>(batch->B, g->nz, g->ny, g->nx, n_rec, rec_cells,
-                                                          static_cast<const float2 *>(p.sol), static_cast<float2 *>(d));
-  else
-    k3_sample<double2><<<(tot + 127) / 128, 128, 0, p.s>>>(batch->B, g->nz, g->ny, g->nx, n_rec, rec_cells,
-                                                           static_cast<const double2 *>(p.sol),
-                                                           static_cast<double2 *>(d));
-  return check_launch("k3_sample");
+  return frechet3(c, u_b, rec_cells, n_rec, dm, d);
 }
 
 extern "C" int adjoint_apply_3d(const dbi_model3 *background, const dbi_batch *batch, const void *Ghat,
@@ -871,44 +935,131 @@ extern "C" int adjoint_apply_3d(const dbi_model3 *background, const dbi_batch *b
                                 void *work, size_t work_bytes, dbi_stream stream) {
   clear_error();
   Arena ar(work, work_bytes);
-  Prod3 p{};
-  int rc = prepare3(background, batch, Ghat, u_b, rec_cells, n_rec, opts, restart, precision, work, work_bytes,
-                    stream, ar, p);
+  Ctx3 c{};
+  int rc = prepare3(background, batch, Ghat, u_b, rec_cells, n_rec, opts, restart, status, precision, work,
+                    work_bytes, 0, stream, ar, c);
   if (rc || batch->B == 0) return rc;
   if (!r || !g_out) { set_error("NULL r or g"); return DBI_ERR_ARG; }
-  const dbi_grid3 *g = &background->grid;
-  const size_t n = size_t(3) * g->nz * g->ny * g->nx;
-  const int tot = batch->B * n_rec;
-  cudaError_t e = cudaMemsetAsync(p.sol, 0, bytes_field3(g, batch->B, precision), p.s);
-  if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(adjoint source)", e);
-  if (precision == DBI_C64)
-    k3_inject_conj<float2><<<(tot + 127) / 128, 128, 0, p.s>>>(batch->B, g->nz, g->ny, g->nx, n_rec, rec_cells,
-                                                               static_cast<const float2 *>(r),
-                                                               static_cast<float2 *>(p.sol));
-  else
-    k3_inject_conj<double2><<<(tot + 127) / 128, 128, 0, p.s>>>(batch->B, g->nz, g->ny, g->nx, n_rec, rec_cells,
-                                                                static_cast<const double2 *>(r),
-                                                                static_cast<double2 *>(p.sol));
-  if ((rc = check_launch("k3_inject_conj"))) return rc;
-  // src = G * q (plain convolution), then u_a = A_b^-1 src
-  if ((rc = pow2_scales(p.sol, precision, false, batch->B, n, p.sc.part, p.sc.scale, p.sc.inv, nullptr, p.s)))
-    return rc;
-  OpArgs a = p.op;
-  a.stencil = false;
-  a.in = p.sol; a.ident = nullptr; a.out = p.src;
-  a.in_scale = p.sc.scale; a.out_scale = p.sc.inv;
-  if ((rc = run_operator(a, p.s))) return rc;
-  if ((rc = run_gmres(p.op, ar, bytes_field3(g, batch->B, precision), restart, p.src, p.sol, true, *opts, status,
-                      p.s)))
-    return rc;
-  const dim3 grid((g->nx + 127) / 128, g->nz * g->ny);
-  if (precision == DBI_C64)
-    k3_imaging<float2><<<grid, 128, 0, p.s>>>(batch->B, batch->nf, g->nz, g->ny, g->nx, g->h, batch->omega,
-                                              batch->fidx, static_cast<const float2 *>(p.sol),
-                                              static_cast<const float2 *>(u_b), static_cast<float *>(g_out));
-  else
-    k3_imaging<double2><<<grid, 128, 0, p.s>>>(batch->B, batch->nf, g->nz, g->ny, g->nx, g->h, batch->omega,
-                                               batch->fidx, static_cast<const double2 *>(p.sol),
-                                               static_cast<const double2 *>(u_b), static_cast<double *>(g_out));
-  return check_launch("k3_imaging");
+  if (precision == DBI_C64) return adjoint3(c, u_b, rec_cells, n_rec, r, static_cast<float *>(g_out));
+  return adjoint3(c, u_b, rec_cells, n_rec, r, static_cast<double *>(g_out));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tikhonov normal equation in 3D (Eq. 23, 24): (Re J~^H J~ + lambda I) x = Re J~^H dd on the
+// relative unknowns x_p = dm_p / s_p, s = (rho0, C11_0 for C11 and C13, C33_0, C55_0, C66_0)
+// ---------------------------------------------------------------------------------------------
+static size_t bytes_ncg3(const dbi_grid3 *g, int B, int precision, int n_rec, int iters) {
+  const size_t nm = size_t(6) * g->nz * g->ny * g->nx;
+  return 5 * align256(nm * sizeof(double)) + align256(nm * sizeof(double)) + align256(kMBlocks * sizeof(double)) +
+         256 + align256(size_t(iters + 1) * sizeof(double)) +
+         align256(size_t(B) * n_rec * 3 * (precision == DBI_C64 ? sizeof(float2) : sizeof(double2)));
+}
+
+extern "C" size_t dbi_normal_cg_workspace_bytes_3d(const dbi_grid3 *g, int B, int precision, int restart, int n_rec,
+                                                  int iters) {
+  if (check_grid3(g) || check_precision(precision) || B < 1 || restart < 1 || restart > kGmresMaxRestart ||
+      n_rec < 1 || iters < 0)
+    return 0;
+  return bytes_products3(g, B, precision, restart) + bytes_ncg3(g, B, precision, n_rec, iters);
+}
+
+extern "C" int normal_cg_3d(const dbi_model3 *background, const dbi_batch *batch, const void *Ghat, const void *u_b,
+                            const int *rec_cells, int n_rec, const void *dd, const dbi_cg_opts *cg,
+                            const void *power_start, void *dm, double *lambda_out, double *hist_out,
+                            const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
+                            void *work, size_t work_bytes, dbi_stream stream) {
+  clear_error();
+  if (!cg || cg->iters < 0 || cg->iters > 4096 ||
+      (!(cg->lambda > 0) && (cg->power_iters < 1 || !power_start || !(cg->lambda_rel > 0)))) {
+    set_error("CG options need 0 <= iters <= 4096 and lambda > 0, or lambda_rel > 0, power_iters >= 1 and a start vector");
+    return DBI_ERR_ARG;
+  }
+  if (!batch || batch->B < 1) { set_error("normal_cg_3d needs at least one problem"); return DBI_ERR_ARG; }
+  if (!dd || !dm) { set_error("NULL dd or dm"); return DBI_ERR_ARG; }
+  Arena ar(work, work_bytes);
+  Ctx3 c{};
+  const size_t extra = background ? bytes_ncg3(&background->grid, batch->B, precision, n_rec, cg->iters) : 0;
+  int rc = prepare3(background, batch, Ghat, u_b, rec_cells, n_rec, opts, restart, status, precision, work,
+                    work_bytes, extra, stream, ar, c);
+  if (rc) return rc;
+  const dbi_grid3 *g = c.g;
+  const size_t plane = size_t(g->nz) * g->ny * g->nx, nm = 6 * plane, mb = nm * sizeof(double);
+  double *x = static_cast<double *>(ar.take(mb));
+  double *r = static_cast<double *>(ar.take(mb));
+  double *p = static_cast<double *>(ar.take(mb));
+  double *q = static_cast<double *>(ar.take(mb));
+  double *gd = static_cast<double *>(ar.take(mb));
+  void *dmt = ar.take(mb);  // the precision's real type
+  double *part = static_cast<double *>(ar.take(kMBlocks * sizeof(double)));
+  double *sc = static_cast<double *>(ar.take(16 * sizeof(double)));
+  double *hist = static_cast<double *>(ar.take(size_t(cg->iters + 1) * sizeof(double)));
+  void *dvec = ar.take(size_t(batch->B) * n_rec * 3 * (precision == DBI_C64 ? sizeof(float2) : sizeof(double2)));
+  cudaStream_t s = c.s;
+  const dbi_medium &m0 = background->ref;
+  const double a2 = m0.rho0 * m0.alpha0 * m0.alpha0, b2 = m0.rho0 * m0.beta0 * m0.beta0;
+  const MScale MS{{m0.rho0, a2, a2, a2, b2, b2}};
+  const MScale one{{1, 1, 1, 1, 1, 1}};
+  const int mblocks = int(std::min<size_t>((nm + 255) / 256, 4096));
+  auto H = [&](const double *pin, double *qout) -> int {  // S Re J^H J S p
+    int e;
+    if (precision == DBI_C64) k_mscale<double, float><<<mblocks, 256, 0, s>>>(6, plane, pin, static_cast<float *>(dmt), MS);
+    else k_mscale<double, double><<<mblocks, 256, 0, s>>>(6, plane, pin, static_cast<double *>(dmt), MS);
+    if ((e = check_launch("k_mscale"))) return e;
+    if ((e = frechet3(c, u_b, rec_cells, n_rec, dmt, dvec))) return e;
+    if ((e = adjoint3<double>(c, u_b, rec_cells, n_rec, dvec, gd))) return e;
+    k_mscale<double, double><<<mblocks, 256, 0, s>>>(6, plane, gd, qout, MS);
+    return check_launch("k_mscale");
+  };
+  auto dot = [&](const double *a, const double *b) -> int {
+    k_mdot<<<kMBlocks, kMThreads, 0, s>>>(nm, a, b, part);
+    return check_launch("k_mdot");
+  };
+  auto scal = [&](int what, int k) -> int {
+    k_scalar<<<1, 32, 0, s>>>(what, part, sc, hist, k);
+    return check_launch("k_scalar");
+  };
+  auto axpy = [&](int mode, const double *xx, double *yy, const double *qq, double *rr) -> int {
+    k_maxpy<<<mblocks, 256, 0, s>>>(nm, mode, sc, xx, yy, qq, rr);
+    return check_launch("k_maxpy");
+  };
+  double init_sc[16] = {0};
+  init_sc[S_LAMBDA] = cg->lambda;
+  init_sc[S_LREL] = cg->lambda_rel;
+  cudaError_t e = cudaMemcpyAsync(sc, init_sc, sizeof(init_sc), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync(scalars)", e);
+  if (!(cg->lambda > 0)) {  // lambda = lambda_rel x the Rayleigh quotient after power steps
+    if (precision == DBI_C64) k_mscale<float, double><<<mblocks, 256, 0, s>>>(6, plane, static_cast<const float *>(power_start), p, one);
+    else k_mscale<double, double><<<mblocks, 256, 0, s>>>(6, plane, static_cast<const double *>(power_start), p, one);
+    if ((rc = check_launch("k_mscale"))) return rc;
+    if ((rc = dot(p, p)) || (rc = scal(3, 0)) || (rc = axpy(2, p, p, nullptr, nullptr))) return rc;
+    for (int it = 0; it < cg->power_iters; ++it)
+      if ((rc = H(p, q)) || (rc = dot(q, q)) || (rc = scal(3, 0)) || (rc = axpy(2, q, p, nullptr, nullptr))) return rc;
+    if ((rc = H(p, q)) || (rc = dot(p, q)) || (rc = scal(4, 0))) return rc;
+  }
+  if ((rc = adjoint3<double>(c, u_b, rec_cells, n_rec, dd, gd))) return rc;  // r = p = S Re J^H dd, x = 0
+  k_mscale<double, double><<<mblocks, 256, 0, s>>>(6, plane, gd, r, MS);
+  if ((rc = check_launch("k_mscale"))) return rc;
+  e = cudaMemsetAsync(x, 0, mb, s);
+  if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(x)", e);
+  if ((rc = axpy(4, r, p, nullptr, nullptr)) || (rc = dot(r, r)) || (rc = scal(0, 0))) return rc;
+  for (int k = 0; k < cg->iters; ++k) {
+    if ((rc = H(p, q)) || (rc = axpy(3, p, q, nullptr, nullptr))) return rc;  // q = H p + lambda p
+    if ((rc = dot(p, q)) || (rc = scal(1, 0))) return rc;
+    if ((rc = axpy(0, p, x, q, r))) return rc;
+    if ((rc = dot(r, r)) || (rc = scal(2, k + 1))) return rc;
+    if ((rc = axpy(1, r, p, nullptr, nullptr))) return rc;
+  }
+  if (precision == DBI_C64) k_mscale<double, float><<<mblocks, 256, 0, s>>>(6, plane, x, static_cast<float *>(dm), MS);
+  else k_mscale<double, double><<<mblocks, 256, 0, s>>>(6, plane, x, static_cast<double *>(dm), MS);
+  if ((rc = check_launch("k_mscale"))) return rc;
+  double lam = 0.0;
+  std::vector<double> h(size_t(cg->iters) + 1);
+  e = cudaMemcpyAsync(&lam, sc + S_LAMBDA, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail("reading the CG results", e);
+  if (lambda_out) *lambda_out = lam;
+  if (hist_out) for (size_t i = 0; i < h.size(); ++i) hist_out[i] = h[i];
+  return DBI_OK;
 }

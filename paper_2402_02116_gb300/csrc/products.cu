@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "krylov.cuh"
+#include "mspace.cuh"
 
 namespace dbi {
 
@@ -166,94 +167,6 @@ __global__ void k_residual(int B, int nrec, int nz, int nx, const int *cells, co
     for (int w = 0; w < int(blockDim.x >> 5); ++w) s += sh[w];
     *phi = 0.5 * s;
   }
-}
-
-// ----------------------------------------------------------------------------------------------
-// model-space vectors of the normal-equation CG (FP64)
-// ----------------------------------------------------------------------------------------------
-constexpr int kMBlocks = 64, kMThreads = 256;
-
-__global__ void k_mdot(size_t n, const double *a, const double *b, double *part) {
-  __shared__ double sh[kMThreads / 32];
-  double acc = 0.0;
-  for (size_t i = size_t(blockIdx.x) * kMThreads + threadIdx.x; i < n; i += size_t(kMBlocks) * kMThreads)
-    acc += a[i] * b[i];
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kMThreads / 32; ++w) s += sh[w];
-    part[blockIdx.x] = s;
-  }
-}
-
-__device__ __forceinline__ double sum_parts(const double *part) {
-  double s = 0.0;
-  for (int i = 0; i < kMBlocks; ++i) s += part[i];
-  return s;
-}
-
-// Scalar steps of CG and of the power iteration; sc holds the FP64 scalars:
-// 0 rr, 1 alpha, 2 beta, 3 lambda, 4 scratch (1/norm), 5 lambda_rel
-enum { S_RR = 0, S_ALPHA = 1, S_BETA = 2, S_LAMBDA = 3, S_INV = 4, S_LREL = 5 };
-
-__global__ void k_scalar(int what, const double *part, double *sc, double *hist, int k) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double s = sum_parts(part);
-  switch (what) {
-    case 0:  // rr = s, hist[0]
-      sc[S_RR] = s;
-      hist[0] = sqrt(s);
-      break;
-    case 1:  // alpha = rr / <p, q>
-      sc[S_ALPHA] = s != 0.0 ? sc[S_RR] / s : 0.0;
-      break;
-    case 2:  // beta = rr_new / rr, hist[k]
-      sc[S_BETA] = sc[S_RR] != 0.0 ? s / sc[S_RR] : 0.0;
-      sc[S_RR] = s;
-      hist[k] = sqrt(s);
-      break;
-    case 3:  // 1 / ||v||
-      sc[S_INV] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-      break;
-    case 4:  // lambda = lambda_rel * <v, H v>
-      sc[S_LAMBDA] = sc[S_LREL] * s;
-      break;
-  }
-}
-
-// y = alpha_sel * x + beta_sel * y elementwise with scalars picked from sc (or 1 / 0)
-__global__ void k_maxpy(size_t n, int mode, const double *sc, const double *x, double *y,
-                        const double *q, double *r) {
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    switch (mode) {
-      case 0:  // x += alpha p (y = x, x = p); r -= alpha q
-        y[i] += sc[S_ALPHA] * x[i];
-        r[i] -= sc[S_ALPHA] * q[i];
-        break;
-      case 1:  // p = r + beta p  (y = p, x = r)
-        y[i] = x[i] + sc[S_BETA] * y[i];
-        break;
-      case 2:  // y = x * inv
-        y[i] = x[i] * sc[S_INV];
-        break;
-      case 3:  // q += lambda p  (y = q, x = p)
-        y[i] += sc[S_LAMBDA] * x[i];
-        break;
-      case 4:  // copy
-        y[i] = x[i];
-        break;
-    }
-  }
-}
-
-// y[p][cell] = s_p * x[p][cell], converting between model-space types
-template <typename TI, typename TO>
-__global__ void k_mscale(size_t plane, const TI *x, TO *y, double s0, double s1, double s2, double s3, double s4) {
-  const double sc[5] = {s0, s1, s2, s3, s4};
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < 5 * plane; i += size_t(gridDim.x) * blockDim.x)
-    y[i] = TO(double(x[i]) * sc[i / plane]);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -506,18 +419,18 @@ extern "C" int normal_cg(const dbi_model *background, const dbi_batch *batch, co
   cudaStream_t s = c.s;
   double rv[5];
   reference_values(background->ref, rv);
-  const double S[5] = {rv[0], rv[1], rv[1], rv[3], rv[4]};  // C13 takes the scale of C11
+  const MScale MS{{rv[0], rv[1], rv[1], rv[3], rv[4], 0.0}};  // C13 takes the scale of C11
   const int mblocks = int(std::min<size_t>((nm + 255) / 256, 4096));
 
   // q = S adjoint(frechet(S p)) in FP64 model space
   auto H = [&](const double *pin, double *qout) -> int {
     int e;
-    if (precision == DBI_C64) k_mscale<double, float><<<mblocks, 256, 0, s>>>(plane, pin, static_cast<float *>(dmt), S[0], S[1], S[2], S[3], S[4]);
-    else k_mscale<double, double><<<mblocks, 256, 0, s>>>(plane, pin, static_cast<double *>(dmt), S[0], S[1], S[2], S[3], S[4]);
+    if (precision == DBI_C64) k_mscale<double, float><<<mblocks, 256, 0, s>>>(5, plane, pin, static_cast<float *>(dmt), MS);
+    else k_mscale<double, double><<<mblocks, 256, 0, s>>>(5, plane, pin, static_cast<double *>(dmt), MS);
     if ((e = check_launch("k_mscale"))) return e;
     if ((e = frechet_internal(c, u_b, rec, dmt, dvec))) return e;
     if ((e = adjoint_internal<double>(c, u_b, rec, dvec, gd))) return e;
-    k_mscale<double, double><<<mblocks, 256, 0, s>>>(plane, gd, qout, S[0], S[1], S[2], S[3], S[4]);
+    k_mscale<double, double><<<mblocks, 256, 0, s>>>(5, plane, gd, qout, MS);
     return check_launch("k_mscale");
   };
   auto dot = [&](const double *a, const double *b) -> int {
@@ -541,8 +454,9 @@ extern "C" int normal_cg(const dbi_model *background, const dbi_batch *batch, co
   if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync(scalars)", e);
 
   if (!(cg->lambda > 0)) {  // power iteration on Re J~^H J~
-    if (precision == DBI_C64) k_mscale<float, double><<<mblocks, 256, 0, s>>>(plane, static_cast<const float *>(power_start), p, 1, 1, 1, 1, 1);
-    else k_mscale<double, double><<<mblocks, 256, 0, s>>>(plane, static_cast<const double *>(power_start), p, 1, 1, 1, 1, 1);
+    const MScale one{{1, 1, 1, 1, 1, 1}};
+    if (precision == DBI_C64) k_mscale<float, double><<<mblocks, 256, 0, s>>>(5, plane, static_cast<const float *>(power_start), p, one);
+    else k_mscale<double, double><<<mblocks, 256, 0, s>>>(5, plane, static_cast<const double *>(power_start), p, one);
     if ((rc = check_launch("k_mscale"))) return rc;
     if ((rc = dot(p, p)) || (rc = scal(3, 0)) || (rc = axpy(2, p, p, nullptr, nullptr))) return rc;
     for (int it = 0; it < cg->power_iters; ++it) {
@@ -552,7 +466,7 @@ extern "C" int normal_cg(const dbi_model *background, const dbi_batch *batch, co
   }
   // CG from x = 0: r = p = S Re J^H dd
   if ((rc = adjoint_internal<double>(c, u_b, rec, dd, gd))) return rc;
-  k_mscale<double, double><<<mblocks, 256, 0, s>>>(plane, gd, r, S[0], S[1], S[2], S[3], S[4]);
+  k_mscale<double, double><<<mblocks, 256, 0, s>>>(5, plane, gd, r, MS);
   if ((rc = check_launch("k_mscale"))) return rc;
   e = cudaMemsetAsync(x, 0, mb, s);
   if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(x)", e);
@@ -564,8 +478,8 @@ extern "C" int normal_cg(const dbi_model *background, const dbi_batch *batch, co
     if ((rc = dot(r, r)) || (rc = scal(2, k + 1))) return rc;                  // beta, hist
     if ((rc = axpy(1, r, p, nullptr, nullptr))) return rc;                     // p
   }
-  if (precision == DBI_C64) k_mscale<double, float><<<mblocks, 256, 0, s>>>(plane, x, static_cast<float *>(dm), S[0], S[1], S[2], S[3], S[4]);
-  else k_mscale<double, double><<<mblocks, 256, 0, s>>>(plane, x, static_cast<double *>(dm), S[0], S[1], S[2], S[3], S[4]);
+  if (precision == DBI_C64) k_mscale<double, float><<<mblocks, 256, 0, s>>>(5, plane, x, static_cast<float *>(dm), MS);
+  else k_mscale<double, double><<<mblocks, 256, 0, s>>>(5, plane, x, static_cast<double *>(dm), MS);
   if ((rc = check_launch("k_mscale"))) return rc;
   double lam = 0.0;
   std::vector<double> h(size_t(cg->iters) + 1);

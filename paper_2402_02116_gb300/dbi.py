@@ -134,6 +134,10 @@ SIGNATURES = {
     "adjoint_apply_3d": (c_int, [POINTER(Model3), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p,
                                  c_void_p, POINTER(KrylovOpts), c_int, POINTER(Status), c_int, c_void_p, c_size_t,
                                  c_void_p]),
+    "dbi_normal_cg_workspace_bytes_3d": (c_size_t, [POINTER(Grid3), c_int, c_int, c_int, c_int, c_int]),
+    "normal_cg_3d": (c_int, [POINTER(Model3), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                             POINTER(CGOpts), c_void_p, c_void_p, POINTER(c_double), POINTER(c_double),
+                             POINTER(KrylovOpts), c_int, POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
     "greens_tabulate_k": (c_int, [POINTER(Grid), POINTER(Medium), c_void_p, c_int, c_int, c_void_p, c_void_p,
                                   c_size_t, c_void_p]),
     "ls_apply_k": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p, c_int,
@@ -539,6 +543,33 @@ def adjoint_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_
     g = torch.empty((6, grid.nz, grid.ny, grid.nx), dtype=real_dtype(_precision(u_b)), device=u_b.device)
     return _products3("adjoint_apply_3d", grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, r, g, tol, max_iter,
                       restart, check_every)
+
+
+def normal_cg_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, dd, iters=30, lam=None,
+                 lambda_rel=1e-3, power_iters=10, power_start=None, tol=1e-6, max_iter=1000, restart=30,
+                 check_every=8):
+    """Tikhonov normal-equation CG in 3D; returns (dm [6][nz][ny][nx], lambda, residual history)."""
+    precision = _precision(u_b)
+    _need_cuda(Ghat, u_b, dd, rec_cells, *([] if power_start is None else [power_start]))
+    model = _model3(grid, ref, m_b, precision)
+    batch = _batch(omega, fidx)
+    n_rec = int(rec_cells.shape[0])
+    n = int(load().dbi_normal_cg_workspace_bytes_3d(ctypes.byref(grid), batch.B, precision, int(restart), n_rec,
+                                                    int(iters)))
+    if n == 0:
+        raise DBIError("invalid arguments for the 3D normal-equation workspace query")
+    work = torch.empty(n, dtype=torch.uint8, device=u_b.device)
+    dm = torch.empty((6, grid.nz, grid.ny, grid.nx), dtype=real_dtype(precision), device=u_b.device)
+    (its, relres, code), st = _status(batch.B, u_b.device)
+    opts = _kopts(tol, max_iter, check_every, zero_guess=True)
+    cg = CGOpts(int(iters), float(lam) if lam is not None else 0.0, float(lambda_rel), int(power_iters))
+    lam_out = c_double(0.0)
+    hist = (c_double * (int(iters) + 1))()
+    _check(load().normal_cg_3d(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u_b), _ptr(rec_cells),
+                               n_rec, _ptr(dd), ctypes.byref(cg), _ptr(power_start), _ptr(dm), ctypes.byref(lam_out),
+                               hist, ctypes.byref(opts), int(restart), ctypes.byref(st), precision, _ptr(work), n,
+                               _stream(u_b.device)), "normal_cg_3d")
+    return dm, float(lam_out.value), list(hist)
 
 
 def greens_tabulate_k(grid: Grid, ref: Medium, omega: torch.Tensor, precision: int = C64):

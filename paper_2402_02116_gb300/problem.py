@@ -163,6 +163,13 @@ class DeviceProblem3D:
         return dbi.adjoint_apply_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u_b,
                                     self.rec_cells, r, tol=tol, max_iter=max_iter, restart=restart)
 
+    def normal_cg(self, u_b, dd, iters=30, lam=None, lambda_rel=1e-3, power_iters=10, power_start=None, tol=None,
+                  max_iter=2000, restart=30):
+        tol = self.w.krylov_tol if tol is None else tol
+        return dbi.normal_cg_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u_b, self.rec_cells,
+                                dd, iters=iters, lam=lam, lambda_rel=lambda_rel, power_iters=power_iters,
+                                power_start=power_start, tol=tol, max_iter=max_iter, restart=restart)
+
     def solve(self, rhs, restart=30, tol=None, max_iter=2000, check_every=8, u0=None):
         tol = self.w.krylov_tol if tol is None else tol
         return dbi.ls_solve_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, rhs, u0=u0,

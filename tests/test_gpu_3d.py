@@ -137,3 +137,30 @@ def test_frechet_and_adjoint_match_oracle(precision):
     lhs = float(np.real(np.vdot(npy(P.to_field(r)).astype(np.complex128), npy(d).astype(np.complex128))))
     rhs = float(np.sum(dm * npy(g)))
     assert abs(lhs - rhs) <= (1e-9 if precision == dbi.C128 else 1e-4) * abs(lhs)
+
+
+@pytest.mark.parametrize("estimate_lambda", [False, True])
+def test_normal_cg_matches_oracle(estimate_lambda):
+    """Six CG steps of the 3D normal equation (complex128) against the oracle's, with a given
+    lambda or lambda from power steps on the normal operator."""
+    w = inputs.small_case_3d(nz=4, ny=3, nx=5, freqs=(9.0,), n_src=2, amp=0.1, seed=33)
+    P = DeviceProblem3D(w, dbi.C128)
+    U_b, _, _, code = P.solve(P.incident(), tol=1e-12, max_iter=500)
+    rng = np.random.default_rng(6)
+    dd = rng.standard_normal((P.B, len(w.rec_cells), 3)) + 1j * rng.standard_normal((P.B, len(w.rec_cells), 3))
+    start = rng.standard_normal((6, w.nz, w.ny, w.nx))
+    kw = dict(iters=6, tol=1e-12)
+    if estimate_lambda:
+        kw.update(lam=None, lambda_rel=1e-2, power_iters=4)
+    else:
+        kw.update(lam=3e-4)
+    dm, lam, hist = P.normal_cg(U_b, P.to_field(dd), power_start=P.to_model(start) if estimate_lambda else None,
+                                **kw)
+    orc = oracle_for(w)
+    rec = [tuple(c) for c in w.rec_cells]
+    okw = dict(iters=6, tol=1e-13, lam=None if estimate_lambda else 3e-4, lam_rel=1e-2, power_start=start,
+               power_iters=4)
+    want, lam_o, hist_o = o3.normal_cg_3d(orc, w.model, npy(U_b), list(w.problem_fidx()), dd, rec, **okw)
+    assert lam == pytest.approx(lam_o, rel=1e-8)
+    assert np.allclose(hist, hist_o, rtol=1e-7)
+    assert rel(npy(dm), want) < 1e-7

@@ -177,3 +177,24 @@ def test_frechet_equals_the_derivative_of_the_forward_map():
 
     fd = (data(model + eps * dm) - data(model - eps * dm)) / (2 * eps)
     assert np.linalg.norm(fd - Jdm) <= 1e-6 * np.linalg.norm(Jdm)
+
+
+def test_normal_cg_against_a_dense_solve():
+    """Enough CG steps on the 3D normal equation reach the dense solution of
+    (Re J~^T J~ + lambda I) x = Re J~^T dd built column by column from the Frechet product."""
+    orc, model, ref, rng, fidx, U_b, rec, _, _ = products_case()
+    dd = rng.standard_normal((2, len(rec), 3)) + 1j * rng.standard_normal((2, len(rec), 3))
+    sc = o3.param_scale_3d(orc.rho0, orc.alpha0, orc.beta0)[:, None, None, None]
+    n = 6 * 4 * 3 * 5
+    cols = []
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        cols.append(o3.frechet_3d(orc, model, U_b, fidx, sc * e.reshape(6, 4, 3, 5), rec, tol=1e-13).reshape(-1))
+    J = np.stack(cols, axis=1)
+    lam = 1e-3 * np.linalg.norm(J, 2) ** 2
+    b = np.real(J.conj().T @ dd.reshape(-1))
+    x_dense = np.linalg.solve(np.real(J.conj().T @ J) + lam * np.eye(n), b)
+    dm, lam_out, hist = o3.normal_cg_3d(orc, model, U_b, fidx, dd, rec, iters=150, lam=lam, tol=1e-13)
+    assert lam_out == lam and hist[-1] < 1e-8 * hist[0]
+    assert np.linalg.norm(dm / sc - x_dense.reshape(6, 4, 3, 5)) <= 1e-6 * np.linalg.norm(x_dense)
