@@ -268,6 +268,11 @@ int adjoint_apply_3d(const dbi_model3 *background, const dbi_batch *batch, const
                      const dbi_krylov_opts *opts, int restart, const dbi_status *status, int precision,
                      void *work, size_t work_bytes, dbi_stream stream);
 
+/* sample_3d -- d[b][r][c] = u[b][c] at receiver cell r (the sampling P of Eq. 27 in 3D); u device
+ * [B][3][nz][ny][nx], rec_cells device [n_rec][3] int, d device [B][n_rec][3] complex out. */
+int sample_3d(const dbi_grid3 *g, int B, const int *rec_cells, int n_rec, const void *u, void *d,
+              int precision, dbi_stream stream);
+
 /* dbi_normal_cg_workspace_bytes_3d -- work-buffer size of normal_cg_3d. */
 size_t dbi_normal_cg_workspace_bytes_3d(const dbi_grid3 *g, int B, int precision, int restart, int n_rec,
                                         int iters);

@@ -1063,3 +1063,22 @@ extern "C" int normal_cg_3d(const dbi_model3 *background, const dbi_batch *batch
   if (hist_out) for (size_t i = 0; i < h.size(); ++i) hist_out[i] = h[i];
   return DBI_OK;
 }
+
+extern "C" int sample_3d(const dbi_grid3 *g, int B, const int *rec_cells, int n_rec, const void *u, void *d,
+                         int precision, dbi_stream stream) {
+  clear_error();
+  int rc;
+  if ((rc = check_grid3(g)) || (rc = check_precision(precision))) return rc;
+  if (B < 0 || n_rec < 0) { set_error("need B >= 0 and n_rec >= 0"); return DBI_ERR_ARG; }
+  if (B == 0 || n_rec == 0) return DBI_OK;
+  if (!rec_cells || !u || !d) { set_error("NULL receivers, u or d"); return DBI_ERR_ARG; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int tot = B * n_rec;
+  if (precision == DBI_C64)
+    k3_sample<float2><<<(tot + 127) / 128, 128, 0, s>>>(B, g->nz, g->ny, g->nx, n_rec, rec_cells,
+                                                        static_cast<const float2 *>(u), static_cast<float2 *>(d));
+  else
+    k3_sample<double2><<<(tot + 127) / 128, 128, 0, s>>>(B, g->nz, g->ny, g->nx, n_rec, rec_cells,
+                                                         static_cast<const double2 *>(u), static_cast<double2 *>(d));
+  return check_launch("k3_sample");
+}

@@ -138,6 +138,7 @@ SIGNATURES = {
     "normal_cg_3d": (c_int, [POINTER(Model3), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_int, c_void_p,
                              POINTER(CGOpts), c_void_p, c_void_p, POINTER(c_double), POINTER(c_double),
                              POINTER(KrylovOpts), c_int, POINTER(Status), c_int, c_void_p, c_size_t, c_void_p]),
+    "sample_3d": (c_int, [POINTER(Grid3), c_int, c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
     "greens_tabulate_k": (c_int, [POINTER(Grid), POINTER(Medium), c_void_p, c_int, c_int, c_void_p, c_void_p,
                                   c_size_t, c_void_p]),
     "ls_apply_k": (c_int, [POINTER(Model), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p, c_int,
@@ -543,6 +544,16 @@ def adjoint_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_
     g = torch.empty((6, grid.nz, grid.ny, grid.nx), dtype=real_dtype(_precision(u_b)), device=u_b.device)
     return _products3("adjoint_apply_3d", grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, r, g, tol, max_iter,
                       restart, check_every)
+
+
+def sample_3d(grid: Grid3, rec_cells, u):
+    """P u: [B][n_rec][3] complex."""
+    precision = _precision(u)
+    _need_cuda(rec_cells, u)
+    d = torch.empty((u.shape[0], rec_cells.shape[0], 3), dtype=u.dtype, device=u.device)
+    _check(load().sample_3d(ctypes.byref(grid), int(u.shape[0]), _ptr(rec_cells), int(rec_cells.shape[0]), _ptr(u),
+                            _ptr(d), precision, _stream(u.device)), "sample_3d")
+    return d
 
 
 def normal_cg_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, dd, iters=30, lam=None,

@@ -102,3 +102,56 @@ def dbi_inversion(w, d_obs, m0, precision=dbi.C64, max_iter=10, eps_d_stop=1e-3,
             m = (m + dm).contiguous()
         res.m = m
     return res
+
+
+# ---------------------------------------------------------------------------------------------
+# 3D (the paper's 3D VTI example): the same loop over the 3D entry points
+# ---------------------------------------------------------------------------------------------
+def observed_data_3d(w, m_true, precision=dbi.C64, tol=None):
+    """Synthetic observed data per frequency of a 3D workload: [nf] list of [n_src][n_rec][3]."""
+    from .problem import DeviceProblem3D
+    out = []
+    for fi in range(len(w.freqs_hz)):
+        P = DeviceProblem3D(single_frequency(w, fi), precision, model=m_true)
+        u, _, _, code = P.solve(P.incident(), tol=tol)
+        if not bool((code == dbi.CONVERGED).all()):
+            raise RuntimeError("3D forward solve for the observed data did not converge")
+        out.append(P.sample(u))
+    return out
+
+
+def dbi_inversion_3d(w, d_obs, m0, precision=dbi.C64, max_iter=10, eps_d_stop=1e-3, cg_iters=30,
+                     lambda_rel=1e-3, cooling=0.5, m_true=None, tol=None, power_iters=10, power_seed=17):
+    """The DBI loop of dbi_inversion for a 3D workload (models [6][nz][ny][nx]): background GMRES
+    solves, sampled data, the 3D normal equation, model updates, per frequency from the lowest."""
+    from .problem import DeviceProblem3D
+    rdt = dbi.real_dtype(precision)
+    m = torch.as_tensor(np.asarray(m0, dtype=np.float64)).to("cuda", rdt).contiguous()
+    mt = None if m_true is None else torch.as_tensor(np.asarray(m_true, dtype=np.float64)).to("cuda", torch.float64)
+    rng = np.random.default_rng(power_seed)
+    power_start = rng.standard_normal((6, w.nz, w.ny, w.nx))
+    res = DBIResult(m=m)
+    for fi in np.argsort(np.asarray(w.freqs_hz)):
+        P = DeviceProblem3D(single_frequency(w, int(fi)), precision, model=m.double().cpu().numpy())
+        d = d_obs[int(fi)].to(P.device, P.cdt)
+        ps = P.to_model(power_start)
+        lam = None
+        for k in range(max_iter + 1):
+            u_b, iters, _, code = P.solve(P.incident(), m=m, tol=tol)
+            if not bool((code == dbi.CONVERGED).all()):
+                raise RuntimeError(f"3D background solve did not converge at {w.freqs_hz[fi]} Hz")
+            d_cal = P.sample(u_b)
+            eps_d = normalized(d_cal, d)
+            eps_m = None if mt is None else normalized(m.double(), mt)
+            rec = DBIRecord(float(w.freqs_hz[fi]), k, eps_d, eps_m, solve_iters_max=int(iters.max()))
+            res.history.append(rec)
+            if eps_d < eps_d_stop or k == max_iter:
+                break
+            dm, lam_used, _ = P.normal_cg(u_b, (d - d_cal).contiguous(), iters=cg_iters, lam=lam,
+                                          lambda_rel=lambda_rel, power_iters=power_iters, power_start=ps, m_b=m,
+                                          tol=tol)
+            rec.lam = lam_used
+            lam = lam_used * cooling
+            m = (m + dm).contiguous()
+        res.m = m
+    return res

@@ -153,24 +153,29 @@ class DeviceProblem3D:
     def to_model(self, arr) -> torch.Tensor:
         return torch.as_tensor(np.asarray(arr, dtype=np.float64)).to(self.device, self.rdt).contiguous()
 
-    def frechet(self, u_b, dm, tol=None, max_iter=2000, restart=30):
-        tol = self.w.krylov_tol if tol is None else tol
-        return dbi.frechet_apply_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u_b,
-                                    self.rec_cells, dm, tol=tol, max_iter=max_iter, restart=restart)
+    def sample(self, u):
+        return dbi.sample_3d(self.grid, self.rec_cells, u)
 
-    def adjoint(self, u_b, r, tol=None, max_iter=2000, restart=30):
+    def frechet(self, u_b, dm, m_b=None, tol=None, max_iter=2000, restart=30):
         tol = self.w.krylov_tol if tol is None else tol
-        return dbi.adjoint_apply_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u_b,
-                                    self.rec_cells, r, tol=tol, max_iter=max_iter, restart=restart)
+        return dbi.frechet_apply_3d(self.grid, self.ref, self.m if m_b is None else m_b, self.omega, self.fidx,
+                                    self.Ghat, u_b, self.rec_cells, dm, tol=tol, max_iter=max_iter, restart=restart)
 
-    def normal_cg(self, u_b, dd, iters=30, lam=None, lambda_rel=1e-3, power_iters=10, power_start=None, tol=None,
-                  max_iter=2000, restart=30):
+    def adjoint(self, u_b, r, m_b=None, tol=None, max_iter=2000, restart=30):
         tol = self.w.krylov_tol if tol is None else tol
-        return dbi.normal_cg_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, u_b, self.rec_cells,
-                                dd, iters=iters, lam=lam, lambda_rel=lambda_rel, power_iters=power_iters,
-                                power_start=power_start, tol=tol, max_iter=max_iter, restart=restart)
+        return dbi.adjoint_apply_3d(self.grid, self.ref, self.m if m_b is None else m_b, self.omega, self.fidx,
+                                    self.Ghat, u_b, self.rec_cells, r, tol=tol, max_iter=max_iter, restart=restart)
 
-    def solve(self, rhs, restart=30, tol=None, max_iter=2000, check_every=8, u0=None):
+    def normal_cg(self, u_b, dd, iters=30, lam=None, lambda_rel=1e-3, power_iters=10, power_start=None, m_b=None,
+                  tol=None, max_iter=2000, restart=30):
         tol = self.w.krylov_tol if tol is None else tol
-        return dbi.ls_solve_3d(self.grid, self.ref, self.m, self.omega, self.fidx, self.Ghat, rhs, u0=u0,
+        return dbi.normal_cg_3d(self.grid, self.ref, self.m if m_b is None else m_b, self.omega, self.fidx,
+                                self.Ghat, u_b, self.rec_cells, dd, iters=iters, lam=lam, lambda_rel=lambda_rel,
+                                power_iters=power_iters, power_start=power_start, tol=tol, max_iter=max_iter,
+                                restart=restart)
+
+    def solve(self, rhs, m=None, restart=30, tol=None, max_iter=2000, check_every=8, u0=None):
+        tol = self.w.krylov_tol if tol is None else tol
+        return dbi.ls_solve_3d(self.grid, self.ref, self.m if m is None else m, self.omega, self.fidx, self.Ghat,
+                               rhs, u0=u0,
                                restart=restart, tol=tol, max_iter=max_iter, check_every=check_every)
