@@ -944,6 +944,19 @@ extern "C" int adjoint_apply_3d(const dbi_model3 *background, const dbi_batch *b
   return adjoint3(c, u_b, rec_cells, n_rec, r, static_cast<double *>(g_out));
 }
 
+namespace dbi {
+// y = s_p x (scale = sc[S_INV]) or y = s_p x / sc[S_INV] (invert): the normal operator is applied to
+// p / ||p|| and its result multiplied by ||p||, so that the single-precision fields of the Frechet
+// and adjoint solves stay far from underflow whatever the size of the CG vectors
+template <typename TO>
+static __global__ void k3_mscale_norm(int np, size_t plane, const double *x, TO *y, MScale s, const double *sc,
+                                      int invert) {
+  const double f = invert ? (sc[S_INV] > 0.0 ? 1.0 / sc[S_INV] : 0.0) : sc[S_INV];
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np * plane; i += size_t(gridDim.x) * blockDim.x)
+    y[i] = TO(x[i] * s.s[i / plane] * f);
+}
+}  // namespace dbi
+
 // ---------------------------------------------------------------------------------------------
 // Tikhonov normal equation in 3D (Eq. 23, 24): (Re J~^H J~ + lambda I) x = Re J~^H dd on the
 // relative unknowns x_p = dm_p / s_p, s = (rho0, C11_0 for C11 and C13, C33_0, C55_0, C66_0)
@@ -1000,16 +1013,6 @@ extern "C" int normal_cg_3d(const dbi_model3 *background, const dbi_batch *batch
   const MScale MS{{m0.rho0, a2, a2, a2, b2, b2}};
   const MScale one{{1, 1, 1, 1, 1, 1}};
   const int mblocks = int(std::min<size_t>((nm + 255) / 256, 4096));
-  auto H = [&](const double *pin, double *qout) -> int {  // S Re J^H J S p
-    int e;
-    if (precision == DBI_C64) k_mscale<double, float><<<mblocks, 256, 0, s>>>(6, plane, pin, static_cast<float *>(dmt), MS);
-    else k_mscale<double, double><<<mblocks, 256, 0, s>>>(6, plane, pin, static_cast<double *>(dmt), MS);
-    if ((e = check_launch("k_mscale"))) return e;
-    if ((e = frechet3(c, u_b, rec_cells, n_rec, dmt, dvec))) return e;
-    if ((e = adjoint3<double>(c, u_b, rec_cells, n_rec, dvec, gd))) return e;
-    k_mscale<double, double><<<mblocks, 256, 0, s>>>(6, plane, gd, qout, MS);
-    return check_launch("k_mscale");
-  };
   auto dot = [&](const double *a, const double *b) -> int {
     k_mdot<<<kMBlocks, kMThreads, 0, s>>>(nm, a, b, part);
     return check_launch("k_mdot");
@@ -1017,6 +1020,18 @@ extern "C" int normal_cg_3d(const dbi_model3 *background, const dbi_batch *batch
   auto scal = [&](int what, int k) -> int {
     k_scalar<<<1, 32, 0, s>>>(what, part, sc, hist, k);
     return check_launch("k_scalar");
+  };
+  auto H = [&](const double *pin, double *qout) -> int {  // S Re J^H J S p, applied to p / ||p||
+    int e;
+    if ((e = dot(pin, pin)) || (e = scal(3, 0))) return e;  // sc[S_INV] = 1 / ||p||
+    if (precision == DBI_C64)
+      k3_mscale_norm<float><<<mblocks, 256, 0, s>>>(6, plane, pin, static_cast<float *>(dmt), MS, sc, 0);
+    else k3_mscale_norm<double><<<mblocks, 256, 0, s>>>(6, plane, pin, static_cast<double *>(dmt), MS, sc, 0);
+    if ((e = check_launch("k3_mscale_norm"))) return e;
+    if ((e = frechet3(c, u_b, rec_cells, n_rec, dmt, dvec))) return e;
+    if ((e = adjoint3<double>(c, u_b, rec_cells, n_rec, dvec, gd))) return e;
+    k3_mscale_norm<double><<<mblocks, 256, 0, s>>>(6, plane, gd, qout, MS, sc, 1);
+    return check_launch("k3_mscale_norm");
   };
   auto axpy = [&](int mode, const double *xx, double *yy, const double *qq, double *rr) -> int {
     k_maxpy<<<mblocks, 256, 0, s>>>(nm, mode, sc, xx, yy, qq, rr);

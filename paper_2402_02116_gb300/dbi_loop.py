@@ -137,9 +137,10 @@ def dbi_inversion_3d(w, d_obs, m0, precision=dbi.C64, max_iter=10, eps_d_stop=1e
         ps = P.to_model(power_start)
         lam = None
         for k in range(max_iter + 1):
-            u_b, iters, _, code = P.solve(P.incident(), m=m, tol=tol)
+            u_b, iters, relres, code = P.solve(P.incident(), m=m, tol=tol)
             if not bool((code == dbi.CONVERGED).all()):
-                raise RuntimeError(f"3D background solve did not converge at {w.freqs_hz[fi]} Hz")
+                raise RuntimeError(f"3D background solve did not converge at {w.freqs_hz[fi]} Hz, update {k}: "
+                                   f"codes {code.tolist()}, steps {iters.tolist()}, residuals {relres.tolist()}")
             d_cal = P.sample(u_b)
             eps_d = normalized(d_cal, d)
             eps_m = None if mt is None else normalized(m.double(), mt)
