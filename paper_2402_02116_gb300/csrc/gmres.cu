@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(kRedThreads) k_gm_scale_v(Span sp, const int *
 }
 
 // Partials of h_i = <v_i, w> for the basis vectors i of group blockIdx.z (i <= j), w = v_(j+1),
-// and (group 0 of round 0) of ||w||^2. Round 1 runs only for the problems that re-orthogonalise.
+// and (group 0 of the first pass) of ||w||^2. The second Gram-Schmidt pass (round = 1) runs only
+// for the problems that re-orthogonalise.
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads) k_gm_dots(Span sp, const int *plist, const int *active,
                                                          const GState *st, const C *__restrict__ V,
@@ -222,8 +223,8 @@ __global__ void __launch_bounds__(kRedThreads) k_gm_dots(Span sp, const int *pli
 }
 
 // h_i = <v_i, K v_j> (i <= j) from the partials, in a fixed order; hc[b][i] = h_i and column j
-// of the Hessenberg matrix of A = I - K gets delta_ij - h_i (round 0) or -h_i more (round 1);
-// round 0 also stores ||K v_j||^2. One CTA of 2 kGmresMaxRestart + 32 threads per problem.
+// of the Hessenberg matrix of A = I - K gets delta_ij - h_i (first pass) or -h_i more (second pass);
+// the first pass also stores ||K v_j||^2. One CTA of 2 kGmresMaxRestart + 32 threads per problem.
 __global__ void k_gm_hsum(const int *plist, const int *active, GState *st, const double *partD, double2 *hc,
                           double2 *H, int j, int round, int m) {
   const int b = problem_at(plist, blockIdx.x);
