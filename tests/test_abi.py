@@ -84,3 +84,33 @@ def test_argument_errors_are_reported_without_a_gpu(lib):
                       None, 0, None)
     assert rc == -1 and b"tol" in lib.dbi_last_error()
     assert lib.dbi_version() >= 100
+
+
+def test_3d_argument_errors_are_reported_without_a_gpu(lib):
+    g = dbi.make_grid3(4, 3, 5, 16, 16, 16, 10.0)
+    assert dbi.workspace_bytes_3d(g, 2, dbi.C64, dbi.OP_APPLY) > 0
+    assert dbi.workspace_bytes_3d(g, 2, dbi.C64, dbi.OP_SOLVE, restart=65) == 0
+    small = dbi.make_grid3(9, 3, 5, 16, 16, 16, 10.0)  # lz = 16 < 2 * 9 - 1
+    assert dbi.workspace_bytes_3d(small, 2, dbi.C64, dbi.OP_APPLY) == 0
+    odd = dbi.make_grid3(4, 3, 5, 16, 24, 16, 10.0)  # 24 is not a supported FFT length
+    assert dbi.workspace_bytes_3d(odd, 2, dbi.C64, dbi.OP_APPLY) == 0
+    vti = dbi.make_medium_vti(2200.0, 1.65e10, 5.6e9, 1.375e10, 4.58e9)
+    rc = lib.greens_tabulate_3d(ctypes.byref(g), ctypes.byref(vti), None, 1, 0, None, None, None, 0, None)
+    assert rc == -1 and b"isotropic" in lib.dbi_last_error()
+    ref = dbi.make_medium(2000.0, 2000.0, 1155.0)
+    model = dbi.Model3(g, ref, None)
+    batch = dbi.Batch(2, 1, 1, 1)  # non-NULL placeholders: validation fails before any device access
+    rc = lib.ls_apply_3d(ctypes.byref(model), ctypes.byref(batch), None, None, None, 0, None, 0, None)
+    assert rc == -1 and b"NULL" in lib.dbi_last_error()
+    opts = dbi.KrylovOpts(1e-6, 10, 1, 1)
+    rc = lib.ls_solve_3d(ctypes.byref(model), ctypes.byref(batch), None, None, None, ctypes.byref(opts), 0, None, 0,
+                         None, 0, None)
+    assert rc == -1 and b"restart" in lib.dbi_last_error()
+    big = dbi.Batch(30000, 1, 1, 1)  # B * 3 * nz exceeds the launch limit of the y pass
+    rc = lib.ls_apply_3d(ctypes.byref(model), ctypes.byref(big), None, None, None, 0, None, 0, None)
+    assert rc == -2 and b"too large" in lib.dbi_last_error()
+    cg = dbi.CGOpts(5, 0.0, 0.0, 0)  # neither lambda nor an estimate
+    rc = lib.normal_cg_3d(ctypes.byref(model), ctypes.byref(batch), None, None, None, 1, None, ctypes.byref(cg), None,
+                          None, None, None, ctypes.byref(opts), 30, None, 0, None, 0, None)
+    assert rc == -1 and b"CG options" in lib.dbi_last_error()
+    assert lib.sample_3d(ctypes.byref(g), -1, None, 1, None, None, 0, None) == -1
