@@ -202,18 +202,21 @@ template <typename C, int LZ> struct ZCfg {
   static constexpr int MIN_BLOCKS = sizeof(C) == 8 ? (NT <= 192 ? 8 : (NT <= 384 ? 4 : 2)) : 1;
 };
 template <typename C, int LZ>
-__global__ void __launch_bounds__(ZCfg<C, LZ>::NT, ZCfg<C, LZ>::MIN_BLOCKS) k3_fft_z_mul(int nz, int nf, size_t plane, const int *plist,
+__global__ void __launch_bounds__(ZCfg<C, LZ>::NT, ZCfg<C, LZ>::MIN_BLOCKS) k3_fft_z_mul(int nb, int nz, int nf, size_t plane, const int *plist,
                                                                 const int *active, const int *fidx, const C *Ghat,
                                                                 const C *tw, C *T) {
   using Z = ZCfg<C, LZ>;
   constexpr int CC = Z::CC, NL = Z::NL, LS = Z::LS, NT = Z::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *s = reinterpret_cast<C *>(smem_raw);
-  const int slot = blockIdx.y;
+  // slot fastest: the CTAs in flight cover every slot of a few column tiles, so the slots of one
+  // frequency read each tile of Ghat together and all but the first find it in L2 (one frequency's
+  // table can exceed L2, and the slots of one frequency would otherwise each stream all of it)
+  const int slot = int(blockIdx.x % unsigned(nb));
   const int b = slot_problem(plist, active, slot);
   if (b < 0 || unsigned(fidx[b]) >= unsigned(nf)) return;
   C *Tb = T + size_t(slot) * 3 * nz * plane;
-  const size_t q0 = size_t(blockIdx.x) * CC;
+  const size_t q0 = size_t(blockIdx.x / unsigned(nb)) * CC;
   for (int idx = threadIdx.x; idx < NL * LZ; idx += NT) {
     const int z = idx / NL, l = idx - z * NL, c = l / CC, j = l - c * CC;
     s[l * LS + z] = (z < nz && q0 + j < plane) ? Tb[(size_t(c) * nz + z) * plane + q0 + j] : czero<C>();
@@ -333,9 +336,14 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
     const size_t bytes = size_t(Z::NL) * Z::LS * sizeof(C);
     const size_t plane = size_t(a.ly) * a.lx;
     cudaError_t e = allow_smem(k3_fft_z_mul<C, LZ>, bytes);
-    const dim3 grid(unsigned((plane + Z::CC - 1) / Z::CC), nb);
+    const size_t blocks = (plane + Z::CC - 1) / Z::CC * size_t(nb);
+    if (blocks > size_t(INT32_MAX)) {
+      set_error("3D z pass: %zu blocks exceed the launch limit", blocks);
+      rc = DBI_ERR_UNSUPPORTED;
+      return;
+    }
     if (e == cudaSuccess)
-      k3_fft_z_mul<C, LZ><<<grid, Z::NT, bytes, s>>>(a.nz, a.nf, plane, a.plist, a.active, a.fidx,
+      k3_fft_z_mul<C, LZ><<<unsigned(blocks), Z::NT, bytes, s>>>(nb, a.nz, a.nf, plane, a.plist, a.active, a.fidx,
                                                      static_cast<const C *>(a.Ghat), tw, T);
     rc = e != cudaSuccess ? cuda_fail("k3_fft_z_mul smem", e) : check_launch("k3_fft_z_mul");
   });
