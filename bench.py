@@ -774,7 +774,9 @@ def run_hess3d(args):
     z_s = z_ms * 1e-3
     roof = {"bound": "alu", "achieved": z_flops / z_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
             "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured median)", "traffic": None,
-            "kernel": "k3_fft_z_mul (z-line FFTs of the three components, 3 x 3 kernel, inverse)",
+            "kernel": ("k3_fft_z_reg (register z-line FFTs of the three components, 3 x 3 kernel, inverse)"
+                       if w.lz <= 256 else
+                       "k3_fft_z_mul (z-line FFTs of the three components, 3 x 3 kernel, inverse)"),
             "hbm_frac_of_algorithmic_bytes": z_bytes / z_s / (peaks.get("hbm_gbs", 6800.0) * 1e9),
             "launches_timed": z_launches, "avg_launch_ms": z_ms / max(z_launches, 1),
             "share_of_step_time": z_ms / ms if ms > 0 else None}

@@ -215,7 +215,6 @@ template <int L, int V = 0> struct RegPlan {
 #pragma unroll
             for (int l = 0; l < NLT; ++l) F::template butterflies<R, NS, INV, H>(v[l], wp);
             if constexpr (!LAST) {
-#pragma unroll
               constexpr int LAY = layout_of<L, V>(p);
 #pragma unroll
               for (int l = 0; l < NLT; ++l) F::template scatter<R, NS, LAY>(v[l], lines[l], t);

@@ -9,8 +9,9 @@
 //   k3_source       w^2 drho u + div sigma                                 -> T rows (x < nx)
 //   k3_fft_x        forward FFT along x of every row, zero-padded to lx    (in place in T)
 //   k3_fft_y        forward FFT along y (rows y >= ny read as zero)        (in place)
-//   k3_fft_z_mul    per (ky, kx) column: forward FFT along z of the three components, the
+//   k3_fft_z_reg    per (ky, kx) column: forward FFT along z of the three components, the
 //                   symmetric 3 x 3 Ghat product, inverse FFT along z      (in place, z < nz kept)
+//                   with register FFTs (complex64, lz <= 256; k3_fft_z_mul otherwise)
 //   k3_fft_y        inverse, y < ny kept
 //   k3_fft_x_epi    inverse FFT along x, x < nx kept, out = ident - result
 // Without the stencil (plain convolution of the input, for the adjoint source) k3_copy_source
@@ -24,6 +25,7 @@
 #include "fft.cuh"
 #include "krylov.cuh"
 #include "mspace.cuh"
+#include "op_tiles.cuh"
 
 namespace dbi {
 
@@ -243,6 +245,85 @@ __global__ void __launch_bounds__(ZCfg<C, LZ>::NT, ZCfg<C, LZ>::MIN_BLOCKS) k3_f
   }
 }
 
+// The z pass with register-resident FFTs (complex64, LZ <= 256: a column's T = LZ / 8 threads are
+// one warp or part of one). A CTA of 256 threads takes CC = 256 / T columns: the nz rows of its
+// 3 CC lines are staged through shared memory with runs of CC consecutive columns, each column's
+// T threads hold its three components' lines in registers (8 points each) and exchange through
+// the staged lines, and the result goes back the same way.
+#ifndef DBI_3D_ZREG_MINB
+#define DBI_3D_ZREG_MINB 2  // CTAs per SM: 128 registers; 3 (80 registers) was 15 % slower, 4 no faster
+#endif
+template <int LZ> struct ZRegCfg {
+  using C = float2;
+  static constexpr int T = LZ / 8, NT = kTileThreads, CC = NT / T;
+  static constexpr int LP = RegFFT<C, LZ>::LP;
+  static constexpr size_t smem = size_t(3) * CC * LP * sizeof(C);
+};
+template <int LZ>
+__global__ void __launch_bounds__(kTileThreads, DBI_3D_ZREG_MINB) k3_fft_z_reg(int nb, int nz, int nf, size_t plane, const int *plist,
+                                                               const int *active, const int *fidx, const float2 *Ghat,
+                                                               const float2 *tw, float2 *T) {
+  using C = float2;
+  using Z = ZRegCfg<LZ>;
+  constexpr int TZ = Z::T, CC = Z::CC, LP = Z::LP, NT = Z::NT, NL = 3 * CC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *s = reinterpret_cast<C *>(smem_raw);
+  const int slot = int(blockIdx.x % unsigned(nb));  // slot fastest, as in k3_fft_z_mul
+  const int b = slot_problem(plist, active, slot);
+  if (b < 0 || unsigned(fidx[b]) >= unsigned(nf)) return;  // uniform over the CTA
+  C *Tb = T + size_t(slot) * 3 * nz * plane;
+  const size_t q0 = size_t(blockIdx.x / unsigned(nb)) * CC;
+  for (int idx = threadIdx.x; idx < NL * nz; idx += NT) {
+    const int z = idx / NL, l = idx - z * NL, c = l / CC, j = l - c * CC;
+    s[l * LP + z] = q0 + j < plane ? Tb[(size_t(c) * nz + z) * plane + q0 + j] : czero<C>();
+  }
+  __syncthreads();
+  const int g = threadIdx.x / TZ, t = threadIdx.x - g * TZ;
+  const size_t q = q0 + g;
+  const bool live = q < plane;
+  C *const lines[3] = {s + size_t(g) * LP, s + size_t(CC + g) * LP, s + size_t(2 * CC + g) * LP};
+  const TwReg<C, LZ> tr(t, tw);
+  const RowSync<TZ> sync{1 + g};
+  C v[3][8];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int z = t + m * TZ;
+      v[c][m] = (m < kHalf && z < nz) ? lines[c][z] : czero<C>();
+    }
+  sync();  // the transform's first exchange overwrites the staged lines
+  RegPlan<LZ>::template run<C, 3, false, true>(v, lines, t, tr, sync);
+  if (live) {
+    const size_t e = size_t(LZ) * plane;
+    const C *G = Ghat + size_t(fidx[b]) * 6 * e + q;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const size_t o = size_t(t + m * TZ) * plane;
+      const C g11 = __ldg(G + o), g12 = __ldg(G + e + o), g13 = __ldg(G + 2 * e + o);
+      const C g22 = __ldg(G + 3 * e + o), g23 = __ldg(G + 4 * e + o), g33 = __ldg(G + 5 * e + o);
+      const C v1 = v[0][m], v2 = v[1][m], v3 = v[2][m];
+      v[0][m] = cadd(cadd(cmul(g11, v1), cmul(g12, v2)), cmul(g13, v3));
+      v[1][m] = cadd(cadd(cmul(g12, v1), cmul(g22, v2)), cmul(g23, v3));
+      v[2][m] = cadd(cadd(cmul(g13, v1), cmul(g23, v2)), cmul(g33, v3));
+    }
+  }
+  RegPlan<LZ>::template run<C, 3, true>(v, lines, t, tr, sync);
+  // every thread of the column is past the transform's last exchange: its lines are free
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int m = 0; m < kHalf; ++m) {
+      const int z = t + m * TZ;
+      if (z < nz) lines[c][z] = v[c][m];
+    }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NL * nz; idx += NT) {
+    const int z = idx / NL, l = idx - z * NL, c = l / CC, j = l - c * CC;
+    if (q0 + j < plane) Tb[(size_t(c) * nz + z) * plane + q0 + j] = s[l * LP + z];
+  }
+}
+
 // Inverse FFT along x of the rows (slot, c, z, y < ny); out = ident - osc result (x < nx).
 template <typename C, int LX>
 __global__ void __launch_bounds__(256) k3_fft_x_epi(int nb, int nz, int ny, int nx, int ly, const int *plist,
@@ -332,6 +413,23 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
   prof_mark(PROF_COLS, false, s);
   rc = DBI_ERR_UNSUPPORTED;
   dispatch_len(a.lz, [&]<int LZ>() {
+    if constexpr (sizeof(C) == 8 && LZ <= 256) {
+      using Z = ZRegCfg<LZ>;
+      const size_t plane = size_t(a.ly) * a.lx;
+      const size_t blocks = (plane + Z::CC - 1) / Z::CC * size_t(nb);
+      if (blocks > size_t(INT32_MAX)) {
+        set_error("3D z pass: %zu blocks exceed the launch limit", blocks);
+        rc = DBI_ERR_UNSUPPORTED;
+        return;
+      }
+      cudaError_t e = allow_smem(k3_fft_z_reg<LZ>, Z::smem);
+      if (e == cudaSuccess)
+        k3_fft_z_reg<LZ><<<unsigned(blocks), Z::NT, Z::smem, s>>>(
+            nb, a.nz, a.nf, plane, a.plist, a.active, a.fidx, static_cast<const float2 *>(a.Ghat),
+            reinterpret_cast<const float2 *>(tw), reinterpret_cast<float2 *>(T));
+      rc = e != cudaSuccess ? cuda_fail("k3_fft_z_reg smem", e) : check_launch("k3_fft_z_reg");
+      return;
+    }
     using Z = ZCfg<C, LZ>;
     const size_t bytes = size_t(Z::NL) * Z::LS * sizeof(C);
     const size_t plane = size_t(a.ly) * a.lx;

@@ -40,6 +40,8 @@ SHAPES = [
     dict(nz=1, ny=2, nx=9),                      # one layer
     dict(nz=6, ny=5, nx=20, lz=16, ly=32, lx=64),  # oversized, non-cubic FFT grid
     dict(nz=9, ny=12, nx=30),                    # several CTAs per pass
+    dict(nz=40, ny=2, nx=3),                     # tall columns: z transforms of length 128
+    dict(nz=100, ny=1, nx=2),                    # and 256
 ]
 IDS = ["x".join(str(s[k]) for k in ("nz", "ny", "nx")) for s in SHAPES]
 
