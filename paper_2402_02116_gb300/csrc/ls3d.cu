@@ -8,7 +8,8 @@
 //   k3_stress       sigma = dC : eps(u)  (6 Voigt components)              -> T2
 //   k3_source       w^2 drho u + div sigma                                 -> T rows (x < nx)
 //   k3_fft_x        forward FFT along x of every row, zero-padded to lx    (in place in T)
-//   k3_fft_y        forward FFT along y (rows y >= ny read as zero)        (in place)
+//   k3_fft_y        forward FFT along y (rows y >= ny read as zero)        (in place; register
+//                   FFTs in k3_fft_y_reg for complex64 and ly <= 256)
 //   k3_fft_z_reg    per (ky, kx) column: forward FFT along z of the three components, the
 //                   symmetric 3 x 3 Ghat product, inverse FFT along z      (in place, z < nz kept)
 //                   with register FFTs (complex64, lz <= 256; k3_fft_z_mul otherwise)
@@ -189,18 +190,72 @@ __global__ void __launch_bounds__(256) k3_fft_y(int nz, int ny, int lx, const in
   }
 }
 
+// The y passes with register-resident FFTs (complex64, LY <= 256): per plane (slot, c, z), CC =
+// 256 / T columns per CTA staged through shared memory in runs of CC consecutive columns, each
+// column's T = LY / 8 threads holding its line in registers. Forward: rows y < ny staged (the rest
+// zero), all ly written; inverse: all staged, y < ny written.
+template <int LY> struct YRegCfg {
+  using C = float2;
+  static constexpr int T = LY / 8, NT = kTileThreads, CC = NT / T;
+  static constexpr int LP = RegFFT<C, LY>::LP;
+  static constexpr size_t smem = size_t(CC) * LP * sizeof(C);
+};
+template <int LY, bool INV>
+__global__ void __launch_bounds__(kTileThreads, 4) k3_fft_y_reg(int nz, int ny, int lx, const int *plist,
+                                                               const int *active, const float2 *tw, float2 *T) {
+  using C = float2;
+  using Y = YRegCfg<LY>;
+  constexpr int TY = Y::T, CC = Y::CC, LP = Y::LP, NT = Y::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *s = reinterpret_cast<C *>(smem_raw);
+  const int plane = blockIdx.y, slot = plane / (3 * nz);
+  if (slot_problem(plist, active, slot) < 0) return;  // uniform over the CTA
+  C *M = T + size_t(plane) * LY * lx;
+  const int c0 = blockIdx.x * CC;
+  const int rows_in = INV ? LY : ny, rows_out = INV ? ny : LY;
+  for (int idx = threadIdx.x; idx < CC * rows_in; idx += NT) {
+    const int y = idx / CC, j = idx - y * CC;
+    s[j * LP + y] = c0 + j < lx ? M[size_t(y) * lx + c0 + j] : czero<C>();
+  }
+  __syncthreads();
+  const int g = threadIdx.x / TY, t = threadIdx.x - g * TY;
+  C *const line[1] = {s + size_t(g) * LP};
+  const TwReg<C, LY> tr(t, tw);
+  const RowSync<TY> sync{1 + g};
+  C v[1][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int y = t + m * TY;
+    v[0][m] = (INV || (m < kHalf && y < ny)) ? line[0][y] : czero<C>();
+  }
+  sync();  // the transform's first exchange overwrites the staged line
+  RegPlan<LY>::template run<C, 1, INV, !INV>(v, line, t, tr, sync);
+  // every thread of the column is past the transform's last exchange: its line is free
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int y = t + m * TY;
+    if (!INV || (m < kHalf && y < ny)) line[0][y] = v[0][m];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < CC * rows_out; idx += NT) {
+    const int y = idx / CC, j = idx - y * CC;
+    if (c0 + j < lx) M[size_t(y) * lx + c0 + j] = s[j * LP + y];
+  }
+}
+
 // Per (ky, kx) column q of a slot: the three components' z-lines (z < nz, zero-padded to LZ),
-// forward FFT, out_i = sum_j Ghat_ij(kz, q) v_j, inverse FFT, z < nz written back.
-// CC = 512 / LZ columns per CTA (192 threads up to LZ = 512): small CTAs, several per SM. Wider
-// tiles (32 columns, 768 threads) gave longer row runs but fewer resident warps and were 60 %
-// slower at LZ = 64.
+// forward FFT, out_i = sum_j Ghat_ij(kz, q) v_j, inverse FFT, z < nz written back, with the
+// shared-memory FFTs of fft.cuh (complex128, and complex64 beyond LZ = 256).
+// CC = 1024 / LZ columns per CTA (384 threads up to LZ = 1024): small CTAs, several per SM. Wider
+// tiles (32 columns, 768 threads at LZ = 64) gave longer row runs but fewer resident warps and
+// were 60 % slower.
 #ifndef DBI_3D_ZCOLS
 #define DBI_3D_ZCOLS 1024
 #endif
 template <typename C, int LZ> struct ZCfg {
   static constexpr int CC = DBI_3D_ZCOLS / LZ > 0 ? DBI_3D_ZCOLS / LZ : 1;
   static constexpr int NL = 3 * CC, LS = LZ + 1, NT = NL * LZ / 8;
-  // 40 registers for complex64 (8 CTAs of 192 threads per SM); complex128 would spill
+  // complex64: 8 CTAs per SM up to 192 threads, 4 up to 384; complex128 would spill
   static constexpr int MIN_BLOCKS = sizeof(C) == 8 ? (NT <= 192 ? 8 : (NT <= 384 ? 4 : 2)) : 1;
 };
 template <typename C, int LZ>
@@ -400,6 +455,17 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
     constexpr bool INV = decltype(inv_tag)::value;
     rc = DBI_ERR_UNSUPPORTED;
     dispatch_len(a.ly, [&]<int LY>() {
+      if constexpr (sizeof(C) == 8 && LY <= 256) {
+        using Y = YRegCfg<LY>;
+        cudaError_t e = allow_smem(k3_fft_y_reg<LY, INV>, Y::smem);
+        const dim3 grid((a.lx + Y::CC - 1) / Y::CC, nb * 3 * a.nz);
+        if (e == cudaSuccess)
+          k3_fft_y_reg<LY, INV><<<grid, Y::NT, Y::smem, s>>>(a.nz, a.ny, a.lx, a.plist, a.active,
+                                                             reinterpret_cast<const float2 *>(tw),
+                                                             reinterpret_cast<float2 *>(T));
+        rc = e != cudaSuccess ? cuda_fail("k3_fft_y_reg smem", e) : check_launch("k3_fft_y_reg");
+        return;
+      }
       constexpr int CC = YCfg<C, LY>::CC, NT = YCfg<C, LY>::NT;
       const size_t bytes = size_t(CC) * (LY + 1) * sizeof(C);
       cudaError_t e = allow_smem(k3_fft_y<C, LY, INV>, bytes);

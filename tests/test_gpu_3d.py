@@ -42,6 +42,8 @@ SHAPES = [
     dict(nz=9, ny=12, nx=30),                    # several CTAs per pass
     dict(nz=40, ny=2, nx=3),                     # tall columns: z transforms of length 128
     dict(nz=100, ny=1, nx=2),                    # and 256
+    dict(nz=2, ny=30, nx=3),                     # y transforms of length 64
+    dict(nz=1, ny=100, nx=2),                    # and 256
 ]
 IDS = ["x".join(str(s[k]) for k in ("nz", "ny", "nx")) for s in SHAPES]
 
