@@ -255,17 +255,13 @@ def run_ours(args):
                 "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = "k_cols (column FFTs x Green's tensor x inverse column FFTs)"
-    # DRAM bytes per launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum of one k_cols launch
-    # over 64 problems of this workload, per problem, times the problems an average timed launch
-    # processed (the traffic grows with the launch's problems). Only valid for the 256 x 256 /
-    # L = 512 shapes it was measured on.
+    # DRAM bytes per launch: null, because k_cols changed (its FFT line layout is now chosen per
+    # exchange) after its last ncu DRAM capture on these shapes; that capture is kept as context
+    roof["traffic"] = None
     if (w.nz, w.nx, w.lz, w.lx) == (256, 256, 512, 512):
-        per_launch_problems = rank_applies / max(cols_launches, 1)
-        roof["traffic"] = COLS_DRAM_BYTES_PER_PROBLEM * per_launch_problems
-        roof["traffic_note"] = ("ncu dram bytes of k_cols, 4.35 MB per problem (64-problem capture), "
-                                f"x {per_launch_problems:.1f} problems per timed launch")
-    else:
-        roof["traffic"] = None
+        roof["traffic_note"] = ("null: k_cols changed after its last ncu DRAM capture, which gave "
+                                f"{COLS_DRAM_BYTES_PER_PROBLEM / 1e6:.2f} MB per problem (64-problem capture) "
+                                "against 4.39 MB algorithmic")
     roof["hbm_frac_of_algorithmic_bytes"] = cols_algo_bytes / cols_s / hbm_peak
     roof["launches_timed"] = cols_launches
     roof["avg_launch_ms"] = cols_ms / max(cols_launches, 1)
@@ -379,7 +375,7 @@ def plain_c128_sample(w, dev, cells, value_c64):
 # ---------------------------------------------------------------------------------------------
 # roofline arithmetic of the column pass (per D-cell per operator pass)
 # ---------------------------------------------------------------------------------------------
-COLS_DRAM_BYTES_PER_PROBLEM = 4.35e6
+COLS_DRAM_BYTES_PER_PROBLEM = 4.35e6  # ncu, k_cols before the per-exchange line layout
 
 
 def cols_bytes_per_cell_apply(w):
