@@ -2,8 +2,9 @@
 G = [k_s^2 g_s I + grad grad (g_s - g_p)] / (rho w^2) differentiated numerically, the elastic wave
 equation by finite differences (residual O(d^2)), the self-cell ball mean against a quadrature of
 the closed form, the direct sum against the FFT convolution, zero contrast, the Born series
-against the solve, reciprocity of the discrete responses, and the 3D Frechet and adjoint products
-(the dot test, and the Frechet product against central differences of the forward map)."""
+against the solve, reciprocity of the discrete responses, the 3D Frechet and adjoint products
+(the dot test, and the Frechet product against central differences of the forward map), and the
+Voigt-form contrast source against the full VTI stiffness tensor, symbolically (sympy)."""
 import math
 
 import numpy as np
@@ -198,3 +199,62 @@ def test_normal_cg_against_a_dense_solve():
     dm, lam_out, hist = o3.normal_cg_3d(orc, model, U_b, fidx, dd, rec, iters=150, lam=lam, tol=1e-13)
     assert lam_out == lam and hist[-1] < 1e-8 * hist[0]
     assert np.linalg.norm(dm / sc - x_dense.reshape(6, 4, 3, 5)) <= 1e-6 * np.linalg.norm(x_dense)
+
+
+def _vti_stiffness(C11, C13, C33, C55, C66):
+    """C_ijkl of a VTI medium with symmetry axis x3 (0-based indices), from the tensor's minor and
+    major symmetries and the five independent moduli: C_1111 = C_2222 = C11, C_3333 = C33,
+    C_1122 = C11 - 2 C66 (isotropy in the x1-x2 plane), C_1133 = C_2233 = C13,
+    C_2323 = C_1313 = C55 (= C44), C_1212 = C66; every other entry is zero."""
+    C = {}
+
+    def put(i, j, k, l, v):
+        for a, b in ((i, j), (j, i)):
+            for c, d in ((k, l), (l, k)):
+                C[(a, b, c, d)] = v
+                C[(c, d, a, b)] = v
+
+    put(0, 0, 0, 0, C11)
+    put(1, 1, 1, 1, C11)
+    put(2, 2, 2, 2, C33)
+    put(0, 0, 1, 1, C11 - 2 * C66)
+    put(0, 0, 2, 2, C13)
+    put(1, 1, 2, 2, C13)
+    put(1, 2, 1, 2, C55)
+    put(0, 2, 0, 2, C55)
+    put(0, 1, 0, 1, C66)
+    return lambda i, j, k, l: C.get((i, j, k, l), 0)
+
+
+def test_contrast_source_equals_the_tensor_form():
+    """For quadratic u and linear contrasts the central differences are exact, so on cells two or
+    more from the edge the oracle's Voigt-form source equals w^2 drho u_i + d_j (C_ijkl eps_kl)
+    computed symbolically from the full stiffness tensor and eps_kl = (d_k u_l + d_l u_k) / 2.
+    Catches a wrong Voigt index, shear factor, C12, axis mapping or divergence index."""
+    sp = pytest.importorskip("sympy")
+    X = sp.symbols("x1 x2 x3")
+    rng = np.random.default_rng(41)
+    c = lambda: complex(rng.normal(), rng.normal())  # noqa: E731
+    monomials = [1, *X, *(X[a] * X[b] for a in range(3) for b in range(a, 3))]
+    u = [sum(c() * m for m in monomials) for _ in range(3)]
+    lin = lambda s: s * (1 + sum(0.01 * rng.normal() * x for x in X))  # noqa: E731
+    drho = lin(170.0)
+    mod = [lin(3e8), lin(-1e8), lin(2e8), lin(7e7), lin(9e7)]  # C11, C13, C33, C55, C66
+    Cijkl = _vti_stiffness(*mod)
+    eps = [[(sp.diff(u[l], X[k]) + sp.diff(u[k], X[l])) / 2 for l in range(3)] for k in range(3)]
+    sig = [[sum(Cijkl(i, j, k, l) * eps[k][l] for k in range(3) for l in range(3)) for j in range(3)]
+           for i in range(3)]
+    omega = 2 * math.pi * 6.0
+    src = [omega ** 2 * drho * u[i] + sum(sp.diff(sig[i][j], X[j]) for j in range(3)) for i in range(3)]
+    nz, ny, nx, h = 7, 8, 9, 3.0
+    Z, Y, Xg = np.meshgrid(np.arange(nz) * h, np.arange(ny) * h, np.arange(nx) * h, indexing="ij")
+
+    def ev(e):
+        return np.broadcast_to(sp.lambdify(X, e, "numpy")(Xg, Y, Z), (nz, ny, nx)).astype(complex)
+
+    field = np.stack([ev(ui) for ui in u])
+    dmod = np.stack([ev(drho).real] + [ev(m).real for m in mod])
+    got = o3.contrast_source_3d(field, dmod, omega, h)
+    want = np.stack([ev(s) for s in src])
+    sl = (slice(None), slice(2, nz - 2), slice(2, ny - 2), slice(2, nx - 2))
+    assert np.max(np.abs(got[sl] - want[sl])) < 1e-9 * np.max(np.abs(want[sl]))
