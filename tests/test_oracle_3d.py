@@ -1,4 +1,6 @@
-"""Pins of the 3D oracle (CPU only): the closed-form tensor against its potential representation
+"""Pins of the 3D oracle (CPU only): the unit point force (traction balance on a small sphere), the
+outgoing far field with the point-force radiation amplitudes, the closed-form tensor against its
+potential representation
 G = [k_s^2 g_s I + grad grad (g_s - g_p)] / (rho w^2) differentiated numerically, the elastic wave
 equation by finite differences (residual O(d^2)), the self-cell ball mean against a quadrature of
 the closed form, the direct sum against the FFT convolution, zero contrast, the Born series
@@ -258,3 +260,56 @@ def test_contrast_source_equals_the_tensor_form():
     want = np.stack([ev(s) for s in src])
     sl = (slice(None), slice(2, nz - 2), slice(2, ny - 2), slice(2, nx - 2))
     assert np.max(np.abs(got[sl] - want[sl])) < 1e-9 * np.max(np.abs(want[sl]))
+
+
+@pytest.mark.parametrize("j", [0, 2])
+def test_green_point_force_traction(j):
+    """The traction of column j of G on a small sphere around the source integrates to -e_j: G is
+    the response to a unit point force (fixes its scale and sign, which the homogeneous wave
+    equation cannot). Radius 1e-3 of the S wavelength over 2 pi (dynamic correction ~ (k r)^2);
+    4th-order differences of the closed form; Gauss-Legendre in cos(theta) x trapezoid in phi,
+    exact for the traction's low-degree angular dependence."""
+    omega = 2 * math.pi * 10.0
+    mu, lam = RHO * BETA ** 2, RHO * (ALPHA ** 2 - 2 * BETA ** 2)
+    eps = 1e-3 * BETA / omega
+    d = 1e-2 * eps
+    E = np.eye(3)
+
+    def col(p):
+        return G_full(p, omega)[:, j]
+
+    def grad(p):  # du[i][k] = d u_i / d x_k
+        g = np.empty((3, 3), dtype=np.complex128)
+        for k in range(3):
+            e = d * E[k]
+            g[:, k] = (-col(p + 2 * e) + 8 * col(p + e) - 8 * col(p - e) + col(p - 2 * e)) / (12 * d)
+        return g
+
+    mus, wmu = np.polynomial.legendre.leggauss(12)
+    nphi = 24
+    total = np.zeros(3, dtype=np.complex128)
+    for m, wm in zip(mus, wmu):
+        s = math.sqrt(1 - m * m)
+        for phi in np.arange(nphi) * 2 * math.pi / nphi:
+            n = np.array([s * math.cos(phi), s * math.sin(phi), m])
+            du = grad(eps * n)
+            sig = lam * np.trace(du) * E + mu * (du + du.T)
+            total += (sig @ n) * wm * (2 * math.pi / nphi) * eps * eps
+    assert np.max(np.abs(total + E[j])) < 1e-4
+
+
+def test_green_far_field_outgoing():
+    """Far from the source on the x3 axis G33 is the P wave exp(-i k_p r) / (4 pi rho alpha^2 r)
+    and G11 the S wave exp(-i k_s r) / (4 pi rho beta^2 r) (the point-force radiation pattern):
+    the phase falls at the wavenumber's rate (outgoing for exp(+i w t), the 2D tensor's
+    convention) and the amplitudes decay like 1/r with the stated constants (at 200 km the near
+    field and the other wave type are ~3e-4 of the far field on this axis)."""
+    omega = 2 * math.pi * 15.0
+    r0, dr = 200000.0, 0.5
+    for comp, c in ((2, ALPHA), (0, BETA)):
+        k = omega / c
+        g = [G_full((0.0, 0.0, r), omega)[comp, comp] for r in (r0, r0 + dr)]
+        rate = np.angle(g[1] / g[0]) / dr
+        assert abs(rate + k) < 2e-3 * k, comp
+        far = 1.0 / (4 * math.pi * RHO * c * c * r0)
+        assert abs(abs(g[0]) / far - 1) < 2e-3, comp
