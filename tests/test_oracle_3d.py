@@ -313,3 +313,22 @@ def test_green_far_field_outgoing():
         assert abs(rate + k) < 2e-3 * k, comp
         far = 1.0 / (4 * math.pi * RHO * c * c * r0)
         assert abs(abs(g[0]) / far - 1) < 2e-3, comp
+
+
+def test_incident_field_is_the_point_force_response():
+    """u0 of a point force f at cell x_s (Eq. 7) is the convolution of G_h with the force density
+    f delta(x - x_s) / h^3 (the discrete delta), and away from the source it is the closed form
+    G(x - x_s) f (pins the window offsets and the scale of the incident field)."""
+    orc, _, _ = case(nz=4, ny=3, nx=5)
+    src, force = (1, 2, 3), np.array([0.3, -0.2, 1.0])
+    u0 = orc.incident(0, src, force)
+    s = np.zeros((3, 4, 3, 5), dtype=np.complex128)
+    s[:, src[0], src[1], src[2]] = force / orc.h ** 3
+    conv = orc.convolve(s, 0)
+    assert np.linalg.norm(u0 - conv) <= 1e-12 * np.linalg.norm(conv)
+    w = orc.omegas[0]
+    for cell in ((0, 0, 0), (3, 1, 4), (1, 2, 0)):
+        y = [(cell[2] - src[2]) * orc.h, (cell[1] - src[1]) * orc.h, (cell[0] - src[0]) * orc.h]  # x1, x2, x3
+        want = G_full(y, w) @ force
+        got = u0[:, cell[0], cell[1], cell[2]]
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), cell
