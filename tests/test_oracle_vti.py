@@ -2,8 +2,9 @@
 over slowness directions), CPU only: the isotropic limit against the closed form of Appendix A
 (the Hankel functions), the self-cell mean against the isotropic disk average, the elastic wave
 equation of a VTI medium by finite differences away from the source (residual falling as h^2),
-the mirror symmetries, and the LS operator with a VTI reference against the isotropic one when
-the VTI stiffness is isotropic."""
+the mirror symmetries, the LS operator with a VTI reference against the isotropic one when
+the VTI stiffness is isotropic, and the unit point force of the anisotropic medium (traction
+balance on a small circle)."""
 import math
 
 import numpy as np
@@ -147,3 +148,33 @@ def test_far_offset_quadrature_against_multiprecision():
     for c in range(3):
         want = entry(c, 0) + 1j * entry(c, 1)
         assert abs(g[c] - want) <= 1e-12 * scale, c
+
+
+def test_vti_point_force_traction():
+    """The traction of the VTI tensor's column for a vertical force, on a small circle around the
+    source, integrates to -e_3: G is the response to a unit point force in the anisotropic medium
+    too. The isotropic-limit pin cannot see a normalisation error that depends on the anisotropy
+    (a constant factor leaves the homogeneous wave equation satisfied); this pin can. Stress from
+    the VTI stiffness in the x1-x3 plane: s11 = C11 e11 + C13 e33, s33 = C13 e11 + C33 e33,
+    s13 = 2 C55 e13; radius 1e-4 of the S wavelength over 2 pi; central differences of step
+    1e-3 of the radius; 24-point trapezoid over the circle."""
+    rho, c11, c13, c33, c55 = vti_params()
+    omega = 2 * math.pi * 10.0
+    eps = 1e-4 * math.sqrt(c55 / rho) / omega
+    d = 1e-3 * eps
+
+    def u(y1, y3):  # column 3 of G: (G13, G33)
+        g11, g13, g33 = O.green_vti_2d(y1, y3, omega, rho, c11, c13, c33, c55, epsrel=1e-13)
+        return np.array([g13, g33])
+
+    n = 24
+    total = np.zeros(2, dtype=np.complex128)
+    for t in (np.arange(n) + 0.5) * 2 * math.pi / n:
+        n1, n3 = math.cos(t), math.sin(t)
+        y1, y3 = eps * n1, eps * n3
+        d1 = (u(y1 + d, y3) - u(y1 - d, y3)) / (2 * d)  # d/dx1 of (u1, u3)
+        d3 = (u(y1, y3 + d) - u(y1, y3 - d)) / (2 * d)  # d/dx3
+        e11, e33, e13 = d1[0], d3[1], 0.5 * (d3[0] + d1[1])
+        s11, s33, s13 = c11 * e11 + c13 * e33, c13 * e11 + c33 * e33, 2 * c55 * e13
+        total += np.array([s11 * n1 + s13 * n3, s13 * n1 + s33 * n3]) * (2 * math.pi * eps / n)
+    assert np.max(np.abs(total - np.array([0.0, -1.0]))) < 1e-4, total
