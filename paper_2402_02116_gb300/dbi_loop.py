@@ -69,18 +69,21 @@ def observed_data(w, m_true, precision=dbi.C64, tol=None):
 
 
 def dbi_inversion(w, d_obs, m0, precision=dbi.C64, max_iter=10, eps_d_stop=1e-3, cg_iters=30,
-                  lambda_rel=1e-3, cooling=0.5, m_true=None, tol=None, power_iters=10, power_seed=17):
+                  lambda_rel=1e-3, cooling=0.5, m_true=None, tol=None, power_iters=10, power_seed=17,
+                  problem=DeviceProblem, device="cuda"):
     """Run the DBI loop from model m0 ([5][nz][nx], absolute values) against d_obs (from
-    observed_data); returns the final model and one DBIRecord per data-error evaluation."""
+    observed_data); returns the final model and one DBIRecord per data-error evaluation.
+    `problem` builds the per-frequency problem (the library's DeviceProblem; the CPU tests of the
+    loop's control logic pass a stand-in with the same methods) on `device`."""
     rdt = dbi.real_dtype(precision)
-    m = torch.as_tensor(np.asarray(m0, dtype=np.float64)).to("cuda", rdt).contiguous()
-    mt = None if m_true is None else torch.as_tensor(np.asarray(m_true, dtype=np.float64)).to("cuda", torch.float64)
+    m = torch.as_tensor(np.asarray(m0, dtype=np.float64)).to(device, rdt).contiguous()
+    mt = None if m_true is None else torch.as_tensor(np.asarray(m_true, dtype=np.float64)).to(device, torch.float64)
     rng = np.random.default_rng(power_seed)
     power_start = rng.standard_normal((5, w.nz, w.nx))
     res = DBIResult(m=m)
     order = np.argsort(np.asarray(w.freqs_hz))
     for fi in order:
-        P = DeviceProblem(single_frequency(w, int(fi)), precision, model=m.double().cpu().numpy())
+        P = problem(single_frequency(w, int(fi)), precision, model=m.double().cpu().numpy())
         d = d_obs[int(fi)].to(P.device, P.cdt)
         lam = None
         for k in range(max_iter + 1):
@@ -121,18 +124,21 @@ def observed_data_3d(w, m_true, precision=dbi.C64, tol=None):
 
 
 def dbi_inversion_3d(w, d_obs, m0, precision=dbi.C64, max_iter=10, eps_d_stop=1e-3, cg_iters=30,
-                     lambda_rel=1e-3, cooling=0.5, m_true=None, tol=None, power_iters=10, power_seed=17):
+                     lambda_rel=1e-3, cooling=0.5, m_true=None, tol=None, power_iters=10, power_seed=17,
+                     problem=None, device="cuda"):
     """The DBI loop of dbi_inversion for a 3D workload (models [6][nz][ny][nx]): background GMRES
-    solves, sampled data, the 3D normal equation, model updates, per frequency from the lowest."""
-    from .problem import DeviceProblem3D
+    solves, sampled data, the 3D normal equation, model updates, per frequency from the lowest.
+    `problem` defaults to the library's DeviceProblem3D."""
+    if problem is None:
+        from .problem import DeviceProblem3D as problem
     rdt = dbi.real_dtype(precision)
-    m = torch.as_tensor(np.asarray(m0, dtype=np.float64)).to("cuda", rdt).contiguous()
-    mt = None if m_true is None else torch.as_tensor(np.asarray(m_true, dtype=np.float64)).to("cuda", torch.float64)
+    m = torch.as_tensor(np.asarray(m0, dtype=np.float64)).to(device, rdt).contiguous()
+    mt = None if m_true is None else torch.as_tensor(np.asarray(m_true, dtype=np.float64)).to(device, torch.float64)
     rng = np.random.default_rng(power_seed)
     power_start = rng.standard_normal((6, w.nz, w.ny, w.nx))
     res = DBIResult(m=m)
     for fi in np.argsort(np.asarray(w.freqs_hz)):
-        P = DeviceProblem3D(single_frequency(w, int(fi)), precision, model=m.double().cpu().numpy())
+        P = problem(single_frequency(w, int(fi)), precision, model=m.double().cpu().numpy())
         d = d_obs[int(fi)].to(P.device, P.cdt)
         ps = P.to_model(power_start)
         lam = None
