@@ -442,6 +442,64 @@ def oracle_sample(w, problems=None):
             "seconds": dt}
 
 
+def _oracle_rate(passes, cells, dt, sample):
+    return {"value": passes * cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": dt}
+
+
+def oracle_formk_sample(w, b, passes=16):
+    """Operator passes of the paper-literal form (Eq. 9) on problem b by the FP64 oracle as it stands;
+    its derivative tables are built before the timed passes, as the GPU line times passes only."""
+    import oracle as O
+    f, s = int(w.problem_fidx()[b]), int(w.problem_src()[b])
+    orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
+    u = orc.incident(0, w.src_cells[s], w.src_force[s])
+    orc.apply_k(u, w.model, 0)
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        orc.apply_k(u, w.model, 0)
+    dt = time.perf_counter() - t0
+    return _oracle_rate(passes, w.nz * w.nx, dt, f"problem {b} (source {s}, {w.freqs_hz[f]:.2f} Hz) of {w.name}: "
+                        f"{passes} paper-literal operator passes in {dt:.1f} s (tables built before)")
+
+
+def oracle_gmres_sample(w, b, restart=30):
+    """One GMRES(restart) forward solve of problem b to the bench tolerance by the FP64 oracle; every
+    operator pass it makes (Arnoldi steps, the residual of each cycle, the final check) is counted."""
+    import oracle as O
+    f, s = int(w.problem_fidx()[b]), int(w.problem_src()[b])
+    orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
+    u0 = orc.incident(0, w.src_cells[s], w.src_force[s])
+    calls, apply = [0], orc.apply
+
+    def counted(u, model, fi):
+        calls[0] += 1
+        return apply(u, model, fi)
+
+    orc.apply = counted
+    t0 = time.perf_counter()
+    _, info = orc.solve_gmres(u0, w.model, 0, restart=restart, tol=TOL)
+    dt = time.perf_counter() - t0
+    return _oracle_rate(calls[0], w.nz * w.nx, dt, f"problem {b} (source {s}, {w.freqs_hz[f]:.2f} Hz) of {w.name}: "
+                        f"GMRES({restart}) to {TOL:g}, {info['iters']} Arnoldi steps, {calls[0]} operator passes "
+                        f"in {dt:.1f} s")
+
+
+def oracle_3d_sample(w, b, passes=4):
+    """3D operator passes on wavefield b by the FP64 3D oracle as it stands (tables built before)."""
+    import oracle as O
+    f, s = int(w.problem_fidx()[b]), int(w.problem_src()[b])
+    orc = O.o3d.LSOracle3D(w.nz, w.ny, w.nx, w.h, w.lz, w.ly, w.lx, w.rho0, w.alpha0, w.beta0,
+                           w.omegas[f:f + 1])
+    u = orc.incident(0, tuple(w.src_cells[s]), w.src_force[s])
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        orc.apply(u, w.model, 0)
+    dt = time.perf_counter() - t0
+    return _oracle_rate(passes, w.nz * w.ny * w.nx, dt, f"wavefield {b} (source {s}, {w.freqs_hz[f]:.2f} Hz) of "
+                        f"{w.name}: {passes} 3D operator passes in {dt:.1f} s (tables built before)")
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -645,6 +703,8 @@ def run_formk(args):
                             "note": "||A_K u0 - A_S u0|| / ||A_S u0 - u0|| over the batch: the boundary layer "
                                     "the divergence form leaves out where the contrast reaches the edge of D"},
     }
+    if not args.no_cpu_baseline:
+        result["cpu_baseline"] = oracle_formk_sample(w, w.n_problems // 2 + 3)
     print(json.dumps(result), flush=True)
 
 
@@ -708,6 +768,8 @@ def run_gmres(args):
                      "all_converged": bool((code_b == dbi.CONVERGED).all()), "clocks": clocks_b},
         "solutions_relative_difference": agree,
     }
+    if not args.no_cpu_baseline:
+        result["cpu_baseline"] = oracle_gmres_sample(w, w.n_problems // 2 + 3, args.restart)
     print(json.dumps(result), flush=True)
 
 
@@ -790,6 +852,8 @@ def run_hess3d(args):
         "gmres_solve": {"seconds": solve_s, "all_converged": bool((code == dbi.CONVERGED).all()),
                         "arnoldi_steps_mean": float(iters.float().mean()), "arnoldi_steps_max": int(iters.max())},
     }
+    if not args.no_cpu_baseline:
+        result["cpu_baseline"] = oracle_3d_sample(w, w.n_problems // 2 + 3)
     print(json.dumps(result), flush=True)
 
 

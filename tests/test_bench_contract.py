@@ -60,3 +60,25 @@ def test_reference_arm_json_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("kind", ["formk", "gmres", "3d"])
+def test_oracle_samples_of_the_other_workloads(kind):
+    """The CPU baselines beside the form-K, GMRES and 3D lines: the oracle's own operator passes,
+    counted and timed on one problem (small cases here)."""
+    if kind == "3d":
+        w = inputs.small_case_3d(nz=4, ny=3, nx=5, freqs=(6.0,))
+        r = bench.oracle_3d_sample(w, 1, passes=2)
+        assert "2 3D operator passes" in r["sample"]
+    elif kind == "formk":
+        w = inputs.small_case(nz=8, nx=7)
+        r = bench.oracle_formk_sample(w, 1, passes=3)
+        assert "3 paper-literal operator passes" in r["sample"]
+    else:
+        w = inputs.small_case(nz=8, nx=7)
+        r = bench.oracle_gmres_sample(w, 1, restart=5)
+        steps = int(r["sample"].split("Arnoldi steps")[0].split(",")[-1])
+        passes = int(r["sample"].split("operator passes")[0].split(",")[-1])
+        assert passes >= steps + 2  # at least one residual pass per cycle and the final check
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["unit"] == bench.UNIT
+    assert r["value"] > 0 and r["seconds"] > 0
