@@ -500,6 +500,32 @@ def oracle_3d_sample(w, b, passes=4):
                         f"{w.name}: {passes} 3D operator passes in {dt:.1f} s (tables built before)")
 
 
+def oracle_uneven_sample(ws):
+    """One operator pass by the FP64 oracle on one problem of each grid size of the uneven batch; each
+    size's time per cell is weighted by its share of the batch's cells, so the rate is the oracle's
+    on this mix of sizes."""
+    import oracle as O
+    by_size = {}
+    for w in ws:
+        by_size.setdefault((w.nz, w.nx, w.lz, w.lx), []).append(w)
+    t_mix, cells_mix, seconds, parts = 0.0, 0, 0.0, []
+    for key in sorted(by_size):
+        w = by_size[key][0]
+        orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[:1])
+        u = orc.incident(0, w.src_cells[0], w.src_force[0])
+        t0 = time.perf_counter()
+        orc.apply(u, w.model, 0)
+        dt = time.perf_counter() - t0
+        cells = sum(g.n_problems * g.nz * g.nx for g in by_size[key])
+        t_mix += dt / (w.nz * w.nx) * cells
+        cells_mix += cells
+        seconds += dt
+        parts.append(f"{w.nz}x{w.nx} (L {w.lz}): {dt * 1e3:.0f} ms")
+    return {"value": cells_mix / t_mix, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one oracle operator pass per grid size (" + ", ".join(parts)
+                      + "), weighted by each size's cells in the batch", "seconds": seconds}
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -600,6 +626,8 @@ def run_uneven(args):
                   "iterations_mean": float(iters.float().mean()), "iterations_max": int(iters.max()),
                   "useful_cell_applies_per_s": useful / solve_s, "graph_captured": True},
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = oracle_uneven_sample(ws)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

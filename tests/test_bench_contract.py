@@ -82,3 +82,11 @@ def test_oracle_samples_of_the_other_workloads(kind):
         assert passes >= steps + 2  # at least one residual pass per cycle and the final check
     assert r["kind"] == "oracle" and r["cores"] == 1 and r["unit"] == bench.UNIT
     assert r["value"] > 0 and r["seconds"] > 0
+
+
+def test_oracle_sample_of_the_uneven_batch():
+    """One oracle pass per distinct grid size, weighted by each size's cells in the batch."""
+    ws = [inputs.small_case(nz=8, nx=7), inputs.small_case(nz=12, nx=10), inputs.small_case(nz=8, nx=7, seed=3)]
+    r = bench.oracle_uneven_sample(ws)
+    assert r["sample"].count("x") >= 2 and "8x7" in r["sample"] and "12x10" in r["sample"]
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
