@@ -7,9 +7,12 @@
 // orders, forward (with and without the zero-half first pass) and inverse, complex64 and
 // complex128. The line buffer carries guard slots on both sides that must stay untouched.
 //
-// Usage: fft_reg_host <out.bin>. For every case the file holds a header of six int32 values
-// (precision bytes, L, V, INV, HIN, 0) followed by the input and the output of one line as
-// complex128 (the input as the plan saw it, after rounding to the precision).
+// Lines per thread group: 1, and 2 and 3 (the kernels transform a column's components together,
+// sharing the twiddle powers), each line with its own input.
+//
+// Usage: fft_reg_host <out.bin>. For every line the file holds a header of six int32 values
+// (precision bytes, L, V, INV, HIN, lines of the group) followed by the input and the output of
+// that line as complex128 (the input as the plan saw it, after rounding to the precision).
 #include <barrier>
 #include <cmath>
 #include <cstdint>
@@ -56,44 +59,51 @@ template <typename C> std::vector<C> make_input(int L, bool hin, uint64_t seed) 
   return x;
 }
 
-template <typename C, int L, int V, bool INV, bool HIN>
+template <typename C, int L, int V, bool INV, bool HIN, int NLT = 1>
 bool run_case(FILE *f, const std::vector<C> &tw, uint64_t seed) {
-  constexpr int T = L / 8, LP = RegFFT<C, L>::LP;
-  const std::vector<C> in = make_input<C>(L, HIN, seed);
-  std::vector<C> out(L);
-  std::vector<C> buf(LP + 2 * kGuard);
+  constexpr int T = L / 8, LP = RegFFT<C, L>::LP, SPAN = LP + 2 * kGuard;
+  std::vector<std::vector<C>> in(NLT), out(NLT, std::vector<C>(L));
+  for (int l = 0; l < NLT; ++l) in[l] = make_input<C>(L, HIN, seed * 8 + l);
+  std::vector<C> buf(size_t(NLT) * SPAN);  // each line between its own guards
   const double sentinel = 1.0e30;
   for (auto &c : buf) { c.x = decltype(c.x)(sentinel); c.y = decltype(c.y)(-sentinel); }
-  C *line = buf.data() + kGuard;
   std::barrier<> bar(T);
   std::vector<std::thread> threads;
   threads.reserve(T);
   for (int t = 0; t < T; ++t) {
     threads.emplace_back([&, t] {
       const TwReg<C, L, V> tr(t, tw.data());
-      C v[1][8];
-      for (int m = 0; m < 8; ++m) v[0][m] = in[t + m * T];
-      C *const lines[1] = {line};
-      RegPlan<L, V>::template run<C, 1, INV, HIN>(v, lines, t, tr, HostSync{&bar});
-      for (int m = 0; m < 8; ++m) out[t + m * T] = v[0][m];
+      C v[NLT][8];
+      C *lines_[NLT];
+      for (int l = 0; l < NLT; ++l) {
+        lines_[l] = buf.data() + size_t(l) * SPAN + kGuard;
+        for (int m = 0; m < 8; ++m) v[l][m] = in[l][t + m * T];
+      }
+      C *const(&lines)[NLT] = lines_;
+      RegPlan<L, V>::template run<C, NLT, INV, HIN>(v, lines, t, tr, HostSync{&bar});
+      for (int l = 0; l < NLT; ++l)
+        for (int m = 0; m < 8; ++m) out[l][t + m * T] = v[l][m];
     });
   }
   for (auto &th : threads) th.join();
-  for (int i = 0; i < kGuard; ++i) {
-    const C a = buf[i], b = buf[kGuard + LP + i];
-    if (a.x != decltype(a.x)(sentinel) || b.x != decltype(b.x)(sentinel)) {
-      std::fprintf(stderr, "guard overwritten: L=%d V=%d INV=%d HIN=%d\n", L, V, int(INV), int(HIN));
-      return false;
+  for (int l = 0; l < NLT; ++l)
+    for (int i = 0; i < kGuard; ++i) {
+      const C a = buf[size_t(l) * SPAN + i], b = buf[size_t(l) * SPAN + kGuard + LP + i];
+      if (a.x != decltype(a.x)(sentinel) || b.x != decltype(b.x)(sentinel)) {
+        std::fprintf(stderr, "guard overwritten: L=%d V=%d INV=%d HIN=%d NLT=%d\n", L, V, int(INV), int(HIN), NLT);
+        return false;
+      }
     }
+  for (int l = 0; l < NLT; ++l) {
+    const int32_t hdr[6] = {int32_t(sizeof(C)), L, V, int32_t(INV), int32_t(HIN), NLT};
+    std::fwrite(hdr, sizeof(hdr), 1, f);
+    const std::vector<C> *both[2] = {&in[l], &out[l]};
+    for (const std::vector<C> *vec : both)
+      for (const C &c : *vec) {
+        const double z[2] = {double(c.x), double(c.y)};
+        std::fwrite(z, sizeof(z), 1, f);
+      }
   }
-  const int32_t hdr[6] = {int32_t(sizeof(C)), L, V, int32_t(INV), int32_t(HIN), 0};
-  std::fwrite(hdr, sizeof(hdr), 1, f);
-  const std::vector<C> *both[2] = {&in, &out};
-  for (const std::vector<C> *vec : both)
-    for (const C &c : *vec) {
-      const double z[2] = {double(c.x), double(c.y)};
-      std::fwrite(z, sizeof(z), 1, f);
-    }
   return true;
 }
 
@@ -105,6 +115,10 @@ template <typename C, int L> bool run_length(FILE *f, const std::vector<C> &tw, 
   ok &= run_case<C, L, 1, false, false>(f, tw, ++seed);
   ok &= run_case<C, L, 1, false, true>(f, tw, ++seed);
   ok &= run_case<C, L, 1, true, false>(f, tw, ++seed);
+  ok &= run_case<C, L, 0, false, true, 2>(f, tw, ++seed);
+  ok &= run_case<C, L, 1, true, false, 2>(f, tw, ++seed);
+  ok &= run_case<C, L, 0, false, true, 3>(f, tw, ++seed);
+  ok &= run_case<C, L, 0, true, false, 3>(f, tw, ++seed);
   return ok;
 }
 

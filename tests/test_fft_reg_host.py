@@ -4,7 +4,9 @@
 and runs every line with one std::thread per GPU lane and a std::barrier for the line's exchange
 barrier. The outputs must equal numpy's FFT (the definition of the DFT: exp(-2 pi i jk/L) forward,
 exp(+2 pi i jk/L) inverse, unnormalised) to the rounding of the precision, for every supported
-length, both radix orders, the zero-half first pass and the inverse; two runs must agree bit for
+length, both radix orders, the zero-half first pass and the inverse, with one line per thread
+group and with two and three lines sharing the group's twiddle powers (as the column passes
+transform a column's components together); two runs must agree bit for
 bit (a missing barrier between the lanes' stores and loads shows up as a run-to-run difference);
 and the guard slots around each line must stay untouched (the harness checks them)."""
 import os
@@ -32,7 +34,7 @@ def harness(tmp_path_factory):
         pytest.skip("nvcc not available")
     out = tmp_path_factory.mktemp("fft_reg_host")
     exe = str(out / "fft_reg_host")
-    cmd = [cc, "-std=c++20", "-O2", "--expt-relaxed-constexpr", "-diag-suppress", "20014",
+    cmd = [cc, "-std=c++20", "-O0", "--expt-relaxed-constexpr", "-diag-suppress", "20014",
            "-gencode", "arch=compute_103a,code=sm_103a", SRC, "-o", exe]
     res = subprocess.run(cmd, capture_output=True, text=True)
     assert res.returncode == 0, res.stderr
@@ -48,13 +50,13 @@ def _run(exe, path):
 def _cases(blob):
     off, cases = 0, []
     while off < len(blob):
-        cb, L, V, inv, hin, _ = (int(v) for v in np.frombuffer(blob[off:off + 24], dtype=np.int32))
+        cb, L, V, inv, hin, nlt = (int(v) for v in np.frombuffer(blob[off:off + 24], dtype=np.int32))
         off += 24
         x = np.frombuffer(blob[off:off + 16 * L], dtype=np.complex128)
         off += 16 * L
         y = np.frombuffer(blob[off:off + 16 * L], dtype=np.complex128)
         off += 16 * L
-        cases.append((cb, L, V, bool(inv), bool(hin), x, y))
+        cases.append((cb, L, V, bool(inv), bool(hin), nlt, x, y))
     return cases
 
 
@@ -62,17 +64,20 @@ def test_register_plans_equal_the_dft(harness):
     exe, out = harness
     cases = _cases(_run(exe, out / "a.bin"))
     lengths = (16, 32, 64, 128, 256, 512, 1024)
-    assert len(cases) == 2 * len(lengths) * 6
+    assert len(cases) == 2 * len(lengths) * (6 + 2 * 2 + 2 * 3)
     seen = set()
-    for cb, L, V, inv, hin, x, y in cases:
-        seen.add((cb, L, V, inv, hin))
+    for cb, L, V, inv, hin, nlt, x, y in cases:
+        seen.add((cb, L, V, inv, hin, nlt))
         if hin:
             assert not np.any(x[L // 2:]), (L, V)
         want = L * np.fft.ifft(x) if inv else np.fft.fft(x)
         err = np.linalg.norm(y - want) / np.linalg.norm(want)
         assert err <= (1e-6 if cb == 8 else 1e-14), (cb, L, V, inv, hin, err)
-    assert seen == {(cb, L, V, inv, hin) for cb in (8, 16) for L in lengths for V in (0, 1)
-                    for inv, hin in ((False, False), (False, True), (True, False))}
+    single = {(cb, L, V, inv, hin, 1) for cb in (8, 16) for L in lengths for V in (0, 1)
+              for inv, hin in ((False, False), (False, True), (True, False))}
+    grouped = {(cb, L, V, inv, hin, n) for cb in (8, 16) for L in lengths
+               for V, inv, hin, n in ((0, False, True, 2), (1, True, False, 2), (0, False, True, 3), (0, True, False, 3))}
+    assert seen == single | grouped
 
 
 def test_register_plans_are_deterministic(harness):
