@@ -114,3 +114,33 @@ def test_3d_argument_errors_are_reported_without_a_gpu(lib):
                           None, None, None, ctypes.byref(opts), 30, None, 0, None, 0, None)
     assert rc == -1 and b"CG options" in lib.dbi_last_error()
     assert lib.sample_3d(ctypes.byref(g), -1, None, 1, None, None, 0, None) == -1
+
+
+def test_empty_batches_are_no_ops_without_a_gpu(lib):
+    """B = 0 returns 0 after validating the arguments and before any device work, in every entry
+    point that takes a batch of wavefields (the problem arrays may then be NULL; omega is a
+    placeholder that is never read)."""
+    ref = dbi.make_medium(2000.0, 2000.0, 1155.0)
+    g = dbi.make_grid(8, 8, 16, 16, 10.0)
+    model = dbi.Model(g, ref, None)
+    empty = dbi.Batch(0, 1, 1, None)
+    opts = dbi.KrylovOpts(1e-6, 10, 1, 1)
+    by = ctypes.byref
+    assert lib.green_convolve(by(g), by(empty), None, None, None, 0, None, 0, None) == 0
+    assert lib.incident_field(by(g), by(empty), None, None, None, None, 0, None) == 0
+    assert lib.ls_apply(by(model), by(empty), None, None, None, 0, None, 0, None) == 0
+    assert lib.ls_apply_noalloc(by(model), by(empty), None, None, None, 0, None) == 0
+    assert lib.ls_solve(by(model), by(empty), None, None, None, by(opts), None, 0, None, 0, None) == 0
+    assert lib.ls_solve_gmres(by(model), by(empty), None, None, None, by(opts), 30, None, 0, None, 0, None) == 0
+    assert lib.ls_apply_k(by(model), by(empty), None, None, None, None, 0, None, 0, None) == 0
+    assert lib.ls_solve_k(by(model), by(empty), None, None, None, None, by(opts), None, 0, None, 0, None) == 0
+    g3 = dbi.make_grid3(4, 3, 5, 16, 16, 16, 10.0)
+    model3 = dbi.Model3(g3, ref, None)
+    assert lib.incident_field_3d(by(g3), by(empty), None, None, None, None, 0, None) == 0
+    assert lib.ls_apply_3d(by(model3), by(empty), None, None, None, 0, None, 0, None) == 0
+    assert lib.ls_solve_3d(by(model3), by(empty), None, None, None, by(opts), 30, None, 0, None, 0, None) == 0
+    assert lib.sample_3d(by(g3), 0, None, 1, None, None, 0, None) == 0
+    # the checks before the early return still apply to an empty batch
+    bad_opts = dbi.KrylovOpts(-1.0, 10, 1, 1)
+    assert lib.ls_solve(by(model), by(empty), None, None, None, by(bad_opts), None, 0, None, 0, None) == -1
+    assert lib.ls_solve_3d(by(model3), by(empty), None, None, None, by(opts), 0, None, 0, None, 0, None) == -1
