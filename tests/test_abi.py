@@ -144,3 +144,23 @@ def test_empty_batches_are_no_ops_without_a_gpu(lib):
     bad_opts = dbi.KrylovOpts(-1.0, 10, 1, 1)
     assert lib.ls_solve(by(model), by(empty), None, None, None, by(bad_opts), None, 0, None, 0, None) == -1
     assert lib.ls_solve_3d(by(model3), by(empty), None, None, None, by(opts), 0, None, 0, None, 0, None) == -1
+
+
+def test_the_abi_from_plain_c(lib, tmp_path):
+    """`tests/native/abi_from_c.c` includes both headers as C11 (-pedantic, warnings as errors),
+    links the library and calls its host-side entry points: version, workspace queries (2D, 3D,
+    both precisions, an unsupported FFT length) and an argument error with its message."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(build.LIB)
+    exe = str(tmp_path / "abi_from_c")
+    res = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                          os.path.join(ROOT, "tests", "native", "abi_from_c.c"), "-L", libdir, "-ldbi",
+                          f"-Wl,-rpath,{libdir}", "-o", exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, run.stdout + run.stderr
+    assert run.stdout.count("ok ") == 7
