@@ -164,3 +164,22 @@ def test_the_abi_from_plain_c(lib, tmp_path):
     run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert run.returncode == 0, run.stdout + run.stderr
     assert run.stdout.count("ok ") == 7
+
+
+def test_the_product_path_fails_loudly_without_the_library_or_a_gpu():
+    """No CPU fallback: loading a missing library raises with the build instruction, and on a
+    machine without a GPU a device problem cannot be made (fresh interpreters, since the library
+    handle is cached per process)."""
+    import subprocess
+    import sys
+    import torch
+    code = "from paper_2402_02116_gb300 import dbi; dbi.load('/nonexistent/libdbi.so')"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "CUDA library not built" in r.stderr
+    if not torch.cuda.is_available():
+        code = ("from paper_2402_02116_gb300 import dbi, inputs\n"
+                "from paper_2402_02116_gb300.problem import DeviceProblem\n"
+                "DeviceProblem(inputs.small_case(nz=4, nx=4), dbi.C64)\n"
+                "print('no error')")
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+        assert r.returncode != 0 and "no error" not in r.stdout
