@@ -92,3 +92,62 @@ def test_unbound_plan_refuses_work(lib):
         assert lib.dbi_set_radix_plan(dbi.C64, 48, 1) == -1
     finally:
         lib.dbi_group_destroy(h)
+
+
+def _pow2_at_least(n):
+    return 1 << max(4, (n - 1).bit_length())
+
+
+def test_random_plans_keep_their_invariants(lib):
+    """200 seeded random member lists (1-6 members, grids 1-300 cells per side, FFT grids from the
+    smallest allowed up to twice that, 1-5 slots each, both precisions): the slot count, the field
+    offsets (members and their slots in order, 2 nz nx elements each), the spectra held by the
+    apply workspace, solve >= apply, and destroy."""
+    import numpy as np
+    rng = np.random.default_rng(23)
+    for trial in range(200):
+        specs = []
+        for _ in range(int(rng.integers(1, 7))):
+            nz, nx = int(rng.integers(1, 301)), int(rng.integers(1, 301))
+            lz = min(1024, _pow2_at_least(2 * nz - 1) * int(rng.choice([1, 1, 2])))
+            lx = min(1024, _pow2_at_least(2 * nx - 1) * int(rng.choice([1, 1, 2])))
+            specs.append((nz, nx, lz, lx, int(rng.integers(1, 6))))
+        prec = dbi.C64 if trial % 2 == 0 else dbi.C128
+        rc, h = make(lib, specs, prec)
+        assert rc == 0, (specs, lib.dbi_last_error())
+        try:
+            slots = sum(s[4] for s in specs)
+            assert lib.dbi_group_slots(h) == slots
+            offs = (ctypes.c_longlong * (slots + 1))()
+            assert lib.dbi_group_offsets(h, offs) == 0
+            want = [0]
+            for nz, nx, _, _, B in specs:
+                want += [want[-1] + 2 * nz * nx * (k + 1) for k in range(B)]
+            assert list(offs) == want and lib.dbi_group_field_elems(h) == want[-1]
+            csize = 8 if prec == dbi.C64 else 16
+            spectra = sum(2 * B * lx * nz * csize for nz, nx, lz, lx, B in specs)
+            apply_b = lib.dbi_group_workspace_bytes(h, dbi.OP_APPLY)
+            assert apply_b >= spectra and lib.dbi_group_workspace_bytes(h, dbi.OP_SOLVE) >= apply_b
+        finally:
+            lib.dbi_group_destroy(h)
+
+
+def test_random_invalid_members_are_rejected(lib):
+    """A valid list with one member broken at random (FFT length not a power of two, FFT grid
+    smaller than 2 n - 1, no slots) is rejected as a whole with no plan."""
+    import numpy as np
+    rng = np.random.default_rng(29)
+    for trial in range(60):
+        specs = [(16, 16, 32, 32, 1), (40, 24, 128, 64, 2)]
+        kind = trial % 3
+        nz, nx = int(rng.integers(2, 200)), int(rng.integers(2, 200))
+        lz, lx = _pow2_at_least(2 * nz - 1), _pow2_at_least(2 * nx - 1)
+        if kind == 0:
+            bad = (nz, nx, 3 * lz // 2 if lz >= 32 else 48, lx, 1)
+        elif kind == 1:
+            bad = (nz, nx, lz // 2 if lz > 16 and lz // 2 < 2 * nz - 1 else lz, lx // 2 if lx > 16 else 8, 1)
+        else:
+            bad = (nz, nx, lz, lx, 0)
+        specs.insert(int(rng.integers(0, 3)), bad)
+        rc, h = make(lib, specs)
+        assert rc < 0 and not h.value, (bad, rc)
