@@ -218,6 +218,17 @@ def _need_cuda(*ts):
             raise DBIError("every tensor must be a contiguous CUDA tensor")
 
 
+def _fields(fidx, comps: int, cells: int, **named):
+    """Every field argument holds one [comps][cells] block per problem (B = the length of fidx),
+    which the kernels index from its first element: a tensor of another size would be read or
+    written past its end."""
+    B = int(fidx.numel())
+    for name, t in named.items():
+        if t is not None and t.numel() != B * comps * cells:
+            raise DBIError(f"{name} holds {t.numel()} elements; {B} problems x {comps} components x "
+                           f"{cells} cells need {B * comps * cells}")
+
+
 def make_grid(nz, nx, lz, lx, h) -> Grid:
     return Grid(int(nz), int(nx), int(lz), int(lx), float(h))
 
@@ -339,6 +350,7 @@ def incident_field(grid: Grid, omega, fidx, Gspace, src_cells, forces):
 def green_convolve(grid: Grid, omega, fidx, Ghat, src):
     """h^2 G * src for every problem."""
     precision = _precision(src)
+    _fields(fidx, 2, grid.nz * grid.nx, src=src)
     _need_cuda(Ghat, src)
     batch = _batch(omega, fidx)
     out = torch.empty_like(src)
@@ -351,6 +363,7 @@ def green_convolve(grid: Grid, omega, fidx, Ghat, src):
 def ls_apply(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None, work=None):
     """A u (Eq. 10) for every problem."""
     precision = _precision(u)
+    _fields(fidx, 2, grid.nz * grid.nx, u=u, out=out)
     _need_cuda(Ghat, u)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
@@ -367,6 +380,7 @@ def ls_apply(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None, work=No
 def ls_apply_noalloc(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None):
     """A u like ls_apply, with the library's fixed scratch array instead of a work buffer."""
     precision = _precision(u)
+    _fields(fidx, 2, grid.nz * grid.nx, u=u, out=out)
     _need_cuda(Ghat, u)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
@@ -384,6 +398,7 @@ def ls_solve(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, tol=1e
              check_every=8, work=None, out=None):
     """Solve A u = rhs for every problem (from u0, or from zero); returns (u, iters, relres, code)."""
     precision = _precision(rhs)
+    _fields(fidx, 2, grid.nz * grid.nx, rhs=rhs, u0=u0, out=out)
     _need_cuda(Ghat, rhs)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
@@ -414,6 +429,7 @@ def ls_solve_gmres(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, 
     """Solve A u = rhs by restarted GMRES(restart); returns (u, iters, relres, code), iters in Arnoldi
     steps (operator passes inside the cycles)."""
     precision = _precision(rhs)
+    _fields(fidx, 2, grid.nz * grid.nx, rhs=rhs, u0=u0)
     _need_cuda(Ghat, rhs)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
@@ -483,6 +499,7 @@ def incident_field_3d(grid: Grid3, omega, fidx, Gspace, src_cells, forces):
 
 def ls_apply_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, u, out=None):
     precision = _precision(u)
+    _fields(fidx, 3, grid.nz * grid.ny * grid.nx, u=u, out=out)
     _need_cuda(Ghat, u)
     model = _model3(grid, ref, m, precision)
     batch = _batch(omega, fidx)
@@ -497,6 +514,7 @@ def ls_solve_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, re
                 check_every=8):
     """A u = rhs in 3D by GMRES(restart); returns (u, iters, relres, code)."""
     precision = _precision(rhs)
+    _fields(fidx, 3, grid.nz * grid.ny * grid.nx, rhs=rhs, u0=u0)
     _need_cuda(Ghat, rhs)
     model = _model3(grid, ref, m, precision)
     batch = _batch(omega, fidx)
@@ -513,6 +531,7 @@ def ls_solve_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, re
 def _products3(name, grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, x, out, tol, max_iter, restart,
                check_every):
     precision = _precision(u_b)
+    _fields(fidx, 3, grid.nz * grid.ny * grid.nx, u_b=u_b)
     _need_cuda(Ghat, u_b, rec_cells, x)
     if rec_cells.dtype != torch.int32 or rec_cells.dim() != 2 or rec_cells.shape[1] != 3:
         raise DBIError("rec_cells must be int32 [n_rec][3]")
@@ -541,6 +560,7 @@ def frechet_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_
 def adjoint_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, r, tol=1e-6,
                      max_iter=1000, restart=30, check_every=8):
     """Re J^H r in 3D summed over the problems: [6][nz][ny][nx] real (and the solves' status)."""
+    _fields(fidx, int(rec_cells.shape[0]), 3, r=r)
     g = torch.empty((6, grid.nz, grid.ny, grid.nx), dtype=real_dtype(_precision(u_b)), device=u_b.device)
     return _products3("adjoint_apply_3d", grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, r, g, tol, max_iter,
                       restart, check_every)
@@ -561,6 +581,8 @@ def normal_cg_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cell
                  check_every=8):
     """Tikhonov normal-equation CG in 3D; returns (dm [6][nz][ny][nx], lambda, residual history)."""
     precision = _precision(u_b)
+    _fields(fidx, 3, grid.nz * grid.ny * grid.nx, u_b=u_b)
+    _fields(fidx, int(rec_cells.shape[0]), 3, dd=dd)
     _need_cuda(Ghat, u_b, dd, rec_cells, *([] if power_start is None else [power_start]))
     model = _model3(grid, ref, m_b, precision)
     batch = _batch(omega, fidx)
@@ -599,6 +621,7 @@ def greens_tabulate_k(grid: Grid, ref: Medium, omega: torch.Tensor, precision: i
 def ls_apply_k(grid: Grid, ref: Medium, m, omega, fidx, Ghat, Dhat, u, out=None):
     """A u in the paper-literal form of Eq. 9 (the gradient on the Green's tensor)."""
     precision = _precision(u)
+    _fields(fidx, 2, grid.nz * grid.nx, u=u, out=out)
     _need_cuda(Ghat, Dhat, u)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
@@ -613,6 +636,7 @@ def ls_solve_k(grid: Grid, ref: Medium, m, omega, fidx, Ghat, Dhat, rhs, u0=None
                check_every=8):
     """Solve A u = rhs with the operator of ls_apply_k; returns (u, iters, relres, code)."""
     precision = _precision(rhs)
+    _fields(fidx, 2, grid.nz * grid.nx, rhs=rhs, u0=u0)
     _need_cuda(Ghat, Dhat, rhs)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
@@ -630,6 +654,7 @@ def frechet_apply(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cell
                   max_iter=1000, check_every=8, with_status=False):
     """J dm sampled at the receivers, [B][n_rec][2] (and the solve's (iters, relres, code))."""
     precision = _precision(u_b)
+    _fields(fidx, 2, grid.nz * grid.nx, u_b=u_b)
     _need_cuda(Ghat, u_b, dm)
     model = _model(grid, ref, m_b, precision)
     if dm.dtype != real_dtype(precision):
@@ -650,6 +675,8 @@ def adjoint_apply(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cell
                   max_iter=1000, check_every=8, with_status=False):
     """Re J^H r summed over problems, [5][nz][nx] (and the solve's (iters, relres, code))."""
     precision = _precision(u_b)
+    _fields(fidx, 2, grid.nz * grid.nx, u_b=u_b)
+    _fields(fidx, int(rec_cells.shape[0]), 2, r=r)
     _need_cuda(Ghat, u_b, r)
     model = _model(grid, ref, m_b, precision)
     batch = _batch(omega, fidx)
@@ -667,6 +694,8 @@ def adjoint_apply(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cell
 def data_residual(grid: Grid, omega, fidx, rec_cells, u, d_obs):
     """(r = P u - d_obs, phi = 1/2 ||r||^2 as a device float64 scalar tensor)."""
     precision = _precision(u)
+    _fields(fidx, 2, grid.nz * grid.nx, u=u)
+    _fields(fidx, int(rec_cells.shape[0]), 2, d_obs=d_obs)
     _need_cuda(u, d_obs)
     batch = _batch(omega, fidx)
     rec = _receivers(rec_cells)
@@ -681,6 +710,8 @@ def normal_cg(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, d
               lambda_rel=1e-3, power_iters=10, power_start=None, tol=1e-6, max_iter=1000, check_every=8):
     """Tikhonov normal-equation CG; returns (dm [5][nz][nx], lambda, residual history)."""
     precision = _precision(u_b)
+    _fields(fidx, 2, grid.nz * grid.nx, u_b=u_b)
+    _fields(fidx, int(rec_cells.shape[0]), 2, dd=dd)
     _need_cuda(Ghat, u_b, dd, power_start)
     model = _model(grid, ref, m_b, precision)
     batch = _batch(omega, fidx)

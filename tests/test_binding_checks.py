@@ -1,0 +1,79 @@
+"""The binding's size checks on field arguments (CPU only): every wrapper that hands wavefields or
+receiver data to the library checks that each holds one block per problem (B = the length of
+fidx) before anything reaches the device, so a wrongly sized tensor is an error, not a read or
+write past its end. With CPU tensors a correctly sized call gets as far as the CUDA check."""
+import pytest
+import torch
+
+from paper_2402_02116_gb300 import dbi
+
+B, NZ, NX, NY, NREC = 3, 4, 5, 2, 6
+C = torch.complex64
+
+
+def f(*shape):
+    return torch.zeros(shape, dtype=C)
+
+
+def common2d():
+    g = dbi.make_grid(NZ, NX, 16, 16, 10.0)
+    ref = dbi.make_medium(2000.0, 2000.0, 1155.0)
+    m = torch.zeros((5, NZ, NX), dtype=torch.float32)
+    omega = torch.ones(1, dtype=torch.float64)
+    fidx = torch.zeros(B, dtype=torch.int32)
+    rec = torch.zeros((NREC, 2), dtype=torch.int32)
+    return g, ref, m, omega, fidx, f(1, 3, 16, 16), rec
+
+
+def common3d():
+    g = dbi.make_grid3(NZ, NY, NX, 16, 16, 16, 10.0)
+    ref = dbi.make_medium(2000.0, 2000.0, 1155.0)
+    m = torch.zeros((6, NZ, NY, NX), dtype=torch.float32)
+    omega = torch.ones(1, dtype=torch.float64)
+    fidx = torch.zeros(B, dtype=torch.int32)
+    rec = torch.zeros((NREC, 3), dtype=torch.int32)
+    return g, ref, m, omega, fidx, f(1, 6, 16, 16, 16), rec
+
+
+def calls():
+    g, ref, m, om, fi, G, rec = common2d()
+    u, bad = f(B, 2, NZ, NX), f(B - 1, 2, NZ, NX)
+    d, dbad = f(B, NREC, 2), f(B, NREC - 1, 2)
+    dm = torch.zeros((5, NZ, NX), dtype=torch.float32)
+    g3, ref3, m3, om3, fi3, G3, rec3 = common3d()
+    u3, bad3 = f(B, 3, NZ, NY, NX), f(B, 3, NZ, NY, NX - 1)
+    d3, d3bad = f(B, NREC, 3), f(B + 1, NREC, 3)
+    dm3 = torch.zeros((6, NZ, NY, NX), dtype=torch.float32)
+    yield "ls_apply", lambda x: dbi.ls_apply(g, ref, m, om, fi, G, x), u, bad
+    yield "ls_apply out", lambda x: dbi.ls_apply(g, ref, m, om, fi, G, u, out=x), u, bad
+    yield "ls_apply_noalloc", lambda x: dbi.ls_apply_noalloc(g, ref, m, om, fi, G, x), u, bad
+    yield "ls_solve", lambda x: dbi.ls_solve(g, ref, m, om, fi, G, x), u, bad
+    yield "ls_solve u0", lambda x: dbi.ls_solve(g, ref, m, om, fi, G, u, u0=x), u, bad
+    yield "ls_solve_gmres", lambda x: dbi.ls_solve_gmres(g, ref, m, om, fi, G, x), u, bad
+    yield "green_convolve", lambda x: dbi.green_convolve(g, om, fi, G, x), u, bad
+    yield "ls_apply_k", lambda x: dbi.ls_apply_k(g, ref, m, om, fi, G, G, x), u, bad
+    yield "ls_solve_k", lambda x: dbi.ls_solve_k(g, ref, m, om, fi, G, G, x), u, bad
+    yield "frechet_apply", lambda x: dbi.frechet_apply(g, ref, m, om, fi, G, x, rec, dm), u, bad
+    yield "adjoint_apply u_b", lambda x: dbi.adjoint_apply(g, ref, m, om, fi, G, x, rec, d), u, bad
+    yield "adjoint_apply r", lambda x: dbi.adjoint_apply(g, ref, m, om, fi, G, u, rec, x), d, dbad
+    yield "data_residual u", lambda x: dbi.data_residual(g, om, fi, rec, x, d), u, bad
+    yield "data_residual d_obs", lambda x: dbi.data_residual(g, om, fi, rec, u, x), d, dbad
+    yield "normal_cg u_b", lambda x: dbi.normal_cg(g, ref, m, om, fi, G, x, rec, d), u, bad
+    yield "normal_cg dd", lambda x: dbi.normal_cg(g, ref, m, om, fi, G, u, rec, x), d, dbad
+    yield "ls_apply_3d", lambda x: dbi.ls_apply_3d(g3, ref3, m3, om3, fi3, G3, x), u3, bad3
+    yield "ls_solve_3d", lambda x: dbi.ls_solve_3d(g3, ref3, m3, om3, fi3, G3, x), u3, bad3
+    yield "frechet_apply_3d", lambda x: dbi.frechet_apply_3d(g3, ref3, m3, om3, fi3, G3, x, rec3, dm3), u3, bad3
+    yield "adjoint_apply_3d r", lambda x: dbi.adjoint_apply_3d(g3, ref3, m3, om3, fi3, G3, u3, rec3, x), d3, d3bad
+    yield "normal_cg_3d u_b", lambda x: dbi.normal_cg_3d(g3, ref3, m3, om3, fi3, G3, x, rec3, d3), u3, bad3
+    yield "normal_cg_3d dd", lambda x: dbi.normal_cg_3d(g3, ref3, m3, om3, fi3, G3, u3, rec3, x), d3, d3bad
+
+
+CALLS = list(calls())
+
+
+@pytest.mark.parametrize("name, call, good, bad", CALLS, ids=[c[0] for c in CALLS])
+def test_field_sizes_are_checked_before_the_device(name, call, good, bad):
+    with pytest.raises(dbi.DBIError, match="holds .* elements"):
+        call(bad)
+    with pytest.raises(dbi.DBIError, match="CUDA tensor"):
+        call(good)
