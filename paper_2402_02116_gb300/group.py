@@ -90,8 +90,18 @@ class UnevenBatch:
         self._bound = op
 
     # --- entry points ---------------------------------------------------------------------------
+    def _fields(self, **named):
+        """Field arguments hold every slot's block (field_elems elements of the batch's dtype): the
+        persistent kernels index them by the plan's offsets."""
+        for name, t in named.items():
+            if t is not None and (t.numel() != self.field_elems or t.dtype != self.cdt):
+                raise dbi.DBIError(f"{name} holds {t.numel()} elements of {t.dtype}; the batch's fields hold "
+                                   f"{self.field_elems} of {self.cdt}")
+        dbi._need_cuda(*named.values())
+
     def apply(self, u, out=None):
         """A u for every slot (flat fields)."""
+        self._fields(u=u, out=out)
         self.bind(dbi.OP_APPLY)
         out = torch.empty_like(u) if out is None else out
         dbi._check(dbi.load().ls_apply_group(self._h, dbi._ptr(u), dbi._ptr(out), dbi._stream(self.device)),
@@ -100,6 +110,7 @@ class UnevenBatch:
 
     def solve(self, rhs, tol=1e-6, max_iter=2000, check_every=8, graph=True, u0=None):
         """Solve A u = rhs for every slot; returns (u, iters, relres, code), status per slot."""
+        self._fields(rhs=rhs, u0=u0)
         self.bind(dbi.OP_SOLVE)
         u = torch.empty_like(rhs) if u0 is None else u0.clone()
         (iters, relres, code), st = dbi._status(self.slots, self.device)
@@ -111,6 +122,7 @@ class UnevenBatch:
 
     def tune(self, u):
         """Autotune radix plans and persistent grids on field u; returns the measurements."""
+        self._fields(u=u)
         self.bind(dbi.OP_APPLY)
         out = torch.empty_like(u)
         rep = dbi.GroupTuning()

@@ -77,3 +77,19 @@ def test_field_sizes_are_checked_before_the_device(name, call, good, bad):
         call(bad)
     with pytest.raises(dbi.DBIError, match="CUDA tensor"):
         call(good)
+
+
+def test_uneven_batch_fields_are_checked_before_the_device():
+    """UnevenBatch.apply / solve / tune take flat fields of every slot: a tensor of another size or
+    dtype is an error before the work buffer is bound or anything reaches the device."""
+    from paper_2402_02116_gb300.group import UnevenBatch
+    G = UnevenBatch.__new__(UnevenBatch)  # the checks need only the field size and dtype
+    G.field_elems, G.cdt = 40, torch.complex64
+    good, short, wide = f(40), f(39), torch.zeros(40, dtype=torch.complex128)
+    for call in (lambda x: G.apply(x), lambda x: G.apply(good, out=x), lambda x: G.solve(x),
+                 lambda x: G.solve(good, u0=x), lambda x: G.tune(x)):
+        for bad in (short, wide):
+            with pytest.raises(dbi.DBIError, match="holds .* elements"):
+                call(bad)
+        with pytest.raises(dbi.DBIError, match="CUDA tensor"):
+            call(good)
