@@ -397,12 +397,12 @@ def small_case_3d(nz=4, ny=3, nx=5, h=10.0, seed=21, n_src=2, freqs=(8.0,), amp=
         krylov_tol=1e-10, seed=seed)
 
 
-def hess3d_like(nz=32, ny=40, nx=80, h=25.0, n_src=16, freqs=(3.0, 5.0, 7.0, 9.0), seed=6) -> Workload3D:
+def hess3d_like(nz=32, ny=40, nx=80, h=25.0, n_src=16, freqs=(3.0, 5.0, 7.0, 9.0), seed=6, n_rec=None) -> Workload3D:
     """The size of the paper's modified 3D VTI example (2000 m x 1000 m x 800 m at h = 25 m:
     80 x 40 x 32 cells): the VTI background extended along y (C66 = C55), three horizontal layers
     and four Gaussian anomalies of +-15 % per parameter; isotropic reference; vertical forces on a
-    4 x 4 surface grid; receivers on every 2nd surface cell. (The paper's Hess model itself is not
-    available.)"""
+    4 x 4 surface grid; receivers on every 2nd surface cell, or on an even surface grid of n_rec.
+    (The paper's Hess model itself is not available.)"""
     rng = np.random.default_rng(seed)
     m_bg = vti_background_3d(nz, ny, nx)
     pert = np.zeros((6, nz, ny, nx))
@@ -425,5 +425,13 @@ def hess3d_like(nz=32, ny=40, nx=80, h=25.0, n_src=16, freqs=(3.0, 5.0, 7.0, 9.0
         lz=fft_len(nz), ly=fft_len(ny), lx=fft_len(nx), rho0=rho, alpha0=a0, beta0=b0, model=model,
         freqs_hz=np.asarray(freqs, dtype=np.float64), src_cells=src,
         src_force=np.tile([0.0, 0.0, 1.0], (len(src), 1)),
-        rec_cells=np.array([[0, y, x] for y in range(0, ny, 2) for x in range(0, nx, 2)], dtype=np.int64),
+        rec_cells=(np.array([[0, y, x] for y in range(0, ny, 2) for x in range(0, nx, 2)], dtype=np.int64)
+                   if n_rec is None else _surface_grid(ny, nx, n_rec)),
         krylov_tol=1e-5, seed=seed)
+
+
+def hess3d_paper_acquisition(seed=6) -> Workload3D:
+    """The acquisition of the paper's 3D example on the hess3d_like model: 100 vertical forces on a
+    10 x 10 surface grid, 400 receivers on a 20 x 20 surface grid, 7 frequencies 3-15 Hz (700
+    wavefields; the DBI loop takes them one frequency, 100 wavefields, at a time)."""
+    return hess3d_like(n_src=100, freqs=(3.0, 5.0, 7.0, 9.0, 11.0, 13.0, 15.0), seed=seed, n_rec=400)

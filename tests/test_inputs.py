@@ -102,3 +102,18 @@ def test_seeded_and_deterministic(make):
     a, b = make(), make()
     assert np.array_equal(a.model, b.model) and np.array_equal(a.src_cells, b.src_cells)
     assert math.isclose(float(np.sum(a.model)), float(np.sum(b.model)), rel_tol=0, abs_tol=0)
+
+
+def test_the_paper_3d_acquisition():
+    """100 sources and 400 receivers uniformly on the surface, 7 frequencies 3-15 Hz, on the same
+    80 x 40 x 32 model as the benchmark's 3D workload."""
+    w, base = I.hess3d_paper_acquisition(), I.hess3d_like()
+    assert w.n_src == 100 and len(w.rec_cells) == 400 and list(w.freqs_hz) == [3.0, 5.0, 7.0, 9.0, 11.0, 13.0, 15.0]
+    assert np.array_equal(w.model, base.model)
+    for cells in (w.src_cells, w.rec_cells):
+        assert np.all(cells[:, 0] == 0) and len({tuple(c) for c in cells.tolist()}) == len(cells)
+        assert np.all((cells[:, 1] >= 0) & (cells[:, 1] < 40) & (cells[:, 2] >= 0) & (cells[:, 2] < 80))
+    ys, xs = np.unique(w.rec_cells[:, 1]), np.unique(w.rec_cells[:, 2])
+    assert len(ys) == 20 and len(xs) == 20 and np.ptp(np.diff(ys)) <= 1 and np.ptp(np.diff(xs)) <= 1
+    # one frequency of it is one library call: B * 3 * nz = 100 * 3 * 32 within the 3D launch limit
+    assert w.n_src * 3 * w.nz <= 65535
