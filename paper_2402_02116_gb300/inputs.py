@@ -183,6 +183,38 @@ def config2_batched_forward(n=256, n_src=32, nf=8, seed=2) -> Workload:
         krylov_tol=1e-5, seed=seed)
 
 
+def _paper_2d_example(name, nz, nx, n_src, n_rec, freqs, smooth, seed) -> Workload:
+    """A stand-in with the geometry of one of the paper's 2D VTI examples (their models are not
+    available): nz x nx cells of 20 m, n_src vertical forces and n_rec receivers evenly on the
+    surface; true model = the config-2 VTI background with 3 random horizontal layers and 4
+    Gaussian anomalies (sigma 3-10 cells), each +/-15 % per parameter, clipped to +/-15 %; initial
+    model = the true model smoothed by a Gaussian of `smooth` cells, as the paper builds it."""
+    rng = np.random.default_rng(seed)
+    m_bg = vti_background(nz, nx)
+    rho0, a0, b0 = isotropic_reference_for(m_bg)
+    pert = _random_layers(rng, nz, nx, 3, 0.15) + _random_anomalies(rng, nz, nx, 4, 0.15, (3.0, 10.0))
+    m_true = m_bg * (1.0 + np.clip(pert, -0.15, 0.15))
+    m0 = np.stack([_gauss_filter(m_true[p], smooth) for p in range(5)])
+    src, rec = surface_line(nx, n_src), surface_line(nx, n_rec)
+    return Workload(
+        name=name, nz=nz, nx=nx, h=20.0, lz=fft_len(nz), lx=fft_len(nx), rho0=rho0, alpha0=a0, beta0=b0,
+        model=m0, model_true=m_true, freqs_hz=np.asarray(freqs, dtype=np.float64),
+        src_cells=np.stack([np.zeros_like(src), src], axis=1), src_force=np.tile([0.0, 1.0], (n_src, 1)),
+        rec_cells=np.stack([np.zeros_like(rec), rec], axis=1), krylov_tol=1e-5, seed=seed)
+
+
+def reservoir_like(seed=7) -> Workload:
+    """The geometry of the paper's 2D VTI reservoir example: 180 x 45 cells (3600 m x 900 m), 45
+    sources, 90 receivers, 9 frequencies 3-19 Hz, initial model smoothed over 15 cells."""
+    return _paper_2d_example("reservoir_like_180x45", 45, 180, 45, 90, np.arange(3.0, 20.0, 2.0), 15.0, seed)
+
+
+def hess2d_like(seed=8) -> Workload:
+    """The geometry of the paper's 2D VTI Hess example: 161 x 43 cells (3220 m x 860 m), 40 sources,
+    80 receivers, 8 frequencies 3-17 Hz, initial model smoothed over 14 cells."""
+    return _paper_2d_example("hess2d_like_161x43", 43, 161, 40, 80, np.arange(3.0, 18.0, 2.0), 14.0, seed)
+
+
 def config3_linear_dbi(n=128, n_src=16, freqs=(4.0, 8.0, 12.0, 16.0), seed=3) -> Workload:
     """Isotropic reference (2000, 1155, 2000); true model = reference + 4 seeded Gaussian anomalies
     (+/-10 % per parameter); the DBI background is the true model smoothed by a Gaussian of 8 cells

@@ -117,3 +117,22 @@ def test_the_paper_3d_acquisition():
     assert len(ys) == 20 and len(xs) == 20 and np.ptp(np.diff(ys)) <= 1 and np.ptp(np.diff(xs)) <= 1
     # one frequency of it is one library call: B * 3 * nz = 100 * 3 * 32 within the 3D launch limit
     assert w.n_src * 3 * w.nz <= 65535
+
+
+@pytest.mark.parametrize("make, shape, n_src, n_rec, freqs", [
+    (I.reservoir_like, (45, 180), 45, 90, [3, 5, 7, 9, 11, 13, 15, 17, 19]),
+    (I.hess2d_like, (43, 161), 40, 80, [3, 5, 7, 9, 11, 13, 15, 17]),
+])
+def test_the_paper_2d_example_geometries(make, shape, n_src, n_rec, freqs):
+    """The reservoir (3600 m x 900 m) and 2D Hess (3220 m x 860 m) examples' grids of 20 m cells,
+    surface acquisition and frequencies; the initial model is the smoothed true model."""
+    w = make()
+    assert (w.nz, w.nx, w.h) == (*shape, 20.0) and w.lz >= 2 * w.nz - 1 and w.lx >= 2 * w.nx - 1
+    assert w.n_src == n_src and len(w.rec_cells) == n_rec and list(w.freqs_hz) == freqs
+    for cells in (w.src_cells, w.rec_cells):
+        assert np.all(cells[:, 0] == 0) and len(np.unique(cells[:, 1])) == len(cells)
+    ratio = w.model_true / I.vti_background(w.nz, w.nx)
+    assert ratio.min() >= 0.85 - 1e-12 and ratio.max() <= 1.15 + 1e-12
+    tv = lambda m: np.abs(np.diff(m, axis=-1)).sum() + np.abs(np.diff(m, axis=-2)).sum()  # noqa: E731
+    for p in range(5):
+        assert tv(w.model[p]) < tv(w.model_true[p])
