@@ -183,3 +183,37 @@ def test_the_product_path_fails_loudly_without_the_library_or_a_gpu():
                 "print('no error')")
         r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
         assert r.returncode != 0 and "no error" not in r.stdout
+
+
+def test_workspace_queries_grow_with_the_batch_and_never_wrap(lib):
+    """Every workspace query, for seeded random grids and batches: the size grows with B, complex128
+    needs at least what complex64 does, and a batch far beyond any GPU (2^20 problems) gives a size
+    above the bytes of its own wavefields (no 32-bit products that would wrap)."""
+    import numpy as np
+    rng = np.random.default_rng(31)
+    ops2d = [dbi.OP_CONVOLVE, dbi.OP_APPLY, dbi.OP_SOLVE, dbi.OP_FRECHET, dbi.OP_ADJOINT, dbi.OP_NORMAL_CG,
+             dbi.OP_APPLY_K, dbi.OP_SOLVE_K]
+    for _ in range(60):
+        nz, nx = int(rng.integers(1, 513)), int(rng.integers(1, 513))
+        g = dbi.make_grid(nz, nx, max(16, 1 << (2 * nz - 2).bit_length()), max(16, 1 << (2 * nx - 2).bit_length()), 5.0)
+        B = int(rng.integers(1, 300))
+        for op in ops2d:
+            small = dbi.workspace_bytes(g, B, dbi.C64, op)
+            assert small > 0 and dbi.workspace_bytes(g, B + 7, dbi.C64, op) >= small, (nz, nx, B, op)
+            assert dbi.workspace_bytes(g, B, dbi.C128, op) >= small
+            huge = dbi.workspace_bytes(g, 1 << 20, dbi.C64, op)
+            assert huge >= (1 << 20) * 2 * nz * nx * 8 // 4 and huge >= small, (nz, nx, op, huge)
+        gm = lib.dbi_gmres_workspace_bytes(ctypes.byref(g), B, dbi.C64, 30)
+        assert gm >= 31 * B * 2 * nz * nx * 8 and lib.dbi_gmres_workspace_bytes(ctypes.byref(g), 1 << 20, dbi.C64, 30) > gm
+    for _ in range(30):
+        nz, ny, nx = (int(v) for v in rng.integers(1, 65, size=3))
+        g3 = dbi.make_grid3(nz, ny, nx, *(max(16, 1 << (2 * n - 2).bit_length()) for n in (nz, ny, nx)), 25.0)
+        B = int(rng.integers(1, 100))
+        field = B * 3 * nz * ny * nx * 8
+        for op, restart in ((dbi.OP_APPLY, 1), (dbi.OP_SOLVE, 30)):
+            a = dbi.workspace_bytes_3d(g3, B, dbi.C64, op, restart)
+            assert a > 0 and dbi.workspace_bytes_3d(g3, B + 3, dbi.C64, op, restart) >= a
+            assert dbi.workspace_bytes_3d(g3, B, dbi.C128, op, restart) >= a
+        assert dbi.workspace_bytes_3d(g3, B, dbi.C64, dbi.OP_SOLVE, 30) >= 31 * field
+        p = lib.dbi_products_workspace_bytes_3d(ctypes.byref(g3), B, dbi.C64, 30)
+        assert p >= 31 * field and lib.dbi_products_workspace_bytes_3d(ctypes.byref(g3), 1 << 20, dbi.C64, 30) > p
