@@ -7,7 +7,7 @@ import torch
 
 import oracle as O
 from paper_2402_02116_gb300 import build, dbi, inputs
-from paper_2402_02116_gb300.dbi_loop import dbi_inversion, observed_data, single_frequency
+from paper_2402_02116_gb300.dbi_loop import dbi_inversion, observed_data
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]

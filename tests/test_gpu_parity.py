@@ -5,7 +5,6 @@ for solves; complex64 path 1e-5 for wavefields and data (the wavefield tolerance
 benchmark configurations) and 1e-4 for gradients. The complex64 bound comes from FP32 rounding
 (u = 6e-8) amplified by the O(log L) depth of the FFTs and the stencil's cancellation.
 """
-import math
 
 import numpy as np
 import pytest
