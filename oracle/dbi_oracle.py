@@ -29,9 +29,11 @@ leaves unstated):
     (Re J^H r)_rho = Re(w^2 u_a . u_b), (Re J^H r)_p = -Re(eps(u_a)^T B_p eps(u_b)).
   * Normal equation (Eq. 23, 24): (Re J^H J + lambda I) dm = Re J^H du by CG on relative unknowns.
 
-Parity of the whole LS solution against physics is pinned only through invariants (zero
-contrast, Born series, reciprocity, dense solve, finite-difference derivatives); the paper
-prints no wavefield or data values.
+Pins (tests/test_oracle_pins.py): besides invariants (zero contrast, Born series, reciprocity,
+dense solve, finite-difference derivatives), the assembled LS solution is tied to the physics: its
+finite-difference residual of the heterogeneous elastic equation falls as O(h^2) under grid
+refinement, and the offset lattice's orientation is fixed by the P and S phase rates along each
+axis of a non-square lattice. The paper prints no wavefield or data values.
 """
 from __future__ import annotations
 
