@@ -1,23 +1,30 @@
 #!/usr/bin/env python
-"""Benchmark of the batched hot path on the 256 x 256 VTI workload (32 sources x 8 frequencies).
+"""Benchmark of the batched hot path: one step = the misfit gradient of a batch of (source,
+frequency) problems.
 
-One step = one pass of the whole hot path over the batch: Green's tables for the 8 frequencies,
-incident fields, the batched complex64 BiCGSTAB forward solve of A u = u0 (every iteration two
-fused LS-operator passes), the data residual at the receivers, and the adjoint: conj(residual)
-injected at the receivers, convolved with G, solved in the background and imaged against u into
-the misfit gradient for (rho, C11, C13, C33, C55). The metric counts LS-operator cell-applies
-(cells x problems x operator passes, the Green's convolution of the adjoint source included) per
-second of wall time on the device.
+Default workload (`vti512`): 512 x 512 VTI cells of 5 m, FFT grid 1024 x 1024, 64 surface sources x
+6 frequencies (3-18 Hz) = 384 problems, 256 receivers, a smooth random contrast of +/-10 %. One
+step: Green's tables for the 6 frequencies, incident fields, the batched complex64 BiCGSTAB
+forward solve of A u = u0 to a relative residual of 1e-6 (every iteration two fused LS-operator
+passes), the data residual at the receivers, and the adjoint: conj(residual) injected at the
+receivers, convolved with G, solved in the background and imaged against u into the misfit
+gradient for (rho, C11, C13, C33, C55). The metric counts LS-operator cell-applies (cells x
+problems x operator passes, the Green's convolution of the adjoint source included) per second
+of device time. The line also carries the same step on the 256 x 256 workload (32 sources x 8
+frequencies, 5-20 Hz), the accuracy of sampled wavefields, data, residuals and a sub-batch
+gradient against the FP64 CPU oracle, and the oracle's own rate on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload vti256       # the 256^2 gradient step alone
     python bench.py --workload uneven40     # the 40-problem uneven batch (grids 64^2 .. 512^2)
     python bench.py --workload formk256     # operator passes in the paper-literal form of Eq. 9
     python bench.py --workload gmres256     # batched forward solves by GMRES(30) beside BiCGSTAB
     python bench.py --workload hess3d       # 3D operator passes and GMRES solves, 80 x 40 x 32 cells
 
-With N > 1 (torchrun, one rank per GPU) every rank runs its own 32 sources x 8 frequencies
-(weak scaling) and the gradients are summed across ranks with one all-reduce per step.
-`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+With N > 1 (torchrun, one rank per GPU) every rank runs its own sources x all frequencies (weak
+scaling) and the gradients are summed across ranks with one all-reduce per step.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload, one
+process per host core.
 """
 from __future__ import annotations
 
@@ -37,12 +44,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2402_02116_gb300 import inputs  # noqa: E402
-from paper_2402_02116_gb300.shard import reduce_gradient, shard_workload  # noqa: E402
 
 METRIC = "LS operator cell-applies/s (cells x sources x frequencies)"
 UNIT = "cell-applies/s"
-TOL = 1e-5
+TOL = 1e-6          # BiCGSTAB relative residual of the benchmark's solves
 MAX_ITER = 3000
+ORACLE_TOL = 1e-12  # the FP64 oracle's solves that the accuracy block compares against
 
 
 def parse_args():
@@ -53,36 +60,54 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle sample")
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 plain-path sample")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy block (FP64 oracle)")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 256^2 line inside the 512^2 one")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparator")
+    ap.add_argument("--cores", type=int, default=0, help="host processes for the oracle (0: every core)")
     ap.add_argument("--check-every", type=int, default=4,
                     help="BiCGSTAB iterations between host convergence checks (each check also "
                          "compacts the launches to the problems still active)")
-    ap.add_argument("--workload", choices=["vti256", "uneven40", "formk256", "gmres256", "hess3d"],
-                    default="vti256",
-                    help="vti256: the gradient step of the benchmark (default); uneven40: operator "
-                         "passes over the 40-problem uneven batch (persistent launches, autotuned), "
+    ap.add_argument("--workload", choices=["vti512", "vti256", "uneven40", "formk256", "gmres256", "hess3d"],
+                    default="vti512",
+                    help="vti512: the gradient step on 512^2 cells, 64 sources x 6 frequencies (default); "
+                         "vti256: the gradient step on 256^2 cells, 32 sources x 8 frequencies; uneven40: "
+                         "operator passes over the 40-problem uneven batch (persistent launches, autotuned), "
                          "plus one graph-captured solve; formk256: operator passes over the 256^2 "
                          "batch in the paper-literal form (derivatives on G, Eq. 9) beside the "
                          "divergence form; gmres256: batched forward solves of the 256^2 batch by "
                          "restarted GMRES beside BiCGSTAB; hess3d: 3D operator passes and GMRES "
                          "solves on 80 x 40 x 32 cells (16 sources x 4 frequencies)")
     ap.add_argument("--restart", type=int, default=30, help="GMRES restart length (gmres256)")
-    ap.add_argument("--sources", type=int, default=32,
-                    help="sources per GPU (32 is the benchmark workload; fewer make a smaller batch "
-                         "of the same grid for profiler captures)")
+    ap.add_argument("--sources", type=int, default=0,
+                    help="sources per GPU (0: the workload's own, 64 at 512^2 and 32 at 256^2; fewer make a "
+                         "smaller batch of the same grid for profiler captures)")
     return ap.parse_args()
 
 
-def workload(rank: int, world: int, sources: int = 32):
-    """The 256 x 256 VTI workload; with several ranks the job has `sources` surface sources per
-    rank and every rank keeps its round-robin shard of them (weak scaling)."""
-    w = inputs.config2_batched_forward()
-    if world > 1 or sources != 32:
-        cols = inputs.surface_line(w.nx, sources * world)
-        w.src_cells = np.stack([np.zeros_like(cols), cols], axis=1)
-        w.src_force = np.tile([0.0, 1.0], (len(cols), 1))
+def default_sources(name: str) -> int:
+    return 64 if name == "vti512" else 32
+
+
+def workload(name: str, rank: int = 0, world: int = 1, sources: int = 0):
+    """The gradient workloads: `vti512` (512 x 512 cells, smooth random contrast, 6 frequencies
+    3-18 Hz) or `vti256` (256 x 256 cells, layers and anomalies, 8 frequencies 5-20 Hz). With
+    several ranks the job has `sources` surface sources per rank and every rank keeps its
+    round-robin shard of them (weak scaling)."""
+    full = default_sources(name)
+    n = sources or full
+    if name == "vti512":
+        w = inputs.config4_misfit(n_src=n * world)
+    else:
+        w = inputs.config2_batched_forward()
+        if n * world != full:
+            cols = inputs.surface_line(w.nx, n * world)
+            w.src_cells = np.stack([np.zeros_like(cols), cols], axis=1)
+            w.src_force = np.tile([0.0, 1.0], (len(cols), 1))
+    if world > 1:
+        from paper_2402_02116_gb300.shard import shard_workload
         w = shard_workload(w, rank, world)
-        if sources != 32:
-            w.name = f"vti{w.nz}x{w.nx}_{sources}src_{w.nf}f"
+    if n != full:
+        w.name = f"vti{w.nz}x{w.nx}_{n}src_{w.nf}f"
     return w
 
 
@@ -92,14 +117,16 @@ def config_dict(w, world):
             "receivers": int(len(w.rec_cells)), "problems_per_gpu": w.n_problems,
             "krylov": f"BiCGSTAB to {TOL:g} relative residual", "precision": "complex64 operator, FP64 reductions",
             "step": "greens_tabulate + incident_field + ls_solve + data_residual + adjoint_apply (gradient)",
-            "l2": "inputs larger than L2: each wavefield batch is 256 MB (the L2 holds 129 MB)",
+            "l2": f"inputs larger than L2: each wavefield batch is {w.n_problems * 16 * w.nz * w.nx / 1e6:.0f} MB "
+                  "(the L2 holds 129 MB)",
             "parallelism": f"dp{world} (sources sharded, gradient all-reduce)" if world > 1 else "single GPU"}
 
 
 def synthetic_data(w, seed=7):
     """Observed data of the same shape as the receiver data, at the scale of the incident field
-    (|d| ~ 1e-10 m for a unit force): seeded Gaussian."""
-    return inputs.seeded_complex((w.n_problems, len(w.rec_cells), 2), seed) * 1e-10
+    (|d| ~ 1e-10 m for a unit force): seeded Gaussian, rounded to complex64 so that the GPU and the
+    oracle read the same values."""
+    return (inputs.seeded_complex((w.n_problems, len(w.rec_cells), 2), seed) * 1e-10).astype(np.complex64)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -156,12 +183,71 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
+class GradientStep:
+    """One gradient step of a workload on one device: every call goes through the library's C ABI
+    (binding in paper_2402_02116_gb300/dbi.py)."""
+
+    def __init__(self, w, dev, check_every, precision=None):
+        from paper_2402_02116_gb300 import dbi
+        from paper_2402_02116_gb300.problem import DeviceProblem
+        self.dbi = dbi
+        self.w = w
+        self.P = DeviceProblem(w, dbi.C64 if precision is None else precision, device=dev)
+        self.check_every = check_every
+        self.cells = w.nz * w.nx
+
+    def __call__(self, m, d_obs):
+        dbi, P = self.dbi, self.P
+        Ghat, Gspace = dbi.greens_tabulate(P.grid, P.ref, P.omega, P.precision)
+        u0 = dbi.incident_field(P.grid, P.omega, P.fidx, Gspace, P.src_cells, P.forces)
+        u, it_f, _, code_f = dbi.ls_solve(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u0, tol=TOL,
+                                          max_iter=MAX_ITER, check_every=self.check_every)
+        r, phi = dbi.data_residual(P.grid, P.omega, P.fidx, P.rec_cells, u, d_obs)
+        g, (it_a, _, code_a) = dbi.adjoint_apply(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u, P.rec_cells, r,
+                                                 tol=TOL, max_iter=MAX_ITER, check_every=self.check_every,
+                                                 with_status=True)
+        return {"phi": phi, "g": g, "it_f": it_f, "it_a": it_a, "code_f": code_f, "code_a": code_a, "u": u, "r": r}
+
+    @staticmethod
+    def applies(out):
+        # two operator passes per BiCGSTAB iteration, plus the adjoint source's convolution
+        return int(2 * out["it_f"].sum().item() + 2 * out["it_a"].sum().item() + out["it_a"].numel())
+
+
+def timed_steps(step, m, d_obs, steps, warmup, dev, barrier, stage=None):
+    """warmup untimed steps, then `steps` steps between CUDA events on the launching stream; returns
+    (ms, applies, last output, launches, (stage ms, stage launches), clocks)."""
+    import torch
+    from paper_2402_02116_gb300 import dbi
+    for _ in range(warmup):
+        step(m, d_obs)
+    barrier()
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = dbi.kernel_launches()
+    if stage:
+        dbi.profile_begin(stage)
+    outs = []
+    with ClockSampler(gpu_id(dev)) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(steps):
+            outs.append(step(m, d_obs))
+        ev1.record(stream)
+        barrier()
+    prof = dbi.profile_end() if stage else (0.0, 0)
+    launches = dbi.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    applies = sum(GradientStep.applies(o) for o in outs)
+    return ms, applies, outs[-1], launches, prof, clk.summary()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
     from paper_2402_02116_gb300 import build, dbi
-    from paper_2402_02116_gb300.problem import DeviceProblem
+    from paper_2402_02116_gb300.shard import reduce_gradient
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -173,59 +259,25 @@ def run_ours(args):
     build.build()
     dbi.load()
 
-    w = workload(rank, world, args.sources)
-    P = DeviceProblem(w, dbi.C64, device=dev)
+    w = workload(args.workload, rank, world, args.sources)
+    step_fn = GradientStep(w, dev, args.check_every)
+    P = step_fn.P
     d_obs_host = synthetic_data(w, seed=7 + rank)
     d_obs = P.to_field(d_obs_host)
-    cells = w.nz * w.nx
+    cells = step_fn.cells
 
-    def step(m, d_obs):
-        Ghat, Gspace = dbi.greens_tabulate(P.grid, P.ref, P.omega, dbi.C64)
-        u0 = dbi.incident_field(P.grid, P.omega, P.fidx, Gspace, P.src_cells, P.forces)
-        u, it_f, _, code_f = dbi.ls_solve(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u0, tol=TOL,
-                                          max_iter=MAX_ITER, check_every=args.check_every)
-        r, phi = dbi.data_residual(P.grid, P.omega, P.fidx, P.rec_cells, u, d_obs)
-        g, (it_a, _, code_a) = dbi.adjoint_apply(P.grid, P.ref, m, P.omega, P.fidx, Ghat, u, P.rec_cells, r,
-                                                 tol=TOL, max_iter=MAX_ITER, check_every=args.check_every,
-                                                 with_status=True)
-        reduce_gradient(g, phi)  # sum over ranks (no-op on one GPU)
-        return phi, g, it_f, it_a, code_f, code_a
-
-    def applies(it_f, it_a):
-        # two operator passes per BiCGSTAB iteration, plus the adjoint source's convolution
-        return int(2 * it_f.sum().item() + 2 * it_a.sum().item() + it_a.numel())
+    def step(m, d):
+        out = step_fn(m, d)
+        reduce_gradient(out["g"], out["phi"])  # sum over ranks (no-op on one GPU)
+        return out
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up (untimed)
-    for _ in range(args.warmup):
-        out = step(P.m, d_obs)
-    barrier()
-    ok = bool((out[4] == dbi.CONVERGED).all().item() and (out[5] == dbi.CONVERGED).all().item())
-
-    # timed region: device events on the launching stream, barrier + synchronize on both sides
-    stream = torch.cuda.current_stream(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    total_applies = 0
-    launches0 = dbi.kernel_launches()
-    dbi.profile_begin(dbi.PROF_COLS)
-    with ClockSampler(gpu_id(dev)) as clk:
-        barrier()
-        ev0.record(stream)
-        per_step = []
-        for _ in range(args.steps):
-            phi, g, it_f, it_a, code_f, code_a = step(P.m, d_obs)
-            per_step.append((it_f, it_a))
-        ev1.record(stream)
-        barrier()
-    cols_ms, cols_launches = dbi.profile_end()
-    launches = dbi.kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
-    for it_f, it_a in per_step:
-        total_applies += applies(it_f, it_a)
+    ms, total_applies, last, launches, (cols_ms, cols_launches), clocks = timed_steps(
+        step, P.m, d_obs, args.steps, args.warmup, dev, barrier, stage=dbi.PROF_COLS)
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     a = torch.tensor([total_applies], dtype=torch.float64, device=dev)
     if world > 1:
@@ -234,63 +286,131 @@ def run_ours(args):
     ms_max = float(t.item())
     job_applies = float(a.item())
     value = job_applies * cells / (ms_max * 1e-3)
-    ok = ok and bool((code_f == dbi.CONVERGED).all().item() and (code_a == dbi.CONVERGED).all().item())
+    ok = bool((last["code_f"] == dbi.CONVERGED).all().item() and (last["code_a"] == dbi.CONVERGED).all().item())
 
     # roofline of the column-pass kernel (the largest share of the step's device time)
-    peaks = load_peaks()
-    rank_applies = total_applies
-    cols_algo_bytes = cols_bytes_per_cell_apply(w) * cells * rank_applies
-    cols_flops = cols_flops_per_cell_apply(w) * cells * rank_applies
-    cols_s = cols_ms * 1e-3
-    clocks = clk.summary()
-    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6  # FMA lanes x 2 flop x measured SM clock
-    hbm_peak = peaks.get("hbm_gbs", 6800.0) * 1e9
-    t_hbm, t_alu = cols_algo_bytes / hbm_peak, cols_flops / fp32_peak
-    if t_alu >= t_hbm:
-        roof = {"bound": "alu", "achieved": cols_flops / cols_s / 1e12, "peak": fp32_peak / 1e12,
-                "unit": "TFLOP/s", "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured median)"}
-    else:
-        roof = {"bound": "hbm", "achieved": cols_algo_bytes / cols_s / 1e9, "peak": hbm_peak / 1e9,
-                "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = "k_cols (column FFTs x Green's tensor x inverse column FFTs)"
-    # DRAM bytes per launch: null, because k_cols changed (its FFT line layout is now chosen per
-    # exchange) after its last ncu DRAM capture on these shapes; that capture is kept as context
-    roof["traffic"] = None
-    if (w.nz, w.nx, w.lz, w.lx) == (256, 256, 512, 512):
-        roof["traffic_note"] = ("null: k_cols changed after its last ncu DRAM capture, which gave "
-                                f"{COLS_DRAM_BYTES_PER_PROBLEM / 1e6:.2f} MB per problem (64-problem capture) "
-                                "against 4.39 MB algorithmic")
-    roof["hbm_frac_of_algorithmic_bytes"] = cols_algo_bytes / cols_s / hbm_peak
-    roof["launches_timed"] = cols_launches
-    roof["avg_launch_ms"] = cols_ms / max(cols_launches, 1)
-    roof["share_of_step_time"] = cols_ms / ms if ms > 0 else None
+    props = torch.cuda.get_device_properties(dev)
+    sms = int(props.multi_processor_count)
+    fp32 = fp32_peak_probe(dev, sms)
+    roof = column_roofline(w, cells * total_applies, cols_ms, cols_launches, ms, clocks, fp32, sms)
 
     # end to end through the public API with host buffers (copies inside the timed region)
-    e2e = run_e2e(args, P, step, d_obs_host, w, world, dev, barrier, applies)
+    e2e = run_e2e(args, P, step, d_obs_host, w, world, dev, barrier)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 (fp32 complex operator; fp64 inner products and scalars)",
-        "data": "synthetic (seeded VTI model with layers and anomalies; seeded observed data)",
+        "data": "synthetic (seeded VTI model and contrast; seeded observed data)",
         "config": config_dict(w, world),
         "roofline": roof, "e2e": e2e, "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps, "clocks": clocks,
         "all_converged": ok,
-        "krylov_iterations_per_step": {"forward_mean": float(per_step[-1][0].float().mean()),
-                                       "adjoint_mean": float(per_step[-1][1].float().mean())},
+        "krylov_iterations_per_step": {"forward_mean": float(last["it_f"].float().mean()),
+                                       "forward_max": int(last["it_f"].max()),
+                                       "adjoint_mean": float(last["it_a"].float().mean()),
+                                       "adjoint_max": int(last["it_a"].max())},
+        "device": {"name": props.name, "sms": sms},
     }
-    if rank == 0 and world == 1 and not args.no_plain:
+    solo = rank == 0 and world == 1
+    if solo and not args.no_cufft:
+        result["cufft_c64"] = cufft_comparator(P, w, dev)
+    if solo and not args.no_plain:
         result["plain_c128"] = plain_c128_sample(w, dev, cells, value)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = oracle_samples(w, [0, w.n_problems // 2 + 3, w.n_problems - 1])
+    if solo and args.workload == "vti512" and not args.no_secondary:
+        w2 = workload("vti256")
+        s2 = GradientStep(w2, dev, args.check_every)
+        d2 = s2.P.to_field(synthetic_data(w2))
+        ms2, ap2, last2, _, _, clk2 = timed_steps(s2, s2.P.m, d2, max(3, min(args.steps, 10)), 2, dev, barrier)
+        n2 = max(3, min(args.steps, 10))
+        result["vti256"] = {"value": ap2 * s2.cells / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2 / n2,
+                            "steps": n2, "config": config_dict(w2, 1), "clocks": clk2,
+                            "all_converged": bool((last2["code_f"] == dbi.CONVERGED).all().item()
+                                                  and (last2["code_a"] == dbi.CONVERGED).all().item())}
+        del s2, d2, last2
+    if solo and not (args.no_accuracy and args.no_cpu_baseline):
+        acc_problems = accuracy_problems(w)
+        acc_tasks = [] if args.no_accuracy else [(args.workload, args.sources, b) for b in acc_problems]
+        cores = args.cores or (os.cpu_count() or 1)
+        base_tasks = [] if args.no_cpu_baseline else baseline_tasks(args.workload, args.sources, w,
+                                                                    max(1, cores - len(acc_tasks)))
+        gpu_acc = None if args.no_accuracy else gpu_accuracy_side(P, last, acc_problems)
+        acc_res, base_res = run_oracle_pool(acc_tasks, base_tasks)
+        if acc_tasks:
+            result["accuracy"] = accuracy_block(w, gpu_acc, acc_res, d_obs_host)
+        if base_tasks:
+            result["cpu_baseline"] = merge_baseline(base_res)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def fp32_peak_probe(dev, sms, iters=1 << 16, reps=10):
+    """Measured FP32 FMA throughput (TFLOP/s): the library's FMA-only probe over 8 CTAs of 256
+    threads per SM (the resident maximum), best of `reps` launches timed with CUDA events on the
+    launching stream."""
+    import torch
+    from paper_2402_02116_gb300 import dbi
+    blocks = 8 * sms
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        dbi.fma_probe(blocks, iters, dev)
+    best = None
+    flops = 0
+    for _ in range(reps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        flops, _ = dbi.fma_probe(blocks, iters, dev)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1)
+        best = t if best is None else min(best, t)
+    return {"tflops": flops / (best * 1e-3) / 1e12, "ms": best, "blocks": blocks, "flops": flops,
+            "how": f"dbi_fma_probe: {blocks} CTAs x 256 threads x 8 FMA chains x {iters} steps, best of {reps}"}
+
+
+# DRAM bytes of one k_cols launch from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum):
+# (nz, nx, lz, lx) -> (problems in the captured launch, frequencies, bytes). The Green's spectra
+# [nf][3][lx][lz] are read once per launch; the rest grows with the problems a launch processes.
+COLS_DRAM = {}
+
+
+def column_roofline(w, cell_applies, cols_ms, cols_launches, step_ms, clocks, fp32, sms):
+    cols_algo_bytes = cols_bytes_per_cell_apply(w) * cell_applies
+    cols_flops = cols_flops_per_cell_apply(w) * cell_applies
+    cols_s = cols_ms * 1e-3
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0) * 1e9
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    nominal = sms * 128 * 2 * sm_mhz * 1e6
+    roof = {"bound": "alu", "achieved": cols_flops / cols_s / 1e12, "peak": fp32["tflops"], "unit": "TFLOP/s",
+            "peak_source": "measured: " + fp32["how"],
+            "peak_nominal": nominal / 1e12,
+            "peak_nominal_source": f"{sms} SMs (device query) x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled median)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["frac_of_nominal"] = roof["achieved"] / roof["peak_nominal"]
+    roof["kernel"] = "k_cols (column FFTs x Green's tensor x inverse column FFTs)"
+    roof["flops_per_cell_apply"] = cols_flops_per_cell_apply(w)
+    roof["algorithmic_bytes_per_cell_apply"] = cols_bytes_per_cell_apply(w)
+    per_launch_problems = cell_applies / (w.nz * w.nx) / max(cols_launches, 1)
+    cap = COLS_DRAM.get((w.nz, w.nx, w.lz, w.lx))
+    if cap:
+        nb, nf, byts = cap
+        tables = 3 * w.lz * w.lx * 8 * nf
+        roof["traffic"] = tables * w.nf / nf + (byts - tables) / nb * per_launch_problems
+        roof["traffic_source"] = (f"ncu capture of one k_cols launch over {nb} problems ({nf} frequencies): "
+                                  f"{byts / 1e6:.1f} MB, scaled to the {per_launch_problems:.0f} problems of an "
+                                  "average timed launch (the tables once per launch)")
+    else:
+        roof["traffic"] = None
+    roof["hbm_frac_of_algorithmic_bytes"] = cols_algo_bytes / cols_s / hbm_peak
+    roof["launches_timed"] = cols_launches
+    roof["avg_launch_ms"] = cols_ms / max(cols_launches, 1)
+    roof["avg_launch_problems"] = per_launch_problems
+    roof["share_of_step_time"] = cols_ms / step_ms if step_ms > 0 else None
+    return roof
 
 
 def gpu_id(dev):
@@ -304,9 +424,10 @@ def gpu_id(dev):
         return vis.split(",")[dev.index] if vis else str(dev.index)
 
 
-def run_e2e(args, P, step, d_obs_host, w, world, dev, barrier, applies):
+def run_e2e(args, P, step, d_obs_host, w, world, dev, barrier):
     """Same step, with the model and observed data copied from pinned host memory each step and
-    the gradient and misfit read back."""
+    the gradient and misfit read back. The public entry points (dbi.*) hand device pointers of
+    these copies to the C ABI."""
     import torch
     m_host = torch.as_tensor(np.asarray(w.model, dtype=np.float32)).pin_memory()
     d_host = torch.as_tensor(np.asarray(d_obs_host, dtype=np.complex64)).pin_memory()
@@ -318,24 +439,26 @@ def run_e2e(args, P, step, d_obs_host, w, world, dev, barrier, applies):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     ev0.record(stream)
-    its = []
+    total = 0
+    outs = []
     for _ in range(args.steps):
         m_dev.copy_(m_host, non_blocking=True)
         d_dev.copy_(d_host, non_blocking=True)
-        phi, g, it_f, it_a, _, _ = step(m_dev, d_dev)
-        g_host.copy_(g, non_blocking=True)
-        phi_host.copy_(phi, non_blocking=True)
-        its.append((it_f, it_a))
+        out = step(m_dev, d_dev)
+        g_host.copy_(out["g"], non_blocking=True)
+        phi_host.copy_(out["phi"], non_blocking=True)
+        outs.append((out["it_f"], out["it_a"]))
     ev1.record(stream)
     barrier()
-    total = sum(applies(it_f, it_a) for it_f, it_a in its)
+    total = sum(int(2 * f.sum() + 2 * a.sum() + a.numel()) for f, a in outs)
     ms = ev0.elapsed_time(ev1)
     cells = w.nz * w.nx
     h2d = m_host.numel() * 4 + d_host.numel() * 8
     d2h = g_host.numel() * 4 + 8
     return {"value": total * world * cells / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": ms / args.steps,
-            "api": "dbi.greens_tabulate/incident_field/ls_solve/data_residual/adjoint_apply"}
+            "api": "dbi.greens_tabulate/incident_field/ls_solve/data_residual/adjoint_apply (ctypes C ABI; the model "
+                   "and data are copied from pinned host memory to device tensors whose pointers the C ABI receives)"}
 
 
 def plain_c128_sample(w, dev, cells, value_c64):
@@ -370,6 +493,89 @@ def plain_c128_sample(w, dev, cells, value_c64):
             "ms_per_problem_gradient": tot_ms / len(sample),
             "est_ms_per_step": tot_ms / len(sample) * w.n_problems,
             "speedup_c64_batched": value_c64 / rate}
+
+
+def cufft_comparator(P, w, dev, reps=5):
+    """A cuFFT-based complex64 LS operator pass on the same batch, for comparison only (it is not
+    part of the library): the contrast source by the same central differences in torch
+    elementwise ops, zero padding and 2D FFTs by torch.fft (cuFFT), the symmetric 2 x 2 product
+    with the library's Green's spectra (transposed to row-major once, outside the timing), inverse
+    2D FFTs, crop, u - K u. Timed per pass with CUDA events beside the library's ls_apply on the
+    same input; the two outputs are compared."""
+    import torch
+    from paper_2402_02116_gb300 import dbi
+    nz, nx, lz, lx, h = w.nz, w.nx, w.lz, w.lx, w.h
+    nf, ns = w.nf, w.n_src
+    u = P.incident()
+    ref = torch.tensor(reference_values(w), dtype=torch.float32, device=dev)
+    dm = (P.m - ref[:, None, None]).contiguous()
+    w2 = (P.omega.to(torch.float32) ** 2)[P.fidx.long()].view(-1, 1, 1)
+    G = P.Ghat.transpose(-1, -2).contiguous().view(nf, 1, 3, lz, lx)  # [nf][1][3][lz][lx]
+    inv2h = 1.0 / (2.0 * h)
+
+    def d1(v):  # central difference along x, zero outside the grid
+        o = torch.zeros_like(v)
+        o[..., 1:-1] = v[..., 2:] - v[..., :-2]
+        o[..., 0] = v[..., 1]
+        o[..., -1] = -v[..., -2]
+        return o * inv2h
+
+    def d3(v):
+        o = torch.zeros_like(v)
+        o[..., 1:-1, :] = v[..., 2:, :] - v[..., :-2, :]
+        o[..., 0, :] = v[..., 1, :]
+        o[..., -1, :] = -v[..., -2, :]
+        return o * inv2h
+
+    def apply(u):
+        u1, u3 = u[:, 0], u[:, 1]
+        e1, e3, e5 = d1(u1), d3(u3), d3(u1) + d1(u3)
+        s1 = dm[1] * e1 + dm[2] * e3
+        s3 = dm[2] * e1 + dm[3] * e3
+        s5 = dm[4] * e5
+        src = torch.stack([w2 * dm[0] * u1 + d1(s1) + d3(s5), w2 * dm[0] * u3 + d1(s5) + d3(s3)], dim=1)
+        S = torch.fft.fft2(src, s=(lz, lx)).view(nf, ns, 2, lz, lx)
+        O = torch.stack([G[:, :, 0] * S[:, :, 0] + G[:, :, 1] * S[:, :, 1],
+                         G[:, :, 1] * S[:, :, 0] + G[:, :, 2] * S[:, :, 1]], dim=2)
+        o = torch.fft.ifft2(O.view(-1, 2, lz, lx), norm="forward")[..., :nz, :nx]
+        return u - o
+
+    stream = torch.cuda.current_stream(dev)
+
+    def time_it(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps, out
+
+    out_buf = torch.empty_like(u)
+    ms_lib, a_lib = time_it(lambda: dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u, out=out_buf))
+    a_lib = a_lib.clone()
+    ms_fft, a_fft = time_it(lambda: apply(u))
+    ms_fft_only, _ = time_it(lambda: torch.fft.ifft2(torch.fft.fft2(u, s=(lz, lx)), norm="forward"))
+    diff = float(torch.linalg.norm(a_fft - a_lib) / torch.linalg.norm(a_lib - u))
+    cells = nz * nx * P.B
+    del a_fft
+    torch.cuda.empty_cache()
+    return {"value": cells / (ms_fft * 1e-3), "unit": UNIT, "ms_per_pass": ms_fft,
+            "library_ls_apply": {"value": cells / (ms_lib * 1e-3), "ms_per_pass": ms_lib},
+            "cufft_transforms_only_ms": ms_fft_only,
+            "speedup_library_over_cufft": ms_fft / ms_lib,
+            "relative_difference_to_library": diff,
+            "what": "one operator pass over every problem: torch elementwise stencil + torch.fft.fft2/ifft2 (cuFFT, "
+                    f"{lz}x{lx}, 2 components) + 2x2 product; transforms_only = forward + inverse 2D FFTs of the field"}
+
+
+def reference_values(w):
+    """(rho, C11, C13, C33, C55) of the isotropic reference medium of a workload (Eq. 4)."""
+    a2, b2 = w.alpha0 ** 2, w.beta0 ** 2
+    return [w.rho0, w.rho0 * a2, w.rho0 * (a2 - 2 * b2), w.rho0 * a2, w.rho0 * b2]
 
 
 # ---------------------------------------------------------------------------------------------
@@ -407,39 +613,141 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------------------------------------
-# the FP64 CPU oracle on a bounded sample
+# the FP64 CPU oracle: accuracy of sampled problems and the CPU baseline, one process per core
 # ---------------------------------------------------------------------------------------------
-def oracle_samples(w, problems):
-    """oracle_sample over several problems, merged into one rate."""
-    res = [oracle_sample(w, b) for b in problems]
-    sec = sum(r["seconds"] for r in res)
-    applies = sum(r["value"] * r["seconds"] for r in res)
-    return {"value": applies / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": " | ".join(r["sample"] for r in res), "seconds": sec}
+def accuracy_problems(w):
+    """Problems whose wavefields, data and gradient the accuracy block compares with the FP64
+    oracle: the first source at the lowest frequency and the middle source at the highest."""
+    return [0, (w.nf - 1) * w.n_src + w.n_src // 2]
 
 
-def oracle_sample(w, problems=None):
-    """One gradient contribution (forward solve, residual, adjoint solve, imaging) of one problem
-    of the workload, by the FP64 CPU oracle as it stands (numpy, one core)."""
+def baseline_tasks(name, sources, w, n):
+    """n problems at the lowest frequency (distinct sources) for the oracle's CPU baseline: the
+    rate per cell-apply hardly depends on the frequency, and the lowest needs the fewest passes."""
+    return [(name, sources, int(k * w.n_src // n) % w.n_src) for k in range(n)]
+
+
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def run_oracle_pool(acc_tasks, base_tasks):
+    """Runs the oracle tasks in a pool of spawned processes (one core each), all at once."""
+    if not acc_tasks and not base_tasks:
+        return [], []
+    import multiprocessing as mp
+    _single_thread_env()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=len(acc_tasks) + len(base_tasks)) as pool:
+        acc = [pool.apply_async(_oracle_accuracy_task, (t,)) for t in acc_tasks]
+        base = [pool.apply_async(_oracle_gradient_task, (t,)) for t in base_tasks]
+        return [r.get() for r in acc], [r.get() for r in base]
+
+
+def _oracle_inputs(name, sources, b):
+    """Workload, problem b's frequency and source, and the inputs as the GPU reads them (model
+    rounded to float32, observed data to complex64), all from the seeded recipes."""
+    w = workload(name, 0, 1, sources)
+    f, s = int(w.problem_fidx()[b]), int(w.problem_src()[b])
+    model = np.asarray(w.model, dtype=np.float32).astype(np.float64)
+    d_obs = synthetic_data(w)[b].astype(np.complex128)
+    return w, f, s, model, d_obs
+
+
+def _oracle_accuracy_task(task):
+    """The FP64 oracle's solution of problem b to ORACLE_TOL: wavefield, receiver data, residual
+    and the problem's gradient contribution (adjoint solve to ORACLE_TOL, imaging)."""
     import oracle as O
-    b = w.n_problems // 2 + 3 if problems is None else problems
-    f = int(w.problem_fidx()[b])
-    s = int(w.problem_src()[b])
+    name, sources, b = task
+    w, f, s, model, d_obs = _oracle_inputs(name, sources, b)
+    t0 = time.perf_counter()
+    orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
+    u, info_f = orc.solve_info(orc.incident(0, w.src_cells[s], w.src_force[s]), model, 0, tol=ORACLE_TOL)
+    d = orc.sample(u, w.rec_cells)
+    r = d - d_obs
+    ua, info_a = orc.solve_info(orc.convolve(orc.inject(np.conj(r), w.rec_cells), 0), model, 0, tol=ORACLE_TOL)
+    g = orc.imaging(ua, u, orc.omegas[0], orc.h)
+    return {"b": b, "u": u, "d": d, "r": r, "g": g, "iters": (info_f["iters"], info_a["iters"]),
+            "relres": (info_f["relres"], info_a["relres"]), "seconds": time.perf_counter() - t0,
+            "freq_hz": float(w.freqs_hz[f]), "source": s}
+
+
+def _oracle_gradient_task(task):
+    """One problem's gradient contribution (forward solve, residual, adjoint solve, imaging) by the
+    FP64 oracle as it stands, at the benchmark's tolerance; returns its operator passes and time."""
+    import oracle as O
+    name, sources, b = task
+    w, f, s, model, d_obs = _oracle_inputs(name, sources, b)
     t0 = time.perf_counter()
     orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
     u0 = orc.incident(0, w.src_cells[s], w.src_force[s])
-    u, info_f = orc.solve_info(u0, w.model, 0, tol=TOL)
-    r = orc.sample(u, w.rec_cells) - synthetic_data(w)[b]
-    q = orc.inject(np.conj(r), w.rec_cells)
-    ua, info_a = orc.solve_info(orc.convolve(q, 0), w.model, 0, tol=TOL)
+    u, info_f = orc.solve_info(u0, model, 0, tol=TOL)
+    r = orc.sample(u, w.rec_cells) - d_obs
+    ua, info_a = orc.solve_info(orc.convolve(orc.inject(np.conj(r), w.rec_cells), 0), model, 0, tol=TOL)
     orc.imaging(ua, u, orc.omegas[0], orc.h)
     dt = time.perf_counter() - t0
     # the oracle's solve_info applies A once more to report the true residual
-    applies = 2 * info_f["iters"] + 1 + 2 * info_a["iters"] + 1 + 1
-    return {"value": applies * w.nz * w.nx / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"problem {b} (source {s}, {w.freqs_hz[f]:.2f} Hz) of {w.name}: forward solve, residual, "
-                      f"adjoint solve, imaging; {applies} operator passes in {dt:.1f} s",
-            "seconds": dt}
+    passes = 2 * info_f["iters"] + 1 + 2 * info_a["iters"] + 1 + 1
+    return {"passes": passes, "cells": w.nz * w.nx, "seconds": dt,
+            "sample": f"problem {b} (source {s}, {w.freqs_hz[f]:.2f} Hz): {passes} passes in {dt:.1f} s"}
+
+
+def merge_baseline(res):
+    """Aggregate rate of oracle tasks that ran at the same time, one per process and core: all
+    their cell-applies over the longest task's time."""
+    applies = sum(r["passes"] * r["cells"] for r in res)
+    wall = max(r["seconds"] for r in res)
+    return {"value": applies / wall, "unit": UNIT, "cores": len(res), "kind": "oracle",
+            "sample": f"{len(res)} processes at once (one host core each), each one problem's gradient contribution "
+                      "(forward solve, residual, adjoint solve, imaging) by the FP64 numpy oracle; "
+                      + "; ".join(r["sample"] for r in res[:3]) + ("; ..." if len(res) > 3 else ""),
+            "seconds": wall, "host_cpu_count": os.cpu_count()}
+
+
+def gpu_accuracy_side(P, last, problems):
+    """GPU values of the sampled problems from the last timed step (wavefield, residual), and the
+    gradient of the sub-batch of those problems by one more adjoint_apply at the benchmark's
+    tolerance."""
+    import torch
+    from paper_2402_02116_gb300 import dbi
+    idx = torch.tensor(problems, dtype=torch.long, device=P.device)
+    u = last["u"].index_select(0, idx).contiguous()
+    r = last["r"].index_select(0, idx).contiguous()
+    fidx = P.fidx.index_select(0, idx).contiguous()
+    g = dbi.adjoint_apply(P.grid, P.ref, P.m, P.omega, fidx, P.Ghat, u, P.rec_cells, r, tol=TOL, max_iter=MAX_ITER)
+    torch.cuda.synchronize()
+    return {"u": u.cpu().numpy().astype(np.complex128), "r": r.cpu().numpy().astype(np.complex128),
+            "g": g.cpu().numpy().astype(np.float64)}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def accuracy_block(w, gpu, res, d_obs_host):
+    """Relative L2 errors against the FP64 oracle (solved to ORACLE_TOL): every sampled problem's
+    wavefield, receiver data (P u) and data residual, and the sub-batch gradient per parameter."""
+    per = []
+    g_or = np.zeros_like(gpu["g"])
+    for k, r in enumerate(res):
+        d_gpu = gpu["r"][k] + d_obs_host[r["b"]].astype(np.complex128)
+        per.append({"problem": r["b"], "source": r["source"], "freq_hz": r["freq_hz"],
+                    "wavefield": _rel(gpu["u"][k], r["u"]), "data": _rel(d_gpu, r["d"]),
+                    "residual": _rel(gpu["r"][k], r["r"]),
+                    "oracle_iters": r["iters"], "oracle_relres": r["relres"], "oracle_seconds": r["seconds"]})
+        g_or += r["g"]
+    grad = {p: _rel(gpu["g"][i], g_or[i]) for i, p in enumerate(inputs.PARAMS)}
+    return {"reference": f"FP64 numpy oracle, BiCGSTAB to {ORACLE_TOL:g} (same seeded inputs: model rounded to "
+                         "float32, observed data to complex64, as the GPU reads them)",
+            "gpu": f"complex64 BiCGSTAB to {TOL:g} (the timed step's last solutions; the gradient by adjoint_apply "
+                   "on the sub-batch of the sampled problems)",
+            "problems": per,
+            "wavefield_max": max(p["wavefield"] for p in per), "data_max": max(p["data"] for p in per),
+            "residual_max": max(p["residual"] for p in per),
+            "gradient_subbatch": grad, "gradient_max": max(grad.values()),
+            "gradient_all": _rel(gpu["g"], g_or),
+            "tolerances": {"wavefield": 1e-5, "data": 1e-5, "residual": 1e-5, "gradient": 1e-4}}
 
 
 def _oracle_rate(passes, cells, dt, sample):
@@ -526,31 +834,62 @@ def oracle_uneven_sample(ws):
                       + "), weighted by each size's cells in the batch", "seconds": seconds}
 
 
+_REF_CACHE = {}
+
+
+def _oracle_passes_task(task):
+    """Reference-arm step of one process: `passes` LS-operator passes (the oracle's `apply`) on
+    problem b's incident field; the oracle's tables for the problem's frequency are built once per
+    process (in the warm-up)."""
+    import oracle as O
+    name, sources, b, passes = task
+    w, f, s, model, _ = _oracle_inputs(name, sources, b)
+    key = (name, sources, f)
+    if key not in _REF_CACHE:
+        _REF_CACHE.clear()
+        orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
+        _REF_CACHE[key] = (orc, orc.incident(0, w.src_cells[s], w.src_force[s]))
+    orc, u = _REF_CACHE[key]
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        u = orc.apply(u, model, 0)
+    return {"passes": passes, "cells": w.nz * w.nx, "seconds": time.perf_counter() - t0}
+
+
 def run_reference(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
+    """The FP64 CPU oracle as it stands on the host cores: one process per core, each step every
+    process runs two LS-operator passes (one BiCGSTAB iteration's worth) on its own problem of the
+    workload (lowest frequency, distinct sources); warm-up steps build the oracle's tables."""
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    w = workload(0, 1)
-    # each step is one problem's gradient contribution (a bounded sample of the batch)
-    problems = [w.n_problems // 2 + 3, 0, w.n_problems - 1]
-    if args.warmup > 0:  # one untimed sample warms numpy/scipy; more would only add minutes
-        oracle_sample(w, problems[0])
+    import multiprocessing as mp
+    name = args.workload if args.workload in ("vti512", "vti256") else "vti512"
+    w = workload(name, 0, 1, args.sources)
+    cores = args.cores or (os.cpu_count() or 1)
+    tasks = [(name, args.sources, int(k * w.n_src // cores) % w.n_src, 2) for k in range(cores)]
+    _single_thread_env()
+    ctx = mp.get_context("spawn")
     t_applies, t_sec = 0.0, 0.0
-    samples = []
-    for k in range(args.steps):
-        res = oracle_sample(w, problems[k % len(problems)])
-        t_applies += res["value"] * res["seconds"]
-        t_sec += res["seconds"]
-        samples.append(res["sample"])
+    with ctx.Pool(processes=cores) as pool:
+        for _ in range(max(args.warmup, 1)):  # the first builds every process's tables
+            pool.map(_oracle_passes_task, [(n, so, b, 1) for n, so, b, _ in tasks], chunksize=1)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_passes_task, tasks, chunksize=1)
+            t_sec += time.perf_counter() - t0
+            t_applies += sum(r["passes"] * r["cells"] for r in res)
     value = t_applies / t_sec
+    sample = (f"{cores} processes at once (one host core each), each step 2 LS-operator passes per process on its own "
+              f"problem of {w.name} (lowest frequency, distinct sources) by the FP64 numpy oracle's apply; step time = "
+              "wall time of the slowest process")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_sec / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_sec / max(args.steps, 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)",
             "data": "synthetic", "config": config_dict(w, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                             "sample": "one problem's gradient contribution per step (FP64 numpy oracle): "
-                                       + "; ".join(samples[:3])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores, "sample": sample,
+                             "host_cpu_count": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -664,7 +1003,7 @@ def run_formk(args):
     torch.cuda.set_device(dev)
     build.build()
     dbi.load()
-    w = workload(0, 1, args.sources)
+    w = workload("vti256", 0, 1, args.sources)
     P = DeviceProblem(w, dbi.C64, device=dev)
     u = P.incident()
     out = torch.empty_like(u)
@@ -748,7 +1087,7 @@ def run_gmres(args):
     torch.cuda.set_device(dev)
     build.build()
     dbi.load()
-    w = workload(0, 1, args.sources)
+    w = workload("vti256", 0, 1, args.sources)
     P = DeviceProblem(w, dbi.C64, device=dev)
     u0 = P.incident()
     cells = w.nz * w.nx

@@ -49,7 +49,11 @@ enum dbi_code {
   DBI_ERR_CUDA = -4         /* a CUDA launch or copy failed; the message names it */
 };
 
-enum dbi_problem_code { DBI_CONVERGED = 0, DBI_NOT_CONVERGED = 1, DBI_BREAKDOWN = 2 };
+/* Per-problem outcome of a Krylov solve. DBI_BREAKDOWN: the last BiCGSTAB step broke down and the
+ * problem restarted from its iterate (a later step overwrites it). DBI_NONFINITE: a NaN or an
+ * infinity appeared in the right-hand side, the model or an inner product; the problem stopped at
+ * once (its iterate is not meaningful). */
+enum dbi_problem_code { DBI_CONVERGED = 0, DBI_NOT_CONVERGED = 1, DBI_BREAKDOWN = 2, DBI_NONFINITE = 3 };
 
 enum dbi_op {
   DBI_OP_GREENS = 0,
@@ -414,6 +418,15 @@ size_t dbi_noalloc_scratch_bytes(void);
 unsigned long long dbi_kernel_launches(void);
 int dbi_profile_begin(int stage);
 int dbi_profile_end(double *total_ms, long long *launches);
+
+/*
+ * dbi_fma_probe -- launch `blocks` CTAs of 256 threads that issue nothing but FP32 fused
+ *   multiply-adds (8 independent chains per thread, `iters` steps each) on `stream`, to measure
+ *   the FP32 arithmetic peak that bounds the FFT-bound operator kernels (time it with events on the
+ *   same stream). out: device float[blocks * 256], written (the chains' sums). Returns the number
+ *   of floating-point operations launched (2 per FMA), or a negative dbi_code.
+ */
+long long dbi_fma_probe(int blocks, int iters, float *out, dbi_stream stream);
 
 #ifdef __cplusplus
 }

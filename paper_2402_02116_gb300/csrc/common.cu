@@ -169,6 +169,14 @@ int imaging_chunks(int B) { return B < 16 ? (B > 0 ? B : 1) : 16; }
 
 using namespace dbi;
 
+namespace dbi {
+int Arena::check(const char *who) const {
+  if (!overflow) return DBI_OK;
+  set_error("%s: the work buffer of %zu bytes is too small for the buffers carved from it", who, cap);
+  return DBI_ERR_WORKSPACE;
+}
+}  // namespace dbi
+
 extern "C" const char *dbi_last_error(void) { return g_err; }
 
 extern "C" int dbi_version(void) { return 100; }

@@ -84,17 +84,27 @@ int check_precision(int precision);
 // Twiddle table W_3072^m, m in [0, 3072), in the precision's complex type (written into `tw`).
 int launch_twiddles(void *tw, int precision, cudaStream_t s);
 
-// A bump allocator over the caller's work buffer.
+// A bump allocator over the caller's work buffer. A carve that does not fit (or a missing buffer)
+// returns nullptr and sets `overflow` for good; every entry point calls check() after its last
+// carve and before its first launch, so no kernel is ever handed a pointer outside the buffer.
 struct Arena {
   char *base;
   size_t cap;
   size_t used = 0;
+  bool overflow = false;
   Arena(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
   void *take(size_t n) {
-    size_t off = used;
-    used += align256(n);
-    return (base && used <= cap) ? base + off : nullptr;
+    const size_t off = used, a = align256(n);
+    if (overflow || !base || a < n || off + a < off || off + a > cap) {
+      overflow = true;
+      used = cap;
+      return nullptr;
+    }
+    used = off + a;
+    return base + off;
   }
+  // DBI_OK, or DBI_ERR_WORKSPACE with a message naming `who` after a carve past the buffer.
+  int check(const char *who) const;
 };
 
 // Sizes of the buffers each operation carves out of the work buffer (see workspace.cu).

@@ -386,6 +386,7 @@ extern "C" int ls_apply_k(const dbi_model *model, const dbi_batch *batch, const 
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral_k(g, batch->B, precision));
   Scales sc = carve_scales(ar, batch->B);
+  if ((rc = ar.check("ls_apply_k"))) return rc;
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   if ((rc = pow2_scales(u, precision, false, batch->B, size_t(2) * g->nz * g->nx, sc.part, sc.scale, sc.inv,
                         nullptr, s)))
@@ -408,6 +409,7 @@ extern "C" int ls_solve_k(const dbi_model *model, const dbi_batch *batch, const 
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral_k(g, batch->B, precision));
   SolverBufs sb = carve_solver(ar, g, batch->B, precision);
+  if ((rc = ar.check("ls_solve_k"))) return rc;
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   OpArgs a = k_args(model, batch, Ghat, Dhat, precision, T, tw);
   return run_bicgstab(a, sb, rhs, u, opts->zero_guess != 0, *opts, status, s, true);

@@ -147,7 +147,9 @@ __global__ void k_gm_begin(GState *st, int *active, double2 *g, const double *pa
   k.res = beta;
   k.k = 0;
   int act = 0;
-  if (k.zero_rhs || s[1] <= tol * tol * k.bnorm2) {
+  if (!finite_value(k.bnorm2) || !finite_value(s[1])) {  // NaN or infinity in the data, the model or the iterate
+    k.code = DBI_NONFINITE;
+  } else if (k.zero_rhs || s[1] <= tol * tol * k.bnorm2) {
     k.code = DBI_CONVERGED;
   } else if (k.iters >= max_iter) {
     k.code = DBI_NOT_CONVERGED;
@@ -342,7 +344,10 @@ __global__ void k_gm_close(const int *plist, int *active, GState *st, double2 *H
   k.k = j + 1;
   k.hn_inv = hn > 0.0 ? -1.0 / hn : 0.0;  // v_(j+1) = (A v_j - sum H_ij v_i) / hn = -w' / hn
   int act = 1;
-  if (k.res <= tol * sqrt(k.bnorm2) || hn <= 1e-14 * t) {
+  if (!finite_value(k.res) || !finite_value(hn)) {
+    k.code = DBI_NONFINITE;
+    act = 0;
+  } else if (k.res <= tol * sqrt(k.bnorm2) || hn <= 1e-14 * t) {
     k.code = DBI_CONVERGED;
     act = 0;
   } else if (k.iters >= max_iter) {
@@ -522,6 +527,8 @@ static int gmres_typed(OpArgs op, const GmresBufs &gb, int m, const void *rhs_, 
 int run_gmres(const OpArgs &op, Arena &ar, size_t field_bytes, int m, const void *rhs, void *x, bool x_zero,
               const dbi_krylov_opts &o, const dbi_status *status, cudaStream_t s) {
   const GmresBufs gb = carve_gmres(ar, field_bytes, op.B, m);
+  const int rc = ar.check("GMRES");
+  if (rc) return rc;
   return op.precision == DBI_C64 ? gmres_typed<float2>(op, gb, m, rhs, x, x_zero, o, status, s)
                                  : gmres_typed<double2>(op, gb, m, rhs, x, x_zero, o, status, s);
 }
@@ -563,6 +570,7 @@ extern "C" int ls_solve_gmres(const dbi_model *model, const dbi_batch *batch, co
   Arena ar(work, work_bytes);
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral(g, batch->B, precision));
+  if ((rc = ar.check("ls_solve_gmres"))) return rc;
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   OpArgs a{};
   a.precision = precision; a.nz = g->nz; a.nx = g->nx; a.lz = g->lz; a.lx = g->lx; a.h = g->h;

@@ -292,6 +292,7 @@ extern "C" int greens_tabulate_k(const dbi_grid *g, const dbi_medium *ref, const
   double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
   const size_t tab = size_t(nf) * 6 * g->lz * g->lx;
   double2 *W = static_cast<double2 *>(ar.take(tab * sizeof(double2)));
+  if ((rc = ar.check("greens_tabulate_k"))) return rc;
   if ((rc = launch_twiddles(tw, DBI_C128, s))) return rc;
   cudaError_t e = cudaMemsetAsync(W, 0, tab * sizeof(double2), s);
   if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(derivative table)", e);
@@ -340,6 +341,7 @@ extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const d
   Arena ar(work, work_bytes);
   double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
   double2 *W = static_cast<double2 *>(ar.take(size_t(nf) * 3 * g->lz * g->lx * sizeof(double2)));
+  if ((rc = ar.check("greens_tabulate"))) return rc;
   if ((rc = launch_twiddles(tw, DBI_C128, s))) return rc;
   const size_t tab = size_t(nf) * 3 * g->lz * g->lx;
   cudaError_t e = cudaMemsetAsync(W, 0, tab * sizeof(double2), s);

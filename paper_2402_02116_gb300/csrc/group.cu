@@ -244,6 +244,7 @@ extern "C" int dbi_group_bind(dbi_group *g, void *work, size_t work_bytes, int o
   g->T = ar.take(size_t(g->T_elems) * csize(g->precision));
   g->sc = carve_scales(ar, g->B);
   if (op == DBI_OP_SOLVE) g->sb = carve_solver_fields(ar, size_t(g->field_elems) * csize(g->precision), g->B);
+  if (const int crc = ar.check("dbi_group_bind")) return crc;
   cudaError_t e = cudaMemcpyAsync(g->d_desc, g->desc.data(), g->desc.size() * sizeof(GMember),
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)

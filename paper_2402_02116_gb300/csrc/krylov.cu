@@ -98,10 +98,11 @@ __global__ void k_init_state(KState *st, int *active, int *counters, const doubl
     k.beta_re = 0.0; k.beta_im = 0.0;  // p = r on the first iteration (p = v = 0)
     k.rhatnorm2 = s[1];
     k.zero_rhs = s[0] == 0.0;
-    const bool conv = k.zero_rhs || s[1] <= tol * tol * s[0];
-    k.code = conv ? DBI_CONVERGED : DBI_NOT_CONVERGED;
+    const bool bad = !finite_value(s[0]) || !finite_value(s[1]);  // NaN or infinity in the right-hand side or x0
+    const bool conv = !bad && (k.zero_rhs || s[1] <= tol * tol * s[0]);
+    k.code = bad ? DBI_NONFINITE : conv ? DBI_CONVERGED : DBI_NOT_CONVERGED;
     st[b] = k;
-    const int act = (!conv && max_iter > 0) ? 1 : 0;
+    const int act = (!bad && !conv && max_iter > 0) ? 1 : 0;
     active[b] = act;
     atomicAdd(&counters[1], act);
   }
@@ -210,7 +211,8 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(Span sp, const int *p
   block_sum_store<3>(acc, partC + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
 
-// Convergence test, breakdown restart and beta for the next iteration (one CTA per problem).
+// Convergence test, breakdown restart and beta for the next iteration (one CTA per problem;
+// the decision itself is bicgstab_decide in krylov.cuh).
 __global__ void k_check(const int *plist, KState *st, int *active, int *counters, int parity,
                         const double *partC, double tol, int max_iter) {
   const int b = problem_at(plist, blockIdx.x);
@@ -219,39 +221,7 @@ __global__ void k_check(const int *plist, KState *st, int *active, int *counters
   gather_n<3>(partC + size_t(b) * kRedBlocks * kRedSlots, kRedBlocks, q);
   if (threadIdx.x != 0) return;
   KState k = st[b];
-  k.iters += 1;
-  k.rnorm2 = q[2];
-  k.restart = 0;
-  const bool conv = k.half || q[2] <= tol * tol * k.bnorm2;
-  int act = 1;
-  if (conv) {
-    k.code = DBI_CONVERGED;
-    act = 0;
-  } else if (k.iters >= max_iter) {
-    k.code = DBI_NOT_CONVERGED;
-    act = 0;
-  } else {
-    const double2 rho_new = make_double2(q[0], q[1]);
-    const double rho_abs = sqrt(rho_new.x * rho_new.x + rho_new.y * rho_new.y);
-    const bool om_zero = k.om_re == 0.0 && k.om_im == 0.0;
-    const bool breakdown = om_zero || rho_abs <= 1e-14 * sqrt(k.rhatnorm2 * q[2]);
-    if (breakdown) {  // restart: rhat := r, p := r, so <rhat, r> = ||r||^2
-      k.restart = 1;
-      k.code = DBI_BREAKDOWN;
-      k.rho_re = q[2]; k.rho_im = 0.0;
-      k.alpha_re = 1.0; k.alpha_im = 0.0;
-      k.om_re = 1.0; k.om_im = 0.0;
-      k.beta_re = 0.0; k.beta_im = 0.0;
-      k.rhatnorm2 = q[2];
-    } else {
-      const double2 rho = make_double2(k.rho_re, k.rho_im);
-      const double2 beta = zmul(zdiv(rho_new, rho),
-                                zdiv(make_double2(k.alpha_re, k.alpha_im), make_double2(k.om_re, k.om_im)));
-      k.rho_re = rho_new.x; k.rho_im = rho_new.y;
-      k.beta_re = beta.x; k.beta_im = beta.y;
-      k.code = DBI_NOT_CONVERGED;
-    }
-  }
+  const int act = bicgstab_decide(k, q, tol, max_iter);
   st[b] = k;
   active[b] = act;
   atomicAdd(&counters[parity], act);
@@ -540,6 +510,7 @@ extern "C" int ls_solve(const dbi_model *model, const dbi_batch *batch, const vo
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral(g, batch->B, precision));
   SolverBufs sb = carve_solver(ar, g, batch->B, precision);
+  if ((rc = ar.check("ls_solve"))) return rc;
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   OpArgs a{};
   a.precision = precision; a.nz = g->nz; a.nx = g->nx; a.lz = g->lz; a.lx = g->lx; a.h = g->h;

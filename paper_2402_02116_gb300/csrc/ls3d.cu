@@ -732,6 +732,7 @@ extern "C" int greens_tabulate_3d(const dbi_grid3 *g, const dbi_medium *ref, con
   double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
   const size_t vol = size_t(g->lz) * g->ly * g->lx, tab = size_t(nf) * 6 * vol;
   double2 *W = static_cast<double2 *>(ar.take(tab * sizeof(double2)));
+  if ((rc = ar.check("greens_tabulate_3d"))) return rc;
   if ((rc = launch_twiddles(tw, DBI_C128, s))) return rc;
   cudaError_t e = cudaMemsetAsync(W, 0, tab * sizeof(double2), s);
   if (e == cudaSuccess && Gspace) e = cudaMemsetAsync(Gspace, 0, tab * csize3(precision), s);
@@ -826,6 +827,7 @@ extern "C" int ls_apply_3d(const dbi_model3 *model, const dbi_batch *batch, cons
   void *T = ar.take(bytes_spec3(g, batch->B, precision));
   void *T2 = ar.take(bytes_sig3(g, batch->B, precision));
   Scales sc = carve_scales(ar, batch->B);
+  if ((rc = ar.check("ls_apply_3d"))) return rc;
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   const size_t n = size_t(3) * g->nz * g->ny * g->nx;
   if ((rc = pow2_scales(u, precision, false, batch->B, n, sc.part, sc.scale, sc.inv, nullptr, s))) return rc;
@@ -859,6 +861,7 @@ extern "C" int ls_solve_3d(const dbi_model3 *model, const dbi_batch *batch, cons
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spec3(g, batch->B, precision));
   void *T2 = ar.take(bytes_sig3(g, batch->B, precision));
+  if ((rc = ar.check("ls_solve_3d"))) return rc;
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   OpArgs a = args3(model, batch, Ghat, precision, T, T2, tw);
   return run_gmres(a, ar, bytes_field3(g, batch->B, precision), restart, rhs, u, opts->zero_guess != 0, *opts,
@@ -1080,6 +1083,7 @@ static int prepare3(const dbi_model3 *bg, const dbi_batch *batch, const void *Gh
   c.sol = ar.take(c.fbytes);
   c.gm_bytes = gmres_bytes_fields(c.fbytes, batch->B, restart);
   c.gm_base = ar.take(c.gm_bytes);
+  if ((rc = ar.check("3D products"))) return rc;
   if ((rc = launch_twiddles(tw, precision, c.s))) return rc;
   c.op = args3(bg, batch, Ghat, precision, T, T2, tw);
   return DBI_OK;
@@ -1179,6 +1183,7 @@ extern "C" int normal_cg_3d(const dbi_model3 *background, const dbi_batch *batch
   double *sc = static_cast<double *>(ar.take(16 * sizeof(double)));
   double *hist = static_cast<double *>(ar.take(size_t(cg->iters + 1) * sizeof(double)));
   void *dvec = ar.take(size_t(batch->B) * n_rec * 3 * (precision == DBI_C64 ? sizeof(float2) : sizeof(double2)));
+  if ((rc = ar.check("normal_cg_3d"))) return rc;
   cudaStream_t s = c.s;
   const dbi_medium &m0 = background->ref;
   const double a2 = m0.rho0 * m0.alpha0 * m0.alpha0, b2 = m0.rho0 * m0.beta0 * m0.beta0;

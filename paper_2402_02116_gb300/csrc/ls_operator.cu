@@ -249,6 +249,7 @@ extern "C" int green_convolve(const dbi_grid *g, const dbi_batch *batch, const v
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral(g, batch->B, precision));
   Scales sc = carve_scales(ar, batch->B);
+  if ((rc = ar.check(__func__))) return rc;
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   if ((rc = pow2_scales(src, precision, false, batch->B, size_t(2) * g->nz * g->nx, sc.part, sc.scale, sc.inv,
                         nullptr, s)))
@@ -275,6 +276,7 @@ extern "C" int ls_apply(const dbi_model *model, const dbi_batch *batch, const vo
   void *tw = ar.take(bytes_twiddles(precision));
   void *T = ar.take(bytes_spectral(g, batch->B, precision));
   Scales sc = carve_scales(ar, batch->B);
+  if ((rc = ar.check(__func__))) return rc;
   if ((rc = launch_twiddles(tw, precision, s))) return rc;
   if ((rc = pow2_scales(u, precision, false, batch->B, size_t(2) * g->nz * g->nx, sc.part, sc.scale, sc.inv,
                         nullptr, s)))

@@ -302,6 +302,7 @@ static int prepare(ProdCtx &c, Arena &ar, const dbi_model *bg, const dbi_batch *
   c.img = static_cast<double *>(ar.take(size_t(imaging_chunks(batch->B)) * 5 * c.g->nz * c.g->nx * sizeof(double)));
   c.opts = *opts;
   c.status = status;
+  if (const int rc = ar.check("distorted-Born products")) return rc;
   return launch_twiddles(const_cast<void *>(c.tw), precision, c.s);
 }
 
@@ -416,6 +417,7 @@ extern "C" int normal_cg(const dbi_model *background, const dbi_batch *batch, co
   double *sc = static_cast<double *>(ar.take(16 * sizeof(double)));
   double *hist = static_cast<double *>(ar.take(size_t(cg->iters + 1) * sizeof(double)));
   void *dvec = ar.take(size_t(batch->B) * g->nz * g->nx * 2 * (precision == DBI_C64 ? sizeof(float2) : sizeof(double2)));
+  if ((rc = ar.check("normal_cg"))) return rc;
   cudaStream_t s = c.s;
   double rv[5];
   reference_values(background->ref, rv);

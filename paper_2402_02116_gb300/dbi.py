@@ -22,7 +22,7 @@ from . import build as _build
 C64, C128 = 0, 1
 OP_GREENS, OP_CONVOLVE, OP_APPLY, OP_SOLVE, OP_FRECHET, OP_ADJOINT, OP_NORMAL_CG = range(7)
 OP_GREENS_K, OP_APPLY_K, OP_SOLVE_K = 7, 8, 9
-CONVERGED, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+CONVERGED, NOT_CONVERGED, BREAKDOWN, NONFINITE = 0, 1, 2, 3
 
 
 class DBIError(RuntimeError):
@@ -91,6 +91,7 @@ SIGNATURES = {
     "dbi_kernel_launches": (ctypes.c_ulonglong, []),
     "dbi_profile_begin": (c_int, [c_int]),
     "dbi_profile_end": (c_int, [POINTER(c_double), POINTER(ctypes.c_longlong)]),
+    "dbi_fma_probe": (ctypes.c_longlong, [c_int, c_int, c_void_p, c_void_p]),
     "greens_tabulate": (c_int, [POINTER(Grid), POINTER(Medium), c_void_p, c_int, c_int, c_void_p,
                                 c_void_p, c_void_p, c_size_t, c_void_p]),
     "incident_field": (c_int, [POINTER(Grid), POINTER(Batch), c_void_p, c_void_p, c_void_p, c_void_p,
@@ -218,15 +219,45 @@ def _need_cuda(*ts):
             raise DBIError("every tensor must be a contiguous CUDA tensor")
 
 
-def _fields(fidx, comps: int, cells: int, **named):
-    """Every field argument holds one [comps][cells] block per problem (B = the length of fidx),
-    which the kernels index from its first element: a tensor of another size would be read or
-    written past its end."""
+def _fields(fidx, comps: int, cells: int, dtype, **named) -> list:
+    """Every field argument is a tensor of the call's complex dtype holding one [comps][cells] block
+    per problem (B = the length of fidx), which the kernels index from its first element: a tensor
+    of another size or element type would be read or written past its end. Returns the tensors,
+    which the caller then passes to _need_cuda with the others (a host tensor would hand the kernels
+    a host address): every size and dtype is checked before any device."""
     B = int(fidx.numel())
-    for name, t in named.items():
-        if t is not None and t.numel() != B * comps * cells:
+    ts = {k: t for k, t in named.items() if t is not None}
+    for name, t in ts.items():
+        if not isinstance(t, torch.Tensor):
+            raise DBIError(f"{name} must be a torch tensor")
+        if t.numel() != B * comps * cells:
             raise DBIError(f"{name} holds {t.numel()} elements; {B} problems x {comps} components x "
                            f"{cells} cells need {B * comps * cells}")
+    for name, t in ts.items():
+        if t.dtype != dtype:
+            raise DBIError(f"{name} is {t.dtype}; this call needs {dtype}")
+    return list(ts.values())
+
+
+def _checked(name, t, n: int, dtype, what: str):
+    if not isinstance(t, torch.Tensor):
+        raise DBIError(f"{name} must be a torch tensor")
+    if t.numel() != n:
+        raise DBIError(f"{name} holds {t.numel()} elements; {what} need {n}")
+    if t.dtype != dtype:
+        raise DBIError(f"{name} is {t.dtype}; this call needs {dtype}")
+
+
+def _table(name, t, nf: int, comps: int, cells: int, dtype):
+    """A Green's table argument (Ghat, Dhat, Gspace): a tensor of the call's complex dtype with
+    nf x comps x cells elements (cells = the FFT grid's points); the caller checks the device."""
+    _checked(name, t, nf * comps * cells, dtype, f"{nf} frequencies x {comps} components x {cells} FFT-grid points")
+
+
+def _real(name, t, n: int, dtype):
+    """A real per-cell argument (a model perturbation, a CG start): dtype and n elements; the caller
+    checks the device."""
+    _checked(name, t, n, dtype, "the parameters x cells")
 
 
 def make_grid(nz, nx, lz, lx, h) -> Grid:
@@ -308,6 +339,15 @@ def profile_begin(stage: int):
     _check(load().dbi_profile_begin(int(stage)), "dbi_profile_begin")
 
 
+def fma_probe(blocks: int, iters: int, device) -> tuple:
+    """Launch the FP32 FMA probe on the current stream of `device`; returns (flops, output tensor)."""
+    out = torch.empty(int(blocks) * 256, dtype=torch.float32, device=device)
+    n = int(load().dbi_fma_probe(int(blocks), int(iters), _ptr(out), _stream(out.device)))
+    if n < 0:
+        _check(n, "dbi_fma_probe")
+    return n, out
+
+
 def profile_end():
     """(summed ms, launches) of the stage timed since profile_begin."""
     ms, n = c_double(0.0), ctypes.c_longlong(0)
@@ -337,6 +377,7 @@ def greens_tabulate(grid: Grid, ref: Medium, omega: torch.Tensor, precision: int
 def incident_field(grid: Grid, omega, fidx, Gspace, src_cells, forces):
     """u0 [B][2][nz][nx] = G_h(x - x_s) f for every problem."""
     precision = _precision(Gspace)
+    _table("Gspace", Gspace, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
     _need_cuda(Gspace, src_cells, forces)
     if src_cells.dtype != torch.int32 or forces.dtype != torch.float64:
         raise DBIError("src_cells must be int32 [B][2] and forces float64 [B][2]")
@@ -350,8 +391,9 @@ def incident_field(grid: Grid, omega, fidx, Gspace, src_cells, forces):
 def green_convolve(grid: Grid, omega, fidx, Ghat, src):
     """h^2 G * src for every problem."""
     precision = _precision(src)
-    _fields(fidx, 2, grid.nz * grid.nx, src=src)
-    _need_cuda(Ghat, src)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), src=src)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, src)
     batch = _batch(omega, fidx)
     out = torch.empty_like(src)
     work, n = _work(grid, batch.B, precision, OP_CONVOLVE, src.device)
@@ -363,8 +405,9 @@ def green_convolve(grid: Grid, omega, fidx, Ghat, src):
 def ls_apply(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None, work=None):
     """A u (Eq. 10) for every problem."""
     precision = _precision(u)
-    _fields(fidx, 2, grid.nz * grid.nx, u=u, out=out)
-    _need_cuda(Ghat, u)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), u=u, out=out)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, u)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
     out = torch.empty_like(u) if out is None else out
@@ -380,8 +423,9 @@ def ls_apply(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None, work=No
 def ls_apply_noalloc(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None):
     """A u like ls_apply, with the library's fixed scratch array instead of a work buffer."""
     precision = _precision(u)
-    _fields(fidx, 2, grid.nz * grid.nx, u=u, out=out)
-    _need_cuda(Ghat, u)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), u=u, out=out)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, u)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
     out = torch.empty_like(u) if out is None else out
@@ -398,8 +442,9 @@ def ls_solve(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, tol=1e
              check_every=8, work=None, out=None):
     """Solve A u = rhs for every problem (from u0, or from zero); returns (u, iters, relres, code)."""
     precision = _precision(rhs)
-    _fields(fidx, 2, grid.nz * grid.nx, rhs=rhs, u0=u0, out=out)
-    _need_cuda(Ghat, rhs)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), rhs=rhs, u0=u0, out=out)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, rhs)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
     if out is None:
@@ -429,8 +474,9 @@ def ls_solve_gmres(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, 
     """Solve A u = rhs by restarted GMRES(restart); returns (u, iters, relres, code), iters in Arnoldi
     steps (operator passes inside the cycles)."""
     precision = _precision(rhs)
-    _fields(fidx, 2, grid.nz * grid.nx, rhs=rhs, u0=u0)
-    _need_cuda(Ghat, rhs)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), rhs=rhs, u0=u0)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, rhs)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
     u = torch.empty_like(rhs) if u0 is None else u0.clone()
@@ -489,6 +535,7 @@ def greens_tabulate_3d(grid: Grid3, ref: Medium, omega: torch.Tensor, precision:
 
 def incident_field_3d(grid: Grid3, omega, fidx, Gspace, src_cells, forces):
     precision = _precision(Gspace)
+    _table("Gspace", Gspace, int(omega.numel()), 6, grid.lz * grid.ly * grid.lx, complex_dtype(precision))
     _need_cuda(Gspace, src_cells, forces)
     batch = _batch(omega, fidx)
     u0 = torch.empty((batch.B, 3, grid.nz, grid.ny, grid.nx), dtype=Gspace.dtype, device=Gspace.device)
@@ -499,8 +546,9 @@ def incident_field_3d(grid: Grid3, omega, fidx, Gspace, src_cells, forces):
 
 def ls_apply_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, u, out=None):
     precision = _precision(u)
-    _fields(fidx, 3, grid.nz * grid.ny * grid.nx, u=u, out=out)
-    _need_cuda(Ghat, u)
+    on_device = _fields(fidx, 3, grid.nz * grid.ny * grid.nx, complex_dtype(precision), u=u, out=out)
+    _table("Ghat", Ghat, int(omega.numel()), 6, grid.lz * grid.ly * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, u)
     model = _model3(grid, ref, m, precision)
     batch = _batch(omega, fidx)
     out = torch.empty_like(u) if out is None else out
@@ -514,8 +562,9 @@ def ls_solve_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, re
                 check_every=8):
     """A u = rhs in 3D by GMRES(restart); returns (u, iters, relres, code)."""
     precision = _precision(rhs)
-    _fields(fidx, 3, grid.nz * grid.ny * grid.nx, rhs=rhs, u0=u0)
-    _need_cuda(Ghat, rhs)
+    on_device = _fields(fidx, 3, grid.nz * grid.ny * grid.nx, complex_dtype(precision), rhs=rhs, u0=u0)
+    _table("Ghat", Ghat, int(omega.numel()), 6, grid.lz * grid.ly * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, rhs)
     model = _model3(grid, ref, m, precision)
     batch = _batch(omega, fidx)
     u = torch.empty_like(rhs) if u0 is None else u0.clone()
@@ -531,8 +580,9 @@ def ls_solve_3d(grid: Grid3, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, re
 def _products3(name, grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, x, out, tol, max_iter, restart,
                check_every):
     precision = _precision(u_b)
-    _fields(fidx, 3, grid.nz * grid.ny * grid.nx, u_b=u_b)
-    _need_cuda(Ghat, u_b, rec_cells, x)
+    on_device = _fields(fidx, 3, grid.nz * grid.ny * grid.nx, complex_dtype(precision), u_b=u_b)
+    _table("Ghat", Ghat, int(omega.numel()), 6, grid.lz * grid.ly * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, u_b, rec_cells, x)
     if rec_cells.dtype != torch.int32 or rec_cells.dim() != 2 or rec_cells.shape[1] != 3:
         raise DBIError("rec_cells must be int32 [n_rec][3]")
     model = _model3(grid, ref, m_b, precision)
@@ -552,6 +602,7 @@ def _products3(name, grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, x, out, 
 def frechet_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, dm, tol=1e-6,
                      max_iter=1000, restart=30, check_every=8):
     """J dm in 3D: [B][n_rec][3] complex data perturbations (and the solves' status)."""
+    _real("dm", dm, 6 * grid.nz * grid.ny * grid.nx, real_dtype(_precision(u_b)))
     d = torch.empty((u_b.shape[0], rec_cells.shape[0], 3), dtype=u_b.dtype, device=u_b.device)
     return _products3("frechet_apply_3d", grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, dm, d, tol, max_iter,
                       restart, check_every)
@@ -560,7 +611,8 @@ def frechet_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_
 def adjoint_apply_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, r, tol=1e-6,
                      max_iter=1000, restart=30, check_every=8):
     """Re J^H r in 3D summed over the problems: [6][nz][ny][nx] real (and the solves' status)."""
-    _fields(fidx, int(rec_cells.shape[0]), 3, r=r)
+    precision = _precision(u_b)
+    on_device = _fields(fidx, int(rec_cells.shape[0]), 3, complex_dtype(precision), r=r)
     g = torch.empty((6, grid.nz, grid.ny, grid.nx), dtype=real_dtype(_precision(u_b)), device=u_b.device)
     return _products3("adjoint_apply_3d", grid, ref, m_b, omega, fidx, Ghat, u_b, rec_cells, r, g, tol, max_iter,
                       restart, check_every)
@@ -581,9 +633,12 @@ def normal_cg_3d(grid: Grid3, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cell
                  check_every=8):
     """Tikhonov normal-equation CG in 3D; returns (dm [6][nz][ny][nx], lambda, residual history)."""
     precision = _precision(u_b)
-    _fields(fidx, 3, grid.nz * grid.ny * grid.nx, u_b=u_b)
-    _fields(fidx, int(rec_cells.shape[0]), 3, dd=dd)
-    _need_cuda(Ghat, u_b, dd, rec_cells, *([] if power_start is None else [power_start]))
+    on_device = _fields(fidx, 3, grid.nz * grid.ny * grid.nx, complex_dtype(precision), u_b=u_b)
+    on_device += _fields(fidx, int(rec_cells.shape[0]), 3, complex_dtype(precision), dd=dd)
+    _table("Ghat", Ghat, int(omega.numel()), 6, grid.lz * grid.ly * grid.lx, complex_dtype(precision))
+    if power_start is not None:
+        _real("power_start", power_start, 6 * grid.nz * grid.ny * grid.nx, real_dtype(precision))
+    _need_cuda(*on_device, Ghat, u_b, dd, rec_cells, *([] if power_start is None else [power_start]))
     model = _model3(grid, ref, m_b, precision)
     batch = _batch(omega, fidx)
     n_rec = int(rec_cells.shape[0])
@@ -621,8 +676,10 @@ def greens_tabulate_k(grid: Grid, ref: Medium, omega: torch.Tensor, precision: i
 def ls_apply_k(grid: Grid, ref: Medium, m, omega, fidx, Ghat, Dhat, u, out=None):
     """A u in the paper-literal form of Eq. 9 (the gradient on the Green's tensor)."""
     precision = _precision(u)
-    _fields(fidx, 2, grid.nz * grid.nx, u=u, out=out)
-    _need_cuda(Ghat, Dhat, u)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), u=u, out=out)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _table("Dhat", Dhat, int(omega.numel()), 6, grid.lz * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, Dhat, u)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
     out = torch.empty_like(u) if out is None else out
@@ -636,8 +693,10 @@ def ls_solve_k(grid: Grid, ref: Medium, m, omega, fidx, Ghat, Dhat, rhs, u0=None
                check_every=8):
     """Solve A u = rhs with the operator of ls_apply_k; returns (u, iters, relres, code)."""
     precision = _precision(rhs)
-    _fields(fidx, 2, grid.nz * grid.nx, rhs=rhs, u0=u0)
-    _need_cuda(Ghat, Dhat, rhs)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), rhs=rhs, u0=u0)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _table("Dhat", Dhat, int(omega.numel()), 6, grid.lz * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, Dhat, rhs)
     model = _model(grid, ref, m, precision)
     batch = _batch(omega, fidx)
     u = torch.empty_like(rhs) if u0 is None else u0.clone()
@@ -654,8 +713,10 @@ def frechet_apply(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cell
                   max_iter=1000, check_every=8, with_status=False):
     """J dm sampled at the receivers, [B][n_rec][2] (and the solve's (iters, relres, code))."""
     precision = _precision(u_b)
-    _fields(fidx, 2, grid.nz * grid.nx, u_b=u_b)
-    _need_cuda(Ghat, u_b, dm)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), u_b=u_b)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _real("dm", dm, 5 * grid.nz * grid.nx, real_dtype(precision))
+    _need_cuda(*on_device, Ghat, u_b, dm)
     model = _model(grid, ref, m_b, precision)
     if dm.dtype != real_dtype(precision):
         raise DBIError("dm must have the model's real dtype")
@@ -675,9 +736,10 @@ def adjoint_apply(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cell
                   max_iter=1000, check_every=8, with_status=False):
     """Re J^H r summed over problems, [5][nz][nx] (and the solve's (iters, relres, code))."""
     precision = _precision(u_b)
-    _fields(fidx, 2, grid.nz * grid.nx, u_b=u_b)
-    _fields(fidx, int(rec_cells.shape[0]), 2, r=r)
-    _need_cuda(Ghat, u_b, r)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), u_b=u_b)
+    on_device += _fields(fidx, int(rec_cells.shape[0]), 2, complex_dtype(precision), r=r)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    _need_cuda(*on_device, Ghat, u_b, r)
     model = _model(grid, ref, m_b, precision)
     batch = _batch(omega, fidx)
     rec = _receivers(rec_cells)
@@ -694,9 +756,9 @@ def adjoint_apply(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cell
 def data_residual(grid: Grid, omega, fidx, rec_cells, u, d_obs):
     """(r = P u - d_obs, phi = 1/2 ||r||^2 as a device float64 scalar tensor)."""
     precision = _precision(u)
-    _fields(fidx, 2, grid.nz * grid.nx, u=u)
-    _fields(fidx, int(rec_cells.shape[0]), 2, d_obs=d_obs)
-    _need_cuda(u, d_obs)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), u=u)
+    on_device += _fields(fidx, int(rec_cells.shape[0]), 2, complex_dtype(precision), d_obs=d_obs)
+    _need_cuda(*on_device, u, d_obs)
     batch = _batch(omega, fidx)
     rec = _receivers(rec_cells)
     r = torch.empty_like(d_obs)
@@ -710,9 +772,12 @@ def normal_cg(grid: Grid, ref: Medium, m_b, omega, fidx, Ghat, u_b, rec_cells, d
               lambda_rel=1e-3, power_iters=10, power_start=None, tol=1e-6, max_iter=1000, check_every=8):
     """Tikhonov normal-equation CG; returns (dm [5][nz][nx], lambda, residual history)."""
     precision = _precision(u_b)
-    _fields(fidx, 2, grid.nz * grid.nx, u_b=u_b)
-    _fields(fidx, int(rec_cells.shape[0]), 2, dd=dd)
-    _need_cuda(Ghat, u_b, dd, power_start)
+    on_device = _fields(fidx, 2, grid.nz * grid.nx, complex_dtype(precision), u_b=u_b)
+    on_device += _fields(fidx, int(rec_cells.shape[0]), 2, complex_dtype(precision), dd=dd)
+    _table("Ghat", Ghat, int(omega.numel()), 3, grid.lz * grid.lx, complex_dtype(precision))
+    if power_start is not None:
+        _real("power_start", power_start, 5 * grid.nz * grid.nx, real_dtype(precision))
+    _need_cuda(*on_device, Ghat, u_b, dd, power_start)
     model = _model(grid, ref, m_b, precision)
     batch = _batch(omega, fidx)
     rec = _receivers(rec_cells)

@@ -3,6 +3,8 @@ host-side argument checks reject bad calls before any CUDA work. No GPU is neede
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -186,15 +188,16 @@ def test_the_product_path_fails_loudly_without_the_library_or_a_gpu():
 
 
 def test_workspace_queries_grow_with_the_batch_and_never_wrap(lib):
-    """Every workspace query, for seeded random grids and batches: the size grows with B, complex128
-    needs at least what complex64 does, and a batch far beyond any GPU (2^20 problems) gives a size
-    above the bytes of its own wavefields (no 32-bit products that would wrap)."""
+    """Every workspace query, for seeded random grids and batches and the one-cell grid: the size grows
+    with B, complex128 needs at least what complex64 does, and a batch far beyond any GPU (2^20
+    problems) gives a size above the bytes of its own complex64 wavefields (no 32-bit products
+    that would wrap)."""
     import numpy as np
     rng = np.random.default_rng(31)
     ops2d = [dbi.OP_CONVOLVE, dbi.OP_APPLY, dbi.OP_SOLVE, dbi.OP_FRECHET, dbi.OP_ADJOINT, dbi.OP_NORMAL_CG,
              dbi.OP_APPLY_K, dbi.OP_SOLVE_K]
-    for _ in range(60):
-        nz, nx = int(rng.integers(1, 513)), int(rng.integers(1, 513))
+    shapes = [(1, 1)] + [(int(rng.integers(1, 513)), int(rng.integers(1, 513))) for _ in range(60)]
+    for nz, nx in shapes:
         g = dbi.make_grid(nz, nx, max(16, 1 << (2 * nz - 2).bit_length()), max(16, 1 << (2 * nx - 2).bit_length()), 5.0)
         B = int(rng.integers(1, 300))
         for op in ops2d:
@@ -202,7 +205,9 @@ def test_workspace_queries_grow_with_the_batch_and_never_wrap(lib):
             assert small > 0 and dbi.workspace_bytes(g, B + 7, dbi.C64, op) >= small, (nz, nx, B, op)
             assert dbi.workspace_bytes(g, B, dbi.C128, op) >= small
             huge = dbi.workspace_bytes(g, 1 << 20, dbi.C64, op)
-            assert huge >= (1 << 20) * 2 * nz * nx * 8 // 4 and huge >= small, (nz, nx, op, huge)
+            # every 2D operation holds at least one complex64 field's worth per problem (its
+            # spectral scratch has lx >= nx columns); Python's integers do not wrap
+            assert huge >= (1 << 20) * 2 * nz * nx * 8 and huge >= small, (nz, nx, op, huge)
         gm = lib.dbi_gmres_workspace_bytes(ctypes.byref(g), B, dbi.C64, 30)
         assert gm >= 31 * B * 2 * nz * nx * 8 and lib.dbi_gmres_workspace_bytes(ctypes.byref(g), 1 << 20, dbi.C64, 30) > gm
     for _ in range(30):
@@ -217,3 +222,45 @@ def test_workspace_queries_grow_with_the_batch_and_never_wrap(lib):
         assert dbi.workspace_bytes_3d(g3, B, dbi.C64, dbi.OP_SOLVE, 30) >= 31 * field
         p = lib.dbi_products_workspace_bytes_3d(ctypes.byref(g3), B, dbi.C64, 30)
         assert p >= 31 * field and lib.dbi_products_workspace_bytes_3d(ctypes.byref(g3), 1 << 20, dbi.C64, 30) > p
+
+
+def test_work_buffer_arena_overflow_is_reported(tmp_path):
+    """The library's work-buffer arena (the bump allocator every entry point carves its scratch
+    from), compiled into a host program and linked against the library: carves are aligned and
+    inside the buffer; a carve past the end, a missing buffer or a wrapping size returns NULL and
+    sets a sticky overflow flag, which the entry points check before their first launch
+    (DBI_ERR_WORKSPACE with the caller's name in dbi_last_error)."""
+    cc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(cc):
+        pytest.skip("nvcc not available")
+    lib = build.build()
+    libdir = os.path.dirname(lib)
+    exe = str(tmp_path / "arena_host")
+    res = subprocess.run([cc, "-std=c++20", "-O1", "--expt-relaxed-constexpr", "-gencode",
+                          "arch=compute_103a,code=sm_103a", os.path.join(ROOT, "tests", "native", "arena_host.cu"),
+                          "-o", exe, "-L", libdir, "-ldbi", "-Xlinker", "-rpath=" + libdir],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr[-3000:]
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, run.stderr
+    assert "arena ok" in run.stdout
+
+
+def test_bicgstab_decision_branches_on_the_host(tmp_path):
+    """The library's BiCGSTAB end-of-iteration decision compiled for the CPU from its own header and
+    run on crafted inner products: NaN or infinity stops a problem with DBI_NONFINITE before any
+    other test, convergence (residual or half step), the iteration limit, both breakdowns (omega = 0,
+    <rhat, r> negligible) restart from the iterate with rhat := r and report DBI_BREAKDOWN, and beta
+    equals (rho_new / rho)(alpha / omega) in std::complex arithmetic."""
+    cc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(cc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "krylov_decide_host")
+    res = subprocess.run([cc, "-std=c++20", "-O1", "--expt-relaxed-constexpr", "-gencode",
+                          "arch=compute_103a,code=sm_103a",
+                          os.path.join(ROOT, "tests", "native", "krylov_decide_host.cu"), "-o", exe],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr[-3000:]
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, run.stderr
+    assert "decide ok" in run.stdout

@@ -43,8 +43,8 @@ def test_form_k_column_kernel_units():
 
 def test_reference_arm_json_line():
     """`bench.py --impl reference` prints one JSON line with the contract's keys: the metric of
-    the GPU arm on its workload, the oracle as the CPU baseline (kind, cores, sample) and an e2e
-    object with no host-device traffic."""
+    the GPU arm on its workload (the 512 x 512 gradient batch), the oracle as the CPU baseline on
+    every host core (kind, cores, sample) and an e2e object with no host-device traffic."""
     res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                           "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert res.returncode == 0, res.stderr[-2000:]
@@ -54,9 +54,11 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference"
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 1 and d["n_gpus"] == 1
-    assert d["config"]["workload"] == "vti256x256_32src_8f"
+    assert d["config"]["workload"] == "vti512x512_64src_6f_misfit"
+    assert (d["config"]["nz"], d["config"]["lz"], d["config"]["problems_per_gpu"]) == (512, 1024, 384)
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1) and cb["sample"]
+    assert cb["value"] == d["value"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
@@ -90,3 +92,38 @@ def test_oracle_sample_of_the_uneven_batch():
     r = bench.oracle_uneven_sample(ws)
     assert r["sample"].count("x") >= 2 and "8x7" in r["sample"] and "12x10" in r["sample"]
     assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
+
+
+def test_column_kernel_units_on_the_512_workload():
+    """512 x 512 cells, 1024 x 1024 FFT grid, 64 sources x 6 frequencies (384 problems):
+    flops: 2 x 2 x 1024 columns x 5 * 1024 * 10 = 209,715,200 plus 28 x 1024^2 = 29,360,128, per
+    cell 912; bytes: T read and written 2 x 2 x 512 x 1024 x 8 = 16,777,216 plus 3 x 1024^2 x 8 of
+    each frequency over its 64 sources = 393,216, per cell 65.5."""
+    w = bench.workload("vti512")
+    assert (w.nz, w.nx, w.lz, w.lx, w.nf, w.n_problems) == (512, 512, 1024, 1024, 6, 384)
+    assert bench.cols_flops_per_cell_apply(w) == pytest.approx(239_075_328 / 262_144, rel=1e-12)
+    assert bench.cols_bytes_per_cell_apply(w) == pytest.approx(17_170_432 / 262_144, rel=1e-12)
+
+
+def test_accuracy_block_and_baseline_merge():
+    """The accuracy block's relative errors and the multi-process baseline, on stand-in values:
+    a wavefield off by 1e-6 relative gives 1e-6, the gradient error is per parameter, and the
+    baseline's rate is all cell-applies over the longest process's time."""
+    import numpy as np
+    w = inputs.small_case(nz=6, nx=5, n_src=2, freqs=(5.0, 9.0))
+    rng = np.random.default_rng(0)
+    u = rng.normal(size=(2, 2, 6, 5)) + 1j * rng.normal(size=(2, 2, 6, 5))
+    d_obs = (rng.normal(size=(w.n_problems, 3, 2)) * (1 + 1j)).astype(np.complex64)
+    rr = rng.normal(size=(2, 3, 2)) + 0j
+    g = rng.normal(size=(5, 6, 5))
+    res = [{"b": b, "u": u[k], "d": rr[k] + d_obs[b], "r": rr[k], "g": g / 2, "iters": (3, 4),
+            "relres": (1e-13, 1e-13), "seconds": 1.0, "freq_hz": 5.0, "source": 0} for k, b in enumerate((0, 3))]
+    gpu = {"u": u * (1 + 1e-6), "r": rr.copy(), "g": g * (1 + np.array([0, 0, 2e-5, 0, 0]))[:, None, None]}
+    acc = bench.accuracy_block(w, gpu, res, d_obs)
+    assert acc["wavefield_max"] == pytest.approx(1e-6, rel=1e-6)
+    assert acc["residual_max"] == 0.0 and acc["data_max"] < 1e-15
+    assert acc["gradient_subbatch"]["C13"] == pytest.approx(2e-5, rel=1e-6)
+    assert acc["gradient_subbatch"]["rho"] == 0.0 and acc["gradient_max"] == acc["gradient_subbatch"]["C13"]
+    m = bench.merge_baseline([{"passes": 10, "cells": 100, "seconds": 2.0, "sample": "a"},
+                              {"passes": 30, "cells": 100, "seconds": 4.0, "sample": "b"}])
+    assert m["value"] == pytest.approx(4000 / 4.0) and m["cores"] == 2 and m["kind"] == "oracle"

@@ -1,7 +1,9 @@
-"""The binding's size checks on field arguments (CPU only): every wrapper that hands wavefields or
-receiver data to the library checks that each holds one block per problem (B = the length of
-fidx) before anything reaches the device, so a wrongly sized tensor is an error, not a read or
-write past its end. With CPU tensors a correctly sized call gets as far as the CUDA check."""
+"""The binding's checks on field and table arguments (CPU only): every wrapper that hands
+wavefields, receiver data, Green's tables or per-cell parameters to the library checks that each
+holds one block per problem (B = the length of fidx) or the table's nf x components x FFT-grid
+points, in the call's dtype, before anything reaches the device, so a wrongly sized or typed tensor
+is an error, not a read or write past its end. With CPU tensors a correctly sized and typed call
+gets as far as the CUDA check."""
 import pytest
 import torch
 
@@ -51,8 +53,9 @@ def calls():
     yield "ls_solve u0", lambda x: dbi.ls_solve(g, ref, m, om, fi, G, u, u0=x), u, bad
     yield "ls_solve_gmres", lambda x: dbi.ls_solve_gmres(g, ref, m, om, fi, G, x), u, bad
     yield "green_convolve", lambda x: dbi.green_convolve(g, om, fi, G, x), u, bad
-    yield "ls_apply_k", lambda x: dbi.ls_apply_k(g, ref, m, om, fi, G, G, x), u, bad
-    yield "ls_solve_k", lambda x: dbi.ls_solve_k(g, ref, m, om, fi, G, G, x), u, bad
+    D = f(1, 6, 16, 16)
+    yield "ls_apply_k", lambda x: dbi.ls_apply_k(g, ref, m, om, fi, G, D, x), u, bad
+    yield "ls_solve_k", lambda x: dbi.ls_solve_k(g, ref, m, om, fi, G, D, x), u, bad
     yield "frechet_apply", lambda x: dbi.frechet_apply(g, ref, m, om, fi, G, x, rec, dm), u, bad
     yield "adjoint_apply u_b", lambda x: dbi.adjoint_apply(g, ref, m, om, fi, G, x, rec, d), u, bad
     yield "adjoint_apply r", lambda x: dbi.adjoint_apply(g, ref, m, om, fi, G, u, rec, x), d, dbad
@@ -93,3 +96,50 @@ def test_uneven_batch_fields_are_checked_before_the_device():
                 call(bad)
         with pytest.raises(dbi.DBIError, match="CUDA tensor"):
             call(good)
+
+
+def typed_calls():
+    """(name, call taking the checked argument, a correct value, a wrong value, expected message)."""
+    g, ref, m, om, fi, G, rec = common2d()
+    u = f(B, 2, NZ, NX)
+    wide = torch.zeros((B, 2, NZ, NX), dtype=torch.complex128)
+    d = f(B, NREC, 2)
+    dm = torch.zeros((5, NZ, NX), dtype=torch.float32)
+    D = f(1, 6, 16, 16)
+    Gshort, Gwide = f(1, 3, 16, 15), torch.zeros((1, 3, 16, 16), dtype=torch.complex128)
+    yield "ls_apply out dtype", lambda x: dbi.ls_apply(g, ref, m, om, fi, G, u, out=x), u, wide, "needs"
+    yield "ls_apply_noalloc out dtype", lambda x: dbi.ls_apply_noalloc(g, ref, m, om, fi, G, u, out=x), u, wide, "needs"
+    yield "ls_solve u0 dtype", lambda x: dbi.ls_solve(g, ref, m, om, fi, G, u, u0=x), u, wide, "needs"
+    yield "ls_solve out dtype", lambda x: dbi.ls_solve(g, ref, m, om, fi, G, u, out=x), u, wide, "needs"
+    for name, bad, msg in (("size", Gshort, "FFT-grid points"), ("dtype", Gwide, "needs")):
+        yield f"ls_apply Ghat {name}", lambda x: dbi.ls_apply(g, ref, m, om, fi, x, u), G, bad, msg
+        yield f"ls_apply_noalloc Ghat {name}", lambda x: dbi.ls_apply_noalloc(g, ref, m, om, fi, x, u), G, bad, msg
+        yield f"ls_solve Ghat {name}", lambda x: dbi.ls_solve(g, ref, m, om, fi, x, u), G, bad, msg
+        yield f"green_convolve Ghat {name}", lambda x: dbi.green_convolve(g, om, fi, x, u), G, bad, msg
+        yield f"frechet_apply Ghat {name}", lambda x: dbi.frechet_apply(g, ref, m, om, fi, x, u, rec, dm), G, bad, msg
+        yield f"adjoint_apply Ghat {name}", lambda x: dbi.adjoint_apply(g, ref, m, om, fi, x, u, rec, d), G, bad, msg
+        yield f"normal_cg Ghat {name}", lambda x: dbi.normal_cg(g, ref, m, om, fi, x, u, rec, d), G, bad, msg
+        yield f"ls_apply_k Ghat {name}", lambda x: dbi.ls_apply_k(g, ref, m, om, fi, x, D, u), G, bad, msg
+    yield "ls_apply_k Dhat size", lambda x: dbi.ls_apply_k(g, ref, m, om, fi, G, x, u), D, G, "FFT-grid points"
+    yield "incident_field Gspace size", (lambda x: dbi.incident_field(
+        g, om, fi, x, torch.zeros((B, 2), dtype=torch.int32), torch.zeros((B, 2), dtype=torch.float64))), \
+        G, Gshort, "FFT-grid points"
+    yield "frechet_apply dm size", (lambda x: dbi.frechet_apply(g, ref, m, om, fi, G, u, rec, x)), dm, \
+        torch.zeros((5, NZ, NX - 1), dtype=torch.float32), "holds"
+    yield "frechet_apply dm dtype", (lambda x: dbi.frechet_apply(g, ref, m, om, fi, G, u, rec, x)), dm, \
+        torch.zeros((5, NZ, NX), dtype=torch.float64), "needs"
+    yield "normal_cg power_start size", (lambda x: dbi.normal_cg(g, ref, m, om, fi, G, u, rec, d, power_start=x)), \
+        dm, torch.zeros((4, NZ, NX), dtype=torch.float32), "holds"
+
+
+TYPED = list(typed_calls())
+
+
+@pytest.mark.parametrize("name, call, good, bad, msg", TYPED, ids=[c[0] for c in TYPED])
+def test_dtypes_and_tables_are_checked_before_the_device(name, call, good, bad, msg):
+    """A wrong dtype of an output or initial guess, and a Green's table or per-cell argument of the
+    wrong size or dtype, are errors before the device; the correct value reaches the CUDA check."""
+    with pytest.raises(dbi.DBIError, match=msg):
+        call(bad)
+    with pytest.raises(dbi.DBIError, match="CUDA tensor"):
+        call(good)

@@ -371,3 +371,24 @@ def test_second_radix_plan_matches_oracle(L, precision):
     for b in range(P.B):
         want = orc.apply(npy(u[b]).astype(np.complex128), w.model, 0)
         assert rel(out[b], want) < TOL[precision], b
+
+
+def test_binding_rejects_host_or_mistyped_outputs_with_device_inputs():
+    """With device inputs, a host output, an output of the other precision and a Green's table of
+    the other precision or size are errors before the library is called (each would have the
+    kernels write through a host address or past the tensor's end)."""
+    w = inputs.small_case(nz=6, nx=5, n_src=1, freqs=(8.0,))
+    P = DeviceProblem(w, dbi.C64)
+    u = P.incident()
+    n0 = dbi.kernel_launches()
+    with pytest.raises(dbi.DBIError, match="CUDA tensor"):
+        dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u, out=torch.empty_like(u, device="cpu"))
+    with pytest.raises(dbi.DBIError, match="needs"):
+        dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u, out=u.to(torch.complex128))
+    with pytest.raises(dbi.DBIError, match="needs"):
+        dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat.to(torch.complex128), u)
+    with pytest.raises(dbi.DBIError, match="FFT-grid points"):
+        dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat[:, :2].contiguous(), u)
+    with pytest.raises(dbi.DBIError, match="CUDA tensor"):
+        dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat.cpu(), u)
+    assert dbi.kernel_launches() == n0

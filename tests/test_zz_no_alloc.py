@@ -51,3 +51,27 @@ def test_noalloc_rejects_a_batch_beyond_the_array():
     u = P.incident()
     with pytest.raises(dbi.DBIError, match="scratch"):
         dbi.ls_apply_noalloc(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u)
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The entry point's promise, measured: with a preallocated output and after one warm-up call
+    (which looks up the array's address), further calls leave both PyTorch's allocation count and
+    the device's free memory unchanged, and give the same result every time."""
+    build.build()
+    dbi.load()
+    w = inputs.small_case(nz=64, nx=48, n_src=3, freqs=(7.0, 12.0), amp=0.1, vti=True, seed=9)
+    P = DeviceProblem(w, dbi.C64)
+    u = P.to_field(inputs.seeded_complex((P.B, 2, w.nz, w.nx), 31))
+    out = torch.empty_like(u)
+    dbi.ls_apply_noalloc(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u, out=out)
+    torch.cuda.synchronize()
+    first = out.clone()
+    torch.cuda.synchronize()
+    allocs = torch.cuda.memory_stats()["allocation.all.allocated"]
+    free = torch.cuda.mem_get_info()[0]
+    for _ in range(4):
+        dbi.ls_apply_noalloc(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u, out=out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, first)
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == allocs
+    assert torch.cuda.mem_get_info()[0] == free
