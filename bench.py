@@ -331,16 +331,13 @@ def run_ours(args):
         del s2, d2, last2
     if solo and not (args.no_accuracy and args.no_cpu_baseline):
         acc_problems = accuracy_problems(w)
-        acc_tasks = [] if args.no_accuracy else [(args.workload, args.sources, b) for b in acc_problems]
-        cores = args.cores or (os.cpu_count() or 1)
-        base_tasks = [] if args.no_cpu_baseline else baseline_tasks(args.workload, args.sources, w,
-                                                                    max(1, cores - len(acc_tasks)))
         gpu_acc = None if args.no_accuracy else gpu_accuracy_side(P, last, acc_problems)
-        acc_res, base_res = run_oracle_pool(acc_tasks, base_tasks)
-        if acc_tasks:
-            result["accuracy"] = accuracy_block(w, gpu_acc, acc_res, d_obs_host)
-        if base_tasks:
-            result["cpu_baseline"] = merge_baseline(base_res)
+        acc_res, base = run_cpp_oracle(w, d_obs_host, [] if args.no_accuracy else acc_problems,
+                                       not args.no_cpu_baseline, args.cores)
+        if acc_res is not None:
+            result["accuracy"] = accuracy_block(w, gpu_acc, acc_res[0], acc_res[1], d_obs_host)
+        if base is not None:
+            result["cpu_baseline"] = base
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -624,88 +621,60 @@ def accuracy_problems(w):
     return [0, (w.nf - 1) * w.n_src + w.n_src // 2]
 
 
-def baseline_tasks(name, sources, w, n):
-    """n problems at the lowest frequency (distinct sources) for the oracle's CPU baseline: the
-    rate per cell-apply hardly depends on the frequency, and the lowest needs the fewest passes."""
-    return [(name, sources, int(k * w.n_src // n) % w.n_src) for k in range(n)]
+def run_cpp_oracle(w, d_obs_host, acc_problems, baseline, cores=0):
+    """The C++17 FP64 oracle (OpenMP, one problem per thread) on the host cores, two jobs at once:
+    the accuracy reference (the sampled problems solved to ORACLE_TOL) on one thread per sampled
+    problem, and the CPU baseline (one gradient contribution per remaining core at the benchmark's
+    tolerance, the lowest frequency, distinct sources). Returns (accuracy results or None, baseline
+    line or None)."""
+    import threading
+    from oracle import cpp_oracle as C
+    cores = cores or (os.cpu_count() or 1)
+    model = np.asarray(w.model, dtype=np.float32).astype(np.float64)  # as the GPU reads it
+    d_obs = np.asarray(d_obs_host).astype(np.complex128)
+    fidx_all, src_all = w.problem_fidx(), w.problem_src()
+    out = {}
 
+    def acc_job():
+        b = np.asarray(acc_problems)
+        fs = sorted(set(int(f) for f in fidx_all[b]))
+        orc = C.Oracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, model, w.omegas[fs],
+                       threads=len(b))
+        fidx = np.array([fs.index(int(f)) for f in fidx_all[b]], dtype=np.int32)
+        t0 = time.perf_counter()
+        g, r, passes, relres, u = orc.gradient(fidx, w.src_cells[src_all[b]], w.src_force[src_all[b]], w.rec_cells,
+                                               d_obs[b], tol=ORACLE_TOL, threads=len(b), keep_fields=True)
+        dt = time.perf_counter() - t0
+        out["acc"] = ([{"b": int(bb), "u": u[k], "d": r[k] + d_obs[bb], "r": r[k], "passes": int(passes[k]),
+                        "relres": tuple(float(x) for x in relres[k]), "seconds": dt,
+                        "freq_hz": float(w.freqs_hz[fidx_all[bb]]), "source": int(src_all[bb])}
+                       for k, bb in enumerate(b)], g)
 
-def _single_thread_env():
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
-        os.environ[k] = "1"
+    def base_job(n):
+        bs = [int(k * w.n_src // n) % w.n_src for k in range(n)]  # lowest frequency, distinct sources
+        orc = C.Oracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, model, w.omegas[:1], threads=n)
+        t0 = time.perf_counter()
+        g, r, passes, relres, _ = orc.gradient(np.zeros(n, dtype=np.int32), w.src_cells[bs], w.src_force[bs],
+                                               w.rec_cells, d_obs[bs], tol=TOL, threads=n)
+        dt = time.perf_counter() - t0
+        out["base"] = {"value": float(passes.sum()) * w.nz * w.nx / dt, "unit": UNIT, "cores": n, "kind": "oracle",
+                       "sample": f"C++17 FP64 oracle (own radix-2 FFT, OpenMP, one problem per thread) on {n} host "
+                                 f"cores: the gradient contributions (forward solve, residual, adjoint solve, imaging) "
+                                 f"of {n} problems of {w.name} at {w.freqs_hz[0]:g} Hz, BiCGSTAB to {TOL:g}, "
+                                 f"{int(passes.sum())} operator passes in {dt:.1f} s (tables built before)",
+                       "seconds": dt, "host_cpu_count": os.cpu_count()}
 
-
-def run_oracle_pool(acc_tasks, base_tasks):
-    """Runs the oracle tasks in a pool of spawned processes (one core each), all at once."""
-    if not acc_tasks and not base_tasks:
-        return [], []
-    import multiprocessing as mp
-    _single_thread_env()
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(processes=len(acc_tasks) + len(base_tasks)) as pool:
-        acc = [pool.apply_async(_oracle_accuracy_task, (t,)) for t in acc_tasks]
-        base = [pool.apply_async(_oracle_gradient_task, (t,)) for t in base_tasks]
-        return [r.get() for r in acc], [r.get() for r in base]
-
-
-def _oracle_inputs(name, sources, b):
-    """Workload, problem b's frequency and source, and the inputs as the GPU reads them (model
-    rounded to float32, observed data to complex64), all from the seeded recipes."""
-    w = workload(name, 0, 1, sources)
-    f, s = int(w.problem_fidx()[b]), int(w.problem_src()[b])
-    model = np.asarray(w.model, dtype=np.float32).astype(np.float64)
-    d_obs = synthetic_data(w)[b].astype(np.complex128)
-    return w, f, s, model, d_obs
-
-
-def _oracle_accuracy_task(task):
-    """The FP64 oracle's solution of problem b to ORACLE_TOL: wavefield, receiver data, residual
-    and the problem's gradient contribution (adjoint solve to ORACLE_TOL, imaging)."""
-    import oracle as O
-    name, sources, b = task
-    w, f, s, model, d_obs = _oracle_inputs(name, sources, b)
-    t0 = time.perf_counter()
-    orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
-    u, info_f = orc.solve_info(orc.incident(0, w.src_cells[s], w.src_force[s]), model, 0, tol=ORACLE_TOL)
-    d = orc.sample(u, w.rec_cells)
-    r = d - d_obs
-    ua, info_a = orc.solve_info(orc.convolve(orc.inject(np.conj(r), w.rec_cells), 0), model, 0, tol=ORACLE_TOL)
-    g = orc.imaging(ua, u, orc.omegas[0], orc.h)
-    return {"b": b, "u": u, "d": d, "r": r, "g": g, "iters": (info_f["iters"], info_a["iters"]),
-            "relres": (info_f["relres"], info_a["relres"]), "seconds": time.perf_counter() - t0,
-            "freq_hz": float(w.freqs_hz[f]), "source": s}
-
-
-def _oracle_gradient_task(task):
-    """One problem's gradient contribution (forward solve, residual, adjoint solve, imaging) by the
-    FP64 oracle as it stands, at the benchmark's tolerance; returns its operator passes and time."""
-    import oracle as O
-    name, sources, b = task
-    w, f, s, model, d_obs = _oracle_inputs(name, sources, b)
-    t0 = time.perf_counter()
-    orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
-    u0 = orc.incident(0, w.src_cells[s], w.src_force[s])
-    u, info_f = orc.solve_info(u0, model, 0, tol=TOL)
-    r = orc.sample(u, w.rec_cells) - d_obs
-    ua, info_a = orc.solve_info(orc.convolve(orc.inject(np.conj(r), w.rec_cells), 0), model, 0, tol=TOL)
-    orc.imaging(ua, u, orc.omegas[0], orc.h)
-    dt = time.perf_counter() - t0
-    # the oracle's solve_info applies A once more to report the true residual
-    passes = 2 * info_f["iters"] + 1 + 2 * info_a["iters"] + 1 + 1
-    return {"passes": passes, "cells": w.nz * w.nx, "seconds": dt,
-            "sample": f"problem {b} (source {s}, {w.freqs_hz[f]:.2f} Hz): {passes} passes in {dt:.1f} s"}
-
-
-def merge_baseline(res):
-    """Aggregate rate of oracle tasks that ran at the same time, one per process and core: all
-    their cell-applies over the longest task's time."""
-    applies = sum(r["passes"] * r["cells"] for r in res)
-    wall = max(r["seconds"] for r in res)
-    return {"value": applies / wall, "unit": UNIT, "cores": len(res), "kind": "oracle",
-            "sample": f"{len(res)} processes at once (one host core each), each one problem's gradient contribution "
-                      "(forward solve, residual, adjoint solve, imaging) by the FP64 numpy oracle; "
-                      + "; ".join(r["sample"] for r in res[:3]) + ("; ..." if len(res) > 3 else ""),
-            "seconds": wall, "host_cpu_count": os.cpu_count()}
+    jobs = []
+    if acc_problems:
+        jobs.append(threading.Thread(target=acc_job))
+    n_base = max(1, cores - len(acc_problems))
+    if baseline:
+        jobs.append(threading.Thread(target=base_job, args=(n_base,)))
+    for j in jobs:
+        j.start()
+    for j in jobs:
+        j.join()
+    return out.get("acc"), out.get("base")
 
 
 def gpu_accuracy_side(P, last, problems):
@@ -728,20 +697,19 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def accuracy_block(w, gpu, res, d_obs_host):
+def accuracy_block(w, gpu, res, g_or, d_obs_host):
     """Relative L2 errors against the FP64 oracle (solved to ORACLE_TOL): every sampled problem's
-    wavefield, receiver data (P u) and data residual, and the sub-batch gradient per parameter."""
+    wavefield, receiver data (P u) and data residual, and the sub-batch gradient (g_or: the oracle's
+    gradient summed over the sampled problems) per parameter."""
     per = []
-    g_or = np.zeros_like(gpu["g"])
     for k, r in enumerate(res):
         d_gpu = gpu["r"][k] + d_obs_host[r["b"]].astype(np.complex128)
         per.append({"problem": r["b"], "source": r["source"], "freq_hz": r["freq_hz"],
                     "wavefield": _rel(gpu["u"][k], r["u"]), "data": _rel(d_gpu, r["d"]),
                     "residual": _rel(gpu["r"][k], r["r"]),
-                    "oracle_iters": r["iters"], "oracle_relres": r["relres"], "oracle_seconds": r["seconds"]})
-        g_or += r["g"]
+                    "oracle_passes": r["passes"], "oracle_relres": r["relres"], "oracle_seconds": r["seconds"]})
     grad = {p: _rel(gpu["g"][i], g_or[i]) for i, p in enumerate(inputs.PARAMS)}
-    return {"reference": f"FP64 numpy oracle, BiCGSTAB to {ORACLE_TOL:g} (same seeded inputs: model rounded to "
+    return {"reference": f"C++17 FP64 oracle, BiCGSTAB to {ORACLE_TOL:g} (same seeded inputs: model rounded to "
                          "float32, observed data to complex64, as the GPU reads them)",
             "gpu": f"complex64 BiCGSTAB to {TOL:g} (the timed step's last solutions; the gradient by adjoint_apply "
                    "on the sub-batch of the sampled problems)",
@@ -837,56 +805,36 @@ def oracle_uneven_sample(ws):
                       + "), weighted by each size's cells in the batch", "seconds": seconds}
 
 
-_REF_CACHE = {}
-
-
-def _oracle_passes_task(task):
-    """Reference-arm step of one process: `passes` LS-operator passes (the oracle's `apply`) on
-    problem b's incident field; the oracle's tables for the problem's frequency are built once per
-    process (in the warm-up)."""
-    import oracle as O
-    name, sources, b, passes = task
-    w, f, s, model, _ = _oracle_inputs(name, sources, b)
-    key = (name, sources, f)
-    if key not in _REF_CACHE:
-        _REF_CACHE.clear()
-        orc = O.LSOracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, w.omegas[f:f + 1])
-        _REF_CACHE[key] = (orc, orc.incident(0, w.src_cells[s], w.src_force[s]))
-    orc, u = _REF_CACHE[key]
-    t0 = time.perf_counter()
-    for _ in range(passes):
-        u = orc.apply(u, model, 0)
-    return {"passes": passes, "cells": w.nz * w.nx, "seconds": time.perf_counter() - t0}
-
-
 def run_reference(args):
-    """The FP64 CPU oracle as it stands on the host cores: one process per core, each step every
-    process runs two LS-operator passes (one BiCGSTAB iteration's worth) on its own problem of the
-    workload (lowest frequency, distinct sources); warm-up steps build the oracle's tables."""
+    """The C++17 FP64 oracle as it stands on every host core (OpenMP, one problem per thread): each
+    step runs two LS-operator passes (one BiCGSTAB iteration's worth) on each of `cores` problems of
+    the workload (lowest frequency, distinct sources); the oracle's tables are built before the
+    warm-up steps."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    import multiprocessing as mp
+    from oracle import cpp_oracle as C
     name = args.workload if args.workload in ("vti512", "vti256") else "vti512"
     w = workload(name, 0, 1, args.sources)
     cores = args.cores or (os.cpu_count() or 1)
-    tasks = [(name, args.sources, int(k * w.n_src // cores) % w.n_src, 2) for k in range(cores)]
-    _single_thread_env()
-    ctx = mp.get_context("spawn")
-    t_applies, t_sec = 0.0, 0.0
-    with ctx.Pool(processes=cores) as pool:
-        for _ in range(max(args.warmup, 1)):  # the first builds every process's tables
-            pool.map(_oracle_passes_task, [(n, so, b, 1) for n, so, b, _ in tasks], chunksize=1)
-        for _ in range(args.steps):
-            t0 = time.perf_counter()
-            res = pool.map(_oracle_passes_task, tasks, chunksize=1)
-            t_sec += time.perf_counter() - t0
-            t_applies += sum(r["passes"] * r["cells"] for r in res)
+    model = np.asarray(w.model, dtype=np.float32).astype(np.float64)
+    orc = C.Oracle(w.nz, w.nx, w.h, w.lz, w.lx, w.rho0, w.alpha0, w.beta0, model, w.omegas[:1], threads=cores)
+    bs = [int(k * w.n_src // cores) % w.n_src for k in range(cores)]
+    fidx = np.zeros(cores, dtype=np.int32)
+    u = np.stack([np.asarray(inputs.seeded_complex((2, w.nz, w.nx), 100 + b)) for b in bs])
+    for _ in range(args.warmup):
+        orc.apply(fidx, u, threads=cores)
+    t_sec, t_applies = 0.0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        v = orc.apply(fidx, u, threads=cores)
+        orc.apply(fidx, v, threads=cores)
+        t_sec += time.perf_counter() - t0
+        t_applies += 2.0 * cores * w.nz * w.nx
     value = t_applies / t_sec
-    sample = (f"{cores} processes at once (one host core each), each step 2 LS-operator passes per process on its own "
-              f"problem of {w.name} (lowest frequency, distinct sources) by the FP64 numpy oracle's apply; step time = "
-              "wall time of the slowest process")
+    sample = (f"C++17 FP64 oracle (own radix-2 FFT, OpenMP, one problem per thread) on {cores} host cores: each step "
+              f"2 LS-operator passes on each of {cores} problems of {w.name} (lowest frequency, distinct sources)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_sec / max(args.steps, 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)",

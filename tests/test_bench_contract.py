@@ -105,10 +105,9 @@ def test_column_kernel_units_on_the_512_workload():
     assert bench.cols_bytes_per_cell_apply(w) == pytest.approx(17_170_432 / 262_144, rel=1e-12)
 
 
-def test_accuracy_block_and_baseline_merge():
-    """The accuracy block's relative errors and the multi-process baseline, on stand-in values:
-    a wavefield off by 1e-6 relative gives 1e-6, the gradient error is per parameter, and the
-    baseline's rate is all cell-applies over the longest process's time."""
+def test_accuracy_block():
+    """The accuracy block's relative errors on stand-in values: a wavefield off by 1e-6 relative
+    gives 1e-6, and the gradient error is per parameter."""
     import numpy as np
     w = inputs.small_case(nz=6, nx=5, n_src=2, freqs=(5.0, 9.0))
     rng = np.random.default_rng(0)
@@ -116,14 +115,25 @@ def test_accuracy_block_and_baseline_merge():
     d_obs = (rng.normal(size=(w.n_problems, 3, 2)) * (1 + 1j)).astype(np.complex64)
     rr = rng.normal(size=(2, 3, 2)) + 0j
     g = rng.normal(size=(5, 6, 5))
-    res = [{"b": b, "u": u[k], "d": rr[k] + d_obs[b], "r": rr[k], "g": g / 2, "iters": (3, 4),
-            "relres": (1e-13, 1e-13), "seconds": 1.0, "freq_hz": 5.0, "source": 0} for k, b in enumerate((0, 3))]
+    res = [{"b": b, "u": u[k], "d": rr[k] + d_obs[b], "r": rr[k], "passes": 7, "relres": (1e-13, 1e-13),
+            "seconds": 1.0, "freq_hz": 5.0, "source": 0} for k, b in enumerate((0, 3))]
     gpu = {"u": u * (1 + 1e-6), "r": rr.copy(), "g": g * (1 + np.array([0, 0, 2e-5, 0, 0]))[:, None, None]}
-    acc = bench.accuracy_block(w, gpu, res, d_obs)
+    acc = bench.accuracy_block(w, gpu, res, g, d_obs)
     assert acc["wavefield_max"] == pytest.approx(1e-6, rel=1e-6)
     assert acc["residual_max"] == 0.0 and acc["data_max"] < 1e-15
     assert acc["gradient_subbatch"]["C13"] == pytest.approx(2e-5, rel=1e-6)
     assert acc["gradient_subbatch"]["rho"] == 0.0 and acc["gradient_max"] == acc["gradient_subbatch"]["C13"]
-    m = bench.merge_baseline([{"passes": 10, "cells": 100, "seconds": 2.0, "sample": "a"},
-                              {"passes": 30, "cells": 100, "seconds": 4.0, "sample": "b"}])
-    assert m["value"] == pytest.approx(4000 / 4.0) and m["cores"] == 2 and m["kind"] == "oracle"
+
+
+def test_cpp_oracle_legs_on_a_small_workload():
+    """The C++ oracle legs of the benchmark on a small workload: the accuracy reference returns each
+    sampled problem's wavefield, data and residual and the sub-batch gradient, and the baseline
+    reports its rate on the cores it used."""
+    import numpy as np
+    w = inputs.small_case(nz=10, nx=9, n_src=3, freqs=(6.0, 11.0), vti=True, seed=4)
+    d_obs = bench.synthetic_data(w)
+    acc, base = bench.run_cpp_oracle(w, d_obs, [0, w.n_problems - 1], True, cores=3)
+    res, g = acc
+    assert [r["b"] for r in res] == [0, w.n_problems - 1] and g.shape == (5, w.nz, w.nx)
+    assert all(np.allclose(r["d"] - r["r"], d_obs[r["b"]], rtol=0, atol=1e-16) for r in res)
+    assert base["cores"] == 1 and base["value"] > 0 and base["kind"] == "oracle" and "C++17" in base["sample"]

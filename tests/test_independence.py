@@ -43,3 +43,16 @@ def test_the_oracle_imports_nothing_from_the_package():
 def test_the_input_generators_import_neither():
     mods = imported_modules(os.path.join(PKG, "inputs.py"))
     assert not any(m.startswith("oracle") or m.startswith(".") or "paper_2402_02116_gb300" in m for m in mods), mods
+
+
+def test_the_cpp_oracle_includes_nothing_from_the_library():
+    """The C++ oracle's sources include only the standard library (and OpenMP): no header of the
+    CUDA library, no CUDA runtime."""
+    folder = os.path.join(ORACLE, "cpp")
+    for name in os.listdir(folder):
+        if not name.endswith((".cpp", ".h", ".hpp")):
+            continue
+        for line in open(os.path.join(folder, name)):
+            if line.lstrip().startswith("#include"):
+                inc = line.split("#include", 1)[1].strip()
+                assert inc.startswith("<") and "cuda" not in inc and "dbi" not in inc, (name, line)
