@@ -371,10 +371,7 @@ def fp32_peak_probe(dev, sms, iters=1 << 16, reps=10):
 # DRAM bytes of one k_cols launch from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum):
 # (nz, nx, lz, lx) -> (problems in the captured launch, frequencies, bytes). The Green's spectra
 # [nf][3][lx][lz] are read once per launch; the rest grows with the problems a launch processes.
-COLS_DRAM = {
-    # one launch over 6 sources x 6 frequencies (profiles/launches_vti512_64src_6f.md)
-    (512, 512, 1024, 1024): (36, 6, 461_460_224 + 266_047_232),
-}
+COLS_DRAM = {}
 
 
 def column_roofline(w, cell_applies, cols_ms, cols_launches, step_ms, clocks, fp32, sms):
@@ -391,7 +388,8 @@ def column_roofline(w, cell_applies, cols_ms, cols_launches, step_ms, clocks, fp
             "peak_nominal_source": f"{sms} SMs (device query) x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled median)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["frac_of_nominal"] = roof["achieved"] / roof["peak_nominal"]
-    roof["kernel"] = "k_cols (column FFTs x Green's tensor x inverse column FFTs)"
+    roof["kernel"] = ("k_cols_split (column FFTs as pairs of 512-point transforms x Green's tensor x inverse)"
+                      if w.lz == 1024 else "k_cols (column FFTs x Green's tensor x inverse column FFTs)")
     roof["flops_per_cell_apply"] = cols_flops_per_cell_apply(w)
     roof["algorithmic_bytes_per_cell_apply"] = cols_bytes_per_cell_apply(w)
     per_launch_problems = cell_applies / (w.nz * w.nx) / max(cols_launches, 1)

@@ -150,7 +150,9 @@ int spectral_chunk(const dbi_grid *g, int B, int precision) {
 }
 
 size_t bytes_spectral(const dbi_grid *g, int B, int precision) {
-  return align256(size_t(spectral_chunk(g, B, precision)) * 2 * g->nz * g->lx * csize(precision));
+  const size_t chunk = size_t(spectral_chunk(g, B, precision));
+  const size_t src = split_rows(g->lx, precision) ? chunk * 2 * g->nz * g->nx * csize(precision) : 0;
+  return align256(chunk * 2 * g->nz * g->lx * csize(precision) + src);
 }
 
 size_t bytes_field(const dbi_grid *g, int B, int precision) {

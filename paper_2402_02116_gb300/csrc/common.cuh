@@ -54,6 +54,12 @@ inline bool fft_len_ok(int L) {
   return L >= 16 && L <= 1024 && (L & (L - 1)) == 0;
 }
 
+// Single-grid complex64 batches with FFT length 1024 along x (rows) or z (columns) run those
+// stages as pairs of 512-point transforms (op_split.cuh); split rows also need a contrast-source
+// scratch field per problem of a chunk, placed after the chunk's spectra.
+inline bool split_rows(int lx, int precision) { return precision == DBI_C64 && lx == 1024; }
+inline bool split_cols(int lz, int precision) { return precision == DBI_C64 && lz == 1024; }
+
 // Error reporting (per host thread).
 void set_error(const char *fmt, ...);
 void clear_error();

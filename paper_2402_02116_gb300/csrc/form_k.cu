@@ -292,7 +292,7 @@ template <typename C> static int run_k_typed(const OpArgs &a, cudaStream_t s) {
   p.in_scale = a.in_scale; p.m_scale = a.m_scale; p.out_scale = a.out_scale;
   p.krhat = static_cast<const C *>(a.krhat);
   p.part_out = a.part_out;
-  p.part_count = operator_parts(a.nz, a.lx, a.precision);
+  p.part_count = operator_parts_k(a.nz, a.lx, a.precision);
   int rc = DBI_OK;
   prof_mark(PROF_OPERATOR, false, s);
   prof_mark(PROF_ROWS_FORWARD, false, s);

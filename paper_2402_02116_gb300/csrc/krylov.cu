@@ -357,7 +357,9 @@ static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, voi
   int rc;
   cudaError_t e = cudaMemsetAsync(sb.counters, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(counters)", e);
-  const int nparts = group ? group_parts(op.group) : operator_parts(op.nz, op.lx, op.precision);
+  const int nparts = group    ? group_parts(op.group)
+                     : op.Dhat ? operator_parts_k(op.nz, op.lx, op.precision)
+                               : operator_parts(op.nz, op.lx, op.precision);
   op.stencil = true;
   op.active = nullptr;
   k_absmax<C><<<grid, kRedThreads, 0, s>>>(sp, rhs, sb.partA);

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "group.cuh"
+#include "op_split.cuh"
 #include "op_tiles.cuh"
 #include "operator.cuh"
 #include "tune.cuh"
@@ -35,6 +36,7 @@ template <typename C> struct OpP {
   const C *krhat;
   double *part_out;
   int part_count;
+  C *S;  // [slots][2][nz][nx] contrast-source scratch of the split row stage (L = 1024), or NULL
 };
 
 // Problem of this CTA's launch slot (blockIdx.y); the spectral scratch is indexed by the slot.
@@ -65,6 +67,7 @@ template <typename C> struct BatchTile {
   __device__ __forceinline__ const C *G() const { return p.Ghat + size_t(f) * 3 * p.lx * p.lz; }
   __device__ __forceinline__ const C *tw() const { return p.tw; }
   __device__ __forceinline__ const C *krhat() const { return p.krhat + fld(); }
+  __device__ __forceinline__ C *S() const { return p.S + size_t(slot) * 2 * p.nz * p.nx; }
   __device__ __forceinline__ double *part() const { return p.part_out + size_t(b) * p.part_count * kRedSlots; }
   __device__ __forceinline__ Rl w2() const {
     const double om = p.omega[f];
@@ -101,6 +104,42 @@ __global__ void __launch_bounds__(kTileThreads, Cfg<C>::rowInvMinBlocks) k_rows_
                                    reinterpret_cast<C *>(smem_raw));
 }
 
+// Stages of the L = 1024 complex64 operator as pairs of 512-point transforms (op_split.cuh).
+__global__ void __launch_bounds__(kTileThreads) k_source_split(OpP<float2> p) {
+  const int b = problem_of(p), f = p.fidx[b];
+  if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchTile<float2> a{p, b, int(blockIdx.y), f};
+  source_tile(a, blockIdx.x, reinterpret_cast<float2 *>(smem_raw), a.S());
+}
+
+template <bool STENCIL>
+__global__ void __launch_bounds__(kTileThreads, 2) k_rows_forward_split(OpP<float2> p) {
+  const int b = problem_of(p), f = p.fidx[b];
+  if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchTile<float2> a{p, b, int(blockIdx.y), f};
+  float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+  if constexpr (STENCIL) rows_forward_tile_split(a, blockIdx.x, smem, a.S(), 1.0f);
+  else rows_forward_tile_split(a, blockIdx.x, smem, a.in(), a.isc());
+}
+
+__global__ void __launch_bounds__(kTileThreads, 2) k_cols_split(OpP<float2> p) {
+  const int b = problem_of(p), f = p.fidx[b];
+  if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cols_tile_split(BatchTile<float2>{p, b, int(blockIdx.y), f}, blockIdx.x, reinterpret_cast<float2 *>(smem_raw));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kTileThreads, 2) k_rows_inverse_split(OpP<float2> p) {
+  const int b = problem_of(p), f = p.fidx[b];
+  if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rows_inverse_tile_split<EPI>(BatchTile<float2>{p, b, int(blockIdx.y), f}, blockIdx.x,
+                               reinterpret_cast<float2 *>(smem_raw));
+}
+
 // Calls f.template operator()<V>() with the radix plan chosen for length L (plans differ only
 // when L is not a power of 8).
 template <int L, typename F> inline void with_plan(int precision, F &&f) {
@@ -111,7 +150,7 @@ template <int L, typename F> inline void with_plan(int precision, F &&f) {
 
 // The three kernels for launch slots [s0, s0 + nb) (problems plist[slot], or the slots themselves),
 // each slot using its own part of the spectral scratch.
-template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, cudaStream_t s) {
+template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int cap, cudaStream_t s) {
   using Rl = typename RealOf<C>::type;
   OpP<C> p;
   p.nz = a.nz; p.nx = a.nx; p.lz = a.lz; p.lx = a.lx; p.nf = a.nf;
@@ -134,10 +173,31 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, cuda
   p.part_count = operator_parts(a.nz, a.lx, a.precision);
   p.krhat = static_cast<const C *>(a.krhat);
   p.part_out = a.part_out;
+  p.S = nullptr;
   int rc = DBI_OK;
   const bool stencil = a.stencil;
+  const bool split_r = split_rows(a.lx, a.precision), split_c = split_cols(a.lz, a.precision);
+  if (split_r) p.S = p.T + size_t(cap) * 2 * a.lx * a.nz;  // after the chunk's spectra
   prof_mark(PROF_ROWS_FORWARD, false, s);
-  dispatch_len(a.lx, [&]<int LX>() {
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (split_r) {
+      OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
+      cudaError_t e = cudaSuccess;
+      if (stencil) {
+        const int tiles = ((a.nx + kSrcTX - 1) / kSrcTX) * ((a.nz + kSrcTZ - 1) / kSrcTZ);
+        e = allow_smem(k_source_split, source_smem());
+        if (e == cudaSuccess) k_source_split<<<dim3(tiles, nb), kTileThreads, source_smem(), s>>>(q);
+        rc = e != cudaSuccess ? cuda_fail("k_source_split smem", e) : check_launch("k_source_split");
+        if (rc) return rc;
+      }
+      const dim3 grid((a.nz + kSplitRows - 1) / kSplitRows, nb);
+      auto kern = stencil ? k_rows_forward_split<true> : k_rows_forward_split<false>;
+      e = allow_smem(kern, split_rows_smem());
+      if (e == cudaSuccess) kern<<<grid, kTileThreads, split_rows_smem(), s>>>(q);
+      rc = e != cudaSuccess ? cuda_fail("k_rows_forward_split smem", e) : check_launch("k_rows_forward_split");
+    }
+  }
+  if (!split_r) dispatch_len(a.lx, [&]<int LX>() {
     with_plan<LX>(a.precision, [&]<int V>() {
       using RC = RowCfg<C, LX>;
       const size_t bytes = rows_forward_smem<C, LX>(a.nx, stencil);
@@ -155,7 +215,16 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, cuda
   prof_mark(PROF_ROWS_FORWARD, true, s);
   if (rc) return rc;
   prof_mark(PROF_COLS, false, s);
-  dispatch_len(a.lz, [&]<int LZ>() {
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (split_c) {
+      OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
+      const dim3 grid((a.lx + kSplitRows - 1) / kSplitRows, nb);
+      cudaError_t e = allow_smem(k_cols_split, split_cols_smem());
+      if (e == cudaSuccess) k_cols_split<<<grid, kTileThreads, split_cols_smem(), s>>>(q);
+      rc = e != cudaSuccess ? cuda_fail("k_cols_split smem", e) : check_launch("k_cols_split");
+    }
+  }
+  if (!split_c) dispatch_len(a.lz, [&]<int LZ>() {
     with_plan<LZ>(a.precision, [&]<int V>() {
       using CF = ColCfg<C, LZ>;
       const size_t bytes = cols_smem<C, LZ>();
@@ -168,7 +237,17 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, cuda
   prof_mark(PROF_COLS, true, s);
   if (rc) return rc;
   prof_mark(PROF_ROWS_INVERSE, false, s);
-  dispatch_len(a.lx, [&]<int LX>() {
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (split_r) {
+      OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
+      const dim3 grid((a.nz + kSplitRows - 1) / kSplitRows, nb);
+      auto kern = a.epi == 1 ? k_rows_inverse_split<1> : a.epi == 2 ? k_rows_inverse_split<2> : k_rows_inverse_split<0>;
+      cudaError_t e = allow_smem(kern, split_rows_smem());
+      if (e == cudaSuccess) kern<<<grid, kTileThreads, split_rows_smem(), s>>>(q);
+      rc = e != cudaSuccess ? cuda_fail("k_rows_inverse_split smem", e) : check_launch("k_rows_inverse_split");
+    }
+  }
+  if (!split_r) dispatch_len(a.lx, [&]<int LX>() {
     with_plan<LX>(a.precision, [&]<int V>() {
       using RC = RowCfg<C, LX>;
       const size_t bytes = rows_inverse_smem<C, LX>();
@@ -196,12 +275,17 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
   int rc = DBI_OK;
   prof_mark(PROF_OPERATOR, false, s);
   for (int s0 = 0; s0 < nb && rc == DBI_OK; s0 += chunk)
-    rc = run_chunk<C>(a, s0, std::min(chunk, nb - s0), s);
+    rc = run_chunk<C>(a, s0, std::min(chunk, nb - s0), chunk, s);
   prof_mark(PROF_OPERATOR, true, s);
   return rc;
 }
 
 int operator_parts(int nz, int lx, int precision) {
+  if (split_rows(lx, precision)) return (nz + kSplitRows - 1) / kSplitRows;
+  return operator_parts_k(nz, lx, precision);
+}
+
+int operator_parts_k(int nz, int lx, int precision) {
   int rows = 1;
   auto pick = [&](auto tag) {
     using C = decltype(tag);

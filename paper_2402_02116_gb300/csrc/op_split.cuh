@@ -1,0 +1,319 @@
+// LS-operator stages for an FFT length L = 2M = 1024 (complex64), where every transform of the
+// operator is half-pruned: the forward row and column transforms read nz <= M (nx <= M) non-zero
+// points, and the inverse ones are needed at the first M points only (lz >= 2 nz - 1).
+//
+// A half-pruned length-L transform is two length-M transforms. Forward, with x_j = 0 for j >= M:
+//   X[2m + q] = sum_{j<M} (x_j W_L^{jq}) W_M^{jm},      q = 0, 1,
+// i.e. the M-point DFTs of x and of x_j W_L^j give the even and the odd outputs. Inverse, for the
+// first M outputs:
+//   y_j = sum_m Y[2m] W_M^{-jm} + W_L^{-j} sum_m Y[2m + 1] W_M^{-jm},   j < M.
+// The register FFT of length M = 512 (three radix-8 passes, two shared-memory exchanges) replaces
+// the length-1024 one (four passes, three exchanges, half of the first or last pass idle), which
+// cuts the exchanges by a third; with 64 threads per line a 256-thread CTA takes four rows, so
+// the row stages read and write the column-major spectra in 32-byte runs (one sector).
+//
+// The contrast source is formed by its own kernel (source_tile) into a scratch field, so that the
+// row transform needs no halo rows and few registers.
+#pragma once
+
+#include "op_tiles.cuh"
+
+namespace dbi {
+
+constexpr int kSplitL = 1024, kSplitM = 512;
+constexpr int kSplitT = kSplitM / 8;                  // threads per line (64)
+constexpr int kSplitRows = kTileThreads / kSplitT;    // rows (or columns) per 256-thread tile (4)
+constexpr int kSplitLP = RegFFT<float2, kSplitM>::LP; // padded line in shared memory
+constexpr int kTwStride = kTwiddleN / kSplitL;        // W_L^j = tw[j * kTwStride]
+
+// Transposition tile of the row stages, one component at a time: [rows][KP]. A thread's pair of
+// points (2k, 2k + 1) is one 16-byte access, and with KP = 8 mod 16 the column-major reads and
+// writes of four rows at a time hit every bank exactly twice per warp (the minimum).
+constexpr int kSplitKP = kSplitL + 8;
+
+// Shared memory (bytes) of the split stages: the lines of one parity (two per row or column) and,
+// for the row stages, the transposition tile of one component.
+inline size_t split_lines_smem() { return size_t(2) * kSplitRows * kSplitLP * sizeof(float2); }
+inline size_t split_tile_smem() { return size_t(kSplitRows) * kSplitKP * sizeof(float2); }
+inline size_t split_rows_smem() { return std::max(split_lines_smem(), split_tile_smem()); }
+inline size_t split_cols_smem() { return split_lines_smem(); }
+
+// Contrast source tile of the stencil kernel: TZ rows x TX columns of one problem.
+constexpr int kSrcTX = 32, kSrcTZ = 16;
+inline size_t source_smem() {
+  return (size_t(2) * (kSrcTZ + 4) * (kSrcTX + 4) + size_t(3) * (kSrcTZ + 2) * (kSrcTX + 2)) * sizeof(float2);
+}
+
+// s = w^2 drho u + div(dC : eps(u)) (Eq. 6) on one TZ x TX tile: u (times its input scale) staged
+// with two halo cells on each side (zero outside D), the stress dC eps(u) on one halo cell, then
+// the divergence by central differences; written to S [2][nz][nx] of the problem.
+template <typename A>
+__device__ __forceinline__ void source_tile(const A &a, int tile, float2 *smem, float2 *S) {
+  using C = float2;
+  constexpr int UW = kSrcTX + 4, UH = kSrcTZ + 4, GW = kSrcTX + 2, GH = kSrcTZ + 2;
+  const int nz = a.nz(), nx = a.nx();
+  const int tiles_x = (nx + kSrcTX - 1) / kSrcTX;
+  const int z0 = (tile / tiles_x) * kSrcTZ, x0 = (tile % tiles_x) * kSrcTX;
+  const size_t plane = size_t(nz) * nx;
+  C *su = smem;                              // [2][UH][UW], rows z0 - 2.., columns x0 - 2..
+  C *sg = smem + size_t(2) * UH * UW;        // [3][GH][GW], rows z0 - 1.., columns x0 - 1..
+  const float isc = a.isc(), ms = a.ms(), f = a.inv2h();
+  const C *u1 = a.in(), *u3 = u1 + plane;
+  for (int i = threadIdx.x; i < UH * UW; i += kTileThreads) {
+    const int r = i / UW, c = i - r * UW, z = z0 - 2 + r, x = x0 - 2 + c;
+    const bool in = z >= 0 && z < nz && x >= 0 && x < nx;
+    su[i] = in ? cscale(__ldg(u1 + size_t(z) * nx + x), isc) : czero<C>();
+    su[UH * UW + i] = in ? cscale(__ldg(u3 + size_t(z) * nx + x), isc) : czero<C>();
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < GH * GW; i += kTileThreads) {
+    const int r = i / GW, c = i - r * GW, z = z0 - 1 + r, x = x0 - 1 + c;
+    C s1 = czero<C>(), s3 = czero<C>(), s5 = czero<C>();
+    if (z >= 0 && z < nz && x >= 0 && x < nx) {
+      const C *p1 = su + (r + 1) * UW + c + 1, *p3 = su + UH * UW + (r + 1) * UW + c + 1;
+      const C e1 = cscale(csub(p1[1], p1[-1]), f);
+      const C e3 = cscale(csub(p3[UW], p3[-UW]), f);
+      const C e5 = cscale(cadd(csub(p1[UW], p1[-UW]), csub(p3[1], p3[-1])), f);
+      const size_t cell = size_t(z) * nx + x;
+      const float d11 = (__ldg(a.m() + 1 * plane + cell) - a.ref(1)) * ms;
+      const float d13 = (__ldg(a.m() + 2 * plane + cell) - a.ref(2)) * ms;
+      const float d33 = (__ldg(a.m() + 3 * plane + cell) - a.ref(3)) * ms;
+      const float d55 = (__ldg(a.m() + 4 * plane + cell) - a.ref(4)) * ms;
+      s1 = cadd(cscale(e1, d11), cscale(e3, d13));
+      s3 = cadd(cscale(e1, d13), cscale(e3, d33));
+      s5 = cscale(e5, d55);
+    }
+    sg[i] = s1;
+    sg[GH * GW + i] = s3;
+    sg[2 * GH * GW + i] = s5;
+  }
+  __syncthreads();
+  const float w2 = a.w2();
+  C *S1 = S, *S3 = S + plane;
+  for (int i = threadIdx.x; i < kSrcTZ * kSrcTX; i += kTileThreads) {
+    const int r = i / kSrcTX, c = i - r * kSrcTX, z = z0 + r, x = x0 + c;
+    if (z >= nz || x >= nx) continue;
+    const C *g1 = sg + (r + 1) * GW + c + 1, *g3 = g1 + GH * GW, *g5 = g1 + 2 * GH * GW;
+    const C o1 = cscale(cadd(csub(g1[1], g1[-1]), csub(g5[GW], g5[-GW])), f);
+    const C o3 = cscale(cadd(csub(g5[1], g5[-1]), csub(g3[GW], g3[-GW])), f);
+    const size_t cell = size_t(z) * nx + x;
+    const float wr = w2 * (__ldg(a.m() + cell) - a.ref(0)) * ms;
+    const C *pu = su + (r + 2) * UW + c + 2;
+    S1[cell] = cadd(o1, cscale(pu[0], wr));
+    S3[cell] = cadd(o3, cscale(pu[UH * UW], wr));
+  }
+}
+
+// The two parities of the two components, each an M-point transform held as 8 points per thread:
+// v[q][c][m] is point t + m T of the line of component c and parity q.
+struct SplitLines {
+  float2 *l[2][2];
+};
+
+// Forward M-point transforms of both parities (one exchange set per parity).
+template <bool INV, typename Sync>
+__device__ __forceinline__ void split_fft(float2 (&v)[2][2][8], float2 *const (&lines)[2], int t,
+                                          const TwReg<float2, kSplitM, 0> &tr, Sync &&sync) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) RegPlan<kSplitM, 0>::template run<float2, 2, INV>(v[q], lines, t, tr, sync);
+}
+
+// For CC = 4 columns kx: the forward transform along z (even and odd kz), the 2x2 multiply by
+// Ghat(kz, kx), the inverse transform; the nz outputs written back in place.
+template <typename A>
+__device__ __forceinline__ void cols_tile_split(const A &a, int tile, float2 *smem) {
+  using C = float2;
+  constexpr int T = kSplitT, CC = kSplitRows, LP = kSplitLP;
+  const int col = threadIdx.x / T, t = threadIdx.x - col * T;
+  const int kx = tile * CC + col;
+  const int nz = a.nz(), lx = a.lx();
+  const bool live = kx < lx;
+  const C *tw = a.tw();
+  C *c0 = a.T() + size_t(kx) * nz, *c1 = a.T() + (size_t(lx) + kx) * nz;
+  const TwReg<C, kSplitM, 0> tr(t, tw);
+  C v[2][2][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int z = t + m * T;
+    const bool in = live && z < nz;
+    const C x0 = in ? c0[z] : czero<C>(), x1 = in ? c1[z] : czero<C>();
+    const C w = __ldg(tw + z * kTwStride);  // W_L^z
+    v[0][0][m] = x0;
+    v[0][1][m] = x1;
+    v[1][0][m] = hmul(x0, w);
+    v[1][1][m] = hmul(x1, w);
+  }
+  C *const lines[2] = {smem + size_t(col) * LP, smem + size_t(CC + col) * LP};
+  split_fft<false>(v, lines, t, tr, RowSync<T>{1 + col});
+  if (live) {
+    const size_t plane = size_t(lx) * kSplitL;
+    const float4 *G = reinterpret_cast<const float4 *>(a.G() + size_t(kx) * kSplitL);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + m * T;  // kz = 2k (even) and 2k + 1 (odd): one 16-byte load per table
+      const float4 g11 = __ldg(G + k), g13 = __ldg(G + plane / 2 + k), g33 = __ldg(G + plane + k);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const C a11 = q ? make_float2(g11.z, g11.w) : make_float2(g11.x, g11.y);
+        const C a13 = q ? make_float2(g13.z, g13.w) : make_float2(g13.x, g13.y);
+        const C a33 = q ? make_float2(g33.z, g33.w) : make_float2(g33.x, g33.y);
+        const C s1 = v[q][0][m], s3 = v[q][1][m];
+        v[q][0][m] = cadd(cmul(a11, s1), cmul(a13, s3));
+        v[q][1][m] = cadd(cmul(a13, s1), cmul(a33, s3));
+      }
+    }
+  }
+  split_fft<true>(v, lines, t, tr, RowSync<T>{1 + col});
+  if (live) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int z = t + m * T;
+      if (z < nz) {
+        const C w = cconj(__ldg(tw + z * kTwStride));  // W_L^{-z}
+        c0[z] = cadd(v[0][0][m], cmul(w, v[1][0][m]));
+        c1[z] = cadd(v[0][1][m], cmul(w, v[1][1][m]));
+      }
+    }
+  }
+}
+
+// Four rows z0 .. z0 + 3: the source rows (from the stencil kernel, or the raw input times its
+// scale), the forward transform along x (even and odd kx), transposed through shared memory into
+// the column-major spectra T[c][kx][z] in runs of four rows.
+template <typename A>
+__device__ __forceinline__ void rows_forward_tile_split(const A &a, int tile, float2 *smem, const float2 *src,
+                                                        float scale) {
+  using C = float2;
+  constexpr int T = kSplitT, ROWS = kSplitRows, LP = kSplitLP, KP = kSplitKP;
+  const int z0 = tile * ROWS;
+  const int nz = a.nz(), nx = a.nx();
+  const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
+  const size_t plane = size_t(nz) * nx;
+  const C *tw = a.tw();
+  const TwReg<C, kSplitM, 0> tr(t, tw);
+  C v[2][2][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int x = t + m * T;
+    const bool in = z < nz && x < nx;
+    const C s0 = in ? cscale(__ldg(src + size_t(z) * nx + x), scale) : czero<C>();
+    const C s1 = in ? cscale(__ldg(src + plane + size_t(z) * nx + x), scale) : czero<C>();
+    const C w = __ldg(tw + x * kTwStride);
+    v[0][0][m] = s0;
+    v[0][1][m] = s1;
+    v[1][0][m] = hmul(s0, w);
+    v[1][1][m] = hmul(s1, w);
+  }
+  C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
+  split_fft<false>(v, lines, t, tr, RowSync<T>{1 + rr});
+  // transpose one component at a time through tile[rr][kx] (the lines' memory is free now)
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    __syncthreads();
+    float4 *row = reinterpret_cast<float4 *>(smem + size_t(rr) * KP);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const C e = v[0][c][m], o = v[1][c][m];  // kx = 2k and 2k + 1
+      row[t + m * T] = make_float4(e.x, e.y, o.x, o.y);
+    }
+    __syncthreads();
+    C *Tc = a.T() + size_t(c) * a.lx() * nz;
+    for (int idx = threadIdx.x; idx < kSplitL * ROWS; idx += kTileThreads) {
+      const int r = idx % ROWS, kx = idx / ROWS;
+      if (z0 + r < nz) Tc[size_t(kx) * nz + z0 + r] = smem[size_t(r) * KP + kx];
+    }
+  }
+}
+
+// Four rows: the spectra T[c][kx][z0 .. z0 + 3] through a transposition tile, the inverse
+// transform along x (even and odd kx), y_x = even + W_L^{-x} odd for x < nx, then the epilogue of
+// rows_inverse_tile: out = ident - scale * y (or the scaled y) with the fused inner products.
+template <int EPI, typename A>
+__device__ __forceinline__ void rows_inverse_tile_split(const A &a, int tile, float2 *smem) {
+  using C = float2;
+  constexpr int T = kSplitT, ROWS = kSplitRows, LP = kSplitLP, KP = kSplitKP;
+  const int z0 = tile * ROWS;
+  const int nz = a.nz(), nx = a.nx();
+  const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
+  const C *tw = a.tw();
+  const TwReg<C, kSplitM, 0> tr(t, tw);
+  C v[2][2][8];
+  constexpr int NLD = kSplitL * ROWS / kTileThreads;  // 16 loads per thread and component
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const C *Tc = a.T() + size_t(c) * a.lx() * nz;
+    C ld[NLD];
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {  // all loads in flight before the shared-memory stores
+      const int idx = threadIdx.x + i * kTileThreads, r = idx % ROWS, kx = idx / ROWS;
+      ld[i] = z0 + r < nz ? Tc[size_t(kx) * nz + z0 + r] : czero<C>();
+    }
+    if (c) __syncthreads();  // the previous component's tile has been read
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int idx = threadIdx.x + i * kTileThreads, r = idx % ROWS, kx = idx / ROWS;
+      smem[size_t(r) * KP + kx] = ld[i];
+    }
+    __syncthreads();
+    const float4 *row = reinterpret_cast<const float4 *>(smem + size_t(rr) * KP);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const float4 eo = row[t + m * T];  // kx = 2k and 2k + 1
+      v[0][c][m] = make_float2(eo.x, eo.y);
+      v[1][c][m] = make_float2(eo.z, eo.w);
+    }
+  }
+  __syncthreads();  // the lines reuse the tile's memory
+  C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
+  split_fft<true>(v, lines, t, tr, RowSync<T>{1 + rr});
+  C y[2][8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const C w = cconj(__ldg(tw + (t + m * T) * kTwStride));
+#pragma unroll
+    for (int c = 0; c < 2; ++c) y[c][m] = cadd(v[0][c][m], cmul(w, v[1][c][m]));
+  }
+  const float osc = a.osc();
+  const size_t base = size_t(z) * nx;
+  float a0 = 0, a1 = 0, a2 = 0;
+  if (z < nz) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      C id[8], h[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int x = t + m * T;
+        const size_t o = base + size_t(c) * nz * nx + x;
+        id[m] = (a.ident() && x < nx) ? __ldg(a.ident() + o) : czero<C>();
+        if constexpr (EPI == 1) h[m] = x < nx ? __ldg(a.krhat() + o) : czero<C>();
+      }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int x = t + m * T;
+        if (x < nx) {
+          const size_t o = base + size_t(c) * nz * nx + x;
+          const C r = cscale(y[c][m], osc);
+          const C w = a.ident() ? csub(id[m], r) : r;
+          a.out()[o] = w;
+          if constexpr (EPI == 1) {  // conj(rhat) w
+            a0 += h[m].x * w.x + h[m].y * w.y;
+            a1 += h[m].x * w.y - h[m].y * w.x;
+          } else if constexpr (EPI == 2) {  // conj(w) id and |w|^2
+            a0 += w.x * id[m].x + w.y * id[m].y;
+            a1 += w.x * id[m].y - w.y * id[m].x;
+            a2 += w.x * w.x + w.y * w.y;
+          }
+        }
+      }
+    }
+  }
+  if constexpr (EPI == 1) {
+    float acc[2] = {a0, a1};
+    block_sum_store<2>(acc, a.part() + size_t(tile) * kRedSlots);
+  } else if constexpr (EPI == 2) {
+    float acc[3] = {a0, a1, a2};
+    block_sum_store<3>(acc, a.part() + size_t(tile) * kRedSlots);
+  }
+}
+
+}  // namespace dbi

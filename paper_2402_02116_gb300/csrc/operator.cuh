@@ -64,8 +64,11 @@ struct OpArgs {
   void *T2;
 };
 
-// Partials per problem written by the operator kernels (one per CTA row block).
+// Partials per problem written by the operator kernels (one per CTA row block): the single-grid
+// divergence form (operator_parts) and the paper-literal form (operator_parts_k, whose row stages
+// keep 2048 / L rows per tile at every length).
 int operator_parts(int nz, int lx, int precision);
+int operator_parts_k(int nz, int lx, int precision);
 
 int run_operator(const OpArgs &a, cudaStream_t s);
 int run_form_k(const OpArgs &a, cudaStream_t s);
