@@ -105,12 +105,12 @@ __global__ void __launch_bounds__(kTileThreads, Cfg<C>::rowInvMinBlocks) k_rows_
 }
 
 // Stages of the L = 1024 complex64 operator as pairs of 512-point transforms (op_split.cuh).
-__global__ void __launch_bounds__(kTileThreads) k_source_split(OpP<float2> p) {
+__global__ void __launch_bounds__(kSrcThreads) k_source_split(OpP<float2> p) {
   const int b = problem_of(p), f = p.fidx[b];
   if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BatchTile<float2> a{p, b, int(blockIdx.y), f};
-  source_tile(a, blockIdx.x, reinterpret_cast<float2 *>(smem_raw), a.S());
+  source_rows(a, blockIdx.x, reinterpret_cast<float2 *>(smem_raw), a.S());
 }
 
 template <bool STENCIL>
@@ -184,9 +184,9 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int 
       OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
       cudaError_t e = cudaSuccess;
       if (stencil) {
-        const int tiles = ((a.nx + kSrcTX - 1) / kSrcTX) * ((a.nz + kSrcTZ - 1) / kSrcTZ);
+        const int chunks = (a.nz + kSrcRows - 1) / kSrcRows;
         e = allow_smem(k_source_split, source_smem());
-        if (e == cudaSuccess) k_source_split<<<dim3(tiles, nb), kTileThreads, source_smem(), s>>>(q);
+        if (e == cudaSuccess) k_source_split<<<dim3(chunks, nb), kSrcThreads, source_smem(), s>>>(q);
         rc = e != cudaSuccess ? cuda_fail("k_source_split smem", e) : check_launch("k_source_split");
         if (rc) return rc;
       }

@@ -12,7 +12,7 @@
 // cuts the exchanges by a third; with 64 threads per line a 256-thread CTA takes four rows, so
 // the row stages read and write the column-major spectra in 32-byte runs (one sector).
 //
-// The contrast source is formed by its own kernel (source_tile) into a scratch field, so that the
+// The contrast source is formed by its own kernel (source_rows) into a scratch field, so that the
 // row transform needs no halo rows and few registers.
 #pragma once
 
@@ -38,69 +38,86 @@ inline size_t split_tile_smem() { return size_t(kSplitRows) * kSplitKP * sizeof(
 inline size_t split_rows_smem() { return std::max(split_lines_smem(), split_tile_smem()); }
 inline size_t split_cols_smem() { return split_lines_smem(); }
 
-// Contrast source tile of the stencil kernel: TZ rows x TX columns of one problem.
-constexpr int kSrcTX = 32, kSrcTZ = 16;
-inline size_t source_smem() {
-  return (size_t(2) * (kSrcTZ + 4) * (kSrcTX + 4) + size_t(3) * (kSrcTZ + 2) * (kSrcTX + 2)) * sizeof(float2);
-}
+// Contrast source of the stencil kernel: one thread per column (nx <= M = 512 columns, the zero
+// columns x = -1 and x = nx on either side), a chunk of kSrcRows rows per CTA walked downwards.
+constexpr int kSrcThreads = kSplitM, kSrcRows = 32, kSrcW = kSrcThreads + 2;
+inline size_t source_smem() { return size_t(8) * kSrcW * sizeof(float2); }
 
-// s = w^2 drho u + div(dC : eps(u)) (Eq. 6) on one TZ x TX tile: u (times its input scale) staged
-// with two halo cells on each side (zero outside D), the stress dC eps(u) on one halo cell, then
-// the divergence by central differences; written to S [2][nz][nx] of the problem.
+// s = w^2 drho u + div(dC : eps(u)) (Eq. 6) on rows [zb, zb + kSrcRows) of one problem, written to
+// S [2][nz][nx]. Row by row: u of the next row is loaded (times the input scale; zero outside D),
+// the stress sigma = dC eps(u) of the row above it is formed from u one row up and down (held in
+// registers) and u one column left and right (shared memory), and the source of the row above
+// that from sigma5, sigma3 one row up and down (registers) and sigma1, sigma5 one column left and
+// right (shared memory). Every thread takes part in every barrier.
 template <typename A>
-__device__ __forceinline__ void source_tile(const A &a, int tile, float2 *smem, float2 *S) {
+__device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem, float2 *S) {
   using C = float2;
-  constexpr int UW = kSrcTX + 4, UH = kSrcTZ + 4, GW = kSrcTX + 2, GH = kSrcTZ + 2;
-  const int nz = a.nz(), nx = a.nx();
-  const int tiles_x = (nx + kSrcTX - 1) / kSrcTX;
-  const int z0 = (tile / tiles_x) * kSrcTZ, x0 = (tile % tiles_x) * kSrcTX;
+  const int nz = a.nz(), nx = a.nx(), x = threadIdx.x, zb = chunk * kSrcRows;
+  const int ze = min(zb + kSrcRows, nz);
   const size_t plane = size_t(nz) * nx;
-  C *su = smem;                              // [2][UH][UW], rows z0 - 2.., columns x0 - 2..
-  C *sg = smem + size_t(2) * UH * UW;        // [3][GH][GW], rows z0 - 1.., columns x0 - 1..
-  const float isc = a.isc(), ms = a.ms(), f = a.inv2h();
-  const C *u1 = a.in(), *u3 = u1 + plane;
-  for (int i = threadIdx.x; i < UH * UW; i += kTileThreads) {
-    const int r = i / UW, c = i - r * UW, z = z0 - 2 + r, x = x0 - 2 + c;
-    const bool in = z >= 0 && z < nz && x >= 0 && x < nx;
-    su[i] = in ? cscale(__ldg(u1 + size_t(z) * nx + x), isc) : czero<C>();
-    su[UH * UW + i] = in ? cscale(__ldg(u3 + size_t(z) * nx + x), isc) : czero<C>();
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < GH * GW; i += kTileThreads) {
-    const int r = i / GW, c = i - r * GW, z = z0 - 1 + r, x = x0 - 1 + c;
+  const bool col = x < nx;
+  const float isc = a.isc(), ms = a.ms(), f = a.inv2h(), w2 = a.w2();
+  const float r1 = a.ref(1), r2 = a.ref(2), r3 = a.ref(3), r4 = a.ref(4), r0 = a.ref(0);
+  const C *u1p = a.in(), *u3p = u1p + plane;
+  const float *m = a.m();
+  // shared rows (index x + 1; entries 0 and nx + 1 .. stay zero): u1, u3 and sigma1, sigma5, two
+  // slots each by row parity
+  C *su = smem, *sg = smem + 4 * kSrcW;
+  auto U = [&](int slot, int c) { return su + (slot * 2 + c) * kSrcW + 1; };
+  auto G = [&](int slot, int c) { return sg + (slot * 2 + c) * kSrcW + 1; };
+  for (int i = threadIdx.x; i < 8 * kSrcW; i += kSrcThreads) smem[i] = czero<C>();
+  auto load_u = [&](int z, C &v1, C &v3) {
+    const bool in = col && z >= 0 && z < nz;
+    v1 = in ? cscale(__ldg(u1p + size_t(z) * nx + x), isc) : czero<C>();
+    v3 = in ? cscale(__ldg(u3p + size_t(z) * nx + x), isc) : czero<C>();
+  };
+  // window: u at rows j - 1, j, j + 1; sigma3, sigma5 at rows j - 2, j - 1, j
+  C ua1, ua3, ub1, ub3, uc1, uc3;  // u(j - 1), u(j), u(j + 1)
+  C s3a = czero<C>(), s5a = czero<C>(), s3b = czero<C>(), s5b = czero<C>();  // sigma(j - 2), sigma(j - 1)
+  const int j0 = zb - 1;
+  load_u(j0 - 1, ua1, ua3);
+  load_u(j0, ub1, ub3);
+  __syncthreads();  // the zero fill precedes every row store
+  U(j0 & 1, 0)[x] = ub1;
+  U(j0 & 1, 1)[x] = ub3;
+  for (int j = j0; j <= ze; ++j) {
+    load_u(j + 1, uc1, uc3);
+    const int sl = j & 1, sn = (j + 1) & 1;
+    U(sn, 0)[x] = uc1;
+    U(sn, 1)[x] = uc3;
+    __syncthreads();
+    // sigma(j, x)
     C s1 = czero<C>(), s3 = czero<C>(), s5 = czero<C>();
-    if (z >= 0 && z < nz && x >= 0 && x < nx) {
-      const C *p1 = su + (r + 1) * UW + c + 1, *p3 = su + UH * UW + (r + 1) * UW + c + 1;
-      const C e1 = cscale(csub(p1[1], p1[-1]), f);
-      const C e3 = cscale(csub(p3[UW], p3[-UW]), f);
-      const C e5 = cscale(cadd(csub(p1[UW], p1[-UW]), csub(p3[1], p3[-1])), f);
-      const size_t cell = size_t(z) * nx + x;
-      const float d11 = (__ldg(a.m() + 1 * plane + cell) - a.ref(1)) * ms;
-      const float d13 = (__ldg(a.m() + 2 * plane + cell) - a.ref(2)) * ms;
-      const float d33 = (__ldg(a.m() + 3 * plane + cell) - a.ref(3)) * ms;
-      const float d55 = (__ldg(a.m() + 4 * plane + cell) - a.ref(4)) * ms;
+    if (col && j >= 0 && j < nz) {
+      const C *r1u = U(sl, 0), *r3u = U(sl, 1);
+      const C e1 = cscale(csub(r1u[x + 1], r1u[x - 1]), f);
+      const C e3 = cscale(csub(uc3, ua3), f);
+      const C e5 = cscale(cadd(csub(uc1, ua1), csub(r3u[x + 1], r3u[x - 1])), f);
+      const size_t cell = size_t(j) * nx + x;
+      const float d11 = (__ldg(m + 1 * plane + cell) - r1) * ms;
+      const float d13 = (__ldg(m + 2 * plane + cell) - r2) * ms;
+      const float d33 = (__ldg(m + 3 * plane + cell) - r3) * ms;
+      const float d55 = (__ldg(m + 4 * plane + cell) - r4) * ms;
       s1 = cadd(cscale(e1, d11), cscale(e3, d13));
       s3 = cadd(cscale(e1, d13), cscale(e3, d33));
       s5 = cscale(e5, d55);
     }
-    sg[i] = s1;
-    sg[GH * GW + i] = s3;
-    sg[2 * GH * GW + i] = s5;
-  }
-  __syncthreads();
-  const float w2 = a.w2();
-  C *S1 = S, *S3 = S + plane;
-  for (int i = threadIdx.x; i < kSrcTZ * kSrcTX; i += kTileThreads) {
-    const int r = i / kSrcTX, c = i - r * kSrcTX, z = z0 + r, x = x0 + c;
-    if (z >= nz || x >= nx) continue;
-    const C *g1 = sg + (r + 1) * GW + c + 1, *g3 = g1 + GH * GW, *g5 = g1 + 2 * GH * GW;
-    const C o1 = cscale(cadd(csub(g1[1], g1[-1]), csub(g5[GW], g5[-GW])), f);
-    const C o3 = cscale(cadd(csub(g5[1], g5[-1]), csub(g3[GW], g3[-GW])), f);
-    const size_t cell = size_t(z) * nx + x;
-    const float wr = w2 * (__ldg(a.m() + cell) - a.ref(0)) * ms;
-    const C *pu = su + (r + 2) * UW + c + 2;
-    S1[cell] = cadd(o1, cscale(pu[0], wr));
-    S3[cell] = cadd(o3, cscale(pu[UH * UW], wr));
+    G(sl, 0)[x] = s1;
+    G(sl, 1)[x] = s5;
+    __syncthreads();
+    // source at row j - 1
+    const int z = j - 1;
+    if (col && z >= zb && z < ze) {
+      const C *g1 = G(sl ^ 1, 0), *g5 = G(sl ^ 1, 1);
+      const C o1 = cscale(cadd(csub(g1[x + 1], g1[x - 1]), csub(s5, s5a)), f);
+      const C o3 = cscale(cadd(csub(g5[x + 1], g5[x - 1]), csub(s3, s3a)), f);
+      const size_t cell = size_t(z) * nx + x;
+      const float wr = w2 * (__ldg(m + cell) - r0) * ms;
+      S[cell] = cadd(o1, cscale(ua1, wr));  // u(j - 1)
+      S[plane + cell] = cadd(o3, cscale(ua3, wr));
+    }
+    ua1 = ub1; ua3 = ub3; ub1 = uc1; ub3 = uc3;
+    s3a = s3b; s5a = s5b; s3b = s3; s5b = s5;
   }
 }
 

@@ -392,3 +392,37 @@ def test_binding_rejects_host_or_mistyped_outputs_with_device_inputs():
     with pytest.raises(dbi.DBIError, match="CUDA tensor"):
         dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat.cpu(), u)
     assert dbi.kernel_launches() == n0
+
+
+# FFT length 1024 (complex64) runs each half-pruned transform as two 512-point transforms and the
+# contrast source by its own kernel in chunks of 32 rows: ragged row and column counts, one row,
+# one column, and 1024 along one axis only.
+SPLIT_SHAPES = [
+    dict(nz=37, nx=300, lz=1024, lx=1024),   # two source chunks, ragged columns
+    dict(nz=1, nx=511, lz=16, lx=1024),      # one row, split rows only
+    dict(nz=500, nx=1, lz=1024, lx=16),      # one column, split columns only
+    dict(nz=70, nx=45, lz=1024, lx=128),     # split columns, a partial source chunk
+    dict(nz=64, nx=512, lz=128, lx=1024, vti=True),  # full-width rows, split rows
+]
+
+
+@pytest.mark.parametrize("shape", SPLIT_SHAPES, ids=lambda s: f"{s['nz']}x{s['nx']}_L{s['lz']}x{s['lx']}")
+def test_length_1024_split_stages(shape):
+    w = inputs.small_case(freqs=(4.0, 15.0), n_src=2, amp=0.12, h=5.0, **shape)
+    P = DeviceProblem(w, dbi.C64)
+    orc = oracle_for(w)
+    u = inputs.seeded_complex((P.B, 2, w.nz, w.nx), 77)
+    out = npy(P.apply(P.to_field(u)))
+    conv = npy(P.convolve(P.to_field(u)))
+    for b, f in enumerate(w.problem_fidx()):
+        want = orc.apply(u[b], w.model, f)
+        assert rel(out[b] - u[b], want - u[b]) < TOL[dbi.C64], b
+        assert rel(conv[b], orc.convolve(u[b].astype(np.complex128), f)) < TOL[dbi.C64], b
+    # the fused inner products of the solver on the same stages
+    u0 = P.incident()
+    x, _, _, code = P.solve(u0, tol=1e-6)
+    assert np.all(npy(code) == dbi.CONVERGED)
+    xs, bs = npy(x).astype(np.complex128), npy(u0).astype(np.complex128)
+    for b, f in enumerate(w.problem_fidx()):
+        ref = orc.solve(bs[b], w.model, f, tol=1e-12)
+        assert rel(xs[b], ref) < 1e-5, b
