@@ -371,7 +371,10 @@ def fp32_peak_probe(dev, sms, iters=1 << 16, reps=10):
 # DRAM bytes of one k_cols launch from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum):
 # (nz, nx, lz, lx) -> (problems in the captured launch, frequencies, bytes). The Green's spectra
 # [nf][3][lx][lz] are read once per launch; the rest grows with the problems a launch processes.
-COLS_DRAM = {}
+COLS_DRAM = {
+    # one k_cols_split launch over 6 sources x 6 frequencies (profiles/operator_kernels_vti512_6src_6f.md)
+    (512, 512, 1024, 1024): (36, 6, 459_338_496 + 259_350_272),
+}
 
 
 def column_roofline(w, cell_applies, cols_ms, cols_launches, step_ms, clocks, fp32, sms):

@@ -48,7 +48,9 @@ inline size_t source_smem() { return size_t(8) * kSrcW * sizeof(float2); }
 // the stress sigma = dC eps(u) of the row above it is formed from u one row up and down (held in
 // registers) and u one column left and right (shared memory), and the source of the row above
 // that from sigma5, sigma3 one row up and down (registers) and sigma1, sigma5 one column left and
-// right (shared memory). Every thread takes part in every barrier.
+// right (shared memory). The global loads of each step are issued one step ahead (u two rows
+// down, the stiffness one row down, the density of the current row), so that their latency
+// overlaps a step's work. Every thread takes part in every barrier.
 template <typename A>
 __device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem, float2 *S) {
   using C = float2;
@@ -57,7 +59,7 @@ __device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem,
   const size_t plane = size_t(nz) * nx;
   const bool col = x < nx;
   const float isc = a.isc(), ms = a.ms(), f = a.inv2h(), w2 = a.w2();
-  const float r1 = a.ref(1), r2 = a.ref(2), r3 = a.ref(3), r4 = a.ref(4), r0 = a.ref(0);
+  const float r0 = a.ref(0), r1 = a.ref(1), r2 = a.ref(2), r3 = a.ref(3), r4 = a.ref(4);
   const C *u1p = a.in(), *u3p = u1p + plane;
   const float *m = a.m();
   // shared rows (index x + 1; entries 0 and nx + 1 .. stay zero): u1, u3 and sigma1, sigma5, two
@@ -66,38 +68,61 @@ __device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem,
   auto U = [&](int slot, int c) { return su + (slot * 2 + c) * kSrcW + 1; };
   auto G = [&](int slot, int c) { return sg + (slot * 2 + c) * kSrcW + 1; };
   for (int i = threadIdx.x; i < 8 * kSrcW; i += kSrcThreads) smem[i] = czero<C>();
+  auto in_d = [&](int z) { return col && z >= 0 && z < nz; };
   auto load_u = [&](int z, C &v1, C &v3) {
-    const bool in = col && z >= 0 && z < nz;
-    v1 = in ? cscale(__ldg(u1p + size_t(z) * nx + x), isc) : czero<C>();
-    v3 = in ? cscale(__ldg(u3p + size_t(z) * nx + x), isc) : czero<C>();
+    const bool in = in_d(z);
+    v1 = in ? __ldg(u1p + size_t(z) * nx + x) : czero<C>();
+    v3 = in ? __ldg(u3p + size_t(z) * nx + x) : czero<C>();
   };
-  // window: u at rows j - 1, j, j + 1; sigma3, sigma5 at rows j - 2, j - 1, j
-  C ua1, ua3, ub1, ub3, uc1, uc3;  // u(j - 1), u(j), u(j + 1)
-  C s3a = czero<C>(), s5a = czero<C>(), s3b = czero<C>(), s5b = czero<C>();  // sigma(j - 2), sigma(j - 1)
+  struct Stiff {
+    float d11, d13, d33, d55;
+  };
+  auto load_stiff = [&](int z, Stiff &d) {
+    const bool in = in_d(z);
+    const size_t cell = size_t(in ? z : 0) * nx + (col ? x : 0);
+    d.d11 = in ? __ldg(m + 1 * plane + cell) : r1;
+    d.d13 = in ? __ldg(m + 2 * plane + cell) : r2;
+    d.d33 = in ? __ldg(m + 3 * plane + cell) : r3;
+    d.d55 = in ? __ldg(m + 4 * plane + cell) : r4;
+  };
+  auto load_rho = [&](int z) { return in_d(z) ? __ldg(m + size_t(z) * nx + x) : r0; };
+  // window: u at rows j - 1, j, j + 1 (scaled); sigma3, sigma5 at rows j - 2, j - 1, j
+  C ua1, ua3, ub1, ub3, uc1, uc3;
+  C s3a = czero<C>(), s5a = czero<C>(), s3b = czero<C>(), s5b = czero<C>();
   const int j0 = zb - 1;
   load_u(j0 - 1, ua1, ua3);
   load_u(j0, ub1, ub3);
+  ua1 = cscale(ua1, isc); ua3 = cscale(ua3, isc);
+  ub1 = cscale(ub1, isc); ub3 = cscale(ub3, isc);
+  C nu1, nu3;  // u(j + 1), loaded one step ahead
+  Stiff nd;    // stiffness of row j
+  float nrho;  // density of row j - 1
+  load_u(j0 + 1, nu1, nu3);
+  load_stiff(j0, nd);
+  nrho = load_rho(j0 - 1);
   __syncthreads();  // the zero fill precedes every row store
   U(j0 & 1, 0)[x] = ub1;
   U(j0 & 1, 1)[x] = ub3;
   for (int j = j0; j <= ze; ++j) {
-    load_u(j + 1, uc1, uc3);
+    uc1 = cscale(nu1, isc);
+    uc3 = cscale(nu3, isc);
+    const Stiff d = nd;
+    const float rho = nrho;
+    load_u(j + 2, nu1, nu3);  // the next step's loads
+    load_stiff(j + 1, nd);
+    nrho = load_rho(j);
     const int sl = j & 1, sn = (j + 1) & 1;
     U(sn, 0)[x] = uc1;
     U(sn, 1)[x] = uc3;
     __syncthreads();
     // sigma(j, x)
     C s1 = czero<C>(), s3 = czero<C>(), s5 = czero<C>();
-    if (col && j >= 0 && j < nz) {
+    if (in_d(j)) {
       const C *r1u = U(sl, 0), *r3u = U(sl, 1);
       const C e1 = cscale(csub(r1u[x + 1], r1u[x - 1]), f);
       const C e3 = cscale(csub(uc3, ua3), f);
       const C e5 = cscale(cadd(csub(uc1, ua1), csub(r3u[x + 1], r3u[x - 1])), f);
-      const size_t cell = size_t(j) * nx + x;
-      const float d11 = (__ldg(m + 1 * plane + cell) - r1) * ms;
-      const float d13 = (__ldg(m + 2 * plane + cell) - r2) * ms;
-      const float d33 = (__ldg(m + 3 * plane + cell) - r3) * ms;
-      const float d55 = (__ldg(m + 4 * plane + cell) - r4) * ms;
+      const float d11 = (d.d11 - r1) * ms, d13 = (d.d13 - r2) * ms, d33 = (d.d33 - r3) * ms, d55 = (d.d55 - r4) * ms;
       s1 = cadd(cscale(e1, d11), cscale(e3, d13));
       s3 = cadd(cscale(e1, d13), cscale(e3, d33));
       s5 = cscale(e5, d55);
@@ -112,7 +137,7 @@ __device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem,
       const C o1 = cscale(cadd(csub(g1[x + 1], g1[x - 1]), csub(s5, s5a)), f);
       const C o3 = cscale(cadd(csub(g5[x + 1], g5[x - 1]), csub(s3, s3a)), f);
       const size_t cell = size_t(z) * nx + x;
-      const float wr = w2 * (__ldg(m + cell) - r0) * ms;
+      const float wr = w2 * (rho - r0) * ms;
       S[cell] = cadd(o1, cscale(ua1, wr));  // u(j - 1)
       S[plane + cell] = cadd(o3, cscale(ua3, wr));
     }
