@@ -12,6 +12,7 @@
 #include "../../include/dbi_group.h"
 #include "group.cuh"
 #include "krylov.cuh"
+#include "op_split.cuh"
 #include "op_tiles.cuh"
 #include "tune.cuh"
 
@@ -65,7 +66,7 @@ Layout layout(const dbi_group *g, int op) {
   l.desc = align256(g->desc.size() * sizeof(GMember));
   l.offs = align256(g->offs.size() * sizeof(long long));
   l.tw = align256(bytes_twiddles(g->precision));
-  l.T = align256(size_t(g->T_elems) * csize(g->precision));
+  l.T = align256(size_t(g->T_elems + g->gl.S_elems) * csize(g->precision));
   l.scales = align256(size_t(g->B) * sizeof(double)) * 3 + 256 + bytes_partials(g->B);
   l.solver = op == DBI_OP_SOLVE ? bytes_solver_fields(size_t(g->field_elems) * csize(g->precision), g->B) : 0;
   l.total = l.desc + l.offs + l.tw + l.T + l.scales + l.solver;
@@ -74,13 +75,14 @@ Layout layout(const dbi_group *g, int op) {
 
 template <typename C> void stage_smem(dbi_group *g) {
   size_t s[4] = {0, 0, 0, 0};
-  for (const GMember &M : g->desc) {
-    dispatch_len(M.lx, [&]<int LX>() {
-      s[0] = std::max(s[0], rows_forward_smem<C, LX>(M.nx, true));
-      s[1] = std::max(s[1], rows_forward_smem<C, LX>(M.nx, false));
-      s[3] = std::max(s[3], rows_inverse_smem<C, LX>());
-    });
-    dispatch_len(M.lz, [&]<int LZ>() { s[2] = std::max(s[2], cols_smem<C, LZ>()); });
+  for (const GMember &M : g->desc) {  // the members the non-split kernels run
+    if (!M.split_rows)
+      dispatch_len(M.lx, [&]<int LX>() {
+        s[0] = std::max(s[0], rows_forward_smem<C, LX>(M.nx, true));
+        s[1] = std::max(s[1], rows_forward_smem<C, LX>(M.nx, false));
+        s[3] = std::max(s[3], rows_inverse_smem<C, LX>());
+      });
+    if (!M.split_cols) dispatch_len(M.lz, [&]<int LZ>() { s[2] = std::max(s[2], cols_smem<C, LZ>()); });
   }
   for (int i = 0; i < 4; ++i) g->gl.smem[i] = s[i];
 }
@@ -152,20 +154,25 @@ extern "C" int dbi_group_create(const dbi_group_member *members, int n, int prec
   g->mem.assign(members, members + n);
   // slots and field / spectra offsets in the caller's order
   std::vector<int> slot0(n);
-  std::vector<long long> f0(n), t0(n);
+  std::vector<long long> f0(n), t0(n), s0(n);
   g->offs.assign(1, 0);
+  long long S_elems = 0;
   for (int k = 0; k < n; ++k) {
     const dbi_grid &gr = members[k].model.grid;
     slot0[k] = g->B;
     f0[k] = g->field_elems;
     t0[k] = g->T_elems;
+    s0[k] = S_elems;
     for (int q = 0; q < members[k].B; ++q) {
       g->field_elems += 2LL * gr.nz * gr.nx;
       g->offs.push_back(g->field_elems);
     }
     g->T_elems += 2LL * members[k].B * gr.lx * gr.nz;
+    if (split_rows(gr.lx, precision)) S_elems += 2LL * members[k].B * gr.nz * gr.nx;
     g->B += members[k].B;
   }
+  g->gl.T_elems = g->T_elems;
+  g->gl.S_elems = S_elems;
   // tile order: decreasing lx, then lz, then the caller's order
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
@@ -173,7 +180,7 @@ extern "C" int dbi_group_create(const dbi_group_member *members, int n, int prec
     const dbi_grid &ga = members[a].model.grid, &gb = members[b].model.grid;
     return ga.lx != gb.lx ? ga.lx > gb.lx : ga.lz > gb.lz;
   });
-  long long tot[3] = {0, 0, 0};
+  long long tot[4] = {0, 0, 0, 0};
   g->gl.parts = 1;
   for (int k : order) {
     const dbi_group_member &U = members[k];
@@ -184,23 +191,29 @@ extern "C" int dbi_group_create(const dbi_group_member *members, int n, int prec
     reference_values(U.model.ref, M.ref);
     M.m = U.model.m; M.Ghat = U.Ghat; M.omega = U.omega; M.fidx = U.fidx;
     M.nf = U.nf; M.B = U.B;
-    M.slot0 = slot0[k]; M.field0 = f0[k]; M.T0 = t0[k];
-    const int rows = 2048 / gr.lx, cols = 2048 / gr.lz;  // rows / columns per tile (op_tiles.cuh)
+    M.slot0 = slot0[k]; M.field0 = f0[k]; M.T0 = t0[k]; M.S0 = s0[k];
+    M.split_rows = split_rows(gr.lx, precision) ? 1 : 0;
+    M.split_cols = split_cols(gr.lz, precision) ? 1 : 0;
+    g->gl.split_rows |= M.split_rows;
+    g->gl.split_cols |= M.split_cols;
+    // rows / columns per tile (op_tiles.cuh; op_split.cuh for the split stages)
+    const int rows = M.split_rows ? kSplitRows : 2048 / gr.lx, cols = M.split_cols ? kSplitRows : 2048 / gr.lz;
     M.tiles[kStageRowsForward] = M.tiles[kStageRowsInverse] = (gr.nz + rows - 1) / rows;
     M.tiles[kStageCols] = (gr.lx + cols - 1) / cols;
-    for (int st = 0; st < 3; ++st) {
+    M.tiles[kStageSource] = M.split_rows ? (gr.nz + kSrcRows - 1) / kSrcRows : 0;
+    for (int st = 0; st < 4; ++st) {
       M.tile0[st] = int(tot[st]);
       tot[st] += (long long)M.tiles[st] * U.B;
     }
     g->gl.parts = std::max(g->gl.parts, M.tiles[kStageRowsForward]);
     g->desc.push_back(M);
   }
-  if (tot[0] > 0x7fffffffLL || tot[1] > 0x7fffffffLL) {
+  if (tot[0] > 0x7fffffffLL || tot[1] > 0x7fffffffLL || tot[3] > 0x7fffffffLL) {
     set_error("group too large: %lld tiles", std::max(tot[0], tot[1]));
     delete g;
     return DBI_ERR_ARG;
   }
-  for (int st = 0; st < 3; ++st) g->gl.total[st] = int(tot[st]);
+  for (int st = 0; st < 4; ++st) g->gl.total[st] = int(tot[st]);
   g->gl.nm = n;
   g->gl.B = g->B;
   if (precision == DBI_C64) stage_smem<float2>(g);
@@ -238,10 +251,11 @@ extern "C" int dbi_group_bind(dbi_group *g, void *work, size_t work_bytes, int o
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Arena ar(work, work_bytes);
-  g->d_desc = static_cast<GMember *>(ar.take(g->desc.size() * sizeof(GMember)));
-  g->d_offs = static_cast<long long *>(ar.take(g->offs.size() * sizeof(long long)));
-  g->tw = ar.take(bytes_twiddles(g->precision));
-  g->T = ar.take(size_t(g->T_elems) * csize(g->precision));
+  // the carves take the sizes of the workspace query's layout, so the two cannot disagree
+  g->d_desc = static_cast<GMember *>(ar.take(l.desc));
+  g->d_offs = static_cast<long long *>(ar.take(l.offs));
+  g->tw = ar.take(l.tw);
+  g->T = ar.take(l.T);  // spectra, then the split-row sources
   g->sc = carve_scales(ar, g->B);
   if (op == DBI_OP_SOLVE) g->sb = carve_solver_fields(ar, size_t(g->field_elems) * csize(g->precision), g->B);
   if (const int crc = ar.check("dbi_group_bind")) return crc;
@@ -270,6 +284,11 @@ extern "C" int dbi_group_bind(dbi_group *g, void *work, size_t work_bytes, int o
     occ[2] = std::min(occ[2], n);
   }
   for (int st = 0; st < 3; ++st) g->max_ctas[st] = std::max(1, occ[st]);
+  if (g->gl.split_rows || g->gl.split_cols) {  // the split kernels: the resident maximum per SM
+    int sp[4] = {0, 0, 0, 0};
+    if ((rc = group_split_occupancy(sp))) return rc;
+    for (int i = 0; i < 4; ++i) g->gl.split_blocks[i] = std::max(1, sp[i]) * std::max(1, g->sms);
+  }
   g->gl.desc = g->d_desc;
   set_blocks(g);
   g->work = work;

@@ -6,7 +6,7 @@
 
 namespace dbi {
 
-enum { kStageRowsForward = 0, kStageCols = 1, kStageRowsInverse = 2 };
+enum { kStageRowsForward = 0, kStageCols = 1, kStageRowsInverse = 2, kStageSource = 3 };
 
 // One member, as the kernels see it (device array in tile order: members by decreasing lx, lz).
 struct GMember {
@@ -21,8 +21,11 @@ struct GMember {
   int slot0;            // global index of the member's first slot
   long long field0;     // element offset of the first slot's field
   long long T0;         // element offset of the first slot's spectra
-  int tile0[3];         // first tile of the member in each stage's tile space
-  int tiles[3];         // tiles per slot in each stage
+  long long S0;         // element offset of the first slot's contrast-source scratch (split rows)
+  int split_rows;       // complex64 with lx = 1024: row stages as pairs of 512-point transforms
+  int split_cols;       // complex64 with lz = 1024: column stage as pairs of 512-point transforms
+  int tile0[4];         // first tile of the member in each stage's tile space (kStage*)
+  int tiles[4];         // tiles per slot in each stage (the source stage: split-row members only)
 };
 
 // Host-side launch description (lives in the plan; passed through OpArgs::group).
@@ -30,11 +33,15 @@ struct GroupLaunch {
   const GMember *desc;   // device [nm]
   int nm;
   int B;                 // slots
-  int total[3];          // tiles per stage
+  int total[4];          // tiles per stage
   size_t smem[4];        // dynamic shared memory: rows forward with stencil, without, cols, rows inverse
   int blocks[3];         // persistent CTAs of each stage's launch
   int parts;             // fused-reduction partials per slot (largest row-tile count)
   signed char plan[11];  // radix plan per log2 of the FFT length
+  int split_rows, split_cols;  // some member runs split row / column stages
+  int split_blocks[4];   // persistent CTAs of the split kernels: source, rows forward, cols, rows inverse
+  long long T_elems;     // spectra of every slot (elements)
+  long long S_elems;     // contrast-source scratch of the split-row slots, after the spectra
 };
 
 inline int group_parts(const GroupLaunch *g) { return g->parts; }
@@ -45,6 +52,8 @@ template <typename C> int run_group_typed(const OpArgs &a, cudaStream_t s);
 // Resident CTAs per SM of one stage's kernel with `smem` bytes (stage: 0 rows forward with
 // stencil, 1 rows forward without, 2 cols, 3 rows inverse with epilogue epi).
 template <typename C> int group_occupancy(int stage, int epi, size_t smem, int *per_sm);
+// Resident CTAs per SM of the split kernels (complex64): [source, rows forward, cols, rows inverse].
+int group_split_occupancy(int per_sm[4]);
 
 int run_group_operator(const OpArgs &a, cudaStream_t s);
 

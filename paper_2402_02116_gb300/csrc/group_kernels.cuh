@@ -5,6 +5,7 @@
 #pragma once
 
 #include "group.cuh"
+#include "op_split.cuh"
 #include "op_tiles.cuh"
 
 namespace dbi {
@@ -16,6 +17,7 @@ template <typename C> struct GroupP {
   const C *ident;
   C *out;
   C *T;
+  C *S;  // contrast-source scratch of the split-row slots (element offsets GMember::S0)
   const C *tw;
   const int *active;
   const double *in_scale, *m_scale, *out_scale;
@@ -63,12 +65,19 @@ __device__ __forceinline__ TileArgs<C> group_args(const GroupP<C> &g, const GMem
   return a;
 }
 
-// Runs body(M, b, q, f, tt) for every tile of `stage` assigned to this CTA whose slot is active.
-template <int STAGE, typename C, typename Body>
+// Whether member M runs `stage` on the split (pairs of 512-point transforms) kernels.
+__device__ __forceinline__ int split_stage(const GMember &M, int stage) {
+  return stage == kStageCols ? M.split_cols : M.split_rows;
+}
+
+// Runs body(M, b, q, f, tt) for every tile of `stage` assigned to this CTA whose slot is active and
+// whose member runs the stage on this kind of kernel (SPLIT = 1: the split kernels, 0: the others).
+template <int STAGE, int SPLIT = 0, typename C, typename Body>
 __device__ __forceinline__ void for_tiles(const GroupP<C> &g, Body &&body) {
   for (int tile = blockIdx.x; tile < g.total; tile += gridDim.x) {
     const int i = find_member(g.desc, g.nm, STAGE, tile);
     const GMember &M = g.desc[i];
+    if (split_stage(M, STAGE) != SPLIT) continue;  // uniform per CTA
     const int rel = tile - M.tile0[STAGE];
     const int q = rel / M.tiles[STAGE], tt = rel - q * M.tiles[STAGE];
     const int b = M.slot0 + q;
@@ -143,6 +152,82 @@ __global__ void __launch_bounds__(kTileThreads, Cfg<C>::rowInvMinBlocks) kg_rows
   });
 }
 
+// Split kernels of the members with FFT length 1024 (complex64 only, op_split.cuh): the contrast
+// source (512 threads, 32 rows per tile), the rows and columns as pairs of 512-point transforms (4
+// rows or columns per tile). Templates on the element type so that only the complex64 unit
+// instantiates them.
+template <typename C> __device__ __forceinline__ C *group_S(const GroupP<C> &g, const GMember &M, int q) {
+  return g.S + size_t(M.S0) + size_t(q) * 2 * M.nz * M.nx;
+}
+
+template <typename C> __global__ void __launch_bounds__(kSrcThreads) kg_source_split(GroupP<C> g) {
+  static_assert(sizeof(C) == sizeof(float2), "complex64 only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageSource, 1>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    source_rows(group_args(g, M, b, q, f), tt, smem, group_S(g, M, q));
+  });
+}
+
+template <typename C, bool STENCIL>
+__global__ void __launch_bounds__(kTileThreads, 2) kg_rows_forward_split(GroupP<C> g) {
+  static_assert(sizeof(C) == sizeof(float2), "complex64 only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageRowsForward, 1>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    const TileArgs<C> a = group_args(g, M, b, q, f);
+    if constexpr (STENCIL) rows_forward_tile_split(a, tt, smem, group_S(g, M, q), 1.0f);
+    else rows_forward_tile_split(a, tt, smem, a.in(), a.isc());
+  });
+}
+
+// (a call of its own: inlined into the tile loop the body spills; called, it keeps its registers)
+template <typename C> __device__ __noinline__ void call_cols_split(const TileArgs<C> &a, int tt, C *smem) {
+  cols_tile_split(a, tt, smem);
+}
+
+template <typename C> __global__ void __launch_bounds__(kTileThreads, 2) kg_cols_split(GroupP<C> g) {
+  static_assert(sizeof(C) == sizeof(float2), "complex64 only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageCols, 1>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    call_cols_split(group_args(g, M, b, q, f), tt, smem);
+  });
+}
+
+template <typename C, int EPI>
+__global__ void __launch_bounds__(kTileThreads, 2) kg_rows_inverse_split(GroupP<C> g) {
+  static_assert(sizeof(C) == sizeof(float2), "complex64 only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageRowsInverse, 1>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    rows_inverse_tile_split<EPI>(group_args(g, M, b, q, f), tt, smem);
+  });
+}
+
+template <typename C> int group_split_occupancy_impl(int per_sm[4]) {
+  cudaError_t e = cudaSuccess;
+  auto occ = [&](auto kernel, int threads, size_t smem, int *n) {
+    if (e != cudaSuccess) return;
+    e = allow_smem(kernel, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel, threads, smem);
+  };
+  occ(kg_source_split<C>, kSrcThreads, source_smem(), &per_sm[0]);
+  int x = 0, y = 0;
+  occ(kg_rows_forward_split<C, true>, kTileThreads, split_rows_smem(), &x);
+  occ(kg_rows_forward_split<C, false>, kTileThreads, split_rows_smem(), &y);
+  per_sm[1] = std::min(x, y);
+  occ(kg_cols_split<C>, kTileThreads, split_cols_smem(), &per_sm[2]);
+  per_sm[3] = 1 << 20;
+  occ(kg_rows_inverse_split<C, 0>, kTileThreads, split_rows_smem(), &x);
+  per_sm[3] = std::min(per_sm[3], x);
+  occ(kg_rows_inverse_split<C, 1>, kTileThreads, split_rows_smem(), &x);
+  per_sm[3] = std::min(per_sm[3], x);
+  occ(kg_rows_inverse_split<C, 2>, kTileThreads, split_rows_smem(), &x);
+  per_sm[3] = std::min(per_sm[3], x);
+  return e == cudaSuccess ? DBI_OK : cuda_fail("occupancy of the split group kernels", e);
+}
+
 template <typename C> int run_group_typed(const OpArgs &a, cudaStream_t s) {
   const GroupLaunch &gl = *a.group;
   GroupP<C> g;
@@ -152,6 +237,7 @@ template <typename C> int run_group_typed(const OpArgs &a, cudaStream_t s) {
   g.ident = static_cast<const C *>(a.ident);
   g.out = static_cast<C *>(a.out);
   g.T = static_cast<C *>(a.T);
+  g.S = g.T + size_t(gl.T_elems);  // the split-row sources follow the spectra
   g.tw = static_cast<const C *>(a.tw);
   g.active = a.active;
   g.in_scale = a.in_scale;
@@ -170,11 +256,54 @@ template <typename C> int run_group_typed(const OpArgs &a, cudaStream_t s) {
     kernel<<<blocks, kTileThreads, smem, s>>>(g);
     return check_launch(what);
   };
-  int rc;
+  // the split kernels of the length-1024 members (complex64), each stage before the others' kernel
+  auto launch_split = [&](auto kernel, int stage, int slot, int threads, size_t smem, const char *what) -> int {
+    g.total = gl.total[stage];
+    if (g.total == 0) return DBI_OK;
+    cudaError_t e = allow_smem(kernel, smem);
+    if (e != cudaSuccess) return cuda_fail(what, e);
+    const int blocks = std::max(1, std::min(gl.split_blocks[slot], g.total));
+    kernel<<<blocks, threads, smem, s>>>(g);
+    return check_launch(what);
+  };
+  int rc = DBI_OK;
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (gl.split_rows) {
+      if (a.stencil &&
+          (rc = launch_split(kg_source_split<C>, kStageSource, 0, kSrcThreads, source_smem(), "kg_source_split")))
+        return rc;
+      if (a.stencil)
+        rc = launch_split(kg_rows_forward_split<C, true>, kStageRowsForward, 1, kTileThreads, split_rows_smem(),
+                          "kg_rows_forward_split");
+      else
+        rc = launch_split(kg_rows_forward_split<C, false>, kStageRowsForward, 1, kTileThreads, split_rows_smem(),
+                          "kg_rows_forward_split");
+      if (rc) return rc;
+    }
+  }
   if (a.stencil) rc = launch(kg_rows_forward<C, true>, kStageRowsForward, gl.smem[0], "kg_rows_forward");
   else rc = launch(kg_rows_forward<C, false>, kStageRowsForward, gl.smem[1], "kg_rows_forward");
   if (rc) return rc;
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (gl.split_cols &&
+        (rc = launch_split(kg_cols_split<C>, kStageCols, 2, kTileThreads, split_cols_smem(), "kg_cols_split")))
+      return rc;
+  }
   if ((rc = launch(kg_cols<C>, kStageCols, gl.smem[2], "kg_cols"))) return rc;
+  if constexpr (sizeof(C) == sizeof(float2)) {
+    if (gl.split_rows) {
+      if (a.epi == 1)
+        rc = launch_split(kg_rows_inverse_split<C, 1>, kStageRowsInverse, 3, kTileThreads, split_rows_smem(),
+                          "kg_rows_inverse_split");
+      else if (a.epi == 2)
+        rc = launch_split(kg_rows_inverse_split<C, 2>, kStageRowsInverse, 3, kTileThreads, split_rows_smem(),
+                          "kg_rows_inverse_split");
+      else
+        rc = launch_split(kg_rows_inverse_split<C, 0>, kStageRowsInverse, 3, kTileThreads, split_rows_smem(),
+                          "kg_rows_inverse_split");
+      if (rc) return rc;
+    }
+  }
   if (a.epi == 1) rc = launch(kg_rows_inverse<C, 1>, kStageRowsInverse, gl.smem[3], "kg_rows_inverse");
   else if (a.epi == 2) rc = launch(kg_rows_inverse<C, 2>, kStageRowsInverse, gl.smem[3], "kg_rows_inverse");
   else rc = launch(kg_rows_inverse<C, 0>, kStageRowsInverse, gl.smem[3], "kg_rows_inverse");

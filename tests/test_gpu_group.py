@@ -34,7 +34,7 @@ def rel(a, b):
 
 
 # A small mixed batch: ragged shapes, non-square and oversized FFT grids, one-row and one-slot
-# members, isotropic and VTI backgrounds, several row and column tiles.
+# members, isotropic and VTI backgrounds, several row and column tiles, FFT length 1024.
 MINI = [
     dict(nz=12, nx=10, n_src=2, freqs=(8.0, 14.0), seed=71),
     dict(nz=5, nx=9, lz=16, lx=32, n_src=1, freqs=(11.0,), seed=72),
@@ -42,6 +42,11 @@ MINI = [
     dict(nz=1, nx=8, n_src=1, freqs=(10.0,), seed=74),
     dict(nz=20, nx=20, vti=True, lz=64, lx=64, n_src=2, freqs=(12.0,), seed=75),
     dict(nz=30, nx=60, n_src=2, freqs=(5.0, 7.0), seed=76),
+    # FFT length 1024 along one or both axes: complex64 runs these stages on the split kernels
+    # (pairs of 512-point transforms, the source kernel in 32-row tiles) beside the others
+    dict(nz=35, nx=33, lz=1024, lx=1024, vti=True, n_src=1, freqs=(9.0,), seed=77),
+    dict(nz=9, nx=50, lz=32, lx=1024, n_src=1, freqs=(13.0,), seed=78),
+    dict(nz=40, nx=7, lz=1024, lx=16, n_src=1, freqs=(6.0,), seed=79),
 ]
 
 
