@@ -909,7 +909,9 @@ def run_uneven(args):
         "config": {"workload": "uneven40: 40 problems, square grids " + "/".join(f"{n}^2" for n in sizes)
                    + ", 1-32 sources x 1-8 frequencies (2-25 Hz) each", "members": len(Ps),
                    "wavefields": G.slots, "cells_per_pass": cells, "step": "one operator pass over every "
-                   "wavefield (3 persistent launches + input scaling)",
+                   "wavefield (per stage one persistent launch for each kernel kind present: ordinary, "
+                   "pairs of 512-point and triples of 256-point transforms; the source kernel; input scaling)",
+                   "fft_lengths": sorted({P.w.lz for P in Ps} | {P.w.lx for P in Ps}),
                    "l2": f"inputs larger than L2: {cells * 16 / 1e9:.1f} GB per field"},
         "autotuner": tuning, "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
         "clocks": clk.summary(),

@@ -70,7 +70,10 @@ enum dbi_op {
 
 typedef struct dbi_grid {
   int nz, nx; /* cells of the domain D (rows: depth x3; columns: x1) */
-  int lz, lx; /* FFT grid; lz >= 2 nz - 1, lx >= 2 nx - 1, each a power of two in [16, 1024] */
+  int lz, lx; /* FFT grid; lz >= 2 nz - 1, lx >= 2 nx - 1, each a power of two in [16, 1024]; with
+               * complex64, 768 is also taken (3 x 256: Eq. 12 holds for any lengths >= 2n - 1) by
+               * the Green's tables, the incident field, the operator and everything built on it
+               * (not by the paper-literal form K entry points, which return DBI_ERR_UNSUPPORTED) */
   double h;   /* cell size in metres */
 } dbi_grid;
 
@@ -138,7 +141,9 @@ size_t dbi_workspace_bytes(const dbi_grid *g, int B, int precision, int op);
  *   the lz x lx grid (other slots 0), and takes the FP64 2D FFT.
  *   omega  device [nf] angular frequencies.
  *   Ghat   device [nf][3][lx][lz] complex out: h^2 / (lz lx) * FFT(G) for components 11, 13, 33,
- *          stored column-major: entry [f][c][kx][kz] holds wavenumber (kz, kx).
+ *          stored column-major: entry [f][c][kx][kz] holds wavenumber (kz, kx). At lz = 768 the kz
+ *          entries of a column are residue-major: entry [f][c][kx][(kz mod 3) 256 + kz / 3] holds
+ *          wavenumber (kz, kx), the order in which the length-768 column stage reads them.
  *   Gspace device [nf][3][lz][lx] complex out (may be NULL): the spatial G_h on the same slots.
  *   Work: DBI_OP_GREENS bytes.
  */

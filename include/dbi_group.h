@@ -84,9 +84,9 @@ int ls_solve_group(const dbi_group *g, const void *rhs, void *u, const dbi_krylo
                    const dbi_status *status, int flags, dbi_stream stream);
 
 typedef struct dbi_group_tuning {
-  int lengths[7];      /* FFT lengths present (0 = unused entry) */
-  int plan[7];         /* radix plan chosen for lengths[i] (0: radix 8 first, 1: small radix first) */
-  double plan_ms[7][2];/* apply time (ms) measured with each plan of lengths[i] (0 when one plan) */
+  int lengths[8];      /* FFT lengths present (0 = unused entry) */
+  int plan[8];         /* radix plan chosen for lengths[i] (0: radix 8 first, 1: small radix first) */
+  double plan_ms[8][2];/* apply time (ms) measured with each plan of lengths[i] (0 when one plan) */
   int ctas_per_sm[3];  /* persistent CTAs per SM chosen for each stage */
   int max_ctas[3];     /* resident CTAs per SM possible for each stage */
   double apply_ms;     /* apply time with the chosen settings */

@@ -78,14 +78,16 @@ cudaError_t allow_dynamic_smem(const void *kernel, size_t bytes) {
   return e;
 }
 
-int check_grid(const dbi_grid *g) {
+static int check_grid_impl(const dbi_grid *g, bool allow768, bool mention768) {
   if (!g) { set_error("grid is NULL"); return DBI_ERR_ARG; }
   if (g->nz < 1 || g->nx < 1 || !(g->h > 0)) {
     set_error("grid needs nz, nx >= 1 and h > 0 (got %d, %d, %g)", g->nz, g->nx, g->h);
     return DBI_ERR_ARG;
   }
-  if (!fft_len_ok(g->lz) || !fft_len_ok(g->lx)) {
-    set_error("FFT grid %d x %d: each side must be a power of two in [16, 1024]", g->lz, g->lx);
+  auto ok = [&](int L) { return fft_len_ok(L) || (allow768 && L == 768); };
+  if (!ok(g->lz) || !ok(g->lx)) {
+    set_error("FFT grid %d x %d: each side must be a power of two in [16, 1024]%s", g->lz, g->lx,
+              mention768 ? " (or 768 with complex64)" : "");
     return DBI_ERR_UNSUPPORTED;
   }
   if (g->lz < 2 * g->nz - 1 || g->lx < 2 * g->nx - 1) {
@@ -94,6 +96,9 @@ int check_grid(const dbi_grid *g) {
   }
   return DBI_OK;
 }
+
+int check_grid(const dbi_grid *g) { return check_grid_impl(g, false, false); }
+int check_grid(const dbi_grid *g, int precision) { return check_grid_impl(g, precision == DBI_C64, true); }
 
 int check_batch(const dbi_batch *b) {
   if (!b) { set_error("batch is NULL"); return DBI_ERR_ARG; }
@@ -217,7 +222,7 @@ extern "C" int dbi_profile_end(double *total_ms, long long *launches) {
 }
 
 extern "C" size_t dbi_workspace_bytes(const dbi_grid *g, int B, int precision, int op) {
-  if (check_grid(g) != DBI_OK || check_precision(precision) != DBI_OK || B < 0) return 0;
+  if (check_grid(g, precision) != DBI_OK || check_precision(precision) != DBI_OK || B < 0) return 0;
   const size_t tw = bytes_twiddles(precision);
   const size_t spec = bytes_spectral(g, B, precision);
   const size_t fld = bytes_field(g, B, precision);

@@ -54,11 +54,17 @@ inline bool fft_len_ok(int L) {
   return L >= 16 && L <= 1024 && (L & (L - 1)) == 0;
 }
 
-// Single-grid complex64 batches with FFT length 1024 along x (rows) or z (columns) run those
-// stages as pairs of 512-point transforms (op_split.cuh); split rows also need a contrast-source
-// scratch field per problem of a chunk, placed after the chunk's spectra.
-inline bool split_rows(int lx, int precision) { return precision == DBI_C64 && lx == 1024; }
-inline bool split_cols(int lz, int precision) { return precision == DBI_C64 && lz == 1024; }
+// Complex64 operator stages with FFT length 1024 along x (rows) or z (columns) run as pairs of
+// 512-point transforms (op_split.cuh), and with length 768 as triples of 256-point transforms
+// (op_split3.cuh); split_kind gives the number of sub-transforms (0: the ordinary stages). Split
+// rows also need a contrast-source scratch field per problem of a chunk, after the chunk's spectra.
+constexpr int kSplitPair = 2, kSplitTriple = 3;
+inline int split_kind(int L, int precision) {
+  if (precision != DBI_C64) return 0;
+  return L == 1024 ? kSplitPair : L == 768 ? kSplitTriple : 0;
+}
+inline bool split_rows(int lx, int precision) { return split_kind(lx, precision) != 0; }
+inline bool split_cols(int lz, int precision) { return split_kind(lz, precision) != 0; }
 
 // Error reporting (per host thread).
 void set_error(const char *fmt, ...);
@@ -82,8 +88,12 @@ template <typename K> inline cudaError_t allow_smem(K kernel, size_t bytes) {
   return allow_dynamic_smem(reinterpret_cast<const void *>(kernel), bytes);
 }
 
-// Validation shared by the entry points.
+// Validation shared by the entry points. check_grid(g) takes FFT sides that are powers of two in
+// [16, 1024]; check_grid(g, precision), for the entry points whose stages also run length 768 (the
+// operator and everything built on it, the Green's tables and incident fields), also takes 768
+// with complex64.
 int check_grid(const dbi_grid *g);
+int check_grid(const dbi_grid *g, int precision);
 int check_batch(const dbi_batch *b);
 int check_precision(int precision);
 

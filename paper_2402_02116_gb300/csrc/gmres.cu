@@ -538,7 +538,7 @@ int run_gmres(const OpArgs &op, Arena &ar, size_t field_bytes, int m, const void
 using namespace dbi;
 
 extern "C" size_t dbi_gmres_workspace_bytes(const dbi_grid *g, int B, int precision, int restart) {
-  if (!g || check_grid(g) || check_precision(precision) || B < 0 || restart < 1 || restart > kGmresMaxRestart)
+  if (!g || check_grid(g, precision) || check_precision(precision) || B < 0 || restart < 1 || restart > kGmresMaxRestart)
     return 0;
   return bytes_twiddles(precision) + bytes_spectral(g, B, precision) +
          gmres_bytes_fields(bytes_field(g, B, precision), B, restart);
@@ -551,7 +551,7 @@ extern "C" int ls_solve_gmres(const dbi_model *model, const dbi_batch *batch, co
   int rc;
   if (!model) { set_error("model is NULL"); return DBI_ERR_ARG; }
   const dbi_grid *g = &model->grid;
-  if ((rc = check_grid(g)) || (rc = check_batch(batch)) || (rc = check_precision(precision)) ||
+  if ((rc = check_grid(g, precision)) || (rc = check_batch(batch)) || (rc = check_precision(precision)) ||
       (rc = check_krylov(opts)))
     return rc;
   if (restart < 1 || restart > kGmresMaxRestart) {

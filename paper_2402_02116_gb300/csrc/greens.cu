@@ -141,8 +141,67 @@ __global__ void __launch_bounds__(256) k_fft_cols64(double2 *data, int width, co
   }
 }
 
+// FP64 FFT of length 768 = 3 x 256 by one decimation-in-frequency step: with the thirds
+// x_p[i] = x[i + 256 p] of a line, X[3m + q] = sum_i W_256^{im} W_768^{iq} sum_p W_3^{pq} x_p[i], i.e.
+// the 256-point DFTs of the three folded lines. A block holds NL lines; line l's third p is loaded
+// to s[(3 l + p) LS + i], and the fold writes its residue q to the same slots (3 l + q), in place.
+constexpr int k768NL = 2, k768LS = 257, k768NT = 3 * k768NL * 256 / 8;
+
+__device__ __forceinline__ void fold768_fp64(double2 *s, const double2 *tw) {
+  const double2 w3 = tw[kTwiddleN / 3], w3b = tw[2 * kTwiddleN / 3];  // W_3, W_3^2
+  constexpr int TWS = kTwiddleN / 768;
+  for (int idx = threadIdx.x; idx < k768NL * 256; idx += k768NT) {
+    const int l = idx >> 8, i = idx & 255;
+    double2 *p = s + 3 * l * k768LS + i;
+    const double2 a0 = p[0], a1 = p[k768LS], a2 = p[2 * k768LS];
+    p[0] = cadd(a0, cadd(a1, a2));
+    p[k768LS] = cmul(tw[i * TWS], cadd(a0, cadd(cmul(w3, a1), cmul(w3b, a2))));
+    p[2 * k768LS] = cmul(tw[2 * i * TWS], cadd(a0, cadd(cmul(w3b, a1), cmul(w3, a2))));
+  }
+}
+
+__global__ void __launch_bounds__(k768NT) k_fft_rows64_768(double2 *data, long nlines, const double2 *tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *s = reinterpret_cast<double2 *>(smem_raw);
+  const long l0 = long(blockIdx.x) * k768NL;
+  for (int idx = threadIdx.x; idx < k768NL * 768; idx += k768NT) {
+    const int l = idx / 768, k = idx - l * 768;
+    s[(3 * l + (k >> 8)) * k768LS + (k & 255)] = l0 + l < nlines ? data[(l0 + l) * 768 + k] : make_double2(0, 0);
+  }
+  __syncthreads();
+  fold768_fp64(s, tw);
+  __syncthreads();
+  Plan<256>::template run<double2, 3 * k768NL, k768LS, k768NT, false>(s, tw);
+  for (int idx = threadIdx.x; idx < k768NL * 768; idx += k768NT) {
+    const int l = idx / 768, k = idx - l * 768, m = k / 3, q = k - 3 * m;
+    if (l0 + l < nlines) data[(l0 + l) * 768 + k] = s[(3 * l + q) * k768LS + m];
+  }
+}
+
+// The same along the columns of row-major [768][width] matrices (matrix blockIdx.y).
+__global__ void __launch_bounds__(k768NT) k_fft_cols64_768(double2 *data, int width, const double2 *tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *s = reinterpret_cast<double2 *>(smem_raw);
+  double2 *M = data + size_t(blockIdx.y) * 768 * width;
+  const int c0 = blockIdx.x * k768NL;
+  for (int idx = threadIdx.x; idx < k768NL * 768; idx += k768NT) {
+    const int z = idx / k768NL, j = idx - z * k768NL;
+    s[(3 * j + (z >> 8)) * k768LS + (z & 255)] = c0 + j < width ? M[size_t(z) * width + c0 + j] : make_double2(0, 0);
+  }
+  __syncthreads();
+  fold768_fp64(s, tw);
+  __syncthreads();
+  Plan<256>::template run<double2, 3 * k768NL, k768LS, k768NT, false>(s, tw);
+  for (int idx = threadIdx.x; idx < k768NL * 768; idx += k768NT) {
+    const int z = idx / k768NL, j = idx - z * k768NL, m = z / 3, q = z - 3 * m;
+    if (c0 + j < width) M[size_t(z) * width + c0 + j] = s[(3 * j + q) * k768LS + m];
+  }
+}
+
 // Ghat[f][c][kx][kz] = scale * W[f][c][kz][kx]: scaled, rounded and stored column-major (kz
 // contiguous) for the column pass. One 32 x 32 tile per block, transposed through shared memory.
+// At lz = 768 the kz slots are residue-major: slot (kz mod 3) 256 + kz / 3 (the order in which the
+// column stage's three 256-point transforms consume them).
 template <typename C>
 __global__ void k_scale_cast_t(const double2 *W, C *Ghat, int lz, int lx, double scale) {
   using R = typename RealOf<C>::type;
@@ -160,13 +219,19 @@ __global__ void k_scale_cast_t(const double2 *W, C *Ghat, int lz, int lx, double
     const int kx = kx0 + i, kz = kz0 + threadIdx.x;
     if (kz < lz && kx < lx) {
       const double2 w = tile[threadIdx.x][i];
-      Gm[size_t(kx) * lz + kz] = mk<C>(R(w.x * scale), R(w.y * scale));
+      const int slot = lz == 768 ? (kz % 3) * 256 + kz / 3 : kz;
+      Gm[size_t(kx) * lz + slot] = mk<C>(R(w.x * scale), R(w.y * scale));
     }
   }
 }
 
 
 int fft_rows_fp64(double2 *W, long nlines, int L, const double2 *tw, cudaStream_t s) {
+  if (L == 768) {
+    const size_t bytes = size_t(3 * k768NL) * k768LS * sizeof(double2);
+    k_fft_rows64_768<<<unsigned((nlines + k768NL - 1) / k768NL), k768NT, bytes, s>>>(W, nlines, tw);
+    return check_launch("k_fft_rows64_768");
+  }
   int rc = DBI_ERR_UNSUPPORTED;
   dispatch_len(L, [&]<int LL>() {
     constexpr int NL = 2048 / LL > 0 ? 2048 / LL : 1, LS = LL + 1, NT = NL * LL / 8;
@@ -179,6 +244,11 @@ int fft_rows_fp64(double2 *W, long nlines, int L, const double2 *tw, cudaStream_
 }
 
 int fft_cols_fp64(double2 *W, int nmat, int L, int width, const double2 *tw, cudaStream_t s) {
+  if (L == 768) {
+    const size_t bytes = size_t(3 * k768NL) * k768LS * sizeof(double2);
+    k_fft_cols64_768<<<dim3((width + k768NL - 1) / k768NL, nmat), k768NT, bytes, s>>>(W, width, tw);
+    return check_launch("k_fft_cols64_768");
+  }
   int rc = DBI_ERR_UNSUPPORTED;
   dispatch_len(L, [&]<int LL>() {
     constexpr int CC = 2048 / LL > 0 ? 2048 / LL : 1, LS = LL + 1, NT = CC * LL / 8;
@@ -324,7 +394,7 @@ extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const d
                                size_t work_bytes, dbi_stream stream) {
   clear_error();
   int rc;
-  if ((rc = check_grid(g)) || (rc = check_precision(precision))) return rc;
+  if ((rc = check_grid(g, precision)) || (rc = check_precision(precision))) return rc;
   const bool vti = ref && reference_is_vti(*ref);
   if (vti && (rc = check_vti(ref))) return rc;
   if (!vti && (!ref || !(ref->rho0 > 0) || !(ref->alpha0 > 0) || !(ref->beta0 > 0) || !(ref->alpha0 > ref->beta0))) {
@@ -375,7 +445,7 @@ extern "C" int incident_field(const dbi_grid *g, const dbi_batch *batch, const v
                               dbi_stream stream) {
   clear_error();
   int rc;
-  if ((rc = check_grid(g)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
+  if ((rc = check_grid(g, precision)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
   if (batch->B == 0) return DBI_OK;
   if (!Gspace || !src_cells || !forces || !u0) { set_error("NULL Gspace, sources, forces or u0"); return DBI_ERR_ARG; }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

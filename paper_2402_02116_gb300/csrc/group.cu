@@ -13,6 +13,7 @@
 #include "group.cuh"
 #include "krylov.cuh"
 #include "op_split.cuh"
+#include "op_split3.cuh"
 #include "op_tiles.cuh"
 #include "tune.cuh"
 
@@ -142,7 +143,7 @@ extern "C" int dbi_group_create(const dbi_group_member *members, int n, int prec
   if (!members || n < 1) { set_error("need at least one member"); return DBI_ERR_ARG; }
   for (int k = 0; k < n; ++k) {
     const dbi_group_member &M = members[k];
-    if ((rc = check_grid(&M.model.grid))) return rc;
+    if ((rc = check_grid(&M.model.grid, precision))) return rc;
     if (M.B < 1 || M.nf < 1 || !M.model.m || !M.Ghat || !M.omega || !M.fidx) {
       set_error("member %d needs B >= 1, nf >= 1 and device m, Ghat, omega, fidx", k);
       return DBI_ERR_ARG;
@@ -192,11 +193,15 @@ extern "C" int dbi_group_create(const dbi_group_member *members, int n, int prec
     M.m = U.model.m; M.Ghat = U.Ghat; M.omega = U.omega; M.fidx = U.fidx;
     M.nf = U.nf; M.B = U.B;
     M.slot0 = slot0[k]; M.field0 = f0[k]; M.T0 = t0[k]; M.S0 = s0[k];
-    M.split_rows = split_rows(gr.lx, precision) ? 1 : 0;
-    M.split_cols = split_cols(gr.lz, precision) ? 1 : 0;
-    g->gl.split_rows |= M.split_rows;
-    g->gl.split_cols |= M.split_cols;
-    // rows / columns per tile (op_tiles.cuh; op_split.cuh for the split stages)
+    M.split_rows = split_kind(gr.lx, precision);
+    M.split_cols = split_kind(gr.lz, precision);
+    g->gl.split_rows |= M.split_rows == kSplitPair;
+    g->gl.split_cols |= M.split_cols == kSplitPair;
+    g->gl.s3_rows |= M.split_rows == kSplitTriple;
+    g->gl.s3_cols |= M.split_cols == kSplitTriple;
+    // rows / columns per tile (op_tiles.cuh; op_split.cuh and op_split3.cuh for the split stages,
+    // both four rows or columns)
+    static_assert(kS3Units == kSplitRows, "split tiles hold the same number of rows or columns");
     const int rows = M.split_rows ? kSplitRows : 2048 / gr.lx, cols = M.split_cols ? kSplitRows : 2048 / gr.lz;
     M.tiles[kStageRowsForward] = M.tiles[kStageRowsInverse] = (gr.nz + rows - 1) / rows;
     M.tiles[kStageCols] = (gr.lx + cols - 1) / cols;
@@ -284,10 +289,12 @@ extern "C" int dbi_group_bind(dbi_group *g, void *work, size_t work_bytes, int o
     occ[2] = std::min(occ[2], n);
   }
   for (int st = 0; st < 3; ++st) g->max_ctas[st] = std::max(1, occ[st]);
-  if (g->gl.split_rows || g->gl.split_cols) {  // the split kernels: the resident maximum per SM
-    int sp[4] = {0, 0, 0, 0};
+  if (g->gl.split_rows || g->gl.split_cols || g->gl.s3_rows || g->gl.s3_cols) {
+    // the split kernels: the resident maximum per SM
+    int sp[7] = {0, 0, 0, 0, 0, 0, 0};
     if ((rc = group_split_occupancy(sp))) return rc;
     for (int i = 0; i < 4; ++i) g->gl.split_blocks[i] = std::max(1, sp[i]) * std::max(1, g->sms);
+    for (int i = 0; i < 3; ++i) g->gl.s3_blocks[i] = std::max(1, sp[4 + i]) * std::max(1, g->sms);
   }
   g->gl.desc = g->d_desc;
   set_blocks(g);
@@ -354,10 +361,10 @@ extern "C" int dbi_group_tune(dbi_group *g, const void *u, void *out, dbi_stream
   double best = 0.0;
   rc = time_apply(&best);
   // radix plan per length (coordinate descent: one length at a time, the others fixed)
-  for (size_t i = 0; i < lens.size() && rc == DBI_OK && i < 7; ++i) {
+  for (size_t i = 0; i < lens.size() && rc == DBI_OK && i < 8; ++i) {
     const int L = lens[i], k = log2i(L);
     rep.lengths[i] = L;
-    if (L == 64 || L == 512) continue;  // one plan only
+    if (L == 64 || L == 512 || L == 768) continue;  // one plan only
     double t[2];
     for (int v = 0; v < 2 && rc == DBI_OK; ++v) {
       g->gl.plan[k] = static_cast<signed char>(v);

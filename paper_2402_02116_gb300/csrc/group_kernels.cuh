@@ -6,6 +6,7 @@
 
 #include "group.cuh"
 #include "op_split.cuh"
+#include "op_split3.cuh"
 #include "op_tiles.cuh"
 
 namespace dbi {
@@ -65,19 +66,21 @@ __device__ __forceinline__ TileArgs<C> group_args(const GroupP<C> &g, const GMem
   return a;
 }
 
-// Whether member M runs `stage` on the split (pairs of 512-point transforms) kernels.
+// The split kind of member M's `stage`: 0 (the ordinary kernels), kSplitPair (pairs of 512-point
+// transforms) or kSplitTriple (triples of 256-point transforms).
 __device__ __forceinline__ int split_stage(const GMember &M, int stage) {
   return stage == kStageCols ? M.split_cols : M.split_rows;
 }
 
 // Runs body(M, b, q, f, tt) for every tile of `stage` assigned to this CTA whose slot is active and
-// whose member runs the stage on this kind of kernel (SPLIT = 1: the split kernels, 0: the others).
+// whose member runs the stage on this kind of kernel (SPLIT: the member's split kind; the source
+// stage has tiles of split-row members only and serves both kinds).
 template <int STAGE, int SPLIT = 0, typename C, typename Body>
 __device__ __forceinline__ void for_tiles(const GroupP<C> &g, Body &&body) {
   for (int tile = blockIdx.x; tile < g.total; tile += gridDim.x) {
     const int i = find_member(g.desc, g.nm, STAGE, tile);
     const GMember &M = g.desc[i];
-    if (split_stage(M, STAGE) != SPLIT) continue;  // uniform per CTA
+    if (STAGE != kStageSource && split_stage(M, STAGE) != SPLIT) continue;  // uniform per CTA
     const int rel = tile - M.tile0[STAGE];
     const int q = rel / M.tiles[STAGE], tt = rel - q * M.tiles[STAGE];
     const int b = M.slot0 + q;
@@ -152,10 +155,10 @@ __global__ void __launch_bounds__(kTileThreads, Cfg<C>::rowInvMinBlocks) kg_rows
   });
 }
 
-// Split kernels of the members with FFT length 1024 (complex64 only, op_split.cuh): the contrast
-// source (512 threads, 32 rows per tile), the rows and columns as pairs of 512-point transforms (4
-// rows or columns per tile). Templates on the element type so that only the complex64 unit
-// instantiates them.
+// Split kernels of the members with FFT length 1024 or 768 (complex64 only, op_split.cuh,
+// op_split3.cuh): the contrast source of both (512 threads, 32 rows per tile), the rows and columns
+// as pairs of 512-point transforms or triples of 256-point transforms (4 rows or columns per tile).
+// Templates on the element type so that only the complex64 unit instantiates them.
 template <typename C> __device__ __forceinline__ C *group_S(const GroupP<C> &g, const GMember &M, int q) {
   return g.S + size_t(M.S0) + size_t(q) * 2 * M.nz * M.nx;
 }
@@ -164,7 +167,7 @@ template <typename C> __global__ void __launch_bounds__(kSrcThreads) kg_source_s
   static_assert(sizeof(C) == sizeof(float2), "complex64 only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *smem = reinterpret_cast<C *>(smem_raw);
-  for_tiles<kStageSource, 1>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+  for_tiles<kStageSource>(g, [&](const GMember &M, int b, int q, int f, int tt) {
     source_rows(group_args(g, M, b, q, f), tt, smem, group_S(g, M, q));
   });
 }
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) kg_rows_forward_split(GroupP<
   static_assert(sizeof(C) == sizeof(float2), "complex64 only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *smem = reinterpret_cast<C *>(smem_raw);
-  for_tiles<kStageRowsForward, 1>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+  for_tiles<kStageRowsForward, kSplitPair>(g, [&](const GMember &M, int b, int q, int f, int tt) {
     const TileArgs<C> a = group_args(g, M, b, q, f);
     if constexpr (STENCIL) rows_forward_tile_split(a, tt, smem, group_S(g, M, q), 1.0f);
     else rows_forward_tile_split(a, tt, smem, a.in(), a.isc());
@@ -190,7 +193,7 @@ template <typename C> __global__ void __launch_bounds__(kTileThreads, 2) kg_cols
   static_assert(sizeof(C) == sizeof(float2), "complex64 only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *smem = reinterpret_cast<C *>(smem_raw);
-  for_tiles<kStageCols, 1>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+  for_tiles<kStageCols, kSplitPair>(g, [&](const GMember &M, int b, int q, int f, int tt) {
     call_cols_split(group_args(g, M, b, q, f), tt, smem);
   });
 }
@@ -200,12 +203,43 @@ __global__ void __launch_bounds__(kTileThreads, 2) kg_rows_inverse_split(GroupP<
   static_assert(sizeof(C) == sizeof(float2), "complex64 only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *smem = reinterpret_cast<C *>(smem_raw);
-  for_tiles<kStageRowsInverse, 1>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+  for_tiles<kStageRowsInverse, kSplitPair>(g, [&](const GMember &M, int b, int q, int f, int tt) {
     rows_inverse_tile_split<EPI>(group_args(g, M, b, q, f), tt, smem);
   });
 }
 
-template <typename C> int group_split_occupancy_impl(int per_sm[4]) {
+template <typename C, bool STENCIL>
+__global__ void __launch_bounds__(kS3Threads, 2) kg_rows_forward_s3(GroupP<C> g) {
+  static_assert(sizeof(C) == sizeof(float2), "complex64 only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageRowsForward, kSplitTriple>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    const TileArgs<C> a = group_args(g, M, b, q, f);
+    if constexpr (STENCIL) rows_forward_tile_s3(a, tt, smem, group_S(g, M, q), 1.0f);
+    else rows_forward_tile_s3(a, tt, smem, a.in(), a.isc());
+  });
+}
+
+template <typename C> __global__ void __launch_bounds__(kS3Threads, 2) kg_cols_s3(GroupP<C> g) {
+  static_assert(sizeof(C) == sizeof(float2), "complex64 only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageCols, kSplitTriple>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    cols_tile_s3(group_args(g, M, b, q, f), tt, smem);
+  });
+}
+
+template <typename C, int EPI>
+__global__ void __launch_bounds__(kS3Threads, 2) kg_rows_inverse_s3(GroupP<C> g) {
+  static_assert(sizeof(C) == sizeof(float2), "complex64 only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *smem = reinterpret_cast<C *>(smem_raw);
+  for_tiles<kStageRowsInverse, kSplitTriple>(g, [&](const GMember &M, int b, int q, int f, int tt) {
+    rows_inverse_tile_s3<EPI>(group_args(g, M, b, q, f), tt, smem);
+  });
+}
+
+template <typename C> int group_split_occupancy_impl(int per_sm[7]) {
   cudaError_t e = cudaSuccess;
   auto occ = [&](auto kernel, int threads, size_t smem, int *n) {
     if (e != cudaSuccess) return;
@@ -225,6 +259,17 @@ template <typename C> int group_split_occupancy_impl(int per_sm[4]) {
   per_sm[3] = std::min(per_sm[3], x);
   occ(kg_rows_inverse_split<C, 2>, kTileThreads, split_rows_smem(), &x);
   per_sm[3] = std::min(per_sm[3], x);
+  occ(kg_rows_forward_s3<C, true>, kS3Threads, s3_smem(), &x);
+  occ(kg_rows_forward_s3<C, false>, kS3Threads, s3_smem(), &y);
+  per_sm[4] = std::min(x, y);
+  occ(kg_cols_s3<C>, kS3Threads, s3_smem(), &per_sm[5]);
+  per_sm[6] = 1 << 20;
+  occ(kg_rows_inverse_s3<C, 0>, kS3Threads, s3_smem(), &x);
+  per_sm[6] = std::min(per_sm[6], x);
+  occ(kg_rows_inverse_s3<C, 1>, kS3Threads, s3_smem(), &x);
+  per_sm[6] = std::min(per_sm[6], x);
+  occ(kg_rows_inverse_s3<C, 2>, kS3Threads, s3_smem(), &x);
+  per_sm[6] = std::min(per_sm[6], x);
   return e == cudaSuccess ? DBI_OK : cuda_fail("occupancy of the split group kernels", e);
 }
 
@@ -256,27 +301,40 @@ template <typename C> int run_group_typed(const OpArgs &a, cudaStream_t s) {
     kernel<<<blocks, kTileThreads, smem, s>>>(g);
     return check_launch(what);
   };
-  // the split kernels of the length-1024 members (complex64), each stage before the others' kernel
-  auto launch_split = [&](auto kernel, int stage, int slot, int threads, size_t smem, const char *what) -> int {
+  // the split kernels of the length-1024 and length-768 members (complex64), each stage before the
+  // others' kernel
+  auto launch_split = [&](auto kernel, int stage, int blocks_max, int threads, size_t smem, const char *what) -> int {
     g.total = gl.total[stage];
     if (g.total == 0) return DBI_OK;
     cudaError_t e = allow_smem(kernel, smem);
     if (e != cudaSuccess) return cuda_fail(what, e);
-    const int blocks = std::max(1, std::min(gl.split_blocks[slot], g.total));
+    const int blocks = std::max(1, std::min(blocks_max, g.total));
     kernel<<<blocks, threads, smem, s>>>(g);
     return check_launch(what);
   };
   int rc = DBI_OK;
   if constexpr (sizeof(C) == sizeof(float2)) {
-    if (gl.split_rows) {
-      if (a.stencil &&
-          (rc = launch_split(kg_source_split<C>, kStageSource, 0, kSrcThreads, source_smem(), "kg_source_split")))
-        return rc;
+    if (a.stencil && (gl.split_rows || gl.s3_rows) &&
+        (rc = launch_split(kg_source_split<C>, kStageSource, gl.split_blocks[0], kSrcThreads, source_smem(),
+                           "kg_source_split")))
+      return rc;
+    if (gl.s3_rows) {
       if (a.stencil)
-        rc = launch_split(kg_rows_forward_split<C, true>, kStageRowsForward, 1, kTileThreads, split_rows_smem(),
+        rc = launch_split(kg_rows_forward_s3<C, true>, kStageRowsForward, gl.s3_blocks[0], kS3Threads, s3_smem(),
+                          "kg_rows_forward_s3");
+      else
+        rc = launch_split(kg_rows_forward_s3<C, false>, kStageRowsForward, gl.s3_blocks[0], kS3Threads, s3_smem(),
+                          "kg_rows_forward_s3");
+      if (rc) return rc;
+    }
+    if (gl.split_rows) {
+      if (a.stencil)
+        rc = launch_split(kg_rows_forward_split<C, true>, kStageRowsForward, gl.split_blocks[1], kTileThreads,
+                          split_rows_smem(),
                           "kg_rows_forward_split");
       else
-        rc = launch_split(kg_rows_forward_split<C, false>, kStageRowsForward, 1, kTileThreads, split_rows_smem(),
+        rc = launch_split(kg_rows_forward_split<C, false>, kStageRowsForward, gl.split_blocks[1], kTileThreads,
+                          split_rows_smem(),
                           "kg_rows_forward_split");
       if (rc) return rc;
     }
@@ -285,22 +343,40 @@ template <typename C> int run_group_typed(const OpArgs &a, cudaStream_t s) {
   else rc = launch(kg_rows_forward<C, false>, kStageRowsForward, gl.smem[1], "kg_rows_forward");
   if (rc) return rc;
   if constexpr (sizeof(C) == sizeof(float2)) {
-    if (gl.split_cols &&
-        (rc = launch_split(kg_cols_split<C>, kStageCols, 2, kTileThreads, split_cols_smem(), "kg_cols_split")))
+    if (gl.split_cols && (rc = launch_split(kg_cols_split<C>, kStageCols, gl.split_blocks[2], kTileThreads,
+                                            split_cols_smem(), "kg_cols_split")))
+      return rc;
+    if (gl.s3_cols &&
+        (rc = launch_split(kg_cols_s3<C>, kStageCols, gl.s3_blocks[1], kS3Threads, s3_smem(), "kg_cols_s3")))
       return rc;
   }
   if ((rc = launch(kg_cols<C>, kStageCols, gl.smem[2], "kg_cols"))) return rc;
   if constexpr (sizeof(C) == sizeof(float2)) {
     if (gl.split_rows) {
       if (a.epi == 1)
-        rc = launch_split(kg_rows_inverse_split<C, 1>, kStageRowsInverse, 3, kTileThreads, split_rows_smem(),
+        rc = launch_split(kg_rows_inverse_split<C, 1>, kStageRowsInverse, gl.split_blocks[3], kTileThreads,
+                          split_rows_smem(),
                           "kg_rows_inverse_split");
       else if (a.epi == 2)
-        rc = launch_split(kg_rows_inverse_split<C, 2>, kStageRowsInverse, 3, kTileThreads, split_rows_smem(),
+        rc = launch_split(kg_rows_inverse_split<C, 2>, kStageRowsInverse, gl.split_blocks[3], kTileThreads,
+                          split_rows_smem(),
                           "kg_rows_inverse_split");
       else
-        rc = launch_split(kg_rows_inverse_split<C, 0>, kStageRowsInverse, 3, kTileThreads, split_rows_smem(),
+        rc = launch_split(kg_rows_inverse_split<C, 0>, kStageRowsInverse, gl.split_blocks[3], kTileThreads,
+                          split_rows_smem(),
                           "kg_rows_inverse_split");
+      if (rc) return rc;
+    }
+    if (gl.s3_rows) {
+      if (a.epi == 1)
+        rc = launch_split(kg_rows_inverse_s3<C, 1>, kStageRowsInverse, gl.s3_blocks[2], kS3Threads, s3_smem(),
+                          "kg_rows_inverse_s3");
+      else if (a.epi == 2)
+        rc = launch_split(kg_rows_inverse_s3<C, 2>, kStageRowsInverse, gl.s3_blocks[2], kS3Threads, s3_smem(),
+                          "kg_rows_inverse_s3");
+      else
+        rc = launch_split(kg_rows_inverse_s3<C, 0>, kStageRowsInverse, gl.s3_blocks[2], kS3Threads, s3_smem(),
+                          "kg_rows_inverse_s3");
       if (rc) return rc;
     }
   }

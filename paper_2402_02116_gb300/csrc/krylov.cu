@@ -496,7 +496,7 @@ extern "C" int ls_solve(const dbi_model *model, const dbi_batch *batch, const vo
   int rc;
   if (!model) { set_error("model is NULL"); return DBI_ERR_ARG; }
   const dbi_grid *g = &model->grid;
-  if ((rc = check_grid(g)) || (rc = check_batch(batch)) || (rc = check_precision(precision)) ||
+  if ((rc = check_grid(g, precision)) || (rc = check_batch(batch)) || (rc = check_precision(precision)) ||
       (rc = check_krylov(opts)))
     return rc;
   if (batch->B == 0) return DBI_OK;

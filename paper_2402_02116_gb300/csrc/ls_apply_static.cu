@@ -56,7 +56,7 @@ extern "C" int ls_apply_noalloc(const dbi_model *model, const dbi_batch *batch, 
   clear_error();
   int rc;
   if (!model) { set_error("model is NULL"); return DBI_ERR_ARG; }
-  if ((rc = check_grid(&model->grid)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
+  if ((rc = check_grid(&model->grid, precision)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
   const size_t need = dbi_workspace_bytes(&model->grid, batch->B, precision, DBI_OP_APPLY);
   if (need > kStaticScratchBytes) {
     set_error("ls_apply_noalloc: %d problems of %d x %d cells (FFT grid %d x %d) need %zu bytes of scratch, "

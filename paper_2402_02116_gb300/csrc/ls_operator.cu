@@ -9,6 +9,7 @@
 
 #include "group.cuh"
 #include "op_split.cuh"
+#include "op_split3.cuh"
 #include "op_tiles.cuh"
 #include "operator.cuh"
 #include "tune.cuh"
@@ -36,7 +37,7 @@ template <typename C> struct OpP {
   const C *krhat;
   double *part_out;
   int part_count;
-  C *S;  // [slots][2][nz][nx] contrast-source scratch of the split row stage (L = 1024), or NULL
+  C *S;  // [slots][2][nz][nx] contrast-source scratch of the split row stages (L = 1024, 768), or NULL
 };
 
 // Problem of this CTA's launch slot (blockIdx.y); the spectral scratch is indexed by the slot.
@@ -140,6 +141,35 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_rows_inverse_split(OpP<floa
                                reinterpret_cast<float2 *>(smem_raw));
 }
 
+// Stages of the L = 768 complex64 operator as triples of 256-point transforms (op_split3.cuh);
+// the contrast source comes from k_source_split.
+template <bool STENCIL>
+__global__ void __launch_bounds__(kS3Threads, 2) k_rows_forward_s3(OpP<float2> p) {
+  const int b = problem_of(p), f = p.fidx[b];
+  if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchTile<float2> a{p, b, int(blockIdx.y), f};
+  float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+  if constexpr (STENCIL) rows_forward_tile_s3(a, blockIdx.x, smem, a.S(), 1.0f);
+  else rows_forward_tile_s3(a, blockIdx.x, smem, a.in(), a.isc());
+}
+
+__global__ void __launch_bounds__(kS3Threads, 2) k_cols_s3(OpP<float2> p) {
+  const int b = problem_of(p), f = p.fidx[b];
+  if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cols_tile_s3(BatchTile<float2>{p, b, int(blockIdx.y), f}, blockIdx.x, reinterpret_cast<float2 *>(smem_raw));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kS3Threads, 2) k_rows_inverse_s3(OpP<float2> p) {
+  const int b = problem_of(p), f = p.fidx[b];
+  if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rows_inverse_tile_s3<EPI>(BatchTile<float2>{p, b, int(blockIdx.y), f}, blockIdx.x,
+                            reinterpret_cast<float2 *>(smem_raw));
+}
+
 // Calls f.template operator()<V>() with the radix plan chosen for length L (plans differ only
 // when L is not a power of 8).
 template <int L, typename F> inline void with_plan(int precision, F &&f) {
@@ -176,7 +206,8 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int 
   p.S = nullptr;
   int rc = DBI_OK;
   const bool stencil = a.stencil;
-  const bool split_r = split_rows(a.lx, a.precision), split_c = split_cols(a.lz, a.precision);
+  const int kr = split_kind(a.lx, a.precision), kc = split_kind(a.lz, a.precision);
+  const bool split_r = kr != 0, split_c = kc != 0;
   if (split_r) p.S = p.T + size_t(cap) * 2 * a.lx * a.nz;  // after the chunk's spectra
   prof_mark(PROF_ROWS_FORWARD, false, s);
   if constexpr (sizeof(C) == sizeof(float2)) {
@@ -190,11 +221,19 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int 
         rc = e != cudaSuccess ? cuda_fail("k_source_split smem", e) : check_launch("k_source_split");
         if (rc) return rc;
       }
-      const dim3 grid((a.nz + kSplitRows - 1) / kSplitRows, nb);
-      auto kern = stencil ? k_rows_forward_split<true> : k_rows_forward_split<false>;
-      e = allow_smem(kern, split_rows_smem());
-      if (e == cudaSuccess) kern<<<grid, kTileThreads, split_rows_smem(), s>>>(q);
-      rc = e != cudaSuccess ? cuda_fail("k_rows_forward_split smem", e) : check_launch("k_rows_forward_split");
+      if (kr == kSplitPair) {
+        const dim3 grid((a.nz + kSplitRows - 1) / kSplitRows, nb);
+        auto kern = stencil ? k_rows_forward_split<true> : k_rows_forward_split<false>;
+        e = allow_smem(kern, split_rows_smem());
+        if (e == cudaSuccess) kern<<<grid, kTileThreads, split_rows_smem(), s>>>(q);
+        rc = e != cudaSuccess ? cuda_fail("k_rows_forward_split smem", e) : check_launch("k_rows_forward_split");
+      } else {
+        const dim3 grid((a.nz + kS3Units - 1) / kS3Units, nb);
+        auto kern = stencil ? k_rows_forward_s3<true> : k_rows_forward_s3<false>;
+        e = allow_smem(kern, s3_smem());
+        if (e == cudaSuccess) kern<<<grid, kS3Threads, s3_smem(), s>>>(q);
+        rc = e != cudaSuccess ? cuda_fail("k_rows_forward_s3 smem", e) : check_launch("k_rows_forward_s3");
+      }
     }
   }
   if (!split_r) dispatch_len(a.lx, [&]<int LX>() {
@@ -216,12 +255,18 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int 
   if (rc) return rc;
   prof_mark(PROF_COLS, false, s);
   if constexpr (sizeof(C) == sizeof(float2)) {
-    if (split_c) {
+    if (kc == kSplitPair) {
       OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
       const dim3 grid((a.lx + kSplitRows - 1) / kSplitRows, nb);
       cudaError_t e = allow_smem(k_cols_split, split_cols_smem());
       if (e == cudaSuccess) k_cols_split<<<grid, kTileThreads, split_cols_smem(), s>>>(q);
       rc = e != cudaSuccess ? cuda_fail("k_cols_split smem", e) : check_launch("k_cols_split");
+    } else if (kc == kSplitTriple) {
+      OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
+      const dim3 grid((a.lx + kS3Units - 1) / kS3Units, nb);
+      cudaError_t e = allow_smem(k_cols_s3, s3_smem());
+      if (e == cudaSuccess) k_cols_s3<<<grid, kS3Threads, s3_smem(), s>>>(q);
+      rc = e != cudaSuccess ? cuda_fail("k_cols_s3 smem", e) : check_launch("k_cols_s3");
     }
   }
   if (!split_c) dispatch_len(a.lz, [&]<int LZ>() {
@@ -238,13 +283,20 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int 
   if (rc) return rc;
   prof_mark(PROF_ROWS_INVERSE, false, s);
   if constexpr (sizeof(C) == sizeof(float2)) {
-    if (split_r) {
+    if (kr == kSplitPair) {
       OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
       const dim3 grid((a.nz + kSplitRows - 1) / kSplitRows, nb);
       auto kern = a.epi == 1 ? k_rows_inverse_split<1> : a.epi == 2 ? k_rows_inverse_split<2> : k_rows_inverse_split<0>;
       cudaError_t e = allow_smem(kern, split_rows_smem());
       if (e == cudaSuccess) kern<<<grid, kTileThreads, split_rows_smem(), s>>>(q);
       rc = e != cudaSuccess ? cuda_fail("k_rows_inverse_split smem", e) : check_launch("k_rows_inverse_split");
+    } else if (kr == kSplitTriple) {
+      OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
+      const dim3 grid((a.nz + kS3Units - 1) / kS3Units, nb);
+      auto kern = a.epi == 1 ? k_rows_inverse_s3<1> : a.epi == 2 ? k_rows_inverse_s3<2> : k_rows_inverse_s3<0>;
+      cudaError_t e = allow_smem(kern, s3_smem());
+      if (e == cudaSuccess) kern<<<grid, kS3Threads, s3_smem(), s>>>(q);
+      rc = e != cudaSuccess ? cuda_fail("k_rows_inverse_s3 smem", e) : check_launch("k_rows_inverse_s3");
     }
   }
   if (!split_r) dispatch_len(a.lx, [&]<int LX>() {
@@ -281,6 +333,7 @@ template <typename C> static int run_typed(const OpArgs &a, cudaStream_t s) {
 }
 
 int operator_parts(int nz, int lx, int precision) {
+  static_assert(kS3Units == kSplitRows, "split row tiles hold the same number of rows");
   if (split_rows(lx, precision)) return (nz + kSplitRows - 1) / kSplitRows;
   return operator_parts_k(nz, lx, precision);
 }
@@ -311,7 +364,7 @@ using namespace dbi;
 static int check_op(const dbi_grid *g, const dbi_batch *batch, const void *Ghat, const void *in,
                     const void *out, int precision, void *work, size_t work_bytes, int op) {
   int rc;
-  if ((rc = check_grid(g)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
+  if ((rc = check_grid(g, precision)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
   if (batch->B > 0 && (!Ghat || !in || !out)) { set_error("NULL Ghat, input or output"); return DBI_ERR_ARG; }
   if (in == out && batch->B > 0) { set_error("input and output must be distinct buffers"); return DBI_ERR_ARG; }
   const size_t need = dbi_workspace_bytes(g, batch->B, precision, op);

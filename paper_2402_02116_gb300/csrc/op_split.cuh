@@ -27,9 +27,10 @@ constexpr int kSplitLP = RegFFT<float2, kSplitM>::LP; // padded line in shared m
 constexpr int kTwStride = kTwiddleN / kSplitL;        // W_L^j = tw[j * kTwStride]
 
 // Transposition tile of the row stages, one component at a time: [rows][KP]. A thread's pair of
-// points (2k, 2k + 1) is one 16-byte access, and with KP = 8 mod 16 the column-major reads and
-// writes of four rows at a time hit every bank exactly twice per warp (the minimum).
-constexpr int kSplitKP = kSplitL + 8;
+// points (2k, 2k + 1) is one 16-byte access (a quarter warp covers 128 contiguous bytes); the
+// column-major 8-byte reads and writes of four rows at a time are served half a warp at a time,
+// and with KP = 4 mod 16 the four rows x four kx of a half warp hit 16 distinct 8-byte bank slots.
+constexpr int kSplitKP = kSplitL + 4;
 
 // Shared memory (bytes) of the split stages: the lines of one parity (two per row or column) and,
 // for the row stages, the transposition tile of one component.

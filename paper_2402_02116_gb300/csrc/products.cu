@@ -311,7 +311,7 @@ static int check_products(const dbi_model *bg, const dbi_batch *batch, const voi
                           const dbi_krylov_opts *opts, int precision, void *work, size_t work_bytes, int op) {
   int rc;
   if (!bg) { set_error("background model is NULL"); return DBI_ERR_ARG; }
-  if ((rc = check_grid(&bg->grid)) || (rc = check_batch(batch)) || (rc = check_precision(precision)) ||
+  if ((rc = check_grid(&bg->grid, precision)) || (rc = check_batch(batch)) || (rc = check_precision(precision)) ||
       (rc = check_krylov(opts)))
     return rc;
   if (!rec || rec->n < 0 || (rec->n > 0 && !rec->cells)) { set_error("bad receivers"); return DBI_ERR_ARG; }
@@ -371,7 +371,7 @@ extern "C" int data_residual(const dbi_grid *g, const dbi_batch *batch, const db
                              dbi_stream stream) {
   clear_error();
   int rc;
-  if ((rc = check_grid(g)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
+  if ((rc = check_grid(g, precision)) || (rc = check_batch(batch)) || (rc = check_precision(precision))) return rc;
   if (!rec || rec->n < 0 || (rec->n > 0 && !rec->cells)) { set_error("bad receivers"); return DBI_ERR_ARG; }
   if (batch->B > 0 && rec->n > 0 && (!u || !d_obs || !r)) { set_error("NULL u, d_obs or r"); return DBI_ERR_ARG; }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -77,7 +77,7 @@ class GroupMember(ctypes.Structure):
 
 
 class GroupTuning(ctypes.Structure):
-    _fields_ = [("lengths", c_int * 7), ("plan", c_int * 7), ("plan_ms", (c_double * 2) * 7),
+    _fields_ = [("lengths", c_int * 8), ("plan", c_int * 8), ("plan_ms", (c_double * 2) * 8),
                 ("ctas_per_sm", c_int * 3), ("max_ctas", c_int * 3), ("apply_ms", c_double)]
 
 

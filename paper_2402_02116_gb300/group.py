@@ -129,6 +129,6 @@ class UnevenBatch:
         dbi._check(dbi.load().dbi_group_tune(self._h, dbi._ptr(u), dbi._ptr(out), dbi._stream(self.device),
                                              ctypes.byref(rep)), "dbi_group_tune")
         lens = [(rep.lengths[i], rep.plan[i], (rep.plan_ms[i][0], rep.plan_ms[i][1]))
-                for i in range(7) if rep.lengths[i]]
+                for i in range(8) if rep.lengths[i]]
         return {"lengths": lens, "ctas_per_sm": list(rep.ctas_per_sm), "max_ctas": list(rep.max_ctas),
                 "apply_ms": rep.apply_ms}

@@ -263,12 +263,13 @@ def config4_misfit(n=512, n_src=64, nf=6, seed=4) -> Workload:
 
 
 def config5_uneven(sizes=(64, 128, 256, 384, 512), n_members=40, max_src=32, max_f=8, f_range=(2.0, 25.0),
-                   h=5.0, seed=5) -> list:
+                   h=5.0, seed=5, radix3=True) -> list:
     """Uneven batch: n_members independent problems, each with a square grid drawn from `sizes`,
     1..max_src surface sources, 1..max_f frequencies drawn in f_range (sorted), an isotropic
     (rho 2000, alpha 2000, beta 1155) or VTI background (as config 2) and 1-4 Gaussian anomalies
     (sigma N/32 .. N/8 cells) of +/-15 % with a random sign per parameter. The FFT grid of each is
-    the smallest power of two >= 2N - 1 (384 cells -> 1024)."""
+    the smallest complex64 length >= 2N - 1 (fft_len: 384 cells -> 768; with radix3=False the
+    smallest power of two, 384 cells -> 1024)."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n_members):
@@ -287,7 +288,7 @@ def config5_uneven(sizes=(64, 128, 256, 384, 512), n_members=40, max_src=32, max
         pert = _random_anomalies(rng, n, n, count, 0.15, (n / 32.0, n / 8.0))
         model = m_bg * (1.0 + np.clip(pert, -0.15, 0.15))
         cols = surface_line(n, n_src)
-        L = fft_len(n)
+        L = fft_len(n, radix3)
         out.append(Workload(
             name=f"{'vti' if vti else 'iso'}{n}x{n}_{n_src}src_{nf}f", nz=n, nx=n, h=h, lz=L, lx=L,
             rho0=rho0, alpha0=a0, beta0=b0, model=model, freqs_hz=freqs,
@@ -298,12 +299,13 @@ def config5_uneven(sizes=(64, 128, 256, 384, 512), n_members=40, max_src=32, max
     return out
 
 
-def fft_len(n: int) -> int:
-    """Smallest power of two >= max(16, 2n - 1): an FFT length that holds every offset of n cells."""
+def fft_len(n: int, radix3: bool = False) -> int:
+    """Smallest power of two >= max(16, 2n - 1): an FFT length that holds every offset of n cells.
+    With radix3, 768 (= 3 x 256, a complex64 length of the library) when 512 < 2n - 1 <= 768."""
     p = 16
     while p < 2 * n - 1:
         p *= 2
-    return p
+    return 768 if radix3 and p == 1024 and 2 * n - 1 <= 768 else p
 
 
 def small_case(nz=12, nx=10, h=10.0, seed=11, n_src=2, freqs=(8.0, 14.0), amp=0.1, vti=False,

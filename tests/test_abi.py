@@ -53,6 +53,11 @@ def test_workspace_query_is_host_only(lib):
     assert dbi.workspace_bytes(bad, 4, dbi.C64, dbi.OP_APPLY) == 0
     small = dbi.make_grid(40, 32, 64, 64, 10.0)  # 64 < 2 * 40 - 1
     assert dbi.workspace_bytes(small, 4, dbi.C64, dbi.OP_APPLY) == 0
+    g768 = dbi.make_grid(384, 300, 768, 768, 5.0)  # 3 x 256: a complex64 length only
+    spectra, sources = 4 * 2 * 768 * 384 * 8, 4 * 2 * 384 * 300 * 8
+    assert dbi.workspace_bytes(g768, 4, dbi.C64, dbi.OP_APPLY) >= spectra + sources
+    assert dbi.workspace_bytes(g768, 4, dbi.C128, dbi.OP_APPLY) == 0
+    assert dbi.workspace_bytes(dbi.make_grid(384, 300, 768, 512, 5.0), 4, dbi.C64, dbi.OP_APPLY) == 0  # 512 < 599
 
 
 def test_argument_errors_are_reported_without_a_gpu(lib):
@@ -74,6 +79,13 @@ def test_argument_errors_are_reported_without_a_gpu(lib):
     vti = dbi.make_medium_vti(2200.0, 1.65e10, 5.6e9, 1.375e10, 4.58e9)
     rc = lib.greens_tabulate_k(ctypes.byref(g), ctypes.byref(vti), None, 1, 0, None, None, 0, None)
     assert rc == -1 and b"isotropic" in lib.dbi_last_error()
+    g768 = dbi.make_grid(300, 300, 768, 768, 5.0)  # the paper-literal form K has no length-768 stages
+    rc = lib.greens_tabulate_k(ctypes.byref(g768), ctypes.byref(ref), None, 1, 0, None, None, 0, None)
+    assert rc == -2 and b"power of two" in lib.dbi_last_error()
+    rc = lib.greens_tabulate(ctypes.byref(g768), ctypes.byref(ref), None, 1, 1, None, None, None, 0, None)
+    assert rc == -2 and b"768 with complex64" in lib.dbi_last_error()  # complex128
+    rc = lib.greens_tabulate(ctypes.byref(g768), ctypes.byref(ref), None, 1, 0, None, None, None, 0, None)
+    assert rc == -1 and b"need nf" in lib.dbi_last_error()  # complex64: the grid passes
     rc = lib.dbi_gmres_workspace_bytes(ctypes.byref(g), 4, 0, 65)
     assert rc == 0
     model = dbi.Model(g, ref, None)

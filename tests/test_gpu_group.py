@@ -34,7 +34,7 @@ def rel(a, b):
 
 
 # A small mixed batch: ragged shapes, non-square and oversized FFT grids, one-row and one-slot
-# members, isotropic and VTI backgrounds, several row and column tiles, FFT length 1024.
+# members, isotropic and VTI backgrounds, several row and column tiles, FFT lengths 1024 and 768.
 MINI = [
     dict(nz=12, nx=10, n_src=2, freqs=(8.0, 14.0), seed=71),
     dict(nz=5, nx=9, lz=16, lx=32, n_src=1, freqs=(11.0,), seed=72),
@@ -47,11 +47,17 @@ MINI = [
     dict(nz=35, nx=33, lz=1024, lx=1024, vti=True, n_src=1, freqs=(9.0,), seed=77),
     dict(nz=9, nx=50, lz=32, lx=1024, n_src=1, freqs=(13.0,), seed=78),
     dict(nz=40, nx=7, lz=1024, lx=16, n_src=1, freqs=(6.0,), seed=79),
+    # FFT length 768 (complex64: triples of 256-point transforms), alone and beside 1024
+    dict(nz=29, nx=300, lz=768, lx=768, vti=True, n_src=1, freqs=(8.0,), seed=81),
+    dict(nz=33, nx=257, lz=1024, lx=768, n_src=1, freqs=(12.0,), seed=82),
+    dict(nz=300, nx=12, lz=768, lx=32, n_src=1, freqs=(7.0,), seed=83),
 ]
 
 
-def mini_workloads():
-    return [inputs.small_case(amp=0.1, **kw) for kw in MINI]
+def mini_workloads(precision=dbi.C64):
+    """The small mixed batch (complex128: without the length-768 members, a complex64 length)."""
+    return [inputs.small_case(amp=0.1, **kw) for kw in MINI
+            if precision == dbi.C64 or 768 not in (kw.get("lz"), kw.get("lx"))]
 
 
 def member_oracle(w, omegas=None):
@@ -61,7 +67,7 @@ def member_oracle(w, omegas=None):
 
 @pytest.mark.parametrize("precision", [dbi.C128, dbi.C64])
 def test_group_apply_matches_oracle(precision):
-    ws = mini_workloads()
+    ws = mini_workloads(precision)
     Ps = [DeviceProblem(w, precision) for w in ws]
     G = UnevenBatch(Ps, precision)
     u = G.join([torch.as_tensor(inputs.seeded_complex((P.B, 2, P.w.nz, P.w.nx), 80 + k)).to(P.device, P.cdt)
@@ -91,7 +97,7 @@ def test_group_apply_equals_single_grid_path():
 
 @pytest.mark.parametrize("precision,graph", [(dbi.C128, True), (dbi.C128, False), (dbi.C64, True)])
 def test_group_solve_matches_oracle(precision, graph):
-    ws = mini_workloads()
+    ws = mini_workloads(precision)
     Ps = [DeviceProblem(w, precision) for w in ws]
     G = UnevenBatch(Ps, precision)
     rhs = G.incident()

@@ -426,3 +426,73 @@ def test_length_1024_split_stages(shape):
     for b, f in enumerate(w.problem_fidx()):
         ref = orc.solve(bs[b], w.model, f, tol=1e-12)
         assert rel(xs[b], ref) < 1e-5, b
+
+
+# FFT length 768 = 3 x 256 (complex64): each half-pruned transform as three 256-point transforms of
+# the folded, twiddled line, the contrast source by the 32-row source kernel, the Green's tables by
+# the FP64 768-point table FFT (stored residue-major along kz). Ragged rows and columns, more than
+# 256 points (the fold's second third), one row, one column, 768 along one axis only and beside
+# 1024 along the other.
+S3_SHAPES = [
+    dict(nz=37, nx=300, lz=768, lx=768),     # ragged, nx > 256
+    dict(nz=1, nx=384, lz=16, lx=768),       # one row at full width, triple rows only
+    dict(nz=384, nx=1, lz=768, lx=16),       # one column at full height, triple columns only
+    dict(nz=130, nx=45, lz=768, lx=128, vti=True),  # triple columns, a partial source chunk
+    dict(nz=200, nx=380, lz=768, lx=1024),   # triple columns beside pair rows
+    dict(nz=300, nx=257, lz=1024, lx=768),   # pair columns beside triple rows
+]
+
+
+def residue_major_to_natural(Ghat_kz_last, lz):
+    """Entries [..., kz] in natural order from the stored order (residue-major at lz = 768)."""
+    if lz != 768:
+        return Ghat_kz_last
+    slots = np.array([(k % 3) * 256 + k // 3 for k in range(768)])
+    return Ghat_kz_last[..., slots]
+
+
+@pytest.mark.parametrize("shape", S3_SHAPES, ids=lambda s: f"{s['nz']}x{s['nx']}_L{s['lz']}x{s['lx']}")
+def test_length_768_triple_stages(shape):
+    w = inputs.small_case(freqs=(4.0, 15.0), n_src=2, amp=0.12, h=5.0, **shape)
+    P = DeviceProblem(w, dbi.C64)
+    orc = oracle_for(w)
+    for f in range(w.nf):
+        Gh = np.swapaxes(orc.G_hat[f] * w.h * w.h / (w.lz * w.lx), -1, -2)  # [c][kx][kz]
+        assert rel(residue_major_to_natural(npy(P.Ghat[f]), w.lz), Gh) < 1e-5, f
+        assert rel(npy(P.Gspace[f]), O.embed_circulant(orc.G_lat[f], w.lz, w.lx)) < 1e-6, f
+    u = inputs.seeded_complex((P.B, 2, w.nz, w.nx), 78)
+    out = npy(P.apply(P.to_field(u)))
+    conv = npy(P.convolve(P.to_field(u)))
+    for b, f in enumerate(w.problem_fidx()):
+        want = orc.apply(u[b], w.model, f)
+        assert rel(out[b] - u[b], want - u[b]) < TOL[dbi.C64], b
+        assert rel(conv[b], orc.convolve(u[b].astype(np.complex128), f)) < TOL[dbi.C64], b
+    # the incident field and the solver's fused inner products on the same stages
+    u0 = P.incident()
+    srcs = w.problem_src()
+    x, _, _, code = P.solve(u0, tol=1e-6)
+    assert np.all(npy(code) == dbi.CONVERGED)
+    xs, bs = npy(x).astype(np.complex128), npy(u0).astype(np.complex128)
+    for b, f in enumerate(w.problem_fidx()):
+        assert rel(bs[b], orc.incident(f, w.src_cells[srcs[b]], w.src_force[srcs[b]])) < 1e-6, b
+        assert rel(xs[b], orc.solve(bs[b], w.model, f, tol=1e-12)) < 1e-5, b
+
+
+def test_length_768_products():
+    """The distorted-Born products on the length-768 stages: the Frechet derivative against the
+    oracle, and the dot test between it and the adjoint imaging."""
+    w = inputs.small_case(nz=40, nx=300, lz=128, lx=768, amp=0.12, vti=True, n_src=2, freqs=(7.0, 12.0),
+                          seed=35, h=5.0)
+    P = DeviceProblem(w, dbi.C64)
+    orc = oracle_for(w)
+    fidx = w.problem_fidx()
+    U = orc.forward(w.model, fidx, w.src_cells[w.problem_src()], w.src_force[w.problem_src()])
+    Ub = P.to_field(U)
+    dm = inputs.seeded_real((5, w.nz, w.nx), 16) * orc.param_scale()[:, None, None] * 0.01
+    Jd = npy(P.frechet(Ub, P.to_model(dm), tol=1e-7)).astype(np.complex128)
+    assert rel(Jd, orc.frechet(w.model, U, fidx, dm, w.rec_cells)) < 1e-5
+    R = inputs.seeded_complex((len(fidx), len(w.rec_cells), 2), 17)
+    g = npy(P.adjoint(Ub, P.to_field(R), tol=1e-7)).astype(np.float64)
+    lhs = np.real(np.vdot(R, Jd))
+    rhs = np.sum(npy(P.to_model(dm)).astype(np.float64) * g)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5

@@ -82,6 +82,23 @@ def test_bad_members_are_rejected(lib):
     assert lib.dbi_group_create(m, 1, dbi.C64, ctypes.byref(h)) == -1
 
 
+def test_length_768_members_are_complex64_only(lib):
+    """FFT length 768 (3 x 256) is a complex64 length: a member with it is planned in complex64, and
+    its row stages add a contrast-source scratch field per slot to the workspace; complex128 rejects
+    it like any other length that is not a power of two."""
+    specs = [(384, 384, 768, 768, 2), (40, 300, 128, 768, 1), (64, 64, 128, 128, 3)]
+    rc, h = make(lib, specs, dbi.C64)
+    assert rc == 0
+    try:
+        spectra = sum(2 * B * lx * nz * 8 for nz, nx, lz, lx, B in specs)
+        sources = sum(2 * B * nz * nx * 8 for nz, nx, lz, lx, B in specs if lx == 768)
+        assert lib.dbi_group_workspace_bytes(h, dbi.OP_APPLY) >= spectra + sources
+    finally:
+        lib.dbi_group_destroy(h)
+    rc, h = make(lib, specs, dbi.C128)
+    assert rc == -2 and not h.value and b"power of two" in lib.dbi_last_error()
+
+
 def test_unbound_plan_refuses_work(lib):
     rc, h = make(lib, [(8, 8, 16, 16, 1)])
     try:
@@ -142,8 +159,9 @@ def test_random_invalid_members_are_rejected(lib):
         kind = trial % 3
         nz, nx = int(rng.integers(2, 200)), int(rng.integers(2, 200))
         lz, lx = _pow2_at_least(2 * nz - 1), _pow2_at_least(2 * nx - 1)
-        if kind == 0:
-            bad = (nz, nx, 3 * lz // 2 if lz >= 32 else 48, lx, 1)
+        if kind == 0:  # not a power of two, and not 768 (3 x 256, a complex64 length)
+            bl = 3 * lz // 2 if lz >= 32 else 48
+            bad = (nz, nx, 640 if bl == 768 else bl, lx, 1)
         elif kind == 1:
             bad = (nz, nx, lz // 2 if lz > 16 and lz // 2 < 2 * nz - 1 else lz, lx // 2 if lx > 16 else 8, 1)
         else:

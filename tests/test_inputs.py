@@ -73,13 +73,20 @@ def test_config4_misfit_workload():
     assert np.allclose(p, 0.1, rtol=1e-12)
 
 
+def test_fft_len():
+    assert [I.fft_len(n) for n in (1, 8, 9, 256, 257, 384, 385, 512)] == [16, 16, 32, 512, 1024, 1024, 1024, 1024]
+    assert [I.fft_len(n, radix3=True) for n in (256, 257, 384, 385, 512)] == [512, 768, 768, 1024, 1024]
+
+
 def test_config5_uneven_batch():
     ws = I.config5_uneven()
+    assert [w.lz for w in I.config5_uneven(radix3=False)] == [1024 if w.lz == 768 else w.lz for w in ws]
     assert len(ws) == 40
     assert sum(w.n_problems for w in ws) == 3074
     assert sum(w.n_problems * w.nz * w.nx for w in ws) == 289_759_232
     for w in ws:
-        assert w.nz == w.nx and w.nz in (64, 128, 256, 384, 512) and w.lz == w.lx == _pow2_at_least(2 * w.nz - 1)
+        L = 768 if w.nz == 384 else _pow2_at_least(2 * w.nz - 1)  # 3 x 256 for the 384^2 members
+        assert w.nz == w.nx and w.nz in (64, 128, 256, 384, 512) and w.lz == w.lx == L
         assert 1 <= w.n_src <= 32 and 1 <= len(w.freqs_hz) <= 8
         assert np.all(np.diff(w.freqs_hz) >= 0) and w.freqs_hz.min() >= 2.0 and w.freqs_hz.max() <= 25.0
 
