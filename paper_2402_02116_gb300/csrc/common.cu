@@ -117,18 +117,21 @@ int check_precision(int precision) {
   return DBI_OK;
 }
 
-// W_3072^m = exp(-2 pi i m / 3072) evaluated in FP64 with sincospi and rounded to the precision.
+// W_3072^m = exp(-2 pi i m / 3072) for m < 3072, then W_1024^j for j = m - 3072 < 1024, evaluated
+// in FP64 with sincospi and rounded to the precision (W_1024^j has the argument of W_3072^{3j}
+// exactly, so the two tables agree bit for bit).
 template <typename C>
 __global__ void twiddle_kernel(C *tw) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= kTwiddleN) return;
+  if (m >= kTwiddleTotal) return;
   double s, c;
-  sincospi(-2.0 * double(m) / double(kTwiddleN), &s, &c);
+  if (m < kTwiddleN) sincospi(-2.0 * double(m) / double(kTwiddleN), &s, &c);
+  else sincospi(-2.0 * double(m - kTw1024) / 1024.0, &s, &c);
   tw[m] = mk<C>(c, s);
 }
 
 int launch_twiddles(void *tw, int precision, cudaStream_t s) {
-  const int threads = 256, blocks = (kTwiddleN + threads - 1) / threads;
+  const int threads = 256, blocks = (kTwiddleTotal + threads - 1) / threads;
   if (precision == DBI_C64) twiddle_kernel<float2><<<blocks, threads, 0, s>>>(static_cast<float2 *>(tw));
   else twiddle_kernel<double2><<<blocks, threads, 0, s>>>(static_cast<double2 *>(tw));
   return check_launch("twiddle_kernel");
@@ -136,7 +139,7 @@ int launch_twiddles(void *tw, int precision, cudaStream_t s) {
 
 static size_t csize(int precision) { return precision == DBI_C64 ? sizeof(float2) : sizeof(double2); }
 
-size_t bytes_twiddles(int precision) { return align256(size_t(kTwiddleN) * csize(precision)); }
+size_t bytes_twiddles(int precision) { return align256(size_t(kTwiddleTotal) * csize(precision)); }
 
 int spectral_chunk(const dbi_grid *g, int B, int precision) {
   // Default: the whole batch in one pass (measured faster on the 256-problem benchmark batch than
@@ -230,7 +233,7 @@ extern "C" size_t dbi_workspace_bytes(const dbi_grid *g, int B, int precision, i
   const size_t model = align256(size_t(5) * g->nz * g->nx * sizeof(double));
   switch (op) {
     case DBI_OP_GREENS:  // B counts frequencies here
-      return align256(size_t(kTwiddleN) * sizeof(double2)) +
+      return bytes_twiddles(DBI_C128) +
              align256(size_t(B) * 3 * g->lz * g->lx * sizeof(double2));
     case DBI_OP_CONVOLVE:
     case DBI_OP_APPLY:
@@ -248,7 +251,7 @@ extern "C" size_t dbi_workspace_bytes(const dbi_grid *g, int B, int precision, i
              align256(4097 * sizeof(double));
     }
     case DBI_OP_GREENS_K:  // B counts frequencies here
-      return align256(size_t(kTwiddleN) * sizeof(double2)) +
+      return bytes_twiddles(DBI_C128) +
              align256(size_t(B) * 6 * g->lz * g->lx * sizeof(double2));
     case DBI_OP_APPLY_K:  // spectra of the five sources and of the two outputs
       return tw + bytes_spectral_k(g, B, precision) + bytes_scales(B);

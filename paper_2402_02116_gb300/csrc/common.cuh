@@ -47,6 +47,11 @@ template <typename C> __device__ __forceinline__ C czero() { return mk<C>(0, 0);
 // sizes and launch helpers
 // ---------------------------------------------------------------------------------------------
 constexpr int kTwiddleN = 3072;  // W_3072^m covers every FFT length that divides 3072
+// The twiddle buffer holds W_3072^m (m < 3072) and after it W_1024^j (j < 1024) contiguously, so
+// that the length-1024 kernels' per-point twiddles W_1024^{t + 64 m} are coalesced loads (from
+// the first table they are 24 bytes apart: three times the sectors).
+constexpr int kTw1024 = kTwiddleN;
+constexpr int kTwiddleTotal = kTwiddleN + 1024;
 
 inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 

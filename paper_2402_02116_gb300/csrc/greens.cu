@@ -359,7 +359,7 @@ extern "C" int greens_tabulate_k(const dbi_grid *g, const dbi_medium *ref, const
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Arena ar(work, work_bytes);
-  double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
+  double2 *tw = static_cast<double2 *>(ar.take(bytes_twiddles(DBI_C128)));
   const size_t tab = size_t(nf) * 6 * g->lz * g->lx;
   double2 *W = static_cast<double2 *>(ar.take(tab * sizeof(double2)));
   if ((rc = ar.check("greens_tabulate_k"))) return rc;
@@ -409,7 +409,7 @@ extern "C" int greens_tabulate(const dbi_grid *g, const dbi_medium *ref, const d
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Arena ar(work, work_bytes);
-  double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
+  double2 *tw = static_cast<double2 *>(ar.take(bytes_twiddles(DBI_C128)));
   double2 *W = static_cast<double2 *>(ar.take(size_t(nf) * 3 * g->lz * g->lx * sizeof(double2)));
   if ((rc = ar.check("greens_tabulate"))) return rc;
   if ((rc = launch_twiddles(tw, DBI_C128, s))) return rc;

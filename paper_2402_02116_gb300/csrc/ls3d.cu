@@ -698,7 +698,7 @@ extern "C" size_t dbi_workspace_bytes_3d(const dbi_grid3 *g, int B, int precisio
   const size_t tw = bytes_twiddles(precision);
   switch (op) {
     case DBI_OP_GREENS:  // B counts frequencies
-      return align256(size_t(kTwiddleN) * sizeof(double2)) +
+      return bytes_twiddles(DBI_C128) +
              align256(size_t(B) * 6 * g->lz * g->ly * g->lx * sizeof(double2));
     case DBI_OP_APPLY:
       return tw + bytes_spec3(g, B, precision) + bytes_sig3(g, B, precision) + bytes_scales(B);
@@ -729,7 +729,7 @@ extern "C" int greens_tabulate_3d(const dbi_grid3 *g, const dbi_medium *ref, con
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   Arena ar(work, work_bytes);
-  double2 *tw = static_cast<double2 *>(ar.take(size_t(kTwiddleN) * sizeof(double2)));
+  double2 *tw = static_cast<double2 *>(ar.take(bytes_twiddles(DBI_C128)));
   const size_t vol = size_t(g->lz) * g->ly * g->lx, tab = size_t(nf) * 6 * vol;
   double2 *W = static_cast<double2 *>(ar.take(tab * sizeof(double2)));
   if ((rc = ar.check("greens_tabulate_3d"))) return rc;

@@ -24,7 +24,7 @@ constexpr int kSplitL = 1024, kSplitM = 512;
 constexpr int kSplitT = kSplitM / 8;                  // threads per line (64)
 constexpr int kSplitRows = kTileThreads / kSplitT;    // rows (or columns) per 256-thread tile (4)
 constexpr int kSplitLP = RegFFT<float2, kSplitM>::LP; // padded line in shared memory
-constexpr int kTwStride = kTwiddleN / kSplitL;        // W_L^j = tw[j * kTwStride]
+static_assert(kSplitL == 1024, "the per-point twiddles come from the contiguous W_1024 table");
 
 // Transposition tile of the row stages, one component at a time: [rows][KP]. A thread's pair of
 // points (2k, 2k + 1) is one 16-byte access (a quarter warp covers 128 contiguous bytes); the
@@ -45,13 +45,14 @@ constexpr int kSrcThreads = kSplitM, kSrcRows = 32, kSrcW = kSrcThreads + 2;
 inline size_t source_smem() { return size_t(8) * kSrcW * sizeof(float2); }
 
 // s = w^2 drho u + div(dC : eps(u)) (Eq. 6) on rows [zb, zb + kSrcRows) of one problem, written to
-// S [2][nz][nx]. Row by row: u of the next row is loaded (times the input scale; zero outside D),
-// the stress sigma = dC eps(u) of the row above it is formed from u one row up and down (held in
-// registers) and u one column left and right (shared memory), and the source of the row above
-// that from sigma5, sigma3 one row up and down (registers) and sigma1, sigma5 one column left and
-// right (shared memory). The global loads of each step are issued one step ahead (u two rows
-// down, the stiffness one row down, the density of the current row), so that their latency
-// overlaps a step's work. Every thread takes part in every barrier.
+// S [2][nz][nx]. Step j: the stress sigma = dC eps(u) of row j is formed from u one row up and down
+// (registers) and u one column left and right (shared memory, stored by the step before), and the
+// source of row j - 1 from sigma5, sigma3 of rows j and j - 2 (registers) and sigma1, sigma5 of row
+// j - 1 one column left and right (shared memory, stored by the step before); then u of row j + 1
+// and sigma of row j are stored for the next step. The reads and writes of a step touch different
+// parity slots, so one barrier per row suffices. The global loads of a step are issued one step
+// ahead (u two rows down, the stiffness one row down, the density of the current row) so that
+// their latency overlaps a step's work. Every thread takes part in every barrier.
 template <typename A>
 __device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem, float2 *S) {
   using C = float2;
@@ -59,38 +60,42 @@ __device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem,
   const int ze = min(zb + kSrcRows, nz);
   const size_t plane = size_t(nz) * nx;
   const bool col = x < nx;
+  const int xc = col ? x : 0;
   const float isc = a.isc(), ms = a.ms(), f = a.inv2h(), w2 = a.w2();
   const float r0 = a.ref(0), r1 = a.ref(1), r2 = a.ref(2), r3 = a.ref(3), r4 = a.ref(4);
-  const C *u1p = a.in(), *u3p = u1p + plane;
-  const float *m = a.m();
+  // this thread's column (row 0) of every field; row z lies z * nx further
+  const C *u1p = a.in() + xc, *u3p = u1p + plane;
+  const float *m0 = a.m() + xc;
+  C *o1p = S + xc, *o3p = o1p + plane;
   // shared rows (index x + 1; entries 0 and nx + 1 .. stay zero): u1, u3 and sigma1, sigma5, two
   // slots each by row parity
   C *su = smem, *sg = smem + 4 * kSrcW;
   auto U = [&](int slot, int c) { return su + (slot * 2 + c) * kSrcW + 1; };
   auto G = [&](int slot, int c) { return sg + (slot * 2 + c) * kSrcW + 1; };
   for (int i = threadIdx.x; i < 8 * kSrcW; i += kSrcThreads) smem[i] = czero<C>();
-  auto in_d = [&](int z) { return col && z >= 0 && z < nz; };
+  auto in_d = [&](int z) { return col && unsigned(z) < unsigned(nz); };
   auto load_u = [&](int z, C &v1, C &v3) {
     const bool in = in_d(z);
-    v1 = in ? __ldg(u1p + size_t(z) * nx + x) : czero<C>();
-    v3 = in ? __ldg(u3p + size_t(z) * nx + x) : czero<C>();
+    const int o = in ? z * nx : 0;
+    v1 = in ? __ldg(u1p + o) : czero<C>();
+    v3 = in ? __ldg(u3p + o) : czero<C>();
   };
   struct Stiff {
     float d11, d13, d33, d55;
   };
   auto load_stiff = [&](int z, Stiff &d) {
     const bool in = in_d(z);
-    const size_t cell = size_t(in ? z : 0) * nx + (col ? x : 0);
-    d.d11 = in ? __ldg(m + 1 * plane + cell) : r1;
-    d.d13 = in ? __ldg(m + 2 * plane + cell) : r2;
-    d.d33 = in ? __ldg(m + 3 * plane + cell) : r3;
-    d.d55 = in ? __ldg(m + 4 * plane + cell) : r4;
+    const float *mz = m0 + (in ? z * nx : 0);
+    d.d11 = in ? __ldg(mz + 1 * plane) : r1;
+    d.d13 = in ? __ldg(mz + 2 * plane) : r2;
+    d.d33 = in ? __ldg(mz + 3 * plane) : r3;
+    d.d55 = in ? __ldg(mz + 4 * plane) : r4;
   };
-  auto load_rho = [&](int z) { return in_d(z) ? __ldg(m + size_t(z) * nx + x) : r0; };
-  // window: u at rows j - 1, j, j + 1 (scaled); sigma3, sigma5 at rows j - 2, j - 1, j
-  C ua1, ua3, ub1, ub3, uc1, uc3;
+  auto load_rho = [&](int z) { return in_d(z) ? __ldg(m0 + z * nx) : r0; };
+  // window: u at rows j - 1, j (scaled); sigma3, sigma5 at rows j - 2, j - 1
+  C ua1, ua3, ub1, ub3;
   C s3a = czero<C>(), s5a = czero<C>(), s3b = czero<C>(), s5b = czero<C>();
-  const int j0 = zb - 1;
+  const int j0 = zb - 1;  // odd: zb is a multiple of kSrcRows (even), so step parities are static
   load_u(j0 - 1, ua1, ua3);
   load_u(j0, ub1, ub3);
   ua1 = cscale(ua1, isc); ua3 = cscale(ua3, isc);
@@ -104,22 +109,18 @@ __device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem,
   __syncthreads();  // the zero fill precedes every row store
   U(j0 & 1, 0)[x] = ub1;
   U(j0 & 1, 1)[x] = ub3;
-  for (int j = j0; j <= ze; ++j) {
-    uc1 = cscale(nu1, isc);
-    uc3 = cscale(nu3, isc);
+  __syncthreads();
+  auto step = [&]<int P>(int j) {  // P = j & 1
+    const C uc1 = cscale(nu1, isc), uc3 = cscale(nu3, isc);
     const Stiff d = nd;
     const float rho = nrho;
     load_u(j + 2, nu1, nu3);  // the next step's loads
     load_stiff(j + 1, nd);
     nrho = load_rho(j);
-    const int sl = j & 1, sn = (j + 1) & 1;
-    U(sn, 0)[x] = uc1;
-    U(sn, 1)[x] = uc3;
-    __syncthreads();
     // sigma(j, x)
     C s1 = czero<C>(), s3 = czero<C>(), s5 = czero<C>();
     if (in_d(j)) {
-      const C *r1u = U(sl, 0), *r3u = U(sl, 1);
+      const C *r1u = U(P, 0), *r3u = U(P, 1);
       const C e1 = cscale(csub(r1u[x + 1], r1u[x - 1]), f);
       const C e3 = cscale(csub(uc3, ua3), f);
       const C e5 = cscale(cadd(csub(uc1, ua1), csub(r3u[x + 1], r3u[x - 1])), f);
@@ -128,23 +129,32 @@ __device__ __forceinline__ void source_rows(const A &a, int chunk, float2 *smem,
       s3 = cadd(cscale(e1, d13), cscale(e3, d33));
       s5 = cscale(e5, d55);
     }
-    G(sl, 0)[x] = s1;
-    G(sl, 1)[x] = s5;
-    __syncthreads();
     // source at row j - 1
     const int z = j - 1;
     if (col && z >= zb && z < ze) {
-      const C *g1 = G(sl ^ 1, 0), *g5 = G(sl ^ 1, 1);
+      const C *g1 = G(P ^ 1, 0), *g5 = G(P ^ 1, 1);
       const C o1 = cscale(cadd(csub(g1[x + 1], g1[x - 1]), csub(s5, s5a)), f);
       const C o3 = cscale(cadd(csub(g5[x + 1], g5[x - 1]), csub(s3, s3a)), f);
-      const size_t cell = size_t(z) * nx + x;
+      const int cell = z * nx;
       const float wr = w2 * (rho - r0) * ms;
-      S[cell] = cadd(o1, cscale(ua1, wr));  // u(j - 1)
-      S[plane + cell] = cadd(o3, cscale(ua3, wr));
+      o1p[cell] = cadd(o1, cscale(ua1, wr));  // u(j - 1)
+      o3p[cell] = cadd(o3, cscale(ua3, wr));
     }
+    // u(j + 1) and sigma(j) for the next step (slots read by the step before)
+    U(P ^ 1, 0)[x] = uc1;
+    U(P ^ 1, 1)[x] = uc3;
+    G(P, 0)[x] = s1;
+    G(P, 1)[x] = s5;
+    __syncthreads();
     ua1 = ub1; ua3 = ub3; ub1 = uc1; ub3 = uc3;
     s3a = s3b; s5a = s5b; s3b = s3; s5b = s5;
+  };
+  int j = j0;
+  for (; j + 1 <= ze; j += 2) {
+    step.template operator()<1>(j);
+    step.template operator()<0>(j + 1);
   }
+  if (j <= ze) step.template operator()<1>(j);
 }
 
 // The two parities of the two components, each an M-point transform held as 8 points per thread:
@@ -180,7 +190,7 @@ __device__ __forceinline__ void cols_tile_split(const A &a, int tile, float2 *sm
     const int z = t + m * T;
     const bool in = live && z < nz;
     const C x0 = in ? c0[z] : czero<C>(), x1 = in ? c1[z] : czero<C>();
-    const C w = __ldg(tw + z * kTwStride);  // W_L^z
+    const C w = __ldg(tw + kTw1024 + z);  // W_L^z
     v[0][0][m] = x0;
     v[0][1][m] = x1;
     v[1][0][m] = hmul(x0, w);
@@ -212,7 +222,7 @@ __device__ __forceinline__ void cols_tile_split(const A &a, int tile, float2 *sm
     for (int m = 0; m < 8; ++m) {
       const int z = t + m * T;
       if (z < nz) {
-        const C w = cconj(__ldg(tw + z * kTwStride));  // W_L^{-z}
+        const C w = cconj(__ldg(tw + kTw1024 + z));  // W_L^{-z}
         c0[z] = cadd(v[0][0][m], cmul(w, v[1][0][m]));
         c1[z] = cadd(v[0][1][m], cmul(w, v[1][1][m]));
       }
@@ -241,7 +251,7 @@ __device__ __forceinline__ void rows_forward_tile_split(const A &a, int tile, fl
     const bool in = z < nz && x < nx;
     const C s0 = in ? cscale(__ldg(src + size_t(z) * nx + x), scale) : czero<C>();
     const C s1 = in ? cscale(__ldg(src + plane + size_t(z) * nx + x), scale) : czero<C>();
-    const C w = __ldg(tw + x * kTwStride);
+    const C w = __ldg(tw + kTw1024 + x);  // W_L^x
     v[0][0][m] = s0;
     v[0][1][m] = s1;
     v[1][0][m] = hmul(s0, w);
@@ -312,7 +322,7 @@ __device__ __forceinline__ void rows_inverse_tile_split(const A &a, int tile, fl
   C y[2][8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    const C w = cconj(__ldg(tw + (t + m * T) * kTwStride));
+    const C w = cconj(__ldg(tw + kTw1024 + t + m * T));  // W_L^{-x}
 #pragma unroll
     for (int c = 0; c < 2; ++c) y[c][m] = cadd(v[0][c][m], cmul(w, v[1][c][m]));
   }
