@@ -33,6 +33,7 @@ template <typename C> struct OpP {
   const int *active;
   const int *plist;  // slot -> problem (NULL: problem = s0 + slot)
   int s0;            // first slot of this launch
+  int nb;            // slots in this launch
   const double *in_scale, *m_scale, *out_scale;
   const C *krhat;
   double *part_out;
@@ -125,11 +126,36 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_rows_forward_split(OpP<floa
   else rows_forward_tile_split(a, blockIdx.x, smem, a.in(), a.isc());
 }
 
+// Column kx = blockIdx.x of the four launch slots 4 blockIdx.y .. + 3 (64 threads each). The
+// column's Green's tables of the first slot's frequency are staged in shared memory by
+// asynchronous copies issued before the forward transforms, so their latency is hidden; slots of
+// that frequency (consecutive slots share it, problems being frequency-major) read them there,
+// others from global memory.
 __global__ void __launch_bounds__(kTileThreads, 2) k_cols_split(OpP<float2> p) {
-  const int b = problem_of(p), f = p.fidx[b];
-  if ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cols_tile_split(BatchTile<float2>{p, b, int(blockIdx.y), f}, blockIdx.x, reinterpret_cast<float2 *>(smem_raw));
+  float2 *smem = reinterpret_cast<float2 *>(smem_raw);
+  float4 *Gs = reinterpret_cast<float4 *>(smem + split_lines_smem() / sizeof(float2));
+  const int g = threadIdx.x / kSplitT, kx = blockIdx.x;
+  const int sl0 = 4 * int(blockIdx.y), sl = sl0 + g;
+  auto prob = [&](int slot) { return p.plist ? p.plist[p.s0 + slot] : p.s0 + slot; };
+  auto freq = [&](int slot) {  // the slot's table, or -1 when it has no work
+    if (slot >= p.nb) return -1;
+    const int b = prob(slot), f = p.fidx[b];
+    return ((p.active && !p.active[b]) || unsigned(f) >= unsigned(p.nf)) ? -1 : f;
+  };
+  const int f0 = freq(sl0), f = freq(sl);
+  if (f0 >= 0) {  // Ghat(:, kx) of table f0: 3 x 1024 points, six 16-byte copies per thread
+    const float2 *G = p.Ghat + size_t(f0) * 3 * p.lx * kSplitL + size_t(kx) * kSplitL;
+    const size_t plane = size_t(p.lx) * kSplitL;
+#pragma unroll
+    for (int i = 0; i < 3 * kSplitL / 2 / kTileThreads; ++i) {
+      const int e = threadIdx.x + i * kTileThreads, tb = e / (kSplitL / 2), k = e - tb * (kSplitL / 2);
+      cp_async16(Gs + e, G + tb * plane + 2 * k);
+    }
+  }
+  const int b = f >= 0 ? prob(sl) : 0;
+  cols_column_split<true>(BatchTile<float2>{p, b, sl, f >= 0 ? f : 0}, kx, g, f >= 0, smem,
+                          f == f0 ? Gs : nullptr);
 }
 
 template <int EPI>
@@ -197,6 +223,7 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int 
   p.active = a.active;
   p.plist = a.plist;
   p.s0 = s0;
+  p.nb = nb;
   p.in_scale = a.in_scale;
   p.m_scale = a.m_scale;
   p.out_scale = a.out_scale;
@@ -257,9 +284,9 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int 
   if constexpr (sizeof(C) == sizeof(float2)) {
     if (kc == kSplitPair) {
       OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
-      const dim3 grid((a.lx + kSplitRows - 1) / kSplitRows, nb);
-      cudaError_t e = allow_smem(k_cols_split, split_cols_smem());
-      if (e == cudaSuccess) k_cols_split<<<grid, kTileThreads, split_cols_smem(), s>>>(q);
+      const dim3 grid(a.lx, (nb + 3) / 4);
+      cudaError_t e = allow_smem(k_cols_split, split_cols_staged_smem());
+      if (e == cudaSuccess) k_cols_split<<<grid, kTileThreads, split_cols_staged_smem(), s>>>(q);
       rc = e != cudaSuccess ? cuda_fail("k_cols_split smem", e) : check_launch("k_cols_split");
     } else if (kc == kSplitTriple) {
       OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);

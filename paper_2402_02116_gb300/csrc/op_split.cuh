@@ -34,10 +34,12 @@ constexpr int kSplitKP = kSplitL + 4;
 
 // Shared memory (bytes) of the split stages: the lines of one parity (two per row or column) and,
 // for the row stages, the transposition tile of one component.
-inline size_t split_lines_smem() { return size_t(2) * kSplitRows * kSplitLP * sizeof(float2); }
-inline size_t split_tile_smem() { return size_t(kSplitRows) * kSplitKP * sizeof(float2); }
-inline size_t split_rows_smem() { return std::max(split_lines_smem(), split_tile_smem()); }
-inline size_t split_cols_smem() { return split_lines_smem(); }
+__host__ __device__ constexpr size_t split_lines_smem() { return size_t(2) * kSplitRows * kSplitLP * sizeof(float2); }
+__host__ __device__ constexpr size_t split_tile_smem() { return size_t(kSplitRows) * kSplitKP * sizeof(float2); }
+__host__ __device__ constexpr size_t split_rows_smem() {
+  return split_lines_smem() > split_tile_smem() ? split_lines_smem() : split_tile_smem();
+}
+__host__ __device__ constexpr size_t split_cols_smem() { return split_lines_smem(); }
 
 // Contrast source of the stencil kernel: one thread per column (nx <= M = 512 columns, the zero
 // columns x = -1 and x = nx on either side), a chunk of kSrcRows rows per CTA walked downwards.
@@ -171,40 +173,68 @@ __device__ __forceinline__ void split_fft(float2 (&v)[2][2][8], float2 *const (&
   for (int q = 0; q < 2; ++q) RegPlan<kSplitM, 0>::template run<float2, 2, INV>(v[q], lines, t, tr, sync);
 }
 
-// For CC = 4 columns kx: the forward transform along z (even and odd kz), the 2x2 multiply by
-// Ghat(kz, kx), the inverse transform; the nz outputs written back in place.
-template <typename A>
-__device__ __forceinline__ void cols_tile_split(const A &a, int tile, float2 *smem) {
+// Asynchronous 16-byte global-to-shared copy (L2 only) and the wait for all of a thread's copies.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Shared memory of the column stage with the column's Green's tables staged: the lines, then
+// Ghat(:, kx) of the three tables [3][L].
+__host__ __device__ constexpr size_t split_cols_staged_smem() {
+  return split_lines_smem() + size_t(3) * kSplitL * sizeof(float2);
+}
+
+// Column kx of one problem, by the 64 threads of group g of the CTA (named barrier 1 + g): the
+// forward transform along z (even and odd kz), the 2 x 2 multiply by Ghat(kz, kx), the inverse
+// transform; the nz outputs written back in place. Ghat comes from Gs (the column's three tables
+// staged in shared memory, [3][L]) or, when Gs is null, from global memory. STAGED: the CTA stages
+// the tables with asynchronous copies; every thread of the CTA (live or not) waits for them at the
+// barrier between the transforms. `live` is uniform over the group.
+template <bool STAGED, typename A>
+__device__ __forceinline__ void cols_column_split(const A &a, int kx, int g, bool live, float2 *smem,
+                                                  const float4 *Gs) {
   using C = float2;
   constexpr int T = kSplitT, CC = kSplitRows, LP = kSplitLP;
-  const int col = threadIdx.x / T, t = threadIdx.x - col * T;
-  const int kx = tile * CC + col;
+  const int t = threadIdx.x - g * T;
   const int nz = a.nz(), lx = a.lx();
-  const bool live = kx < lx;
   const C *tw = a.tw();
   C *c0 = a.T() + size_t(kx) * nz, *c1 = a.T() + (size_t(lx) + kx) * nz;
   const TwReg<C, kSplitM, 0> tr(t, tw);
+  C *const lines[2] = {smem + size_t(g) * LP, smem + size_t(CC + g) * LP};
   C v[2][2][8];
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int z = t + m * T;
-    const bool in = live && z < nz;
-    const C x0 = in ? c0[z] : czero<C>(), x1 = in ? c1[z] : czero<C>();
-    const C w = __ldg(tw + kTw1024 + z);  // W_L^z
-    v[0][0][m] = x0;
-    v[0][1][m] = x1;
-    v[1][0][m] = hmul(x0, w);
-    v[1][1][m] = hmul(x1, w);
-  }
-  C *const lines[2] = {smem + size_t(col) * LP, smem + size_t(CC + col) * LP};
-  split_fft<false>(v, lines, t, tr, RowSync<T>{1 + col});
   if (live) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int z = t + m * T;
+      const bool in = z < nz;
+      const C x0 = in ? c0[z] : czero<C>(), x1 = in ? c1[z] : czero<C>();
+      const C w = __ldg(tw + kTw1024 + z);  // W_L^z
+      v[0][0][m] = x0;
+      v[0][1][m] = x1;
+      v[1][0][m] = hmul(x0, w);
+      v[1][1][m] = hmul(x1, w);
+    }
+    split_fft<false>(v, lines, t, tr, RowSync<T>{1 + g});
+  }
+  if constexpr (STAGED) {
+    cp_async_wait_all();
+    __syncthreads();  // every thread's table copies have landed
+  }
+  if (!live) return;
+  {
     const size_t plane = size_t(lx) * kSplitL;
     const float4 *G = reinterpret_cast<const float4 *>(a.G() + size_t(kx) * kSplitL);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int k = t + m * T;  // kz = 2k (even) and 2k + 1 (odd): one 16-byte load per table
-      const float4 g11 = __ldg(G + k), g13 = __ldg(G + plane / 2 + k), g33 = __ldg(G + plane + k);
+      float4 g11, g13, g33;
+      if (Gs) {
+        g11 = Gs[k]; g13 = Gs[kSplitL / 2 + k]; g33 = Gs[kSplitL + k];
+      } else {
+        g11 = __ldg(G + k); g13 = __ldg(G + plane / 2 + k); g33 = __ldg(G + plane + k);
+      }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const C a11 = q ? make_float2(g11.z, g11.w) : make_float2(g11.x, g11.y);
@@ -216,18 +246,23 @@ __device__ __forceinline__ void cols_tile_split(const A &a, int tile, float2 *sm
       }
     }
   }
-  split_fft<true>(v, lines, t, tr, RowSync<T>{1 + col});
-  if (live) {
+  split_fft<true>(v, lines, t, tr, RowSync<T>{1 + g});
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int z = t + m * T;
-      if (z < nz) {
-        const C w = cconj(__ldg(tw + kTw1024 + z));  // W_L^{-z}
-        c0[z] = cadd(v[0][0][m], cmul(w, v[1][0][m]));
-        c1[z] = cadd(v[0][1][m], cmul(w, v[1][1][m]));
-      }
+  for (int m = 0; m < 8; ++m) {
+    const int z = t + m * T;
+    if (z < nz) {
+      const C w = cconj(__ldg(tw + kTw1024 + z));  // W_L^{-z}
+      c0[z] = cadd(v[0][0][m], cmul(w, v[1][0][m]));
+      c1[z] = cadd(v[0][1][m], cmul(w, v[1][1][m]));
     }
   }
+}
+
+// For CC = 4 columns kx = 4 tile .. 4 tile + 3 of one problem (the uneven-batch tiles).
+template <typename A>
+__device__ __forceinline__ void cols_tile_split(const A &a, int tile, float2 *smem) {
+  const int g = threadIdx.x / kSplitT, kx = tile * kSplitRows + g;
+  cols_column_split<false>(a, kx, g, kx < a.lx(), smem, nullptr);
 }
 
 // Four rows z0 .. z0 + 3: the source rows (from the stencil kernel, or the raw input times its
