@@ -373,7 +373,7 @@ def fp32_peak_probe(dev, sms, iters=1 << 16, reps=10):
 # [nf][3][lx][lz] are read once per launch; the rest grows with the problems a launch processes.
 COLS_DRAM = {
     # one k_cols_split launch over 6 sources x 6 frequencies (profiles/operator_kernels_vti512_6src_6f.md)
-    (512, 512, 1024, 1024): (36, 6, 459_338_496 + 259_350_272),
+    (512, 512, 1024, 1024): (36, 6, 475_259_648 + 252_412_672),
 }
 
 
