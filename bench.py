@@ -314,6 +314,8 @@ def run_ours(args):
         "device": {"name": props.name, "sms": sms},
     }
     solo = rank == 0 and world == 1
+    if solo:
+        result["operator_hbm"] = operator_stages(P, w, dev)
     if solo and not args.no_cufft:
         result["cufft_c64"] = cufft_comparator(P, w, dev)
     if solo and not args.no_plain:
@@ -494,6 +496,61 @@ def plain_c128_sample(w, dev, cells, value_c64):
             "ms_per_problem_gradient": tot_ms / len(sample),
             "est_ms_per_step": tot_ms / len(sample) * w.n_problems,
             "speedup_c64_batched": value_c64 / rate}
+
+
+def operator_stage_bytes(w, precision_c64=True):
+    """Algorithmic bytes per cell-apply of each stage of one ls_apply pass (complex64: 8-byte
+    points; r = lx / nx, the spectra per domain cell): rows forward (with the contrast-source kernel
+    where the row stage is split: u in, the source field out and back in), the spectra T written;
+    cols: T read and written, the Green's spectra [3][lz][lx] once per frequency shared by its
+    sources; rows inverse: T read, the identity term u read, the output written. The model (shared
+    by the whole batch) is not counted."""
+    r = w.lx / w.nx
+    split = precision_c64 and w.lx in (768, 1024)
+    g = 3 * w.lz * w.lx * 8 * w.nf / (w.n_problems * w.nz * w.nx)
+    return {"rows_forward": (16 + 16 + 16 if split else 16) + 16 * r,
+            "cols": 32 * r + g,
+            "rows_inverse": 16 * r + 16 + 16}
+
+
+def operator_stages(P, w, dev, passes=5):
+    """Each stage of ls_apply over the whole batch timed by the library's stage events (CUDA events
+    on the launching stream around every launch of the stage), `passes` passes per stage after a
+    warm-up, and the pass as a whole; achieved bandwidth on the stage's algorithmic bytes against
+    the measured copy bandwidth."""
+    import torch
+    from paper_2402_02116_gb300 import dbi
+    u = P.incident()
+    out = torch.empty_like(u)
+    work, _ = dbi._work(P.grid, P.B, P.precision, dbi.OP_APPLY, u.device)
+
+    def f():
+        dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u, out=out, work=work)
+    for _ in range(3):
+        f()
+    torch.cuda.synchronize()
+    peak = load_peaks().get("hbm_gbs", 6800.0)
+    cells = w.nz * w.nx
+    bpc = operator_stage_bytes(w)
+    stages = {}
+    for stage, name in ((dbi.PROF_ROWS_FORWARD, "rows_forward"), (dbi.PROF_COLS, "cols"),
+                        (dbi.PROF_ROWS_INVERSE, "rows_inverse"), (dbi.PROF_OPERATOR, "pass")):
+        dbi.profile_begin(stage)
+        for _ in range(passes):
+            f()
+        ms, n = dbi.profile_end()
+        us = ms / n / P.B * 1e3  # per problem
+        b = sum(bpc.values()) if name == "pass" else bpc[name]
+        gbs = b * cells / (us * 1e-6) / 1e9
+        stages[name] = {"us_per_problem": us, "bytes_per_cell_apply": b, "achieved_gbs": gbs,
+                        "hbm_frac": gbs / peak}
+    del work, out, u
+    torch.cuda.empty_cache()
+    return {"stages": stages, "hbm_peak_gbs": peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
+            "passes_per_stage": passes, "grid": [w.nz, w.nx, w.lz, w.lx], "problems": P.B,
+            "bytes": "algorithmic bytes per cell-apply: rows forward u 16 (+ the source field 16 out and 16 "
+                     "in where the row stage is split) + spectra 16 lx/nx out; cols spectra 2 x 16 lx/nx + "
+                     "Green's spectra once per frequency; rows inverse spectra 16 lx/nx + u 16 + out 16"}
 
 
 def cufft_comparator(P, w, dev, reps=5):

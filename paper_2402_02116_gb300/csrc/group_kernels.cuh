@@ -253,11 +253,11 @@ template <typename C> int group_split_occupancy_impl(int per_sm[7]) {
   per_sm[1] = std::min(x, y);
   occ(kg_cols_split<C>, kTileThreads, split_cols_smem(), &per_sm[2]);
   per_sm[3] = 1 << 20;
-  occ(kg_rows_inverse_split<C, 0>, kTileThreads, split_rows_smem(), &x);
+  occ(kg_rows_inverse_split<C, 0>, kTileThreads, split_rows_inverse_smem(), &x);
   per_sm[3] = std::min(per_sm[3], x);
-  occ(kg_rows_inverse_split<C, 1>, kTileThreads, split_rows_smem(), &x);
+  occ(kg_rows_inverse_split<C, 1>, kTileThreads, split_rows_inverse_smem(), &x);
   per_sm[3] = std::min(per_sm[3], x);
-  occ(kg_rows_inverse_split<C, 2>, kTileThreads, split_rows_smem(), &x);
+  occ(kg_rows_inverse_split<C, 2>, kTileThreads, split_rows_inverse_smem(), &x);
   per_sm[3] = std::min(per_sm[3], x);
   occ(kg_rows_forward_s3<C, true>, kS3Threads, s3_smem(), &x);
   occ(kg_rows_forward_s3<C, false>, kS3Threads, s3_smem(), &y);
@@ -355,15 +355,15 @@ template <typename C> int run_group_typed(const OpArgs &a, cudaStream_t s) {
     if (gl.split_rows) {
       if (a.epi == 1)
         rc = launch_split(kg_rows_inverse_split<C, 1>, kStageRowsInverse, gl.split_blocks[3], kTileThreads,
-                          split_rows_smem(),
+                          split_rows_inverse_smem(),
                           "kg_rows_inverse_split");
       else if (a.epi == 2)
         rc = launch_split(kg_rows_inverse_split<C, 2>, kStageRowsInverse, gl.split_blocks[3], kTileThreads,
-                          split_rows_smem(),
+                          split_rows_inverse_smem(),
                           "kg_rows_inverse_split");
       else
         rc = launch_split(kg_rows_inverse_split<C, 0>, kStageRowsInverse, gl.split_blocks[3], kTileThreads,
-                          split_rows_smem(),
+                          split_rows_inverse_smem(),
                           "kg_rows_inverse_split");
       if (rc) return rc;
     }

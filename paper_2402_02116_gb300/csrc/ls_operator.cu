@@ -314,8 +314,8 @@ template <typename C> static int run_chunk(const OpArgs &a, int s0, int nb, int 
       OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);
       const dim3 grid((a.nz + kSplitRows - 1) / kSplitRows, nb);
       auto kern = a.epi == 1 ? k_rows_inverse_split<1> : a.epi == 2 ? k_rows_inverse_split<2> : k_rows_inverse_split<0>;
-      cudaError_t e = allow_smem(kern, split_rows_smem());
-      if (e == cudaSuccess) kern<<<grid, kTileThreads, split_rows_smem(), s>>>(q);
+      cudaError_t e = allow_smem(kern, split_rows_inverse_smem());
+      if (e == cudaSuccess) kern<<<grid, kTileThreads, split_rows_inverse_smem(), s>>>(q);
       rc = e != cudaSuccess ? cuda_fail("k_rows_inverse_split smem", e) : check_launch("k_rows_inverse_split");
     } else if (kr == kSplitTriple) {
       OpP<float2> &q = reinterpret_cast<OpP<float2> &>(p);

@@ -40,6 +40,10 @@ __host__ __device__ constexpr size_t split_rows_smem() {
   return split_lines_smem() > split_tile_smem() ? split_lines_smem() : split_tile_smem();
 }
 __host__ __device__ constexpr size_t split_cols_smem() { return split_lines_smem(); }
+// The inverse row stage stages the tiles of both components at once: [2][rows][KP].
+__host__ __device__ constexpr size_t split_rows_inverse_smem() {
+  return split_lines_smem() > 2 * split_tile_smem() ? split_lines_smem() : 2 * split_tile_smem();
+}
 
 // Contrast source of the stencil kernel: one thread per column (nx <= M = 512 columns, the zero
 // columns x = -1 and x = nx on either side), a chunk of kSrcRows rows per CTA walked downwards.
@@ -179,6 +183,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Asynchronous 8-byte copy; zero fill of the destination when `valid` is false (nothing is read).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
 
 // Shared memory of the column stage with the column's Green's tables staged: the lines, then
 // Ghat(:, kx) of the three tables [3][L].
@@ -326,24 +335,25 @@ __device__ __forceinline__ void rows_inverse_tile_split(const A &a, int tile, fl
   const C *tw = a.tw();
   const TwReg<C, kSplitM, 0> tr(t, tw);
   C v[2][2][8];
-  constexpr int NLD = kSplitL * ROWS / kTileThreads;  // 16 loads per thread and component
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const C *Tc = a.T() + size_t(c) * a.lx() * nz;
-    C ld[NLD];
-#pragma unroll
-    for (int i = 0; i < NLD; ++i) {  // all loads in flight before the shared-memory stores
-      const int idx = threadIdx.x + i * kTileThreads, r = idx % ROWS, kx = idx / ROWS;
-      ld[i] = z0 + r < nz ? Tc[size_t(kx) * nz + z0 + r] : czero<C>();
-    }
-    if (c) __syncthreads();  // the previous component's tile has been read
+  // the spectra of both components into tile[c][r][kx] by asynchronous copies (zeros for rows
+  // beyond nz), all in flight at once and without register staging
+  constexpr int NLD = 2 * kSplitL * ROWS / kTileThreads;  // 32 copies per thread
+  {
+    const int r = threadIdx.x % ROWS;  // the same row for all of a thread's copies
+    const bool in = z0 + r < nz;
+    const C *T0 = a.T() + (in ? z0 + r : 0);
+    const size_t cplane = size_t(a.lx()) * nz;
 #pragma unroll
     for (int i = 0; i < NLD; ++i) {
-      const int idx = threadIdx.x + i * kTileThreads, r = idx % ROWS, kx = idx / ROWS;
-      smem[size_t(r) * KP + kx] = ld[i];
+      const int idx = threadIdx.x + i * kTileThreads, kx = (idx / ROWS) % kSplitL, c = idx / (ROWS * kSplitL);
+      cp_async8(smem + size_t(c * ROWS + r) * KP + kx, T0 + c * cplane + size_t(kx) * nz, in);
     }
-    __syncthreads();
-    const float4 *row = reinterpret_cast<const float4 *>(smem + size_t(rr) * KP);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const float4 *row = reinterpret_cast<const float4 *>(smem + size_t(c * ROWS + rr) * KP);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const float4 eo = row[t + m * T];  // kx = 2k and 2k + 1

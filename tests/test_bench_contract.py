@@ -137,3 +137,12 @@ def test_cpp_oracle_legs_on_a_small_workload():
     assert [r["b"] for r in res] == [0, w.n_problems - 1] and g.shape == (5, w.nz, w.nx)
     assert all(np.allclose(r["d"] - r["r"], d_obs[r["b"]], rtol=0, atol=1e-16) for r in res)
     assert base["cores"] == 1 and base["value"] > 0 and base["kind"] == "oracle" and "C++17" in base["sample"]
+
+
+def test_operator_stage_bytes():
+    """Algorithmic bytes per cell-apply of the ls_apply stages: 512^2 on L = 1024 (split rows: the
+    source field out and back in), 256^2 on L = 512."""
+    b = bench.operator_stage_bytes(bench.workload("vti512"))
+    assert b == {"rows_forward": 80.0, "cols": 64.0 + 96 * 6 / 384, "rows_inverse": 64.0}
+    b = bench.operator_stage_bytes(bench.workload("vti256"))
+    assert b == {"rows_forward": 48.0, "cols": 64.0 + 96 * 8 / 256, "rows_inverse": 64.0}
