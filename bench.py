@@ -67,12 +67,14 @@ def parse_args():
     ap.add_argument("--check-every", type=int, default=4,
                     help="BiCGSTAB iterations between host convergence checks (each check also "
                          "compacts the launches to the problems still active)")
-    ap.add_argument("--workload", choices=["vti512", "vti256", "uneven40", "formk256", "gmres256", "hess3d"],
+    ap.add_argument("--workload", choices=["vti512", "vti256", "uneven40", "op384", "formk256", "gmres256", "hess3d"],
                     default="vti512",
                     help="vti512: the gradient step on 512^2 cells, 64 sources x 6 frequencies (default); "
                          "vti256: the gradient step on 256^2 cells, 32 sources x 8 frequencies; uneven40: "
                          "operator passes over the 40-problem uneven batch (persistent launches, autotuned), "
-                         "plus one graph-captured solve; formk256: operator passes over the 256^2 "
+                         "plus one graph-captured solve; op384: operator passes over one 384^2 member of "
+                         "the uneven recipe (96 problems) on FFT length 768 beside 1024; formk256: operator "
+                         "passes over the 256^2 "
                          "batch in the paper-literal form (derivatives on G, Eq. 9) beside the "
                          "divergence form; gmres256: batched forward solves of the 256^2 batch by "
                          "restarted GMRES beside BiCGSTAB; hess3d: 3D operator passes and GMRES "
@@ -368,6 +370,16 @@ def fp32_peak_probe(dev, sms, iters=1 << 16, reps=10):
         best = t if best is None else min(best, t)
     return {"tflops": flops / (best * 1e-3) / 1e12, "ms": best, "blocks": blocks, "flops": flops,
             "how": f"dbi_fma_probe: {blocks} CTAs x 256 threads x 8 FMA chains x {iters} steps, best of {reps}"}
+
+
+def measured_alu_peak(dev, clocks):
+    """The FP32 peak of the secondary workloads' ALU rooflines: the FMA probe (as for the default
+    line), with the nominal figure from the device's SM count and the sampled clock beside it."""
+    import torch
+    sms = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    fp32 = fp32_peak_probe(dev, sms)
+    sm_mhz = clocks["sm_mhz"] or load_peaks().get("sm_max_mhz", 2070.0)
+    return fp32["tflops"], "measured: " + fp32["how"], sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # DRAM bytes of one k_cols launch from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum):
@@ -985,6 +997,67 @@ def run_uneven(args):
         dist.destroy_process_group()
 
 
+def run_op384(args):
+    """Operator passes over one 384^2 member of the uneven recipe (seed 7, its first 16 sources x 6
+    frequencies: 96 problems) on FFT length 768, where every half-pruned transform runs as three
+    256-point transforms; one step = one ls_apply pass over the 96 problems. The same batch on
+    length 1024 (pairs of 512-point transforms) is timed beside it, and every stage of both by the
+    library's stage events."""
+    import dataclasses
+    import torch
+    from paper_2402_02116_gb300 import build, dbi
+    from paper_2402_02116_gb300.problem import DeviceProblem
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    build.build()
+    dbi.load()
+    runs = {}
+    for radix3 in (True, False):
+        w = inputs.config5_uneven(sizes=(384,), n_members=1, max_src=32, max_f=8, seed=7, radix3=radix3)[0]
+        w = dataclasses.replace(w, src_cells=w.src_cells[:16], src_force=w.src_force[:16],
+                                name=f"{w.name.split('_')[0]}_16src_{w.nf}f_L{w.lz}")
+        P = DeviceProblem(w, dbi.C64, device=dev)
+        u = P.incident()
+        out = torch.empty_like(u)
+        work, _ = dbi._work(P.grid, P.B, dbi.C64, dbi.OP_APPLY, u.device)
+
+        def f():
+            dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u, out=out, work=work)
+        for _ in range(args.warmup):
+            f()
+        stream = torch.cuda.current_stream(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = dbi.kernel_launches()
+        with ClockSampler(gpu_id(dev)) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                f()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        runs[w.lz] = {"w": w, "ms": ms, "launches": dbi.kernel_launches() - n0, "clocks": clk.summary(),
+                      "stages": operator_stages(P, w, dev), "cells": P.B * w.nz * w.nx}
+        del P, u, out, work
+        torch.cuda.empty_cache()
+    r, r2 = runs[768], runs[1024]
+    w = r["w"]
+    result = {
+        "metric": METRIC, "value": r["cells"] * args.steps / (r["ms"] * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex operator)",
+        "data": "synthetic (seeded model of the uneven recipe: background with Gaussian anomalies)",
+        "config": {"workload": f"op384: {w.name}, one ls_apply pass over the {w.n_problems} problems",
+                   "nz": w.nz, "nx": w.nx, "lz": w.lz, "lx": w.lx,
+                   "l2": f"spectra larger than L2: {w.n_problems * 2 * w.lx * w.nz * 8 / 1e9:.2f} GB per pass"},
+        "operator_hbm": r["stages"], "gpu_launches": int(r["launches"]),
+        "gpu_launches_per_step": r["launches"] / args.steps, "clocks": r["clocks"],
+        "length_1024": {"value": r2["cells"] * args.steps / (r2["ms"] * 1e-3), "unit": UNIT,
+                        "ms_per_step": r2["ms"] / args.steps, "operator_hbm": r2["stages"], "clocks": r2["clocks"]},
+    }
+    print(json.dumps(result), flush=True)
+
+
 def formk_cols_bytes_per_cell_apply(w):
     """Compulsory bytes of kk_cols: the five row-transformed sources [5][nz][lx] read and the two
     outputs [2][nz][lx] written (complex64), plus Ghat [3][lz][lx] and the derivative tables
@@ -1047,8 +1120,7 @@ def run_formk(args):
     diff = float(torch.linalg.norm(a_k - out_s) / torch.linalg.norm(out_s - u))
     value = cells * args.steps / (ms_k * 1e-3)
     peaks = load_peaks()
-    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6
+    peak_tf, peak_src, nominal_tf = measured_alu_peak(dev, clocks)
     cols_s = cols_ms * 1e-3
     flops = formk_cols_flops_per_cell_apply(w) * cells * args.steps
     algo_bytes = formk_cols_bytes_per_cell_apply(w) * cells * args.steps
@@ -1059,8 +1131,8 @@ def run_formk(args):
     if (w.nz, w.nx, w.lz, w.lx, w.nf) == (256, 256, 512, 512, 8):
         tables = 9 * w.lz * w.lx * 8 * w.nf
         traffic = tables + (373.98e6 - tables) / 32 * cells * args.steps / (w.nz * w.nx) / max(cols_launches, 1)
-    roof = {"bound": "alu", "achieved": flops / cols_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured median)",
+    roof = {"bound": "alu", "achieved": flops / cols_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+            "peak_source": peak_src, "peak_nominal": nominal_tf,
             "traffic": traffic, "kernel": "kk_cols (five forward column FFTs, 2 x 5 kernel, two inverse)",
             "hbm_frac_of_algorithmic_bytes": algo_bytes / cols_s / (peaks.get("hbm_gbs", 6800.0) * 1e9),
             "launches_timed": cols_launches, "avg_launch_ms": cols_ms / max(cols_launches, 1),
@@ -1200,16 +1272,15 @@ def run_hess3d(args):
     solve_s = time.time() - t0
     clocks = clk.summary()
     peaks = load_peaks()
-    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6
+    peak_tf, peak_src, nominal_tf = measured_alu_peak(dev, clocks)
     # the z pass: per (ky, kx) column of every wavefield three forward and three inverse FFTs of
     # length lz (5 L log2 L flops each) and the symmetric 3 x 3 complex product (66 flops) per kz
     cols = P.B * w.ly * w.lx
     z_flops = cols * (6 * 5 * w.lz * math.log2(w.lz) + 66 * w.lz) * args.steps
     z_bytes = (P.B * 2 * 3 * w.nz * w.ly * w.lx * 8 + w.nf * 6 * w.lz * w.ly * w.lx * 8) * args.steps
     z_s = z_ms * 1e-3
-    roof = {"bound": "alu", "achieved": z_flops / z_s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (measured median)", "traffic": None,
+    roof = {"bound": "alu", "achieved": z_flops / z_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+            "peak_source": peak_src, "peak_nominal": nominal_tf, "traffic": None,
             "kernel": ("k3_fft_z_reg (register z-line FFTs of the three components, 3 x 3 kernel, inverse)"
                        if w.lz <= 256 else
                        "k3_fft_z_mul (z-line FFTs of the three components, 3 x 3 kernel, inverse)"),
@@ -1241,6 +1312,8 @@ def main():
         run_reference(args)
     elif args.workload == "uneven40":
         run_uneven(args)
+    elif args.workload == "op384":
+        run_op384(args)
     elif args.workload == "formk256":
         run_formk(args)
     elif args.workload == "gmres256":
