@@ -7,14 +7,15 @@
 // of Eq. A-1 as printed). Kernels per operator pass:
 //   k3_stress       sigma = dC : eps(u)  (6 Voigt components)              -> T2
 //   k3_source       w^2 drho u + div sigma                                 -> T rows (x < nx)
-//   k3_fft_x        forward FFT along x of every row, zero-padded to lx    (in place in T)
+//   k3_fft_x        forward FFT along x of every row, zero-padded to lx    (in place in T; register
+//                   FFTs in k3_fft_x_reg for complex64 and lx <= 512)
 //   k3_fft_y        forward FFT along y (rows y >= ny read as zero)        (in place; register
 //                   FFTs in k3_fft_y_reg for complex64 and ly <= 256)
 //   k3_fft_z_reg    per (ky, kx) column: forward FFT along z of the three components, the
 //                   symmetric 3 x 3 Ghat product, inverse FFT along z      (in place, z < nz kept)
 //                   with register FFTs (complex64, lz <= 256; k3_fft_z_mul otherwise)
 //   k3_fft_y        inverse, y < ny kept
-//   k3_fft_x_epi    inverse FFT along x, x < nx kept, out = ident - result
+//   k3_fft_x_epi    inverse FFT along x, x < nx kept, out = ident - result (k3_fft_x_reg likewise)
 // Without the stencil (plain convolution of the input, for the adjoint source) k3_copy_source
 // replaces the first two kernels. The FFTs are the shared-memory Stockham transforms of fft.cuh. Ghat [nf][6][lz][ly][lx]
 // (components 11, 12, 13, 22, 23, 33) carries h^3 / (lz ly lx).
@@ -160,6 +161,71 @@ __global__ void __launch_bounds__(256) k3_fft_x(int nb, int nz, int ny, int nx, 
     bool live;
     C *p = row_ptr(r0 + l, live);
     if (live) p[k] = s[l * LS + k];
+  }
+}
+
+// The x passes with register-resident FFTs (complex64, LX <= 512): a row's T = LX / 8 threads hold
+// its points x = t + m T, so the row is read and written in place with coalesced accesses and no
+// staging; ROWS = 256 / T rows per CTA, each exchanging through its own shared-memory line. Every
+// row of the CTA runs the transform (rows past the batch or of inactive slots on zeros, without
+// loads or stores), so the warp-level barriers of rows sharing a warp always meet. EPI = false: the
+// forward transform of the nx source points of each row (the second half of the line is zero);
+// EPI = true: the inverse transform of the lx spectra, out = ident - osc y for x < nx.
+template <int LX> struct XRegCfg {
+  static constexpr int T = LX / 8, ROWS = kTileThreads / T;
+  static constexpr int LP = RegFFT<float2, LX>::LP;
+  static constexpr size_t smem = size_t(ROWS) * LP * sizeof(float2);
+};
+template <int LX, bool EPI>
+__global__ void __launch_bounds__(kTileThreads) k3_fft_x_reg(int nb, int nz, int ny, int nx, int ly, const int *plist,
+                                                             const int *active, const float2 *tw, float2 *T,
+                                                             const float2 *ident, const double *out_scale,
+                                                             float2 *out) {
+  using C = float2;
+  using X = XRegCfg<LX>;
+  constexpr int TX = X::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *s = reinterpret_cast<C *>(smem_raw);
+  const int rr = threadIdx.x / TX, t = threadIdx.x - rr * TX;
+  const long per = long(3) * nz * ny, rows = long(nb) * per;
+  const long r = long(blockIdx.x) * X::ROWS + rr;
+  const int slot = int(r < rows ? r / per : 0);
+  const long rem = r - long(slot) * per;
+  const int cz = int(rem / ny), y = int(rem - long(cz) * ny);  // cz = c nz + z
+  const int b = r < rows ? slot_problem(plist, active, slot) : -1;
+  const bool live = b >= 0;
+  C *row = T + ((size_t(slot) * 3 * nz + cz) * ly + y) * LX;
+  const TwReg<C, LX> tr(t, tw);
+  C *const line[1] = {s + size_t(rr) * X::LP};
+  C v[1][8];
+  if constexpr (!EPI) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int x = t + m * TX;
+      v[0][m] = (live && m < kHalf && x < nx) ? row[x] : czero<C>();
+    }
+    RegPlan<LX>::template run<C, 1, false, true>(v, line, t, tr, RowSync<TX>{1 + rr});
+    if (live) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) row[t + m * TX] = v[0][m];
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[0][m] = live ? row[t + m * TX] : czero<C>();
+    RegPlan<LX>::template run<C, 1, true>(v, line, t, tr, RowSync<TX>{1 + rr});
+    if (live) {
+      const size_t cells = size_t(nz) * ny * nx;
+      const float osc = out_scale ? float(out_scale[b]) : 1.0f;
+      const size_t o0 = size_t(b) * 3 * cells + (size_t(cz) * ny + y) * nx;
+#pragma unroll
+      for (int m = 0; m < kHalf; ++m) {
+        const int x = t + m * TX;
+        if (x < nx) {
+          const C w = cscale(v[0][m], osc);
+          out[o0 + x] = ident ? csub(ident[o0 + x], w) : w;
+        }
+      }
+    }
   }
 }
 
@@ -440,7 +506,27 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
     if ((rc = check_launch("k3_copy_source"))) return rc;
   }
   rc = DBI_ERR_UNSUPPORTED;
-  dispatch_len(a.lx, [&]<int LX>() {
+  // the x passes: register FFTs for complex64 and lx <= 512, the shared-memory form otherwise
+  auto fft_x_reg = [&](auto epi_tag) {
+    constexpr bool EPI = decltype(epi_tag)::value;
+    bool done = false;
+    dispatch_len(a.lx, [&]<int LX>() {
+      if constexpr (sizeof(C) == 8 && LX <= 512) {
+        using X = XRegCfg<LX>;
+        const long rows = long(nb) * 3 * a.nz * a.ny;
+        cudaError_t e = allow_smem(k3_fft_x_reg<LX, EPI>, X::smem);
+        if (e == cudaSuccess)
+          k3_fft_x_reg<LX, EPI><<<unsigned((rows + X::ROWS - 1) / X::ROWS), kTileThreads, X::smem, s>>>(
+              nb, a.nz, a.ny, a.nx, a.ly, a.plist, a.active, reinterpret_cast<const float2 *>(tw),
+              reinterpret_cast<float2 *>(T), static_cast<const float2 *>(a.ident), a.out_scale,
+              static_cast<float2 *>(a.out));
+        rc = e != cudaSuccess ? cuda_fail("k3_fft_x_reg smem", e) : check_launch("k3_fft_x_reg");
+        done = true;
+      }
+    });
+    return done;
+  };
+  if (!fft_x_reg(std::false_type{})) dispatch_len(a.lx, [&]<int LX>() {
     constexpr int NL = 2048 / LX, NT = NL * LX / 8;
     const size_t bytes = size_t(NL) * (LX + 1) * sizeof(C);
     const long rows = long(nb) * 3 * a.nz * a.ny;
@@ -515,7 +601,7 @@ template <typename C> static int run3_typed(const OpArgs &a, cudaStream_t s) {
   if (rc) return rc;
   if ((rc = fft_y(std::true_type{}))) return rc;
   rc = DBI_ERR_UNSUPPORTED;
-  dispatch_len(a.lx, [&]<int LX>() {
+  if (!fft_x_reg(std::true_type{})) dispatch_len(a.lx, [&]<int LX>() {
     constexpr int NL = 2048 / LX, NT = NL * LX / 8;
     const size_t bytes = size_t(NL) * (LX + 1) * sizeof(C);
     const long rows = long(nb) * 3 * a.nz * a.ny;
