@@ -260,10 +260,14 @@ __global__ void __launch_bounds__(256) k3_fft_y(int nz, int ny, int lx, const in
 // 256 / T columns per CTA staged through shared memory in runs of CC consecutive columns, each
 // column's T = LY / 8 threads holding its line in registers. Forward: rows y < ny staged (the rest
 // zero), all ly written; inverse: all staged, y < ny written.
+// Line pitch of the staged y and z lines: odd (in 8-byte points), so that the staging loops, whose
+// consecutive threads walk consecutive lines at one point, hit 16 distinct bank slots per half warp
+// (with the even RegFFT pitch they hit 4 to 8).
+template <int L> constexpr int staged_pitch() { return RegFFT<float2, L>::LP | 1; }
 template <int LY> struct YRegCfg {
   using C = float2;
   static constexpr int T = LY / 8, NT = kTileThreads, CC = NT / T;
-  static constexpr int LP = RegFFT<C, LY>::LP;
+  static constexpr int LP = staged_pitch<LY>();
   static constexpr size_t smem = size_t(CC) * LP * sizeof(C);
 };
 template <int LY, bool INV>
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(ZCfg<C, LZ>::NT, ZCfg<C, LZ>::MIN_BLOCKS) k3_f
 template <int LZ> struct ZRegCfg {
   using C = float2;
   static constexpr int T = LZ / 8, NT = kTileThreads, CC = NT / T;
-  static constexpr int LP = RegFFT<C, LZ>::LP;
+  static constexpr int LP = staged_pitch<LZ>();
   static constexpr size_t smem = size_t(3) * CC * LP * sizeof(C);
 };
 template <int LZ>
