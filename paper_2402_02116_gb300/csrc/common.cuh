@@ -71,6 +71,21 @@ inline int split_kind(int L, int precision) {
 inline bool split_rows(int lx, int precision) { return split_kind(lx, precision) != 0; }
 inline bool split_cols(int lz, int precision) { return split_kind(lz, precision) != 0; }
 
+#ifdef __CUDACC__
+// Asynchronous global-to-shared copies: 16 bytes (L2 only), 8 bytes with a zero fill of the
+// destination when `valid` is false (nothing is read then), and the wait for all of a thread's
+// copies (a barrier after it makes them visible to the other threads of the CTA).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+#endif
+
 // Error reporting (per host thread).
 void set_error(const char *fmt, ...);
 void clear_error();

@@ -177,17 +177,6 @@ __device__ __forceinline__ void split_fft(float2 (&v)[2][2][8], float2 *const (&
   for (int q = 0; q < 2; ++q) RegPlan<kSplitM, 0>::template run<float2, 2, INV>(v[q], lines, t, tr, sync);
 }
 
-// Asynchronous 16-byte global-to-shared copy (L2 only) and the wait for all of a thread's copies.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-// Asynchronous 8-byte copy; zero fill of the destination when `valid` is false (nothing is read).
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
-}
 
 // Shared memory of the column stage with the column's Green's tables staged: the lines, then
 // Ghat(:, kx) of the three tables [3][L].
