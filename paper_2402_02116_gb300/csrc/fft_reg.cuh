@@ -88,12 +88,14 @@ template <int L, int V> struct PlanInfo {
 };
 
 // Line layout of exchange p (after pass p) of each plan: the cheapest layout (RegFFT::pad) whose
-// stores and loads need the minimum shared-memory wavefronts, found by counting the wavefronts of
-// every access of every layout for each plan (one line per warp from L = 256; two or more below).
+// stores and loads need the fewest shared-memory wavefronts, found by counting the wavefronts of
+// every access of every layout for each plan, with 8-byte points served half a warp at a time
+// (one line per warp from L = 256; two or more below, at the line pitch RegFFT::LP, chosen with
+// the layouts for L <= 64).
 template <int L, int V> constexpr int layout_of(int p) {
-  if constexpr (L == 16) return 0;
-  else if constexpr (L == 32) return V == 0 ? 1 : 0;
-  else if constexpr (L == 64) return 1;
+  if constexpr (L == 16) return V == 0 ? 3 : 0;
+  else if constexpr (L == 32) return 3;
+  else if constexpr (L == 64) return 3;
   else if constexpr (L == 128 || L == 256) return (p == 1 && V == 0) ? 2 : 1;
   else if constexpr (L == 512) return p == 0 ? 1 : 2;
   else return p == 0 ? 1 : (p == 1 ? (V == 0 ? 2 : 1) : 0);
@@ -123,19 +125,23 @@ template <typename C, int L, int V = 0> struct TwReg {
 
 template <typename C, int L> struct RegFFT {
   static constexpr int T = L / 8;                 // threads per line
-  static constexpr int LP = L + L / 16 + 2;       // padded line length in shared memory
+  // padded line length (and pitch of consecutive lines) in shared memory
+  static constexpr int LP = L == 16 ? 18 : L == 64 ? 72 : L + L / 16 + 2;
   static constexpr int TWS = kTwiddleN / L;       // table stride of W_L
 
   // Position of point i of a line in shared memory, by layout (chosen per exchange, see
-  // Layouts): 0 = i; 1 = i + i/16 (one padding slot per 16 points); 2 = inside each 16-point
+  // layout_of): 0 = i; 1 = i + i/16 (one padding slot per 16 points); 2 = inside each 16-point
   // block, the low four bits XORed with the block index (bits 0-2) and with bit 2 of the block
-  // index moved to bit 3 (a bijection on every block). Each exchange takes the cheapest layout
-  // under which its stores and loads need the minimum two wavefronts per warp of 8-byte points.
+  // index moved to bit 3 (a bijection on every block); 3 = i + i/8 (one padding slot per 8
+  // points: with several lines per warp at a pitch of 8 mod 16 the scatter of the first radix-8
+  // pass and the natural-order gather both spread two lines over 16 bank slots).
   template <int LAY> __host__ __device__ __forceinline__ static int pad(int i) {
     if constexpr (LAY == 0) {
       return i;
     } else if constexpr (LAY == 1) {
       return i + (i >> 4);
+    } else if constexpr (LAY == 3) {
+      return i + (i >> 3);
     } else {
       const int h = i >> 4;
       return (i & ~15) | ((i & 15) ^ ((((h >> 2) & 1) << 3) | (h & 7)));

@@ -372,17 +372,24 @@ __global__ void __launch_bounds__(ZCfg<C, LZ>::NT, ZCfg<C, LZ>::MIN_BLOCKS) k3_f
 
 // The z pass with register-resident FFTs (complex64, LZ <= 256: a column's T = LZ / 8 threads are
 // one warp or part of one). A CTA of 256 threads takes CC = 256 / T columns: the nz rows of its
-// 3 CC lines are staged through shared memory with runs of CC consecutive columns, each column's
-// T threads hold its three components' lines in registers (8 points each) and exchange through
-// the staged lines, and the result goes back the same way.
+// 3 CC lines are staged through shared memory with runs of CC consecutive columns (rows [z][line]),
+// each column's T threads read its three components' lines into registers (8 points each) and
+// exchange through lines at the transforms' own pitch and layout (aliasing the staged rows), and
+// the result goes back the same way.
 #ifndef DBI_3D_ZREG_MINB
 #define DBI_3D_ZREG_MINB 2  // CTAs per SM: 128 registers; 3 (80 registers) was 15 % slower, 4 no faster
 #endif
 template <int LZ> struct ZRegCfg {
   using C = float2;
-  static constexpr int T = LZ / 8, NT = kTileThreads, CC = NT / T;
-  static constexpr int LP = staged_pitch<LZ>();
-  static constexpr size_t smem = size_t(3) * CC * LP * sizeof(C);
+  static constexpr int T = LZ / 8, NT = kTileThreads, CC = NT / T, NL = 3 * CC;
+  static constexpr int LP = RegFFT<C, LZ>::LP;  // the lines of the transforms' exchanges
+  // The staged rows [z][NL] (z < nz <= LZ / 2) alias the lines. Row pitch PL = 16 / min(T, 16) mod
+  // 16: the staging loops (consecutive lines) and the threads' own reads and writes (a half warp
+  // holds 16 / T lines x T points, or 16 points of one line) hit 16 distinct 8-byte bank slots.
+  static constexpr int PQ = 16 / (T < 16 ? T : 16);
+  static constexpr int PL = NL + ((PQ - NL % 16) + 16) % 16;
+  static constexpr size_t lines = size_t(NL) * LP, rows = size_t(LZ / 2) * PL;
+  static constexpr size_t smem = (lines > rows ? lines : rows) * sizeof(C);
 };
 template <int LZ>
 __global__ void __launch_bounds__(kTileThreads, DBI_3D_ZREG_MINB) k3_fft_z_reg(int nb, int nz, int nf, size_t plane, const int *plist,
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(kTileThreads, DBI_3D_ZREG_MINB) k3_fft_z_reg(i
                                                                const float2 *tw, float2 *T) {
   using C = float2;
   using Z = ZRegCfg<LZ>;
-  constexpr int TZ = Z::T, CC = Z::CC, LP = Z::LP, NT = Z::NT, NL = 3 * CC;
+  constexpr int TZ = Z::T, CC = Z::CC, LP = Z::LP, NT = Z::NT, NL = Z::NL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *s = reinterpret_cast<C *>(smem_raw);
   const int slot = int(blockIdx.x % unsigned(nb));  // slot fastest, as in k3_fft_z_mul
@@ -398,9 +405,10 @@ __global__ void __launch_bounds__(kTileThreads, DBI_3D_ZREG_MINB) k3_fft_z_reg(i
   if (b < 0 || unsigned(fidx[b]) >= unsigned(nf)) return;  // uniform over the CTA
   C *Tb = T + size_t(slot) * 3 * nz * plane;
   const size_t q0 = size_t(blockIdx.x / unsigned(nb)) * CC;
-  for (int idx = threadIdx.x; idx < NL * nz; idx += NT) {
+  constexpr int PL = Z::PL;
+  for (int idx = threadIdx.x; idx < NL * nz; idx += NT) {  // rows [z][l], l = c CC + j
     const int z = idx / NL, l = idx - z * NL, c = l / CC, j = l - c * CC;
-    s[l * LP + z] = q0 + j < plane ? Tb[(size_t(c) * nz + z) * plane + q0 + j] : czero<C>();
+    s[z * PL + l] = q0 + j < plane ? Tb[(size_t(c) * nz + z) * plane + q0 + j] : czero<C>();
   }
   __syncthreads();
   const int g = threadIdx.x / TZ, t = threadIdx.x - g * TZ;
@@ -415,9 +423,9 @@ __global__ void __launch_bounds__(kTileThreads, DBI_3D_ZREG_MINB) k3_fft_z_reg(i
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int z = t + m * TZ;
-      v[c][m] = (m < kHalf && z < nz) ? lines[c][z] : czero<C>();
+      v[c][m] = (m < kHalf && z < nz) ? s[z * PL + c * CC + g] : czero<C>();
     }
-  sync();  // the transform's first exchange overwrites the staged lines
+  __syncthreads();  // every staged row has been read: the lines alias them
   RegPlan<LZ>::template run<C, 3, false, true>(v, lines, t, tr, sync);
   if (live) {
     const size_t e = size_t(LZ) * plane;
@@ -434,18 +442,18 @@ __global__ void __launch_bounds__(kTileThreads, DBI_3D_ZREG_MINB) k3_fft_z_reg(i
     }
   }
   RegPlan<LZ>::template run<C, 3, true>(v, lines, t, tr, sync);
-  // every thread of the column is past the transform's last exchange: its lines are free
+  __syncthreads();  // every line's last exchange is done: the rows alias them
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
     for (int m = 0; m < kHalf; ++m) {
       const int z = t + m * TZ;
-      if (z < nz) lines[c][z] = v[c][m];
+      if (z < nz) s[z * PL + c * CC + g] = v[c][m];
     }
   __syncthreads();
   for (int idx = threadIdx.x; idx < NL * nz; idx += NT) {
     const int z = idx / NL, l = idx - z * NL, c = l / CC, j = l - c * CC;
-    if (q0 + j < plane) Tb[(size_t(c) * nz + z) * plane + q0 + j] = s[l * LP + z];
+    if (q0 + j < plane) Tb[(size_t(c) * nz + z) * plane + q0 + j] = s[z * PL + l];
   }
 }
 
