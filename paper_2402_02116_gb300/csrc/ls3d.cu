@@ -283,10 +283,12 @@ __global__ void __launch_bounds__(kTileThreads, 4) k3_fft_y_reg(int nz, int ny, 
   C *M = T + size_t(plane) * LY * lx;
   const int c0 = blockIdx.x * CC;
   const int rows_in = INV ? LY : ny, rows_out = INV ? ny : LY;
-  for (int idx = threadIdx.x; idx < CC * rows_in; idx += NT) {
+  for (int idx = threadIdx.x; idx < CC * rows_in; idx += NT) {  // all copies in flight at once
     const int y = idx / CC, j = idx - y * CC;
-    s[j * LP + y] = c0 + j < lx ? M[size_t(y) * lx + c0 + j] : czero<C>();
+    const bool in = c0 + j < lx;
+    cp_async8(s + j * LP + y, M + (in ? size_t(y) * lx + c0 + j : 0), in);
   }
+  cp_async_wait_all();
   __syncthreads();
   const int g = threadIdx.x / TY, t = threadIdx.x - g * TY;
   C *const line[1] = {s + size_t(g) * LP};
@@ -406,10 +408,12 @@ __global__ void __launch_bounds__(kTileThreads, DBI_3D_ZREG_MINB) k3_fft_z_reg(i
   C *Tb = T + size_t(slot) * 3 * nz * plane;
   const size_t q0 = size_t(blockIdx.x / unsigned(nb)) * CC;
   constexpr int PL = Z::PL;
-  for (int idx = threadIdx.x; idx < NL * nz; idx += NT) {  // rows [z][l], l = c CC + j
+  for (int idx = threadIdx.x; idx < NL * nz; idx += NT) {  // rows [z][l], l = c CC + j (all in flight)
     const int z = idx / NL, l = idx - z * NL, c = l / CC, j = l - c * CC;
-    s[z * PL + l] = q0 + j < plane ? Tb[(size_t(c) * nz + z) * plane + q0 + j] : czero<C>();
+    const bool in = q0 + j < plane;
+    cp_async8(s + z * PL + l, Tb + (in ? (size_t(c) * nz + z) * plane + q0 + j : 0), in);
   }
+  cp_async_wait_all();
   __syncthreads();
   const int g = threadIdx.x / TZ, t = threadIdx.x - g * TZ;
   const size_t q = q0 + g;
