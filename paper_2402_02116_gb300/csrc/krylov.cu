@@ -4,9 +4,11 @@
 // Per iteration i (van der Vorst's BiCGSTAB, <a, b> = sum conj(a) b):
 //   p = r + beta (p - omega v)                  k_update_p      (beta from the previous k_check)
 //   v = A p, partials of <rhat, v>              operator (inner product in k_rows_inverse)
-//   alpha = rho / <rhat, v>, s = r - alpha v    k_update_s      (+ partials of ||s||^2)
+//   alpha = rho / <rhat, v>                     k_alpha         (one warp per problem)
+//   s = r - alpha v                             k_update_s      (+ partials of ||s||^2)
 //   t = A s, partials of <t, s>, <t, t>         operator (inner products in k_rows_inverse)
-//   omega = <t,s>/<t,t>, x += alpha p + omega s, r = s - omega t   k_update_xr (+ <rhat, r>, ||r||^2)
+//   omega = <t,s>/<t,t>                         k_omega         (one warp per problem)
+//   x += alpha p + omega s, r = s - omega t     k_update_xr     (+ partials of <rhat, r>, ||r||^2)
 //   convergence, breakdown, beta = (rho_new / rho)(alpha / omega)  k_check
 // Every scalar lives on the device in FP64. Each reduction is two-stage and deterministic: each
 // thread sums its elements, the CTA sums its threads in a fixed tree, and every consumer sums the
@@ -140,26 +142,32 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(Span sp, const int *pl
   }
 }
 
-template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_update_s(Span sp, const int *plist, KState *st,
-                                                          const int *active, int nparts, const double *partA,
-                                                          const C *__restrict__ r, const C *__restrict__ v,
-                                                          C *__restrict__ s, double *partS) {
-  using A = typename Acc<C>::type;
-  const int b = problem_at(plist, blockIdx.y);
+// alpha = rho / <rhat, A p> of every active problem, from the operator's fused partials, once
+// per problem (one warp each) so that the s update starts streaming at once.
+__global__ void k_alpha(const int *plist, KState *st, const int *active, int nparts, const double *partA) {
+  const int b = problem_at(plist, blockIdx.x);
   if (!active[b]) return;
   double sg[2];
   gather_n<2>(partA + size_t(b) * nparts * kRedSlots, nparts, sg);
-  const KState k = st[b];
-  const double2 sigma = make_double2(sg[0], sg[1]);
-  const double2 alpha = (sigma.x == 0.0 && sigma.y == 0.0)
-                            ? make_double2(0.0, 0.0)
-                            : zdiv(make_double2(k.rho_re, k.rho_im), sigma);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
+    const double2 sigma = make_double2(sg[0], sg[1]);
+    const double2 alpha = (sigma.x == 0.0 && sigma.y == 0.0)
+                              ? make_double2(0.0, 0.0)
+                              : zdiv(make_double2(st[b].rho_re, st[b].rho_im), sigma);
     st[b].alpha_re = alpha.x;
     st[b].alpha_im = alpha.y;
   }
-  const C al = from_z<C>(alpha);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_update_s(Span sp, const int *plist, const KState *st,
+                                                          const int *active, const C *__restrict__ r,
+                                                          const C *__restrict__ v, C *__restrict__ s,
+                                                          double *partS) {
+  using A = typename Acc<C>::type;
+  const int b = problem_at(plist, blockIdx.y);
+  if (!active[b]) return;
+  const C al = from_z<C>(make_double2(st[b].alpha_re, st[b].alpha_im));
   A ss = 0;
   DBI_PROBLEM_LOOP(sp) {
     const C si = csub(r[off + i], cmul(al, v[off + i]));
@@ -170,32 +178,38 @@ __global__ void __launch_bounds__(kRedThreads) k_update_s(Span sp, const int *pl
   block_sum_store<1>(acc, partS + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
 
+// omega = <t, s> / ||t||^2 (zero when the half step already met tol) of every active problem,
+// once per problem (one warp each), from the second operator pass's partials and ||s||^2.
+__global__ void k_omega(const int *plist, KState *st, const int *active, int nparts, const double *partB,
+                        const double *partS, double tol) {
+  const int b = problem_at(plist, blockIdx.x);
+  if (!active[b]) return;
+  double q[3], sn[1];
+  gather_n<3>(partB + size_t(b) * nparts * kRedSlots, nparts, q);
+  gather_n<1>(partS + size_t(b) * kRedBlocks * kRedSlots, kRedBlocks, sn);
+  if (threadIdx.x == 0) {
+    const int half = sn[0] <= tol * tol * st[b].bnorm2;
+    const double2 om = (half || q[2] == 0.0) ? make_double2(0.0, 0.0)
+                                             : make_double2(q[0] / q[2], q[1] / q[2]);
+    st[b].om_re = om.x;
+    st[b].om_im = om.y;
+    st[b].half = half;
+    st[b].snorm2 = sn[0];
+  }
+}
+
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads) k_update_xr(Span sp, const int *plist, KState *st,
-                                                           const int *active, int nparts,
-                                                           const double *partB, const double *partS,
-                                                           double tol, const C *__restrict__ p,
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(Span sp, const int *plist, const KState *st,
+                                                           const int *active, const C *__restrict__ p,
                                                            const C *__restrict__ s, const C *__restrict__ t,
                                                            const C *__restrict__ rhat, C *__restrict__ x,
                                                            C *__restrict__ r, double *partC) {
   using A = typename Acc<C>::type;
   const int b = problem_at(plist, blockIdx.y);
   if (!active[b]) return;
-  double q[3], sn[1];
-  gather_n<3>(partB + size_t(b) * nparts * kRedSlots, nparts, q);
-  gather_n<1>(partS + size_t(b) * kRedBlocks * kRedSlots, kRedBlocks, sn);
   const KState k = st[b];
-  const int half = sn[0] <= tol * tol * k.bnorm2;
-  const double2 om = (half || q[2] == 0.0) ? make_double2(0.0, 0.0)
-                                           : make_double2(q[0] / q[2], q[1] / q[2]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st[b].om_re = om.x;
-    st[b].om_im = om.y;
-    st[b].half = half;
-    st[b].snorm2 = sn[0];
-  }
   const C al = from_z<C>(make_double2(k.alpha_re, k.alpha_im));
-  const C o = from_z<C>(om);
+  const C o = from_z<C>(make_double2(k.om_re, k.om_im));
   A re = 0, im = 0, rr = 0;
   DBI_PROBLEM_LOOP(sp) {
     const C si = s[off + i];
@@ -413,12 +427,15 @@ static int bicgstab_typed(OpArgs op, const SolverBufs &sb, const void *rhs_, voi
     if ((rc2 = check_launch("k_update_p"))) return rc2;
     op.epi = 1; op.in = p; op.ident = p; op.out = v; op.part_out = sb.partA;
     if ((rc2 = run_operator(op, st))) return rc2;
-    k_update_s<C><<<g2, kRedThreads, 0, st>>>(sp, plist, sb.st, sb.active, nparts, sb.partA, r, v, sv, sb.partS);
+    k_alpha<<<nrun, 32, 0, st>>>(plist, sb.st, sb.active, nparts, sb.partA);
+    if ((rc2 = check_launch("k_alpha"))) return rc2;
+    k_update_s<C><<<g2, kRedThreads, 0, st>>>(sp, plist, sb.st, sb.active, r, v, sv, sb.partS);
     if ((rc2 = check_launch("k_update_s"))) return rc2;
     op.epi = 2; op.in = sv; op.ident = sv; op.out = t; op.part_out = sb.partB;
     if ((rc2 = run_operator(op, st))) return rc2;
-    k_update_xr<C><<<g2, kRedThreads, 0, st>>>(sp, plist, sb.st, sb.active, nparts, sb.partB, sb.partS, o.tol,
-                                                p, sv, t, rhat, x, r, sb.partC);
+    k_omega<<<nrun, 32, 0, st>>>(plist, sb.st, sb.active, nparts, sb.partB, sb.partS, o.tol);
+    if ((rc2 = check_launch("k_omega"))) return rc2;
+    k_update_xr<C><<<g2, kRedThreads, 0, st>>>(sp, plist, sb.st, sb.active, p, sv, t, rhat, x, r, sb.partC);
     if ((rc2 = check_launch("k_update_xr"))) return rc2;
     k_check<<<nrun, 32, 0, st>>>(plist, sb.st, sb.active, sb.counters, parity, sb.partC, o.tol, o.max_iter);
     return check_launch("k_check");
