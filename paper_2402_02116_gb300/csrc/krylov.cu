@@ -127,19 +127,25 @@ __global__ void __launch_bounds__(kRedThreads) k_update_p(Span sp, const int *pl
   if (!active[b]) return;
   const KState k = st[b];
   if (k.restart) {
-    DBI_PROBLEM_LOOP(sp) {
-      const C ri = r[off + i];
-      rhat[off + i] = ri;
-      p[off + i] = ri;
-    }
+    problem_loop_pairs<C>(sp, b, [&]<int N>(size_t o) {
+      C ri[N];
+      ldN(r + o, ri);
+      stN(rhat + o, ri);
+      stN(p + o, ri);
+    });
     return;
   }
   const C be = from_z<C>(make_double2(k.beta_re, k.beta_im));
   const C om = from_z<C>(make_double2(k.om_re, k.om_im));
-  DBI_PROBLEM_LOOP(sp) {
-    const C pv = csub(p[off + i], cmul(om, v[off + i]));
-    p[off + i] = cadd(r[off + i], cmul(be, pv));
-  }
+  problem_loop_pairs<C>(sp, b, [&]<int N>(size_t o) {
+    C pi[N], vi[N], ri[N];
+    ldN(p + o, pi);
+    ldN(v + o, vi);
+    ldN(r + o, ri);
+#pragma unroll
+    for (int n = 0; n < N; ++n) pi[n] = cadd(ri[n], cmul(be, csub(pi[n], cmul(om, vi[n]))));
+    stN(p + o, pi);
+  });
 }
 
 // alpha = rho / <rhat, A p> of every active problem, from the operator's fused partials, once
@@ -169,11 +175,17 @@ __global__ void __launch_bounds__(kRedThreads) k_update_s(Span sp, const int *pl
   if (!active[b]) return;
   const C al = from_z<C>(make_double2(st[b].alpha_re, st[b].alpha_im));
   A ss = 0;
-  DBI_PROBLEM_LOOP(sp) {
-    const C si = csub(r[off + i], cmul(al, v[off + i]));
-    s[off + i] = si;
-    ss += si.x * si.x + si.y * si.y;
-  }
+  problem_loop_pairs<C>(sp, b, [&]<int N>(size_t o) {
+    C ri[N], vi[N];
+    ldN(r + o, ri);
+    ldN(v + o, vi);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      ri[n] = csub(ri[n], cmul(al, vi[n]));
+      ss += ri[n].x * ri[n].x + ri[n].y * ri[n].y;
+    }
+    stN(s + o, ri);
+  });
   A acc[1] = {ss};
   block_sum_store<1>(acc, partS + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
@@ -211,16 +223,25 @@ __global__ void __launch_bounds__(kRedThreads) k_update_xr(Span sp, const int *p
   const C al = from_z<C>(make_double2(k.alpha_re, k.alpha_im));
   const C o = from_z<C>(make_double2(k.om_re, k.om_im));
   A re = 0, im = 0, rr = 0;
-  DBI_PROBLEM_LOOP(sp) {
-    const C si = s[off + i];
-    x[off + i] = cadd(x[off + i], cadd(cmul(al, p[off + i]), cmul(o, si)));
-    const C ri = csub(si, cmul(o, t[off + i]));
-    r[off + i] = ri;
-    const C h = rhat[off + i];
-    re += h.x * ri.x + h.y * ri.y;
-    im += h.x * ri.y - h.y * ri.x;
-    rr += ri.x * ri.x + ri.y * ri.y;
-  }
+  problem_loop_pairs<C>(sp, b, [&]<int N>(size_t e) {
+    C si[N], xi[N], pi[N], ti[N], hi[N];
+    ldN(s + e, si);
+    ldN(x + e, xi);
+    ldN(p + e, pi);
+    ldN(t + e, ti);
+    ldN(rhat + e, hi);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      xi[n] = cadd(xi[n], cadd(cmul(al, pi[n]), cmul(o, si[n])));
+      const C ri = csub(si[n], cmul(o, ti[n]));
+      si[n] = ri;  // (reused as the new residual)
+      re += hi[n].x * ri.x + hi[n].y * ri.y;
+      im += hi[n].x * ri.y - hi[n].y * ri.x;
+      rr += ri.x * ri.x + ri.y * ri.y;
+    }
+    stN(x + e, xi);
+    stN(r + e, si);
+  });
   A acc[3] = {re, im, rr};
   block_sum_store<3>(acc, partC + (size_t(b) * kRedBlocks + blockIdx.x) * kRedSlots);
 }
