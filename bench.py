@@ -387,7 +387,7 @@ def measured_alu_peak(dev, clocks):
 # [nf][3][lx][lz] are read once per launch; the rest grows with the problems a launch processes.
 COLS_DRAM = {
     # one k_cols_split launch over 6 sources x 6 frequencies (profiles/operator_kernels_vti512_6src_6f.md)
-    (512, 512, 1024, 1024): (36, 6, 475_259_648 + 252_412_672),
+    (512, 512, 1024, 1024): (36, 6, 473_260_032 + 252_288_768),
 }
 
 

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_rows_forward_split(OpP<floa
 __global__ void __launch_bounds__(kTileThreads, 2) k_cols_split(OpP<float2> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *smem = reinterpret_cast<float2 *>(smem_raw);
-  float4 *Gs = reinterpret_cast<float4 *>(smem + split_lines_smem() / sizeof(float2));
+  float4 *Gs = reinterpret_cast<float4 *>(smem + split_cols_lines_smem() / sizeof(float2));
   const int g = threadIdx.x / kSplitT, kx = blockIdx.x;
   const int sl0 = 4 * int(blockIdx.y), sl = sl0 + g;
   auto prob = [&](int slot) { return p.plist ? p.plist[p.s0 + slot] : p.s0 + slot; };

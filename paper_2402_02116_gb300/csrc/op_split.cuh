@@ -34,12 +34,18 @@ constexpr int kSplitKP = kSplitL + 4;
 
 // Shared memory (bytes) of the split stages: the lines of one parity (two per row or column) and,
 // for the row stages, the transposition tile of one component.
+// The row stages run the two parities one after the other through two lines per row (one per
+// component); the column stage runs all four lines of a column at once (the twiddle powers formed
+// once, half the barriers: measured faster there and slower in the row stages).
 __host__ __device__ constexpr size_t split_lines_smem() { return size_t(2) * kSplitRows * kSplitLP * sizeof(float2); }
+__host__ __device__ constexpr size_t split_cols_lines_smem() {
+  return size_t(4) * kSplitRows * kSplitLP * sizeof(float2);
+}
 __host__ __device__ constexpr size_t split_tile_smem() { return size_t(kSplitRows) * kSplitKP * sizeof(float2); }
 __host__ __device__ constexpr size_t split_rows_smem() {
   return split_lines_smem() > split_tile_smem() ? split_lines_smem() : split_tile_smem();
 }
-__host__ __device__ constexpr size_t split_cols_smem() { return split_lines_smem(); }
+__host__ __device__ constexpr size_t split_cols_smem() { return split_cols_lines_smem(); }
 // The inverse row stage stages the tiles of both components at once: [2][rows][KP].
 __host__ __device__ constexpr size_t split_rows_inverse_smem() {
   return split_lines_smem() > 2 * split_tile_smem() ? split_lines_smem() : 2 * split_tile_smem();
@@ -169,7 +175,8 @@ struct SplitLines {
   float2 *l[2][2];
 };
 
-// Forward M-point transforms of both parities (one exchange set per parity).
+// M-point transforms of both parities, one parity at a time through the two lines of the
+// components (the row stages).
 template <bool INV, typename Sync>
 __device__ __forceinline__ void split_fft(float2 (&v)[2][2][8], float2 *const (&lines)[2], int t,
                                           const TwReg<float2, kSplitM, 0> &tr, Sync &&sync) {
@@ -177,11 +184,19 @@ __device__ __forceinline__ void split_fft(float2 (&v)[2][2][8], float2 *const (&
   for (int q = 0; q < 2; ++q) RegPlan<kSplitM, 0>::template run<float2, 2, INV>(v[q], lines, t, tr, sync);
 }
 
+// M-point transforms of both parities and both components at once, four lines through one
+// exchange set (the column stage).
+template <bool INV, typename Sync>
+__device__ __forceinline__ void split_fft4(float2 (&v)[2][2][8], float2 *const (&lines)[4], int t,
+                                           const TwReg<float2, kSplitM, 0> &tr, Sync &&sync) {
+  RegPlan<kSplitM, 0>::template run<float2, 4, INV>(reinterpret_cast<float2(&)[4][8]>(v), lines, t, tr, sync);
+}
+
 
 // Shared memory of the column stage with the column's Green's tables staged: the lines, then
 // Ghat(:, kx) of the three tables [3][L].
 __host__ __device__ constexpr size_t split_cols_staged_smem() {
-  return split_lines_smem() + size_t(3) * kSplitL * sizeof(float2);
+  return split_cols_lines_smem() + size_t(3) * kSplitL * sizeof(float2);
 }
 
 // Column kx of one problem, by the 64 threads of group g of the CTA (named barrier 1 + g): the
@@ -194,13 +209,15 @@ template <bool STAGED, typename A>
 __device__ __forceinline__ void cols_column_split(const A &a, int kx, int g, bool live, float2 *smem,
                                                   const float4 *Gs) {
   using C = float2;
-  constexpr int T = kSplitT, CC = kSplitRows, LP = kSplitLP;
+  constexpr int T = kSplitT, CC = kSplitRows;
   const int t = threadIdx.x - g * T;
   const int nz = a.nz(), lx = a.lx();
   const C *tw = a.tw();
   C *c0 = a.T() + size_t(kx) * nz, *c1 = a.T() + (size_t(lx) + kx) * nz;
   const TwReg<C, kSplitM, 0> tr(t, tw);
-  C *const lines[2] = {smem + size_t(g) * LP, smem + size_t(CC + g) * LP};
+  C *lines[4];  // (parity q, component c) of column group g
+#pragma unroll
+  for (int l = 0; l < 4; ++l) lines[l] = smem + size_t(l * CC + g) * kSplitLP;
   C v[2][2][8];
   if (live) {
 #pragma unroll
@@ -214,7 +231,7 @@ __device__ __forceinline__ void cols_column_split(const A &a, int kx, int g, boo
       v[1][0][m] = hmul(x0, w);
       v[1][1][m] = hmul(x1, w);
     }
-    split_fft<false>(v, lines, t, tr, RowSync<T>{1 + g});
+    split_fft4<false>(v, lines, t, tr, RowSync<T>{1 + g});
   }
   if constexpr (STAGED) {
     cp_async_wait_all();
@@ -244,7 +261,7 @@ __device__ __forceinline__ void cols_column_split(const A &a, int kx, int g, boo
       }
     }
   }
-  split_fft<true>(v, lines, t, tr, RowSync<T>{1 + g});
+  split_fft4<true>(v, lines, t, tr, RowSync<T>{1 + g});
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int z = t + m * T;
@@ -270,7 +287,7 @@ template <typename A>
 __device__ __forceinline__ void rows_forward_tile_split(const A &a, int tile, float2 *smem, const float2 *src,
                                                         float scale) {
   using C = float2;
-  constexpr int T = kSplitT, ROWS = kSplitRows, LP = kSplitLP, KP = kSplitKP;
+  constexpr int T = kSplitT, ROWS = kSplitRows, KP = kSplitKP;
   const int z0 = tile * ROWS;
   const int nz = a.nz(), nx = a.nx();
   const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
@@ -290,7 +307,7 @@ __device__ __forceinline__ void rows_forward_tile_split(const A &a, int tile, fl
     v[1][0][m] = hmul(s0, w);
     v[1][1][m] = hmul(s1, w);
   }
-  C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
+  C *const lines[2] = {smem + size_t(rr) * kSplitLP, smem + size_t(ROWS + rr) * kSplitLP};
   split_fft<false>(v, lines, t, tr, RowSync<T>{1 + rr});
   // transpose one component at a time through tile[rr][kx] (the lines' memory is free now)
 #pragma unroll
@@ -317,7 +334,7 @@ __device__ __forceinline__ void rows_forward_tile_split(const A &a, int tile, fl
 template <int EPI, typename A>
 __device__ __forceinline__ void rows_inverse_tile_split(const A &a, int tile, float2 *smem) {
   using C = float2;
-  constexpr int T = kSplitT, ROWS = kSplitRows, LP = kSplitLP, KP = kSplitKP;
+  constexpr int T = kSplitT, ROWS = kSplitRows, KP = kSplitKP;
   const int z0 = tile * ROWS;
   const int nz = a.nz(), nx = a.nx();
   const int rr = threadIdx.x / T, t = threadIdx.x - rr * T, z = z0 + rr;
@@ -351,7 +368,7 @@ __device__ __forceinline__ void rows_inverse_tile_split(const A &a, int tile, fl
     }
   }
   __syncthreads();  // the lines reuse the tile's memory
-  C *const lines[2] = {smem + size_t(rr) * LP, smem + size_t(ROWS + rr) * LP};
+  C *const lines[2] = {smem + size_t(rr) * kSplitLP, smem + size_t(ROWS + rr) * kSplitLP};
   split_fft<true>(v, lines, t, tr, RowSync<T>{1 + rr});
   C y[2][8];
 #pragma unroll
