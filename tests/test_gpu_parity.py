@@ -496,3 +496,24 @@ def test_length_768_products():
     lhs = np.real(np.vdot(R, Jd))
     rhs = np.sum(npy(P.to_model(dm)).astype(np.float64) * g)
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+def test_length_768_largest_grid():
+    """384 x 384 VTI cells on the 768 x 768 FFT grid (the largest grid length 768 serves), two
+    frequencies: the operator against the oracle, and the solver's fused kernels on the same grid,
+    whose solution the FP64 oracle's operator confirms by its residual."""
+    w = inputs.small_case(nz=384, nx=384, lz=768, lx=768, n_src=1, freqs=(6.0, 14.0), amp=0.1, h=5.0,
+                          vti=True, seed=12)
+    P = DeviceProblem(w, dbi.C64)
+    orc = oracle_for(w)
+    u = inputs.seeded_complex((P.B, 2, 384, 384), 79)
+    out = npy(P.apply(P.to_field(u)))
+    for b, f in enumerate(w.problem_fidx()):
+        want = orc.apply(u[b], w.model, f)
+        assert rel(out[b] - u[b], want - u[b]) < TOL[dbi.C64], b
+    u0 = P.incident()
+    x, _, _, code = P.solve(u0, tol=1e-5)
+    assert np.all(npy(code) == dbi.CONVERGED)
+    xs, bs = npy(x).astype(np.complex128), npy(u0).astype(np.complex128)
+    for b, f in enumerate(w.problem_fidx()):
+        assert rel(orc.apply(xs[b], w.model, f), bs[b]) < 3e-5, b
