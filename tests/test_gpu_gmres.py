@@ -87,6 +87,28 @@ def test_solution_matches_oracle(precision, restart, shape):
         assert rel(npy(u[q]), want) < (1e-8 if precision == dbi.C128 else 1e-5), q
 
 
+# GMRES over the complex64 stages of FFT lengths 1024 (pairs of 512-point transforms) and 768
+# (triples of 256-point transforms), whose kernels complex128 does not use.
+SPLIT_SHAPES = [
+    dict(nz=37, nx=300, lz=1024, lx=1024),
+    dict(nz=37, nx=300, lz=768, lx=768),
+    dict(nz=130, nx=45, lz=768, lx=128, vti=True),
+]
+
+
+@pytest.mark.parametrize("shape", SPLIT_SHAPES, ids=lambda s: f"{s['nz']}x{s['nx']}_L{s['lz']}x{s['lx']}")
+def test_solution_on_the_split_stages_matches_oracle(shape):
+    w = inputs.small_case(freqs=(6.0, 13.0), n_src=1, **shape)
+    P = DeviceProblem(w, dbi.C64)
+    u, iters, relres, code = P.solve_gmres(P.incident(), restart=30, tol=1e-6, max_iter=800, check_every=4)
+    assert bool((code == dbi.CONVERGED).all()) and float(relres.max()) <= 1e-6
+    orc = oracle_for(w)
+    fidx, srcs = w.problem_fidx(), w.problem_src()
+    for q in range(P.B):
+        u0 = orc.incident(fidx[q], w.src_cells[srcs[q]], w.src_force[srcs[q]])
+        assert rel(npy(u[q]), orc.solve(u0, w.model, fidx[q], tol=1e-13)) < 1e-5, q
+
+
 def test_restart_matches_the_oracle_restart_count():
     """GMRES(4) in complex128: the same number of Arnoldi steps to the tolerance as the oracle's
     GMRES(4) (the iterates agree to rounding cycle by cycle), and the same solution."""

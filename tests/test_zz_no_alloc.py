@@ -43,6 +43,22 @@ def test_noalloc_matches_ls_apply_on_consecutive_calls():
     assert _rel(got, want) < 1e-12
 
 
+@pytest.mark.parametrize("lz,lx", [(1024, 1024), (768, 768)])
+def test_noalloc_on_the_split_stages(lz, lx):
+    """The complex64 stages of FFT lengths 1024 and 768 (the contrast-source kernel's scratch and
+    the split row and column kernels) through the fixed array: the same result as ls_apply."""
+    build.build()
+    dbi.load()
+    w = inputs.small_case(nz=37, nx=300, lz=lz, lx=lx, n_src=1, freqs=(6.0, 13.0), amp=0.12, seed=6)
+    P = DeviceProblem(w, dbi.C64)
+    assert dbi.workspace_bytes(P.grid, P.B, dbi.C64, dbi.OP_APPLY) <= dbi.noalloc_scratch_bytes()
+    u = P.to_field(inputs.seeded_complex((P.B, 2, w.nz, w.nx), 24))
+    want = dbi.ls_apply(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u)
+    got = dbi.ls_apply_noalloc(P.grid, P.ref, P.m, P.omega, P.fidx, P.Ghat, u)
+    torch.cuda.synchronize()
+    assert _rel(got, want) < 1e-6
+
+
 def test_noalloc_rejects_a_batch_beyond_the_array():
     build.build()
     w = inputs.config2_batched_forward(n=256, n_src=4, nf=8)  # 32 problems of 256 x 256
