@@ -1,7 +1,8 @@
 """Failure detection on the GPU without a GPU fault: NaN injected on the host into one problem's
 right-hand side, into the model, or into the data residual of the adjoint stops the affected
 problems with DBI_NONFINITE within one iteration (the others converge as before), for BiCGSTAB and
-GMRES in both precisions; nothing hangs and the context stays usable (a clean solve follows)."""
+GMRES in both precisions and on the complex64 stages of FFT lengths 1024 and 768; nothing hangs
+and the context stays usable (a clean solve follows)."""
 import numpy as np
 import pytest
 import torch
@@ -23,10 +24,15 @@ def npy(t):
     return t.detach().cpu().numpy()
 
 
-@pytest.fixture(params=[dbi.C64, dbi.C128], ids=["c64", "c128"])
+# (precision, FFT grid): the default grid, and in complex64 the stages of FFT lengths 1024 (pairs of
+# 512-point transforms) and 768 (triples of 256-point transforms) with their contrast-source kernel
+@pytest.fixture(params=[(dbi.C64, None), (dbi.C128, None), (dbi.C64, 1024), (dbi.C64, 768)],
+                ids=["c64", "c128", "c64_L1024", "c64_L768"])
 def problem(request):
-    w = inputs.small_case(nz=20, nx=16, n_src=2, freqs=(7.0, 11.0), vti=True, amp=0.12, seed=8)
-    return DeviceProblem(w, request.param)
+    precision, L = request.param
+    grid = {} if L is None else dict(lz=L, lx=L)
+    w = inputs.small_case(nz=20, nx=16, n_src=2, freqs=(7.0, 11.0), vti=True, amp=0.12, seed=8, **grid)
+    return DeviceProblem(w, precision)
 
 
 @pytest.mark.parametrize("solver", ["bicgstab", "gmres"])
