@@ -284,6 +284,34 @@ def test_normal_cg(precision):
     assert hist[-1] < 0.2 * hist[0]
 
 
+@pytest.mark.parametrize("lz,lx", [(1024, 16), (768, 32)])
+def test_normal_cg_on_the_split_stages(lz, lx):
+    """The Tikhonov normal-equation CG (Frechet and adjoint solves in every step) on the complex64
+    stages of FFT lengths 1024 and 768: the normal-equation residual of the GPU's 12th iterate,
+    evaluated by the FP64 oracle, is as small as that of the oracle's own iterate."""
+    w = inputs.small_case(nz=8, nx=7, lz=lz, lx=lx, amp=0.1, vti=True, n_src=2, freqs=(8.0, 13.0), seed=41)
+    P = DeviceProblem(w, dbi.C64)
+    orc = oracle_for(w)
+    fidx = w.problem_fidx()
+    U = orc.forward(w.model, fidx, w.src_cells[w.problem_src()], w.src_force[w.problem_src()])
+    dd = inputs.seeded_complex((len(fidx), len(w.rec_cells), 2), 17) * 1e-12
+    start = inputs.seeded_real((5, w.nz, w.nx), 18)
+    dm, lam, hist = P.normal_cg(P.to_field(U), P.to_field(dd), iters=12, power_start=start, tol=1e-7)
+    want, lam_o, _ = orc.normal_cg(w.model, U, fidx, dd, w.rec_cells, iters=12, power_start=start)
+    assert abs(lam - lam_o) / lam_o < 5e-4
+    sc = orc.param_scale()[:, None, None]
+
+    def normal_residual(dmv):
+        x = dmv / sc
+        Hx = sc * orc.adjoint(w.model, U, fidx, orc.frechet(w.model, U, fidx, sc * x, w.rec_cells), w.rec_cells)
+        rhs = sc * orc.adjoint(w.model, U, fidx, dd, w.rec_cells)
+        return np.linalg.norm(rhs - Hx - lam_o * x), np.linalg.norm(rhs)
+
+    r_gpu, r0 = normal_residual(npy(dm).astype(np.float64))
+    r_orc, _ = normal_residual(want)
+    assert r_gpu < 1.3 * r_orc and r_gpu < 0.2 * r0, (r_gpu / r0, r_orc / r0)
+
+
 # --- the batched-forward workload at full size, in the benchmark's launch configuration --------
 @pytest.fixture(scope="module")
 def config2():
