@@ -7,8 +7,9 @@
 // orders, forward (with and without the zero-half first pass) and inverse, complex64 and
 // complex128. The line buffer carries guard slots on both sides that must stay untouched.
 //
-// Lines per thread group: 1, and 2 and 3 (the kernels transform a column's components together,
-// sharing the twiddle powers), each line with its own input.
+// Lines per thread group: 1, and 2, 3 and 4 (the kernels transform a column's components together,
+// sharing the twiddle powers; at FFT length 1024 the column stage runs both parities of both
+// components, four 512-point lines, through one exchange set), each line with its own input.
 //
 // Usage: fft_reg_host <out.bin>. For every line the file holds a header of six int32 values
 // (precision bytes, L, V, INV, HIN, lines of the group) followed by the input and the output of
@@ -119,6 +120,8 @@ template <typename C, int L> bool run_length(FILE *f, const std::vector<C> &tw, 
   ok &= run_case<C, L, 1, true, false, 2>(f, tw, ++seed);
   ok &= run_case<C, L, 0, false, true, 3>(f, tw, ++seed);
   ok &= run_case<C, L, 0, true, false, 3>(f, tw, ++seed);
+  ok &= run_case<C, L, 0, false, false, 4>(f, tw, ++seed);
+  ok &= run_case<C, L, 0, true, false, 4>(f, tw, ++seed);
   return ok;
 }
 

@@ -5,10 +5,11 @@ and runs every line with one std::thread per GPU lane and a std::barrier for the
 barrier. The outputs must equal numpy's FFT (the definition of the DFT: exp(-2 pi i jk/L) forward,
 exp(+2 pi i jk/L) inverse, unnormalised) to the rounding of the precision, for every supported
 length, both radix orders, the zero-half first pass and the inverse, with one line per thread
-group and with two and three lines sharing the group's twiddle powers (as the column passes
-transform a column's components together); two runs must agree bit for
-bit (a missing barrier between the lanes' stores and loads shows up as a run-to-run difference);
-and the guard slots around each line must stay untouched (the harness checks them)."""
+group and with two, three and four lines sharing the group's twiddle powers (as the column passes
+transform a column's components, and at FFT length 1024 both parities of both, together); two
+runs must agree bit for bit (a missing barrier between the lanes' stores and loads shows up as a
+run-to-run difference); and the guard slots around each line must stay untouched (the harness
+checks them)."""
 import os
 import shutil
 import subprocess
@@ -64,7 +65,7 @@ def test_register_plans_equal_the_dft(harness):
     exe, out = harness
     cases = _cases(_run(exe, out / "a.bin"))
     lengths = (16, 32, 64, 128, 256, 512, 1024)
-    assert len(cases) == 2 * len(lengths) * (6 + 2 * 2 + 2 * 3)
+    assert len(cases) == 2 * len(lengths) * (6 + 2 * 2 + 2 * 3 + 2 * 4)
     seen = set()
     for cb, L, V, inv, hin, nlt, x, y in cases:
         seen.add((cb, L, V, inv, hin, nlt))
@@ -76,7 +77,8 @@ def test_register_plans_equal_the_dft(harness):
     single = {(cb, L, V, inv, hin, 1) for cb in (8, 16) for L in lengths for V in (0, 1)
               for inv, hin in ((False, False), (False, True), (True, False))}
     grouped = {(cb, L, V, inv, hin, n) for cb in (8, 16) for L in lengths
-               for V, inv, hin, n in ((0, False, True, 2), (1, True, False, 2), (0, False, True, 3), (0, True, False, 3))}
+               for V, inv, hin, n in ((0, False, True, 2), (1, True, False, 2), (0, False, True, 3), (0, True, False, 3),
+                                   (0, False, False, 4), (0, True, False, 4))}
     assert seen == single | grouped
 
 
