@@ -318,6 +318,8 @@ def run_ours(args):
     solo = rank == 0 and world == 1
     if solo:
         result["operator_hbm"] = operator_stages(P, w, dev)
+        result["path_roofline"] = path_roofline(w, result["operator_hbm"]["stages"]["pass"]["us_per_problem"],
+                                                value, fp32["tflops"], result["operator_hbm"]["hbm_peak_gbs"])
     if solo and not args.no_cufft:
         result["cufft_c64"] = cufft_comparator(P, w, dev)
     if solo and not args.no_plain:
@@ -672,6 +674,42 @@ def cols_flops_per_cell_apply(w):
     fft = 2 * 2 * w.lx * 5 * w.lz * math.log2(w.lz)
     mult = 28 * w.lz * w.lx
     return (fft + mult) / cells
+
+
+def pass_flops_per_cell_apply(w):
+    """Nominal flops of one operator pass: 5 L log2 L per complex FFT (the rows forward and inverse
+    over the nz non-zero rows, 2 components each; the columns forward and inverse over all lx
+    columns, 2 components each) plus the symmetric 2x2 Green's multiply (28 flops per wavenumber).
+    The stencil, the contrast contraction and the epilogue (a few dozen flops per cell) are left
+    out."""
+    rows = 2 * 2 * w.nz * 5 * w.lx * math.log2(w.lx)
+    return rows / (w.nz * w.nx) + cols_flops_per_cell_apply(w)
+
+
+def compulsory_bytes_per_cell_apply(w):
+    """Bytes one operator pass cannot avoid (complex64): the input field read and the output field
+    written (16 B each per cell), the Green's spectra [3][lz][lx] once per frequency and the five
+    float32 contrast parameters once per batch."""
+    cells = w.nz * w.nx
+    return 16 + 16 + 3 * w.lz * w.lx * 8 * w.nf / (w.n_problems * cells) + 20 / w.n_problems
+
+
+def path_roofline(w, pass_us_per_problem, step_value, fp32_tflops, hbm_gbs):
+    """The operator pass and the whole gradient step against the path's own roofline: cell-applies
+    per second ÷ min(HBM bandwidth / compulsory bytes, FP32 peak / pass flops), both per
+    cell-apply. With every transpose on chip the pass would be bound by the smaller of the two; the
+    built pass moves its spectra through HBM between stages (operator_hbm gives that fraction)."""
+    flops = pass_flops_per_cell_apply(w)
+    byts = compulsory_bytes_per_cell_apply(w)
+    alu = fp32_tflops * 1e12 / flops
+    hbm = hbm_gbs * 1e9 / byts
+    bound = min(alu, hbm)
+    achieved = w.nz * w.nx / (pass_us_per_problem * 1e-6)
+    return {"flops_per_cell_apply": flops, "compulsory_bytes_per_cell_apply": byts,
+            "alu_bound": alu, "hbm_bound": hbm, "bound": "alu" if alu <= hbm else "hbm",
+            "unit": "cell-applies/s", "pass_achieved": achieved, "pass_frac": achieved / bound,
+            "step_frac": step_value / bound,
+            "peaks": {"fp32_tflops": fp32_tflops, "hbm_gbs": hbm_gbs, "source": "measured (FMA probe; copy)"}}
 
 
 def load_peaks():

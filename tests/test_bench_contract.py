@@ -146,3 +146,21 @@ def test_operator_stage_bytes():
     assert b == {"rows_forward": 80.0, "cols": 64.0 + 96 * 6 / 384, "rows_inverse": 64.0}
     b = bench.operator_stage_bytes(bench.workload("vti256"))
     assert b == {"rows_forward": 48.0, "cols": 64.0 + 96 * 8 / 256, "rows_inverse": 64.0}
+
+
+def test_path_roofline_units_and_bound():
+    """The path's own roofline on the 512^2 workload (L = 1024, 384 problems, 6 frequencies), by hand:
+    rows forward and inverse over 512 rows, 2 components, 5 * 1024 * 10 flops each = 400 per cell;
+    the columns 912 (as for the column kernel); compulsory bytes u 16 + out 16 + the Green's spectra
+    3 * 1024^2 * 8 * 6 / (384 * 512^2) = 1.5 + the contrast 20 / 384."""
+    w = bench.workload("vti512")
+    assert bench.pass_flops_per_cell_apply(w) == pytest.approx(1312.0, rel=1e-12)
+    assert bench.compulsory_bytes_per_cell_apply(w) == pytest.approx(33.5 + 20 / 384, rel=1e-12)
+    # 1312 flops at 65.6 TFLOP/s: 5e10 cell-applies/s; 33.55 B at 6710 GB/s: 2e11, so the ALU bounds it
+    r = bench.path_roofline(w, 262_144 / 2.5e10 * 1e6, 1.0e10, 65.6, 6710.0)
+    assert r["bound"] == "alu" and r["alu_bound"] == pytest.approx(5e10, rel=1e-12)
+    assert r["pass_achieved"] == pytest.approx(2.5e10, rel=1e-12)
+    assert r["pass_frac"] == pytest.approx(0.5, rel=1e-12) and r["step_frac"] == pytest.approx(0.2, rel=1e-12)
+    # with a slow memory the HBM side bounds it
+    r = bench.path_roofline(w, 10.0, 1.0e9, 65.6, 100.0)
+    assert r["bound"] == "hbm" and r["hbm_bound"] == pytest.approx(100e9 / (33.5 + 20 / 384), rel=1e-12)
