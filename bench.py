@@ -17,6 +17,7 @@ gradient against the FP64 CPU oracle, and the oracle's own rate on the host core
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --workload vti256       # the 256^2 gradient step alone
     python bench.py --workload uneven40     # the 40-problem uneven batch (grids 64^2 .. 512^2)
+    python bench.py --workload op384        # operator passes over 384^2 problems on FFT length 768
     python bench.py --workload formk256     # operator passes in the paper-literal form of Eq. 9
     python bench.py --workload gmres256     # batched forward solves by GMRES(30) beside BiCGSTAB
     python bench.py --workload hess3d       # 3D operator passes and GMRES solves, 80 x 40 x 32 cells
