@@ -19,6 +19,9 @@
  *     `work_bytes` bytes, sized by dbi_workspace_bytes(). A call may use all of it.
  *   - Complex arrays hold interleaved (re, im) pairs: float2 for DBI_C64, double2 for DBI_C128.
  *     Real model-space arrays (m, dm, g) are float for DBI_C64 and double for DBI_C128.
+ *   - Complex arrays and the work buffer must start on a 16-byte boundary (cudaMalloc gives 256):
+ *     the kernels move complex64 values in 16-byte pairs and Green's tables by 16-byte loads and
+ *     copies. The library does not check this; a misaligned start is a device fault.
  *   - Wavefields are C-contiguous [B][2][nz][nx] (component 0 = u1, 1 = u3); receiver data are
  *     [B][n_rec][2]; model-space arrays are [5][nz][nx] in the order rho, C11, C13, C33, C55.
  *   - Problem b has angular frequency omega[fidx[b]] and uses Green's table fidx[b].

@@ -213,10 +213,34 @@ def complex_dtype(precision: int):
     return torch.complex64 if precision == C64 else torch.complex128
 
 
+def _aligned16(name, t):
+    """The kernels read and write complex64 fields and tables, and the work buffer's carves, with
+    16-byte accesses (pairs of complex64 values, 16-byte table loads and asynchronous copies), which
+    a misaligned address turns into a device fault. PyTorch's allocations are aligned; a view whose
+    storage offset moves its start off a 16-byte boundary is an error here."""
+    if t.numel() and t.data_ptr() % 16:
+        raise DBIError(f"{name} starts at an address that is not a multiple of 16 bytes (storage offset "
+                       f"{t.storage_offset()}); the kernels need 16-byte aligned complex and work buffers")
+
+
 def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and t.is_complex():
+            _aligned16("a complex tensor", t)
     for t in ts:
         if t is not None and (not t.is_cuda or not t.is_contiguous()):
             raise DBIError("every tensor must be a contiguous CUDA tensor")
+
+
+def _caller_work(work, device) -> int:
+    """A work buffer supplied by the caller: a contiguous tensor on the call's device, 16-byte
+    aligned; returns its size in bytes (the library checks that it covers the call's carves)."""
+    if not isinstance(work, torch.Tensor):
+        raise DBIError("work must be a torch tensor")
+    _aligned16("work", work)
+    if not work.is_cuda or not work.is_contiguous() or work.device != device:
+        raise DBIError(f"work must be a contiguous CUDA tensor on {device}")
+    return work.numel() * work.element_size()
 
 
 def _fields(fidx, comps: int, cells: int, dtype, **named) -> list:
@@ -414,7 +438,7 @@ def ls_apply(grid: Grid, ref: Medium, m, omega, fidx, Ghat, u, out=None, work=No
     if work is None:
         work, n = _work(grid, batch.B, precision, OP_APPLY, u.device)
     else:
-        n = work.numel()
+        n = _caller_work(work, u.device)
     _check(load().ls_apply(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(u), _ptr(out), precision,
                            _ptr(work), n, _stream(u.device)), "ls_apply")
     return out
@@ -456,7 +480,7 @@ def ls_solve(grid: Grid, ref: Medium, m, omega, fidx, Ghat, rhs, u0=None, tol=1e
     if work is None:
         work, n = _work(grid, batch.B, precision, OP_SOLVE, rhs.device)
     else:
-        n = work.numel()
+        n = _caller_work(work, rhs.device)
     (iters, relres, code), st = _status(batch.B, rhs.device)
     opts = _kopts(tol, max_iter, check_every, zero_guess=u0 is None)
     _check(load().ls_solve(ctypes.byref(model), ctypes.byref(batch), _ptr(Ghat), _ptr(rhs), _ptr(u),

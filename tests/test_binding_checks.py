@@ -143,3 +143,37 @@ def test_dtypes_and_tables_are_checked_before_the_device(name, call, good, bad, 
         call(bad)
     with pytest.raises(dbi.DBIError, match="CUDA tensor"):
         call(good)
+
+
+def test_misaligned_complex_tensors_are_errors_before_the_device():
+    """A complex view whose start is off a 16-byte boundary (the kernels read complex64 pairs and
+    Green's tables with 16-byte loads, which would fault there) is rejected before any device work,
+    as a field, an output and a table; an aligned tensor gets as far as the CUDA check."""
+    g, ref, m, om, fi, G, rec = common2d()
+    u = f(B, 2, NZ, NX)
+    shifted = torch.zeros(u.numel() + 1, dtype=torch.complex64)[1:].view(B, 2, NZ, NX)
+    assert shifted.data_ptr() % 16 == 8
+    Gs = torch.zeros(G.numel() + 1, dtype=torch.complex64)[1:].view(G.shape)
+    for call in (lambda: dbi.ls_apply(g, ref, m, om, fi, G, shifted),
+                 lambda: dbi.ls_apply(g, ref, m, om, fi, G, u, out=shifted),
+                 lambda: dbi.ls_solve(g, ref, m, om, fi, G, shifted),
+                 lambda: dbi.ls_solve_gmres(g, ref, m, om, fi, G, shifted),
+                 lambda: dbi.green_convolve(g, om, fi, G, shifted),
+                 lambda: dbi.ls_apply(g, ref, m, om, fi, Gs, u),
+                 lambda: dbi.ls_solve(g, ref, m, om, fi, Gs, u)):
+        with pytest.raises(dbi.DBIError, match="multiple of 16 bytes"):
+            call()
+    with pytest.raises(dbi.DBIError, match="CUDA tensor"):
+        dbi.ls_apply(g, ref, m, om, fi, G, u)
+
+
+def test_caller_work_buffers_are_checked():
+    """A work buffer the caller passes to ls_apply / ls_solve must be a contiguous, 16-byte aligned
+    tensor on the call's device; its size is counted in bytes whatever its element type."""
+    dev = torch.device("cuda", 0)
+    with pytest.raises(dbi.DBIError, match="multiple of 16 bytes"):
+        dbi._caller_work(torch.zeros(65, dtype=torch.uint8)[1:], dev)
+    with pytest.raises(dbi.DBIError, match="CUDA tensor"):
+        dbi._caller_work(torch.zeros(64, dtype=torch.uint8), dev)
+    with pytest.raises(dbi.DBIError, match="torch tensor"):
+        dbi._caller_work(bytearray(64), dev)
